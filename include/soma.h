@@ -1,0 +1,202 @@
+/*
+ * soma.h -- C ABI of libsoma: single-chain-in-mean-field (SCMF) Monte-Carlo
+ * simulation of soft, coarse-grained diblock copolymer melts on one GB300
+ * (sm_103a), after "SOMA: Soft coarse grained Monte-Carlo Acceleration"
+ * (arXiv:1711.03828).
+ *
+ * One SCMF cycle (Sec. 2.2 of the paper) is
+ *   1. an independent-set Monte-Carlo step of every particle against frozen
+ *      quasi-instantaneous fields omega_t(c) (Sec. 2.2 move + Eq. delta-e; the
+ *      "SET" iteration of Sec. 3.1.2: even then odd chain positions, or the
+ *      reverse, the order drawn per chain and step),
+ *   2. the integer occupation numbers n_t(c) on the collocation grid
+ *      (Eq. density-characteristics, Sec. 3.1.1),
+ *   3. the field update omega_A/B (Eq. omega-fields, option K^0).
+ *
+ * Units and layout (fixed for every entry point):
+ *   - lengths are in units of the grid spacing dL; the grid is cubic
+ *     (Sec. 2.1), so box_Re[d] / grid[d] must agree on the three axes;
+ *   - positions are FP32, structure of arrays: one buffer of 3*M floats holds
+ *     x[0..M), y[0..M), z[0..M); particle m = chain*N + i; positions are
+ *     unwrapped (periodic images are folded only to find the cell);
+ *   - particle i of a chain is type A iff i < N_A = floor(f*N + 1/2);
+ *   - the cell of a position is (floor(x) mod grid_x, ...), index
+ *     (cz*grid_y + cy)*grid_x + cx;
+ *   - occupation numbers are packed per cell: n_A in bits 0..15, n_B in bits
+ *     16..31 (the paper stores them as 16-bit integers, Sec. 3.1.1);
+ *   - omega_t(c) is the per-particle field energy in kT of Eq. (omega-fields):
+ *     omega_A/B = (kappaN/N)(phi_A + phi_B - 1) -/+ (chiN/(2N))(phi_A - phi_B),
+ *     phi_t = n_t / (rho_0 dL^3), rho_0 dL^3 = M / cells.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11) with counter
+ * (id lo32, id hi32, w, purpose<<24 | replica_id) and key (seed lo32, seed
+ * hi32); a move of particle m in sweep s uses purpose 1, id m, w s.  There is
+ * no generator state (the paper's Sec. 3.2.3 stores a PCG state per thread).
+ *
+ * Execution: every call is asynchronous on the handle's stream unless it says
+ * otherwise; calls that return data to the host synchronise that stream.  No
+ * call aborts the process: each returns a soma_status, and soma_last_error()
+ * gives a message for the calling thread.  Device-side conditions (a 16-bit
+ * count saturating) are recorded in a sticky device word and reported by the
+ * next synchronising call.
+ *
+ * Ownership: a soma_t owns every device buffer it allocates (in soma_create)
+ * and frees them in soma_destroy.  Buffers passed by the caller are borrowed
+ * for the duration of the call and never retained.
+ */
+#ifndef SOMA_H
+#define SOMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SOMA_ABI_VERSION 1
+
+typedef enum {
+  SOMA_OK = 0,
+  SOMA_EINVAL = -1,     /* invalid argument or description; nothing was done */
+  SOMA_ENOMEM = -2,     /* a device or host allocation failed */
+  SOMA_ECUDA = -3,      /* a CUDA runtime call failed (message in soma_last_error) */
+  SOMA_EOVERFLOW = -4,  /* a 16-bit occupation number reached 0xC000 (sticky) */
+  SOMA_ETIMEOUT = -5,   /* a bounded device wait gave up (sticky) */
+  SOMA_ESTATE = -6      /* call not valid in the handle's current state */
+} soma_status;
+
+typedef enum { SOMA_MOVE_UNIFORM = 0, SOMA_MOVE_SMC = 1 } soma_move;
+typedef enum { SOMA_SET_ORDER_RANDOM = 0, SOMA_SET_ORDER_FIXED = 1 } soma_set_order;
+typedef enum { SOMA_GRID_F32 = 0, SOMA_GRID_BF16 = 1, SOMA_GRID_F16 = 2 } soma_grid_dtype;
+
+/* Description of one system: a melt of n_chains linear A-B diblock chains.
+ * struct_size must be sizeof(soma_system_desc) (ABI versioning). */
+typedef struct soma_system_desc {
+  uint32_t struct_size;
+  uint32_t N;            /* particles per chain, 1..256 */
+  uint64_t n_chains;     /* >= 1; M = n_chains*N < 2^40 */
+  double f;              /* A fraction of a chain, 0..1 */
+  double box_Re[3];      /* box edges in units of R_e0 (> 0) */
+  uint32_t grid[3];      /* cells per axis, 1..4096; dL = box/grid equal on all axes */
+  uint32_t reserved0;
+  double chiN;           /* Flory-Huggins chi_0 N (Eq. hamil-pair) */
+  double kappaN;         /* inverse compressibility kappa_0 N (Eq. hamil-comp) */
+  double a_Re;           /* maximal trial displacement per axis in R_e0;
+                            <= 0 selects 0.5/sqrt(N-1) (0.5 for N = 1) */
+  int32_t move;          /* soma_move */
+  int32_t set_order;     /* soma_set_order */
+  int32_t grid_dtype;    /* soma_grid_dtype: storage type of omega */
+  int32_t flags;         /* must be 0 */
+  uint64_t seed;         /* Philox key */
+  uint32_t replica_id;   /* Philox counter word 3, low 24 bits */
+  uint32_t reserved1;
+  void* stream;          /* cudaStream_t to run on; NULL: the handle creates its own */
+} soma_system_desc;
+
+typedef struct soma_t soma_t;
+
+/* Observables, reduced in FP64 on the device.  Energies in kT, lengths in dL. */
+typedef struct soma_obs {
+  double E_b;        /* sum over bonds of (k0/2)|b|^2, Eq. (h-bond), (V-harmonic) */
+  double E_nb;       /* Eq. (discrete-ham) with K_fluc + K^0_inter of the current n */
+  double E_tot;      /* E_b + E_nb */
+  double Re2;        /* mean over chains of |r_{N-1} - r_0|^2 */
+  double Re2_rel;    /* Re2 / R_e0^2 */
+  double b2;         /* mean over bonds of |r_{i+1} - r_i|^2 */
+  uint64_t accepted; /* accepted moves since creation */
+  uint64_t attempted;/* attempted moves since creation */
+  uint64_t sweeps;   /* completed SCMF cycles since creation */
+  uint32_t max_cell; /* largest n_A + n_B of any cell */
+  uint32_t reserved;
+} soma_obs;
+
+/* Accumulated device time per kernel while timing is on (soma_set_timing). */
+typedef struct soma_timing {
+  double ms_sweep;        /* MC sweep kernel (move + fused occupation count) */
+  double ms_fields;       /* field-update kernel */
+  uint64_t sweep_launches;
+  uint64_t field_launches;
+  uint64_t kernel_launches; /* every kernel this handle launched since creation */
+} soma_timing;
+
+/* Create a system: validate desc, allocate device state, draw the initial
+ * configuration (first particle of each chain uniform in the box, then
+ * Gaussian bonds with <b^2> = R_e0^2/(N-1); Sec. 2.1 with b0 = sqrt(3/k0)),
+ * then compute n and omega (first stage of the SCMF cycle, Sec. 2.2).
+ * Returns SOMA_EINVAL before touching the GPU when desc is invalid.
+ * On success *out owns the state; on failure *out is NULL. */
+soma_status soma_create(const soma_system_desc* desc, soma_t** out);
+
+/* Free all device state of h (synchronises h's stream).  NULL is a no-op. */
+soma_status soma_destroy(soma_t* h);
+
+/* Run n SCMF cycles: n x (MC step of every particle against the frozen
+ * fields with the occupation count fused into it, then the field update).
+ * Asynchronous.  Sec. 2.2 cycle; Sec. 3.1.2 SET iteration; Eq. (delta-e). */
+soma_status soma_sweep(soma_t* h, uint32_t n);
+
+/* Recompute n and omega from the current positions (first stage of the SCMF
+ * cycle, Eqs. density-characteristics and omega-fields).  Asynchronous. */
+soma_status soma_update_fields(soma_t* h);
+
+/* Copy the packed occupation numbers (n_cells = grid cells entries; bits 0..15
+ * n_A, 16..31 n_B) to dst (device pointer if dst_on_device, else host).
+ * Synchronises.  SOMA_EINVAL if n_cells differs from the grid size. */
+soma_status soma_get_density(soma_t* h, uint32_t* dst, size_t n_cells, int dst_on_device);
+
+/* Copy omega as FP32: dst[0..cells) = omega_A, dst[cells..2 cells) = omega_B
+ * (converted from the storage type).  n must be 2*cells.  Synchronises. */
+soma_status soma_get_fields(soma_t* h, float* dst, size_t n, int dst_on_device);
+
+/* Copy positions (3*M floats, SoA x|y|z, dL units).  Synchronises. */
+soma_status soma_get_positions(soma_t* h, float* dst, size_t n, int dst_on_device);
+
+/* Replace positions (3*M floats, SoA).  Does not recompute the fields: call
+ * soma_update_fields to make n and omega follow.  Asynchronous for device
+ * sources; a host source is copied before the call returns. */
+soma_status soma_set_positions(soma_t* h, const float* src, size_t n, int src_on_device);
+
+/* FP64 observables of the current state (Eq. h-bond, Eq. discrete-ham).
+ * Synchronises. */
+soma_status soma_observables(soma_t* h, soma_obs* out);
+
+/* Composition structure factor S(q) = |sum_c (n_A - n_B)(c) e^{-i q.c}|^2 / M
+ * at q = 2 pi (m_x/grid_x, m_y/grid_y, m_z/grid_z) for k integer triples m
+ * (host array, k x 3); FP64 on the device; out is a host array of k doubles.
+ * The radial S(q,t) of Sec. 5.6 is the shell average of these values.
+ * Synchronises.  k <= 4096. */
+soma_status soma_structure_factor(soma_t* h, const int32_t* m, size_t k, double* out);
+
+/* Sweep counter: the Philox counter word w of the next MC step.  Setting it
+ * (with soma_set_positions) resumes a run bit-exactly: there is no RNG state. */
+soma_status soma_get_sweep(soma_t* h, uint64_t* out);
+soma_status soma_set_sweep(soma_t* h, uint64_t sweep);
+
+/* Per-kernel device timing with CUDA events on the handle's stream (on != 0
+ * enables; enabling resets the sums).  soma_get_timing synchronises. */
+soma_status soma_set_timing(soma_t* h, int on);
+soma_status soma_get_timing(soma_t* h, soma_timing* out);
+
+/* Block until all work queued by h has finished; reports sticky device errors. */
+soma_status soma_sync(soma_t* h);
+
+/* The cudaStream_t the handle runs on. */
+void* soma_stream(soma_t* h);
+
+/* Evaluate the device Philox4x32-10 on n counters: ctr (4n words), key (2n
+ * words), out (4n words), all device pointers; asynchronous on stream.  Used
+ * to check the generator against independent implementations. */
+soma_status soma_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
+                        void* stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* soma_last_error(void);
+
+/* SOMA_ABI_VERSION of the loaded library. */
+int soma_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SOMA_H */

@@ -1,0 +1,228 @@
+"""FP64 CPU oracle of the SCMF Monte-Carlo cycle (arXiv:1711.03828, Sec. 2, 3.1.2).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  It wraps ``liboracle.so`` (plain C in ``soma_oracle.c``, built by
+``oracle.build.build()``) with numpy arrays and shares no code with the CUDA
+library in ``paper_1711_03828_gb300``.
+
+Functions and the paper passage each follows:
+
+* ``philox`` / ``draw``          -- Philox4x32-10 (SC'11), the counter RNG that
+  replaces the stored-state PCG of Sec. 3.2.3.
+* ``System.init_chains``        -- initial Gaussian chains (Sec. 2.1, b0 = sqrt(3/k0)).
+* ``System.histogram``          -- occupation numbers, Eq. (density-characteristics).
+* ``System.fields``             -- interaction fields, Eq. (omega-fields), option K^0.
+* ``System.sweep``              -- one SET Monte-Carlo step (Sec. 2.2, Sec. 3.1.2).
+* ``System.observables``        -- E_b (Eq. h-bond), E_nb (Eq. discrete-ham), R_e^2.
+* ``System.structure_factor``   -- composition S(q) on the grid (Sec. 5.6).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+u32p = ctypes.POINTER(ctypes.c_uint32)
+f32p = ctypes.POINTER(ctypes.c_float)
+f64p = ctypes.POINTER(ctypes.c_double)
+u8p = ctypes.POINTER(ctypes.c_uint8)
+i32p = ctypes.POINTER(ctypes.c_int32)
+
+PURPOSE_INIT, PURPOSE_MOVE, PURPOSE_MOVE2, PURPOSE_CONFIG, PURPOSE_TRAIN = 0, 1, 2, 4, 5
+
+
+class OrSystem(ctypes.Structure):
+    _fields_ = [
+        ("n_chains", ctypes.c_uint64),
+        ("N", ctypes.c_uint32),
+        ("N_A", ctypes.c_uint32),
+        ("grid", ctypes.c_uint32 * 3),
+        ("Re", ctypes.c_double),
+        ("kappaN", ctypes.c_double),
+        ("chiN", ctypes.c_double),
+        ("a", ctypes.c_double),
+        ("a32", ctypes.c_float),
+        ("K_b", ctypes.c_double),
+        ("rho_cell", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("replica", ctypes.c_uint32),
+        ("set_order", ctypes.c_int),
+        ("move", ctypes.c_int),
+    ]
+
+
+class OrSweepStats(ctypes.Structure):
+    _fields_ = [("attempted", ctypes.c_uint64), ("accepted", ctypes.c_uint64),
+                ("near_ties", ctypes.c_uint64)]
+
+
+class OrObs(ctypes.Structure):
+    _fields_ = [("E_b", ctypes.c_double), ("E_nb", ctypes.c_double),
+                ("Re2", ctypes.c_double), ("b2", ctypes.c_double)]
+
+
+def lib():
+    """Load liboracle.so (building it first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        from . import build as _b
+        _b.build()
+    _lib = load(_LIB_PATH)
+    return _lib
+
+
+def load(path):
+    """Load an oracle library from ``path`` (tests load mutated builds this way)."""
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER(OrSystem)
+    L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
+    L.or_draw.argtypes = [P, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, u32p]
+    L.or_uniform_sym.argtypes = [ctypes.c_uint32]
+    L.or_uniform_sym.restype = ctypes.c_double
+    L.or_uniform_open.argtypes = [ctypes.c_uint32]
+    L.or_uniform_open.restype = ctypes.c_double
+    L.or_system_init.argtypes = [P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
+                                 f64p, u32p, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
+                                 ctypes.c_int, ctypes.c_int]
+    L.or_system_init.restype = ctypes.c_int
+    L.or_init_chain_range.argtypes = [P, ctypes.c_uint64, ctypes.c_uint64, f32p, f32p, f32p]
+    L.or_histogram.argtypes = [P, f32p, f32p, f32p, u32p, u32p]
+    L.or_fields.argtypes = [P, u32p, u32p, f64p, f64p, ctypes.c_int]
+    L.or_sweep.argtypes = [P, f32p, f32p, f32p, f64p, f64p, ctypes.c_uint32,
+                           ctypes.c_uint64, ctypes.c_uint64, f64p, u8p,
+                           ctypes.POINTER(OrSweepStats)]
+    L.or_observables.argtypes = [P, f32p, f32p, f32p, u32p, u32p, ctypes.POINTER(OrObs)]
+    L.or_structure_factor.argtypes = [P, u32p, u32p, i32p, ctypes.c_size_t, f64p]
+    L.or_num_threads.restype = ctypes.c_int
+    return L
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+def philox(ctr, key, L=None):
+    """Philox4x32-10 of one 4-word counter and 2-word key."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    (L or lib()).or_philox4x32_10(_ptr(c, u32p), _ptr(k, u32p), _ptr(out, u32p))
+    return out
+
+
+def uniform_sym(r, L=None):
+    return (L or lib()).or_uniform_sym(int(r))
+
+
+def uniform_open(r, L=None):
+    return (L or lib()).or_uniform_open(int(r))
+
+
+def num_threads():
+    return int(lib().or_num_threads())
+
+
+@dataclass
+class Positions:
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+
+    def copy(self):
+        return Positions(self.x.copy(), self.y.copy(), self.z.copy())
+
+    def stacked(self):
+        return np.stack([self.x, self.y, self.z])
+
+
+class System:
+    """One oracle system: the parameters of an SCMF simulation of diblock melts."""
+
+    def __init__(self, n_chains, N, f, box_Re, grid, chiN, kappaN, a_Re=0.0, seed=1,
+                 replica=0, set_order=0, move=0, L=None):
+        self.L = L or lib()
+        self.s = OrSystem()
+        box = (ctypes.c_double * 3)(*[float(v) for v in box_Re])
+        g = (ctypes.c_uint32 * 3)(*[int(v) for v in grid])
+        rc = self.L.or_system_init(ctypes.byref(self.s), int(n_chains), int(N), float(f),
+                                  ctypes.cast(box, f64p), ctypes.cast(g, u32p),
+                                  float(chiN), float(kappaN), float(a_Re), int(seed),
+                                  int(replica), int(set_order), int(move))
+        if rc != 0:
+            raise ValueError("invalid oracle system")
+        self.n_chains = int(n_chains)
+        self.N = int(N)
+        self.M = self.n_chains * self.N
+        self.grid = tuple(int(v) for v in grid)
+        self.cells = self.grid[0] * self.grid[1] * self.grid[2]
+
+    @property
+    def params(self):
+        return self.s
+
+    def draw(self, purpose, idx, w):
+        out = np.zeros(4, dtype=np.uint32)
+        self.L.or_draw(ctypes.byref(self.s), int(purpose), int(idx), int(w), _ptr(out, u32p))
+        return out
+
+    def empty_positions(self):
+        return Positions(np.zeros(self.M, np.float32), np.zeros(self.M, np.float32),
+                         np.zeros(self.M, np.float32))
+
+    def init_chains(self, c0=0, c1=None, pos=None):
+        c1 = self.n_chains if c1 is None else c1
+        pos = self.empty_positions() if pos is None else pos
+        self.L.or_init_chain_range(ctypes.byref(self.s), int(c0), int(c1),
+                                  _ptr(pos.x, f32p), _ptr(pos.y, f32p), _ptr(pos.z, f32p))
+        return pos
+
+    def histogram(self, pos):
+        nA = np.zeros(self.cells, np.uint32)
+        nB = np.zeros(self.cells, np.uint32)
+        self.L.or_histogram(ctypes.byref(self.s), _ptr(pos.x, f32p), _ptr(pos.y, f32p),
+                           _ptr(pos.z, f32p), _ptr(nA, u32p), _ptr(nB, u32p))
+        return nA, nB
+
+    def fields(self, nA, nB, round_mode=0):
+        wA = np.zeros(self.cells, np.float64)
+        wB = np.zeros(self.cells, np.float64)
+        self.L.or_fields(ctypes.byref(self.s), _ptr(nA, u32p), _ptr(nB, u32p),
+                        _ptr(wA, f64p), _ptr(wB, f64p), int(round_mode))
+        return wA, wB
+
+    def sweep(self, pos, wA, wB, sweep, c0=0, c1=None, want_margin=False, want_acc=False):
+        """One SET sweep in place; returns (stats, margin or None, accepted or None)."""
+        c1 = self.n_chains if c1 is None else c1
+        margin = np.full(self.M, np.nan) if want_margin else None
+        acc = np.zeros(self.M, np.uint8) if want_acc else None
+        st = OrSweepStats()
+        self.L.or_sweep(ctypes.byref(self.s), _ptr(pos.x, f32p), _ptr(pos.y, f32p),
+                       _ptr(pos.z, f32p), _ptr(wA, f64p), _ptr(wB, f64p), int(sweep),
+                       int(c0), int(c1), _ptr(margin, f64p), _ptr(acc, u8p),
+                       ctypes.byref(st))
+        return st, margin, acc
+
+    def observables(self, pos, nA, nB):
+        o = OrObs()
+        self.L.or_observables(ctypes.byref(self.s), _ptr(pos.x, f32p), _ptr(pos.y, f32p),
+                             _ptr(pos.z, f32p), _ptr(nA, u32p), _ptr(nB, u32p),
+                             ctypes.byref(o))
+        return {"E_b": o.E_b, "E_nb": o.E_nb, "E_tot": o.E_b + o.E_nb,
+                "Re2": o.Re2, "b2": o.b2}
+
+    def structure_factor(self, nA, nB, m):
+        mm = np.ascontiguousarray(np.asarray(m, dtype=np.int32).reshape(-1, 3))
+        out = np.zeros(len(mm), np.float64)
+        self.L.or_structure_factor(ctypes.byref(self.s), _ptr(nA, u32p), _ptr(nB, u32p),
+                                  _ptr(mm, i32p), len(mm), _ptr(out, f64p))
+        return out

@@ -1,0 +1,386 @@
+/*
+ * soma_oracle.c -- FP64 CPU oracle of the SCMF Monte-Carlo cycle
+ * (arXiv:1711.03828, Sec. 2 and Sec. 3.1.2).  Test infrastructure only: the
+ * product path never loads it.  Every function follows the paper's steps in
+ * the paper's order; nothing is blocked, fused or reordered.
+ */
+#include "soma_oracle.h"
+
+#include <math.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10, the counter-based generator of Salmon et al., "Parallel     */
+/* random numbers: as easy as 1, 2, 3" (SC'11).  The paper's own generator is  */
+/* a stored-state PCG (Sec. 3.2.3); a counter-based generator needs no stored  */
+/* state at all, which is the property Sec. 3.2.3 argues for.                  */
+/* One round: two 32x32->64 products of counter words 0 and 2 by the round     */
+/* multipliers; the high halves are xored with the other two counter words and */
+/* the round key; the low halves pass through; the key is bumped by the Weyl   */
+/* constants between rounds.                                                    */
+/* ------------------------------------------------------------------------- */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const uint64_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) { k0 += W0; k1 += W1; }
+    uint64_t p0 = M0 * (uint64_t)c0;
+    uint64_t p1 = M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+void or_draw(const or_system* s, uint32_t purpose, uint64_t id, uint32_t w, uint32_t out[4]) {
+  uint32_t ctr[4] = { (uint32_t)id, (uint32_t)(id >> 32), w,
+                      (purpose << 24) | (s->replica & 0xFFFFFFu) };
+  uint32_t key[2] = { (uint32_t)s->seed, (uint32_t)(s->seed >> 32) };
+  or_philox4x32_10(ctr, key, out);
+}
+
+/* The 24 leading bits k of a word give the symmetric uniform (2k+1)/2^24 - 1
+ * (never 0, exact in FP32) and the open uniform (k+1/2)/2^24 (never 0 or 1). */
+double or_uniform_sym(uint32_t r) {
+  double k = (double)(r >> 8);
+  return (2.0 * k + 1.0) / 16777216.0 - 1.0;
+}
+double or_uniform_open(uint32_t r) {
+  double k = (double)(r >> 8);
+  return (k + 0.5) / 16777216.0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* System parameters.                                                          */
+/*   R_e0 in dL units follows from the box: grid cells / box length in R_e0.   */
+/*   k0/2 = 3/(2 b0^2) with b0^2 = R_e0^2/(N-1) (Sec. 2.1, b0 = sqrt(3/k0)).    */
+/*   rho_0 dL^3 = particles per cell on average (Sec. 3.1.1).                   */
+/* ------------------------------------------------------------------------- */
+int or_system_init(or_system* s, uint64_t n_chains, uint32_t N, double f,
+                   const double box_Re[3], const uint32_t grid[3],
+                   double chiN, double kappaN, double a_Re, uint64_t seed,
+                   uint32_t replica, int set_order, int move) {
+  memset(s, 0, sizeof(*s));
+  if (n_chains == 0 || N == 0) return -1;
+  s->n_chains = n_chains;
+  s->N = N;
+  s->N_A = (uint32_t)floor(f * (double)N + 0.5);
+  if (s->N_A > N) s->N_A = N;
+  for (int d = 0; d < 3; ++d) s->grid[d] = grid[d];
+  s->Re = (double)grid[0] / box_Re[0];
+  s->kappaN = kappaN;
+  s->chiN = chiN;
+  if (!(a_Re > 0.0)) a_Re = (N > 1) ? 0.5 / sqrt((double)(N - 1)) : 0.5;
+  s->a = a_Re * s->Re;
+  s->a32 = (float)s->a;
+  s->K_b = (N > 1) ? 3.0 * (double)(N - 1) / (2.0 * s->Re * s->Re) : 0.0;
+  double cells = (double)grid[0] * (double)grid[1] * (double)grid[2];
+  s->rho_cell = (double)n_chains * (double)N / cells;
+  s->seed = seed;
+  s->replica = replica;
+  s->set_order = set_order;
+  s->move = move;
+  return 0;
+}
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------- */
+/* a0: first particle uniform in the box, then Gaussian bond vectors with      */
+/* per-component variance R_e0^2 / (3 (N-1)), i.e. <b^2> = b0^2 (Sec. 2.1).    */
+/* Gaussians by the Box-Muller transform of pairs of open uniforms.            */
+/* ------------------------------------------------------------------------- */
+static double or_init_gauss(const or_system* s, uint64_t chain, uint32_t j) {
+  uint32_t w[4];
+  or_draw(s, OR_PURPOSE_INIT, chain, 1u + j / 4u, w);
+  uint32_t p = (j % 4u) / 2u;
+  double u1 = or_uniform_open(w[2 * p]);
+  double u2 = or_uniform_open(w[2 * p + 1]);
+  double rad = sqrt(-2.0 * log(u1));
+  double th = 2.0 * M_PI * u2;
+  return (j % 2u == 0u) ? rad * cos(th) : rad * sin(th);
+}
+
+void or_init_chain_range(const or_system* s, uint64_t c0, uint64_t c1,
+                         float* x, float* y, float* z) {
+  const uint32_t N = s->N;
+  const double sigma = (N > 1) ? s->Re / sqrt(3.0 * (double)(N - 1)) : 0.0;
+  long long i0 = (long long)c0, i1 = (long long)c1;
+#pragma omp parallel for schedule(static)
+  for (long long cc = i0; cc < i1; ++cc) {
+    uint64_t chain = (uint64_t)cc;
+    uint32_t w[4];
+    or_draw(s, OR_PURPOSE_INIT, chain, 0u, w);
+    double r[3];
+    for (int d = 0; d < 3; ++d) r[d] = or_uniform_open(w[d]) * (double)s->grid[d];
+    uint64_t m = chain * N;
+    x[m] = (float)r[0]; y[m] = (float)r[1]; z[m] = (float)r[2];
+    for (uint32_t i = 0; i + 1 < N; ++i) {
+      for (int d = 0; d < 3; ++d) r[d] += sigma * or_init_gauss(s, chain, 3u * i + (uint32_t)d);
+      x[m + i + 1] = (float)r[0]; y[m + i + 1] = (float)r[1]; z[m + i + 1] = (float)r[2];
+    }
+  }
+}
+
+void or_init_chains(const or_system* s, float* x, float* y, float* z) {
+  or_init_chain_range(s, 0, s->n_chains, x, y, z);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Cell of a position: the characteristic function Pi_c of Eq.                 */
+/* (density-characteristics) with half-open cells [c, c+1) in dL units and     */
+/* periodic images folded back into the box.                                    */
+/* ------------------------------------------------------------------------- */
+static uint64_t or_cell(const or_system* s, double x, double y, double z) {
+  long long c[3];
+  double p[3] = { x, y, z };
+  for (int d = 0; d < 3; ++d) {
+    long long n = (long long)s->grid[d];
+    long long f = (long long)floor(p[d]);
+    long long r = f % n;
+    if (r < 0) r += n;
+    c[d] = r;
+  }
+  return ((uint64_t)c[2] * s->grid[1] + (uint64_t)c[1]) * s->grid[0] + (uint64_t)c[0];
+}
+
+/* a3: n_i(c) = number of particles of type i in cell c (Eq.                    */
+/* density-characteristics times rho_0 dL^3; Sec. 3.1.1 occupation numbers).    */
+void or_histogram(const or_system* s, const float* x, const float* y, const float* z,
+                  uint32_t* nA, uint32_t* nB) {
+  const uint64_t cells = (uint64_t)s->grid[0] * s->grid[1] * s->grid[2];
+  memset(nA, 0, cells * sizeof(uint32_t));
+  memset(nB, 0, cells * sizeof(uint32_t));
+  for (uint64_t k = 0; k < s->n_chains; ++k) {
+    for (uint32_t i = 0; i < s->N; ++i) {
+      uint64_t m = k * s->N + i;
+      uint64_t c = or_cell(s, x[m], y[m], z[m]);
+      if (i < s->N_A) nA[c] += 1u; else nB[c] += 1u;
+    }
+  }
+}
+
+/* Round-to-nearest-even of an FP32 value to BF16 / FP16, returned as double. */
+static double or_round_bf16(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7FFFu + lsb;
+  u &= 0xFFFF0000u;
+  float g;
+  memcpy(&g, &u, 4);
+  return (double)g;
+}
+static double or_round_fp16(float f) {
+  _Float16 h = (_Float16)f;
+  return (double)(float)h;
+}
+
+/* a4: omega_i(c) = kappa_0 (sum_k phi_k(c) - 1) - sum_{k != i} chi_0/2 (phi_i - phi_k)  */
+/* with phi_k = n_k / (rho_0 dL^3), kappa_0 = kappaN/N, chi_0 = chiN/N            */
+/* (Eq. omega-fields, option K^0; two types A, B).                                */
+void or_fields(const or_system* s, const uint32_t* nA, const uint32_t* nB,
+               double* wA, double* wB, int round_mode) {
+  const uint64_t cells = (uint64_t)s->grid[0] * s->grid[1] * s->grid[2];
+  const double kappa0 = s->kappaN / (double)s->N;
+  const double chi0 = s->chiN / (double)s->N;
+  for (uint64_t c = 0; c < cells; ++c) {
+    double phiA = (double)nA[c] / s->rho_cell;
+    double phiB = (double)nB[c] / s->rho_cell;
+    double comp = kappa0 * (phiA + phiB - 1.0);
+    double a = comp - 0.5 * chi0 * (phiA - phiB);
+    double b = comp - 0.5 * chi0 * (phiB - phiA);
+    if (round_mode == 1) { a = (double)(float)a; b = (double)(float)b; }
+    else if (round_mode == 2) { a = or_round_bf16((float)a); b = or_round_bf16((float)b); }
+    else if (round_mode == 3) { a = or_round_fp16((float)a); b = or_round_fp16((float)b); }
+    wA[c] = a;
+    wB[c] = b;
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* a2: one Monte-Carlo step with the fields frozen (second stage of the SCMF    */
+/* cycle, Sec. 2.2), iterating each molecule's independent sets in a random     */
+/* order (the SET scheme of Sec. 3.1.2): for a linear chain the even particles  */
+/* form set 0 and the odd ones set 1.                                           */
+/* Move of particle j (Sec. 2.2): trial displacement uniform in [-a, a] per     */
+/* axis; dE = bonded change (Eq. V-harmonic summed over the bonds of j) + the   */
+/* field change omega_t(c') - omega_t(c) (Eq. delta-e); Metropolis acceptance    */
+/* min(1, exp(-dE)), taken as: accept iff dE <= 0 or ln u < -dE.                 */
+/* ------------------------------------------------------------------------- */
+static void or_move_uniform(const or_system* s, float* x, float* y, float* z,
+                            const double* wA, const double* wB, uint32_t sweep,
+                            uint64_t chain, uint32_t i, double* margin, uint8_t* accepted,
+                            uint64_t* acc, uint64_t* ties) {
+  const uint32_t N = s->N;
+  const uint64_t m = chain * N + i;
+  uint32_t w[4];
+  or_draw(s, OR_PURPOSE_MOVE, m, sweep, w);
+  /* trial position: each displacement component a*v rounded to FP32, then the
+   * sum rounded to FP32 (the stored precision of positions) */
+  double r_old[3] = { x[m], y[m], z[m] };
+  double r_new[3];
+  for (int d = 0; d < 3; ++d) {
+    float dx = (float)((double)s->a32 * or_uniform_sym(w[d]));
+    r_new[d] = (double)(float)(r_old[d] + (double)dx);
+  }
+  double u = or_uniform_open(w[3]);
+  /* bonded energy change: neighbours i-1 and i+1 of the linear chain */
+  double dEb = 0.0;
+  for (int side = -1; side <= 1; side += 2) {
+    long long jn = (long long)i + side;
+    if (jn < 0 || jn >= (long long)N) continue;
+    uint64_t n = chain * N + (uint64_t)jn;
+    double rn[3] = { x[n], y[n], z[n] };
+    double d_new = 0.0, d_old = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      d_new += (r_new[d] - rn[d]) * (r_new[d] - rn[d]);
+      d_old += (r_old[d] - rn[d]) * (r_old[d] - rn[d]);
+    }
+    dEb += s->K_b * (d_new - d_old);
+  }
+  /* field energy change, Eq. (delta-e) */
+  const double* w_t = (i < s->N_A) ? wA : wB;
+  uint64_t c_old = or_cell(s, r_old[0], r_old[1], r_old[2]);
+  uint64_t c_new = or_cell(s, r_new[0], r_new[1], r_new[2]);
+  double dE = dEb + (w_t[c_new] - w_t[c_old]);
+  double lnu = log(u);
+  int acc_move = (dE <= 0.0) || (lnu < -dE);
+  if (margin) margin[m] = dE + lnu;
+  if (fabs(dE + lnu) < 1e-4) (*ties)++;
+  if (acc_move) {
+    x[m] = (float)r_new[0]; y[m] = (float)r_new[1]; z[m] = (float)r_new[2];
+    (*acc)++;
+  }
+  if (accepted) accepted[m] = (uint8_t)acc_move;
+}
+
+/* Set order of one chain for one sweep: bit 0 of the fourth word of the move
+ * draw of the chain's first particle picks odd->even (1) or even->odd (0); the
+ * 24 bits that make the acceptance uniform are the word's top bits, so the set
+ * order is independent of every uniform the moves use. */
+static uint32_t or_first_set(const or_system* s, uint64_t chain, uint32_t sweep) {
+  if (s->set_order != 0) return 0u;
+  uint32_t w[4];
+  or_draw(s, OR_PURPOSE_MOVE, chain * s->N, sweep, w);
+  return w[3] & 1u;
+}
+
+void or_sweep(const or_system* s, float* x, float* y, float* z,
+              const double* wA, const double* wB, uint32_t sweep,
+              uint64_t c0, uint64_t c1,
+              double* margin, uint8_t* accepted, or_sweep_stats* st) {
+  const uint32_t N = s->N;
+  uint64_t acc = 0, ties = 0;
+  long long i0 = (long long)c0, i1 = (long long)c1;
+#pragma omp parallel for schedule(static) reduction(+ : acc, ties)
+  for (long long cc = i0; cc < i1; ++cc) {
+    uint64_t chain = (uint64_t)cc;
+    uint32_t first = or_first_set(s, chain, sweep);
+    for (uint32_t k = 0; k < 2; ++k) {
+      uint32_t set = first ^ k;
+      for (uint32_t i = set; i < N; i += 2) {
+        uint64_t a1 = 0, t1 = 0;
+        or_move_uniform(s, x, y, z, wA, wB, sweep, chain, i, margin, accepted, &a1, &t1);
+        acc += a1;
+        ties += t1;
+      }
+    }
+  }
+  if (st) {
+    st->attempted += (c1 - c0) * N;
+    st->accepted += acc;
+    st->near_ties += ties;
+  }
+}
+
+/* One SCMF cycle in the order of Sec. 2.2 as run by the library: the fields of
+ * the current configuration are frozen for the MC step, then the occupation
+ * numbers and the fields are recomputed from the new configuration. */
+void or_cycle(const or_system* s, float* x, float* y, float* z,
+              uint32_t* nA, uint32_t* nB, double* wA, double* wB,
+              uint32_t sweep, int round_mode, or_sweep_stats* st) {
+  or_sweep(s, x, y, z, wA, wB, sweep, 0, s->n_chains, NULL, NULL, st);
+  or_histogram(s, x, y, z, nA, nB);
+  or_fields(s, nA, nB, wA, wB, round_mode);
+}
+
+/* ------------------------------------------------------------------------- */
+/* a5: observables.                                                             */
+/*   E_b  = sum_bonds (k0/2) |b|^2               (Eq. h-bond, V-harmonic)       */
+/*   E_nb = rho_0 dL^3 / N * sum_c [ kappaN/2 (phiA+phiB-1)^2                    */
+/*                                   - chiN/4 (phiA-phiB)^2 ]   (Eq. discrete-ham, */
+/*          K_fluc + K^0 with the A-B pair counted once)                         */
+/* ------------------------------------------------------------------------- */
+void or_observables(const or_system* s, const float* x, const float* y, const float* z,
+                    const uint32_t* nA, const uint32_t* nB, or_obs* out) {
+  const uint32_t N = s->N;
+  double Eb = 0.0, Re2 = 0.0, b2 = 0.0;
+  for (uint64_t k = 0; k < s->n_chains; ++k) {
+    uint64_t m0 = k * N;
+    for (uint32_t i = 0; i + 1 < N; ++i) {
+      double dx = (double)x[m0 + i + 1] - (double)x[m0 + i];
+      double dy = (double)y[m0 + i + 1] - (double)y[m0 + i];
+      double dz = (double)z[m0 + i + 1] - (double)z[m0 + i];
+      double bb = dx * dx + dy * dy + dz * dz;
+      b2 += bb;
+      Eb += s->K_b * bb;
+    }
+    double ex = (double)x[m0 + N - 1] - (double)x[m0];
+    double ey = (double)y[m0 + N - 1] - (double)y[m0];
+    double ez = (double)z[m0 + N - 1] - (double)z[m0];
+    Re2 += ex * ex + ey * ey + ez * ez;
+  }
+  const uint64_t cells = (uint64_t)s->grid[0] * s->grid[1] * s->grid[2];
+  double K = 0.0;
+  for (uint64_t c = 0; c < cells; ++c) {
+    double phiA = (double)nA[c] / s->rho_cell;
+    double phiB = (double)nB[c] / s->rho_cell;
+    double fl = phiA + phiB - 1.0;
+    double df = phiA - phiB;
+    K += 0.5 * s->kappaN * fl * fl - 0.25 * s->chiN * df * df;
+  }
+  out->E_b = Eb;
+  out->E_nb = s->rho_cell / (double)N * K;
+  out->Re2 = Re2 / (double)s->n_chains;
+  out->b2 = (N > 1) ? b2 / ((double)s->n_chains * (double)(N - 1)) : 0.0;
+}
+
+/* Composition structure factor on the collocation grid (the radial S(q) of
+ * Sec. 5.6 is the shell average of this quantity).  Direct DFT. */
+void or_structure_factor(const or_system* s, const uint32_t* nA, const uint32_t* nB,
+                         const int32_t* m, size_t k, double* out) {
+  const double M = (double)s->n_chains * (double)s->N;
+  for (size_t q = 0; q < k; ++q) {
+    double re = 0.0, im = 0.0;
+    for (uint32_t cz = 0; cz < s->grid[2]; ++cz)
+      for (uint32_t cy = 0; cy < s->grid[1]; ++cy)
+        for (uint32_t cx = 0; cx < s->grid[0]; ++cx) {
+          uint64_t c = ((uint64_t)cz * s->grid[1] + cy) * s->grid[0] + cx;
+          double dn = (double)nA[c] - (double)nB[c];
+          if (dn == 0.0) continue;
+          double ph = 2.0 * M_PI * ((double)m[3 * q] * cx / s->grid[0] +
+                                    (double)m[3 * q + 1] * cy / s->grid[1] +
+                                    (double)m[3 * q + 2] * cz / s->grid[2]);
+          re += dn * cos(ph);
+          im -= dn * sin(ph);
+        }
+    out[q] = (re * re + im * im) / M;
+  }
+}

@@ -1,0 +1,123 @@
+/*
+ * soma_oracle.h -- plain, slow, FP64 CPU oracle for the SCMF Monte-Carlo cycle
+ * of Daoulas/Mueller-type soft coarse-grained polymer melts as implemented by
+ * SOMA (arXiv:1711.03828).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / --impl reference legs of bench.py may load this library.  It
+ * shares no code, header, constant table or helper with the CUDA library under
+ * paper_1711_03828_gb300/csrc; neither includes the other.
+ *
+ * Conventions (the readings of the paper are listed in the design doc):
+ *   - lengths in units of the grid spacing dL (cubic cells, Sec. 2.1), so the
+ *     cell of a particle is floor(x) taken modulo the grid extent;
+ *   - energies in kT; omega_t(c) is the per-particle field energy of Eq.
+ *     (omega-fields), i.e. kappa_0 = kappaN/N and chi_0 = chiN/N;
+ *   - linear diblock chains: monomer i of a chain is type A iff i < N_A;
+ *   - positions are stored FP32 structure-of-arrays (x[M], y[M], z[M]),
+ *     monomer m = chain*N + i, unwrapped (only the cell index is wrapped);
+ *   - every arithmetic decision is taken in FP64 from the FP32 stored state.
+ *
+ * Parity pins: see tests/test_oracle_*.py.  Functions whose parity is not
+ * pinned by anything outside the oracle say "parity unpinned" below.
+ */
+#ifndef SOMA_ORACLE_H
+#define SOMA_ORACLE_H
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Philox stream purposes (the fourth counter word holds purpose<<24 | replica). */
+enum { OR_PURPOSE_INIT = 0, OR_PURPOSE_MOVE = 1, OR_PURPOSE_MOVE2 = 2,
+       OR_PURPOSE_CONFIG = 4, OR_PURPOSE_TRAIN = 5 };
+
+typedef struct {
+  uint64_t n_chains;
+  uint32_t N;        /* particles per chain */
+  uint32_t N_A;      /* floor(f*N + 1/2) */
+  uint32_t grid[3];  /* collocation cells per axis */
+  double   Re;       /* R_e0 in units of dL */
+  double   kappaN, chiN;
+  double   a;        /* maximal displacement per axis, units of dL (FP64) */
+  float    a32;      /* the same, rounded to FP32: the move uses this value */
+  double   K_b;      /* k0/2 = 3(N-1)/(2 Re^2), kT / dL^2 */
+  double   rho_cell; /* rho_0 dL^3 = M / n_cells */
+  uint64_t seed;
+  uint32_t replica;
+  int      set_order;  /* 0: random per (chain, sweep); 1: fixed even->odd */
+  int      move;       /* 0 uniform (Metropolis), 1 smart MC (force biased) */
+} or_system;
+
+typedef struct {
+  uint64_t attempted, accepted;
+  uint64_t near_ties;   /* moves with |dE + ln u| < 1e-4 */
+} or_sweep_stats;
+
+/* --- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ------------------- */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* Draw for (purpose, id, w) of a system: ctr = (id lo, id hi, w, purpose<<24|replica),
+ * key = (seed lo, seed hi). */
+void or_draw(const or_system* s, uint32_t purpose, uint64_t id, uint32_t w, uint32_t out[4]);
+double or_uniform_sym(uint32_t r);   /* (2k+1)/2^24 - 1, k = r>>8, in (-1,1) */
+double or_uniform_open(uint32_t r);  /* (k+1/2)/2^24,      k = r>>8, in (0,1)  */
+
+/* --- System description ---------------------------------------------------- */
+int or_system_init(or_system* s, uint64_t n_chains, uint32_t N, double f,
+                   const double box_Re[3], const uint32_t grid[3],
+                   double chiN, double kappaN, double a_Re, uint64_t seed,
+                   uint32_t replica, int set_order, int move);
+
+/* --- a0: initial configuration --------------------------------------------- */
+void or_init_chains(const or_system* s, float* x, float* y, float* z);
+void or_init_chain_range(const or_system* s, uint64_t c0, uint64_t c1,
+                         float* x, float* y, float* z);
+
+/* --- a3: occupation numbers, Eq. (density-characteristics) ----------------- */
+void or_histogram(const or_system* s, const float* x, const float* y, const float* z,
+                  uint32_t* nA, uint32_t* nB);
+
+/* --- a4: interaction fields, Eq. (omega-fields) with K^0 -------------------- */
+/* round_mode: 0 FP64 result, 1 rounded to FP32, 2 to BF16 (RNE), 3 to FP16 (RNE).
+ * For 2/3 the value is first rounded to FP32 (the storage path of the GPU). */
+void or_fields(const or_system* s, const uint32_t* nA, const uint32_t* nB,
+               double* wA, double* wB, int round_mode);
+
+/* --- a2: one SET sweep with frozen fields (Sec. 3.1.2, Listing 2 scheme) --- */
+/* margin (optional, M doubles): dE + ln u of each attempted move.
+ * accepted (optional, M bytes): 1 if the move was accepted.
+ * chain range [c0, c1) lets tests run a sample of chains. */
+void or_sweep(const or_system* s, float* x, float* y, float* z,
+              const double* wA, const double* wB, uint32_t sweep,
+              uint64_t c0, uint64_t c1,
+              double* margin, uint8_t* accepted, or_sweep_stats* st);
+
+/* One full SCMF cycle: sweep all chains, then histogram, then fields. */
+void or_cycle(const or_system* s, float* x, float* y, float* z,
+              uint32_t* nA, uint32_t* nB, double* wA, double* wB,
+              uint32_t sweep, int round_mode, or_sweep_stats* st);
+
+/* --- a5: observables --------------------------------------------------------- */
+typedef struct {
+  double E_b;     /* sum over bonds of K_b |b|^2, Eq. (h-bond)+(V-harmonic) */
+  double E_nb;    /* Eq. (discrete-ham) with K_fluc + K^0_inter */
+  double Re2;     /* mean |r_{N-1} - r_0|^2 over chains, dL^2 */
+  double b2;      /* mean |r_{i+1} - r_i|^2 over bonds, dL^2 */
+} or_obs;
+void or_observables(const or_system* s, const float* x, const float* y, const float* z,
+                    const uint32_t* nA, const uint32_t* nB, or_obs* out);
+
+/* S(q) = |sum_c (nA-nB)(c) exp(-i q.c)|^2 / M with q = 2 pi m / grid, for
+ * k wave-vector index triples m (k x 3 int32). */
+void or_structure_factor(const or_system* s, const uint32_t* nA, const uint32_t* nB,
+                         const int32_t* m, size_t k, double* out);
+
+/* Threads the OpenMP parts use (1 when built without OpenMP). */
+int or_num_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,191 @@
+"""GB300-native SCMF Monte-Carlo for soft coarse-grained diblock melts
+(arXiv:1711.03828, "SOMA").
+
+The compute path is ``libsoma.so`` (hand-written sm_103a CUDA behind the C ABI
+of ``include/soma.h``); this package holds its ctypes binding (``_abi``, same
+names as the C entry points) and ``System``, a thin owner of one handle that
+marshals torch tensors and numpy arrays.  PyTorch is used only for device
+memory and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _abi
+from ._abi import (GRID_BF16, GRID_F16, GRID_F32, MOVE_SMC, MOVE_UNIFORM, SET_ORDER_FIXED,
+                   SET_ORDER_RANDOM, SomaError)
+
+__all__ = ["SystemDesc", "System", "SomaError", "MOVE_UNIFORM", "MOVE_SMC", "SET_ORDER_RANDOM",
+           "SET_ORDER_FIXED", "GRID_F32", "GRID_BF16", "GRID_F16"]
+
+
+@dataclass
+class SystemDesc:
+    """Python mirror of ``soma_system_desc``."""
+    n_chains: int
+    N: int
+    f: float = 0.5
+    box_Re: tuple = (2.0, 2.0, 2.0)
+    grid: tuple = (12, 12, 12)
+    chiN: float = 20.0
+    kappaN: float = 50.0
+    a_Re: float = 0.0
+    move: int = MOVE_UNIFORM
+    set_order: int = SET_ORDER_RANDOM
+    grid_dtype: int = GRID_F32
+    seed: int = 1
+    replica_id: int = 0
+
+    @property
+    def M(self):
+        return self.n_chains * self.N
+
+    @property
+    def cells(self):
+        return int(self.grid[0]) * int(self.grid[1]) * int(self.grid[2])
+
+    def to_c(self, stream=None):
+        d = _abi.SomaSystemDesc()
+        d.struct_size = ctypes.sizeof(_abi.SomaSystemDesc)
+        d.N = int(self.N)
+        d.n_chains = int(self.n_chains)
+        d.f = float(self.f)
+        for k in range(3):
+            d.box_Re[k] = float(self.box_Re[k])
+            d.grid[k] = int(self.grid[k])
+        d.chiN = float(self.chiN)
+        d.kappaN = float(self.kappaN)
+        d.a_Re = float(self.a_Re)
+        d.move = int(self.move)
+        d.set_order = int(self.set_order)
+        d.grid_dtype = int(self.grid_dtype)
+        d.flags = 0
+        d.seed = int(self.seed)
+        d.replica_id = int(self.replica_id)
+        d.stream = stream
+        return d
+
+
+def _torch_stream_handle(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+class System:
+    """One SCMF system on the GPU (owns a ``soma_t``)."""
+
+    def __init__(self, desc: SystemDesc, stream=None):
+        self.desc = desc
+        self._stream_obj = stream
+        h = ctypes.c_void_p()
+        c = desc.to_c(_torch_stream_handle(stream))
+        _abi.soma_create(ctypes.byref(c), ctypes.byref(h))
+        self.h = h
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _abi.soma_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- the SCMF cycle ---------------------------------------------------
+    def sweep(self, n=1):
+        _abi.soma_sweep(self.h, int(n))
+
+    def update_fields(self):
+        _abi.soma_update_fields(self.h)
+
+    def sync(self):
+        _abi.soma_sync(self.h)
+
+    # -- state access -----------------------------------------------------
+    def get_positions(self, out=None):
+        """SoA positions (3, M) float32: numpy by default, or into a CUDA tensor."""
+        M = self.desc.M
+        if out is None:
+            a = np.empty(3 * M, np.float32)
+            _abi.soma_get_positions(self.h, a.ctypes.data, a.size, 0)
+            return a.reshape(3, M)
+        _abi.soma_get_positions(self.h, ctypes.c_void_p(out.data_ptr()), out.numel(), 1)
+        return out
+
+    def set_positions(self, pos):
+        """pos: (3, M) float32 numpy array or CUDA tensor."""
+        M = self.desc.M
+        if isinstance(pos, np.ndarray):
+            a = np.ascontiguousarray(pos, dtype=np.float32).reshape(-1)
+            assert a.size == 3 * M
+            _abi.soma_set_positions(self.h, a.ctypes.data, a.size, 0)
+        else:
+            assert pos.is_contiguous() and pos.numel() == 3 * M
+            _abi.soma_set_positions(self.h, ctypes.c_void_p(pos.data_ptr()), pos.numel(),
+                                    1 if pos.is_cuda else 0)
+
+    def get_density(self, out=None):
+        """Packed occupation numbers (cells,) uint32: n_A | n_B << 16."""
+        cells = self.desc.cells
+        if out is None:
+            a = np.empty(cells, np.uint32)
+            _abi.soma_get_density(self.h, a.ctypes.data, cells, 0)
+            return a
+        _abi.soma_get_density(self.h, ctypes.c_void_p(out.data_ptr()), cells, 1)
+        return out
+
+    def get_density_ab(self):
+        n = self.get_density()
+        return (n & 0xFFFF).astype(np.uint32), (n >> 16).astype(np.uint32)
+
+    def get_fields(self):
+        """omega_A, omega_B as float32 arrays of cells entries."""
+        cells = self.desc.cells
+        a = np.empty(2 * cells, np.float32)
+        _abi.soma_get_fields(self.h, a.ctypes.data, a.size, 0)
+        return a[:cells], a[cells:]
+
+    def observables(self):
+        o = _abi.SomaObs()
+        _abi.soma_observables(self.h, ctypes.byref(o))
+        return {k: getattr(o, k) for k, _ in _abi.SomaObs._fields_ if k != "reserved"}
+
+    def structure_factor(self, m):
+        mm = np.ascontiguousarray(np.asarray(m, dtype=np.int32).reshape(-1, 3))
+        out = np.zeros(len(mm), np.float64)
+        _abi.soma_structure_factor(self.h, mm.ctypes.data, len(mm), out.ctypes.data)
+        return out
+
+    @property
+    def sweep_count(self):
+        v = ctypes.c_uint64()
+        _abi.soma_get_sweep(self.h, ctypes.byref(v))
+        return v.value
+
+    def set_sweep(self, s):
+        _abi.soma_set_sweep(self.h, int(s))
+
+    def set_timing(self, on=True):
+        _abi.soma_set_timing(self.h, 1 if on else 0)
+
+    def timing(self):
+        t = _abi.SomaTiming()
+        _abi.soma_get_timing(self.h, ctypes.byref(t))
+        return {k: getattr(t, k) for k, _ in _abi.SomaTiming._fields_}
+
+    @property
+    def stream_handle(self):
+        return _abi.soma_stream(self.h)

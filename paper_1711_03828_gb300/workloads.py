@@ -1,0 +1,91 @@
+"""Synthetic workloads and seeded input generators.
+
+This module holds no arithmetic of the method: it names the benchmark
+configurations (sizes, interaction strengths, seeds) and draws seeded input
+configurations with numpy for tests that feed the SAME positions to the CUDA
+library and to the CPU oracle.  The paper's workloads are synthetic melts
+(Sec. 5: homopolymer and diblock melts of given N, sqrt(Nbar), dL = R_e0/6),
+so nothing here stands in for a dataset.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import SystemDesc
+
+
+def melt_small(seed=1, **kw):
+    """Symmetric A-B diblock melt, 1024 chains of N=32 in a periodic 2x2x2 R_e0
+    box, 12^3 grid (dL = R_e0/6), chiN=20, kappaN=50: rho_0 R_e0^3 = 4096,
+    sqrt(Nbar) = 128.  32,768 particles."""
+    d = dict(n_chains=1024, N=32, f=0.5, box_Re=(2.0, 2.0, 2.0), grid=(12, 12, 12),
+             chiN=20.0, kappaN=50.0, seed=seed)
+    d.update(kw)
+    return SystemDesc(**d)
+
+
+def melt_large(seed=1, **kw):
+    """Lamella-forming diblock melt at scale: 4,194,304 chains of N=32 in a
+    periodic 32^3 R_e0 box, 192^3 grid, chiN=30, kappaN=50.  134,217,728
+    particles (1.61 GB of FP32 positions)."""
+    d = dict(n_chains=4194304, N=32, f=0.5, box_Re=(32.0, 32.0, 32.0), grid=(192, 192, 192),
+             chiN=30.0, kappaN=50.0, seed=seed)
+    d.update(kw)
+    return SystemDesc(**d)
+
+
+def melt_subbox(seed=1, **kw):
+    """4^3 R_e0 sub-box of the large melt (same density and grid spacing):
+    8192 chains of N=32, 24^3 grid, chiN=30.  262,144 particles."""
+    d = dict(n_chains=8192, N=32, f=0.5, box_Re=(4.0, 4.0, 4.0), grid=(24, 24, 24),
+             chiN=30.0, kappaN=50.0, seed=seed)
+    d.update(kw)
+    return SystemDesc(**d)
+
+
+def melt_slow(seed=1, **kw):
+    """Slow melt: 1,048,576 chains of N=64 in a 32x32x16 R_e0 box, 192x192x96
+    grid, chiN=40, kappaN=50.  67,108,864 particles."""
+    d = dict(n_chains=1048576, N=64, f=0.5, box_Re=(32.0, 32.0, 16.0), grid=(192, 192, 96),
+             chiN=40.0, kappaN=50.0, seed=seed)
+    d.update(kw)
+    return SystemDesc(**d)
+
+
+def scaled(desc: SystemDesc, box_Re, rho_Re3=4096.0):
+    """Same chains and interactions in another box at density rho_0 R_e0^3."""
+    cells_per_Re = desc.grid[0] / desc.box_Re[0]
+    grid = tuple(int(round(b * cells_per_Re)) for b in box_Re)
+    vol = box_Re[0] * box_Re[1] * box_Re[2]
+    n_chains = int(round(rho_Re3 * vol / desc.N))
+    return SystemDesc(n_chains=n_chains, N=desc.N, f=desc.f, box_Re=tuple(box_Re), grid=grid,
+                      chiN=desc.chiN, kappaN=desc.kappaN, a_Re=desc.a_Re, move=desc.move,
+                      set_order=desc.set_order, grid_dtype=desc.grid_dtype, seed=desc.seed,
+                      replica_id=desc.replica_id)
+
+
+def random_walk_positions(desc: SystemDesc, seed: int, bond_sigma: float = None,
+                          spread: float = 1.0) -> np.ndarray:
+    """Seeded synthetic input: chains whose first particle is uniform in the
+    box and whose bond components are normal with standard deviation
+    ``bond_sigma`` (grid units; default R_e0/sqrt(3(N-1))).  Returns a (3, M)
+    float32 array in grid units.  ``spread`` scales the box the first
+    particles are drawn from (values > 1 place chains across periodic images)."""
+    rng = np.random.default_rng(seed)
+    Re = desc.grid[0] / desc.box_Re[0]
+    if bond_sigma is None:
+        bond_sigma = Re / math.sqrt(3.0 * max(desc.N - 1, 1))
+    n, N = desc.n_chains, desc.N
+    first = rng.random((3, n, 1)) * np.asarray(desc.grid, dtype=np.float64)[:, None, None] * spread
+    steps = rng.normal(0.0, bond_sigma, size=(3, n, N - 1)) if N > 1 else np.zeros((3, n, 0))
+    walk = np.concatenate([first, first + np.cumsum(steps, axis=2)], axis=2)
+    return walk.reshape(3, n * N).astype(np.float32)
+
+
+def random_fields(cells: int, seed: int, scale: float = 1.0):
+    """Seeded synthetic field planes (omega_A, omega_B) in kT, uniform in
+    [-scale, scale), FP64."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-scale, scale, cells), rng.uniform(-scale, scale, cells)

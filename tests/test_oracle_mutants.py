@@ -1,0 +1,73 @@
+"""The oracle's pins have teeth: each plausible mistake planted in a copy of
+the oracle source (a dropped term, a wrong sign, a wrong index, a swapped
+operand) makes at least one pin fail.  Mistakes are planted on the CPU only,
+in a temporary build of ``oracle/soma_oracle.c``; no GPU code is involved."""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+from tests import test_oracle_philox as PH
+from tests import test_oracle_pins as PIN
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "soma_oracle.c")
+
+# (id, original text, planted text, pin that must fail)
+MUTANTS = [
+    ("field_sign", "(w_t[c_new] - w_t[c_old])", "(w_t[c_old] - w_t[c_new])",
+     lambda L: PIN.check_two_particle_balance_brute_force(0, L)),
+    ("field_type_swapped", "(i < s->N_A) ? wA : wB", "(i < s->N_A) ? wB : wA",
+     lambda L: PIN.check_two_particle_balance_brute_force(0, L)),
+    ("bond_half_strength", "dEb += s->K_b * (d_new - d_old);", "dEb += 0.5 * s->K_b * (d_new - d_old);",
+     PIN.check_ideal_chain_relaxes_to_gaussian_statistics),
+    ("metropolis_sign", "(lnu < -dE)", "(lnu < dE)",
+     PIN.check_ideal_chain_relaxes_to_gaussian_statistics),
+    ("one_sided_bonds", "for (int side = -1; side <= 1; side += 2)", "for (int side = -1; side < 1; side += 2)",
+     PIN.check_ideal_chain_relaxes_to_gaussian_statistics),
+    ("chi_sign", "double a = comp - 0.5 * chi0 * (phiA - phiB);", "double a = comp + 0.5 * chi0 * (phiA - phiB);",
+     PIN.check_fields_closed_forms),
+    ("kappa_dropped_minus_one", "kappa0 * (phiA + phiB - 1.0)", "kappa0 * (phiA + phiB)",
+     PIN.check_fields_closed_forms),
+    ("energy_pair_counted_twice", "0.25 * s->chiN * df * df", "0.5 * s->chiN * df * df",
+     PIN.check_fields_are_the_energy_derivative),
+    ("type_boundary", "if (i < s->N_A) nA[c] += 1u;", "if (i <= s->N_A) nA[c] += 1u;",
+     PIN.check_histogram_matches_numpy_binning_with_edge_cases),
+    ("truncate_not_floor", "long long f = (long long)floor(p[d]);", "long long f = (long long)(p[d]);",
+     PIN.check_histogram_matches_numpy_binning_with_edge_cases),
+    ("cell_axes_swapped", "return ((uint64_t)c[2] * s->grid[1] + (uint64_t)c[1]) * s->grid[0] + (uint64_t)c[0];",
+     "return ((uint64_t)c[0] * s->grid[1] + (uint64_t)c[1]) * s->grid[2] + (uint64_t)c[2];",
+     PIN.check_histogram_matches_numpy_binning_with_edge_cases),
+    ("init_sigma_N", "s->Re / sqrt(3.0 * (double)(N - 1))", "s->Re / sqrt(3.0 * (double)N)",
+     PIN.check_init_bond_and_end_to_end_statistics),
+    ("init_cos_only", "return (j % 2u == 0u) ? rad * cos(th) : rad * sin(th);", "return rad * cos(th);",
+     PIN.check_init_bond_and_end_to_end_statistics),
+    ("philox_multipliers_swapped", "uint64_t p0 = M0 * (uint64_t)c0;", "uint64_t p0 = M1 * (uint64_t)c0;",
+     lambda L: PH.check_philox_matches_curand_host_generator(1, L)),
+    ("philox_key_bump_late", "if (round > 0) { k0 += W0; k1 += W1; }", "if (round > 1) { k0 += W0; k1 += W1; }",
+     lambda L: PH.check_philox_matches_curand_host_generator(1, L)),
+    ("sq_wrong_axis", "(double)m[3 * q + 1] * cy / s->grid[1]", "(double)m[3 * q + 1] * cy / s->grid[0]",
+     PIN.check_structure_factor_matches_numpy_fft),
+    ("bond_energy_observable", "Eb += s->K_b * bb;", "Eb += 2.0 * s->K_b * bb;",
+     PIN.check_observables_hand_values),
+]
+
+
+@pytest.fixture(scope="module")
+def mutant_dir(tmp_path_factory):
+    return tmp_path_factory.mktemp("oracle_mutants")
+
+
+@pytest.mark.parametrize("mid,old,new,pin", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(oracle_lib, mutant_dir, mid, old, new, pin):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {mid} not found exactly once"
+    path_c = mutant_dir / f"{mid}.c"
+    path_c.write_text(src.replace(old, new))
+    hdr = os.path.join(os.path.dirname(SRC), "soma_oracle.h")
+    so = mutant_dir / f"lib{mid}.so"
+    subprocess.run(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                    f"-I{os.path.dirname(hdr)}", "-o", str(so), str(path_c), "-lm"], check=True)
+    L = oracle.load(str(so))
+    with pytest.raises(AssertionError):
+        pin(L)

@@ -1,0 +1,368 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks one oracle function against something other than itself:
+a closed form, an invariant, a library routine (numpy binning, numpy FFT,
+erf quadrature) or brute force.  Statistical tests use 5-sigma bounds with the
+standard error taken across independent chains.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1711_03828_gb300 import workloads
+from paper_1711_03828_gb300 import SystemDesc
+from tests.conftest import oracle_system
+
+
+# --------------------------------------------------------------------------
+# Initial configuration (Sec. 2.1: Gaussian chain, b0^2 = R_e0^2/(N-1))
+# --------------------------------------------------------------------------
+def check_init_bond_and_end_to_end_statistics(lib=None):
+    d = workloads.melt_small(n_chains=16384)
+    s = oracle_system(d, lib)
+    pos = s.init_chains()
+    P = pos.stacked().astype(np.float64).reshape(3, d.n_chains, d.N)
+    Re = d.grid[0] / d.box_Re[0]
+    sigma2 = Re**2 / (3 * (d.N - 1))
+    b = np.diff(P, axis=2).reshape(3, -1)
+    n = b.shape[1]
+    for k in range(3):
+        assert abs(b[k].mean()) < 5 * math.sqrt(sigma2 / n)
+        var = b[k].var()
+        assert abs(var / sigma2 - 1) < 5 * math.sqrt(2.0 / n)
+        kurt = np.mean(b[k] ** 4) / var**2
+        assert abs(kurt - 3.0) < 5 * math.sqrt(24.0 / n)
+    # components independent: no correlation between the axes of one bond or
+    # between consecutive bonds along the chain
+    B = np.diff(P, axis=2)  # (3, chains, N-1)
+    for k1 in range(3):
+        for k2 in range(3):
+            if k1 < k2:
+                r = np.corrcoef(B[k1].ravel(), B[k2].ravel())[0, 1]
+                assert abs(r) < 5 / math.sqrt(n)
+        r = np.corrcoef(B[k1, :, 1:].ravel(), B[k1, :, :-1].ravel())[0, 1]
+        assert abs(r) < 5 / math.sqrt(n)
+    # <R_e^2> = R_e0^2 (sum of N-1 independent bonds)
+    re2 = ((P[:, :, -1] - P[:, :, 0]) ** 2).sum(0)
+    assert abs(re2.mean() / Re**2 - 1) < 5 * re2.std() / Re**2 / math.sqrt(d.n_chains)
+    # first particles uniform in the box: mean L/2, variance L^2/12
+    for k in range(3):
+        L = d.grid[k]
+        f = P[k, :, 0]
+        assert f.min() > 0 and f.max() < L
+        assert abs(f.mean() - L / 2) < 5 * L / math.sqrt(12 * d.n_chains)
+        assert abs(f.var() / (L * L / 12) - 1) < 5 * math.sqrt(0.8 / d.n_chains)
+
+
+# --------------------------------------------------------------------------
+# Occupation numbers (Eq. density-characteristics)
+# --------------------------------------------------------------------------
+def _numpy_histogram(pos, d):
+    g = np.asarray(d.grid)
+    c = np.floor(pos.astype(np.float64)).astype(np.int64) % g[:, None]
+    idx = (c[2] * g[1] + c[1]) * g[0] + c[0]
+    typeA = (np.arange(d.M) % d.N) < int(math.floor(d.f * d.N + 0.5))
+    cells = int(np.prod(g))
+    return (np.bincount(idx[typeA], minlength=cells).astype(np.uint32),
+            np.bincount(idx[~typeA], minlength=cells).astype(np.uint32))
+
+
+def check_histogram_matches_numpy_binning_with_edge_cases(lib=None):
+    d = SystemDesc(n_chains=600, N=7, f=0.3, box_Re=(3.0, 2.0, 1.0), grid=(9, 6, 3),
+                   chiN=10.0, kappaN=50.0)
+    pos = workloads.random_walk_positions(d, seed=3, spread=3.0)
+    # positions on cell faces, just below zero, on far images, negative images
+    edge = np.array([0.0, -0.0, 1.0, 3.0, -1e-7, -1.0, 9.0, 27.0 + 0.5, -45.25, 8.999999,
+                     np.nextafter(np.float32(9.0), np.float32(0.0)), -9.0, 1e6 + 0.5], np.float32)
+    pos[0, : len(edge)] = edge
+    pos[1, 100: 100 + len(edge)] = edge
+    pos[2, 200: 200 + len(edge)] = edge[::-1]
+    s = oracle_system(d, lib)
+    from oracle import Positions
+    p = Positions(pos[0].copy(), pos[1].copy(), pos[2].copy())
+    nA, nB = s.histogram(p)
+    eA, eB = _numpy_histogram(pos, d)
+    np.testing.assert_array_equal(nA, eA)
+    np.testing.assert_array_equal(nB, eB)
+    assert int(nA.sum()) + int(nB.sum()) == d.M
+    assert int(nA.sum()) == d.n_chains * int(math.floor(d.f * d.N + 0.5))
+
+
+# --------------------------------------------------------------------------
+# Fields (Eq. omega-fields, K^0) against the energy (Eq. discrete-ham)
+# --------------------------------------------------------------------------
+def check_fields_closed_forms(lib=None):
+    # rho_0 dL^3 = 20 particles per cell
+    d = SystemDesc(n_chains=40, N=4, f=0.5, box_Re=(2.0, 2.0, 2.0), grid=(2, 2, 2),
+                   chiN=20.0, kappaN=50.0)
+    s = oracle_system(d, lib)
+    assert s.params.rho_cell == 20.0
+    cells = 8
+    nA = np.full(cells, 10, np.uint32)
+    nB = np.full(cells, 10, np.uint32)
+    wA, wB = s.fields(nA, nB)
+    assert np.all(wA == 0.0) and np.all(wB == 0.0)  # phi_A = phi_B = 1/2: no force
+    nA[0], nB[0] = 20, 0   # pure A cell at the mean density
+    nA[1], nB[1] = 0, 20   # pure B cell
+    nA[2], nB[2] = 20, 20  # twice the density, symmetric
+    wA, wB = s.fields(nA, nB)
+    chi0, kappa0 = 20.0 / 4, 50.0 / 4
+    assert wA[0] == pytest.approx(-chi0 / 2) and wB[0] == pytest.approx(chi0 / 2)
+    assert wA[1] == pytest.approx(chi0 / 2) and wB[1] == pytest.approx(-chi0 / 2)
+    assert wA[2] == pytest.approx(kappa0) and wB[2] == pytest.approx(kappa0)
+
+
+def check_fields_are_the_energy_derivative(lib=None):
+    """omega_i(c) = d(H_nb/kT)/d n_i(c): Eq. (omega-fields) first line with
+    phi = n/(rho_0 dL^3).  H_nb is quadratic, so the central difference in the
+    integer count is exact."""
+    d = SystemDesc(n_chains=300, N=10, f=0.4, box_Re=(1.5, 1.5, 1.0), grid=(3, 3, 2),
+                   chiN=27.0, kappaN=35.0)
+    s = oracle_system(d, lib)
+    rng = np.random.default_rng(7)
+    nA = rng.integers(5, 40, s.cells).astype(np.uint32)
+    nB = rng.integers(5, 40, s.cells).astype(np.uint32)
+    pos = s.empty_positions()
+    wA, wB = s.fields(nA, nB)
+    for c in range(s.cells):
+        for which, w in ((0, wA), (1, wB)):
+            up = [nA.copy(), nB.copy()]
+            dn = [nA.copy(), nB.copy()]
+            up[which][c] += 1
+            dn[which][c] -= 1
+            Eu = s.observables(pos, *up)["E_nb"]
+            Ed = s.observables(pos, *dn)["E_nb"]
+            assert (Eu - Ed) / 2 == pytest.approx(w[c], rel=1e-9, abs=1e-9)
+
+
+def check_field_rounding_modes(lib=None):
+    d = workloads.melt_small()
+    s = oracle_system(d, lib)
+    rng = np.random.default_rng(2)
+    nA = rng.integers(0, 40, s.cells).astype(np.uint32)
+    nB = rng.integers(0, 40, s.cells).astype(np.uint32)
+    w64, _ = s.fields(nA, nB, 0)
+    w32, _ = s.fields(nA, nB, 1)
+    wbf, _ = s.fields(nA, nB, 2)
+    w16, _ = s.fields(nA, nB, 3)
+    np.testing.assert_array_equal(w32, w64.astype(np.float32).astype(np.float64))
+    # BF16 keeps 8 significant bits, FP16 11 (normal range)
+    assert np.all(np.abs(wbf - w32) <= np.abs(w32) * 2.0**-8 + 1e-30)
+    assert np.all(np.abs(w16 - w32) <= np.abs(w32) * 2.0**-11 + 2.0**-24)
+    bits = wbf.astype(np.float32).view(np.uint32)
+    assert np.all(bits & 0xFFFF == 0)
+
+
+# --------------------------------------------------------------------------
+# Moves: ideal chains (chiN = kappaN = 0) relax to the Gaussian closed forms
+# --------------------------------------------------------------------------
+def check_ideal_chain_relaxes_to_gaussian_statistics(lib=None):
+    """With chiN = kappaN = 0 every field vanishes and the Metropolis chain
+    samples exp(-K_b sum b^2): <b^2> = R_e0^2/(N-1) and, the bonds being
+    independent, <R_e^2> = R_e0^2.  Start from bonds stretched by 1.6x so
+    the test sees the sweep relax the bond length."""
+    d = workloads.melt_small(n_chains=1024, N=8, chiN=0.0, kappaN=0.0, box_Re=(2.0, 2.0, 1.0),
+                             grid=(12, 12, 6))
+    s = oracle_system(d, lib)
+    Re = 6.0
+    sigma = Re / math.sqrt(3 * (d.N - 1))
+    pos0 = workloads.random_walk_positions(d, seed=11, bond_sigma=1.6 * sigma)
+    from oracle import Positions
+    p = Positions(pos0[0].copy(), pos0[1].copy(), pos0[2].copy())
+    nA, nB = s.histogram(p)
+    wA, wB = s.fields(nA, nB)
+    assert np.all(wA == 0) and np.all(wB == 0)
+    b2_t, re2_t = [], []
+    acc = att = 0
+    for sweep in range(1600):
+        st, _, _ = s.sweep(p, wA, wB, sweep)
+        acc += st.accepted
+        att += st.attempted
+        if sweep >= 600 and sweep % 4 == 0:
+            P = p.stacked().astype(np.float64).reshape(3, d.n_chains, d.N)
+            b2_t.append((np.diff(P, axis=2) ** 2).sum(0).mean(1))
+            re2_t.append(((P[:, :, -1] - P[:, :, 0]) ** 2).sum(0))
+    b2 = np.mean(b2_t, axis=0)      # per-chain time averages
+    re2 = np.mean(re2_t, axis=0)
+    se_b2 = b2.std() / math.sqrt(d.n_chains)
+    se_re2 = re2.std() / math.sqrt(d.n_chains)
+    assert abs(b2.mean() - Re**2 / (d.N - 1)) < 5 * se_b2, (b2.mean(), Re**2 / (d.N - 1), se_b2)
+    assert abs(re2.mean() - Re**2) < 5 * se_re2, (re2.mean(), Re**2, se_re2)
+    assert 0.2 < acc / att < 0.95
+
+
+# --------------------------------------------------------------------------
+# Balance: brute force on two bonded particles in fixed random fields
+# --------------------------------------------------------------------------
+def _pair_cell_probabilities(K, L, wA, wB):
+    """Stationary P(c0, c1) of a harmonic dimer, particle 0 of type A and 1 of
+    type B, in fixed fields on a periodic L^3 grid of unit cells:
+    P ∝ exp(-wA(c0) - wB(c1)) prod_axes g(c0_d, c1_d) with
+    g(a, b) = int_a^{a+1} dx0 sum_k int_{b+kL}^{b+kL+1} exp(-K (x1-x0)^2) dx1."""
+    from math import erf, sqrt, pi
+    xs, ws = np.polynomial.legendre.leggauss(64)
+
+    def g(a, b):
+        tot = 0.0
+        for x, w in zip(xs, ws):
+            x0 = a + 0.5 * (x + 1.0)
+            inner = 0.0
+            for k in range(-6, 7):
+                lo, hi = b + k * L - x0, b + k * L + 1 - x0
+                inner += 0.5 * sqrt(pi / K) * (erf(sqrt(K) * hi) - erf(sqrt(K) * lo))
+            tot += 0.5 * w * inner
+        return tot
+
+    G1 = np.array([[g(a, b) for b in range(L)] for a in range(L)])
+    cells = L**3
+    P = np.zeros((cells, cells))
+    for c0 in range(cells):
+        a = (c0 % L, (c0 // L) % L, c0 // (L * L))
+        for c1 in range(cells):
+            b = (c1 % L, (c1 // L) % L, c1 // (L * L))
+            P[c0, c1] = (math.exp(-wA[c0] - wB[c1]) * G1[a[0], b[0]] * G1[a[1], b[1]]
+                         * G1[a[2], b[2]])
+    return P / P.sum()
+
+
+def _cells_of(P3, L):
+    c = np.floor(P3.astype(np.float64)).astype(np.int64) % L
+    return (c[2] * L + c[1]) * L + c[0]
+
+
+def check_two_particle_balance_brute_force(set_order, lib=None):
+    L = 2
+    Re = 1.5
+    d = SystemDesc(n_chains=4096, N=2, f=0.5, box_Re=(L / Re,) * 3, grid=(L,) * 3,
+                   chiN=0.0, kappaN=0.0, set_order=set_order, seed=17)
+    s = oracle_system(d, lib)
+    K = s.params.K_b
+    assert K == pytest.approx(3.0 / (2 * Re * Re))
+    wA, wB = workloads.random_fields(L**3, seed=5, scale=1.0)
+    Pex = _pair_cell_probabilities(K, L, wA, wB)
+    p = s.init_chains()
+    for sweep in range(100):
+        s.sweep(p, wA, wB, sweep)
+    counts = np.zeros((d.n_chains, L**3 * L**3))
+    T = 1500
+    for sweep in range(100, 100 + T):
+        s.sweep(p, wA, wB, sweep)
+        P = p.stacked().reshape(3, d.n_chains, 2)
+        c0 = _cells_of(P[:, :, 0], L)
+        c1 = _cells_of(P[:, :, 1], L)
+        counts[np.arange(d.n_chains), c0 * L**3 + c1] += 1
+    freq = counts / T
+    est = freq.mean(0)
+    se = freq.std(0) / math.sqrt(d.n_chains)
+    z = (est - Pex.reshape(-1)) / np.maximum(se, 1e-12)
+    assert np.max(np.abs(z)) < 5.0, (np.max(np.abs(z)), np.argmax(np.abs(z)))
+    chi2 = float(np.sum(z**2))
+    assert chi2 < 64 + 8 * math.sqrt(2 * 64)  # 64 bins, loose upper bound
+
+
+# --------------------------------------------------------------------------
+# Sweep mechanics: displacements bounded by a, accepted moves land on the draw
+# --------------------------------------------------------------------------
+def check_sweep_moves_follow_the_draws(lib=None):
+    d = workloads.melt_small(n_chains=64)
+    s = oracle_system(d, lib)
+    p = s.init_chains()
+    nA, nB = s.histogram(p)
+    wA, wB = s.fields(nA, nB)
+    before = p.copy()
+    st, margin, acc = s.sweep(p, wA, wB, 3, want_margin=True, want_acc=True)
+    a32 = float(np.float32(s.params.a32))
+    for k in range(d.M):
+        w = s.draw(1, k, 3)
+        prop = [np.float32(np.float64(getattr(before, ax)[k]) +
+                           np.float64(np.float32(a32 * (((int(w[j]) >> 8) * 2 + 1) / 2**24 - 1))))
+                for j, ax in enumerate("xyz")]
+        now = [getattr(p, ax)[k] for ax in "xyz"]
+        old = [getattr(before, ax)[k] for ax in "xyz"]
+        if acc[k]:
+            assert now == prop
+        else:
+            assert now == old
+        assert (margin[k] > 0) == (not acc[k]) or margin[k] <= 0
+    assert st.accepted == int(acc.sum())
+    assert st.attempted == d.M
+    assert np.all(np.abs(p.stacked() - before.stacked()) <= a32 * (1 + 1e-6))
+
+
+# --------------------------------------------------------------------------
+# Observables
+# --------------------------------------------------------------------------
+def check_observables_hand_values(lib=None):
+    d = SystemDesc(n_chains=1, N=3, f=0.0, box_Re=(1.0, 1.0, 1.0), grid=(4, 4, 4),
+                   chiN=0.0, kappaN=0.0)
+    s = oracle_system(d, lib)
+    from oracle import Positions
+    p = Positions(np.array([0, 1, 1], np.float32), np.array([0, 0, 2], np.float32),
+                  np.array([0, 0, 0], np.float32))
+    nA, nB = s.histogram(p)
+    o = s.observables(p, nA, nB)
+    # R_e0 = 4 dL, k0/2 = 3(N-1)/(2 R_e0^2) = 6/32; bonds |b|^2 = 1 and 4
+    assert o["E_b"] == pytest.approx(5 * 6 / 32)
+    assert o["Re2"] == pytest.approx(5.0)
+    assert o["b2"] == pytest.approx(2.5)
+
+
+def check_structure_factor_matches_numpy_fft(lib=None):
+    d = SystemDesc(n_chains=400, N=8, f=0.5, box_Re=(2.0, 1.0, 1.5), grid=(8, 4, 6),
+                   chiN=10.0, kappaN=50.0)
+    s = oracle_system(d, lib)
+    p = s.init_chains()
+    nA, nB = s.histogram(p)
+    ms = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 1, 3), (-1, 2, -3), (7, 3, 5)]
+    got = s.structure_factor(nA, nB, ms)
+    dn = (nA.astype(np.float64) - nB.astype(np.float64)).reshape(d.grid[2], d.grid[1], d.grid[0])
+    F = np.fft.fftn(dn)
+    for (mx, my, mz), v in zip(ms, got):
+        ref = abs(F[mz % d.grid[2], my % d.grid[1], mx % d.grid[0]]) ** 2 / d.M
+        assert v == pytest.approx(ref, rel=1e-10, abs=1e-9)
+
+
+# --------------------------------------------------------------------------
+# The pins as tests (the mutation tests run the same checks on planted mistakes)
+# --------------------------------------------------------------------------
+
+def test_init_bond_and_end_to_end_statistics(oracle_lib):
+    check_init_bond_and_end_to_end_statistics()
+
+
+def test_histogram_matches_numpy_binning_with_edge_cases(oracle_lib):
+    check_histogram_matches_numpy_binning_with_edge_cases()
+
+
+def test_fields_closed_forms(oracle_lib):
+    check_fields_closed_forms()
+
+
+def test_fields_are_the_energy_derivative(oracle_lib):
+    check_fields_are_the_energy_derivative()
+
+
+def test_field_rounding_modes(oracle_lib):
+    check_field_rounding_modes()
+
+
+def test_ideal_chain_relaxes_to_gaussian_statistics(oracle_lib):
+    check_ideal_chain_relaxes_to_gaussian_statistics()
+
+
+@pytest.mark.parametrize("set_order", [0, 1])
+def test_two_particle_balance_brute_force(oracle_lib, set_order):
+    check_two_particle_balance_brute_force(set_order)
+
+
+def test_sweep_moves_follow_the_draws(oracle_lib):
+    check_sweep_moves_follow_the_draws()
+
+
+def test_observables_hand_values(oracle_lib):
+    check_observables_hand_values()
+
+
+def test_structure_factor_matches_numpy_fft(oracle_lib):
+    check_structure_factor_matches_numpy_fft()
