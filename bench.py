@@ -1,0 +1,323 @@
+"""Benchmark: monomer Monte-Carlo moves per second of the SCMF cycle
+(sweep + occupation count + field update), arXiv:1711.03828.
+
+Default workload: the lamella-forming diblock melt at scale, 4,194,304 chains
+of N=32 (134,217,728 particles) in a 32^3 R_e0 box, 192^3 grid, chiN=30,
+kappaN=50.  One step = one SCMF cycle of every particle.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs an independent
+replica of the workload (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "monomer MC moves/s incl. field update"
+UNIT = "moves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="melt_large",
+                    choices=["melt_large", "melt_small", "melt_slow", "melt_subbox"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def workload(name, replica=0):
+    from paper_1711_03828_gb300 import workloads
+    d = getattr(workloads, name)(seed=1)
+    d.replica_id = replica
+    return d
+
+
+def config_of(d, name, l2_note):
+    return {"workload": f"{name}: {d.n_chains} chains x N={d.N}, box {d.box_Re} R_e0, grid "
+                        f"{d.grid}, chiN={d.chiN}, kappaN={d.kappaN}",
+            "n_chains": d.n_chains, "N": d.N, "particles": d.M, "grid": list(d.grid),
+            "box_Re": list(d.box_Re), "chiN": d.chiN, "kappaN": d.kappaN, "move": "uniform",
+            "set_order": "random per chain and sweep", "l2": l2_note}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (the baseline; never tuned)
+# --------------------------------------------------------------------------
+def oracle_rate(name, seconds, max_steps=None):
+    """Oracle cycles (sweep + histogram + fields) on a 4^3 R_e0 sub-box of the
+    workload (same N, density, grid spacing, chiN).  Returns (moves/s, cores,
+    sample, steps)."""
+    import oracle
+    from paper_1711_03828_gb300 import workloads
+    d = workload(name)
+    sub = workloads.scaled(d, (4.0, 4.0, 4.0))
+    o = oracle.System(sub.n_chains, sub.N, sub.f, sub.box_Re, sub.grid, sub.chiN, sub.kappaN,
+                      seed=sub.seed)
+    p = o.init_chains()
+    nA, nB = o.histogram(p)
+    wA, wB = o.fields(nA, nB)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        o.sweep(p, wA, wB, steps)
+        nA, nB = o.histogram(p)
+        wA, wB = o.fields(nA, nB)
+        steps += 1
+        el = time.perf_counter() - t0
+        if (max_steps is not None and steps >= max_steps) or (max_steps is None and el >= seconds):
+            break
+    sample = (f"oracle cycles on a 4^3 R_e0 sub-box of the workload ({sub.n_chains} chains x "
+              f"N={sub.N}, grid {sub.grid}, chiN={sub.chiN}): {steps} cycles, {el:.2f} s")
+    return sub.M * steps / el, oracle.num_threads(), sample, steps, el
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import build as ob
+    if not os.path.exists(os.path.join(ROOT, "oracle", "liboracle.so")):
+        ob.build()
+    total = args.warmup + args.steps
+    # warm-up cycles are not timed: run them first
+    oracle_rate(args.workload, 0.0, max_steps=max(args.warmup, 1))
+    rate, cores, sample, steps, el = oracle_rate(args.workload, 0.0, max_steps=args.steps)
+    d = workload(args.workload)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(d, args.workload, "CPU"),
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    _ = total
+
+
+# --------------------------------------------------------------------------
+# Clock sampling during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.lines = []
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+            time.sleep(0.3)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for l in self.proc.stdout:
+            self.lines.append(l.strip())
+
+    def __exit__(self, *a):
+        if self.proc is None:
+            self.out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                pw.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        import statistics
+        self.out = {"sm_mhz": statistics.median(sm) if sm else None,
+                    "sm_max_mhz": max(mx) if mx else None,
+                    "power_w_max": max(pw) if pw else None,
+                    "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            v = json.load(f)
+        return float(v["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def sweep_kernel_bytes(d):
+    """Algorithmic bytes of one sweep-kernel launch: every position read and
+    written once (24 B per particle), each omega plane read once and the
+    occupation grid written once (12 B per cell for FP32 omega)."""
+    cells = d.grid[0] * d.grid[1] * d.grid[2]
+    wb = 4 if d.grid_dtype == 0 else 2
+    return 24 * d.M + cells * (2 * wb + 4)
+
+
+def field_kernel_bytes(d):
+    cells = d.grid[0] * d.grid[1] * d.grid[2]
+    wb = 4 if d.grid_dtype == 0 else 2
+    return cells * (4 + 4 + 2 * wb)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as tdist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1711_03828_gb300 import System, _abi
+
+    d = workload(args.workload, replica=rank)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    s = System(d, stream=stream)
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+
+    # warm-up (graph path and eager path both exercised)
+    s.sweep(args.warmup)
+    s.sync()
+    s.set_timing(True)
+    t_before = s.timing()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record(stream)
+        s.sweep(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    t_after = s.timing()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    launches = t_after["kernel_launches"] - t_before["kernel_launches"]
+    value = d.M * args.steps * world / (ms * 1e-3)
+    sweep_ms = t_after["ms_sweep"] / max(t_after["sweep_launches"] - t_before["sweep_launches"], 1)
+    field_ms = t_after["ms_fields"] / max(t_after["field_launches"] - t_before["field_launches"], 1)
+    s.set_timing(False)
+    peak, peak_kind = measured_peak_hbm()
+    achieved = sweep_kernel_bytes(d) / (sweep_ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers: every step copies the
+    # positions in from pinned memory, runs one cycle and reads the occupation
+    # grid back
+    host_pos = torch.empty(3 * d.M, dtype=torch.float32, pin_memory=True)
+    import ctypes
+    _abi.soma_get_positions(s.h, ctypes.c_void_p(host_pos.data_ptr()), 3 * d.M, 0)
+    host_n = torch.empty(d.cells, dtype=torch.int32, pin_memory=True)
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        _abi.soma_set_positions(s.h, ctypes.c_void_p(host_pos.data_ptr()), 3 * d.M, 0)
+        _abi.soma_sweep(s.h, 1)
+        _abi.soma_get_density(s.h, ctypes.c_void_p(host_n.data_ptr()), d.cells, 0)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": d.M * e2e_steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 12 * d.M, "d2h_bytes_per_step": 4 * d.cells,
+           "steps": e2e_steps}
+    obs = s.observables()
+    s.close()
+
+    if rank != 0:
+        if world > 1:
+            tdist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_of(d, args.workload,
+                            f"inputs larger than L2 ({12 * d.M / 1e9:.2f} GB of positions)"),
+        "roofline": {"bound": "hbm", "kernel": "sweep_uniform_kernel", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "traffic": None,
+                     "bytes_per_launch": sweep_kernel_bytes(d), "ms_per_launch": sweep_ms,
+                     "field_kernel_ms": field_ms,
+                     "field_kernel_gbs": field_kernel_bytes(d) / (field_ms * 1e-3) / 1e9},
+        "e2e": e2e,
+        "clocks": clk.out,
+        "gpu_launches": int(launches),
+        "acceptance": obs["accepted"] / max(obs["attempted"], 1),
+    }
+    if not args.no_cpu_baseline and world == 1:
+        rate, cores, sample, _, _ = oracle_rate(args.workload, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

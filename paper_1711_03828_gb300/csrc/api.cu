@@ -1,0 +1,590 @@
+// api.cu -- the C ABI of libsoma (declared in include/soma.h).
+//
+// A soma_t owns the device state of one system:
+//   positions   3 FP32 planes x|y|z of M floats (one allocation, planes
+//               256-byte aligned), unwrapped, dL units;
+//   n[2]        packed occupation grids (A | B<<16), double-buffered: the
+//               sweep of step s counts into n[(s+1)&1] while omega holds the
+//               fields of n[s&1];
+//   omega       two planes (A, B) of the storage type (FP32/BF16/FP16);
+//   counters    sweep counter (the Philox word w), accepted moves, sticky
+//               error bits, the field kernel's arrival counter;
+//   scratch     FP64 partial sums of the observables and S(q) reductions.
+// A cycle is two launches (sweep, fields); soma_sweep replays them from a
+// CUDA graph of GRAPH_CHUNK cycles when timing is off.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/soma.h"
+#include "kernels.h"
+
+using namespace soma;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+soma_status fail(soma_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+soma_status fail(soma_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+soma_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? SOMA_ENOMEM : SOMA_ECUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define SOMA_CUDA(call)                                  \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+constexpr uint32_t GRAPH_CHUNK = 16;
+constexpr uint64_t MAX_M = 1ull << 40;
+
+}  // namespace
+
+struct soma_t {
+  soma_system_desc desc;
+  Geom g;
+  double Re;        // R_e0 in dL
+  double a64;       // maximal displacement in dL
+  float a32;
+  double K_b;
+  double rho_cell;  // rho_0 dL^3
+  double sigma;     // bond component standard deviation in dL
+  int grid_dtype;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  uint64_t M = 0;
+  uint64_t plane = 0;  // floats per position plane (padded)
+  float* pos = nullptr;
+  uint32_t* n[2] = {nullptr, nullptr};
+  void* w[2] = {nullptr, nullptr};
+  unsigned long long* d_counters = nullptr;  // [0] sweep, [1] accepted
+  unsigned* d_err = nullptr;                 // [0] error bits, [1] arrival counter
+  double* d_scratch = nullptr;
+  double* d_out = nullptr;
+  size_t scratch_doubles = 0;
+  double* d_tw = nullptr;
+  size_t tw_doubles = 0;
+  SweepShape shape;
+  uint64_t host_sweep = 0;
+  uint64_t launches = 0;
+  bool timing = false;
+  struct EvPair { cudaEvent_t a, b; int kind; };
+  std::vector<EvPair> ev_pending;
+  std::vector<cudaEvent_t> ev_free;
+  soma_timing t{};
+  cudaGraphExec_t graph = nullptr;
+
+  float* x() { return pos; }
+  float* y() { return pos + plane; }
+  float* z() { return pos + 2 * plane; }
+};
+
+namespace {
+
+soma_status validate(const soma_system_desc* d) {
+  if (!d) return fail(SOMA_EINVAL, "desc is NULL");
+  if (d->struct_size != sizeof(soma_system_desc))
+    return fail(SOMA_EINVAL, "desc.struct_size %u != %zu", d->struct_size, sizeof(soma_system_desc));
+  if (d->N < 1 || d->N > 256) return fail(SOMA_EINVAL, "N=%u outside 1..256", d->N);
+  if (d->n_chains < 1) return fail(SOMA_EINVAL, "n_chains must be >= 1");
+  if (d->n_chains > MAX_M / d->N) return fail(SOMA_EINVAL, "M = n_chains*N exceeds 2^40");
+  if (!(d->f >= 0.0 && d->f <= 1.0)) return fail(SOMA_EINVAL, "f=%g outside [0,1]", d->f);
+  uint64_t cells = 1;
+  for (int k = 0; k < 3; ++k) {
+    if (!(d->box_Re[k] > 0.0) || !std::isfinite(d->box_Re[k]))
+      return fail(SOMA_EINVAL, "box_Re[%d]=%g must be > 0", k, d->box_Re[k]);
+    if (d->grid[k] < 1 || d->grid[k] > 4096)
+      return fail(SOMA_EINVAL, "grid[%d]=%u outside 1..4096", k, d->grid[k]);
+    cells *= d->grid[k];
+  }
+  if (cells > 0x7FFFFFFFull) return fail(SOMA_EINVAL, "grid has %llu cells (max 2^31-1)",
+                                         (unsigned long long)cells);
+  const double dl0 = d->box_Re[0] / d->grid[0];
+  for (int k = 1; k < 3; ++k) {
+    const double dl = d->box_Re[k] / d->grid[k];
+    if (std::fabs(dl - dl0) > 1e-9 * dl0)
+      return fail(SOMA_EINVAL, "cells are not cubic: dL differs between axes 0 and %d", k);
+  }
+  if (!std::isfinite(d->chiN) || !std::isfinite(d->kappaN) || !std::isfinite(d->a_Re))
+    return fail(SOMA_EINVAL, "chiN, kappaN and a_Re must be finite");
+  if (d->move != SOMA_MOVE_UNIFORM)
+    return fail(SOMA_EINVAL, "move=%d is not available", d->move);
+  if (d->set_order != SOMA_SET_ORDER_RANDOM && d->set_order != SOMA_SET_ORDER_FIXED)
+    return fail(SOMA_EINVAL, "set_order=%d unknown", d->set_order);
+  if (d->grid_dtype < 0 || d->grid_dtype > 2)
+    return fail(SOMA_EINVAL, "grid_dtype=%d unknown", d->grid_dtype);
+  if (d->flags != 0) return fail(SOMA_EINVAL, "flags must be 0");
+  if (d->replica_id > 0xFFFFFFu) return fail(SOMA_EINVAL, "replica_id must be < 2^24");
+  return SOMA_OK;
+}
+
+void derive(soma_t* h) {
+  const soma_system_desc& d = h->desc;
+  h->Re = (double)d.grid[0] / d.box_Re[0];
+  double a_Re = d.a_Re;
+  if (!(a_Re > 0.0)) a_Re = (d.N > 1) ? 0.5 / std::sqrt((double)(d.N - 1)) : 0.5;
+  h->a64 = a_Re * h->Re;
+  h->a32 = (float)h->a64;
+  h->K_b = (d.N > 1) ? 3.0 * (double)(d.N - 1) / (2.0 * h->Re * h->Re) : 0.0;
+  h->sigma = (d.N > 1) ? h->Re / std::sqrt(3.0 * (double)(d.N - 1)) : 0.0;
+  h->M = d.n_chains * d.N;
+  const double cells = (double)d.grid[0] * (double)d.grid[1] * (double)d.grid[2];
+  h->rho_cell = (double)h->M / cells;
+  h->grid_dtype = d.grid_dtype;
+  Geom& g = h->g;
+  g.n_chains = d.n_chains;
+  g.N = d.N;
+  uint32_t NA = (uint32_t)std::floor(d.f * (double)d.N + 0.5);
+  g.N_A = NA > d.N ? d.N : NA;
+  g.nx = (int)d.grid[0];
+  g.ny = (int)d.grid[1];
+  g.nz = (int)d.grid[2];
+  g.inv_nx = 1.0f / (float)g.nx;
+  g.inv_ny = 1.0f / (float)g.ny;
+  g.inv_nz = 1.0f / (float)g.nz;
+  g.cells = (uint32_t)(d.grid[0] * d.grid[1] * d.grid[2]);
+  g.key0 = (uint32_t)d.seed;
+  g.key1 = (uint32_t)(d.seed >> 32);
+  g.replica = d.replica_id;
+}
+
+size_t wbytes(int dtype) { return dtype == 0 ? 4 : 2; }
+
+void release(soma_t* h) {
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (auto& p : h->ev_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  for (auto e : h->ev_free) cudaEventDestroy(e);
+  cudaFree(h->pos);
+  cudaFree(h->n[0]);
+  cudaFree(h->n[1]);
+  cudaFree(h->w[0]);
+  cudaFree(h->w[1]);
+  cudaFree(h->d_counters);
+  cudaFree(h->d_err);
+  cudaFree(h->d_scratch);
+  cudaFree(h->d_tw);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+FieldArgs field_args(soma_t* h, int after_sweep) {
+  FieldArgs f;
+  f.g = h->g;
+  f.n0 = h->n[0];
+  f.n1 = h->n[1];
+  f.wA = h->w[0];
+  f.wB = h->w[1];
+  f.d_sweep = h->d_counters;
+  f.err = h->d_err;
+  f.inv_rho = (float)(1.0 / h->rho_cell);
+  f.kappa0 = (float)(h->desc.kappaN / (double)h->desc.N);
+  f.half_chi0 = (float)(0.5 * h->desc.chiN / (double)h->desc.N);
+  f.after_sweep = after_sweep;
+  return f;
+}
+
+SweepArgs sweep_args(soma_t* h) {
+  SweepArgs s;
+  s.g = h->g;
+  s.x = h->x();
+  s.y = h->y();
+  s.z = h->z();
+  s.wA = h->w[0];
+  s.wB = h->w[1];
+  s.n0 = h->n[0];
+  s.n1 = h->n[1];
+  s.acc = h->d_counters + 1;
+  s.d_sweep = h->d_counters;
+  s.a = h->a32;
+  s.K_b = (float)h->K_b;
+  s.G = h->shape.G;
+  s.n_tiles = h->shape.n_tiles;
+  s.set_order_random = h->desc.set_order == SOMA_SET_ORDER_RANDOM;
+  return s;
+}
+
+cudaEvent_t take_event(soma_t* h) {
+  if (!h->ev_free.empty()) {
+    cudaEvent_t e = h->ev_free.back();
+    h->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch one kernel (kind 0 sweep, 1 fields), bracketed by events if timing.
+template <typename F>
+soma_status timed(soma_t* h, int kind, F&& launch) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (h->timing) {
+    a = take_event(h);
+    b = take_event(h);
+    SOMA_CUDA(cudaEventRecord(a, h->stream));
+  }
+  cudaError_t e = launch();
+  if (e != cudaSuccess) return cuda_fail(e, kind == 0 ? "sweep kernel launch" : "field kernel launch");
+  ++h->launches;
+  if (kind == 0) ++h->t.sweep_launches; else ++h->t.field_launches;
+  if (h->timing) {
+    SOMA_CUDA(cudaEventRecord(b, h->stream));
+    h->ev_pending.push_back({a, b, kind});
+  }
+  return SOMA_OK;
+}
+
+soma_status one_cycle(soma_t* h) {
+  const SweepArgs sa = sweep_args(h);
+  soma_status st = timed(h, 0, [&] { return launch_sweep_uniform(sa, h->shape, h->grid_dtype, h->stream); });
+  if (st != SOMA_OK) return st;
+  const FieldArgs fa = field_args(h, 1);
+  st = timed(h, 1, [&] { return launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count, h->stream); });
+  if (st != SOMA_OK) return st;
+  ++h->host_sweep;
+  return SOMA_OK;
+}
+
+soma_status build_graph(soma_t* h) {
+  cudaGraph_t gr = nullptr;
+  SOMA_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  const SweepArgs sa = sweep_args(h);
+  const FieldArgs fa = field_args(h, 1);
+  cudaError_t e = cudaSuccess;
+  for (uint32_t k = 0; k < GRAPH_CHUNK && e == cudaSuccess; ++k) {
+    e = launch_sweep_uniform(sa, h->shape, h->grid_dtype, h->stream);
+    if (e == cudaSuccess) e = launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count, h->stream);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(h->stream, &gr);
+  if (e != cudaSuccess) { if (gr) cudaGraphDestroy(gr); return cuda_fail(e, "graph capture"); }
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&h->graph, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) { h->graph = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+  return SOMA_OK;
+}
+
+soma_status check_sticky(soma_t* h) {
+  unsigned err = 0;
+  SOMA_CUDA(cudaMemcpy(&err, h->d_err, sizeof err, cudaMemcpyDeviceToHost));
+  if (err & ERR_OVERFLOW) return fail(SOMA_EOVERFLOW, "a 16-bit occupation number reached 0xC000");
+  if (err & ERR_TIMEOUT) return fail(SOMA_ETIMEOUT, "a bounded device wait gave up");
+  return SOMA_OK;
+}
+
+soma_status sync(soma_t* h) {
+  SOMA_CUDA(cudaStreamSynchronize(h->stream));
+  return check_sticky(h);
+}
+
+soma_status update_fields(soma_t* h) {
+  // count into n[s&1] (cleared first), then omega from it
+  uint32_t* nn = h->n[h->host_sweep & 1];
+  SOMA_CUDA(cudaMemsetAsync(nn, 0, sizeof(uint32_t) * h->g.cells, h->stream));
+  SOMA_CUDA(launch_histogram(h->g, h->x(), h->y(), h->z(), nn, h->sm_count, h->stream));
+  ++h->launches;
+  const FieldArgs fa = field_args(h, 0);
+  SOMA_CUDA(launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count, h->stream));
+  ++h->launches;
+  return SOMA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int soma_abi_version(void) { return SOMA_ABI_VERSION; }
+
+const char* soma_last_error(void) { return g_last_error.c_str(); }
+
+soma_status soma_create(const soma_system_desc* desc, soma_t** out) {
+  if (!out) return fail(SOMA_EINVAL, "out is NULL");
+  *out = nullptr;
+  soma_status st = validate(desc);
+  if (st != SOMA_OK) return st;
+  soma_t* h = new (std::nothrow) soma_t();
+  if (!h) return fail(SOMA_ENOMEM, "host allocation failed");
+  h->desc = *desc;
+  derive(h);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) { delete h; return cuda_fail(e, "device query"); }
+  if (desc->stream) {
+    h->stream = (cudaStream_t)desc->stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaStreamCreate"); }
+    h->own_stream = true;
+  }
+  h->plane = (h->M + 63) & ~63ull;
+  const size_t cells = h->g.cells;
+  const size_t wb = wbytes(h->grid_dtype);
+  h->scratch_doubles = (size_t)SQ_BLOCKS * 2 * SQ_MAX;
+  if (h->scratch_doubles < 4 * (size_t)OBS_BLOCKS) h->scratch_doubles = 4 * (size_t)OBS_BLOCKS;
+#define ALLOC(ptr, bytes)                                                   \
+  do {                                                                      \
+    e = cudaMalloc((void**)&(ptr), (bytes));                                \
+    if (e != cudaSuccess) { release(h); return cuda_fail(e, "cudaMalloc " #ptr); } \
+  } while (0)
+  ALLOC(h->pos, sizeof(float) * 3 * h->plane);
+  ALLOC(h->n[0], sizeof(uint32_t) * cells);
+  ALLOC(h->n[1], sizeof(uint32_t) * cells);
+  ALLOC(h->w[0], wb * cells);
+  ALLOC(h->w[1], wb * cells);
+  ALLOC(h->d_counters, sizeof(unsigned long long) * 2);
+  ALLOC(h->d_err, sizeof(unsigned) * 2);
+  ALLOC(h->d_scratch, sizeof(double) * (h->scratch_doubles + 64));
+#undef ALLOC
+  h->d_out = h->d_scratch + h->scratch_doubles;
+  h->shape = sweep_shape(h->g.n_chains, h->g.N, h->sm_count, h->grid_dtype);
+#define CK(call) do { e = (call); if (e != cudaSuccess) { release(h); return cuda_fail(e, #call); } } while (0)
+  CK(cudaMemsetAsync(h->n[0], 0, sizeof(uint32_t) * cells, h->stream));
+  CK(cudaMemsetAsync(h->n[1], 0, sizeof(uint32_t) * cells, h->stream));
+  CK(cudaMemsetAsync(h->d_counters, 0, sizeof(unsigned long long) * 2, h->stream));
+  CK(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned) * 2, h->stream));
+  CK(launch_init(h->g, h->x(), h->y(), h->z(), h->sigma, h->sm_count, h->stream));
+#undef CK
+  ++h->launches;
+  st = update_fields(h);
+  if (st == SOMA_OK) st = sync(h);
+  if (st != SOMA_OK) { std::string m = g_last_error; release(h); g_last_error = m; return st; }
+  *out = h;
+  return SOMA_OK;
+}
+
+soma_status soma_destroy(soma_t* h) {
+  if (!h) return SOMA_OK;
+  release(h);
+  return SOMA_OK;
+}
+
+soma_status soma_sweep(soma_t* h, uint32_t n) {
+  if (!h) return fail(SOMA_EINVAL, "handle is NULL");
+  uint32_t done = 0;
+  if (!h->timing && n >= GRAPH_CHUNK) {
+    if (!h->graph) {
+      soma_status st = build_graph(h);
+      if (st != SOMA_OK) return st;
+    }
+    while (n - done >= GRAPH_CHUNK) {
+      SOMA_CUDA(cudaGraphLaunch(h->graph, h->stream));
+      h->launches += 2 * GRAPH_CHUNK;
+      h->t.sweep_launches += GRAPH_CHUNK;
+      h->t.field_launches += GRAPH_CHUNK;
+      h->host_sweep += GRAPH_CHUNK;
+      done += GRAPH_CHUNK;
+    }
+  }
+  for (; done < n; ++done) {
+    soma_status st = one_cycle(h);
+    if (st != SOMA_OK) return st;
+  }
+  return SOMA_OK;
+}
+
+soma_status soma_update_fields(soma_t* h) {
+  if (!h) return fail(SOMA_EINVAL, "handle is NULL");
+  return update_fields(h);
+}
+
+soma_status soma_sync(soma_t* h) {
+  if (!h) return fail(SOMA_EINVAL, "handle is NULL");
+  return sync(h);
+}
+
+void* soma_stream(soma_t* h) { return h ? (void*)h->stream : nullptr; }
+
+soma_status soma_get_density(soma_t* h, uint32_t* dst, size_t n_cells, int dst_on_device) {
+  if (!h || !dst) return fail(SOMA_EINVAL, "NULL argument");
+  if (n_cells != h->g.cells) return fail(SOMA_EINVAL, "n_cells=%zu, grid has %u", n_cells, h->g.cells);
+  const uint32_t* src = h->n[h->host_sweep & 1];
+  SOMA_CUDA(cudaMemcpyAsync(dst, src, sizeof(uint32_t) * n_cells,
+                            dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            h->stream));
+  return sync(h);
+}
+
+soma_status soma_get_fields(soma_t* h, float* dst, size_t n, int dst_on_device) {
+  if (!h || !dst) return fail(SOMA_EINVAL, "NULL argument");
+  const size_t cells = h->g.cells;
+  if (n != 2 * cells) return fail(SOMA_EINVAL, "n=%zu, expected 2*cells=%zu", n, 2 * cells);
+  if (h->grid_dtype == 0) {
+    const cudaMemcpyKind k = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    SOMA_CUDA(cudaMemcpyAsync(dst, h->w[0], sizeof(float) * cells, k, h->stream));
+    SOMA_CUDA(cudaMemcpyAsync(dst + cells, h->w[1], sizeof(float) * cells, k, h->stream));
+    return sync(h);
+  }
+  float* tmp = dst;
+  if (!dst_on_device) SOMA_CUDA(cudaMallocAsync((void**)&tmp, sizeof(float) * 2 * cells, h->stream));
+  SOMA_CUDA(launch_convert_fields(h->w[0], h->grid_dtype, tmp, cells, h->stream));
+  SOMA_CUDA(launch_convert_fields(h->w[1], h->grid_dtype, tmp + cells, cells, h->stream));
+  h->launches += 2;
+  if (!dst_on_device) {
+    SOMA_CUDA(cudaMemcpyAsync(dst, tmp, sizeof(float) * 2 * cells, cudaMemcpyDeviceToHost, h->stream));
+    SOMA_CUDA(cudaFreeAsync(tmp, h->stream));
+  }
+  return sync(h);
+}
+
+soma_status soma_get_positions(soma_t* h, float* dst, size_t n, int dst_on_device) {
+  if (!h || !dst) return fail(SOMA_EINVAL, "NULL argument");
+  if (n != 3 * h->M) return fail(SOMA_EINVAL, "n=%zu, expected 3*M=%llu", n, (unsigned long long)(3 * h->M));
+  const cudaMemcpyKind k = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  for (int d = 0; d < 3; ++d)
+    SOMA_CUDA(cudaMemcpyAsync(dst + d * h->M, h->pos + d * h->plane, sizeof(float) * h->M, k, h->stream));
+  return sync(h);
+}
+
+soma_status soma_set_positions(soma_t* h, const float* src, size_t n, int src_on_device) {
+  if (!h || !src) return fail(SOMA_EINVAL, "NULL argument");
+  if (n != 3 * h->M) return fail(SOMA_EINVAL, "n=%zu, expected 3*M=%llu", n, (unsigned long long)(3 * h->M));
+  const cudaMemcpyKind k = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  for (int d = 0; d < 3; ++d)
+    SOMA_CUDA(cudaMemcpyAsync(h->pos + d * h->plane, src + d * h->M, sizeof(float) * h->M, k, h->stream));
+  if (!src_on_device) SOMA_CUDA(cudaStreamSynchronize(h->stream));
+  return SOMA_OK;
+}
+
+soma_status soma_observables(soma_t* h, soma_obs* out) {
+  if (!h || !out) return fail(SOMA_EINVAL, "NULL argument");
+  const uint32_t* nn = h->n[h->host_sweep & 1];
+  SOMA_CUDA(launch_observables(h->g, h->x(), h->y(), h->z(), nn, 1.0 / h->rho_cell,
+                               h->desc.kappaN, h->desc.chiN, h->d_scratch, h->d_out, h->stream));
+  h->launches += 3;
+  double r[4];
+  unsigned long long c[2];
+  SOMA_CUDA(cudaMemcpyAsync(r, h->d_out, sizeof r, cudaMemcpyDeviceToHost, h->stream));
+  SOMA_CUDA(cudaMemcpyAsync(c, h->d_counters, sizeof c, cudaMemcpyDeviceToHost, h->stream));
+  soma_status st = sync(h);
+  if (st != SOMA_OK) return st;
+  const double nch = (double)h->g.n_chains;
+  const double nb = nch * (double)(h->g.N > 1 ? h->g.N - 1 : 0);
+  out->E_b = h->K_b * r[0];
+  out->E_nb = h->rho_cell / (double)h->g.N * r[2];
+  out->E_tot = out->E_b + out->E_nb;
+  out->Re2 = r[1] / nch;
+  out->Re2_rel = out->Re2 / (h->Re * h->Re);
+  out->b2 = nb > 0 ? r[0] / nb : 0.0;
+  out->accepted = c[1];
+  out->sweeps = c[0];
+  out->attempted = c[0] * h->M;
+  out->max_cell = (uint32_t)r[3];
+  out->reserved = 0;
+  return SOMA_OK;
+}
+
+soma_status soma_structure_factor(soma_t* h, const int32_t* m, size_t k, double* out) {
+  if (!h || !m || !out) return fail(SOMA_EINVAL, "NULL argument");
+  if (k > 4096) return fail(SOMA_EINVAL, "k=%zu > 4096", k);
+  if (k == 0) return SOMA_OK;
+  const int nx = h->g.nx, ny = h->g.ny, nz = h->g.nz;
+  const size_t T = (size_t)nx + ny + nz;
+  const size_t need = (size_t)SQ_MAX * T * 2;
+  if (h->tw_doubles < need) {
+    cudaFree(h->d_tw);
+    h->d_tw = nullptr;
+    SOMA_CUDA(cudaMalloc((void**)&h->d_tw, sizeof(double) * need));
+    h->tw_doubles = need;
+  }
+  std::vector<double> tw(need);
+  const uint32_t* nn = h->n[h->host_sweep & 1];
+  const double two_pi = 6.283185307179586;
+  for (size_t q0 = 0; q0 < k; q0 += SQ_MAX) {
+    const int kk = (int)((k - q0) < (size_t)SQ_MAX ? (k - q0) : (size_t)SQ_MAX);
+    for (int q = 0; q < kk; ++q) {
+      const int n3[3] = {nx, ny, nz};
+      size_t off = (size_t)q * T * 2;
+      for (int d = 0; d < 3; ++d) {
+        const long long md = m[3 * (q0 + q) + d];
+        for (int c = 0; c < n3[d]; ++c) {
+          long long r = (md * c) % n3[d];
+          if (r < 0) r += n3[d];
+          const double ph = two_pi * (double)r / (double)n3[d];
+          tw[off++] = std::cos(ph);
+          tw[off++] = -std::sin(ph);
+        }
+      }
+    }
+    SOMA_CUDA(cudaMemcpyAsync(h->d_tw, tw.data(), sizeof(double) * kk * T * 2,
+                              cudaMemcpyHostToDevice, h->stream));
+    SOMA_CUDA(launch_structure_factor(h->g, nn, h->d_tw, kk, h->d_scratch, h->d_out, h->stream));
+    h->launches += 2;
+    SOMA_CUDA(cudaMemcpyAsync(out + q0, h->d_out, sizeof(double) * kk, cudaMemcpyDeviceToHost,
+                              h->stream));
+    soma_status st = sync(h);
+    if (st != SOMA_OK) return st;
+  }
+  return SOMA_OK;
+}
+
+soma_status soma_get_sweep(soma_t* h, uint64_t* out) {
+  if (!h || !out) return fail(SOMA_EINVAL, "NULL argument");
+  *out = h->host_sweep;
+  return SOMA_OK;
+}
+
+soma_status soma_set_sweep(soma_t* h, uint64_t sweep) {
+  if (!h) return fail(SOMA_EINVAL, "handle is NULL");
+  unsigned long long v = sweep;
+  SOMA_CUDA(cudaMemcpyAsync(h->d_counters, &v, sizeof v, cudaMemcpyHostToDevice, h->stream));
+  SOMA_CUDA(cudaStreamSynchronize(h->stream));
+  h->host_sweep = sweep;
+  // the occupation buffer in use depends on the counter's parity
+  SOMA_CUDA(cudaMemsetAsync(h->n[(sweep + 1) & 1], 0, sizeof(uint32_t) * h->g.cells, h->stream));
+  return update_fields(h);
+}
+
+soma_status soma_set_timing(soma_t* h, int on) {
+  if (!h) return fail(SOMA_EINVAL, "handle is NULL");
+  SOMA_CUDA(cudaStreamSynchronize(h->stream));
+  for (auto& p : h->ev_pending) { h->ev_free.push_back(p.a); h->ev_free.push_back(p.b); }
+  h->ev_pending.clear();
+  h->timing = on != 0;
+  if (h->timing) {
+    h->t.ms_sweep = h->t.ms_fields = 0.0;
+  }
+  return SOMA_OK;
+}
+
+soma_status soma_get_timing(soma_t* h, soma_timing* out) {
+  if (!h || !out) return fail(SOMA_EINVAL, "NULL argument");
+  SOMA_CUDA(cudaStreamSynchronize(h->stream));
+  for (auto& p : h->ev_pending) {
+    float ms = 0.f;
+    SOMA_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+    if (p.kind == 0) h->t.ms_sweep += ms; else h->t.ms_fields += ms;
+    h->ev_free.push_back(p.a);
+    h->ev_free.push_back(p.b);
+  }
+  h->ev_pending.clear();
+  *out = h->t;
+  out->kernel_launches = h->launches;
+  return SOMA_OK;
+}
+
+soma_status soma_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
+                        void* stream) {
+  if (n && (!ctr || !key || !out)) return fail(SOMA_EINVAL, "NULL argument");
+  SOMA_CUDA(launch_philox(ctr, key, out, n, (cudaStream_t)stream));
+  return SOMA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// common.cuh -- device-side building blocks of libsoma (sm_103a).
+//
+// Philox4x32-10 counter RNG (Salmon, Moraes, Dror, Shaw, SC'11), the uniform
+// maps, the periodic cell fold and the kernel argument blocks.  Nothing here
+// is shared with the CPU oracle; both sides implement the generator from its
+// published definition.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace soma {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr uint32_t PURPOSE_INIT = 0, PURPOSE_MOVE = 1, PURPOSE_MOVE2 = 2;
+
+// Philox4x32-10: ten rounds of two 32x32->64 products (counter words 0 and 2
+// times the round multipliers) whose high halves are xored with counter words
+// 1 and 3 and the round key, with the key advanced by the Weyl constants
+// between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Symmetric uniform (2k+1)/2^24 - 1 of the top 24 bits k of r: never 0, and
+// exact in FP32 because the odd numerator 2k+1-2^24 has at most 24 bits.
+__device__ __forceinline__ float uniform_sym(uint32_t r) {
+  const int num = (int)(((r >> 8) << 1) | 1u) - (1 << 24);
+  return __int2float_rn(num) * 5.9604644775390625e-8f;  // 2^-24
+}
+
+// ln of the open uniform (k + 1/2)/2^24 = (2k+1)/2^25.
+__device__ __forceinline__ float log_uniform_open(uint32_t r) {
+  const float u = __uint2float_rn(((r >> 8) << 1) | 1u) * 2.98023223876953125e-8f;  // 2^-25
+  return __logf(u);
+}
+
+// Open uniform in FP64 (init path): (k + 1/2)/2^24, exact.
+__device__ __forceinline__ double uniform_open_f64(uint32_t r) {
+  return ((double)(r >> 8) + 0.5) * 5.9604644775390625e-8;
+}
+
+// Cell of one coordinate: floor(x) folded into [0, n).  The quotient estimate
+// may be off by one near multiples of n; one corrective step fixes it for
+// |x| < 2^23 n.  The final clamp keeps every index inside the grid even for
+// positions beyond that range or not finite (they are not produced by moves,
+// but a caller may set them).
+__device__ __forceinline__ int fold_cell(float x, int n, float inv_n) {
+  const int c = __float2int_rd(x);
+  const int q = __float2int_rd(__int2float_rn(c) * inv_n);
+  int r = c - q * n;
+  r += (r < 0) ? n : 0;
+  r -= (r >= n) ? n : 0;
+  return min(max(r, 0), n - 1);
+}
+
+template <typename WT> __device__ __forceinline__ float load_w(const WT* p, uint32_t i);
+template <> __device__ __forceinline__ float load_w<float>(const float* p, uint32_t i) {
+  return __ldg(p + i);
+}
+template <> __device__ __forceinline__ float load_w<__nv_bfloat16>(const __nv_bfloat16* p, uint32_t i) {
+  return __bfloat162float(__ldg(p + i));
+}
+template <> __device__ __forceinline__ float load_w<__half>(const __half* p, uint32_t i) {
+  return __half2float(__ldg(p + i));
+}
+
+template <typename WT> __device__ __forceinline__ WT store_cvt(float v);
+template <> __device__ __forceinline__ float store_cvt<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 store_cvt<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ __half store_cvt<__half>(float v) { return __float2half_rn(v); }
+
+// Geometry and Philox key shared by every kernel of one system.
+struct Geom {
+  uint64_t n_chains;
+  uint32_t N, N_A;
+  int nx, ny, nz;
+  float inv_nx, inv_ny, inv_nz;
+  uint32_t cells;
+  uint32_t key0, key1;
+  uint32_t replica;
+};
+
+struct SweepArgs {
+  Geom g;
+  float* x;
+  float* y;
+  float* z;
+  const void* wA;           // omega_A plane, storage type WT
+  const void* wB;           // omega_B plane
+  uint32_t* n0;             // occupation buffers; the sweep of step s adds into
+  uint32_t* n1;             // n[(s+1)&1]
+  unsigned long long* acc;  // accepted-move counter
+  const unsigned long long* d_sweep;
+  float a;                  // maximal displacement (dL), FP32
+  float K_b;                // k0/2 in kT/dL^2
+  uint32_t G;               // chains per warp tile
+  uint64_t n_tiles;
+  int set_order_random;
+};
+
+struct FieldArgs {
+  Geom g;
+  uint32_t* n0;             // occupation buffers (packed A | B<<16)
+  uint32_t* n1;
+  void* wA;                 // omega_A plane, storage type WT
+  void* wB;                 // omega_B plane
+  unsigned long long* d_sweep;
+  unsigned int* err;        // sticky error bits
+  float inv_rho;            // 1/(rho_0 dL^3)
+  float kappa0;             // kappaN/N
+  float half_chi0;          // chiN/(2N)
+  int after_sweep;          // 1: read n[(s+1)&1], clear n[s&1], then s += 1
+                            // 0: read n[s&1], clear n[(s+1)&1]
+};
+
+constexpr unsigned ERR_OVERFLOW = 1u;
+constexpr unsigned ERR_TIMEOUT = 2u;
+
+}  // namespace soma

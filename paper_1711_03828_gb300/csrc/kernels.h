@@ -1,0 +1,52 @@
+// kernels.h -- host-side launchers of the libsoma kernels (internal).
+#pragma once
+
+#include "common.cuh"
+
+namespace soma {
+
+// Launch shape of the sweep kernel for chains of N particles: Q pairs of
+// particles per lane, G whole chains per 32-lane tile.
+struct SweepShape {
+  int Q;
+  uint32_t G;
+  uint64_t n_tiles;
+  bool vec;
+  int block;
+  int grid;
+};
+
+SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dtype);
+cudaError_t launch_sweep_uniform(const SweepArgs& a, const SweepShape& s, int grid_dtype,
+                                 cudaStream_t st);
+
+cudaError_t launch_init(const Geom& g, float* x, float* y, float* z, double sigma, int sm_count,
+                        cudaStream_t st);
+cudaError_t launch_histogram(const Geom& g, const float* x, const float* y, const float* z,
+                             uint32_t* n, int sm_count, cudaStream_t st);
+cudaError_t launch_fields(const FieldArgs& a, unsigned* arrive, int grid_dtype, int sm_count,
+                          cudaStream_t st);
+cudaError_t launch_convert_fields(const void* w, int grid_dtype, float* dst, uint64_t n,
+                                  cudaStream_t st);
+
+// FP64 observables: partial sums per block into part, then one block folds
+// them in a fixed order into out (device).
+//   out[0] = sum over bonds |b|^2, out[1] = sum over chains |R_e|^2,
+//   out[2] = sum over cells of K(c) (Eq. discrete-ham, without rho dL^3/N),
+//   out[3] = max over cells of n_A + n_B.
+constexpr int OBS_BLOCKS = 1024;
+cudaError_t launch_observables(const Geom& g, const float* x, const float* y, const float* z,
+                               const uint32_t* n, double inv_rho, double kappaN, double chiN,
+                               double* part, double* out, cudaStream_t st);
+
+// S(q) for k <= SQ_MAX wave vectors; tw holds per q the FP64 twiddles
+// (cos, sin) of the three axes, laid out [q][nx + ny + nz][2].
+constexpr int SQ_MAX = 32;
+constexpr int SQ_BLOCKS = 512;
+cudaError_t launch_structure_factor(const Geom& g, const uint32_t* n, const double* tw, int k,
+                                    double* part, double* out, cudaStream_t st);
+
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
+                          cudaStream_t st);
+
+}  // namespace soma

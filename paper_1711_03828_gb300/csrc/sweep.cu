@@ -1,0 +1,264 @@
+// sweep.cu -- the Monte-Carlo step of the SCMF cycle (arXiv:1711.03828,
+// Sec. 2.2 and the SET iteration of Sec. 3.1.2) on sm_103a.
+//
+// Work decomposition.  A 32-lane warp owns a tile of G whole chains laid out
+// contiguously (G*N <= 64Q particles).  Lane l holds the 2Q consecutive
+// particles 2Ql .. 2Ql+2Q-1 of the tile in registers, so each lane owns as
+// many even as odd chain positions and BOTH independent sets keep all lanes
+// busy (the paper's SET scheme leaves half its threads idle per set for a
+// linear chain).  Bond partners in a neighbouring lane are exchanged with
+// warp shuffles; no shared memory and no inter-warp synchronisation.
+//
+// Per particle: one Philox4x32-10 draw (counter = particle, sweep) gives the
+// three displacement uniforms and the acceptance uniform; the set order of a
+// chain is bit 0 of the acceptance word of its first particle.  The trial
+// position is rounded exactly like the stored FP32 state (mul then add, both
+// round-to-nearest, no contraction).  The two field values omega_t(c) and
+// omega_t(c') are gathered from the L2-resident omega planes before the set
+// loop since c' does not depend on the neighbours.  After both sets the final
+// cells are added to the packed occupation grid n[(s+1)&1] with 32-bit
+// atomics (the occupation count of the next field update, fused).
+//
+// Streams: positions are loaded and stored with evict-first hints so the
+// 28 MB grid and the omega planes stay in L2.
+#include "kernels.h"
+
+namespace soma {
+
+template <int S>
+__device__ __forceinline__ void load_slots(const float* __restrict__ p, float (&v)[S]) {
+  if constexpr (S == 2) {
+    const float2 t = __ldcs(reinterpret_cast<const float2*>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < S / 4; ++k) {
+      const float4 t = __ldcs(reinterpret_cast<const float4*>(p) + k);
+      v[4 * k] = t.x;
+      v[4 * k + 1] = t.y;
+      v[4 * k + 2] = t.z;
+      v[4 * k + 3] = t.w;
+    }
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void store_slots(float* __restrict__ p, const float (&v)[S]) {
+  if constexpr (S == 2) {
+    __stcs(reinterpret_cast<float2*>(p), make_float2(v[0], v[1]));
+  } else {
+#pragma unroll
+    for (int k = 0; k < S / 4; ++k)
+      __stcs(reinterpret_cast<float4*>(p) + k,
+             make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
+  }
+}
+
+__device__ __forceinline__ uint32_t cell_of(const Geom& g, float x, float y, float z) {
+  const int cx = fold_cell(x, g.nx, g.inv_nx);
+  const int cy = fold_cell(y, g.ny, g.inv_ny);
+  const int cz = fold_cell(z, g.nz, g.inv_nz);
+  return ((uint32_t)cz * (uint32_t)g.ny + (uint32_t)cy) * (uint32_t)g.nx + (uint32_t)cx;
+}
+
+__device__ __forceinline__ float dist2(float ax, float ay, float az, float bx, float by, float bz) {
+  const float dx = ax - bx, dy = ay - by, dz = az - bz;
+  return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
+template <int Q, bool VEC, typename WT>
+__global__ void __launch_bounds__(256) sweep_uniform_kernel(const SweepArgs p) {
+  constexpr int S = 2 * Q;
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  const unsigned long long s64 = *p.d_sweep;
+  const uint32_t sweep = (uint32_t)s64;
+  uint32_t* __restrict__ nacc = ((s64 + 1ull) & 1ull) ? p.n1 : p.n0;
+  const WT* __restrict__ wA = static_cast<const WT*>(p.wA);
+  const WT* __restrict__ wB = static_cast<const WT*>(p.wB);
+  const uint32_t N = p.g.N, N_A = p.g.N_A;
+  const uint32_t ctr3 = (PURPOSE_MOVE << 24) | (p.g.replica & 0xFFFFFFu);
+  const uint32_t li0 = (uint32_t)lane * S;
+
+  // Tile-invariant slot metadata: chain-local index, chain within the tile,
+  // and (lane, slot) of that chain's first particle.
+  uint32_t ci[S], src_lane[S], src_slot[S];
+  {
+    uint32_t g = li0 / N, i = li0 - g * N;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      ci[j] = i;
+      const uint32_t first = g * N;
+      src_lane[j] = (first / S) & 31u;
+      src_slot[j] = first % S;
+      if (++i == N) { i = 0; ++g; }
+    }
+  }
+
+  unsigned my_acc = 0;
+  for (uint64_t tile = warp0; tile < p.n_tiles; tile += nwarps) {
+    const uint64_t chain0 = tile * p.G;
+    const uint64_t rem = p.g.n_chains - chain0;
+    const uint32_t nmono = (rem < p.G ? (uint32_t)rem : p.G) * N;
+    const uint64_t base = chain0 * N + li0;
+    const bool full = li0 + S <= nmono;
+
+    float x[S], y[S], z[S];
+    if (VEC && full) {
+      load_slots<S>(p.x + base, x);
+      load_slots<S>(p.y + base, y);
+      load_slots<S>(p.z + base, z);
+    } else {
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        const bool ok = li0 + j < nmono;
+        x[j] = ok ? __ldcs(p.x + base + j) : 0.f;
+        y[j] = ok ? __ldcs(p.y + base + j) : 0.f;
+        z[j] = ok ? __ldcs(p.z + base + j) : 0.f;
+      }
+    }
+
+    // Draws, trial positions, cells and the field change of every slot.
+    float xn[S], yn[S], zn[S], lnu[S], dEf[S];
+    uint32_t co[S], cn[S];
+    uint32_t lowbits = 0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      const uint64_t m = base + j;
+      const uint4 r = philox4x32_10(make_uint4((uint32_t)m, (uint32_t)(m >> 32), sweep, ctr3),
+                                    p.g.key0, p.g.key1);
+      xn[j] = __fadd_rn(x[j], __fmul_rn(p.a, uniform_sym(r.x)));
+      yn[j] = __fadd_rn(y[j], __fmul_rn(p.a, uniform_sym(r.y)));
+      zn[j] = __fadd_rn(z[j], __fmul_rn(p.a, uniform_sym(r.z)));
+      lnu[j] = log_uniform_open(r.w);
+      lowbits |= (r.w & 1u) << j;
+      co[j] = cell_of(p.g, x[j], y[j], z[j]);
+      cn[j] = cell_of(p.g, xn[j], yn[j], zn[j]);
+      const WT* wt = (ci[j] < N_A) ? wA : wB;
+      dEf[j] = (li0 + j < nmono) ? load_w<WT>(wt, cn[j]) - load_w<WT>(wt, co[j]) : 0.f;
+    }
+
+    // Set of each slot in this sweep: 0 moves first.
+    uint32_t phase[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      uint32_t b = 0;
+      if (p.set_order_random) b = (__shfl_sync(FULL, lowbits, src_lane[j]) >> src_slot[j]) & 1u;
+      phase[j] = (ci[j] & 1u) ^ b;
+    }
+
+#pragma unroll
+    for (uint32_t ph = 0; ph < 2; ++ph) {
+      const float pxl = __shfl_up_sync(FULL, x[S - 1], 1);
+      const float pyl = __shfl_up_sync(FULL, y[S - 1], 1);
+      const float pzl = __shfl_up_sync(FULL, z[S - 1], 1);
+      const float nxl = __shfl_down_sync(FULL, x[0], 1);
+      const float nyl = __shfl_down_sync(FULL, y[0], 1);
+      const float nzl = __shfl_down_sync(FULL, z[0], 1);
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        if (li0 + j >= nmono || phase[j] != ph) continue;
+        const float qx = (j > 0) ? x[j - 1] : pxl;
+        const float qy = (j > 0) ? y[j - 1] : pyl;
+        const float qz = (j > 0) ? z[j - 1] : pzl;
+        const float rx = (j < S - 1) ? x[j + 1] : nxl;
+        const float ry = (j < S - 1) ? y[j + 1] : nyl;
+        const float rz = (j < S - 1) ? z[j + 1] : nzl;
+        float e = 0.f;
+        if (ci[j] > 0)
+          e += dist2(xn[j], yn[j], zn[j], qx, qy, qz) - dist2(x[j], y[j], z[j], qx, qy, qz);
+        if (ci[j] + 1 < N)
+          e += dist2(xn[j], yn[j], zn[j], rx, ry, rz) - dist2(x[j], y[j], z[j], rx, ry, rz);
+        const float dE = fmaf(p.K_b, e, dEf[j]);
+        if (dE <= 0.f || lnu[j] < -dE) {
+          x[j] = xn[j];
+          y[j] = yn[j];
+          z[j] = zn[j];
+          co[j] = cn[j];
+          ++my_acc;
+        }
+      }
+    }
+
+    if (VEC && full) {
+      store_slots<S>(p.x + base, x);
+      store_slots<S>(p.y + base, y);
+      store_slots<S>(p.z + base, z);
+    } else {
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        if (li0 + j < nmono) {
+          __stcs(p.x + base + j, x[j]);
+          __stcs(p.y + base + j, y[j]);
+          __stcs(p.z + base + j, z[j]);
+        }
+      }
+    }
+
+    // Occupation count of the final cells; consecutive slots in one cell are
+    // merged into a single atomic (A adds 1, B adds 1<<16).
+    uint32_t carry = 0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      if (li0 + j >= nmono) continue;
+      const uint32_t v = carry + ((ci[j] < N_A) ? 1u : 0x10000u);
+      if (j + 1 < S && li0 + j + 1 < nmono && co[j + 1] == co[j]) {
+        carry = v;
+      } else {
+        atomicAdd(nacc + co[j], v);
+        carry = 0;
+      }
+    }
+  }
+
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) my_acc += __shfl_xor_sync(FULL, my_acc, o);
+  if (lane == 0 && my_acc) atomicAdd(p.acc, (unsigned long long)my_acc);
+}
+
+template <int Q, bool VEC>
+static const void* pick_kernel(int grid_dtype) {
+  switch (grid_dtype) {
+    case 1: return (const void*)sweep_uniform_kernel<Q, VEC, __nv_bfloat16>;
+    case 2: return (const void*)sweep_uniform_kernel<Q, VEC, __half>;
+    default: return (const void*)sweep_uniform_kernel<Q, VEC, float>;
+  }
+}
+
+static const void* sweep_kernel_ptr(int Q, bool vec, int grid_dtype) {
+  if (Q == 1) return vec ? pick_kernel<1, true>(grid_dtype) : pick_kernel<1, false>(grid_dtype);
+  if (Q == 2) return vec ? pick_kernel<2, true>(grid_dtype) : pick_kernel<2, false>(grid_dtype);
+  return vec ? pick_kernel<4, true>(grid_dtype) : pick_kernel<4, false>(grid_dtype);
+}
+
+SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dtype) {
+  SweepShape s;
+  s.Q = (N <= 64) ? 1 : (N <= 128 ? 2 : 4);
+  s.G = (uint32_t)(64 * s.Q) / N;
+  s.n_tiles = (n_chains + s.G - 1) / s.G;
+  const uint32_t S = 2u * (uint32_t)s.Q;
+  const uint32_t align = S < 4u ? S : 4u;
+  s.vec = ((uint64_t)s.G * N) % align == 0;
+  s.block = 256;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel_ptr(s.Q, s.vec, grid_dtype),
+                                                s.block, 0);
+  if (per_sm < 1) per_sm = 1;
+  const uint64_t warps_per_block = (uint64_t)s.block / 32;
+  const uint64_t need = (s.n_tiles + warps_per_block - 1) / warps_per_block;
+  const uint64_t cap = (uint64_t)sm_count * (uint64_t)per_sm;
+  s.grid = (int)(need < cap ? need : cap);
+  if (s.grid < 1) s.grid = 1;
+  return s;
+}
+
+cudaError_t launch_sweep_uniform(const SweepArgs& a, const SweepShape& s, int grid_dtype,
+                                 cudaStream_t st) {
+  const void* fn = sweep_kernel_ptr(s.Q, s.vec, grid_dtype);
+  void* args[] = {const_cast<SweepArgs*>(&a)};
+  return cudaLaunchKernel(fn, dim3(s.grid), dim3(s.block), args, 0, st);
+}
+
+}  // namespace soma

@@ -1,0 +1,96 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point include/soma.h declares, and rejects invalid descriptions
+before touching the device."""
+import ctypes
+
+import pytest
+
+from paper_1711_03828_gb300 import SystemDesc, _abi
+
+
+def test_library_exports_every_declared_symbol(soma_lib):
+    names = _abi.declared_symbols()
+    assert "soma_create" in names and "soma_sweep" in names and len(names) >= 18
+    L = soma_lib.lib()
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    assert L.soma_abi_version() == 1
+
+
+def _create_status(desc_c):
+    h = ctypes.c_void_p()
+    st = _abi.lib().soma_create(ctypes.byref(desc_c), ctypes.byref(h))
+    return st, h
+
+
+def _valid():
+    return SystemDesc(n_chains=16, N=8, box_Re=(1.0, 1.0, 1.0), grid=(6, 6, 6))
+
+
+@pytest.mark.parametrize("field,value", [
+    ("N", 0), ("N", 257), ("n_chains", 0), ("f", 1.5), ("f", float("nan")),
+    ("chiN", float("inf")), ("move", 7), ("set_order", 3), ("grid_dtype", 5),
+    ("replica_id", 1 << 24),
+])
+def test_invalid_description_is_rejected_without_gpu(soma_lib, field, value):
+    d = _valid()
+    setattr(d, field, value)
+    st, h = _create_status(d.to_c())
+    assert st == _abi.SOMA_EINVAL
+    assert h.value is None
+    assert _abi.soma_last_error()
+
+
+@pytest.mark.parametrize("mutate", ["struct_size", "flags", "box", "grid", "noncubic", "cells"])
+def test_invalid_geometry_is_rejected_without_gpu(soma_lib, mutate):
+    c = _valid().to_c()
+    if mutate == "struct_size":
+        c.struct_size = 8
+    elif mutate == "flags":
+        c.flags = 1
+    elif mutate == "box":
+        c.box_Re[1] = -1.0
+    elif mutate == "grid":
+        c.grid[2] = 0
+    elif mutate == "noncubic":
+        c.grid[0] = 7
+    elif mutate == "cells":
+        c.grid[0] = c.grid[1] = c.grid[2] = 4096
+        c.box_Re[0] = c.box_Re[1] = c.box_Re[2] = 4096.0
+    st, h = _create_status(c)
+    assert st == _abi.SOMA_EINVAL, _abi.soma_last_error()
+
+
+def test_null_arguments_are_rejected(soma_lib):
+    L = soma_lib.lib()
+    assert L.soma_create(None, None) == _abi.SOMA_EINVAL
+    assert L.soma_sweep(None, 1) == _abi.SOMA_EINVAL
+    assert L.soma_observables(None, None) == _abi.SOMA_EINVAL
+    assert L.soma_destroy(None) == _abi.SOMA_OK
+
+
+def test_struct_layouts_match_header(soma_lib, tmp_path):
+    """The ctypes mirrors have the sizes and field offsets of the C structs."""
+    import os
+    import subprocess
+    inc = os.path.join(os.path.dirname(os.path.dirname(_abi.HERE)), "include")
+    if not os.path.exists(os.path.join(inc, "soma.h")):
+        inc = os.path.join(os.path.dirname(_abi.HERE), "include")
+    structs = {"soma_system_desc": _abi.SomaSystemDesc, "soma_obs": _abi.SomaObs,
+               "soma_timing": _abi.SomaTiming}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "soma.h"', "int main(void){"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", f"-I{inc}", str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, f"{cname}.{f}"
