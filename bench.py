@@ -34,7 +34,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="melt_large",
-                    choices=["melt_large", "melt_small", "melt_slow", "melt_subbox"])
+                    choices=["melt_large", "melt_mid", "melt_small", "melt_slow", "melt_subbox"])
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

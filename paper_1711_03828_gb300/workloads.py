@@ -45,6 +45,16 @@ def melt_subbox(seed=1, **kw):
     return SystemDesc(**d)
 
 
+def melt_mid(seed=1, **kw):
+    """16^3 R_e0 box of the large melt (same density, grid spacing, chiN):
+    524,288 chains of N=32, 96^3 grid.  16,777,216 particles (201 MB of
+    positions, larger than L2): the profiling case of the sweep kernel."""
+    d = dict(n_chains=524288, N=32, f=0.5, box_Re=(16.0, 16.0, 16.0), grid=(96, 96, 96),
+             chiN=30.0, kappaN=50.0, seed=seed)
+    d.update(kw)
+    return SystemDesc(**d)
+
+
 def melt_slow(seed=1, **kw):
     """Slow melt: 1,048,576 chains of N=64 in a 32x32x16 R_e0 box, 192x192x96
     grid, chiN=40, kappaN=50.  67,108,864 particles."""
