@@ -11,6 +11,8 @@ Functions and the paper passage each follows:
 * ``philox`` / ``draw``          -- Philox4x32-10 (SC'11), the counter RNG that
   replaces the stored-state PCG of Sec. 3.2.3.
 * ``System.init_chains``        -- initial Gaussian chains (Sec. 2.1, b0 = sqrt(3/k0)).
+* ``System.sort_chains``        -- spatial (Morton) labelling of whole chains (labels are
+  arbitrary, Sec. 3.1.1).
 * ``System.histogram``          -- occupation numbers, Eq. (density-characteristics).
 * ``System.fields``             -- interaction fields, Eq. (omega-fields), option K^0.
 * ``System.sweep``              -- one SET Monte-Carlo step (Sec. 2.2, Sec. 3.1.2).
@@ -104,6 +106,9 @@ def load(path):
     L.or_observables.argtypes = [P, f32p, f32p, f32p, u32p, u32p, ctypes.POINTER(OrObs)]
     L.or_structure_factor.argtypes = [P, u32p, u32p, i32p, ctypes.c_size_t, f64p]
     L.or_num_threads.restype = ctypes.c_int
+    L.or_chain_key.argtypes = [P, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+    L.or_chain_key.restype = ctypes.c_uint64
+    L.or_sort_chains.argtypes = [P, f32p, f32p, f32p, ctypes.POINTER(ctypes.c_uint64)]
     return L
 
 
@@ -184,6 +189,25 @@ class System:
         pos = self.empty_positions() if pos is None else pos
         self.L.or_init_chain_range(ctypes.byref(self.s), int(c0), int(c1),
                                   _ptr(pos.x, f32p), _ptr(pos.y, f32p), _ptr(pos.z, f32p))
+        return pos
+
+    def chain_key(self, x0, y0, z0):
+        return int(self.L.or_chain_key(ctypes.byref(self.s), float(x0), float(y0), float(z0)))
+
+    def sort_chains(self, pos):
+        """Re-label chains in spatial order in place; returns the old label of
+        each new label."""
+        perm = np.zeros(self.n_chains, np.uint64)
+        self.L.or_sort_chains(ctypes.byref(self.s), _ptr(pos.x, f32p), _ptr(pos.y, f32p),
+                              _ptr(pos.z, f32p), perm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+        return perm
+
+    def initial_state(self, sort=True):
+        """The library's initial configuration: Gaussian chains, then (by
+        default) the spatial labelling."""
+        pos = self.init_chains()
+        if sort:
+            self.sort_chains(pos)
         return pos
 
     def histogram(self, pos):

@@ -7,6 +7,7 @@
 #include "soma_oracle.h"
 
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
@@ -158,6 +159,49 @@ static uint64_t or_cell(const or_system* s, double x, double y, double z) {
     c[d] = r;
   }
   return ((uint64_t)c[2] * s->grid[1] + (uint64_t)c[1]) * s->grid[0] + (uint64_t)c[0];
+}
+
+/* Morton code of the coarse block holding a position: the bits of the block
+ * coordinates bx, by, bz (10 each) interleaved as ...z1y1x1z0y0x0. */
+uint64_t or_chain_key(const or_system* s, float x0, float y0, float z0) {
+  double p[3] = { x0, y0, z0 };
+  uint64_t b[3];
+  for (int d = 0; d < 3; ++d) {
+    long long n = (long long)s->grid[d];
+    long long c = (long long)floor(p[d]) % n;
+    if (c < 0) c += n;
+    b[d] = (uint64_t)(c / OR_SORT_BLOCK);
+  }
+  uint64_t key = 0;
+  for (int bit = 0; bit < 10; ++bit)
+    for (int d = 0; d < 3; ++d) key |= ((b[d] >> bit) & 1u) << (3 * bit + d);
+  return key;
+}
+
+static int or_cmp_u64(const void* a, const void* b) {
+  uint64_t u = *(const uint64_t*)a, v = *(const uint64_t*)b;
+  return (u > v) - (u < v);
+}
+
+void or_sort_chains(const or_system* s, float* x, float* y, float* z, uint64_t* perm) {
+  const uint64_t n = s->n_chains, N = s->N;
+  uint64_t* kv = (uint64_t*)malloc(n * sizeof(uint64_t));
+  float* tmp = (float*)malloc(n * N * sizeof(float));
+  for (uint64_t k = 0; k < n; ++k)
+    kv[k] = (or_chain_key(s, x[k * N], y[k * N], z[k * N]) << 32) | k;
+  qsort(kv, n, sizeof(uint64_t), or_cmp_u64);
+  float* axes[3] = { x, y, z };
+  for (int d = 0; d < 3; ++d) {
+    for (uint64_t j = 0; j < n; ++j) {
+      uint64_t old = kv[j] & 0xFFFFFFFFu;
+      memcpy(tmp + j * N, axes[d] + old * N, N * sizeof(float));
+    }
+    memcpy(axes[d], tmp, n * N * sizeof(float));
+  }
+  if (perm)
+    for (uint64_t j = 0; j < n; ++j) perm[j] = kv[j] & 0xFFFFFFFFu;
+  free(kv);
+  free(tmp);
 }
 
 /* a3: n_i(c) = number of particles of type i in cell c (Eq.                    */

@@ -75,6 +75,17 @@ void or_init_chains(const or_system* s, float* x, float* y, float* z);
 void or_init_chain_range(const or_system* s, uint64_t c0, uint64_t c1,
                          float* x, float* y, float* z);
 
+/* Spatial labelling of chains: chains are re-labelled in increasing order of
+ * the Morton code of the coarse block (OR_SORT_BLOCK^3 cells) holding their
+ * first particle, ties by the previous label.  The labels of molecules are
+ * arbitrary (Sec. 3.1.1 distributes whole molecules freely at
+ * initialisation); this only fixes which particle index, and so which random
+ * stream, each chain uses.  perm (optional, n_chains) receives the old label
+ * of each new label. */
+#define OR_SORT_BLOCK 8
+uint64_t or_chain_key(const or_system* s, float x0, float y0, float z0);
+void or_sort_chains(const or_system* s, float* x, float* y, float* z, uint64_t* perm);
+
 /* --- a3: occupation numbers, Eq. (density-characteristics) ----------------- */
 void or_histogram(const or_system* s, const float* x, const float* y, const float* z,
                   uint32_t* nA, uint32_t* nB);

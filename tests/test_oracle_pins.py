@@ -366,3 +366,40 @@ def test_observables_hand_values(oracle_lib):
 
 def test_structure_factor_matches_numpy_fft(oracle_lib):
     check_structure_factor_matches_numpy_fft()
+
+
+# --------------------------------------------------------------------------
+# Spatial labelling of chains
+# --------------------------------------------------------------------------
+def _morton_ref(b):
+    key = 0
+    for bit in range(10):
+        for d in range(3):
+            key |= ((int(b[d]) >> bit) & 1) << (3 * bit + d)
+    return key
+
+
+def check_sort_chains_is_a_spatial_permutation(lib=None):
+    d = SystemDesc(n_chains=3000, N=6, f=0.5, box_Re=(3.0, 2.0, 4.0), grid=(30, 20, 40),
+                   chiN=0.0, kappaN=0.0)
+    s = oracle_system(d, lib)
+    p = s.init_chains()
+    before = p.copy()
+    perm = s.sort_chains(p)
+    # a permutation of whole chains
+    assert sorted(perm.tolist()) == list(range(d.n_chains))
+    P0 = before.stacked().reshape(3, d.n_chains, d.N)
+    P1 = p.stacked().reshape(3, d.n_chains, d.N)
+    np.testing.assert_array_equal(P1, P0[:, perm.astype(np.int64), :])
+    # keys (numpy floor/mod of the first particle, 8^3 blocks, Morton order) ascend,
+    # ties keep the old order
+    first = P1[:, :, 0].astype(np.float64)
+    c = np.floor(first).astype(np.int64) % np.asarray(d.grid)[:, None]
+    keys = np.array([_morton_ref(c[:, k] // 8) for k in range(d.n_chains)])
+    assert np.all(np.diff(keys) >= 0)
+    same = np.diff(keys) == 0
+    assert np.all(np.diff(perm.astype(np.int64))[same] > 0)
+
+
+def test_sort_chains_is_a_spatial_permutation(oracle_lib):
+    check_sort_chains_is_a_spatial_permutation()
