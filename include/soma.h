@@ -70,6 +70,15 @@ typedef enum { SOMA_MOVE_UNIFORM = 0, SOMA_MOVE_SMC = 1 } soma_move;
 typedef enum { SOMA_SET_ORDER_RANDOM = 0, SOMA_SET_ORDER_FIXED = 1 } soma_set_order;
 typedef enum { SOMA_GRID_F32 = 0, SOMA_GRID_BF16 = 1, SOMA_GRID_F16 = 2 } soma_grid_dtype;
 
+/* desc.flags bits.  By default soma_create labels the chains in spatial order:
+ * increasing Morton code of the 8^3-cell block holding each chain's first
+ * particle (ties keep the drawing order), so that chains with nearby labels
+ * are near each other and share field values in cache.  Labels of molecules
+ * are arbitrary (the paper distributes whole molecules freely, Sec. 3.1.1);
+ * the label decides the particle indices and so the Philox streams.
+ * SOMA_FLAG_NO_SORT keeps the drawing order (chain k = k-th draw). */
+#define SOMA_FLAG_NO_SORT 1
+
 /* Description of one system: a melt of n_chains linear A-B diblock chains.
  * struct_size must be sizeof(soma_system_desc) (ABI versioning). */
 typedef struct soma_system_desc {
@@ -87,7 +96,7 @@ typedef struct soma_system_desc {
   int32_t move;          /* soma_move */
   int32_t set_order;     /* soma_set_order */
   int32_t grid_dtype;    /* soma_grid_dtype: storage type of omega */
-  int32_t flags;         /* must be 0 */
+  int32_t flags;         /* 0 or SOMA_FLAG_NO_SORT */
   uint64_t seed;         /* Philox key */
   uint32_t replica_id;   /* Philox counter word 3, low 24 bits */
   uint32_t reserved1;
@@ -123,6 +132,7 @@ typedef struct soma_timing {
 /* Create a system: validate desc, allocate device state, draw the initial
  * configuration (first particle of each chain uniform in the box, then
  * Gaussian bonds with <b^2> = R_e0^2/(N-1); Sec. 2.1 with b0 = sqrt(3/k0)),
+ * label the chains in spatial order unless desc.flags has SOMA_FLAG_NO_SORT,
  * then compute n and omega (first stage of the SCMF cycle, Sec. 2.2).
  * Returns SOMA_EINVAL before touching the GPU when desc is invalid.
  * On success *out owns the state; on failure *out is NULL. */

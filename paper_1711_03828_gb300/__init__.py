@@ -15,10 +15,10 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import _abi
-from ._abi import (GRID_BF16, GRID_F16, GRID_F32, MOVE_SMC, MOVE_UNIFORM, SET_ORDER_FIXED,
-                   SET_ORDER_RANDOM, SomaError)
+from ._abi import (FLAG_NO_SORT, GRID_BF16, GRID_F16, GRID_F32, MOVE_SMC, MOVE_UNIFORM,
+                   SET_ORDER_FIXED, SET_ORDER_RANDOM, SomaError)
 
-__all__ = ["SystemDesc", "System", "SomaError", "MOVE_UNIFORM", "MOVE_SMC", "SET_ORDER_RANDOM",
+__all__ = ["SystemDesc", "System", "SomaError", "FLAG_NO_SORT", "MOVE_UNIFORM", "MOVE_SMC", "SET_ORDER_RANDOM",
            "SET_ORDER_FIXED", "GRID_F32", "GRID_BF16", "GRID_F16"]
 
 
@@ -38,6 +38,7 @@ class SystemDesc:
     grid_dtype: int = GRID_F32
     seed: int = 1
     replica_id: int = 0
+    flags: int = 0
 
     @property
     def M(self):
@@ -62,7 +63,7 @@ class SystemDesc:
         d.move = int(self.move)
         d.set_order = int(self.set_order)
         d.grid_dtype = int(self.grid_dtype)
-        d.flags = 0
+        d.flags = int(self.flags)
         d.seed = int(self.seed)
         d.replica_id = int(self.replica_id)
         d.stream = stream

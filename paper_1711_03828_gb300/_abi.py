@@ -17,6 +17,7 @@ SOMA_OK, SOMA_EINVAL, SOMA_ENOMEM, SOMA_ECUDA, SOMA_EOVERFLOW, SOMA_ETIMEOUT, SO
 MOVE_UNIFORM, MOVE_SMC = 0, 1
 SET_ORDER_RANDOM, SET_ORDER_FIXED = 0, 1
 GRID_F32, GRID_BF16, GRID_F16 = 0, 1, 2
+FLAG_NO_SORT = 1
 
 
 class SomaSystemDesc(ctypes.Structure):

@@ -129,7 +129,7 @@ soma_status validate(const soma_system_desc* d) {
     return fail(SOMA_EINVAL, "set_order=%d unknown", d->set_order);
   if (d->grid_dtype < 0 || d->grid_dtype > 2)
     return fail(SOMA_EINVAL, "grid_dtype=%d unknown", d->grid_dtype);
-  if (d->flags != 0) return fail(SOMA_EINVAL, "flags must be 0");
+  if (d->flags & ~SOMA_FLAG_NO_SORT) return fail(SOMA_EINVAL, "unknown flags 0x%x", d->flags);
   if (d->replica_id > 0xFFFFFFu) return fail(SOMA_EINVAL, "replica_id must be < 2^24");
   return SOMA_OK;
 }
@@ -155,12 +155,22 @@ void derive(soma_t* h) {
   g.nx = (int)d.grid[0];
   g.ny = (int)d.grid[1];
   g.nz = (int)d.grid[2];
-  g.inv_nx = 1.0f / (float)g.nx;
-  g.inv_ny = 1.0f / (float)g.ny;
-  g.inv_nz = 1.0f / (float)g.nz;
+  const uint32_t n3[3] = {d.grid[0], d.grid[1], d.grid[2]};
+  for (int k = 0; k < 3; ++k) {
+    const uint64_t n = n3[k];
+    uint32_t l = 0;
+    while ((1ull << l) < n) ++l;
+    g.fold_m[k] = n > 1 ? (uint32_t)((1ull << (31 + l)) / n + 1) : 0u;
+    g.fold_sh[k] = n > 1 ? l - 1 : 0u;
+    g.fold_bias[k] = (uint32_t)(n * ((1ull << 30) / n));
+  }
   g.cells = (uint32_t)(d.grid[0] * d.grid[1] * d.grid[2]);
   g.key0 = (uint32_t)d.seed;
   g.key1 = (uint32_t)(d.seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    g.rk0[r] = g.key0 + (uint32_t)r * 0x9E3779B9u;
+    g.rk1[r] = g.key1 + (uint32_t)r * 0xBB67AE85u;
+  }
   g.replica = d.replica_id;
 }
 
@@ -216,6 +226,8 @@ SweepArgs sweep_args(soma_t* h) {
   s.K_b = (float)h->K_b;
   s.G = h->shape.G;
   s.n_tiles = h->shape.n_tiles;
+  s.full_tiles = h->g.n_chains / h->shape.G;
+  s.last_rows = (uint32_t)(h->g.n_chains % h->shape.G) * h->g.N;
   s.set_order_random = h->desc.set_order == SOMA_SET_ORDER_RANDOM;
   return s;
 }
@@ -360,9 +372,29 @@ soma_status soma_create(const soma_system_desc* desc, soma_t** out) {
   CK(cudaMemsetAsync(h->n[1], 0, sizeof(uint32_t) * cells, h->stream));
   CK(cudaMemsetAsync(h->d_counters, 0, sizeof(unsigned long long) * 2, h->stream));
   CK(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned) * 2, h->stream));
-  CK(launch_init(h->g, h->x(), h->y(), h->z(), h->sigma, h->sm_count, h->stream));
+  if ((desc->flags & SOMA_FLAG_NO_SORT) || h->g.n_chains >= (1ull << 32)) {
+    CK(launch_init(h->g, h->x(), h->y(), h->z(), h->sigma, h->sm_count, h->stream));
+    ++h->launches;
+  } else {
+    // draw the chains into a staging buffer, then store them in spatial order
+    uint64_t n_pad = 1;
+    while (n_pad < h->g.n_chains) n_pad <<= 1;
+    float* stage = nullptr;
+    uint64_t* keys = nullptr;
+    e = cudaMallocAsync((void**)&stage, sizeof(float) * 3 * h->plane, h->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&keys, sizeof(uint64_t) * n_pad, h->stream);
+    if (e == cudaSuccess)
+      e = launch_init(h->g, stage, stage + h->plane, stage + 2 * h->plane, h->sigma, h->sm_count,
+                      h->stream);
+    if (e == cudaSuccess)
+      e = launch_sort_chains(h->g, stage, h->plane, h->pos, h->plane, keys, n_pad, h->sm_count,
+                             h->stream);
+    if (stage) cudaFreeAsync(stage, h->stream);
+    if (keys) cudaFreeAsync(keys, h->stream);
+    if (e != cudaSuccess) { release(h); return cuda_fail(e, "initial configuration"); }
+    h->launches += 3;
+  }
 #undef CK
-  ++h->launches;
   st = update_fields(h);
   if (st == SOMA_OK) st = sync(h);
   if (st != SOMA_OK) { std::string m = g_last_error; release(h); g_last_error = m; return st; }

@@ -35,16 +35,15 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 }
 
 // Symmetric uniform (2k+1)/2^24 - 1 of the top 24 bits k of r: never 0, and
-// exact in FP32 because the odd numerator 2k+1-2^24 has at most 24 bits.
+// exact in FP32: k*2^-23 + (2^-24 - 1) is representable, and the fused
+// multiply-add rounds the exact value once.
 __device__ __forceinline__ float uniform_sym(uint32_t r) {
-  const int num = (int)(((r >> 8) << 1) | 1u) - (1 << 24);
-  return __int2float_rn(num) * 5.9604644775390625e-8f;  // 2^-24
+  return fmaf(__uint2float_rn(r >> 8), 1.1920928955078125e-7f, -0.99999994039535522461f);
 }
 
-// ln of the open uniform (k + 1/2)/2^24 = (2k+1)/2^25.
+// ln of the open uniform (k + 1/2)/2^24.
 __device__ __forceinline__ float log_uniform_open(uint32_t r) {
-  const float u = __uint2float_rn(((r >> 8) << 1) | 1u) * 2.98023223876953125e-8f;  // 2^-25
-  return __logf(u);
+  return __logf(fmaf(__uint2float_rn(r >> 8), 5.9604644775390625e-8f, 2.98023223876953125e-8f));
 }
 
 // Open uniform in FP64 (init path): (k + 1/2)/2^24, exact.
@@ -52,18 +51,18 @@ __device__ __forceinline__ double uniform_open_f64(uint32_t r) {
   return ((double)(r >> 8) + 0.5) * 5.9604644775390625e-8;
 }
 
-// Cell of one coordinate: floor(x) folded into [0, n).  The quotient estimate
-// may be off by one near multiples of n; one corrective step fixes it for
-// |x| < 2^23 n.  The final clamp keeps every index inside the grid even for
-// positions beyond that range or not finite (they are not produced by moves,
-// but a caller may set them).
-__device__ __forceinline__ int fold_cell(float x, int n, float inv_n) {
-  const int c = __float2int_rd(x);
-  const int q = __float2int_rd(__int2float_rn(c) * inv_n);
-  int r = c - q * n;
-  r += (r < 0) ? n : 0;
-  r -= (r >= n) ? n : 0;
-  return min(max(r, 0), n - 1);
+// Cell of one coordinate: floor(x) folded into [0, n) by an exact
+// multiply-high division (Granlund & Montgomery 1994, Thm. 4.2, for 31-bit
+// numerators): with l = ceil(log2 n) and m = floor(2^(31+l)/n) + 1,
+// floor(c/n) = umulhi(c, m) >> (l-1) for every 0 <= c < 2^31.  c = floor(x) +
+// bias, bias = n*floor(2^30/n), so every |x| < 2^30 is folded exactly.  The
+// final unsigned min keeps the index inside the grid for any input (and makes
+// an axis with n = 1, which has m = 0, always fold to 0).
+__device__ __forceinline__ uint32_t fold_cell(float x, uint32_t n, uint32_t m, uint32_t sh,
+                                              uint32_t bias) {
+  const uint32_t c = (uint32_t)__float2int_rd(x) + bias;
+  const uint32_t q = __umulhi(c, m) >> sh;
+  return min(c - q * n, n - 1u);
 }
 
 template <typename WT> __device__ __forceinline__ float load_w(const WT* p, uint32_t i);
@@ -89,11 +88,35 @@ struct Geom {
   uint64_t n_chains;
   uint32_t N, N_A;
   int nx, ny, nz;
-  float inv_nx, inv_ny, inv_nz;
+  uint32_t fold_m[3];     // multiply-high magic per axis (0 for n = 1)
+  uint32_t fold_sh[3];    // ceil(log2 n) - 1 per axis
+  uint32_t fold_bias[3];  // n * floor(2^30/n) per axis
   uint32_t cells;
   uint32_t key0, key1;
+  uint32_t rk0[10], rk1[10];  // Philox round keys: key + r * (Weyl constant)
   uint32_t replica;
 };
+
+__device__ __forceinline__ uint32_t cell_of(const Geom& g, float x, float y, float z) {
+  const uint32_t cx = fold_cell(x, (uint32_t)g.nx, g.fold_m[0], g.fold_sh[0], g.fold_bias[0]);
+  const uint32_t cy = fold_cell(y, (uint32_t)g.ny, g.fold_m[1], g.fold_sh[1], g.fold_bias[1]);
+  const uint32_t cz = fold_cell(z, (uint32_t)g.nz, g.fold_m[2], g.fold_sh[2], g.fold_bias[2]);
+  return (cz * (uint32_t)g.ny + cy) * (uint32_t)g.nx + cx;
+}
+
+// Philox4x32-10 with the round keys taken from the kernel parameters (the
+// key schedule is the same for every thread, so it is computed once on the
+// host and read from the constant bank).
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const Geom& g) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ g.rk0[r], (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ g.rk1[r], (uint32_t)p0);
+  }
+  return c;
+}
 
 struct SweepArgs {
   Geom g;
@@ -110,6 +133,8 @@ struct SweepArgs {
   float K_b;                // k0/2 in kT/dL^2
   uint32_t G;               // chains per warp tile
   uint64_t n_tiles;
+  uint64_t full_tiles;      // tiles holding G chains
+  uint32_t last_rows;       // particles in the last, partial tile (0: none)
   int set_order_random;
 };
 

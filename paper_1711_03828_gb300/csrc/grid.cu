@@ -8,13 +8,6 @@
 
 namespace soma {
 
-__device__ __forceinline__ uint32_t cell_index(const Geom& g, float x, float y, float z) {
-  const int cx = fold_cell(x, g.nx, g.inv_nx);
-  const int cy = fold_cell(y, g.ny, g.inv_ny);
-  const int cz = fold_cell(z, g.nz, g.inv_nz);
-  return ((uint32_t)cz * (uint32_t)g.ny + (uint32_t)cy) * (uint32_t)g.nx + (uint32_t)cx;
-}
-
 // ---------------------------------------------------------------------------
 // Occupation count of a whole configuration (used outside the sweep, whose
 // epilogue counts on its own).  One thread per particle.
@@ -25,7 +18,7 @@ __global__ void histogram_kernel(const Geom g, const float* __restrict__ x,
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += stride) {
     const uint32_t i = (uint32_t)(m % g.N);
-    atomicAdd(n + cell_index(g, x[m], y[m], z[m]), (i < g.N_A) ? 1u : 0x10000u);
+    atomicAdd(n + cell_of(g, x[m], y[m], z[m]), (i < g.N_A) ? 1u : 0x10000u);
   }
 }
 
@@ -160,6 +153,75 @@ cudaError_t launch_init(const Geom& g, float* x, float* y, float* z, double sigm
   const uint64_t cap = (uint64_t)sm_count * 16;
   if (blocks > cap) blocks = cap;
   init_kernel<<<(unsigned)blocks, 128, 0, st>>>(g, x, y, z, sigma);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Spatial labelling of chains at initialisation: key = Morton code of the
+// 8^3-cell block of the chain's first particle, packed above the old label so
+// all keys are distinct and the sorted order is unique; a bitonic network
+// sorts them; a gather moves whole chains to their new labels.
+constexpr uint32_t SORT_BLOCK_SHIFT = 3;  // 8-cell blocks
+
+__global__ void chain_key_kernel(const Geom g, const float* __restrict__ x,
+                                 const float* __restrict__ y, const float* __restrict__ z,
+                                 uint64_t* __restrict__ keys, uint64_t n_pad) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_pad; k += stride) {
+    if (k >= g.n_chains) {
+      keys[k] = ~0ull;
+      continue;
+    }
+    const uint64_t m = k * g.N;
+    const uint32_t b[3] = {
+        fold_cell(x[m], (uint32_t)g.nx, g.fold_m[0], g.fold_sh[0], g.fold_bias[0]) >> SORT_BLOCK_SHIFT,
+        fold_cell(y[m], (uint32_t)g.ny, g.fold_m[1], g.fold_sh[1], g.fold_bias[1]) >> SORT_BLOCK_SHIFT,
+        fold_cell(z[m], (uint32_t)g.nz, g.fold_m[2], g.fold_sh[2], g.fold_bias[2]) >> SORT_BLOCK_SHIFT};
+    uint64_t key = 0;
+    for (int bit = 0; bit < 10; ++bit)
+      for (int d = 0; d < 3; ++d) key |= (uint64_t)((b[d] >> bit) & 1u) << (3 * bit + d);
+    keys[k] = (key << 32) | k;
+  }
+}
+
+__global__ void bitonic_step_kernel(uint64_t* __restrict__ a, uint64_t n, uint64_t j, uint64_t k) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint64_t l = i ^ j;
+    if (l <= i) continue;
+    const uint64_t u = a[i], v = a[l];
+    const bool up = (i & k) == 0;
+    if ((u > v) == up) {
+      a[i] = v;
+      a[l] = u;
+    }
+  }
+}
+
+__global__ void chain_gather_kernel(const Geom g, const uint64_t* __restrict__ keys,
+                                    const float* __restrict__ src, float* __restrict__ dst,
+                                    uint64_t src_plane, uint64_t dst_plane) {
+  const uint64_t M = g.n_chains * g.N;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += stride) {
+    const uint64_t j = m / g.N, i = m - j * g.N;
+    const uint64_t old = keys[j] & 0xFFFFFFFFull;
+    const uint64_t from = old * g.N + i;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dst[d * dst_plane + m] = src[d * src_plane + from];
+  }
+}
+
+cudaError_t launch_sort_chains(const Geom& g, const float* src, uint64_t src_plane, float* dst,
+                               uint64_t dst_plane, uint64_t* keys, uint64_t n_pad, int sm_count,
+                               cudaStream_t st) {
+  const unsigned blocks = (unsigned)sm_count * 8;
+  chain_key_kernel<<<blocks, 256, 0, st>>>(g, src, src + src_plane, src + 2 * src_plane, keys,
+                                           n_pad);
+  for (uint64_t k = 2; k <= n_pad; k <<= 1)
+    for (uint64_t j = k >> 1; j > 0; j >>= 1)
+      bitonic_step_kernel<<<blocks, 256, 0, st>>>(keys, n_pad, j, k);
+  chain_gather_kernel<<<blocks, 256, 0, st>>>(g, keys, src, dst, src_plane, dst_plane);
   return cudaGetLastError();
 }
 

@@ -12,6 +12,8 @@ struct SweepShape {
   uint32_t G;
   uint64_t n_tiles;
   bool vec;
+  bool pair;  // even N <= 64: one even and one odd particle per lane
+  bool big;   // 64-bit particle indices (M >= 2^32)
   int block;
   int grid;
 };
@@ -22,6 +24,12 @@ cudaError_t launch_sweep_uniform(const SweepArgs& a, const SweepShape& s, int gr
 
 cudaError_t launch_init(const Geom& g, float* x, float* y, float* z, double sigma, int sm_count,
                         cudaStream_t st);
+// Re-label whole chains in Morton order of the 8^3-cell block of their first
+// particle: src and dst are 3-plane position buffers, keys holds n_pad >=
+// n_chains (a power of two) 64-bit words of scratch.
+cudaError_t launch_sort_chains(const Geom& g, const float* src, uint64_t src_plane, float* dst,
+                               uint64_t dst_plane, uint64_t* keys, uint64_t n_pad, int sm_count,
+                               cudaStream_t st);
 cudaError_t launch_histogram(const Geom& g, const float* x, const float* y, const float* z,
                              uint32_t* n, int sm_count, cudaStream_t st);
 cudaError_t launch_fields(const FieldArgs& a, unsigned* arrive, int grid_dtype, int sm_count,

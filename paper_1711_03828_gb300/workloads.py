@@ -73,7 +73,7 @@ def scaled(desc: SystemDesc, box_Re, rho_Re3=4096.0):
     return SystemDesc(n_chains=n_chains, N=desc.N, f=desc.f, box_Re=tuple(box_Re), grid=grid,
                       chiN=desc.chiN, kappaN=desc.kappaN, a_Re=desc.a_Re, move=desc.move,
                       set_order=desc.set_order, grid_dtype=desc.grid_dtype, seed=desc.seed,
-                      replica_id=desc.replica_id)
+                      replica_id=desc.replica_id, flags=desc.flags)
 
 
 def random_walk_positions(desc: SystemDesc, seed: int, bond_sigma: float = None,

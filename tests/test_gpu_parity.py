@@ -18,7 +18,8 @@ import pytest
 
 import oracle
 from oracle import Positions
-from paper_1711_03828_gb300 import SET_ORDER_FIXED, SET_ORDER_RANDOM, System, SystemDesc, _abi
+from paper_1711_03828_gb300 import (FLAG_NO_SORT, SET_ORDER_FIXED, SET_ORDER_RANDOM, System,
+                                    SystemDesc, _abi)
 from paper_1711_03828_gb300 import workloads
 from tests.conftest import oracle_system
 
@@ -36,6 +37,18 @@ def _fields_tol(desc, nA, nB, rho):
     c0 = desc.chiN / desc.N
     phi = (nA.astype(np.float64) + nB) / rho
     return 4 * 2.0**-24 * (abs(k0) * (phi + 1) + abs(c0) * phi) + 1e-30
+
+
+def check_decisions(bad, margin, N):
+    """Mismatched move decisions are allowed only at near-ties (|dE + ln u| <
+    TIE) and, downstream of such a tie, for the bonded neighbours of a tied
+    particle (they move in the other set and see a different partner)."""
+    bad = np.asarray(bad)
+    tied = set(bad[np.abs(margin[bad]) < TIE].tolist())
+    for m in bad[np.abs(margin[bad]) >= TIE].tolist():
+        same_chain = [k for k in (m - 1, m + 1) if k // N == m // N]
+        assert any(k in tied for k in same_chain), (m, margin[m])
+    return len(tied)
 
 
 class Runner:
@@ -82,7 +95,7 @@ class Runner:
                 bad = np.nonzero(gacc != acc)[0]
                 self.moves += self.d.M
                 if len(bad):
-                    assert np.all(np.abs(margin[bad]) < TIE), margin[bad]
+                    check_decisions(bad, margin, self.d.N)
                     self.mismatch += len(bad)
                     # chains with a tolerated mismatch diverge; all others must agree
                     chains = np.unique(bad // self.d.N)
@@ -135,11 +148,14 @@ def test_philox_matches_oracle_bit_exact(dev):
         np.testing.assert_array_equal(out[i], oracle.philox(ctr[i], key[i]))
 
 
-def test_init_matches_oracle(dev):
-    d = workloads.melt_small()
+@pytest.mark.parametrize("flags", [0, FLAG_NO_SORT])
+def test_init_matches_oracle(dev, flags):
+    """Gaussian chains drawn per label, then (by default) the spatial labelling."""
+    d = workloads.melt_small(n_chains=4096, box_Re=(4.0, 4.0, 2.0), grid=(24, 24, 12),
+                             flags=flags)
     s = System(d)
     g = s.get_positions().astype(np.float64)
-    p = oracle_system(d).init_chains().stacked().astype(np.float64)
+    p = oracle_system(d).initial_state(sort=(flags == 0)).stacked().astype(np.float64)
     diff = np.abs(g - p)
     ulp = np.spacing(np.abs(p).astype(np.float32)).astype(np.float64)
     assert np.all(diff <= ulp), diff.max()
@@ -249,7 +265,7 @@ def test_full_size_lamellar_melt_one_cycle(dev):
     the whole grid and on every particle."""
     d = workloads.melt_large()
     orc = oracle_system(d)
-    p = orc.init_chains()
+    p = orc.initial_state()
     s = System(d)
     s.set_positions(p.stacked())
     s.update_fields()
@@ -264,8 +280,8 @@ def test_full_size_lamellar_melt_one_cycle(dev):
     g = s.get_positions()
     gacc = ((g[0] != old.x) | (g[1] != old.y) | (g[2] != old.z)).astype(np.uint8)
     bad = np.nonzero(gacc != acc)[0]
-    print(f"full size: {d.M} moves, tolerated mismatches {len(bad)}")
-    assert np.all(np.abs(margin[bad]) < TIE)
+    ties = check_decisions(bad, margin, d.N)
+    print(f"full size: {d.M} moves, mismatches {len(bad)}, of which near-ties {ties}")
     assert len(bad) <= 1e-6 * d.M
     keep = np.ones(d.n_chains, bool)
     keep[np.unique(bad // d.N)] = False
