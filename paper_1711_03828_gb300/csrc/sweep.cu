@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(256) sweep_uniform_kernel(const SweepArgs p) {
 // where every difference r - n is exact for bonded neighbours.
 // IDX is the index type: 32-bit when M < 2^32 (Philox counter word 1 = 0).
 template <typename WT, typename IDX>
-__global__ void __launch_bounds__(256, 4) sweep_pair_kernel(const SweepArgs p) {
+__global__ void __launch_bounds__(256, 3) sweep_pair_kernel(const SweepArgs p) {
   const int lane = threadIdx.x & 31;
   // Each block owns a contiguous range of tiles (spatially ordered chains),
   // walked by its warps in step; field values then repeat in L1.
