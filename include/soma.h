@@ -200,6 +200,36 @@ void* soma_stream(soma_t* h);
 soma_status soma_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
                         void* stream);
 
+/* S(q) for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart: this is a library convenience.  It computes
+ * exactly what soma_structure_factor computes, but allocates nothing: no
+ * cudaMalloc, no cudaFree, no host heap.  It is meant for code that cannot
+ * allocate at the moment it wants S(q), e.g. an analysis hook inside a host
+ * application whose memory pool owns all free device memory, or code that
+ * must not synchronise the device (cudaMalloc and cudaFree may).
+ *
+ * desc:     the system (validated like soma_create; desc->stream is ignored).
+ * density:  device pointer to the packed occupation numbers of that system
+ *           (cells words, n_A | n_B << 16, e.g. from soma_get_density).
+ * m, k:     host array of k integer wave-vector triples, k <= SOMA_SQ_NOALLOC_MAX_K.
+ * out:      host array of k doubles; returns after the results are there.
+ * stream:   cudaStream_t to run on (NULL: legacy default stream).
+ *
+ * Scratch (twiddle tables and block partial sums, about 768 KB) lives in one
+ * file-scope device array of libsoma, which every GPU that loads the library
+ * holds until the process exits.  The first call on a device looks up that
+ * array's device address (once per device); make it before any stream
+ * capture.  All calls share the array: two calls that overlap on the GPU
+ * (different streams, or different host threads without ordering) race and
+ * may return wrong values.  Every call overwrites all of the scratch it reads.
+ * Returns SOMA_EINVAL when k exceeds SOMA_SQ_NOALLOC_MAX_K or grid_x + grid_y +
+ * grid_z exceeds SOMA_SQ_NOALLOC_MAX_AXES, and SOMA_ECUDA on a CUDA error. */
+#define SOMA_SQ_NOALLOC_MAX_K 32
+#define SOMA_SQ_NOALLOC_MAX_AXES 1024
+soma_status soma_structure_factor_noalloc(const soma_system_desc* desc, const uint32_t* density,
+                                          const int32_t* m, size_t k, double* out, void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* soma_last_error(void);
 

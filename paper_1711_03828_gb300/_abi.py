@@ -91,6 +91,8 @@ _SIGS = {
     "soma_sync": ([_P], _c.c_int),
     "soma_stream": ([_P], _P),
     "soma_philox": ([_P, _P, _P, _c.c_size_t, _P], _c.c_int),
+    "soma_structure_factor_noalloc": ([_c.POINTER(SomaSystemDesc), _P, _P, _c.c_size_t, _P, _P],
+                                      _c.c_int),
 }
 
 
@@ -144,6 +146,7 @@ soma_get_timing = _wrap("soma_get_timing")
 soma_sync = _wrap("soma_sync")
 soma_stream = _wrap("soma_stream")
 soma_philox = _wrap("soma_philox")
+soma_structure_factor_noalloc = _wrap("soma_structure_factor_noalloc")
 
 
 def soma_last_error():

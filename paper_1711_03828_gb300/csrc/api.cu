@@ -320,6 +320,22 @@ soma_status update_fields(soma_t* h) {
 
 }  // namespace
 
+namespace soma {
+// Validation and geometry of a description for entry points that take no
+// handle (same rules as soma_create).
+soma_status describe(const soma_system_desc* d, Geom* g) {
+  soma_status st = validate(d);
+  if (st != SOMA_OK) return st;
+  soma_t tmp;
+  tmp.desc = *d;
+  derive(&tmp);
+  *g = tmp.g;
+  return SOMA_OK;
+}
+soma_status report(soma_status st, const char* msg) { return fail(st, "%s", msg); }
+soma_status report_cuda(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+}  // namespace soma
+
 extern "C" {
 
 int soma_abi_version(void) { return SOMA_ABI_VERSION; }

@@ -57,4 +57,11 @@ cudaError_t launch_structure_factor(const Geom& g, const uint32_t* n, const doub
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
                           cudaStream_t st);
 
+// Entry-point helpers implemented in api.cu (messages go to soma_last_error).
+}  // namespace soma
+#include "../../include/soma.h"
+namespace soma {
+soma_status describe(const soma_system_desc* d, Geom* g);
+soma_status report(soma_status st, const char* msg);
+soma_status report_cuda(cudaError_t e, const char* what);
 }  // namespace soma
