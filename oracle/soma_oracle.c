@@ -315,6 +315,99 @@ static void or_move_uniform(const or_system* s, float* x, float* y, float* z,
   if (accepted) accepted[m] = (uint8_t)acc_move;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Smart Monte Carlo (force-biased) move of Sec. 2.2 (Rossky, Doll, Friedman;  */
+/* Pangali, Rao, Berne): trial displacement dr = A F(r) + sqrt(2A) xi with xi a */
+/* vector of standard normals and F the force on the particle: the bonded      */
+/* force -2 k0/2 sum_n (r - r_n) plus minus the field gradient, taken by        */
+/* central differences of omega_t over the neighbouring cells.  Accepted with   */
+/* min(1, exp(-dE) T(r'->r)/T(r->r')), T(r->r') = exp(-|r'-r-A F(r)|^2/(4A)),   */
+/* which keeps the move exact for any force.  A = a^2/6, so that the per-axis    */
+/* variance 2A equals that of the uniform move, a^2/3.                          */
+/* Random numbers: normals from the Box-Muller transform of words (0,1) and    */
+/* (2,3) of the move draw (purpose 1), the acceptance uniform from word 0 of    */
+/* the second draw (purpose 2).                                                 */
+/* ------------------------------------------------------------------------- */
+static uint64_t or_cell_shift(const or_system* s, uint64_t c, int axis, int step) {
+  long long n[3] = { s->grid[0], s->grid[1], s->grid[2] };
+  long long k[3] = { (long long)(c % s->grid[0]), (long long)((c / s->grid[0]) % s->grid[1]),
+                     (long long)(c / ((uint64_t)s->grid[0] * s->grid[1])) };
+  k[axis] = ((k[axis] + step) % n[axis] + n[axis]) % n[axis];
+  return ((uint64_t)k[2] * s->grid[1] + (uint64_t)k[1]) * s->grid[0] + (uint64_t)k[0];
+}
+
+static void or_force(const or_system* s, const float* x, const float* y, const float* z,
+                     const double* w_t, uint64_t chain, uint32_t i, const double r[3],
+                     double F[3]) {
+  for (int d = 0; d < 3; ++d) F[d] = 0.0;
+  for (int side = -1; side <= 1; side += 2) {
+    long long jn = (long long)i + side;
+    if (jn < 0 || jn >= (long long)s->N) continue;
+    uint64_t n = chain * s->N + (uint64_t)jn;
+    double rn[3] = { x[n], y[n], z[n] };
+    for (int d = 0; d < 3; ++d) F[d] -= 2.0 * s->K_b * (r[d] - rn[d]);
+  }
+  uint64_t c = or_cell(s, r[0], r[1], r[2]);
+  for (int d = 0; d < 3; ++d)
+    F[d] -= 0.5 * (w_t[or_cell_shift(s, c, d, +1)] - w_t[or_cell_shift(s, c, d, -1)]);
+}
+
+static void or_move_smc(const or_system* s, float* x, float* y, float* z,
+                        const double* wA, const double* wB, uint32_t sweep,
+                        uint64_t chain, uint32_t i, double* margin, uint8_t* accepted,
+                        uint64_t* acc, uint64_t* ties) {
+  const uint32_t N = s->N;
+  const uint64_t m = chain * N + i;
+  const double* w_t = (i < s->N_A) ? wA : wB;
+  uint32_t w1[4], w2[4];
+  or_draw(s, OR_PURPOSE_MOVE, m, sweep, w1);
+  or_draw(s, OR_PURPOSE_MOVE2, m, sweep, w2);
+  double xi[4];
+  for (int p = 0; p < 2; ++p) {
+    double u1 = or_uniform_open(w1[2 * p]), u2 = or_uniform_open(w1[2 * p + 1]);
+    double rad = sqrt(-2.0 * log(u1)), th = 2.0 * M_PI * u2;
+    xi[2 * p] = rad * cos(th);
+    xi[2 * p + 1] = rad * sin(th);
+  }
+  const double A = s->a * s->a / 6.0;
+  double r_old[3] = { x[m], y[m], z[m] };
+  double F_old[3], F_new[3], r_new[3];
+  or_force(s, x, y, z, w_t, chain, i, r_old, F_old);
+  for (int d = 0; d < 3; ++d) {
+    float dx = (float)(A * F_old[d] + sqrt(2.0 * A) * xi[d]);
+    r_new[d] = (double)(float)(r_old[d] + (double)dx);
+  }
+  or_force(s, x, y, z, w_t, chain, i, r_new, F_new);
+  double dEb = 0.0;
+  for (int side = -1; side <= 1; side += 2) {
+    long long jn = (long long)i + side;
+    if (jn < 0 || jn >= (long long)N) continue;
+    uint64_t n = chain * N + (uint64_t)jn;
+    double rn[3] = { x[n], y[n], z[n] };
+    for (int d = 0; d < 3; ++d)
+      dEb += s->K_b * ((r_new[d] - rn[d]) * (r_new[d] - rn[d]) - (r_old[d] - rn[d]) * (r_old[d] - rn[d]));
+  }
+  double dE = dEb + (w_t[or_cell(s, r_new[0], r_new[1], r_new[2])] -
+                     w_t[or_cell(s, r_old[0], r_old[1], r_old[2])]);
+  double fwd = 0.0, rev = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    double f = r_new[d] - r_old[d] - A * F_old[d];
+    double b = r_old[d] - r_new[d] - A * F_new[d];
+    fwd += f * f;
+    rev += b * b;
+  }
+  const double log_alpha = -dE - rev / (4.0 * A) + fwd / (4.0 * A);
+  const double lnu = log(or_uniform_open(w2[0]));
+  const int acc_move = (log_alpha >= 0.0) || (lnu < log_alpha);
+  if (margin) margin[m] = lnu - log_alpha;
+  if (fabs(lnu - log_alpha) < 1e-4) (*ties)++;
+  if (acc_move) {
+    x[m] = (float)r_new[0]; y[m] = (float)r_new[1]; z[m] = (float)r_new[2];
+    (*acc)++;
+  }
+  if (accepted) accepted[m] = (uint8_t)acc_move;
+}
+
 /* Set order of one chain for one sweep: bit 0 of the fourth word of the move
  * draw of the chain's first particle picks odd->even (1) or even->odd (0); the
  * 24 bits that make the acceptance uniform are the word's top bits, so the set
@@ -341,7 +434,10 @@ void or_sweep(const or_system* s, float* x, float* y, float* z,
       uint32_t set = first ^ k;
       for (uint32_t i = set; i < N; i += 2) {
         uint64_t a1 = 0, t1 = 0;
-        or_move_uniform(s, x, y, z, wA, wB, sweep, chain, i, margin, accepted, &a1, &t1);
+        if (s->move == 1)
+          or_move_smc(s, x, y, z, wA, wB, sweep, chain, i, margin, accepted, &a1, &t1);
+        else
+          or_move_uniform(s, x, y, z, wA, wB, sweep, chain, i, margin, accepted, &a1, &t1);
         acc += a1;
         ties += t1;
       }

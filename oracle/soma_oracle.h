@@ -97,7 +97,8 @@ void or_fields(const or_system* s, const uint32_t* nA, const uint32_t* nB,
                double* wA, double* wB, int round_mode);
 
 /* --- a2: one SET sweep with frozen fields (Sec. 3.1.2, Listing 2 scheme) --- */
-/* margin (optional, M doubles): dE + ln u of each attempted move.
+/* margin (optional, M doubles): ln u - ln(acceptance ratio) of each attempted
+ * move (dE + ln u for the uniform move); the move is accepted iff it is < 0.
  * accepted (optional, M bytes): 1 if the move was accepted.
  * chain range [c0, c1) lets tests run a sample of chains. */
 void or_sweep(const or_system* s, float* x, float* y, float* z,

@@ -17,13 +17,19 @@ SRC = os.path.join(os.path.dirname(oracle.__file__), "soma_oracle.c")
 MUTANTS = [
     ("field_sign", "(w_t[c_new] - w_t[c_old])", "(w_t[c_old] - w_t[c_new])",
      lambda L: PIN.check_two_particle_balance_brute_force(0, L)),
-    ("field_type_swapped", "(i < s->N_A) ? wA : wB", "(i < s->N_A) ? wB : wA",
+    ("field_type_swapped", "const double* w_t = (i < s->N_A) ? wA : wB;\n  uint64_t c_old",
+     "const double* w_t = (i < s->N_A) ? wB : wA;\n  uint64_t c_old",
      lambda L: PIN.check_two_particle_balance_brute_force(0, L)),
     ("bond_half_strength", "dEb += s->K_b * (d_new - d_old);", "dEb += 0.5 * s->K_b * (d_new - d_old);",
      PIN.check_ideal_chain_relaxes_to_gaussian_statistics),
     ("metropolis_sign", "(lnu < -dE)", "(lnu < dE)",
      PIN.check_ideal_chain_relaxes_to_gaussian_statistics),
-    ("one_sided_bonds", "for (int side = -1; side <= 1; side += 2)", "for (int side = -1; side < 1; side += 2)",
+    ("one_sided_bonds", "  double dEb = 0.0;\n  for (int side = -1; side <= 1; side += 2) {\n"
+     "    long long jn = (long long)i + side;\n    if (jn < 0 || jn >= (long long)N) continue;\n"
+     "    uint64_t n = chain * N + (uint64_t)jn;\n    double rn[3] = { x[n], y[n], z[n] };\n    double d_new",
+     "  double dEb = 0.0;\n  for (int side = -1; side < 1; side += 2) {\n"
+     "    long long jn = (long long)i + side;\n    if (jn < 0 || jn >= (long long)N) continue;\n"
+     "    uint64_t n = chain * N + (uint64_t)jn;\n    double rn[3] = { x[n], y[n], z[n] };\n    double d_new",
      PIN.check_ideal_chain_relaxes_to_gaussian_statistics),
     ("chi_sign", "double a = comp - 0.5 * chi0 * (phiA - phiB);", "double a = comp + 0.5 * chi0 * (phiA - phiB);",
      PIN.check_fields_closed_forms),
@@ -50,6 +56,17 @@ MUTANTS = [
      PIN.check_structure_factor_matches_numpy_fft),
     ("bond_energy_observable", "Eb += s->K_b * bb;", "Eb += 2.0 * s->K_b * bb;",
      PIN.check_observables_hand_values),
+    ("smc_reverse_density_dropped", "const double log_alpha = -dE - rev / (4.0 * A) + fwd / (4.0 * A);",
+     "const double log_alpha = -dE;",
+     lambda L: PIN.check_two_particle_balance_brute_force(0, L, move=1)),
+    ("smc_field_gradient_sign", "F[d] -= 0.5 * (w_t[or_cell_shift(s, c, d, +1)] - w_t[or_cell_shift(s, c, d, -1)]);",
+     "F[d] += 0.5 * (w_t[or_cell_shift(s, c, d, +1)] - w_t[or_cell_shift(s, c, d, -1)]);",
+     PIN.check_smc_force_direction),
+    ("smc_bond_force_sign", "F[d] -= 2.0 * s->K_b * (r[d] - rn[d]);", "F[d] += 2.0 * s->K_b * (r[d] - rn[d]);",
+     PIN.check_smc_force_direction),
+    ("sort_key_axis", "for (int d = 0; d < 3; ++d) key |= ((b[d] >> bit) & 1u) << (3 * bit + d);",
+     "for (int d = 0; d < 3; ++d) key |= ((b[2 - d] >> bit) & 1u) << (3 * bit + d);",
+     PIN.check_sort_chains_is_a_spatial_permutation),
 ]
 
 

@@ -157,13 +157,13 @@ def check_field_rounding_modes(lib=None):
 # --------------------------------------------------------------------------
 # Moves: ideal chains (chiN = kappaN = 0) relax to the Gaussian closed forms
 # --------------------------------------------------------------------------
-def check_ideal_chain_relaxes_to_gaussian_statistics(lib=None):
+def check_ideal_chain_relaxes_to_gaussian_statistics(lib=None, move=0):
     """With chiN = kappaN = 0 every field vanishes and the Metropolis chain
     samples exp(-K_b sum b^2): <b^2> = R_e0^2/(N-1) and, the bonds being
     independent, <R_e^2> = R_e0^2.  Start from bonds stretched by 1.6x so
     the test sees the sweep relax the bond length."""
     d = workloads.melt_small(n_chains=1024, N=8, chiN=0.0, kappaN=0.0, box_Re=(2.0, 2.0, 1.0),
-                             grid=(12, 12, 6))
+                             grid=(12, 12, 6), move=move)
     s = oracle_system(d, lib)
     Re = 6.0
     sigma = Re / math.sqrt(3 * (d.N - 1))
@@ -189,7 +189,8 @@ def check_ideal_chain_relaxes_to_gaussian_statistics(lib=None):
     se_re2 = re2.std() / math.sqrt(d.n_chains)
     assert abs(b2.mean() - Re**2 / (d.N - 1)) < 5 * se_b2, (b2.mean(), Re**2 / (d.N - 1), se_b2)
     assert abs(re2.mean() - Re**2) < 5 * se_re2, (re2.mean(), Re**2, se_re2)
-    assert 0.2 < acc / att < 0.95
+    # force-biased proposals of a harmonic chain are accepted far more often
+    assert (0.2 < acc / att < 0.95) if move == 0 else (0.5 < acc / att < 0.999)
 
 
 # --------------------------------------------------------------------------
@@ -231,11 +232,11 @@ def _cells_of(P3, L):
     return (c[2] * L + c[1]) * L + c[0]
 
 
-def check_two_particle_balance_brute_force(set_order, lib=None):
+def check_two_particle_balance_brute_force(set_order, lib=None, move=0):
     L = 2
     Re = 1.5
     d = SystemDesc(n_chains=4096, N=2, f=0.5, box_Re=(L / Re,) * 3, grid=(L,) * 3,
-                   chiN=0.0, kappaN=0.0, set_order=set_order, seed=17)
+                   chiN=0.0, kappaN=0.0, set_order=set_order, seed=17, move=move)
     s = oracle_system(d, lib)
     K = s.params.K_b
     assert K == pytest.approx(3.0 / (2 * Re * Re))
@@ -347,13 +348,15 @@ def test_field_rounding_modes(oracle_lib):
     check_field_rounding_modes()
 
 
-def test_ideal_chain_relaxes_to_gaussian_statistics(oracle_lib):
-    check_ideal_chain_relaxes_to_gaussian_statistics()
+@pytest.mark.parametrize("move", [0, 1])
+def test_ideal_chain_relaxes_to_gaussian_statistics(oracle_lib, move):
+    check_ideal_chain_relaxes_to_gaussian_statistics(move=move)
 
 
 @pytest.mark.parametrize("set_order", [0, 1])
-def test_two_particle_balance_brute_force(oracle_lib, set_order):
-    check_two_particle_balance_brute_force(set_order)
+@pytest.mark.parametrize("move", [0, 1])
+def test_two_particle_balance_brute_force(oracle_lib, set_order, move):
+    check_two_particle_balance_brute_force(set_order, move=move)
 
 
 def test_sweep_moves_follow_the_draws(oracle_lib):
@@ -403,3 +406,42 @@ def check_sort_chains_is_a_spatial_permutation(lib=None):
 
 def test_sort_chains_is_a_spatial_permutation(oracle_lib):
     check_sort_chains_is_a_spatial_permutation()
+
+
+# --------------------------------------------------------------------------
+# Smart Monte Carlo: exactness is pinned by the balance tests above (the MH
+# correction makes any force exact); the direction of the force is pinned by
+# efficiency: force-biased trial moves down a field ramp and inside a harmonic
+# chain are accepted far more often than moves biased the wrong way.
+# --------------------------------------------------------------------------
+def check_smc_force_direction(lib=None):
+    d = SystemDesc(n_chains=4096, N=1, f=1.0, box_Re=(64 / 6, 8 / 6, 8 / 6), grid=(64, 8, 8),
+                   chiN=0.0, kappaN=0.0, a_Re=0.15, move=1, seed=3)
+    s = oracle_system(d, lib)
+    p = s.empty_positions()
+    rng = np.random.default_rng(1)
+    p.x[:] = rng.uniform(20, 44, d.M)
+    p.y[:] = rng.uniform(0, 8, d.M)
+    p.z[:] = rng.uniform(0, 8, d.M)
+    ramp = 0.8 * (np.arange(s.cells) % 64).astype(np.float64)  # omega = 0.8 kT per cell along x
+    acc = att = 0
+    for sweep in range(10):
+        st, _, _ = s.sweep(p, ramp, ramp, sweep)
+        acc += st.accepted
+        att += st.attempted
+    assert acc / att > 0.83, acc / att      # 0.87 with the force, 0.74 with it reversed
+    d2 = SystemDesc(n_chains=1024, N=8, box_Re=(2.0, 2.0, 1.0), grid=(12, 12, 6), chiN=0.0,
+                    kappaN=0.0, move=1)
+    s2 = oracle_system(d2, lib)
+    p2 = s2.init_chains()
+    w0 = np.zeros(s2.cells)
+    acc = att = 0
+    for sweep in range(20):
+        st, _, _ = s2.sweep(p2, w0, w0, sweep)
+        acc += st.accepted
+        att += st.attempted
+    assert acc / att > 0.9, acc / att       # 0.95 with the bond force, 0.32 reversed
+
+
+def test_smc_force_direction(oracle_lib):
+    check_smc_force_direction()
