@@ -35,6 +35,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="melt_large",
                     choices=["melt_large", "melt_mid", "melt_small", "melt_slow", "melt_subbox"])
+    ap.add_argument("--move", default="uniform", choices=["uniform", "smc"],
+                    help="trial moves: uniform displacement or smart Monte Carlo")
     ap.add_argument("--grid-dtype", default="f32", choices=["f32", "bf16", "f16"],
                     help="storage type of the omega grids (energies stay FP32)")
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -51,11 +53,12 @@ def dist_env():
 GRID_DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
 
 
-def workload(name, replica=0, grid_dtype="f32"):
+def workload(name, replica=0, grid_dtype="f32", move="uniform"):
     from paper_1711_03828_gb300 import workloads
     d = getattr(workloads, name)(seed=1)
     d.replica_id = replica
     d.grid_dtype = GRID_DTYPES[grid_dtype]
+    d.move = 1 if move == "smc" else 0
     return d
 
 
@@ -63,7 +66,8 @@ def config_of(d, name, l2_note):
     return {"workload": f"{name}: {d.n_chains} chains x N={d.N}, box {d.box_Re} R_e0, grid "
                         f"{d.grid}, chiN={d.chiN}, kappaN={d.kappaN}",
             "n_chains": d.n_chains, "N": d.N, "particles": d.M, "grid": list(d.grid),
-            "box_Re": list(d.box_Re), "chiN": d.chiN, "kappaN": d.kappaN, "move": "uniform",
+            "box_Re": list(d.box_Re), "chiN": d.chiN, "kappaN": d.kappaN,
+            "move": "smart Monte Carlo" if d.move == 1 else "uniform",
             "set_order": "random per chain and sweep",
             "grid_dtype": {0: "f32", 1: "bf16", 2: "f16"}[d.grid_dtype], "l2": l2_note}
 
@@ -239,7 +243,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     from paper_1711_03828_gb300 import System, _abi
 
-    d = workload(args.workload, replica=rank, grid_dtype=args.grid_dtype)
+    d = workload(args.workload, replica=rank, grid_dtype=args.grid_dtype, move=args.move)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     s = System(d, stream=stream)
@@ -315,10 +319,11 @@ def run_ours(args):
         "config": config_of(d, args.workload,
                             f"inputs larger than L2 ({12 * d.M / 1e9:.2f} GB of positions)"),
         "roofline": {"bound": "hbm",
-                     "kernel": "sweep_pair_kernel" if d.N % 2 == 0 and d.N <= 64
-                     else "sweep_uniform_kernel",
+                     "kernel": "sweep_smc_kernel" if d.move == 1 else
+                     ("sweep_pair_kernel" if d.N % 2 == 0 and d.N <= 64 else "sweep_uniform_kernel"),
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_kind": peak_kind, "traffic": measured_traffic(args.workload) if args.grid_dtype == "f32" else None,
+                     "peak_kind": peak_kind, "traffic": measured_traffic(args.workload)
+                     if args.grid_dtype == "f32" and args.move == "uniform" else None,
                      "bytes_per_launch": sweep_kernel_bytes(d), "ms_per_launch": sweep_ms,
                      "field_kernel_ms": field_ms,
                      "field_kernel_gbs": field_kernel_bytes(d) / (field_ms * 1e-3) / 1e9},

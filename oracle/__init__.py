@@ -103,6 +103,9 @@ def load(path):
     L.or_sweep.argtypes = [P, f32p, f32p, f32p, f64p, f64p, ctypes.c_uint32,
                            ctypes.c_uint64, ctypes.c_uint64, f64p, u8p,
                            ctypes.POINTER(OrSweepStats)]
+    L.or_sweep_trial.argtypes = [P, f32p, f32p, f32p, f64p, f64p, ctypes.c_uint32,
+                                 ctypes.c_uint64, ctypes.c_uint64, f64p, u8p, f32p,
+                                 ctypes.POINTER(OrSweepStats)]
     L.or_observables.argtypes = [P, f32p, f32p, f32p, u32p, u32p, ctypes.POINTER(OrObs)]
     L.or_structure_factor.argtypes = [P, u32p, u32p, i32p, ctypes.c_size_t, f64p]
     L.or_num_threads.restype = ctypes.c_int
@@ -224,16 +227,21 @@ class System:
                         _ptr(wA, f64p), _ptr(wB, f64p), int(round_mode))
         return wA, wB
 
-    def sweep(self, pos, wA, wB, sweep, c0=0, c1=None, want_margin=False, want_acc=False):
-        """One SET sweep in place; returns (stats, margin or None, accepted or None)."""
+    def sweep(self, pos, wA, wB, sweep, c0=0, c1=None, want_margin=False, want_acc=False,
+              want_trial=False):
+        """One SET sweep in place; returns (stats, margin or None, accepted or
+        None), plus the (3, M) trial positions when want_trial."""
         c1 = self.n_chains if c1 is None else c1
         margin = np.full(self.M, np.nan) if want_margin else None
         acc = np.zeros(self.M, np.uint8) if want_acc else None
+        trial = np.full(3 * self.M, np.nan, np.float32) if want_trial else None
         st = OrSweepStats()
-        self.L.or_sweep(ctypes.byref(self.s), _ptr(pos.x, f32p), _ptr(pos.y, f32p),
-                       _ptr(pos.z, f32p), _ptr(wA, f64p), _ptr(wB, f64p), int(sweep),
-                       int(c0), int(c1), _ptr(margin, f64p), _ptr(acc, u8p),
-                       ctypes.byref(st))
+        self.L.or_sweep_trial(ctypes.byref(self.s), _ptr(pos.x, f32p), _ptr(pos.y, f32p),
+                              _ptr(pos.z, f32p), _ptr(wA, f64p), _ptr(wB, f64p), int(sweep),
+                              int(c0), int(c1), _ptr(margin, f64p), _ptr(acc, u8p),
+                              _ptr(trial, f32p), ctypes.byref(st))
+        if want_trial:
+            return st, margin, acc, trial.reshape(3, self.M)
         return st, margin, acc
 
     def observables(self, pos, nA, nB):

@@ -271,7 +271,7 @@ void or_fields(const or_system* s, const uint32_t* nA, const uint32_t* nB,
 static void or_move_uniform(const or_system* s, float* x, float* y, float* z,
                             const double* wA, const double* wB, uint32_t sweep,
                             uint64_t chain, uint32_t i, double* margin, uint8_t* accepted,
-                            uint64_t* acc, uint64_t* ties) {
+                            float* trial, uint64_t* acc, uint64_t* ties) {
   const uint32_t N = s->N;
   const uint64_t m = chain * N + i;
   uint32_t w[4];
@@ -285,6 +285,10 @@ static void or_move_uniform(const or_system* s, float* x, float* y, float* z,
     r_new[d] = (double)(float)(r_old[d] + (double)dx);
   }
   double u = or_uniform_open(w[3]);
+  if (trial) {
+    const uint64_t M = s->n_chains * N;
+    for (int d = 0; d < 3; ++d) trial[d * M + m] = (float)r_new[d];
+  }
   /* bonded energy change: neighbours i-1 and i+1 of the linear chain */
   double dEb = 0.0;
   for (int side = -1; side <= 1; side += 2) {
@@ -355,7 +359,7 @@ static void or_force(const or_system* s, const float* x, const float* y, const f
 static void or_move_smc(const or_system* s, float* x, float* y, float* z,
                         const double* wA, const double* wB, uint32_t sweep,
                         uint64_t chain, uint32_t i, double* margin, uint8_t* accepted,
-                        uint64_t* acc, uint64_t* ties) {
+                        float* trial, uint64_t* acc, uint64_t* ties) {
   const uint32_t N = s->N;
   const uint64_t m = chain * N + i;
   const double* w_t = (i < s->N_A) ? wA : wB;
@@ -376,6 +380,10 @@ static void or_move_smc(const or_system* s, float* x, float* y, float* z,
   for (int d = 0; d < 3; ++d) {
     float dx = (float)(A * F_old[d] + sqrt(2.0 * A) * xi[d]);
     r_new[d] = (double)(float)(r_old[d] + (double)dx);
+  }
+  if (trial) {
+    const uint64_t M = s->n_chains * N;
+    for (int d = 0; d < 3; ++d) trial[d * M + m] = (float)r_new[d];
   }
   or_force(s, x, y, z, w_t, chain, i, r_new, F_new);
   double dEb = 0.0;
@@ -423,6 +431,13 @@ void or_sweep(const or_system* s, float* x, float* y, float* z,
               const double* wA, const double* wB, uint32_t sweep,
               uint64_t c0, uint64_t c1,
               double* margin, uint8_t* accepted, or_sweep_stats* st) {
+  or_sweep_trial(s, x, y, z, wA, wB, sweep, c0, c1, margin, accepted, NULL, st);
+}
+
+void or_sweep_trial(const or_system* s, float* x, float* y, float* z,
+                    const double* wA, const double* wB, uint32_t sweep,
+                    uint64_t c0, uint64_t c1,
+                    double* margin, uint8_t* accepted, float* trial, or_sweep_stats* st) {
   const uint32_t N = s->N;
   uint64_t acc = 0, ties = 0;
   long long i0 = (long long)c0, i1 = (long long)c1;
@@ -435,9 +450,9 @@ void or_sweep(const or_system* s, float* x, float* y, float* z,
       for (uint32_t i = set; i < N; i += 2) {
         uint64_t a1 = 0, t1 = 0;
         if (s->move == 1)
-          or_move_smc(s, x, y, z, wA, wB, sweep, chain, i, margin, accepted, &a1, &t1);
+          or_move_smc(s, x, y, z, wA, wB, sweep, chain, i, margin, accepted, trial, &a1, &t1);
         else
-          or_move_uniform(s, x, y, z, wA, wB, sweep, chain, i, margin, accepted, &a1, &t1);
+          or_move_uniform(s, x, y, z, wA, wB, sweep, chain, i, margin, accepted, trial, &a1, &t1);
         acc += a1;
         ties += t1;
       }

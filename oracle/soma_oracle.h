@@ -106,6 +106,13 @@ void or_sweep(const or_system* s, float* x, float* y, float* z,
               uint64_t c0, uint64_t c1,
               double* margin, uint8_t* accepted, or_sweep_stats* st);
 
+/* The same, also recording the trial position of every attempted move in
+ * trial (optional, 3*M floats, x|y|z planes). */
+void or_sweep_trial(const or_system* s, float* x, float* y, float* z,
+                    const double* wA, const double* wB, uint32_t sweep,
+                    uint64_t c0, uint64_t c1,
+                    double* margin, uint8_t* accepted, float* trial, or_sweep_stats* st);
+
 /* One full SCMF cycle: sweep all chains, then histogram, then fields. */
 void or_cycle(const or_system* s, float* x, float* y, float* z,
               uint32_t* nA, uint32_t* nB, double* wA, double* wB,

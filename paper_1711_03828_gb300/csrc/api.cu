@@ -123,7 +123,7 @@ soma_status validate(const soma_system_desc* d) {
   }
   if (!std::isfinite(d->chiN) || !std::isfinite(d->kappaN) || !std::isfinite(d->a_Re))
     return fail(SOMA_EINVAL, "chiN, kappaN and a_Re must be finite");
-  if (d->move != SOMA_MOVE_UNIFORM)
+  if (d->move != SOMA_MOVE_UNIFORM && d->move != SOMA_MOVE_SMC)
     return fail(SOMA_EINVAL, "move=%d is not available", d->move);
   if (d->set_order != SOMA_SET_ORDER_RANDOM && d->set_order != SOMA_SET_ORDER_FIXED)
     return fail(SOMA_EINVAL, "set_order=%d unknown", d->set_order);
@@ -229,6 +229,10 @@ SweepArgs sweep_args(soma_t* h) {
   s.full_tiles = h->g.n_chains / h->shape.G;
   s.last_rows = (uint32_t)(h->g.n_chains % h->shape.G) * h->g.N;
   s.set_order_random = h->desc.set_order == SOMA_SET_ORDER_RANDOM;
+  const double A = h->a64 * h->a64 / 6.0;
+  s.smc_A = (float)A;
+  s.smc_s2A = (float)std::sqrt(2.0 * A);
+  s.smc_inv4A = (float)(1.0 / (4.0 * A));
   return s;
 }
 
@@ -382,7 +386,7 @@ soma_status soma_create(const soma_system_desc* desc, soma_t** out) {
   ALLOC(h->d_scratch, sizeof(double) * (h->scratch_doubles + 64));
 #undef ALLOC
   h->d_out = h->d_scratch + h->scratch_doubles;
-  h->shape = sweep_shape(h->g.n_chains, h->g.N, h->sm_count, h->grid_dtype);
+  h->shape = sweep_shape(h->g.n_chains, h->g.N, h->sm_count, h->grid_dtype, desc->move);
 #define CK(call) do { e = (call); if (e != cudaSuccess) { release(h); return cuda_fail(e, #call); } } while (0)
   CK(cudaMemsetAsync(h->n[0], 0, sizeof(uint32_t) * cells, h->stream));
   CK(cudaMemsetAsync(h->n[1], 0, sizeof(uint32_t) * cells, h->stream));

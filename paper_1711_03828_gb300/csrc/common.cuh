@@ -46,6 +46,28 @@ __device__ __forceinline__ float log_uniform_open(uint32_t r) {
   return __logf(fmaf(__uint2float_rn(r >> 8), 5.9604644775390625e-8f, 2.98023223876953125e-8f));
 }
 
+// ln of the open uniform u = (k + 1/2)/2^24, accurate to about one FP32 ulp of
+// the result for every k: below 1/2 u itself is exact in FP32; above, 1 - u =
+// (2^24 - k - 1/2)/2^24 is exact instead and log1p is used.
+__device__ __forceinline__ float log_uniform_open_accurate(uint32_t r) {
+  const uint32_t k = r >> 8;
+  if (k < (1u << 23)) return logf(fmaf(__uint2float_rn(k), 5.9604644775390625e-8f,
+                                       2.98023223876953125e-8f));
+  const float one_minus_u = fmaf(__uint2float_rn((1u << 24) - k), 5.9604644775390625e-8f,
+                                 -2.98023223876953125e-8f);
+  return log1pf(-one_minus_u);
+}
+
+// cos and sin of 2 pi u for the open uniform u = (k + 1/2)/2^24: with the exact
+// symmetric uniform v = 2u - 1, 2 pi u = pi v + pi, so cos = -cospi(v) and
+// sin = -sinpi(v), evaluated without rounding the phase.
+__device__ __forceinline__ void sincos_2pi_uniform(uint32_t r, float* s, float* c) {
+  float sv, cv;
+  sincospif(uniform_sym(r), &sv, &cv);
+  *s = -sv;
+  *c = -cv;
+}
+
 // Open uniform in FP64 (init path): (k + 1/2)/2^24, exact.
 __device__ __forceinline__ double uniform_open_f64(uint32_t r) {
   return ((double)(r >> 8) + 0.5) * 5.9604644775390625e-8;
@@ -136,6 +158,8 @@ struct SweepArgs {
   uint64_t full_tiles;      // tiles holding G chains
   uint32_t last_rows;       // particles in the last, partial tile (0: none)
   int set_order_random;
+  // smart Monte Carlo: A = a^2/6, sqrt(2A), 1/(4A)
+  float smc_A, smc_s2A, smc_inv4A;
 };
 
 struct FieldArgs {

@@ -14,11 +14,12 @@ struct SweepShape {
   bool vec;
   bool pair;  // even N <= 64: one even and one odd particle per lane
   bool big;   // 64-bit particle indices (M >= 2^32)
+  int move;   // 0 uniform, 1 smart Monte Carlo
   int block;
   int grid;
 };
 
-SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dtype);
+SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dtype, int move);
 cudaError_t launch_sweep_uniform(const SweepArgs& a, const SweepShape& s, int grid_dtype,
                                  cudaStream_t st);
 

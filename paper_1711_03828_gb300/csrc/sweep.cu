@@ -367,6 +367,195 @@ __global__ void __launch_bounds__(256, 3) sweep_pair_kernel(const SweepArgs p) {
   if (lane == 0 && my_acc) atomicAdd(p.acc, (unsigned long long)my_acc);
 }
 
+// ---------------------------------------------------------------------------
+// Smart Monte Carlo (force-biased) step, any N (the tiling of
+// sweep_uniform_kernel).  Trial move dr = A F(r) + sqrt(2A) xi, F = bonded
+// force minus the central-difference gradient of omega_t over the six
+// neighbouring cells; accepted with min(1, exp(-dE) T(r'->r)/T(r->r')),
+// T(r->r') = exp(-|r'-r-A F(r)|^2/(4A)).  Normals by Box-Muller from the
+// first draw (purpose 1), the acceptance uniform from the second (purpose 2).
+__device__ __forceinline__ void cell3(const Geom& g, float x, float y, float z, uint32_t& cx,
+                                      uint32_t& cy, uint32_t& cz) {
+  cx = fold_cell(x, (uint32_t)g.nx, g.fold_m[0], g.fold_sh[0], g.fold_bias[0]);
+  cy = fold_cell(y, (uint32_t)g.ny, g.fold_m[1], g.fold_sh[1], g.fold_bias[1]);
+  cz = fold_cell(z, (uint32_t)g.nz, g.fold_m[2], g.fold_sh[2], g.fold_bias[2]);
+}
+
+// omega at the cell and minus its central-difference gradient (the field force).
+template <typename WT>
+__device__ __forceinline__ float field_and_force(const Geom& g, const WT* w, uint32_t cx, uint32_t cy,
+                                                 uint32_t cz, float& fx, float& fy, float& fz) {
+  const uint32_t nx = g.nx, ny = g.ny, nz = g.nz;
+  const uint32_t row = (cz * ny + cy) * nx;
+  const uint32_t xm = cx == 0 ? nx - 1 : cx - 1, xp = cx + 1 == nx ? 0 : cx + 1;
+  const uint32_t ym = cy == 0 ? ny - 1 : cy - 1, yp = cy + 1 == ny ? 0 : cy + 1;
+  const uint32_t zm = cz == 0 ? nz - 1 : cz - 1, zp = cz + 1 == nz ? 0 : cz + 1;
+  fx = -0.5f * (load_w<WT>(w, row + xp) - load_w<WT>(w, row + xm));
+  fy = -0.5f * (load_w<WT>(w, (cz * ny + yp) * nx + cx) - load_w<WT>(w, (cz * ny + ym) * nx + cx));
+  fz = -0.5f * (load_w<WT>(w, (zp * ny + cy) * nx + cx) - load_w<WT>(w, (zm * ny + cy) * nx + cx));
+  return load_w<WT>(w, row + cx);
+}
+
+template <int Q, typename WT>
+__global__ void __launch_bounds__(256) sweep_smc_kernel(const SweepArgs p) {
+  constexpr int S = 2 * Q;
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  const unsigned long long s64 = *p.d_sweep;
+  const uint32_t sweep = (uint32_t)s64;
+  uint32_t* __restrict__ nacc = ((s64 + 1ull) & 1ull) ? p.n1 : p.n0;
+  const WT* __restrict__ wA = static_cast<const WT*>(p.wA);
+  const WT* __restrict__ wB = static_cast<const WT*>(p.wB);
+  const uint32_t N = p.g.N, N_A = p.g.N_A;
+  const uint32_t ctr3a = (PURPOSE_MOVE << 24) | (p.g.replica & 0xFFFFFFu);
+  const uint32_t ctr3b = (PURPOSE_MOVE2 << 24) | (p.g.replica & 0xFFFFFFu);
+  const uint32_t li0 = (uint32_t)lane * S;
+  const float A = p.smc_A, s2A = p.smc_s2A, inv4A = p.smc_inv4A, K2 = 2.f * p.K_b;
+
+  uint32_t ci[S], src_lane[S], src_slot[S];
+  {
+    uint32_t g = li0 / N, i = li0 - g * N;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      ci[j] = i;
+      const uint32_t first = g * N;
+      src_lane[j] = (first / S) & 31u;
+      src_slot[j] = first % S;
+      if (++i == N) { i = 0; ++g; }
+    }
+  }
+
+  unsigned my_acc = 0;
+  for (uint64_t tile = warp0; tile < p.n_tiles; tile += nwarps) {
+    const uint64_t chain0 = tile * p.G;
+    const uint64_t rem = p.g.n_chains - chain0;
+    const uint32_t nmono = (rem < p.G ? (uint32_t)rem : p.G) * N;
+    const uint64_t base = chain0 * N + li0;
+
+    float x[S], y[S], z[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      const bool ok = li0 + j < nmono;
+      x[j] = ok ? __ldcs(p.x + base + j) : 0.f;
+      y[j] = ok ? __ldcs(p.y + base + j) : 0.f;
+      z[j] = ok ? __ldcs(p.z + base + j) : 0.f;
+    }
+
+    // configuration-independent part: normals, acceptance uniform, old cell,
+    // field and field force at the old cell
+    float gx[S], gy[S], gz[S], lnu[S], w_old[S], fox[S], foy[S], foz[S];
+    uint32_t co[S];
+    uint32_t lowbits = 0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      const uint64_t m = base + j;
+      const uint4 r1 = philox_rk(make_uint4((uint32_t)m, (uint32_t)(m >> 32), sweep, ctr3a), p.g);
+      const uint4 r2 = philox_rk(make_uint4((uint32_t)m, (uint32_t)(m >> 32), sweep, ctr3b), p.g);
+      lowbits |= (r1.w & 1u) << j;
+      float sn, cs;
+      const float rad0 = sqrtf(-2.f * log_uniform_open_accurate(r1.x));
+      sincos_2pi_uniform(r1.y, &sn, &cs);
+      gx[j] = rad0 * cs;
+      gy[j] = rad0 * sn;
+      const float rad1 = sqrtf(-2.f * log_uniform_open_accurate(r1.z));
+      sincos_2pi_uniform(r1.w, &sn, &cs);
+      gz[j] = rad1 * cs;
+      lnu[j] = log_uniform_open_accurate(r2.x);
+      uint32_t cx, cy, cz;
+      cell3(p.g, x[j], y[j], z[j], cx, cy, cz);
+      co[j] = (cz * (uint32_t)p.g.ny + cy) * (uint32_t)p.g.nx + cx;
+      const WT* wt = (ci[j] < N_A) ? wA : wB;
+      w_old[j] = 0.f;
+      fox[j] = foy[j] = foz[j] = 0.f;
+      if (li0 + j < nmono) w_old[j] = field_and_force<WT>(p.g, wt, cx, cy, cz, fox[j], foy[j], foz[j]);
+    }
+
+    uint32_t phase[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      uint32_t b = 0;
+      if (p.set_order_random) b = (__shfl_sync(FULL, lowbits, src_lane[j]) >> src_slot[j]) & 1u;
+      phase[j] = (ci[j] & 1u) ^ b;
+    }
+
+#pragma unroll
+    for (uint32_t ph = 0; ph < 2; ++ph) {
+      const float pxl = __shfl_up_sync(FULL, x[S - 1], 1);
+      const float pyl = __shfl_up_sync(FULL, y[S - 1], 1);
+      const float pzl = __shfl_up_sync(FULL, z[S - 1], 1);
+      const float nxl = __shfl_down_sync(FULL, x[0], 1);
+      const float nyl = __shfl_down_sync(FULL, y[0], 1);
+      const float nzl = __shfl_down_sync(FULL, z[0], 1);
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        if (li0 + j >= nmono || phase[j] != ph) continue;
+        const bool hp = ci[j] > 0, hn = ci[j] + 1 < N;
+        const float qx = (j > 0) ? x[j - 1] : pxl, qy = (j > 0) ? y[j - 1] : pyl,
+                    qz = (j > 0) ? z[j - 1] : pzl;
+        const float rx = (j < S - 1) ? x[j + 1] : nxl, ry = (j < S - 1) ? y[j + 1] : nyl,
+                    rz = (j < S - 1) ? z[j + 1] : nzl;
+        // U = sum over bonded partners of (r - n); bonded force = -2 K_b U
+        float ux = 0.f, uy = 0.f, uz = 0.f;
+        if (hp) { ux += x[j] - qx; uy += y[j] - qy; uz += z[j] - qz; }
+        if (hn) { ux += x[j] - rx; uy += y[j] - ry; uz += z[j] - rz; }
+        const float k = (float)((int)hp + (int)hn);
+        const float Fx = fmaf(-K2, ux, fox[j]), Fy = fmaf(-K2, uy, foy[j]), Fz = fmaf(-K2, uz, foz[j]);
+        const float tx = __fadd_rn(x[j], fmaf(s2A, gx[j], A * Fx));
+        const float ty = __fadd_rn(y[j], fmaf(s2A, gy[j], A * Fy));
+        const float tz = __fadd_rn(z[j], fmaf(s2A, gz[j], A * Fz));
+        uint32_t cx, cy, cz;
+        cell3(p.g, tx, ty, tz, cx, cy, cz);
+        const WT* wt = (ci[j] < N_A) ? wA : wB;
+        float fnx, fny, fnz;
+        const float w_new = field_and_force<WT>(p.g, wt, cx, cy, cz, fnx, fny, fnz);
+        const float dx = tx - x[j], dy = ty - y[j], dz = tz - z[j];
+        // bonded energy change d.(2U + k d); partners' new U' = U + k d
+        const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+        const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float dE = fmaf(p.K_b, fmaf(2.f, du, k * dd), w_new - w_old[j]);
+        const float Gx = fmaf(-K2, fmaf(k, dx, ux), fnx), Gy = fmaf(-K2, fmaf(k, dy, uy), fny),
+                    Gz = fmaf(-K2, fmaf(k, dz, uz), fnz);
+        const float ax = dx - A * Fx, ay = dy - A * Fy, az = dz - A * Fz;   // forward residual
+        const float bx = -dx - A * Gx, by = -dy - A * Gy, bz = -dz - A * Gz;  // reverse residual
+        const float fwd = fmaf(ax, ax, fmaf(ay, ay, az * az));
+        const float rev = fmaf(bx, bx, fmaf(by, by, bz * bz));
+        const float log_alpha = fmaf(fwd - rev, inv4A, -dE);
+        if (log_alpha >= 0.f || lnu[j] < log_alpha) {
+          x[j] = tx;
+          y[j] = ty;
+          z[j] = tz;
+          co[j] = (cz * (uint32_t)p.g.ny + cy) * (uint32_t)p.g.nx + cx;
+          ++my_acc;
+        }
+      }
+    }
+
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      if (li0 + j < nmono) {
+        __stcs(p.x + base + j, x[j]);
+        __stcs(p.y + base + j, y[j]);
+        __stcs(p.z + base + j, z[j]);
+        atomicAdd(nacc + co[j], (ci[j] < N_A) ? 1u : 0x10000u);
+      }
+    }
+  }
+
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) my_acc += __shfl_xor_sync(FULL, my_acc, o);
+  if (lane == 0 && my_acc) atomicAdd(p.acc, (unsigned long long)my_acc);
+}
+
+template <int Q>
+static const void* pick_smc(int grid_dtype) {
+  switch (grid_dtype) {
+    case 1: return (const void*)sweep_smc_kernel<Q, __nv_bfloat16>;
+    case 2: return (const void*)sweep_smc_kernel<Q, __half>;
+    default: return (const void*)sweep_smc_kernel<Q, float>;
+  }
+}
+
 template <int Q, bool VEC>
 static const void* pick_kernel(int grid_dtype) {
   switch (grid_dtype) {
@@ -376,7 +565,10 @@ static const void* pick_kernel(int grid_dtype) {
   }
 }
 
-static const void* sweep_kernel_ptr(int Q, bool vec, int grid_dtype, bool pair, bool big) {
+static const void* sweep_kernel_ptr(int Q, bool vec, int grid_dtype, bool pair, bool big,
+                                    int move) {
+  if (move == 1) return Q == 1 ? pick_smc<1>(grid_dtype) : (Q == 2 ? pick_smc<2>(grid_dtype)
+                                                                    : pick_smc<4>(grid_dtype));
   if (pair) {
     if (big) {
       switch (grid_dtype) {
@@ -396,8 +588,9 @@ static const void* sweep_kernel_ptr(int Q, bool vec, int grid_dtype, bool pair, 
   return vec ? pick_kernel<4, true>(grid_dtype) : pick_kernel<4, false>(grid_dtype);
 }
 
-SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dtype) {
+SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dtype, int move) {
   SweepShape s;
+  s.move = move;
   s.Q = (N <= 64) ? 1 : (N <= 128 ? 2 : 4);
   s.G = (uint32_t)(64 * s.Q) / N;
   s.n_tiles = (n_chains + s.G - 1) / s.G;
@@ -408,7 +601,7 @@ SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dty
   s.big = n_chains * N >= (1ull << 32) || s.n_tiles >= (1ull << 31);
   s.block = 256;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel_ptr(s.Q, s.vec, grid_dtype, s.pair, s.big),
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel_ptr(s.Q, s.vec, grid_dtype, s.pair, s.big, s.move),
                                                 s.block, 0);
   if (per_sm < 1) per_sm = 1;
   const uint64_t warps_per_block = (uint64_t)s.block / 32;
@@ -421,7 +614,7 @@ SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dty
 
 cudaError_t launch_sweep_uniform(const SweepArgs& a, const SweepShape& s, int grid_dtype,
                                  cudaStream_t st) {
-  const void* fn = sweep_kernel_ptr(s.Q, s.vec, grid_dtype, s.pair, s.big);
+  const void* fn = sweep_kernel_ptr(s.Q, s.vec, grid_dtype, s.pair, s.big, s.move);
   void* args[] = {const_cast<SweepArgs*>(&a)};
   return cudaLaunchKernel(fn, dim3(s.grid), dim3(s.block), args, 0, st);
 }
