@@ -200,6 +200,49 @@ void* soma_stream(soma_t* h);
 soma_status soma_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
                         void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent systems advanced together, one sweep launch and
+ * one field launch per cycle for the whole batch (no counterpart in the
+ * paper, which runs one system per MPI rank; the launch shape is chosen by
+ * an autotuner in the spirit of Sec. 3.2.2).
+ *
+ * Members are created as by soma_create and evolve bit-identically to the
+ * same system run alone.  Requirements: even N <= 64, uniform moves, one seed
+ * and one grid_dtype for all members (distinguish members by replica_id),
+ * M < 2^32 per member, at most SOMA_BATCH_MAX members.  soma_batch_system
+ * lends the member's handle for getters and observables; soma_sweep on a lent
+ * handle returns SOMA_ESTATE.  All members run on the batch's stream (NULL:
+ * the batch creates its own).
+ * ------------------------------------------------------------------------ */
+#define SOMA_BATCH_MAX 4096
+typedef struct soma_batch_t soma_batch_t;
+
+/* One launch shape of the batched sweep and its measured time. */
+typedef struct soma_tune_entry {
+  int32_t block;          /* threads per block */
+  int32_t blocks_per_sm;  /* resident blocks per SM (persistent grid) */
+  int32_t item_tiles;     /* 32-lane tiles per work item */
+  int32_t reserved;
+  double ms_per_cycle;    /* sweep + field update, CUDA events */
+} soma_tune_entry;
+
+soma_status soma_batch_create(const soma_system_desc* descs, uint32_t n, void* stream,
+                              soma_batch_t** out);
+soma_status soma_batch_destroy(soma_batch_t* b);
+/* n cycles of every member: n x (one sweep launch, one field launch). */
+soma_status soma_batch_sweep(soma_batch_t* b, uint32_t n);
+soma_status soma_batch_sync(soma_batch_t* b);
+soma_status soma_batch_system(soma_batch_t* b, uint32_t i, soma_t** out);
+/* Time every launch shape (block 128/256/512 x resident blocks per SM x
+ * work-item length 16/64/256 tiles) over cycles_per_candidate real cycles
+ * (the members advance), keep the fastest.  table (optional) receives up to
+ * table_len entries; *n_written the number of shapes tried. */
+soma_status soma_batch_autotune(soma_batch_t* b, uint32_t cycles_per_candidate,
+                                soma_tune_entry* table, uint32_t table_len, uint32_t* n_written);
+soma_status soma_batch_get_shape(soma_batch_t* b, soma_tune_entry* out);
+soma_status soma_batch_set_timing(soma_batch_t* b, int on);
+soma_status soma_batch_get_timing(soma_batch_t* b, soma_timing* out);
+
 /* S(q) for callers that cannot allocate device memory.
  *
  * The paper has no counterpart: this is a library convenience.  It computes

@@ -18,7 +18,7 @@ from . import _abi
 from ._abi import (FLAG_NO_SORT, GRID_BF16, GRID_F16, GRID_F32, MOVE_SMC, MOVE_UNIFORM,
                    SET_ORDER_FIXED, SET_ORDER_RANDOM, SomaError)
 
-__all__ = ["SystemDesc", "System", "SomaError", "FLAG_NO_SORT", "MOVE_UNIFORM", "MOVE_SMC", "SET_ORDER_RANDOM",
+__all__ = ["SystemDesc", "System", "Batch", "SomaError", "FLAG_NO_SORT", "MOVE_UNIFORM", "MOVE_SMC", "SET_ORDER_RANDOM",
            "SET_ORDER_FIXED", "GRID_F32", "GRID_BF16", "GRID_F16"]
 
 
@@ -77,21 +77,26 @@ def _torch_stream_handle(stream):
 
 
 class System:
-    """One SCMF system on the GPU (owns a ``soma_t``)."""
+    """One SCMF system on the GPU (owns a ``soma_t``, or borrows one from a Batch)."""
 
-    def __init__(self, desc: SystemDesc, stream=None):
+    def __init__(self, desc: SystemDesc, stream=None, _borrowed=None):
         self.desc = desc
         self._stream_obj = stream
+        if _borrowed is not None:
+            self.h = _borrowed
+            self._owner = False
+            return
         h = ctypes.c_void_p()
         c = desc.to_c(_torch_stream_handle(stream))
         _abi.soma_create(ctypes.byref(c), ctypes.byref(h))
         self.h = h
+        self._owner = True
 
     # -- lifetime ---------------------------------------------------------
     def close(self):
-        if getattr(self, "h", None) is not None and self.h.value:
+        if getattr(self, "h", None) is not None and self.h.value and getattr(self, "_owner", True):
             _abi.soma_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -190,3 +195,63 @@ class System:
     @property
     def stream_handle(self):
         return _abi.soma_stream(self.h)
+
+
+class Batch:
+    """Many independent systems advanced by one sweep launch and one field
+    launch per cycle (``soma_batch_*``)."""
+
+    def __init__(self, descs, stream=None):
+        self.descs = list(descs)
+        arr = (_abi.SomaSystemDesc * len(self.descs))(*[d.to_c() for d in self.descs])
+        h = ctypes.c_void_p()
+        _abi.soma_batch_create(arr, len(self.descs), _torch_stream_handle(stream), ctypes.byref(h))
+        self.h = h
+        self.members = []
+        for i, d in enumerate(self.descs):
+            m = ctypes.c_void_p()
+            _abi.soma_batch_system(self.h, i, ctypes.byref(m))
+            self.members.append(System(d, _borrowed=m))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            for m in self.members:
+                m.h = None
+            _abi.soma_batch_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n=1):
+        _abi.soma_batch_sweep(self.h, int(n))
+
+    def sync(self):
+        _abi.soma_batch_sync(self.h)
+
+    def autotune(self, cycles_per_candidate=3):
+        tab = (_abi.SomaTuneEntry * 64)()
+        nw = ctypes.c_uint32()
+        _abi.soma_batch_autotune(self.h, int(cycles_per_candidate), tab, 64, ctypes.byref(nw))
+        return [dict(block=t.block, blocks_per_sm=t.blocks_per_sm, item_tiles=t.item_tiles,
+                     ms_per_cycle=t.ms_per_cycle) for t in tab[:nw.value]]
+
+    def shape(self):
+        t = _abi.SomaTuneEntry()
+        _abi.soma_batch_get_shape(self.h, ctypes.byref(t))
+        return dict(block=t.block, blocks_per_sm=t.blocks_per_sm, item_tiles=t.item_tiles)
+
+    def set_timing(self, on=True):
+        _abi.soma_batch_set_timing(self.h, 1 if on else 0)
+
+    def timing(self):
+        t = _abi.SomaTiming()
+        _abi.soma_batch_get_timing(self.h, ctypes.byref(t))
+        return {k: getattr(t, k) for k, _ in _abi.SomaTiming._fields_}
+
+    @property
+    def M(self):
+        return sum(d.M for d in self.descs)

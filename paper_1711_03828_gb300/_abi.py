@@ -61,6 +61,12 @@ class SomaTiming(ctypes.Structure):
     ]
 
 
+class SomaTuneEntry(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("item_tiles", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ms_per_cycle", ctypes.c_double)]
+
+
 class SomaError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"soma status {status}: {msg}")
@@ -93,6 +99,16 @@ _SIGS = {
     "soma_philox": ([_P, _P, _P, _c.c_size_t, _P], _c.c_int),
     "soma_structure_factor_noalloc": ([_c.POINTER(SomaSystemDesc), _P, _P, _c.c_size_t, _P, _P],
                                       _c.c_int),
+    "soma_batch_create": ([_c.POINTER(SomaSystemDesc), _c.c_uint32, _P, _c.POINTER(_P)], _c.c_int),
+    "soma_batch_destroy": ([_P], _c.c_int),
+    "soma_batch_sweep": ([_P, _c.c_uint32], _c.c_int),
+    "soma_batch_sync": ([_P], _c.c_int),
+    "soma_batch_system": ([_P, _c.c_uint32, _c.POINTER(_P)], _c.c_int),
+    "soma_batch_autotune": ([_P, _c.c_uint32, _c.POINTER(SomaTuneEntry), _c.c_uint32,
+                             _c.POINTER(_c.c_uint32)], _c.c_int),
+    "soma_batch_get_shape": ([_P, _c.POINTER(SomaTuneEntry)], _c.c_int),
+    "soma_batch_set_timing": ([_P, _c.c_int], _c.c_int),
+    "soma_batch_get_timing": ([_P, _c.POINTER(SomaTiming)], _c.c_int),
 }
 
 
@@ -147,6 +163,15 @@ soma_sync = _wrap("soma_sync")
 soma_stream = _wrap("soma_stream")
 soma_philox = _wrap("soma_philox")
 soma_structure_factor_noalloc = _wrap("soma_structure_factor_noalloc")
+soma_batch_create = _wrap("soma_batch_create")
+soma_batch_destroy = _wrap("soma_batch_destroy")
+soma_batch_sweep = _wrap("soma_batch_sweep")
+soma_batch_sync = _wrap("soma_batch_sync")
+soma_batch_system = _wrap("soma_batch_system")
+soma_batch_autotune = _wrap("soma_batch_autotune")
+soma_batch_get_shape = _wrap("soma_batch_get_shape")
+soma_batch_set_timing = _wrap("soma_batch_set_timing")
+soma_batch_get_timing = _wrap("soma_batch_get_timing")
 
 
 def soma_last_error():

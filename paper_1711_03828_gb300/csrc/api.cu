@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -89,6 +90,7 @@ struct soma_t {
   std::vector<cudaEvent_t> ev_free;
   soma_timing t{};
   cudaGraphExec_t graph = nullptr;
+  bool batched = false;  // advanced only through its soma_batch_t
 
   float* x() { return pos; }
   float* y() { return pos + plane; }
@@ -430,6 +432,7 @@ soma_status soma_destroy(soma_t* h) {
 
 soma_status soma_sweep(soma_t* h, uint32_t n) {
   if (!h) return fail(SOMA_EINVAL, "handle is NULL");
+  if (h->batched) return fail(SOMA_ESTATE, "this system belongs to a batch: use soma_batch_sweep");
   uint32_t done = 0;
   if (!h->timing && n >= GRAPH_CHUNK) {
     if (!h->graph) {
@@ -636,6 +639,355 @@ soma_status soma_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out,
                         void* stream) {
   if (n && (!ctr || !key || !out)) return fail(SOMA_EINVAL, "NULL argument");
   SOMA_CUDA(launch_philox(ctr, key, out, n, (cudaStream_t)stream));
+  return SOMA_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batches of independent systems (one sweep launch + one field launch per cycle)
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct soma_batch_t {
+  std::vector<soma_t*> sys;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sm_count = 0;
+  int grid_dtype = 0;
+  BatchSys* d_sys = nullptr;
+  BatchItem* d_items = nullptr;
+  uint32_t n_items = 0, items_cap = 0;
+  unsigned* d_aux = nullptr;  // [0] arrival counter, [1] error bits
+  uint32_t total_cells = 0;
+  BatchArgs args{};
+  int block = 256, blocks_per_sm = 2, item_tiles = 64;
+  cudaGraphExec_t graph = nullptr;
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_sweep, ev_field;
+  soma_timing t{};
+};
+
+namespace {
+
+void batch_release(soma_batch_t* b) {
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (auto& e : b->ev_sweep) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+  for (auto& e : b->ev_field) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+  for (soma_t* h : b->sys) {
+    h->batched = false;
+    h->own_stream = false;
+    release(h);
+  }
+  cudaFree(b->d_sys);
+  cudaFree(b->d_items);
+  cudaFree(b->d_aux);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+soma_status batch_items(soma_batch_t* b, int item_tiles) {
+  std::vector<BatchItem> items;
+  for (uint32_t k = 0; k < b->sys.size(); ++k) {
+    const uint32_t nt = (uint32_t)b->sys[k]->shape.n_tiles;
+    for (uint32_t t0 = 0; t0 < nt; t0 += (uint32_t)item_tiles)
+      items.push_back({k, t0, std::min(nt, t0 + (uint32_t)item_tiles)});
+  }
+  if (items.size() > b->items_cap) {
+    cudaFree(b->d_items);
+    b->d_items = nullptr;
+    SOMA_CUDA(cudaMalloc((void**)&b->d_items, sizeof(BatchItem) * items.size()));
+    b->items_cap = (uint32_t)items.size();
+  }
+  SOMA_CUDA(cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(),
+                            cudaMemcpyHostToDevice, b->stream));
+  SOMA_CUDA(cudaStreamSynchronize(b->stream));
+  b->n_items = (uint32_t)items.size();
+  b->item_tiles = item_tiles;
+  b->args.items = b->d_items;
+  b->args.n_items = b->n_items;
+  if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+  return SOMA_OK;
+}
+
+soma_status batch_cycle(soma_batch_t* b) {
+  cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (b->timing)
+    for (auto& x : e) SOMA_CUDA(cudaEventCreate(&x));
+  if (b->timing) SOMA_CUDA(cudaEventRecord(e[0], b->stream));
+  SOMA_CUDA(launch_sweep_batch(b->args, b->sm_count * b->blocks_per_sm, b->block, b->grid_dtype,
+                               b->stream));
+  if (b->timing) {
+    SOMA_CUDA(cudaEventRecord(e[1], b->stream));
+    SOMA_CUDA(cudaEventRecord(e[2], b->stream));
+  }
+  SOMA_CUDA(launch_fields_batch(b->args, b->total_cells, b->d_aux, b->d_aux + 1, b->grid_dtype,
+                                b->sm_count, b->stream));
+  if (b->timing) {
+    SOMA_CUDA(cudaEventRecord(e[3], b->stream));
+    b->ev_sweep.push_back({e[0], e[1]});
+    b->ev_field.push_back({e[2], e[3]});
+  }
+  b->t.sweep_launches++;
+  b->t.field_launches++;
+  b->t.kernel_launches += 2;
+  for (soma_t* h : b->sys) ++h->host_sweep;
+  return SOMA_OK;
+}
+
+soma_status batch_graph(soma_batch_t* b) {
+  cudaGraph_t gr = nullptr;
+  SOMA_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (uint32_t k = 0; k < GRAPH_CHUNK && e == cudaSuccess; ++k) {
+    e = launch_sweep_batch(b->args, b->sm_count * b->blocks_per_sm, b->block, b->grid_dtype,
+                           b->stream);
+    if (e == cudaSuccess)
+      e = launch_fields_batch(b->args, b->total_cells, b->d_aux, b->d_aux + 1, b->grid_dtype,
+                              b->sm_count, b->stream);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(b->stream, &gr);
+  if (e != cudaSuccess) { if (gr) cudaGraphDestroy(gr); return cuda_fail(e, "batch graph capture"); }
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&b->graph, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) { b->graph = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+  return SOMA_OK;
+}
+
+soma_status batch_collect_timing(soma_batch_t* b) {
+  SOMA_CUDA(cudaStreamSynchronize(b->stream));
+  for (auto& e : b->ev_sweep) {
+    float ms = 0.f;
+    SOMA_CUDA(cudaEventElapsedTime(&ms, e.first, e.second));
+    b->t.ms_sweep += ms;
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  for (auto& e : b->ev_field) {
+    float ms = 0.f;
+    SOMA_CUDA(cudaEventElapsedTime(&ms, e.first, e.second));
+    b->t.ms_fields += ms;
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  b->ev_sweep.clear();
+  b->ev_field.clear();
+  return SOMA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+soma_status soma_batch_create(const soma_system_desc* descs, uint32_t n, void* stream,
+                              soma_batch_t** out) {
+  if (!out || !descs) return fail(SOMA_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (n < 1 || n > SOMA_BATCH_MAX) return fail(SOMA_EINVAL, "batch size %u outside 1..%d", n, SOMA_BATCH_MAX);
+  for (uint32_t k = 0; k < n; ++k) {
+    soma_status st = validate(descs + k);
+    if (st != SOMA_OK) return st;
+    const soma_system_desc& d = descs[k];
+    if (d.N % 2 != 0 || d.N > 64)
+      return fail(SOMA_EINVAL, "batch member %u: N=%u (a batch takes even N <= 64)", k, d.N);
+    if (d.move != SOMA_MOVE_UNIFORM)
+      return fail(SOMA_EINVAL, "batch member %u: only uniform moves are batched", k);
+    if (d.seed != descs[0].seed)
+      return fail(SOMA_EINVAL, "batch member %u: all members share one seed (use replica_id)", k);
+    if (d.grid_dtype != descs[0].grid_dtype)
+      return fail(SOMA_EINVAL, "batch member %u: all members share one grid_dtype", k);
+    if (d.n_chains * d.N >= (1ull << 32)) return fail(SOMA_EINVAL, "batch member %u: M >= 2^32", k);
+  }
+  soma_batch_t* b = new (std::nothrow) soma_batch_t();
+  if (!b) return fail(SOMA_ENOMEM, "host allocation failed");
+  cudaError_t e = cudaSuccess;
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaStreamCreate"); }
+    b->own_stream = true;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  b->grid_dtype = descs[0].grid_dtype;
+  std::vector<BatchSys> table(n);
+  uint32_t cells = 0;
+  for (uint32_t k = 0; k < n; ++k) {
+    soma_system_desc d = descs[k];
+    d.stream = b->stream;
+    soma_t* h = nullptr;
+    soma_status st = soma_create(&d, &h);
+    if (st != SOMA_OK) {
+      std::string m = g_last_error;
+      batch_release(b);
+      g_last_error = "batch member " + std::to_string(k) + ": " + m;
+      return st;
+    }
+    h->batched = true;
+    b->sys.push_back(h);
+    BatchSys& S = table[k];
+    S.g = h->g;
+    S.x = h->x();
+    S.y = h->y();
+    S.z = h->z();
+    S.wA = h->w[0];
+    S.wB = h->w[1];
+    S.n0 = h->n[0];
+    S.n1 = h->n[1];
+    S.counters = h->d_counters;
+    S.a = h->a32;
+    S.K_b = (float)h->K_b;
+    S.G = h->shape.G;
+    S.full_tiles = (uint32_t)(h->g.n_chains / h->shape.G);
+    S.last_rows = (uint32_t)(h->g.n_chains % h->shape.G) * h->g.N;
+    S.cell_begin = cells;
+    S.inv_rho = (float)(1.0 / h->rho_cell);
+    S.kappa0 = (float)(h->desc.kappaN / (double)h->desc.N);
+    S.half_chi0 = (float)(0.5 * h->desc.chiN / (double)h->desc.N);
+    S.set_order_random = h->desc.set_order == SOMA_SET_ORDER_RANDOM;
+    cells += h->g.cells;
+    if (cells < h->g.cells) { batch_release(b); return fail(SOMA_EINVAL, "batch grids exceed 2^32 cells"); }
+  }
+  b->total_cells = cells;
+#define BCK(call) do { e = (call); if (e != cudaSuccess) { batch_release(b); return cuda_fail(e, #call); } } while (0)
+  BCK(cudaMalloc((void**)&b->d_sys, sizeof(BatchSys) * n));
+  BCK(cudaMalloc((void**)&b->d_aux, sizeof(unsigned) * 2));
+  BCK(cudaMemsetAsync(b->d_aux, 0, sizeof(unsigned) * 2, b->stream));
+  BCK(cudaMemcpyAsync(b->d_sys, table.data(), sizeof(BatchSys) * n, cudaMemcpyHostToDevice, b->stream));
+#undef BCK
+  b->args.sys = b->d_sys;
+  b->args.n_sys = n;
+  b->args.keys = b->sys[0]->g;
+  b->args.d_sweep = b->sys[0]->d_counters;
+  const int fit = batch_kernel_blocks_per_sm(b->block, b->grid_dtype);
+  b->blocks_per_sm = fit < 1 ? 1 : (fit < 2 ? fit : 2);
+  soma_status st = batch_items(b, b->item_tiles);
+  if (st != SOMA_OK) { std::string m = g_last_error; batch_release(b); g_last_error = m; return st; }
+  *out = b;
+  return SOMA_OK;
+}
+
+soma_status soma_batch_destroy(soma_batch_t* b) {
+  if (!b) return SOMA_OK;
+  batch_release(b);
+  return SOMA_OK;
+}
+
+soma_status soma_batch_system(soma_batch_t* b, uint32_t i, soma_t** out) {
+  if (!b || !out) return fail(SOMA_EINVAL, "NULL argument");
+  if (i >= b->sys.size()) return fail(SOMA_EINVAL, "member %u of a batch of %zu", i, b->sys.size());
+  *out = b->sys[i];
+  return SOMA_OK;
+}
+
+soma_status soma_batch_sweep(soma_batch_t* b, uint32_t n) {
+  if (!b) return fail(SOMA_EINVAL, "batch is NULL");
+  uint32_t done = 0;
+  if (!b->timing && n >= GRAPH_CHUNK) {
+    if (!b->graph) {
+      soma_status st = batch_graph(b);
+      if (st != SOMA_OK) return st;
+    }
+    while (n - done >= GRAPH_CHUNK) {
+      SOMA_CUDA(cudaGraphLaunch(b->graph, b->stream));
+      b->t.sweep_launches += GRAPH_CHUNK;
+      b->t.field_launches += GRAPH_CHUNK;
+      b->t.kernel_launches += 2 * GRAPH_CHUNK;
+      for (soma_t* h : b->sys) h->host_sweep += GRAPH_CHUNK;
+      done += GRAPH_CHUNK;
+    }
+  }
+  for (; done < n; ++done) {
+    soma_status st = batch_cycle(b);
+    if (st != SOMA_OK) return st;
+  }
+  return SOMA_OK;
+}
+
+soma_status soma_batch_sync(soma_batch_t* b) {
+  if (!b) return fail(SOMA_EINVAL, "batch is NULL");
+  SOMA_CUDA(cudaStreamSynchronize(b->stream));
+  unsigned err = 0;
+  SOMA_CUDA(cudaMemcpy(&err, b->d_aux + 1, sizeof err, cudaMemcpyDeviceToHost));
+  if (err & ERR_OVERFLOW) return fail(SOMA_EOVERFLOW, "a 16-bit occupation number reached 0xC000");
+  return SOMA_OK;
+}
+
+soma_status soma_batch_set_timing(soma_batch_t* b, int on) {
+  if (!b) return fail(SOMA_EINVAL, "batch is NULL");
+  soma_status st = batch_collect_timing(b);
+  if (st != SOMA_OK) return st;
+  b->timing = on != 0;
+  if (b->timing) b->t.ms_sweep = b->t.ms_fields = 0.0;
+  return SOMA_OK;
+}
+
+soma_status soma_batch_get_timing(soma_batch_t* b, soma_timing* out) {
+  if (!b || !out) return fail(SOMA_EINVAL, "NULL argument");
+  soma_status st = batch_collect_timing(b);
+  if (st != SOMA_OK) return st;
+  *out = b->t;
+  return SOMA_OK;
+}
+
+soma_status soma_batch_autotune(soma_batch_t* b, uint32_t cycles_per_candidate,
+                                soma_tune_entry* table, uint32_t table_len, uint32_t* n_written) {
+  if (!b) return fail(SOMA_EINVAL, "batch is NULL");
+  if (cycles_per_candidate < 1) cycles_per_candidate = 1;
+  const int blocks[3] = {128, 256, 512};
+  const int items[3] = {16, 64, 256};
+  std::vector<soma_tune_entry> res;
+  cudaEvent_t e0, e1;
+  SOMA_CUDA(cudaEventCreate(&e0));
+  SOMA_CUDA(cudaEventCreate(&e1));
+  const bool was_timing = b->timing;
+  b->timing = false;
+  soma_tune_entry best{};
+  best.ms_per_cycle = 1e30;
+  for (int it : items) {
+    soma_status st = batch_items(b, it);
+    if (st != SOMA_OK) return st;
+    for (int blk : blocks) {
+      const int fit = batch_kernel_blocks_per_sm(blk, b->grid_dtype);
+      for (int bps = 1; bps <= fit && bps <= 4; ++bps) {
+        b->block = blk;
+        b->blocks_per_sm = bps;
+        st = batch_cycle(b);  // warm-up with this shape
+        if (st != SOMA_OK) return st;
+        SOMA_CUDA(cudaEventRecord(e0, b->stream));
+        for (uint32_t c = 0; c < cycles_per_candidate; ++c) {
+          st = batch_cycle(b);
+          if (st != SOMA_OK) return st;
+        }
+        SOMA_CUDA(cudaEventRecord(e1, b->stream));
+        SOMA_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        SOMA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        soma_tune_entry r{blk, bps, it, 0, (double)ms / cycles_per_candidate};
+        res.push_back(r);
+        if (r.ms_per_cycle < best.ms_per_cycle) best = r;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->timing = was_timing;
+  b->block = best.block;
+  b->blocks_per_sm = best.blocks_per_sm;
+  soma_status st = batch_items(b, best.item_tiles);
+  if (st != SOMA_OK) return st;
+  if (table)
+    for (uint32_t k = 0; k < table_len && k < res.size(); ++k) table[k] = res[k];
+  if (n_written) *n_written = (uint32_t)res.size();
+  return SOMA_OK;
+}
+
+soma_status soma_batch_get_shape(soma_batch_t* b, soma_tune_entry* out) {
+  if (!b || !out) return fail(SOMA_EINVAL, "NULL argument");
+  *out = soma_tune_entry{b->block, b->blocks_per_sm, b->item_tiles, 0, 0.0};
   return SOMA_OK;
 }
 

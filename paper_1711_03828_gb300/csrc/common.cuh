@@ -177,6 +177,37 @@ struct FieldArgs {
                             // 0: read n[s&1], clear n[(s+1)&1]
 };
 
+// One system of a batch (device table entry).
+struct BatchSys {
+  Geom g;                          // geometry and cell fold of this system
+  float* x;
+  float* y;
+  float* z;
+  const void* wA;
+  const void* wB;
+  uint32_t* n0;
+  uint32_t* n1;
+  unsigned long long* counters;    // [0] sweep counter, [1] accepted moves
+  float a, K_b;
+  uint32_t G, full_tiles, last_rows;
+  uint32_t cell_begin;             // offset of this grid in the concatenated cells
+  float inv_rho, kappa0, half_chi0;
+  int set_order_random;
+};
+
+struct BatchItem {
+  uint32_t sys, t0, t1;            // tiles [t0, t1) of system sys
+};
+
+struct BatchArgs {
+  const BatchSys* sys;
+  uint32_t n_sys;
+  const BatchItem* items;
+  uint32_t n_items;
+  Geom keys;                       // Philox round keys (one seed for the batch)
+  const unsigned long long* d_sweep;  // every member's counter has this value
+};
+
 constexpr unsigned ERR_OVERFLOW = 1u;
 constexpr unsigned ERR_TIMEOUT = 2u;
 

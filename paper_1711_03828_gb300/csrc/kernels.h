@@ -58,6 +58,12 @@ cudaError_t launch_structure_factor(const Geom& g, const uint32_t* n, const doub
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
                           cudaStream_t st);
 
+cudaError_t launch_sweep_batch(const BatchArgs& a, int grid, int block, int grid_dtype,
+                               cudaStream_t st);
+cudaError_t launch_fields_batch(const BatchArgs& a, uint32_t total_cells, unsigned* arrive,
+                                unsigned* err, int grid_dtype, int sm_count, cudaStream_t st);
+int batch_kernel_blocks_per_sm(int block, int grid_dtype);
+
 // Entry-point helpers implemented in api.cu (messages go to soma_last_error).
 }  // namespace soma
 #include "../../include/soma.h"

@@ -1,0 +1,149 @@
+// pair_body.cuh -- one tile of the paired SET sweep (even N <= 64), shared by
+// the single-system kernel (sweep.cu) and the batched kernel (batch.cu).
+//
+// Lane l of a tile holds particles 2l (even chain position, slot 0) and 2l+1
+// (odd, slot 1) of the SAME chain.  Each SET phase moves exactly one of the
+// two, so every lane does one move per phase with no predicated duplicate
+// work.  After the draws the pair is re-labelled once per tile into A (moves
+// in the first phase) and B (moves in the second) with the chain's set-order
+// bit, so the phases need no selects:
+//   phase 1 moves A; its bond partners are B (same lane) and the adjacent
+//     lane's B (lane-1 if A is the even particle, lane+1 if it is odd);
+//   phase 2 moves B; its partners are A (same lane, already updated) and the
+//     adjacent lane's A (lane+1 if B is odd, lane-1 if it is even).
+// Bond energy change of a move r -> r + d with k partners n:
+//   sum_n |r+d-n|^2 - |r-n|^2 = 2 d.U + k d.d,  U = sum_n (r - n),
+// where every difference r - n is exact for bonded neighbours.
+#pragma once
+
+#include "common.cuh"
+
+namespace soma {
+
+// Per-lane constants of one system (depend on N and the lane only).
+template <typename WT>
+struct PairLane {
+  int lane, first_lane;
+  bool has_prev0, has_next1;
+  const WT* w0;
+  const WT* w1;
+  uint32_t v0, v1;
+  uint32_t li0;
+
+  __device__ __forceinline__ void init(int lane_, uint32_t N, uint32_t N_A, const void* wA,
+                                       const void* wB) {
+    lane = lane_;
+    li0 = 2u * (uint32_t)lane;
+    const uint32_t ci0 = li0 % N;                 // chain position of slot 0 (even)
+    first_lane = (int)((li0 - ci0) >> 1);         // lane holding the chain's particle 0
+    has_prev0 = ci0 > 0u;                         // slot 0 has a partner in lane-1
+    has_next1 = ci0 + 2u < N;                     // slot 1 has a partner in lane+1
+    w0 = static_cast<const WT*>(ci0 < N_A ? wA : wB);
+    w1 = static_cast<const WT*>(ci0 + 1u < N_A ? wA : wB);
+    v0 = ci0 < N_A ? 1u : 0x10000u;
+    v1 = ci0 + 1u < N_A ? 1u : 0x10000u;
+  }
+};
+
+// Moves the pair (x0,y0,z0), (x1,y1,z1) held by this lane (particles base and
+// base+1), stores the result and counts the final cells into nacc.  g gives
+// the cell fold, keys the Philox round keys.  Returns this lane's accepted
+// moves.
+template <typename WT, typename IDX>
+__device__ __forceinline__ unsigned pair_tile(const Geom& g, const Geom& keys, const PairLane<WT>& L,
+                                              float* __restrict__ px, float* __restrict__ py,
+                                              float* __restrict__ pz, uint32_t* __restrict__ nacc,
+                                              IDX base, bool valid, uint32_t sweep, uint32_t ctr3,
+                                              bool set_order_random, float a, float K1, float x0,
+                                              float x1, float y0, float y1, float z0, float z1) {
+  const float K2 = 2.f * K1;
+  const uint32_t hi = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)base >> 32) : 0u;
+  const uint4 r0 = philox_rk(make_uint4((uint32_t)base, hi, sweep, ctr3), keys);
+  const IDX m1 = base + 1u;
+  const uint32_t hi1 = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)m1 >> 32) : 0u;
+  const uint4 r1 = philox_rk(make_uint4((uint32_t)m1, hi1, sweep, ctr3), keys);
+  const float xn0 = __fadd_rn(x0, __fmul_rn(a, uniform_sym(r0.x)));
+  const float yn0 = __fadd_rn(y0, __fmul_rn(a, uniform_sym(r0.y)));
+  const float zn0 = __fadd_rn(z0, __fmul_rn(a, uniform_sym(r0.z)));
+  const float xn1 = __fadd_rn(x1, __fmul_rn(a, uniform_sym(r1.x)));
+  const float yn1 = __fadd_rn(y1, __fmul_rn(a, uniform_sym(r1.y)));
+  const float zn1 = __fadd_rn(z1, __fmul_rn(a, uniform_sym(r1.z)));
+  const uint32_t c0 = cell_of(g, x0, y0, z0);
+  const uint32_t c1 = cell_of(g, x1, y1, z1);
+  const uint32_t cn0 = cell_of(g, xn0, yn0, zn0);
+  const uint32_t cn1 = cell_of(g, xn1, yn1, zn1);
+  float dEf0 = 0.f, dEf1 = 0.f;
+  if (valid) {
+    dEf0 = load_w<WT>(L.w0, cn0) - load_w<WT>(L.w0, c0);
+    dEf1 = load_w<WT>(L.w1, cn1) - load_w<WT>(L.w1, c1);
+  }
+  const float lnu0 = log_uniform_open(r0.w);
+  const float lnu1 = log_uniform_open(r1.w);
+  const bool sw = set_order_random && (__shfl_sync(FULL, r0.w, L.first_lane) & 1u);
+  const int lane = L.lane;
+
+  // A moves first, B second.
+  float Ax = sw ? x1 : x0, Ay = sw ? y1 : y0, Az = sw ? z1 : z0;
+  float Bx = sw ? x0 : x1, By = sw ? y0 : y1, Bz = sw ? z0 : z1;
+  const float tAx = sw ? xn1 : xn0, tAy = sw ? yn1 : yn0, tAz = sw ? zn1 : zn0;
+  const float tBx = sw ? xn0 : xn1, tBy = sw ? yn0 : yn1, tBz = sw ? zn0 : zn1;
+  uint32_t cA = sw ? c1 : c0, cB = sw ? c0 : c1;
+  const uint32_t cnA = sw ? cn1 : cn0, cnB = sw ? cn0 : cn1;
+  const float fA = sw ? dEf1 : dEf0, fB = sw ? dEf0 : dEf1;
+  const float lA = sw ? lnu1 : lnu0, lB = sw ? lnu0 : lnu1;
+  unsigned acc_count = 0;
+
+  {  // first set: A moves against B and the adjacent lane's B
+    const int src = sw ? lane + 1 : lane - 1;
+    const bool cross = sw ? L.has_next1 : L.has_prev0;
+    const float sx = __shfl_sync(FULL, Bx, src & 31);
+    const float sy = __shfl_sync(FULL, By, src & 31);
+    const float sz = __shfl_sync(FULL, Bz, src & 31);
+    const float ex = cross ? sx : Ax, ey = cross ? sy : Ay, ez = cross ? sz : Az;
+    const float dx = tAx - Ax, dy = tAy - Ay, dz = tAz - Az;
+    const float ux = (Ax - Bx) + (Ax - ex), uy = (Ay - By) + (Ay - ey), uz = (Az - Bz) + (Az - ez);
+    const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+    const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float dE = fmaf(cross ? K2 : K1, dd, fmaf(K2, du, fA));
+    const bool acc = valid && (dE <= 0.f || lA < -dE);
+    Ax = acc ? tAx : Ax;
+    Ay = acc ? tAy : Ay;
+    Az = acc ? tAz : Az;
+    cA = acc ? cnA : cA;
+    acc_count += acc;
+  }
+  {  // second set: B moves against A and the adjacent lane's A
+    const int src = sw ? lane - 1 : lane + 1;
+    const bool cross = sw ? L.has_prev0 : L.has_next1;
+    const float sx = __shfl_sync(FULL, Ax, src & 31);
+    const float sy = __shfl_sync(FULL, Ay, src & 31);
+    const float sz = __shfl_sync(FULL, Az, src & 31);
+    const float ex = cross ? sx : Bx, ey = cross ? sy : By, ez = cross ? sz : Bz;
+    const float dx = tBx - Bx, dy = tBy - By, dz = tBz - Bz;
+    const float ux = (Bx - Ax) + (Bx - ex), uy = (By - Ay) + (By - ey), uz = (Bz - Az) + (Bz - ez);
+    const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+    const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float dE = fmaf(cross ? K2 : K1, dd, fmaf(K2, du, fB));
+    const bool acc = valid && (dE <= 0.f || lB < -dE);
+    Bx = acc ? tBx : Bx;
+    By = acc ? tBy : By;
+    Bz = acc ? tBz : Bz;
+    cB = acc ? cnB : cB;
+    acc_count += acc;
+  }
+
+  if (valid) {
+    __stcs(reinterpret_cast<float2*>(px + base), sw ? make_float2(Bx, Ax) : make_float2(Ax, Bx));
+    __stcs(reinterpret_cast<float2*>(py + base), sw ? make_float2(By, Ay) : make_float2(Ay, By));
+    __stcs(reinterpret_cast<float2*>(pz + base), sw ? make_float2(Bz, Az) : make_float2(Az, Bz));
+    if (cA == cB) {
+      atomicAdd(nacc + cA, L.v0 + L.v1);
+    } else {
+      atomicAdd(nacc + cA, sw ? L.v1 : L.v0);
+      atomicAdd(nacc + cB, sw ? L.v0 : L.v1);
+    }
+  }
+  return acc_count;
+}
+
+}  // namespace soma

@@ -22,6 +22,7 @@
 // Streams: positions are loaded and stored with evict-first hints so the
 // 28 MB grid and the omega planes stay in L2.
 #include "kernels.h"
+#include "pair_body.cuh"
 
 namespace soma {
 
@@ -210,25 +211,14 @@ __global__ void __launch_bounds__(256) sweep_uniform_kernel(const SweepArgs p) {
   if (lane == 0 && my_acc) atomicAdd(p.acc, (unsigned long long)my_acc);
 }
 
-// Even N, at most 64 particles per chain: lane l of a tile holds particles
-// 2l (even chain position, slot 0) and 2l+1 (odd, slot 1) of the SAME chain.
-// Each SET phase moves exactly one of the two, so every lane does one move per
-// phase with no predicated duplicate work.  After the draws the pair is
-// re-labelled once per tile into A (moves in the first phase) and B (moves in
-// the second) with the chain's set-order bit, so the phases need no selects:
-//   phase 1 moves A; its bond partners are B (same lane) and the adjacent
-//     lane's B (lane-1 if A is the even particle, lane+1 if it is odd);
-//   phase 2 moves B; its partners are A (same lane, already updated) and the
-//     adjacent lane's A (lane+1 if B is odd, lane-1 if it is even).
-// Bond energy change of a move r -> r + d with k partners n:
-//   sum_n |r+d-n|^2 - |r-n|^2 = 2 d.U + k d.d,  U = sum_n (r - n),
-// where every difference r - n is exact for bonded neighbours.
-// IDX is the index type: 32-bit when M < 2^32 (Philox counter word 1 = 0).
+// Even N <= 64: the paired tile body of pair_body.cuh over one system.  Each
+// block owns a contiguous range of tiles (spatially ordered chains), walked by
+// its warps in step, so field values repeat in L1; the next tile's positions
+// are loaded while the current one is processed.  IDX is the index type:
+// 32-bit when M < 2^32 (Philox counter word 1 = 0).
 template <typename WT, typename IDX>
 __global__ void __launch_bounds__(256, 3) sweep_pair_kernel(const SweepArgs p) {
   const int lane = threadIdx.x & 31;
-  // Each block owns a contiguous range of tiles (spatially ordered chains),
-  // walked by its warps in step; field values then repeat in L1.
   const uint32_t n_tiles_all = (uint32_t)p.n_tiles;
   const uint32_t chunk = (n_tiles_all + gridDim.x - 1) / gridDim.x;
   const uint32_t t_begin = blockIdx.x * chunk;
@@ -238,130 +228,35 @@ __global__ void __launch_bounds__(256, 3) sweep_pair_kernel(const SweepArgs p) {
   const unsigned long long s64 = *p.d_sweep;
   const uint32_t sweep = (uint32_t)s64;
   uint32_t* __restrict__ nacc = ((s64 + 1ull) & 1ull) ? p.n1 : p.n0;
-  const uint32_t N = p.g.N;
   const uint32_t ctr3 = (PURPOSE_MOVE << 24) | (p.g.replica & 0xFFFFFFu);
-  const uint32_t li0 = 2u * (uint32_t)lane;
-  const uint32_t ci0 = li0 % N;                    // chain position of slot 0 (even)
-  const int first_lane = (int)((li0 - ci0) >> 1);  // lane holding the chain's particle 0
-  const bool has_prev0 = ci0 > 0u;                 // slot 0 has a partner in lane-1
-  const bool has_next1 = ci0 + 2u < N;             // slot 1 has a partner in lane+1
-  const WT* __restrict__ w0 = static_cast<const WT*>(ci0 < p.g.N_A ? p.wA : p.wB);
-  const WT* __restrict__ w1 = static_cast<const WT*>(ci0 + 1u < p.g.N_A ? p.wA : p.wB);
-  const uint32_t v0 = ci0 < p.g.N_A ? 1u : 0x10000u;
-  const uint32_t v1 = ci0 + 1u < p.g.N_A ? 1u : 0x10000u;
-  const float a = p.a, K1 = p.K_b, K2 = 2.f * p.K_b;
-  const uint32_t TN = p.G * N;
-  const uint32_t n_tiles = t_end;
+  PairLane<WT> L;
+  L.init(lane, p.g.N, p.g.N_A, p.wA, p.wB);
+  const uint32_t TN = p.G * p.g.N;
   const uint32_t full_tiles = (uint32_t)p.full_tiles;
-  auto lane_ok = [&](uint32_t t) { return t < full_tiles || li0 < p.last_rows; };
+  auto lane_ok = [&](uint32_t t) { return t < full_tiles || L.li0 < p.last_rows; };
 
   float2 px = make_float2(0.f, 0.f), py = px, pz = px;
-  if (warp0 < n_tiles && lane_ok(warp0)) {
-    const IDX b0 = (IDX)warp0 * TN + li0;
+  if (warp0 < t_end && lane_ok(warp0)) {
+    const IDX b0 = (IDX)warp0 * TN + L.li0;
     px = __ldcs(reinterpret_cast<const float2*>(p.x + b0));
     py = __ldcs(reinterpret_cast<const float2*>(p.y + b0));
     pz = __ldcs(reinterpret_cast<const float2*>(p.z + b0));
   }
-
   unsigned my_acc = 0;
-  for (uint32_t tile = warp0; tile < n_tiles; tile += nwarps) {
+  for (uint32_t tile = warp0; tile < t_end; tile += nwarps) {
     const bool valid = lane_ok(tile);
-    const IDX base = (IDX)tile * TN + li0;
+    const IDX base = (IDX)tile * TN + L.li0;
     const float x0 = px.x, x1 = px.y, y0 = py.x, y1 = py.y, z0 = pz.x, z1 = pz.y;
     const uint32_t nt = tile + nwarps;
-    if (nt < n_tiles && lane_ok(nt)) {
-      const IDX bn = (IDX)nt * TN + li0;
+    if (nt < t_end && lane_ok(nt)) {
+      const IDX bn = (IDX)nt * TN + L.li0;
       px = __ldcs(reinterpret_cast<const float2*>(p.x + bn));
       py = __ldcs(reinterpret_cast<const float2*>(p.y + bn));
       pz = __ldcs(reinterpret_cast<const float2*>(p.z + bn));
     }
-
-    const uint32_t hi = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)base >> 32) : 0u;
-    const uint4 r0 = philox_rk(make_uint4((uint32_t)base, hi, sweep, ctr3), p.g);
-    const IDX m1 = base + 1u;
-    const uint32_t hi1 = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)m1 >> 32) : 0u;
-    const uint4 r1 = philox_rk(make_uint4((uint32_t)m1, hi1, sweep, ctr3), p.g);
-    const float xn0 = __fadd_rn(x0, __fmul_rn(a, uniform_sym(r0.x)));
-    const float yn0 = __fadd_rn(y0, __fmul_rn(a, uniform_sym(r0.y)));
-    const float zn0 = __fadd_rn(z0, __fmul_rn(a, uniform_sym(r0.z)));
-    const float xn1 = __fadd_rn(x1, __fmul_rn(a, uniform_sym(r1.x)));
-    const float yn1 = __fadd_rn(y1, __fmul_rn(a, uniform_sym(r1.y)));
-    const float zn1 = __fadd_rn(z1, __fmul_rn(a, uniform_sym(r1.z)));
-    const uint32_t c0 = cell_of(p.g, x0, y0, z0);
-    const uint32_t c1 = cell_of(p.g, x1, y1, z1);
-    const uint32_t cn0 = cell_of(p.g, xn0, yn0, zn0);
-    const uint32_t cn1 = cell_of(p.g, xn1, yn1, zn1);
-    float dEf0 = 0.f, dEf1 = 0.f;
-    if (valid) {
-      dEf0 = load_w<WT>(w0, cn0) - load_w<WT>(w0, c0);
-      dEf1 = load_w<WT>(w1, cn1) - load_w<WT>(w1, c1);
-    }
-    const float lnu0 = log_uniform_open(r0.w);
-    const float lnu1 = log_uniform_open(r1.w);
-    const bool sw = p.set_order_random && (__shfl_sync(FULL, r0.w, first_lane) & 1u);
-
-    // A moves first, B second.
-    float Ax = sw ? x1 : x0, Ay = sw ? y1 : y0, Az = sw ? z1 : z0;
-    float Bx = sw ? x0 : x1, By = sw ? y0 : y1, Bz = sw ? z0 : z1;
-    const float tAx = sw ? xn1 : xn0, tAy = sw ? yn1 : yn0, tAz = sw ? zn1 : zn0;
-    const float tBx = sw ? xn0 : xn1, tBy = sw ? yn0 : yn1, tBz = sw ? zn0 : zn1;
-    uint32_t cA = sw ? c1 : c0, cB = sw ? c0 : c1;
-    const uint32_t cnA = sw ? cn1 : cn0, cnB = sw ? cn0 : cn1;
-    const float fA = sw ? dEf1 : dEf0, fB = sw ? dEf0 : dEf1;
-    const float lA = sw ? lnu1 : lnu0, lB = sw ? lnu0 : lnu1;
-
-    {  // first set: A moves against B and the adjacent lane's B
-      const int src = sw ? lane + 1 : lane - 1;
-      const bool cross = sw ? has_next1 : has_prev0;
-      const float sx = __shfl_sync(FULL, Bx, src & 31);
-      const float sy = __shfl_sync(FULL, By, src & 31);
-      const float sz = __shfl_sync(FULL, Bz, src & 31);
-      const float ex = cross ? sx : Ax, ey = cross ? sy : Ay, ez = cross ? sz : Az;
-      const float dx = tAx - Ax, dy = tAy - Ay, dz = tAz - Az;
-      const float ux = (Ax - Bx) + (Ax - ex), uy = (Ay - By) + (Ay - ey), uz = (Az - Bz) + (Az - ez);
-      const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
-      const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      const float dE = fmaf(cross ? K2 : K1, dd, fmaf(K2, du, fA));
-      const bool acc = valid && (dE <= 0.f || lA < -dE);
-      Ax = acc ? tAx : Ax;
-      Ay = acc ? tAy : Ay;
-      Az = acc ? tAz : Az;
-      cA = acc ? cnA : cA;
-      my_acc += acc;
-    }
-    {  // second set: B moves against A and the adjacent lane's A
-      const int src = sw ? lane - 1 : lane + 1;
-      const bool cross = sw ? has_prev0 : has_next1;
-      const float sx = __shfl_sync(FULL, Ax, src & 31);
-      const float sy = __shfl_sync(FULL, Ay, src & 31);
-      const float sz = __shfl_sync(FULL, Az, src & 31);
-      const float ex = cross ? sx : Bx, ey = cross ? sy : By, ez = cross ? sz : Bz;
-      const float dx = tBx - Bx, dy = tBy - By, dz = tBz - Bz;
-      const float ux = (Bx - Ax) + (Bx - ex), uy = (By - Ay) + (By - ey), uz = (Bz - Az) + (Bz - ez);
-      const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
-      const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      const float dE = fmaf(cross ? K2 : K1, dd, fmaf(K2, du, fB));
-      const bool acc = valid && (dE <= 0.f || lB < -dE);
-      Bx = acc ? tBx : Bx;
-      By = acc ? tBy : By;
-      Bz = acc ? tBz : Bz;
-      cB = acc ? cnB : cB;
-      my_acc += acc;
-    }
-
-    if (valid) {
-      __stcs(reinterpret_cast<float2*>(p.x + base), sw ? make_float2(Bx, Ax) : make_float2(Ax, Bx));
-      __stcs(reinterpret_cast<float2*>(p.y + base), sw ? make_float2(By, Ay) : make_float2(Ay, By));
-      __stcs(reinterpret_cast<float2*>(p.z + base), sw ? make_float2(Bz, Az) : make_float2(Az, Bz));
-      if (cA == cB) {
-        atomicAdd(nacc + cA, v0 + v1);
-      } else {
-        atomicAdd(nacc + cA, sw ? v1 : v0);
-        atomicAdd(nacc + cB, sw ? v0 : v1);
-      }
-    }
+    my_acc += pair_tile<WT, IDX>(p.g, p.g, L, p.x, p.y, p.z, nacc, base, valid, sweep, ctr3,
+                                 p.set_order_random, p.a, p.K_b, x0, x1, y0, y1, z0, z1);
   }
-
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) my_acc += __shfl_xor_sync(FULL, my_acc, o);
   if (lane == 0 && my_acc) atomicAdd(p.acc, (unsigned long long)my_acc);

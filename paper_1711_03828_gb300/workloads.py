@@ -64,6 +64,26 @@ def melt_slow(seed=1, **kw):
     return SystemDesc(**d)
 
 
+def batch_replicas(n=64, seed=1, **kw):
+    """Independent diblock melts of uneven size for one batched launch: box
+    edge L uniform in {2,3,4,6,8} R_e0 (grid 6L, dL = R_e0/6), N in {16,32,64},
+    f in {0.3,0.5}, chiN uniform in [10,40], kappaN=50, rho_0 R_e0^3 = 4096
+    (n_chains = 4096 L^3 / N), one seed, replica id = index.  The choices are
+    drawn with a seeded numpy generator."""
+    rng = np.random.default_rng(seed + 7919)
+    out = []
+    for i in range(n):
+        L = int(rng.choice([2, 3, 4, 6, 8]))
+        N = int(rng.choice([16, 32, 64]))
+        f = float(rng.choice([0.3, 0.5]))
+        chiN = float(rng.uniform(10.0, 40.0))
+        d = dict(n_chains=4096 * L**3 // N, N=N, f=f, box_Re=(float(L),) * 3, grid=(6 * L,) * 3,
+                 chiN=chiN, kappaN=50.0, seed=seed, replica_id=i)
+        d.update(kw)
+        out.append(SystemDesc(**d))
+    return out
+
+
 def scaled(desc: SystemDesc, box_Re, rho_Re3=4096.0):
     """Same chains and interactions in another box at density rho_0 R_e0^3."""
     cells_per_Re = desc.grid[0] / desc.box_Re[0]

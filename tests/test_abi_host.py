@@ -94,3 +94,24 @@ def test_struct_layouts_match_header(soma_lib, tmp_path):
         assert int(got[cname]) == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, f"{cname}.{f}"
+
+
+@pytest.mark.parametrize("bad", ["seed", "odd_N", "long_N", "smc", "dtype", "empty"])
+def test_invalid_batch_is_rejected_without_gpu(soma_lib, bad):
+    descs = [_valid(), _valid()]
+    descs[1].replica_id = 1
+    if bad == "seed":
+        descs[1].seed = 99
+    elif bad == "odd_N":
+        descs[1].N = 7
+    elif bad == "long_N":
+        descs[1].N = 128
+    elif bad == "smc":
+        descs[1].move = 1
+    elif bad == "dtype":
+        descs[1].grid_dtype = 1
+    arr = (_abi.SomaSystemDesc * 2)(*[d.to_c() for d in descs])
+    h = ctypes.c_void_p()
+    n = 0 if bad == "empty" else 2
+    assert _abi.lib().soma_batch_create(arr, n, None, ctypes.byref(h)) == _abi.SOMA_EINVAL
+    assert h.value is None
