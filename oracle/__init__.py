@@ -38,6 +38,16 @@ u8p = ctypes.POINTER(ctypes.c_uint8)
 i32p = ctypes.POINTER(ctypes.c_int32)
 
 PURPOSE_INIT, PURPOSE_MOVE, PURPOSE_MOVE2, PURPOSE_CONFIG, PURPOSE_TRAIN = 0, 1, 2, 4, 5
+MLP_PARAMS = 1604
+
+
+def mlp_forward(W, x, L=None):
+    """Network outputs (mu_x, mu_y, mu_z, log-scale pre-activation) of features x."""
+    Wd = np.ascontiguousarray(W, dtype=np.float64)
+    xd = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(4)
+    (L or lib()).or_mlp_forward(_ptr(Wd, f64p), _ptr(xd, f64p), _ptr(out, f64p))
+    return out
 
 
 class OrSystem(ctypes.Structure):
@@ -57,6 +67,7 @@ class OrSystem(ctypes.Structure):
         ("replica", ctypes.c_uint32),
         ("set_order", ctypes.c_int),
         ("move", ctypes.c_int),
+        ("mlp", ctypes.c_void_p),
     ]
 
 
@@ -109,6 +120,13 @@ def load(path):
     L.or_observables.argtypes = [P, f32p, f32p, f32p, u32p, u32p, ctypes.POINTER(OrObs)]
     L.or_structure_factor.argtypes = [P, u32p, u32p, i32p, ctypes.c_size_t, f64p]
     L.or_num_threads.restype = ctypes.c_int
+    L.or_mlp_forward.argtypes = [f64p, f64p, f64p]
+    L.or_set_mlp.argtypes = [P, f64p]
+    L.or_learned_features.argtypes = [P, f32p, f32p, f32p, f64p, ctypes.c_uint64,
+                                      ctypes.c_uint32, f64p, f64p]
+    L.or_esjd_sample.argtypes = [P, f64p, f32p, f32p, f32p, f64p, f64p, ctypes.c_uint64,
+                                 ctypes.c_uint32, f64p, f64p, f64p]
+    L.or_esjd_sample.restype = ctypes.c_double
     L.or_chain_key.argtypes = [P, ctypes.c_float, ctypes.c_float, ctypes.c_float]
     L.or_chain_key.restype = ctypes.c_uint64
     L.or_sort_chains.argtypes = [P, f32p, f32p, f32p, ctypes.POINTER(ctypes.c_uint64)]
@@ -193,6 +211,32 @@ class System:
         self.L.or_init_chain_range(ctypes.byref(self.s), int(c0), int(c1),
                                   _ptr(pos.x, f32p), _ptr(pos.y, f32p), _ptr(pos.z, f32p))
         return pos
+
+    def set_mlp(self, W):
+        """Parameters of the learned proposal (move 2); kept alive here."""
+        self._mlp = np.ascontiguousarray(W, dtype=np.float64)
+        assert self._mlp.size == MLP_PARAMS
+        self.L.or_set_mlp(ctypes.byref(self.s), _ptr(self._mlp, f64p))
+
+    def learned_features(self, pos, w_t, chain, i, r):
+        f = np.zeros(12)
+        rr = np.ascontiguousarray(r, dtype=np.float64)
+        self.L.or_learned_features(ctypes.byref(self.s), _ptr(pos.x, f32p), _ptr(pos.y, f32p),
+                                   _ptr(pos.z, f32p), _ptr(w_t, f64p), int(chain), int(i),
+                                   _ptr(rr, f64p), _ptr(f, f64p))
+        return f
+
+    def esjd_sample(self, W, pos, wA, wB, chain, i, xi, want_grad=True):
+        """(J, dJ/dW or None, log alpha) of one training sample."""
+        Wd = np.ascontiguousarray(W, dtype=np.float64)
+        g = np.zeros(MLP_PARAMS) if want_grad else None
+        la = np.zeros(1)
+        xid = np.ascontiguousarray(xi, dtype=np.float64)
+        J = self.L.or_esjd_sample(ctypes.byref(self.s), _ptr(Wd, f64p), _ptr(pos.x, f32p),
+                                  _ptr(pos.y, f32p), _ptr(pos.z, f32p), _ptr(wA, f64p),
+                                  _ptr(wB, f64p), int(chain), int(i), _ptr(xid, f64p),
+                                  _ptr(g, f64p), _ptr(la, f64p))
+        return J, g, float(la[0])
 
     def chain_key(self, x0, y0, z0):
         return int(self.L.or_chain_key(ctypes.byref(self.s), float(x0), float(y0), float(z0)))

@@ -416,6 +416,284 @@ static void or_move_smc(const or_system* s, float* x, float* y, float* z,
   if (accepted) accepted[m] = (uint8_t)acc_move;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Learned proposal (move 2).                                                   */
+/* ------------------------------------------------------------------------- */
+enum { L_W1 = 0, L_B1 = 384, L_W2 = 416, L_B2 = 1440, L_W3 = 1472, L_B3 = 1600 };
+
+void or_set_mlp(or_system* s, const double* W) { s->mlp = W; }
+
+typedef struct {
+  double x[12], z1[32], h1[32], z2[32], h2[32], o[4];
+} or_mlp_cache;
+
+static void or_mlp_run(const double* W, const double x[12], or_mlp_cache* c) {
+  for (int k = 0; k < 12; ++k) c->x[k] = x[k];
+  for (int j = 0; j < 32; ++j) {
+    double a = W[L_B1 + j];
+    for (int k = 0; k < 12; ++k) a += W[L_W1 + 12 * j + k] * x[k];
+    c->z1[j] = a;
+    c->h1[j] = tanh(a);
+  }
+  for (int j = 0; j < 32; ++j) {
+    double a = W[L_B2 + j];
+    for (int k = 0; k < 32; ++k) a += W[L_W2 + 32 * j + k] * c->h1[k];
+    c->z2[j] = a;
+    c->h2[j] = tanh(a);
+  }
+  for (int j = 0; j < 4; ++j) {
+    double a = W[L_B3 + j];
+    for (int k = 0; k < 32; ++k) a += W[L_W3 + 32 * j + k] * c->h2[k];
+    c->o[j] = a;
+  }
+}
+
+void or_mlp_forward(const double* W, const double x[12], double out[4]) {
+  or_mlp_cache c;
+  or_mlp_run(W, x, &c);
+  for (int j = 0; j < 4; ++j) out[j] = c.o[j];
+}
+
+/* Back-propagation of output gradients go[4] through the cached run: adds
+ * the parameter gradients to gW (optional) and returns input gradients gx. */
+static void or_mlp_backward(const double* W, const or_mlp_cache* c, const double go[4],
+                            double* gW, double gx[12]) {
+  double gh2[32], gz2[32], gh1[32], gz1[32];
+  for (int k = 0; k < 32; ++k) {
+    double a = 0.0;
+    for (int j = 0; j < 4; ++j) a += W[L_W3 + 32 * j + k] * go[j];
+    gh2[k] = a;
+  }
+  for (int k = 0; k < 32; ++k) gz2[k] = gh2[k] * (1.0 - c->h2[k] * c->h2[k]);
+  for (int k = 0; k < 32; ++k) {
+    double a = 0.0;
+    for (int j = 0; j < 32; ++j) a += W[L_W2 + 32 * j + k] * gz2[j];
+    gh1[k] = a;
+  }
+  for (int k = 0; k < 32; ++k) gz1[k] = gh1[k] * (1.0 - c->h1[k] * c->h1[k]);
+  for (int k = 0; k < 12; ++k) {
+    double a = 0.0;
+    for (int j = 0; j < 32; ++j) a += W[L_W1 + 12 * j + k] * gz1[j];
+    gx[k] = a;
+  }
+  if (gW) {
+    for (int j = 0; j < 4; ++j) {
+      gW[L_B3 + j] += go[j];
+      for (int k = 0; k < 32; ++k) gW[L_W3 + 32 * j + k] += go[j] * c->h2[k];
+    }
+    for (int j = 0; j < 32; ++j) {
+      gW[L_B2 + j] += gz2[j];
+      for (int k = 0; k < 32; ++k) gW[L_W2 + 32 * j + k] += gz2[j] * c->h1[k];
+    }
+    for (int j = 0; j < 32; ++j) {
+      gW[L_B1 + j] += gz1[j];
+      for (int k = 0; k < 12; ++k) gW[L_W1 + 12 * j + k] += gz1[j] * c->x[k];
+    }
+  }
+}
+
+/* Per-axis gradient of omega_t at r: the face differences omega(c) -
+ * omega(c-e) and omega(c+e) - omega(c) interpolated linearly in the position
+ * t = r - floor(r) inside the cell.  dgrad (optional, 3) receives the
+ * derivative of each component with respect to its own coordinate. */
+static void or_field_gradient(const or_system* s, const double* w_t, const double r[3],
+                              double g[3], double dgrad[3]) {
+  uint64_t c = or_cell(s, r[0], r[1], r[2]);
+  for (int d = 0; d < 3; ++d) {
+    double t = r[d] - floor(r[d]);
+    double lo = w_t[c] - w_t[or_cell_shift(s, c, d, -1)];
+    double hi = w_t[or_cell_shift(s, c, d, +1)] - w_t[c];
+    g[d] = (1.0 - t) * lo + t * hi;
+    if (dgrad) dgrad[d] = hi - lo;
+  }
+}
+
+void or_learned_features(const or_system* s, const float* x, const float* y, const float* z,
+                         const double* w_t, uint64_t chain, uint32_t i, const double r[3],
+                         double feat[12]) {
+  for (int k = 0; k < 12; ++k) feat[k] = 0.0;
+  const uint64_t m0 = chain * s->N;
+  if (i > 0) {
+    uint64_t n = m0 + i - 1;
+    feat[0] = r[0] - x[n]; feat[1] = r[1] - y[n]; feat[2] = r[2] - z[n];
+  }
+  if (i + 1 < s->N) {
+    uint64_t n = m0 + i + 1;
+    feat[3] = x[n] - r[0]; feat[4] = y[n] - r[1]; feat[5] = z[n] - r[2];
+  }
+  or_field_gradient(s, w_t, r, feat + 6, NULL);
+  feat[9] = (i < s->N_A) ? 1.0 : 0.0;
+  feat[10] = (i > 0) ? 1.0 : 0.0;
+  feat[11] = (i + 1 < s->N) ? 1.0 : 0.0;
+}
+
+/* proposal parameters of the network outputs */
+static double or_sigma0(const or_system* s) { return s->a / sqrt(3.0); }
+static double or_logsig(const double o3) { return 2.0 * tanh(0.5 * o3); }
+
+/* log q(to | from) up to a constant, for network outputs o at `from` */
+static double or_log_q(const or_system* s, const double o[4], const double from[3],
+                       const double to[3]) {
+  double sig = or_sigma0(s) * exp(or_logsig(o[3]));
+  double r2 = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    double e = to[d] - from[d] - o[d];
+    r2 += e * e;
+  }
+  return -r2 / (2.0 * sig * sig) - 3.0 * log(sig);
+}
+
+static double or_bond_energy(const or_system* s, const float* x, const float* y, const float* z,
+                             uint64_t chain, uint32_t i, const double r[3]) {
+  double e = 0.0;
+  for (int side = -1; side <= 1; side += 2) {
+    long long jn = (long long)i + side;
+    if (jn < 0 || jn >= (long long)s->N) continue;
+    uint64_t n = chain * s->N + (uint64_t)jn;
+    double rn[3] = { x[n], y[n], z[n] };
+    for (int d = 0; d < 3; ++d) e += s->K_b * (r[d] - rn[d]) * (r[d] - rn[d]);
+  }
+  return e;
+}
+
+static void or_move_learned(const or_system* s, float* x, float* y, float* z,
+                            const double* wA, const double* wB, uint32_t sweep,
+                            uint64_t chain, uint32_t i, double* margin, uint8_t* accepted,
+                            float* trial, uint64_t* acc, uint64_t* ties) {
+  const uint64_t m = chain * s->N + i;
+  const double* w_t = (i < s->N_A) ? wA : wB;
+  uint32_t w1[4], w2[4];
+  or_draw(s, OR_PURPOSE_MOVE, m, sweep, w1);
+  or_draw(s, OR_PURPOSE_MOVE2, m, sweep, w2);
+  double xi[4];
+  for (int p = 0; p < 2; ++p) {
+    double u1 = or_uniform_open(w1[2 * p]), u2 = or_uniform_open(w1[2 * p + 1]);
+    double rad = sqrt(-2.0 * log(u1)), th = 2.0 * M_PI * u2;
+    xi[2 * p] = rad * cos(th);
+    xi[2 * p + 1] = rad * sin(th);
+  }
+  double r_old[3] = { x[m], y[m], z[m] }, r_new[3], f[12], o[4], o_rev[4];
+  or_learned_features(s, x, y, z, w_t, chain, i, r_old, f);
+  or_mlp_forward(s->mlp, f, o);
+  const double sig = or_sigma0(s) * exp(or_logsig(o[3]));
+  for (int d = 0; d < 3; ++d) {
+    float dx = (float)(o[d] + sig * xi[d]);
+    r_new[d] = (double)(float)(r_old[d] + (double)dx);
+  }
+  if (trial) {
+    const uint64_t M = s->n_chains * s->N;
+    for (int d = 0; d < 3; ++d) trial[d * M + m] = (float)r_new[d];
+  }
+  or_learned_features(s, x, y, z, w_t, chain, i, r_new, f);
+  or_mlp_forward(s->mlp, f, o_rev);
+  double dE = or_bond_energy(s, x, y, z, chain, i, r_new) - or_bond_energy(s, x, y, z, chain, i, r_old)
+              + (w_t[or_cell(s, r_new[0], r_new[1], r_new[2])] - w_t[or_cell(s, r_old[0], r_old[1], r_old[2])]);
+  const double log_alpha = -dE + or_log_q(s, o_rev, r_new, r_old) - or_log_q(s, o, r_old, r_new);
+  const double lnu = log(or_uniform_open(w2[0]));
+  const int acc_move = (log_alpha >= 0.0) || (lnu < log_alpha);
+  if (margin) margin[m] = lnu - log_alpha;
+  if (fabs(lnu - log_alpha) < 1e-4) (*ties)++;
+  if (acc_move) {
+    x[m] = (float)r_new[0]; y[m] = (float)r_new[1]; z[m] = (float)r_new[2];
+    (*acc)++;
+  }
+  if (accepted) accepted[m] = (uint8_t)acc_move;
+}
+
+/* Expected squared jump of one sample with its reparameterised gradient:
+ * r' = r + mu(x) + sigma(x) xi,  D = |r'-r|^2,
+ * l = -dE(r') + log q(r|r') - log q(r'|r),  J = min(1, e^l) D.
+ * The field term of dE is piecewise constant in r' (zero derivative); the
+ * features at r' depend on r' through the bond vectors and the interpolated
+ * field gradient.  Positions are not rounded to FP32 here (a smooth surrogate
+ * of the move used for training). */
+double or_esjd_sample(const or_system* s, const double* W, const float* x, const float* y,
+                      const float* z, const double* wA, const double* wB, uint64_t chain,
+                      uint32_t i, const double xi[3], double* grad, double* log_alpha_out) {
+  const uint64_t m = chain * s->N + i;
+  const double* w_t = (i < s->N_A) ? wA : wB;
+  const double r[3] = { x[m], y[m], z[m] };
+  double f[12], fr[12];
+  or_mlp_cache cf, cr;
+  or_learned_features(s, x, y, z, w_t, chain, i, r, f);
+  or_mlp_run(W, f, &cf);
+  const double ls = or_logsig(cf.o[3]);
+  const double sig = or_sigma0(s) * exp(ls);
+  double rp[3], dvec[3];
+  for (int d = 0; d < 3; ++d) {
+    dvec[d] = cf.o[d] + sig * xi[d];
+    rp[d] = r[d] + dvec[d];
+  }
+  or_learned_features(s, x, y, z, w_t, chain, i, rp, fr);
+  or_mlp_run(W, fr, &cr);
+  const double lsr = or_logsig(cr.o[3]);
+  const double sigr = or_sigma0(s) * exp(lsr);
+  double e[3], e2 = 0.0, D = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    e[d] = r[d] - rp[d] - cr.o[d];  /* reverse residual */
+    e2 += e[d] * e[d];
+    D += dvec[d] * dvec[d];
+  }
+  double xi2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+  double dE = or_bond_energy(s, x, y, z, chain, i, rp) - or_bond_energy(s, x, y, z, chain, i, r)
+              + (w_t[or_cell(s, rp[0], rp[1], rp[2])] - w_t[or_cell(s, r[0], r[1], r[2])]);
+  double lq_rev = -e2 / (2.0 * sigr * sigr) - 3.0 * log(sigr);
+  double lq_fwd = -0.5 * xi2 - 3.0 * log(sig);
+  double l = -dE + lq_rev - lq_fwd;
+  if (log_alpha_out) *log_alpha_out = l;
+  double alpha = l >= 0.0 ? 1.0 : exp(l);
+  double J = alpha * D;
+  if (!grad) return J;
+  /* dJ = alpha dD + [l < 0] alpha D dl */
+  const double cl = (l < 0.0) ? alpha * D : 0.0;
+  /* gradient with respect to r' (through D, -dE, lq_rev's residual and features) */
+  double g_rp[3];
+  for (int d = 0; d < 3; ++d) g_rp[d] = alpha * 2.0 * dvec[d];
+  /* -dE: bond part */
+  for (int side = -1; side <= 1; side += 2) {
+    long long jn = (long long)i + side;
+    if (jn < 0 || jn >= (long long)s->N) continue;
+    uint64_t n = chain * s->N + (uint64_t)jn;
+    double rn[3] = { x[n], y[n], z[n] };
+    for (int d = 0; d < 3; ++d) g_rp[d] += cl * (-2.0 * s->K_b * (rp[d] - rn[d]));
+  }
+  /* lq_rev: explicit residual e = r - r' - mu_r(r'): de/dr' = -I */
+  for (int d = 0; d < 3; ++d) g_rp[d] += cl * (e[d] / (sigr * sigr));
+  /* lq_rev through the reverse network outputs */
+  double go_r[4];
+  for (int d = 0; d < 3; ++d) go_r[d] = cl * (e[d] / (sigr * sigr));  /* d lq/d mu_r */
+  {
+    /* d lq_rev/d ls_r = e2/sigr^2 - 3 ; d ls/d o3 = 1 - tanh^2(o3/2) */
+    double th = tanh(0.5 * cr.o[3]);
+    go_r[3] = cl * (e2 / (sigr * sigr) - 3.0) * (1.0 - th * th);
+  }
+  double gfr[12];
+  or_mlp_backward(W, &cr, go_r, grad, gfr);
+  /* features at r' -> r': bond vectors (+I for prev, -I for next) and the
+   * interpolated field gradient (d g_d / d r'_d = hi - lo) */
+  double dg[3], gtmp[3];
+  or_field_gradient(s, w_t, rp, gtmp, dg);
+  for (int d = 0; d < 3; ++d) {
+    if (i > 0) g_rp[d] += gfr[d];
+    if (i + 1 < s->N) g_rp[d] -= gfr[3 + d];
+    g_rp[d] += gfr[6 + d] * dg[d];
+  }
+  /* r' = r + mu(x) + sigma(x) xi: to the forward network outputs, plus the
+   * -lq_fwd = +3 ls term */
+  double go_f[4];
+  for (int d = 0; d < 3; ++d) go_f[d] = g_rp[d];
+  {
+    double th = tanh(0.5 * cf.o[3]);
+    double dls = 0.0;
+    for (int d = 0; d < 3; ++d) dls += g_rp[d] * sig * xi[d];
+    dls += cl * 3.0;
+    go_f[3] = dls * (1.0 - th * th);
+  }
+  double gf[12];
+  or_mlp_backward(W, &cf, go_f, grad, gf);
+  return J;
+}
+
 /* Set order of one chain for one sweep: bit 0 of the fourth word of the move
  * draw of the chain's first particle picks odd->even (1) or even->odd (0); the
  * 24 bits that make the acceptance uniform are the word's top bits, so the set
@@ -451,6 +729,8 @@ void or_sweep_trial(const or_system* s, float* x, float* y, float* z,
         uint64_t a1 = 0, t1 = 0;
         if (s->move == 1)
           or_move_smc(s, x, y, z, wA, wB, sweep, chain, i, margin, accepted, trial, &a1, &t1);
+        else if (s->move == 2)
+          or_move_learned(s, x, y, z, wA, wB, sweep, chain, i, margin, accepted, trial, &a1, &t1);
         else
           or_move_uniform(s, x, y, z, wA, wB, sweep, chain, i, margin, accepted, trial, &a1, &t1);
         acc += a1;

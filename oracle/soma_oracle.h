@@ -48,7 +48,8 @@ typedef struct {
   uint64_t seed;
   uint32_t replica;
   int      set_order;  /* 0: random per (chain, sweep); 1: fixed even->odd */
-  int      move;       /* 0 uniform (Metropolis), 1 smart MC (force biased) */
+  int      move;       /* 0 uniform (Metropolis), 1 smart MC (force biased), 2 learned */
+  const double* mlp;   /* learned proposal parameters (move 2), OR_MLP_PARAMS doubles */
 } or_system;
 
 typedef struct {
@@ -112,6 +113,33 @@ void or_sweep_trial(const or_system* s, float* x, float* y, float* z,
                     const double* wA, const double* wB, uint32_t sweep,
                     uint64_t c0, uint64_t c1,
                     double* margin, uint8_t* accepted, float* trial, or_sweep_stats* st);
+
+/* --- a7/a8: learned Metropolis-Hastings proposal ----------------------------
+ * A multilayer perceptron 12 -> 32 -> 32 -> 4 (tanh hidden units) maps the
+ * features of a particle to a drift mu (3) and a log step scale; the trial
+ * move is r' = r + mu + sigma xi with sigma = sigma0 exp(2 tanh(o3/2)),
+ * sigma0 = a/sqrt(3), xi standard normal (Box-Muller of the move draw, as for
+ * the smart Monte Carlo move), accepted with min(1, exp(-dE) q(r|r')/q(r'|r))
+ * where the reverse density evaluates the network at r'.  Features: the bond
+ * vectors r - r_{i-1} and r_{i+1} - r (zero without that partner), the
+ * gradient of omega_t at r (per axis, the face differences of the cell and its
+ * neighbour interpolated linearly in the position inside the cell), is_A,
+ * has_prev, has_next.  Parameters (1604, flat): W1[32][12], b1[32],
+ * W2[32][32], b2[32], W3[4][32], b3[4].  There is no counterpart in the paper
+ * (SMC is its force-biased proposal, Sec. 2.2); parity of the gradient is
+ * pinned by finite differences, exactness of the move by brute force. */
+#define OR_MLP_PARAMS 1604
+void or_mlp_forward(const double* W, const double x[12], double out[4]);
+void or_learned_features(const or_system* s, const float* x, const float* y, const float* z,
+                         const double* w_t, uint64_t chain, uint32_t i, const double r[3],
+                         double feat[12]);
+void or_set_mlp(or_system* s, const double* W);
+/* Expected-squared-jump objective of one sample (chain, i) with normals xi:
+ * J = alpha |r'-r|^2, alpha = min(1, exp(log_alpha)); returns J and adds dJ/dW
+ * to grad (1604, optional).  Fields frozen, neighbours at their positions. */
+double or_esjd_sample(const or_system* s, const double* W, const float* x, const float* y,
+                      const float* z, const double* wA, const double* wB, uint64_t chain,
+                      uint32_t i, const double xi[3], double* grad, double* log_alpha);
 
 /* One full SCMF cycle: sweep all chains, then histogram, then fields. */
 void or_cycle(const or_system* s, float* x, float* y, float* z,

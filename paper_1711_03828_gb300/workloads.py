@@ -119,3 +119,18 @@ def random_fields(cells: int, seed: int, scale: float = 1.0):
     [-scale, scale), FP64."""
     rng = np.random.default_rng(seed)
     return rng.uniform(-scale, scale, cells), rng.uniform(-scale, scale, cells)
+
+
+def random_mlp(seed, scale=0.3):
+    """Seeded parameters of the learned proposal's network (1604 values,
+    layout W1[32][12], b1[32], W2[32][32], b2[32], W3[4][32], b3[4]), uniform
+    in [-scale, scale) per fan-in; rounded to BF16-representable values so
+    the GPU's BF16 weights hold them exactly."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for rows, cols in ((32, 12), (32, 1), (32, 32), (32, 1), (4, 32), (4, 1)):
+        fan = 12 if rows == 32 and cols == 12 else (32 if cols == 32 else 1)
+        parts.append(rng.uniform(-scale, scale, rows * cols) / np.sqrt(max(fan, 1) / 4.0))
+    w = np.concatenate(parts).astype(np.float32)
+    bits = w.view(np.uint32) & np.uint32(0xFFFF0000)  # truncate to a BF16 value
+    return bits.view(np.float32).astype(np.float64)

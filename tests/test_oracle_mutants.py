@@ -64,6 +64,15 @@ MUTANTS = [
      PIN.check_smc_force_direction),
     ("smc_bond_force_sign", "F[d] -= 2.0 * s->K_b * (r[d] - rn[d]);", "F[d] += 2.0 * s->K_b * (r[d] - rn[d]);",
      PIN.check_smc_force_direction),
+    ("learned_reverse_density_dropped",
+     "const double log_alpha = -dE + or_log_q(s, o_rev, r_new, r_old) - or_log_q(s, o, r_old, r_new);",
+     "const double log_alpha = -dE;",
+     lambda L: PIN.check_two_particle_balance_brute_force(0, L, move=2)),
+    ("esjd_gradient_bond_sign", "g_rp[d] += cl * (-2.0 * s->K_b * (rp[d] - rn[d]));",
+     "g_rp[d] += cl * (2.0 * s->K_b * (rp[d] - rn[d]));",
+     PIN.check_esjd_gradient_matches_finite_differences),
+    ("esjd_gradient_logscale_term", "dls += cl * 3.0;", "dls += cl * 2.0;",
+     PIN.check_esjd_gradient_matches_finite_differences),
     ("sort_key_axis", "for (int d = 0; d < 3; ++d) key |= ((b[d] >> bit) & 1u) << (3 * bit + d);",
      "for (int d = 0; d < 3; ++d) key |= ((b[2 - d] >> bit) & 1u) << (3 * bit + d);",
      PIN.check_sort_chains_is_a_spatial_permutation),

@@ -165,6 +165,8 @@ def check_ideal_chain_relaxes_to_gaussian_statistics(lib=None, move=0):
     d = workloads.melt_small(n_chains=1024, N=8, chiN=0.0, kappaN=0.0, box_Re=(2.0, 2.0, 1.0),
                              grid=(12, 12, 6), move=move)
     s = oracle_system(d, lib)
+    if move == 2:
+        s.set_mlp(workloads.random_mlp(7, scale=0.1))
     Re = 6.0
     sigma = Re / math.sqrt(3 * (d.N - 1))
     pos0 = workloads.random_walk_positions(d, seed=11, bond_sigma=1.6 * sigma)
@@ -190,7 +192,8 @@ def check_ideal_chain_relaxes_to_gaussian_statistics(lib=None, move=0):
     assert abs(b2.mean() - Re**2 / (d.N - 1)) < 5 * se_b2, (b2.mean(), Re**2 / (d.N - 1), se_b2)
     assert abs(re2.mean() - Re**2) < 5 * se_re2, (re2.mean(), Re**2, se_re2)
     # force-biased proposals of a harmonic chain are accepted far more often
-    assert (0.2 < acc / att < 0.95) if move == 0 else (0.5 < acc / att < 0.999)
+    lo_hi = {0: (0.2, 0.95), 1: (0.5, 0.999), 2: (0.02, 0.999)}[move]
+    assert lo_hi[0] < acc / att < lo_hi[1]
 
 
 # --------------------------------------------------------------------------
@@ -238,6 +241,8 @@ def check_two_particle_balance_brute_force(set_order, lib=None, move=0):
     d = SystemDesc(n_chains=4096, N=2, f=0.5, box_Re=(L / Re,) * 3, grid=(L,) * 3,
                    chiN=0.0, kappaN=0.0, set_order=set_order, seed=17, move=move)
     s = oracle_system(d, lib)
+    if move == 2:
+        s.set_mlp(workloads.random_mlp(7, scale=0.1))
     K = s.params.K_b
     assert K == pytest.approx(3.0 / (2 * Re * Re))
     wA, wB = workloads.random_fields(L**3, seed=5, scale=1.0)
@@ -348,13 +353,13 @@ def test_field_rounding_modes(oracle_lib):
     check_field_rounding_modes()
 
 
-@pytest.mark.parametrize("move", [0, 1])
+@pytest.mark.parametrize("move", [0, 1, 2])
 def test_ideal_chain_relaxes_to_gaussian_statistics(oracle_lib, move):
     check_ideal_chain_relaxes_to_gaussian_statistics(move=move)
 
 
 @pytest.mark.parametrize("set_order", [0, 1])
-@pytest.mark.parametrize("move", [0, 1])
+@pytest.mark.parametrize("move", [0, 1, 2])
 def test_two_particle_balance_brute_force(oracle_lib, set_order, move):
     check_two_particle_balance_brute_force(set_order, move=move)
 
@@ -445,3 +450,42 @@ def check_smc_force_direction(lib=None):
 
 def test_smc_force_direction(oracle_lib):
     check_smc_force_direction()
+
+
+# --------------------------------------------------------------------------
+# Learned proposal: the gradient of the expected-squared-jump objective
+# (through both network evaluations) against central finite differences.
+# --------------------------------------------------------------------------
+def check_esjd_gradient_matches_finite_differences(lib=None):
+    from oracle import Positions
+    d = workloads.melt_small(n_chains=64, chiN=30.0, move=2)
+    s = oracle_system(d, lib)
+    W = workloads.random_mlp(3)
+    p = workloads.random_walk_positions(d, seed=5)
+    P = Positions(p[0].copy(), p[1].copy(), p[2].copy())
+    nA, nB = s.histogram(P)
+    wA, wB = s.fields(nA, nB)
+    rng = np.random.default_rng(0)
+    checked = 0
+    for _ in range(40):
+        chain, i = int(rng.integers(0, d.n_chains)), int(rng.integers(0, d.N))
+        xi = rng.normal(size=3)
+        J, g, la = s.esjd_sample(W, P, wA, wB, chain, i, xi)
+        if abs(la) < 1e-2:      # stay away from the kink of min(1, e^l)
+            continue
+        for k in rng.choice(1604, 25, replace=False):
+            eps = 1e-6
+            Wp, Wm = W.copy(), W.copy()
+            Wp[k] += eps
+            Wm[k] -= eps
+            Jp, _, lp = s.esjd_sample(Wp, P, wA, wB, chain, i, xi, False)
+            Jm, _, lm = s.esjd_sample(Wm, P, wA, wB, chain, i, xi, False)
+            fd = (Jp - Jm) / (2 * eps)
+            assert abs(fd - g[k]) <= 1e-5 * max(1.0, abs(fd)) or \
+                abs(fd - g[k]) <= 1e-4 * (abs(fd) + abs(g[k])), (chain, i, k, fd, g[k])
+            checked += 1
+    assert checked > 400
+
+
+def test_esjd_gradient_matches_finite_differences(oracle_lib):
+    check_esjd_gradient_matches_finite_differences()
