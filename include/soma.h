@@ -66,7 +66,7 @@ typedef enum {
   SOMA_ESTATE = -6      /* call not valid in the handle's current state */
 } soma_status;
 
-typedef enum { SOMA_MOVE_UNIFORM = 0, SOMA_MOVE_SMC = 1 } soma_move;
+typedef enum { SOMA_MOVE_UNIFORM = 0, SOMA_MOVE_SMC = 1, SOMA_MOVE_LEARNED = 2 } soma_move;
 typedef enum { SOMA_SET_ORDER_RANDOM = 0, SOMA_SET_ORDER_FIXED = 1 } soma_set_order;
 typedef enum { SOMA_GRID_F32 = 0, SOMA_GRID_BF16 = 1, SOMA_GRID_F16 = 2 } soma_grid_dtype;
 
@@ -199,6 +199,61 @@ void* soma_stream(soma_t* h);
  * to check the generator against independent implementations. */
 soma_status soma_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
                         void* stream);
+
+/* ------------------------------------------------------------------------
+ * Learned proposal (desc.move = SOMA_MOVE_LEARNED; no counterpart in the
+ * paper, whose force-biased proposal is the smart Monte Carlo move, Sec. 2.2).
+ *
+ * A multilayer perceptron 12 -> 32 -> 32 -> 4 (tanh hidden units) maps the
+ * features of a particle -- the bond vectors r - r_{i-1} and r_{i+1} - r (zero
+ * without that partner), the gradient of omega_t at r (per axis, the face
+ * differences of its cell interpolated linearly inside the cell), is_A,
+ * has_prev, has_next -- to a drift mu and a log step scale s = 2 tanh(o3/2).
+ * Trial move r' = r + mu + (a/sqrt 3) e^s xi, xi standard normal; accepted
+ * with min(1, exp(-dE) q(r|r')/q(r'|r)), the reverse density evaluating the
+ * network at r', so the move samples the same distribution for any weights.
+ * Parameters (SOMA_MLP_PARAMS floats): W1[32][12], b1[32], W2[32][32], b2[32],
+ * W3[4][32], b3[4].  The sweep uses a BF16 copy with FP32 arithmetic; the
+ * FP32 master copy is trained.  A new handle starts with all weights zero
+ * (a Gaussian random-walk proposal of the uniform move's variance).
+ * ------------------------------------------------------------------------ */
+#define SOMA_MLP_PARAMS 1604
+
+/* Replace the parameters (FP32; host or device source); resets Adam. */
+soma_status soma_proposal_set_weights(soma_t* h, const float* w, size_t n, int src_on_device);
+/* Copy the FP32 master parameters out.  Synchronises. */
+soma_status soma_proposal_get_weights(soma_t* h, float* w, size_t n, int dst_on_device);
+
+/* Expected squared jump J = alpha |r' - r|^2 of n given samples and its
+ * gradient with respect to the parameters (FP32), the training objective:
+ * samples (device, n pairs chain, i), xi (device, 3n normals), w (device FP32
+ * parameters, or NULL for the handle's), grad (device, SOMA_MLP_PARAMS,
+ * overwritten with the sum over samples), J and log_alpha (device, n each,
+ * optional).  The trial position is not rounded to FP32 here (a smooth
+ * surrogate of the move).  Asynchronous. */
+soma_status soma_proposal_grad(soma_t* h, const float* w, const uint32_t* samples, const float* xi,
+                               uint32_t n, float* grad, float* J, float* log_alpha);
+
+typedef struct soma_train_cfg {
+  uint32_t steps;           /* gradient steps */
+  uint32_t batch;           /* samples per step (particles of the current state) */
+  uint32_t sweeps_between;  /* plain (uniform-move) cycles before each step */
+  float lr, beta1, beta2, eps;  /* Adam */
+} soma_train_cfg;
+
+typedef struct soma_train_log {
+  double mean_J_first;      /* mean objective of the first batch */
+  double mean_J_last;       /* ... of the last batch */
+  double mean_alpha_last;   /* mean acceptance probability of the last batch */
+  uint32_t steps_done;
+  uint32_t reserved;
+} soma_train_log;
+
+/* Train the proposal on configurations the plain method generates: per step,
+ * sweeps_between uniform-move cycles of this system, then one Adam step on
+ * -mean J over `batch` particles drawn with Philox (purpose 5).  The system's
+ * state advances.  Synchronises. */
+soma_status soma_proposal_train(soma_t* h, const soma_train_cfg* cfg, soma_train_log* log);
 
 /* ------------------------------------------------------------------------
  * Batches: many independent systems advanced together, one sweep launch and

@@ -15,10 +15,10 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import _abi
-from ._abi import (FLAG_NO_SORT, GRID_BF16, GRID_F16, GRID_F32, MOVE_SMC, MOVE_UNIFORM,
-                   SET_ORDER_FIXED, SET_ORDER_RANDOM, SomaError)
+from ._abi import (FLAG_NO_SORT, GRID_BF16, GRID_F16, GRID_F32, MLP_PARAMS, MOVE_LEARNED,
+                   MOVE_SMC, MOVE_UNIFORM, SET_ORDER_FIXED, SET_ORDER_RANDOM, SomaError)
 
-__all__ = ["SystemDesc", "System", "Batch", "SomaError", "FLAG_NO_SORT", "MOVE_UNIFORM", "MOVE_SMC", "SET_ORDER_RANDOM",
+__all__ = ["SystemDesc", "System", "Batch", "SomaError", "FLAG_NO_SORT", "MOVE_UNIFORM", "MOVE_SMC", "MOVE_LEARNED", "MLP_PARAMS", "SET_ORDER_RANDOM",
            "SET_ORDER_FIXED", "GRID_F32", "GRID_BF16", "GRID_F16"]
 
 
@@ -195,6 +195,47 @@ class System:
     @property
     def stream_handle(self):
         return _abi.soma_stream(self.h)
+
+    # -- learned proposal -------------------------------------------------
+    def set_proposal_weights(self, w):
+        a = np.ascontiguousarray(w, dtype=np.float32)
+        assert a.size == MLP_PARAMS
+        _abi.soma_proposal_set_weights(self.h, a.ctypes.data, a.size, 0)
+
+    def get_proposal_weights(self):
+        a = np.empty(MLP_PARAMS, np.float32)
+        _abi.soma_proposal_get_weights(self.h, a.ctypes.data, a.size, 0)
+        return a
+
+    def proposal_grad(self, samples, xi, w=None):
+        """(grad sum, J, log_alpha) of given samples (n x 2 uint32 (chain, i))
+        and normals (n x 3), as torch CUDA tensors."""
+        import torch
+        dev = torch.device("cuda")
+        s_ = torch.as_tensor(np.ascontiguousarray(samples, dtype=np.uint32).view(np.int32),
+                             device=dev).contiguous()
+        x_ = torch.as_tensor(np.ascontiguousarray(xi, dtype=np.float32), device=dev).contiguous()
+        n = s_.numel() // 2
+        g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=dev)
+        J = torch.empty(n, dtype=torch.float32, device=dev)
+        la = torch.empty(n, dtype=torch.float32, device=dev)
+        wp = None
+        if w is not None:
+            w_ = torch.as_tensor(np.ascontiguousarray(w, dtype=np.float32), device=dev)
+            wp = ctypes.c_void_p(w_.data_ptr())
+        _abi.soma_proposal_grad(self.h, wp, ctypes.c_void_p(s_.data_ptr()),
+                                ctypes.c_void_p(x_.data_ptr()), n, ctypes.c_void_p(g.data_ptr()),
+                                ctypes.c_void_p(J.data_ptr()), ctypes.c_void_p(la.data_ptr()))
+        self.sync()
+        return g.cpu().numpy(), J.cpu().numpy(), la.cpu().numpy()
+
+    def train_proposal(self, steps=200, batch=4096, sweeps_between=1, lr=1e-3, beta1=0.9,
+                       beta2=0.999, eps=1e-8):
+        c = _abi.SomaTrainCfg(steps, batch, sweeps_between, lr, beta1, beta2, eps)
+        lg = _abi.SomaTrainLog()
+        _abi.soma_proposal_train(self.h, ctypes.byref(c), ctypes.byref(lg))
+        return {"mean_J_first": lg.mean_J_first, "mean_J_last": lg.mean_J_last,
+                "mean_alpha_last": lg.mean_alpha_last, "steps": lg.steps_done}
 
 
 class Batch:

@@ -14,7 +14,8 @@ LIB_PATH = os.path.join(HERE, "libsoma.so")
 
 SOMA_OK, SOMA_EINVAL, SOMA_ENOMEM, SOMA_ECUDA, SOMA_EOVERFLOW, SOMA_ETIMEOUT, SOMA_ESTATE = (
     0, -1, -2, -3, -4, -5, -6)
-MOVE_UNIFORM, MOVE_SMC = 0, 1
+MOVE_UNIFORM, MOVE_SMC, MOVE_LEARNED = 0, 1, 2
+MLP_PARAMS = 1604
 SET_ORDER_RANDOM, SET_ORDER_FIXED = 0, 1
 GRID_F32, GRID_BF16, GRID_F16 = 0, 1, 2
 FLAG_NO_SORT = 1
@@ -67,6 +68,18 @@ class SomaTuneEntry(ctypes.Structure):
                 ("ms_per_cycle", ctypes.c_double)]
 
 
+class SomaTrainCfg(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint32), ("batch", ctypes.c_uint32),
+                ("sweeps_between", ctypes.c_uint32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
+
+
+class SomaTrainLog(ctypes.Structure):
+    _fields_ = [("mean_J_first", ctypes.c_double), ("mean_J_last", ctypes.c_double),
+                ("mean_alpha_last", ctypes.c_double), ("steps_done", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
 class SomaError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"soma status {status}: {msg}")
@@ -99,6 +112,10 @@ _SIGS = {
     "soma_philox": ([_P, _P, _P, _c.c_size_t, _P], _c.c_int),
     "soma_structure_factor_noalloc": ([_c.POINTER(SomaSystemDesc), _P, _P, _c.c_size_t, _P, _P],
                                       _c.c_int),
+    "soma_proposal_set_weights": ([_P, _P, _c.c_size_t, _c.c_int], _c.c_int),
+    "soma_proposal_get_weights": ([_P, _P, _c.c_size_t, _c.c_int], _c.c_int),
+    "soma_proposal_grad": ([_P, _P, _P, _P, _c.c_uint32, _P, _P, _P], _c.c_int),
+    "soma_proposal_train": ([_P, _c.POINTER(SomaTrainCfg), _c.POINTER(SomaTrainLog)], _c.c_int),
     "soma_batch_create": ([_c.POINTER(SomaSystemDesc), _c.c_uint32, _P, _c.POINTER(_P)], _c.c_int),
     "soma_batch_destroy": ([_P], _c.c_int),
     "soma_batch_sweep": ([_P, _c.c_uint32], _c.c_int),
@@ -163,6 +180,10 @@ soma_sync = _wrap("soma_sync")
 soma_stream = _wrap("soma_stream")
 soma_philox = _wrap("soma_philox")
 soma_structure_factor_noalloc = _wrap("soma_structure_factor_noalloc")
+soma_proposal_set_weights = _wrap("soma_proposal_set_weights")
+soma_proposal_get_weights = _wrap("soma_proposal_get_weights")
+soma_proposal_grad = _wrap("soma_proposal_grad")
+soma_proposal_train = _wrap("soma_proposal_train")
 soma_batch_create = _wrap("soma_batch_create")
 soma_batch_destroy = _wrap("soma_batch_destroy")
 soma_batch_sweep = _wrap("soma_batch_sweep")

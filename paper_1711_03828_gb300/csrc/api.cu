@@ -91,6 +91,14 @@ struct soma_t {
   soma_timing t{};
   cudaGraphExec_t graph = nullptr;
   bool batched = false;  // advanced only through its soma_batch_t
+  // learned proposal: FP32 master weights, BF16 copy, Adam moments, gradient
+  float* mlp_w = nullptr;
+  void* mlp_q = nullptr;
+  float* mlp_m = nullptr;
+  float* mlp_v = nullptr;
+  float* mlp_g = nullptr;
+  uint32_t train_step = 0;
+  SweepShape plain_shape;  // uniform-move shape (training trajectories)
 
   float* x() { return pos; }
   float* y() { return pos + plane; }
@@ -125,7 +133,7 @@ soma_status validate(const soma_system_desc* d) {
   }
   if (!std::isfinite(d->chiN) || !std::isfinite(d->kappaN) || !std::isfinite(d->a_Re))
     return fail(SOMA_EINVAL, "chiN, kappaN and a_Re must be finite");
-  if (d->move != SOMA_MOVE_UNIFORM && d->move != SOMA_MOVE_SMC)
+  if (d->move != SOMA_MOVE_UNIFORM && d->move != SOMA_MOVE_SMC && d->move != SOMA_MOVE_LEARNED)
     return fail(SOMA_EINVAL, "move=%d is not available", d->move);
   if (d->set_order != SOMA_SET_ORDER_RANDOM && d->set_order != SOMA_SET_ORDER_FIXED)
     return fail(SOMA_EINVAL, "set_order=%d unknown", d->set_order);
@@ -192,6 +200,11 @@ void release(soma_t* h) {
   cudaFree(h->d_err);
   cudaFree(h->d_scratch);
   cudaFree(h->d_tw);
+  cudaFree(h->mlp_w);
+  cudaFree(h->mlp_q);
+  cudaFree(h->mlp_m);
+  cudaFree(h->mlp_v);
+  cudaFree(h->mlp_g);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -235,6 +248,7 @@ SweepArgs sweep_args(soma_t* h) {
   s.smc_A = (float)A;
   s.smc_s2A = (float)std::sqrt(2.0 * A);
   s.smc_inv4A = (float)(1.0 / (4.0 * A));
+  s.learned_sigma0 = (float)(h->a64 / std::sqrt(3.0));
   return s;
 }
 
@@ -269,9 +283,15 @@ soma_status timed(soma_t* h, int kind, F&& launch) {
   return SOMA_OK;
 }
 
+cudaError_t launch_sweep_any(soma_t* h, const SweepArgs& sa) {
+  if (h->desc.move == SOMA_MOVE_LEARNED)
+    return launch_sweep_learned(sa, h->shape, h->grid_dtype, h->mlp_q, h->stream);
+  return launch_sweep_uniform(sa, h->shape, h->grid_dtype, h->stream);
+}
+
 soma_status one_cycle(soma_t* h) {
   const SweepArgs sa = sweep_args(h);
-  soma_status st = timed(h, 0, [&] { return launch_sweep_uniform(sa, h->shape, h->grid_dtype, h->stream); });
+  soma_status st = timed(h, 0, [&] { return launch_sweep_any(h, sa); });
   if (st != SOMA_OK) return st;
   const FieldArgs fa = field_args(h, 1);
   st = timed(h, 1, [&] { return launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count, h->stream); });
@@ -287,7 +307,7 @@ soma_status build_graph(soma_t* h) {
   const FieldArgs fa = field_args(h, 1);
   cudaError_t e = cudaSuccess;
   for (uint32_t k = 0; k < GRAPH_CHUNK && e == cudaSuccess; ++k) {
-    e = launch_sweep_uniform(sa, h->shape, h->grid_dtype, h->stream);
+    e = launch_sweep_any(h, sa);
     if (e == cudaSuccess) e = launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count, h->stream);
   }
   cudaError_t e2 = cudaStreamEndCapture(h->stream, &gr);
@@ -386,14 +406,24 @@ soma_status soma_create(const soma_system_desc* desc, soma_t** out) {
   ALLOC(h->d_counters, sizeof(unsigned long long) * 2);
   ALLOC(h->d_err, sizeof(unsigned) * 2);
   ALLOC(h->d_scratch, sizeof(double) * (h->scratch_doubles + 64));
+  ALLOC(h->mlp_w, sizeof(float) * SOMA_MLP_PARAMS);
+  ALLOC(h->mlp_q, 2 * SOMA_MLP_PARAMS);
+  ALLOC(h->mlp_m, sizeof(float) * SOMA_MLP_PARAMS);
+  ALLOC(h->mlp_v, sizeof(float) * SOMA_MLP_PARAMS);
+  ALLOC(h->mlp_g, sizeof(float) * SOMA_MLP_PARAMS);
 #undef ALLOC
   h->d_out = h->d_scratch + h->scratch_doubles;
   h->shape = sweep_shape(h->g.n_chains, h->g.N, h->sm_count, h->grid_dtype, desc->move);
+  h->plain_shape = sweep_shape(h->g.n_chains, h->g.N, h->sm_count, h->grid_dtype, SOMA_MOVE_UNIFORM);
 #define CK(call) do { e = (call); if (e != cudaSuccess) { release(h); return cuda_fail(e, #call); } } while (0)
   CK(cudaMemsetAsync(h->n[0], 0, sizeof(uint32_t) * cells, h->stream));
   CK(cudaMemsetAsync(h->n[1], 0, sizeof(uint32_t) * cells, h->stream));
   CK(cudaMemsetAsync(h->d_counters, 0, sizeof(unsigned long long) * 2, h->stream));
   CK(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned) * 2, h->stream));
+  CK(cudaMemsetAsync(h->mlp_w, 0, sizeof(float) * SOMA_MLP_PARAMS, h->stream));
+  CK(cudaMemsetAsync(h->mlp_q, 0, 2 * SOMA_MLP_PARAMS, h->stream));
+  CK(cudaMemsetAsync(h->mlp_m, 0, sizeof(float) * SOMA_MLP_PARAMS, h->stream));
+  CK(cudaMemsetAsync(h->mlp_v, 0, sizeof(float) * SOMA_MLP_PARAMS, h->stream));
   if ((desc->flags & SOMA_FLAG_NO_SORT) || h->g.n_chains >= (1ull << 32)) {
     CK(launch_init(h->g, h->x(), h->y(), h->z(), h->sigma, h->sm_count, h->stream));
     ++h->launches;
@@ -632,6 +662,123 @@ soma_status soma_get_timing(soma_t* h, soma_timing* out) {
   h->ev_pending.clear();
   *out = h->t;
   out->kernel_launches = h->launches;
+  return SOMA_OK;
+}
+
+soma_status soma_proposal_set_weights(soma_t* h, const float* w, size_t n, int src_on_device) {
+  if (!h || !w) return fail(SOMA_EINVAL, "NULL argument");
+  if (n != SOMA_MLP_PARAMS) return fail(SOMA_EINVAL, "n=%zu, the network has %d parameters", n, SOMA_MLP_PARAMS);
+  SOMA_CUDA(cudaMemcpyAsync(h->mlp_w, w, sizeof(float) * n,
+                            src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            h->stream));
+  SOMA_CUDA(launch_quantize(h->mlp_w, h->mlp_q, h->stream));
+  SOMA_CUDA(cudaMemsetAsync(h->mlp_m, 0, sizeof(float) * n, h->stream));
+  SOMA_CUDA(cudaMemsetAsync(h->mlp_v, 0, sizeof(float) * n, h->stream));
+  h->train_step = 0;
+  ++h->launches;
+  if (!src_on_device) SOMA_CUDA(cudaStreamSynchronize(h->stream));
+  return SOMA_OK;
+}
+
+soma_status soma_proposal_get_weights(soma_t* h, float* w, size_t n, int dst_on_device) {
+  if (!h || !w) return fail(SOMA_EINVAL, "NULL argument");
+  if (n != SOMA_MLP_PARAMS) return fail(SOMA_EINVAL, "n=%zu, the network has %d parameters", n, SOMA_MLP_PARAMS);
+  SOMA_CUDA(cudaMemcpyAsync(w, h->mlp_w, sizeof(float) * n,
+                            dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            h->stream));
+  return sync(h);
+}
+
+namespace {
+TrainArgs train_args(soma_t* h) {
+  TrainArgs t{};
+  t.g = h->g;
+  t.x = h->x();
+  t.y = h->y();
+  t.z = h->z();
+  t.wA = h->w[0];
+  t.wB = h->w[1];
+  t.w = h->mlp_w;
+  t.grad = h->mlp_g;
+  t.sigma0 = (float)(h->a64 / std::sqrt(3.0));
+  t.K_b = (float)h->K_b;
+  return t;
+}
+}  // namespace
+
+soma_status soma_proposal_grad(soma_t* h, const float* w, const uint32_t* samples, const float* xi,
+                               uint32_t n, float* grad, float* J, float* log_alpha) {
+  if (!h || !samples || !xi || !grad) return fail(SOMA_EINVAL, "NULL argument");
+  TrainArgs t = train_args(h);
+  if (w) t.w = w;
+  t.grad = grad;
+  t.J = J;
+  t.log_alpha = log_alpha;
+  t.samples = samples;
+  t.xi = xi;
+  t.n = n;
+  SOMA_CUDA(cudaMemsetAsync(grad, 0, sizeof(float) * SOMA_MLP_PARAMS, h->stream));
+  SOMA_CUDA(launch_esjd_grad(t, h->grid_dtype, h->sm_count, h->stream));
+  h->launches += 1;
+  return SOMA_OK;
+}
+
+soma_status soma_proposal_train(soma_t* h, const soma_train_cfg* cfg, soma_train_log* log) {
+  if (!h || !cfg) return fail(SOMA_EINVAL, "NULL argument");
+  if (cfg->batch < 1 || cfg->steps < 1) return fail(SOMA_EINVAL, "steps and batch must be >= 1");
+  float* dJ = nullptr;
+  float* dla = nullptr;
+  SOMA_CUDA(cudaMallocAsync((void**)&dJ, sizeof(float) * cfg->batch, h->stream));
+  SOMA_CUDA(cudaMallocAsync((void**)&dla, sizeof(float) * cfg->batch, h->stream));
+  std::vector<float> hJ(cfg->batch), hla(cfg->batch);
+  double first = 0.0, last = 0.0, acc_last = 0.0;
+  const SweepArgs sa = sweep_args(h);
+  const FieldArgs fa = field_args(h, 1);
+  for (uint32_t k = 0; k < cfg->steps; ++k) {
+    // trajectories of the plain method
+    for (uint32_t c = 0; c < cfg->sweeps_between; ++c) {
+      SOMA_CUDA(launch_sweep_uniform(sa, h->plain_shape, h->grid_dtype, h->stream));
+      SOMA_CUDA(launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count, h->stream));
+      ++h->host_sweep;
+      h->launches += 2;
+    }
+    TrainArgs t = train_args(h);
+    t.J = dJ;
+    t.log_alpha = dla;
+    t.n = cfg->batch;
+    t.step = h->train_step;
+    SOMA_CUDA(cudaMemsetAsync(h->mlp_g, 0, sizeof(float) * SOMA_MLP_PARAMS, h->stream));
+    SOMA_CUDA(launch_esjd_grad(t, h->grid_dtype, h->sm_count, h->stream));
+    ++h->train_step;
+    SOMA_CUDA(launch_adam(h->mlp_w, h->mlp_m, h->mlp_v, h->mlp_g, h->mlp_q, cfg->lr, cfg->beta1,
+                          cfg->beta2, cfg->eps, (int)h->train_step, 1.f / (float)cfg->batch,
+                          h->stream));
+    h->launches += 2;
+    if (k == 0 || k + 1 == cfg->steps) {
+      SOMA_CUDA(cudaMemcpyAsync(hJ.data(), dJ, sizeof(float) * cfg->batch, cudaMemcpyDeviceToHost, h->stream));
+      SOMA_CUDA(cudaMemcpyAsync(hla.data(), dla, sizeof(float) * cfg->batch, cudaMemcpyDeviceToHost, h->stream));
+      SOMA_CUDA(cudaStreamSynchronize(h->stream));
+      double sj = 0.0, sa_ = 0.0;
+      for (uint32_t b = 0; b < cfg->batch; ++b) {
+        sj += hJ[b];
+        sa_ += hla[b] >= 0.f ? 1.0 : std::exp((double)hla[b]);
+      }
+      if (k == 0) first = sj / cfg->batch;
+      last = sj / cfg->batch;
+      acc_last = sa_ / cfg->batch;
+    }
+  }
+  cudaFreeAsync(dJ, h->stream);
+  cudaFreeAsync(dla, h->stream);
+  soma_status st = sync(h);
+  if (st != SOMA_OK) return st;
+  if (log) {
+    log->mean_J_first = first;
+    log->mean_J_last = last;
+    log->mean_alpha_last = acc_last;
+    log->steps_done = cfg->steps;
+    log->reserved = 0;
+  }
   return SOMA_OK;
 }
 

@@ -14,7 +14,7 @@
 namespace soma {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
-constexpr uint32_t PURPOSE_INIT = 0, PURPOSE_MOVE = 1, PURPOSE_MOVE2 = 2;
+constexpr uint32_t PURPOSE_INIT = 0, PURPOSE_MOVE = 1, PURPOSE_MOVE2 = 2, PURPOSE_TRAIN = 5;
 
 // Philox4x32-10: ten rounds of two 32x32->64 products (counter words 0 and 2
 // times the round multipliers) whose high halves are xored with counter words
@@ -160,6 +160,26 @@ struct SweepArgs {
   int set_order_random;
   // smart Monte Carlo: A = a^2/6, sqrt(2A), 1/(4A)
   float smc_A, smc_s2A, smc_inv4A;
+  float learned_sigma0;     // a/sqrt(3): scale of the learned proposal
+};
+
+// Training of the learned proposal: one expected-squared-jump sample per thread.
+struct TrainArgs {
+  Geom g;
+  const float* x;
+  const float* y;
+  const float* z;
+  const void* wA;
+  const void* wB;
+  const float* w;            // FP32 parameters (1604)
+  float* grad;               // accumulated dJ/dW (1604)
+  float* J;                  // per-sample objective (optional)
+  float* log_alpha;          // per-sample log acceptance (optional)
+  const uint32_t* samples;   // (chain, i) pairs, or NULL: drawn with Philox (purpose 5)
+  const float* xi;           // 3 normals per sample when samples are given
+  uint32_t n;                // samples
+  uint32_t step;             // training step (counter word of the drawn samples)
+  float sigma0, K_b;
 };
 
 struct FieldArgs {

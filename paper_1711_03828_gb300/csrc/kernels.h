@@ -64,6 +64,14 @@ cudaError_t launch_fields_batch(const BatchArgs& a, uint32_t total_cells, unsign
                                 unsigned* err, int grid_dtype, int sm_count, cudaStream_t st);
 int batch_kernel_blocks_per_sm(int block, int grid_dtype);
 
+cudaError_t launch_sweep_learned(const SweepArgs& a, const SweepShape& s, int grid_dtype,
+                                 const void* wq, cudaStream_t st);
+cudaError_t launch_esjd_grad(const TrainArgs& t, int grid_dtype, int sm_count, cudaStream_t st);
+cudaError_t launch_adam(float* w, float* m, float* v, const float* grad, void* wq, float lr,
+                        float b1, float b2, float eps, int step, float inv_n, cudaStream_t st);
+cudaError_t launch_quantize(const float* w, void* wq, cudaStream_t st);
+const void* learned_kernel_ptr(int Q, int grid_dtype);
+
 // Entry-point helpers implemented in api.cu (messages go to soma_last_error).
 }  // namespace soma
 #include "../../include/soma.h"

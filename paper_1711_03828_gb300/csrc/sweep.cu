@@ -464,6 +464,7 @@ static const void* sweep_kernel_ptr(int Q, bool vec, int grid_dtype, bool pair, 
                                     int move) {
   if (move == 1) return Q == 1 ? pick_smc<1>(grid_dtype) : (Q == 2 ? pick_smc<2>(grid_dtype)
                                                                     : pick_smc<4>(grid_dtype));
+  if (move == 2) return learned_kernel_ptr(Q, grid_dtype);
   if (pair) {
     if (big) {
       switch (grid_dtype) {

@@ -1,0 +1,202 @@
+"""Learned MH-corrected proposal: training gradient and sweep against the FP64
+oracle, exactness by brute force on the GPU, and the gain of training.
+
+Training gradient (FP32 weights): per-sample J and log alpha to 1e-5 relative
+(1e-5 absolute), the gradient summed over samples to 1e-4 of its norm;
+samples whose trial position lies within 1e-4 dL of a cell face or whose log
+alpha is within 1e-3 of the kink of min(1, e^l) are left out (there the FP32
+and FP64 evaluations may take different branches).
+Sweep: one cycle from the same positions and BF16-exact random weights, the
+tolerances of the smart Monte Carlo move (the network and the normals are
+evaluated in FP32 on the GPU, in FP64 in the oracle).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import Positions
+from paper_1711_03828_gb300 import MOVE_LEARNED, MOVE_SMC, System, SystemDesc, workloads
+from tests.conftest import oracle_system
+from tests.test_gpu_parity import _pos
+from tests.test_gpu_smc import _near_face, _tol
+
+pytestmark = pytest.mark.gpu
+
+TIE_LEARNED = 1e-3
+
+
+def _state(d, seed):
+    pos0 = workloads.random_walk_positions(d, seed=seed)
+    s = System(d)
+    s.set_positions(pos0)
+    s.update_fields()
+    orc = oracle_system(d)
+    p = _pos(pos0)
+    nA, nB = orc.histogram(p)
+    wA, wB = orc.fields(nA, nB)
+    return s, orc, p, wA, wB
+
+
+def test_training_gradient_matches_oracle(cuda_device):
+    d = workloads.melt_small(n_chains=256, chiN=30.0, move=MOVE_LEARNED)
+    s, orc, p, wA, wB = _state(d, 21)
+    W = workloads.random_mlp(11).astype(np.float32)
+    rng = np.random.default_rng(4)
+    n = 512
+    samples = np.stack([rng.integers(0, d.n_chains, n), rng.integers(0, d.N, n)], 1).astype(np.uint32)
+    xi = rng.normal(size=(n, 3)).astype(np.float32)
+    _, J, la = s.proposal_grad(samples, xi, w=W)
+    Wd = W.astype(np.float64)
+    keep = []
+    for b in range(n):
+        Jo, _, lo = orc.esjd_sample(Wd, p, wA, wB, samples[b, 0], samples[b, 1], xi[b].astype(np.float64),
+                                    want_grad=False)
+        # trial position of the oracle (no FP32 rounding), for the face check
+        f = orc.learned_features(p, wA if samples[b, 1] < orc.params.N_A else wB, samples[b, 0],
+                                 samples[b, 1],
+                                 [p.x[samples[b, 0] * d.N + samples[b, 1]],
+                                  p.y[samples[b, 0] * d.N + samples[b, 1]],
+                                  p.z[samples[b, 0] * d.N + samples[b, 1]]])
+        import oracle as O
+        o = O.mlp_forward(Wd, f)
+        sig = orc.params.a / math.sqrt(3) * math.exp(2 * math.tanh(0.5 * o[3]))
+        m = samples[b, 0] * d.N + samples[b, 1]
+        rp = np.array([p.x[m], p.y[m], p.z[m]], np.float64) + o[:3] + sig * xi[b]
+        near = np.any(np.abs(rp - np.round(rp)) < 1e-4)
+        if near or abs(lo) < 1e-3:
+            continue
+        assert abs(J[b] - Jo) <= 1e-5 * max(1.0, abs(Jo)), (b, J[b], Jo)
+        assert abs(la[b] - lo) <= 1e-4 * max(1.0, abs(lo)), (b, la[b], lo)
+        keep.append(b)
+    assert len(keep) > 0.8 * n
+    keep = np.asarray(keep)
+    g_gpu, _, _ = s.proposal_grad(samples[keep], xi[keep], w=W)
+    g_or = np.zeros(1604)
+    for b in keep:
+        _, g, _ = orc.esjd_sample(Wd, p, wA, wB, samples[b, 0], samples[b, 1],
+                                  xi[b].astype(np.float64))
+        g_or += g
+    err = np.linalg.norm(g_gpu - g_or) / np.linalg.norm(g_or)
+    print(f"training gradient over {len(keep)} samples: relative error {err:.2e}")
+    assert err < 1e-4
+    s.close()
+
+
+@pytest.mark.parametrize("N,n_chains,grid,box", [
+    (32, 1024, (12, 12, 12), (2.0, 2.0, 2.0)),
+    (7, 1500, (9, 9, 6), (1.5, 1.5, 1.0)),
+    (64, 512, (12, 12, 12), (2.0, 2.0, 2.0)),
+])
+def test_learned_one_cycle_matches_oracle(cuda_device, N, n_chains, grid, box):
+    d = SystemDesc(n_chains=n_chains, N=N, f=0.5, box_Re=box, grid=grid, chiN=30.0,
+                   kappaN=50.0, move=MOVE_LEARNED, seed=11)
+    W = workloads.random_mlp(5, scale=0.2)
+    moves = mism = accepted = 0
+    for k, sweep in enumerate((0, 3, 1000)):
+        pos0 = workloads.random_walk_positions(d, seed=300 + k)
+        orc = oracle_system(d)
+        orc.set_mlp(W)
+        s = System(d)
+        s.set_proposal_weights(W.astype(np.float32))
+        s.set_positions(pos0)
+        s.set_sweep(sweep)
+        p = _pos(pos0)
+        nA, nB = orc.histogram(p)
+        wA, wB = orc.fields(nA, nB)
+        _, margin, acc, trial = orc.sweep(p, wA, wB, sweep, want_margin=True, want_acc=True,
+                                          want_trial=True)
+        s.sweep(1)
+        g = s.get_positions()
+        s.close()
+        gacc = np.any(g != pos0, axis=0).astype(np.uint8)
+        bad = np.nonzero(gacc != acc)[0]
+        ok = set(bad[np.abs(margin[bad]) < TIE_LEARNED].tolist())
+        face = _near_face(trial)
+        ok |= {int(m) for m in bad if face[m]}
+        for m in bad.tolist():
+            if m not in ok:
+                assert any(k2 in ok and k2 // d.N == m // d.N for k2 in (m - 1, m + 1)), (m, margin[m])
+        keep = np.ones(d.n_chains, bool)
+        keep[np.unique(bad // d.N)] = False
+        keep = np.repeat(keep, d.N)
+        np.testing.assert_array_equal(g[:, keep & (acc == 0)], pos0[:, keep & (acc == 0)])
+        sel = keep & (acc == 1)
+        err = np.abs(g[:, sel].astype(np.float64) - trial[:, sel]) / _tol(trial[:, sel])
+        assert err.max(initial=0) <= 1.0, err.max()
+        moves += d.M
+        mism += len(bad)
+        accepted += int(acc.sum())
+    print(f"learned N={N}: {moves} moves, acceptance {accepted / moves:.3f}, mismatches {mism}")
+    assert mism <= max(3, 5e-4 * moves)
+
+
+def _pair_probabilities(K, L):
+    from tests.test_oracle_pins import _pair_cell_probabilities
+    z = np.zeros(L**3)
+    return _pair_cell_probabilities(K, L, z, z)
+
+
+@pytest.mark.parametrize("move", [0, MOVE_SMC, MOVE_LEARNED])
+def test_gpu_two_particle_balance_brute_force(cuda_device, move):
+    """Dimers with chiN = kappaN = 0 on a periodic 2^3 grid: the visited cell
+    pairs follow the exact distribution (erf quadrature) for every move type,
+    the learned one with random weights (a strongly asymmetric proposal)."""
+    L, Re = 2, 1.5
+    d = SystemDesc(n_chains=16384, N=2, f=0.5, box_Re=(L / Re,) * 3, grid=(L,) * 3, chiN=0.0,
+                   kappaN=0.0, move=move, seed=23)
+    s = System(d)
+    if move == MOVE_LEARNED:
+        s.set_proposal_weights(workloads.random_mlp(7, scale=0.1).astype(np.float32))
+    s.sweep(100)
+    T = 400
+    counts = np.zeros((d.n_chains, L**6))
+    for _ in range(T):
+        s.sweep(1)
+        P = s.get_positions().reshape(3, d.n_chains, 2).astype(np.float64)
+        c = np.floor(P).astype(np.int64) % L
+        ci = (c[2] * L + c[1]) * L + c[0]
+        counts[np.arange(d.n_chains), ci[:, 0] * L**3 + ci[:, 1]] += 1
+    s.close()
+    K = 3.0 / (2 * Re * Re)
+    Pex = _pair_probabilities(K, L).reshape(-1)
+    freq = counts / T
+    est = freq.mean(0)
+    se = freq.std(0) / math.sqrt(d.n_chains)
+    z = (est - Pex) / np.maximum(se, 1e-12)
+    print(f"move {move}: max |z| {np.max(np.abs(z)):.2f}")
+    assert np.max(np.abs(z)) < 5.0
+
+
+def test_training_increases_the_expected_jump(cuda_device):
+    """Training on plain-method configurations raises the mean accepted squared
+    displacement per move of the learned proposal above that of the untrained
+    (zero-weight Gaussian) proposal, measured over whole sweeps."""
+    d = workloads.melt_small(chiN=20.0, move=MOVE_LEARNED)
+
+    def msd_per_move(s, sweeps=20):
+        tot = 0.0
+        for _ in range(sweeps):
+            a = s.get_positions().astype(np.float64)
+            s.sweep(1)
+            b = s.get_positions().astype(np.float64)
+            tot += ((b - a) ** 2).sum() / d.M
+        return tot / sweeps
+
+    base = System(d)
+    base.sweep(50)
+    msd0 = msd_per_move(base)
+    base.close()
+    s = System(d)
+    log = s.train_proposal(steps=300, batch=8192, sweeps_between=1, lr=3e-3)
+    msd1 = msd_per_move(s)
+    s.close()
+    uni = System(workloads.melt_small(chiN=20.0))
+    uni.sweep(50)
+    msd_u = msd_per_move(uni)
+    uni.close()
+    print(f"training: J {log['mean_J_first']:.4f} -> {log['mean_J_last']:.4f}, "
+          f"alpha {log['mean_alpha_last']:.3f}; msd/move untrained {msd0:.4f}, "
+          f"trained {msd1:.4f}, uniform {msd_u:.4f}")
+    assert log["mean_J_last"] > log["mean_J_first"]
+    assert msd1 > 1.1 * msd0
