@@ -35,8 +35,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="melt_large",
                     choices=["melt_large", "melt_mid", "melt_small", "melt_slow", "melt_subbox",
-                             "batch64"])
-    ap.add_argument("--move", default="uniform", choices=["uniform", "smc"],
+                             "batch64", "decorrelation"])
+    ap.add_argument("--move", default="uniform", choices=["uniform", "smc", "learned"],
                     help="trial moves: uniform displacement or smart Monte Carlo")
     ap.add_argument("--grid-dtype", default="f32", choices=["f32", "bf16", "f16"],
                     help="storage type of the omega grids (energies stay FP32)")
@@ -59,7 +59,7 @@ def workload(name, replica=0, grid_dtype="f32", move="uniform"):
     d = getattr(workloads, name)(seed=1)
     d.replica_id = replica
     d.grid_dtype = GRID_DTYPES[grid_dtype]
-    d.move = 1 if move == "smc" else 0
+    d.move = {"uniform": 0, "smc": 1, "learned": 2}[move]
     return d
 
 
@@ -68,7 +68,7 @@ def config_of(d, name, l2_note):
                         f"{d.grid}, chiN={d.chiN}, kappaN={d.kappaN}",
             "n_chains": d.n_chains, "N": d.N, "particles": d.M, "grid": list(d.grid),
             "box_Re": list(d.box_Re), "chiN": d.chiN, "kappaN": d.kappaN,
-            "move": "smart Monte Carlo" if d.move == 1 else "uniform",
+            "move": {0: "uniform", 1: "smart Monte Carlo", 2: "learned MH proposal"}[d.move],
             "set_order": "random per chain and sweep",
             "grid_dtype": {0: "f32", 1: "bf16", 2: "f16"}[d.grid_dtype], "l2": l2_note}
 
@@ -248,6 +248,9 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     s = System(d, stream=stream)
+    train_log = None
+    if d.move == 2:  # train the proposal on this system's plain-method configurations
+        train_log = s.train_proposal(steps=200, batch=16384, sweeps_between=1, lr=3e-3)
 
     def barrier():
         if world > 1:
@@ -320,8 +323,9 @@ def run_ours(args):
         "config": config_of(d, args.workload,
                             f"inputs larger than L2 ({12 * d.M / 1e9:.2f} GB of positions)"),
         "roofline": {"bound": "hbm",
-                     "kernel": "sweep_smc_kernel" if d.move == 1 else
-                     ("sweep_pair_kernel" if d.N % 2 == 0 and d.N <= 64 else "sweep_uniform_kernel"),
+                     "kernel": {1: "sweep_smc_kernel", 2: "sweep_learned_kernel"}.get(
+                         d.move, "sweep_pair_kernel" if d.N % 2 == 0 and d.N <= 64
+                         else "sweep_uniform_kernel"),
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": measured_traffic(args.workload)
                      if args.grid_dtype == "f32" and args.move == "uniform" else None,
@@ -333,6 +337,8 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "acceptance": obs["accepted"] / max(obs["attempted"], 1),
     }
+    if train_log is not None:
+        line["training"] = train_log
     if not args.no_cpu_baseline and world == 1:
         rate, cores, sample, _, _ = oracle_rate(args.workload, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -420,12 +426,108 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def tau_int(x, c=5.0):
+    """Integrated autocorrelation time (in samples) of series x (T, chains),
+    chain-averaged autocorrelation, Sokal's automatic window (W >= c tau)."""
+    import numpy as np
+    x = np.asarray(x, dtype=np.float64)
+    if x.ndim == 1:
+        x = x[:, None]
+    x = x - x.mean(0)
+    T = x.shape[0]
+    f = np.fft.rfft(x, n=2 * T, axis=0)
+    acf = np.fft.irfft(f * np.conj(f), n=2 * T, axis=0)[:T].mean(1) / np.arange(T, 0, -1)
+    rho = acf / acf[0]
+    tau = 0.5
+    for W in range(1, T):
+        tau += rho[W]
+        if W >= c * tau:
+            break
+    return float(tau), int(W)
+
+
+def run_decorrelation(args):
+    """R_e^2 decorrelations per second of the uniform, smart Monte Carlo and
+    learned moves on the slow melt (N=64, chiN=40, kappaN=50): tau_int of the
+    per-chain R_e^2 and of S(q*) on an 8x8x4 R_e0 box, wall time per cycle at
+    the 67M-particle scale, decorrelations/s = chains * cycles/s / (2 tau)."""
+    import numpy as np
+    import torch
+    from paper_1711_03828_gb300 import System, workloads
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda")
+    small = workloads.melt_slow(n_chains=16384, box_Re=(8.0, 8.0, 4.0), grid=(48, 48, 24))
+    big = workloads.melt_slow()
+    every, T, equil = 10, max(args.steps, 400), 1000
+    # train the learned proposal on plain-method configurations of the small box
+    tr = System(workloads.melt_slow(n_chains=16384, box_Re=(8.0, 8.0, 4.0), grid=(48, 48, 24),
+                                    move=2))
+    tr.sweep(200)
+    train_log = tr.train_proposal(steps=600, batch=16384, sweeps_between=1, lr=3e-3)
+    W = tr.get_proposal_weights()
+    tr.close()
+    # q*: the strongest low-q shell after equilibration (uniform moves)
+    ms_all = [(i, j, k) for i in range(-4, 5) for j in range(-4, 5) for k in range(0, 3)
+              if 0 < i * i + j * j + k * k <= 16]
+    res = {}
+    for name, move in (("uniform", 0), ("smc", 1), ("learned", 2)):
+        d = workloads.melt_slow(n_chains=16384, box_Re=(8.0, 8.0, 4.0), grid=(48, 48, 24),
+                                move=move)
+        s = System(d)
+        if move == 2:
+            s.set_proposal_weights(W)
+        s.sweep(equil)
+        if name == "uniform":
+            sq = s.structure_factor(ms_all)
+            q_star = [ms_all[int(np.argmax(sq))]]
+        pos = torch.empty(3 * d.M, dtype=torch.float32, device=dev)
+        re2, sqs = [], []
+        for t in range(T):
+            s.sweep(every)
+            s.get_positions(out=pos)
+            P = pos.view(3, d.n_chains, d.N)
+            re2.append(((P[:, :, -1] - P[:, :, 0]) ** 2).sum(0).double().cpu().numpy())
+            sqs.append(float(s.structure_factor(q_star)[0]))
+        s.close()
+        tau_re, w_re = tau_int(np.asarray(re2))
+        tau_sq, w_sq = tau_int(np.asarray(sqs))
+        # wall time per cycle at scale
+        b = System(workloads.melt_slow(move=move))
+        if move == 2:
+            b.set_proposal_weights(W)
+        b.sweep(3)
+        import time as _t
+        b.sync()
+        t0 = _t.perf_counter()
+        b.sweep(20)
+        b.sync()
+        ms_cycle = (_t.perf_counter() - t0) * 1e3 / 20
+        b.close()
+        tau_sweeps = tau_re * every
+        res[name] = {"tau_int_Re2_sweeps": tau_sweeps, "window": w_re * every,
+                     "tau_int_Sq_sweeps": tau_sq * every, "ms_per_cycle_67M": ms_cycle,
+                     "decorrelations_per_s": big.n_chains * (1e3 / ms_cycle) / (2 * tau_sweeps)}
+    line = {"metric": "R_e^2 decorrelations/s (learned vs plain)", "unit": "decorrelations/s",
+            "value": res["learned"]["decorrelations_per_s"], "higher_is_better": True,
+            "n_gpus": 1, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "slow melt: tau_int on 16,384 chains x N=64 in 8x8x4 R_e0 "
+                                   "(48x48x24 grid), wall time on 1,048,576 chains in 32x32x16 R_e0 "
+                                   "(192x192x96 grid), chiN=40, kappaN=50",
+                       "sampling": f"every {every} cycles, {T} samples after {equil} cycles",
+                       "q_star": q_star[0]},
+            "moves": res, "training": train_log}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch64":
         run_batch(args)
+    elif args.workload == "decorrelation":
+        run_decorrelation(args)
     else:
         run_ours(args)
 
