@@ -204,7 +204,7 @@ soma_status soma_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out,
  * Learned proposal (desc.move = SOMA_MOVE_LEARNED; no counterpart in the
  * paper, whose force-biased proposal is the smart Monte Carlo move, Sec. 2.2).
  *
- * A multilayer perceptron 12 -> 32 -> 32 -> 4 (tanh hidden units) maps the
+ * A multilayer perceptron 12 -> 32 -> 32 -> 4 (ReLU hidden units) maps the
  * features of a particle -- the bond vectors r - r_{i-1} and r_{i+1} - r (zero
  * without that partner), the gradient of omega_t at r (per axis, the face
  * differences of its cell interpolated linearly inside the cell), is_A,

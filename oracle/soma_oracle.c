@@ -433,13 +433,13 @@ static void or_mlp_run(const double* W, const double x[12], or_mlp_cache* c) {
     double a = W[L_B1 + j];
     for (int k = 0; k < 12; ++k) a += W[L_W1 + 12 * j + k] * x[k];
     c->z1[j] = a;
-    c->h1[j] = tanh(a);
+    c->h1[j] = a > 0.0 ? a : 0.0;
   }
   for (int j = 0; j < 32; ++j) {
     double a = W[L_B2 + j];
     for (int k = 0; k < 32; ++k) a += W[L_W2 + 32 * j + k] * c->h1[k];
     c->z2[j] = a;
-    c->h2[j] = tanh(a);
+    c->h2[j] = a > 0.0 ? a : 0.0;
   }
   for (int j = 0; j < 4; ++j) {
     double a = W[L_B3 + j];
@@ -464,13 +464,13 @@ static void or_mlp_backward(const double* W, const or_mlp_cache* c, const double
     for (int j = 0; j < 4; ++j) a += W[L_W3 + 32 * j + k] * go[j];
     gh2[k] = a;
   }
-  for (int k = 0; k < 32; ++k) gz2[k] = gh2[k] * (1.0 - c->h2[k] * c->h2[k]);
+  for (int k = 0; k < 32; ++k) gz2[k] = c->z2[k] > 0.0 ? gh2[k] : 0.0;
   for (int k = 0; k < 32; ++k) {
     double a = 0.0;
     for (int j = 0; j < 32; ++j) a += W[L_W2 + 32 * j + k] * gz2[j];
     gh1[k] = a;
   }
-  for (int k = 0; k < 32; ++k) gz1[k] = gh1[k] * (1.0 - c->h1[k] * c->h1[k]);
+  for (int k = 0; k < 32; ++k) gz1[k] = c->z1[k] > 0.0 ? gh1[k] : 0.0;
   for (int k = 0; k < 12; ++k) {
     double a = 0.0;
     for (int j = 0; j < 32; ++j) a += W[L_W1 + 12 * j + k] * gz1[j];

@@ -115,7 +115,7 @@ void or_sweep_trial(const or_system* s, float* x, float* y, float* z,
                     double* margin, uint8_t* accepted, float* trial, or_sweep_stats* st);
 
 /* --- a7/a8: learned Metropolis-Hastings proposal ----------------------------
- * A multilayer perceptron 12 -> 32 -> 32 -> 4 (tanh hidden units) maps the
+ * A multilayer perceptron 12 -> 32 -> 32 -> 4 (ReLU hidden units) maps the
  * features of a particle to a drift mu (3) and a log step scale; the trial
  * move is r' = r + mu + sigma xi with sigma = sigma0 exp(2 tanh(o3/2)),
  * sigma0 = a/sqrt(3), xi standard normal (Box-Muller of the move draw, as for

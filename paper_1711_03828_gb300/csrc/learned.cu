@@ -1,7 +1,7 @@
 // learned.cu -- the learned Metropolis-Hastings proposal (no counterpart in the
 // paper, whose force-biased proposal is the smart Monte Carlo move of Sec. 2.2).
 //
-// A multilayer perceptron 12 -> 32 -> 32 -> 4 (tanh hidden units) maps the
+// A multilayer perceptron 12 -> 32 -> 32 -> 4 (ReLU hidden units) maps the
 // features of a particle (bond vectors to its partners, the interpolated field
 // gradient, is_A / has_prev / has_next) to a drift mu and a log step scale
 // s = 2 tanh(o3/2); the trial move r' = r + mu + sigma0 e^s xi is accepted with
@@ -26,14 +26,14 @@ __device__ __forceinline__ void mlp_fwd(const float* __restrict__ W, const float
     float a = W[L_B1 + j];
 #pragma unroll
     for (int k = 0; k < 12; ++k) a = fmaf(W[L_W1 + 12 * j + k], f[k], a);
-    h1[j] = tanhf(a);
+    h1[j] = fmaxf(a, 0.f);
   }
 #pragma unroll 4
   for (int j = 0; j < 32; ++j) {
     float a = W[L_B2 + j];
 #pragma unroll
     for (int k = 0; k < 32; ++k) a = fmaf(W[L_W2 + 32 * j + k], h1[k], a);
-    h2[j] = tanhf(a);
+    h2[j] = fmaxf(a, 0.f);
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -258,14 +258,14 @@ __device__ __forceinline__ void mlp_bwd(const float* __restrict__ W, const float
     float a = 0.f;
 #pragma unroll
     for (int j = 0; j < 4; ++j) a = fmaf(W[L_W3 + 32 * j + k], go[j], a);
-    gz2[k] = a * (1.f - h2[k] * h2[k]);
+    gz2[k] = h2[k] > 0.f ? a : 0.f;
   }
 #pragma unroll 4
   for (int k = 0; k < 32; ++k) {
     float a = 0.f;
 #pragma unroll
     for (int j = 0; j < 32; ++j) a = fmaf(W[L_W2 + 32 * j + k], gz2[j], a);
-    gz1[k] = a * (1.f - h1[k] * h1[k]);
+    gz1[k] = h1[k] > 0.f ? a : 0.f;
   }
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
