@@ -78,6 +78,10 @@ typedef enum { SOMA_GRID_F32 = 0, SOMA_GRID_BF16 = 1, SOMA_GRID_F16 = 2 } soma_g
  * the label decides the particle indices and so the Philox streams.
  * SOMA_FLAG_NO_SORT keeps the drawing order (chain k = k-th draw). */
 #define SOMA_FLAG_NO_SORT 1
+/* The learned proposal's network runs on the tensor cores (BF16 operands and
+ * activations, FP32 accumulation) for even N <= 64; this flag evaluates it on
+ * the CUDA cores in FP32 instead (the precision the parity tests use). */
+#define SOMA_FLAG_LEARNED_FP32 2
 
 /* Description of one system: a melt of n_chains linear A-B diblock chains.
  * struct_size must be sizeof(soma_system_desc) (ABI versioning). */
@@ -96,7 +100,7 @@ typedef struct soma_system_desc {
   int32_t move;          /* soma_move */
   int32_t set_order;     /* soma_set_order */
   int32_t grid_dtype;    /* soma_grid_dtype: storage type of omega */
-  int32_t flags;         /* 0 or SOMA_FLAG_NO_SORT */
+  int32_t flags;         /* SOMA_FLAG_* bits */
   uint64_t seed;         /* Philox key */
   uint32_t replica_id;   /* Philox counter word 3, low 24 bits */
   uint32_t reserved1;

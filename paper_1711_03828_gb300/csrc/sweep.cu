@@ -484,9 +484,11 @@ static const void* sweep_kernel_ptr(int Q, bool vec, int grid_dtype, bool pair, 
   return vec ? pick_kernel<4, true>(grid_dtype) : pick_kernel<4, false>(grid_dtype);
 }
 
-SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dtype, int move) {
+SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dtype, int move,
+                       bool learned_fp32) {
   SweepShape s;
   s.move = move;
+  s.learned_tc = false;
   s.Q = (N <= 64) ? 1 : (N <= 128 ? 2 : 4);
   s.G = (uint32_t)(64 * s.Q) / N;
   s.n_tiles = (n_chains + s.G - 1) / s.G;
@@ -496,9 +498,14 @@ SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dty
   s.pair = (s.Q == 1) && (N % 2 == 0);
   s.big = n_chains * N >= (1ull << 32) || s.n_tiles >= (1ull << 31);
   s.block = 256;
+  const void* fn = sweep_kernel_ptr(s.Q, s.vec, grid_dtype, s.pair, s.big, s.move);
+  if (move == 2 && s.pair && !s.big && !learned_fp32) {
+    s.learned_tc = true;
+    s.block = 128;
+    fn = learned_tc_kernel_ptr(grid_dtype);
+  }
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel_ptr(s.Q, s.vec, grid_dtype, s.pair, s.big, s.move),
-                                                s.block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, s.block, 0);
   if (per_sm < 1) per_sm = 1;
   const uint64_t warps_per_block = (uint64_t)s.block / 32;
   const uint64_t need = (s.n_tiles + warps_per_block - 1) / warps_per_block;

@@ -8,7 +8,10 @@ alpha is within 1e-3 of the kink of min(1, e^l) are left out (there the FP32
 and FP64 evaluations may take different branches).
 Sweep: one cycle from the same positions and BF16-exact random weights, the
 tolerances of the smart Monte Carlo move (the network and the normals are
-evaluated in FP32 on the GPU, in FP64 in the oracle).
+evaluated in FP32 on the GPU, in FP64 in the oracle), with the FP32 network
+(SOMA_FLAG_LEARNED_FP32).  The tensor-core network (BF16 operands and
+activations) is checked for exactness by brute force and against the FP32
+network by the jump statistics it produces.
 """
 import math
 
@@ -16,7 +19,8 @@ import numpy as np
 import pytest
 
 from oracle import Positions
-from paper_1711_03828_gb300 import MOVE_LEARNED, MOVE_SMC, System, SystemDesc, workloads
+from paper_1711_03828_gb300 import (FLAG_LEARNED_FP32, MOVE_LEARNED, MOVE_SMC, System, SystemDesc,
+                                    workloads)
 from tests.conftest import oracle_system
 from tests.test_gpu_parity import _pos
 from tests.test_gpu_smc import _near_face, _tol
@@ -90,7 +94,7 @@ def test_training_gradient_matches_oracle(cuda_device):
 ])
 def test_learned_one_cycle_matches_oracle(cuda_device, N, n_chains, grid, box):
     d = SystemDesc(n_chains=n_chains, N=N, f=0.5, box_Re=box, grid=grid, chiN=30.0,
-                   kappaN=50.0, move=MOVE_LEARNED, seed=11)
+                   kappaN=50.0, move=MOVE_LEARNED, seed=11, flags=FLAG_LEARNED_FP32)
     W = workloads.random_mlp(5, scale=0.2)
     moves = mism = accepted = 0
     for k, sweep in enumerate((0, 3, 1000)):
@@ -137,14 +141,15 @@ def _pair_probabilities(K, L):
     return _pair_cell_probabilities(K, L, z, z)
 
 
-@pytest.mark.parametrize("move", [0, MOVE_SMC, MOVE_LEARNED])
-def test_gpu_two_particle_balance_brute_force(cuda_device, move):
+@pytest.mark.parametrize("move,flags", [(0, 0), (MOVE_SMC, 0), (MOVE_LEARNED, 0),
+                                        (MOVE_LEARNED, FLAG_LEARNED_FP32)])
+def test_gpu_two_particle_balance_brute_force(cuda_device, move, flags):
     """Dimers with chiN = kappaN = 0 on a periodic 2^3 grid: the visited cell
     pairs follow the exact distribution (erf quadrature) for every move type,
     the learned one with random weights (a strongly asymmetric proposal)."""
     L, Re = 2, 1.5
     d = SystemDesc(n_chains=16384, N=2, f=0.5, box_Re=(L / Re,) * 3, grid=(L,) * 3, chiN=0.0,
-                   kappaN=0.0, move=move, seed=23)
+                   kappaN=0.0, move=move, seed=23, flags=flags)
     s = System(d)
     if move == MOVE_LEARNED:
         s.set_proposal_weights(workloads.random_mlp(7, scale=0.1).astype(np.float32))
@@ -195,8 +200,20 @@ def test_training_increases_the_expected_jump(cuda_device):
     uni.sweep(50)
     msd_u = msd_per_move(uni)
     uni.close()
+    # the same trained weights through the FP32 network
+    W = None
+    f32 = System(workloads.melt_small(chiN=20.0, move=MOVE_LEARNED, flags=FLAG_LEARNED_FP32))
+    s2 = System(d)
+    s2.train_proposal(steps=300, batch=8192, sweeps_between=1, lr=3e-3)
+    W = s2.get_proposal_weights()
+    s2.close()
+    f32.set_proposal_weights(W)
+    f32.sweep(50)
+    msd2 = msd_per_move(f32)
+    f32.close()
     print(f"training: J {log['mean_J_first']:.4f} -> {log['mean_J_last']:.4f}, "
           f"alpha {log['mean_alpha_last']:.3f}; msd/move untrained {msd0:.4f}, "
-          f"trained {msd1:.4f}, uniform {msd_u:.4f}")
+          f"trained {msd1:.4f} (tensor cores) {msd2:.4f} (FP32 network), uniform {msd_u:.4f}")
     assert log["mean_J_last"] > log["mean_J_first"]
     assert msd1 > 1.1 * msd0
+    assert abs(msd1 - msd2) < 0.05 * msd2
