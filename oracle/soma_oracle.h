@@ -126,8 +126,10 @@ void or_sweep_trial(const or_system* s, float* x, float* y, float* z,
  * neighbour interpolated linearly in the position inside the cell), is_A,
  * has_prev, has_next.  Parameters (1604, flat): W1[32][12], b1[32],
  * W2[32][32], b2[32], W3[4][32], b3[4].  There is no counterpart in the paper
- * (SMC is its force-biased proposal, Sec. 2.2); parity of the gradient is
- * pinned by finite differences, exactness of the move by brute force. */
+ * (SMC is its force-biased proposal, Sec. 2.2).  Pins: the forward pass by
+ * a closed form on hand-built weights, the features by a hand-placed chain in
+ * a field with known face differences, the gradient by finite differences,
+ * exactness of the move by brute force. */
 #define OR_MLP_PARAMS 1604
 void or_mlp_forward(const double* W, const double x[12], double out[4]);
 void or_learned_features(const or_system* s, const float* x, const float* y, const float* z,

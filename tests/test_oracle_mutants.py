@@ -73,6 +73,15 @@ MUTANTS = [
      PIN.check_esjd_gradient_matches_finite_differences),
     ("esjd_gradient_logscale_term", "dls += cl * 3.0;", "dls += cl * 2.0;",
      PIN.check_esjd_gradient_matches_finite_differences),
+    ("mlp_second_bias_dropped", "double a = W[L_B2 + j];", "double a = 0.0;",
+     PIN.check_mlp_forward_closed_form),
+    ("mlp_first_layer_transposed", "a += W[L_W1 + 12 * j + k] * x[k];",
+     "a += W[L_W1 + 32 * k + j] * x[k];", PIN.check_mlp_forward_closed_form),
+    ("feature_prev_bond_reversed", "feat[0] = r[0] - x[n]; feat[1] = r[1] - y[n]; feat[2] = r[2] - z[n];",
+     "feat[0] = x[n] - r[0]; feat[1] = y[n] - r[1]; feat[2] = z[n] - r[2];",
+     PIN.check_learned_features_hand_values),
+    ("gradient_interpolation_reversed", "g[d] = (1.0 - t) * lo + t * hi;", "g[d] = t * lo + (1.0 - t) * hi;",
+     PIN.check_learned_features_hand_values),
     ("sort_key_axis", "for (int d = 0; d < 3; ++d) key |= ((b[d] >> bit) & 1u) << (3 * bit + d);",
      "for (int d = 0; d < 3; ++d) key |= ((b[2 - d] >> bit) & 1u) << (3 * bit + d);",
      PIN.check_sort_chains_is_a_spatial_permutation),

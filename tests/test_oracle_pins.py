@@ -489,3 +489,91 @@ def check_esjd_gradient_matches_finite_differences(lib=None):
 
 def test_esjd_gradient_matches_finite_differences(oracle_lib):
     check_esjd_gradient_matches_finite_differences()
+
+
+# --------------------------------------------------------------------------
+# Learned proposal: the network forward pass on hand-built weights whose
+# output has a closed form, o_k = sum_j C_kj |x_j| + 0.75 (k+1) + 0.1 k:
+# layer 1 routes relu(x_j) and relu(-x_j) to separate units and holds 0.5 in
+# eight bias-only units, layer 2 is the identity on the first 24 units and
+# turns one bias unit into relu(2*0.5 - 0.25) = 0.75, layer 3 sums.  A
+# transposed weight matrix, a dropped bias or a missing ReLU changes it.
+# --------------------------------------------------------------------------
+def check_mlp_forward_closed_form(lib=None):
+    import oracle
+    rng = np.random.default_rng(11)
+    C = rng.uniform(0.5, 2.0, (4, 12))
+    W = np.zeros(oracle.MLP_PARAMS)
+    W1 = W[0:384].reshape(32, 12)
+    b1 = W[384:416]
+    W2 = W[416:1440].reshape(32, 32)
+    b2 = W[1440:1472]
+    W3 = W[1472:1600].reshape(4, 32)
+    b3 = W[1600:1604]
+    for j in range(12):
+        W1[j, j] = 1.0
+        W1[12 + j, j] = -1.0
+    b1[24:] = 0.5
+    for j in range(24):
+        W2[j, j] = 1.0
+    W2[24, 24] = 2.0
+    b2[24] = -0.25
+    b2[25:] = -1.0
+    for k in range(4):
+        W3[k, :12] = C[k]
+        W3[k, 12:24] = C[k]
+        W3[k, 24] = k + 1.0
+        b3[k] = 0.1 * k
+    for _ in range(20):
+        x = rng.normal(size=12) * 3.0
+        want = C @ np.abs(x) + 0.75 * np.arange(1, 5) + 0.1 * np.arange(4)
+        got = oracle.mlp_forward(W, x, L=lib)
+        np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+
+
+def test_mlp_forward_closed_form(oracle_lib):
+    check_mlp_forward_closed_form()
+
+
+# --------------------------------------------------------------------------
+# Learned proposal: the features of a hand-placed 3-particle chain in the
+# field omega(c) = 3 cx + cy^2 (8^3 grid), where the face differences are
+# 3 along x (-21 across the periodic seam at cx = 0), 2cy-1 and 2cy+1 along y
+# and 0 along z, so the interpolated gradient is known in closed form.
+# --------------------------------------------------------------------------
+def check_learned_features_hand_values(lib=None):
+    d = SystemDesc(n_chains=1, N=3, f=0.5, box_Re=(8 / 6, 8 / 6, 8 / 6), grid=(8, 8, 8),
+                   chiN=0.0, kappaN=0.0, move=2)
+    s = oracle_system(d, lib)          # N_A = floor(1.5 + 0.5) = 2
+    p = s.empty_positions()
+    R = np.array([[1.25, 2.5, 3.5], [2.0, 2.25, 3.75], [2.5, 3.0, 3.0]], np.float32)
+    p.x[:], p.y[:], p.z[:] = R[:, 0], R[:, 1], R[:, 2]
+    c = np.arange(512)
+    cx, cy = c % 8, (c // 8) % 8
+    w = (3.0 * cx + cy.astype(np.float64) ** 2)
+
+    def grad(r):
+        fx, fy = math.floor(r[0]), math.floor(r[1])
+        tx, ty = r[0] - fx, r[1] - fy
+        lo_x = 3.0 if fx % 8 != 0 else -21.0
+        hi_x = 3.0 if fx % 8 != 7 else -21.0
+        cyy = fy % 8
+        lo_y = cyy ** 2 - ((cyy - 1) % 8) ** 2
+        hi_y = ((cyy + 1) % 8) ** 2 - cyy ** 2
+        return [(1 - tx) * lo_x + tx * hi_x, (1 - ty) * lo_y + ty * hi_y, 0.0]
+
+    cases = [
+        (1, [2.3, 2.75, 3.1], [2.3, 2.75, 3.1] - R[0], R[2] - [2.3, 2.75, 3.1], 1, 1, 1),
+        (0, [0.5, 5.5, 7.9], [0, 0, 0], R[1] - [0.5, 5.5, 7.9], 1, 0, 1),
+        (2, [7.25, 0.75, 1.0], [7.25, 0.75, 1.0] - R[1], [0, 0, 0], 0, 1, 0),
+    ]
+    for i, r, bp, bn, isA, hp, hn in cases:
+        r = np.asarray(r, np.float64)
+        f = s.learned_features(p, w, 0, i, r)
+        want = np.concatenate([np.asarray(bp, np.float64), np.asarray(bn, np.float64), grad(r),
+                               [isA, hp, hn]])
+        np.testing.assert_allclose(f, want, rtol=0, atol=1e-12, err_msg=f"particle {i}")
+
+
+def test_learned_features_hand_values(oracle_lib):
+    check_learned_features_hand_values()
