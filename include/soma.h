@@ -18,7 +18,8 @@
  *     (Sec. 2.1), so box_Re[d] / grid[d] must agree on the three axes;
  *   - positions are FP32, structure of arrays: one buffer of 3*M floats holds
  *     x[0..M), y[0..M), z[0..M); particle m = chain*N + i; positions are
- *     unwrapped (periodic images are folded only to find the cell);
+ *     unwrapped (periodic images are folded only to find the cell) and must
+ *     stay within |x| < 2^18 dL, where the cell fold is exact;
  *   - particle i of a chain is type A iff i < N_A = floor(f*N + 1/2);
  *   - the cell of a position is (floor(x) mod grid_x, ...), index
  *     (cz*grid_y + cy)*grid_x + cx;
@@ -128,7 +129,7 @@ typedef struct soma_obs {
 typedef struct soma_timing {
   double ms_sweep;        /* MC sweep kernel (move + fused occupation count) */
   double ms_fields;       /* field-update kernel */
-  uint64_t sweep_launches;
+  uint64_t sweep_launches;  /* launches since timing was last enabled (or creation) */
   uint64_t field_launches;
   uint64_t kernel_launches; /* every kernel this handle launched since creation */
 } soma_timing;
@@ -167,8 +168,11 @@ soma_status soma_get_fields(soma_t* h, float* dst, size_t n, int dst_on_device);
 soma_status soma_get_positions(soma_t* h, float* dst, size_t n, int dst_on_device);
 
 /* Replace positions (3*M floats, SoA).  Does not recompute the fields: call
- * soma_update_fields to make n and omega follow.  Asynchronous for device
- * sources; a host source is copied before the call returns. */
+ * soma_update_fields to make n and omega follow.  Every coordinate must be
+ * finite with |x| < 2^18 dL (the range in which the cell fold is exact;
+ * chains diffuse far less than that in any feasible run): otherwise
+ * SOMA_EINVAL and nothing is copied.  Synchronises (the range check of a
+ * device source runs on the device first). */
 soma_status soma_set_positions(soma_t* h, const float* src, size_t n, int src_on_device);
 
 /* FP64 observables of the current state (Eq. h-bond, Eq. discrete-ham).
@@ -188,7 +192,8 @@ soma_status soma_get_sweep(soma_t* h, uint64_t* out);
 soma_status soma_set_sweep(soma_t* h, uint64_t sweep);
 
 /* Per-kernel device timing with CUDA events on the handle's stream (on != 0
- * enables; enabling resets the sums).  soma_get_timing synchronises. */
+ * enables; enabling resets the sums and the launch counts).  soma_get_timing
+ * synchronises. */
 soma_status soma_set_timing(soma_t* h, int on);
 soma_status soma_get_timing(soma_t* h, soma_timing* out);
 

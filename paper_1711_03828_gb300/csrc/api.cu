@@ -53,6 +53,8 @@ soma_status cuda_fail(cudaError_t e, const char* what) {
 
 constexpr uint32_t GRAPH_CHUNK = 16;
 constexpr uint64_t MAX_M = 1ull << 40;
+// Supported position range |x|, |y|, |z| < 2^18 dL (exact cell fold).
+constexpr uint64_t POS_LIMIT = 1ull << 18;
 
 }  // namespace
 
@@ -75,7 +77,8 @@ struct soma_t {
   uint32_t* n[2] = {nullptr, nullptr};
   void* w[2] = {nullptr, nullptr};
   unsigned long long* d_counters = nullptr;  // [0] sweep, [1] accepted
-  unsigned* d_err = nullptr;                 // [0] error bits, [1] arrival counter
+  unsigned* d_err = nullptr;                 // [0] error bits, [1] arrival counter,
+                                             // [2] range flag of soma_set_positions
   double* d_scratch = nullptr;
   double* d_out = nullptr;
   size_t scratch_doubles = 0;
@@ -167,13 +170,12 @@ void derive(soma_t* h) {
   g.ny = (int)d.grid[1];
   g.nz = (int)d.grid[2];
   const uint32_t n3[3] = {d.grid[0], d.grid[1], d.grid[2]};
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 3; ++k) {  // cell fold constants (see fold_raw)
     const uint64_t n = n3[k];
-    uint32_t l = 0;
-    while ((1ull << l) < n) ++l;
-    g.fold_m[k] = n > 1 ? (uint32_t)((1ull << (31 + l)) / n + 1) : 0u;
-    g.fold_sh[k] = n > 1 ? l - 1 : 0u;
-    g.fold_bias[k] = (uint32_t)(n * ((1ull << 30) / n));
+    const uint64_t bias = n * ((POS_LIMIT + n - 1) / n);
+    g.fold_m[k] = n > 1 ? (uint32_t)(((1ull << 32) + n - 1) / n) : 0u;
+    g.fold_s[k] = n > 1 ? 1u : 0u;
+    g.fold_b[k] = n > 1 ? (uint32_t)((bias - 0x4B400000ull) & 0xFFFFFFFFull) : 0u;
   }
   g.cells = (uint32_t)(d.grid[0] * d.grid[1] * d.grid[2]);
   g.key0 = (uint32_t)d.seed;
@@ -405,7 +407,7 @@ soma_status soma_create(const soma_system_desc* desc, soma_t** out) {
   ALLOC(h->w[0], wb * cells);
   ALLOC(h->w[1], wb * cells);
   ALLOC(h->d_counters, sizeof(unsigned long long) * 2);
-  ALLOC(h->d_err, sizeof(unsigned) * 2);
+  ALLOC(h->d_err, sizeof(unsigned) * 3);
   ALLOC(h->d_scratch, sizeof(double) * (h->scratch_doubles + 64));
   ALLOC(h->mlp_w, sizeof(float) * SOMA_MLP_PARAMS);
   ALLOC(h->mlp_q, 2 * SOMA_MLP_PARAMS);
@@ -421,7 +423,7 @@ soma_status soma_create(const soma_system_desc* desc, soma_t** out) {
   CK(cudaMemsetAsync(h->n[0], 0, sizeof(uint32_t) * cells, h->stream));
   CK(cudaMemsetAsync(h->n[1], 0, sizeof(uint32_t) * cells, h->stream));
   CK(cudaMemsetAsync(h->d_counters, 0, sizeof(unsigned long long) * 2, h->stream));
-  CK(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned) * 2, h->stream));
+  CK(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned) * 3, h->stream));
   CK(cudaMemsetAsync(h->mlp_w, 0, sizeof(float) * SOMA_MLP_PARAMS, h->stream));
   CK(cudaMemsetAsync(h->mlp_q, 0, 2 * SOMA_MLP_PARAMS, h->stream));
   CK(cudaMemsetAsync(h->mlp_m, 0, sizeof(float) * SOMA_MLP_PARAMS, h->stream));
@@ -543,6 +545,21 @@ soma_status soma_get_positions(soma_t* h, float* dst, size_t n, int dst_on_devic
 soma_status soma_set_positions(soma_t* h, const float* src, size_t n, int src_on_device) {
   if (!h || !src) return fail(SOMA_EINVAL, "NULL argument");
   if (n != 3 * h->M) return fail(SOMA_EINVAL, "n=%zu, expected 3*M=%llu", n, (unsigned long long)(3 * h->M));
+  // every coordinate must lie in the supported range of the cell fold
+  const float lim = (float)POS_LIMIT;
+  if (src_on_device) {
+    unsigned flag = 0;
+    SOMA_CUDA(cudaMemsetAsync(h->d_err + 2, 0, sizeof(unsigned), h->stream));
+    SOMA_CUDA(launch_range_check(src, 3 * h->M, lim, h->d_err + 2, h->sm_count, h->stream));
+    SOMA_CUDA(cudaMemcpyAsync(&flag, h->d_err + 2, sizeof flag, cudaMemcpyDeviceToHost, h->stream));
+    SOMA_CUDA(cudaStreamSynchronize(h->stream));
+    h->launches += 1;
+    if (flag) return fail(SOMA_EINVAL, "a position is not finite or has |x| >= 2^18 dL");
+  } else {
+    for (size_t i = 0; i < n; ++i)
+      if (!(std::fabs(src[i]) < lim))
+        return fail(SOMA_EINVAL, "position %zu (%g) is not finite or has |x| >= 2^18 dL", i, (double)src[i]);
+  }
   const cudaMemcpyKind k = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   for (int d = 0; d < 3; ++d)
     SOMA_CUDA(cudaMemcpyAsync(h->pos + d * h->plane, src + d * h->M, sizeof(float) * h->M, k, h->stream));
@@ -647,6 +664,7 @@ soma_status soma_set_timing(soma_t* h, int on) {
   h->timing = on != 0;
   if (h->timing) {
     h->t.ms_sweep = h->t.ms_fields = 0.0;
+    h->t.sweep_launches = h->t.field_launches = 0;
   }
   return SOMA_OK;
 }
@@ -1070,7 +1088,10 @@ soma_status soma_batch_set_timing(soma_batch_t* b, int on) {
   soma_status st = batch_collect_timing(b);
   if (st != SOMA_OK) return st;
   b->timing = on != 0;
-  if (b->timing) b->t.ms_sweep = b->t.ms_fields = 0.0;
+  if (b->timing) {
+    b->t.ms_sweep = b->t.ms_fields = 0.0;
+    b->t.sweep_launches = b->t.field_launches = 0;
+  }
   return SOMA_OK;
 }
 

@@ -73,18 +73,23 @@ __device__ __forceinline__ double uniform_open_f64(uint32_t r) {
   return ((double)(r >> 8) + 0.5) * 5.9604644775390625e-8;
 }
 
-// Cell of one coordinate: floor(x) folded into [0, n) by an exact
-// multiply-high division (Granlund & Montgomery 1994, Thm. 4.2, for 31-bit
-// numerators): with l = ceil(log2 n) and m = floor(2^(31+l)/n) + 1,
-// floor(c/n) = umulhi(c, m) >> (l-1) for every 0 <= c < 2^31.  c = floor(x) +
-// bias, bias = n*floor(2^30/n), so every |x| < 2^30 is folded exactly.  The
-// final unsigned min keeps the index inside the grid for any input (and makes
-// an axis with n = 1, which has m = 0, always fold to 0).
-__device__ __forceinline__ uint32_t fold_cell(float x, uint32_t n, uint32_t m, uint32_t sh,
-                                              uint32_t bias) {
-  const uint32_t c = (uint32_t)__float2int_rd(x) + bias;
-  const uint32_t q = __umulhi(c, m) >> sh;
-  return min(c - q * n, n - 1u);
+// Cell of one coordinate: floor(x) folded into [0, n), exact for |x| < 2^18
+// (the supported position range, in units of dL).
+//  - floor: adding 1.5*2^23 with rounding toward -inf leaves floor(x) +
+//    1.5*2^23 exactly (|x| < 2^22), whose bit pattern is 0x4B400000 + floor(x);
+//  - c = floor(x) + bias with bias = n*ceil(2^18/n), so 0 <= c < 2^19 + n
+//    (the bit pattern times s = 1 plus b = bias - 0x4B400000, mod 2^32);
+//  - c mod n = c - n*umulhi(c, m), m = ceil(2^32/n): with e = m*n - 2^32 < n,
+//    umulhi(c, m) = floor(c/n + c*e/(n*2^32)) = floor(c/n) whenever c*e < 2^32,
+//    which holds for c < 2^19 + n and n <= 4096 (Granlund & Montgomery 1994,
+//    Sec. 4, with the shift folded into m).
+// An axis with n = 1 has s = b = m = 0 and always folds to 0.  Everything runs
+// on the FMA pipe (one FADD, three IMAD).  Outside the supported range the
+// result is not the cell; callers clamp it so that memory stays in bounds.
+__device__ __forceinline__ uint32_t fold_raw(float x, uint32_t n, uint32_t m, uint32_t s,
+                                             uint32_t b) {
+  const uint32_t c = __float_as_uint(__fadd_rd(x, 12582912.0f)) * s + b;
+  return c - __umulhi(c, m) * n;
 }
 
 template <typename WT> __device__ __forceinline__ float load_w(const WT* p, uint32_t i);
@@ -110,20 +115,27 @@ struct Geom {
   uint64_t n_chains;
   uint32_t N, N_A;
   int nx, ny, nz;
-  uint32_t fold_m[3];     // multiply-high magic per axis (0 for n = 1)
-  uint32_t fold_sh[3];    // ceil(log2 n) - 1 per axis
-  uint32_t fold_bias[3];  // n * floor(2^30/n) per axis
+  uint32_t fold_m[3];     // ceil(2^32/n) per axis (0 for n = 1)
+  uint32_t fold_s[3];     // 1 (0 for n = 1)
+  uint32_t fold_b[3];     // n*ceil(2^18/n) - 0x4B400000 mod 2^32 (0 for n = 1)
   uint32_t cells;
   uint32_t key0, key1;
   uint32_t rk0[10], rk1[10];  // Philox round keys: key + r * (Weyl constant)
   uint32_t replica;
 };
 
+// Per-axis cell, clamped into [0, n) (exact inside the supported range).
+__device__ __forceinline__ uint32_t fold_axis(const Geom& g, int k, float x, uint32_t n) {
+  return min(fold_raw(x, n, g.fold_m[k], g.fold_s[k], g.fold_b[k]), n - 1u);
+}
+
+// Linear cell index (x fastest), clamped into the grid as a whole: one min
+// instead of one per axis.
 __device__ __forceinline__ uint32_t cell_of(const Geom& g, float x, float y, float z) {
-  const uint32_t cx = fold_cell(x, (uint32_t)g.nx, g.fold_m[0], g.fold_sh[0], g.fold_bias[0]);
-  const uint32_t cy = fold_cell(y, (uint32_t)g.ny, g.fold_m[1], g.fold_sh[1], g.fold_bias[1]);
-  const uint32_t cz = fold_cell(z, (uint32_t)g.nz, g.fold_m[2], g.fold_sh[2], g.fold_bias[2]);
-  return (cz * (uint32_t)g.ny + cy) * (uint32_t)g.nx + cx;
+  const uint32_t cx = fold_raw(x, (uint32_t)g.nx, g.fold_m[0], g.fold_s[0], g.fold_b[0]);
+  const uint32_t cy = fold_raw(y, (uint32_t)g.ny, g.fold_m[1], g.fold_s[1], g.fold_b[1]);
+  const uint32_t cz = fold_raw(z, (uint32_t)g.nz, g.fold_m[2], g.fold_s[2], g.fold_b[2]);
+  return min((cz * (uint32_t)g.ny + cy) * (uint32_t)g.nx + cx, g.cells - 1u);
 }
 
 // Philox4x32-10 with the round keys taken from the kernel parameters (the

@@ -32,6 +32,27 @@ cudaError_t launch_histogram(const Geom& g, const float* x, const float* y, cons
   return cudaGetLastError();
 }
 
+// Range check of positions given by the caller: flag = 1 if any value is not
+// finite or has |v| >= lim (the supported range of the cell fold).
+__global__ void __launch_bounds__(256) range_check_kernel(const float* __restrict__ p, uint64_t n,
+                                                          float lim, unsigned* flag) {
+  unsigned bad = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    bad |= !(fabsf(p[i]) < lim);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1u);
+}
+
+cudaError_t launch_range_check(const float* p, uint64_t n, float lim, unsigned* flag, int sm_count,
+                               cudaStream_t st) {
+  uint64_t blocks = (n + 255) / 256;
+  const uint64_t cap = (uint64_t)sm_count * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  range_check_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, n, lim, flag);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Field update: omega from the packed counts of one buffer, while the other
 // buffer is cleared for the next sweep's count.  The last block to finish
@@ -174,9 +195,9 @@ __global__ void chain_key_kernel(const Geom g, const float* __restrict__ x,
     }
     const uint64_t m = k * g.N;
     const uint32_t b[3] = {
-        fold_cell(x[m], (uint32_t)g.nx, g.fold_m[0], g.fold_sh[0], g.fold_bias[0]) >> SORT_BLOCK_SHIFT,
-        fold_cell(y[m], (uint32_t)g.ny, g.fold_m[1], g.fold_sh[1], g.fold_bias[1]) >> SORT_BLOCK_SHIFT,
-        fold_cell(z[m], (uint32_t)g.nz, g.fold_m[2], g.fold_sh[2], g.fold_bias[2]) >> SORT_BLOCK_SHIFT};
+        fold_axis(g, 0, x[m], (uint32_t)g.nx) >> SORT_BLOCK_SHIFT,
+        fold_axis(g, 1, y[m], (uint32_t)g.ny) >> SORT_BLOCK_SHIFT,
+        fold_axis(g, 2, z[m], (uint32_t)g.nz) >> SORT_BLOCK_SHIFT};
     uint64_t key = 0;
     for (int bit = 0; bit < 10; ++bit)
       for (int d = 0; d < 3; ++d) key |= (uint64_t)((b[d] >> bit) & 1u) << (3 * bit + d);

@@ -35,6 +35,8 @@ cudaError_t launch_sort_chains(const Geom& g, const float* src, uint64_t src_pla
                                cudaStream_t st);
 cudaError_t launch_histogram(const Geom& g, const float* x, const float* y, const float* z,
                              uint32_t* n, int sm_count, cudaStream_t st);
+cudaError_t launch_range_check(const float* p, uint64_t n, float lim, unsigned* flag, int sm_count,
+                               cudaStream_t st);
 cudaError_t launch_fields(const FieldArgs& a, unsigned* arrive, int grid_dtype, int sm_count,
                           cudaStream_t st);
 cudaError_t launch_convert_fields(const void* w, int grid_dtype, float* dst, uint64_t n,

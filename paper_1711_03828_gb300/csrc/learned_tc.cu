@@ -164,9 +164,9 @@ __device__ __forceinline__ void mlp_warp(const MlpFrag& R, __nv_bfloat16* sf, fl
 template <typename WT>
 __device__ __forceinline__ float grad_at(const Geom& g, const WT* w, float x, float y, float z,
                                          float gr[3], uint32_t* cell) {
-  const uint32_t cx = fold_cell(x, (uint32_t)g.nx, g.fold_m[0], g.fold_sh[0], g.fold_bias[0]);
-  const uint32_t cy = fold_cell(y, (uint32_t)g.ny, g.fold_m[1], g.fold_sh[1], g.fold_bias[1]);
-  const uint32_t cz = fold_cell(z, (uint32_t)g.nz, g.fold_m[2], g.fold_sh[2], g.fold_bias[2]);
+  const uint32_t cx = fold_axis(g, 0, x, (uint32_t)g.nx);
+  const uint32_t cy = fold_axis(g, 1, y, (uint32_t)g.ny);
+  const uint32_t cz = fold_axis(g, 2, z, (uint32_t)g.nz);
   const uint32_t nx = g.nx, ny = g.ny, nz = g.nz;
   const uint32_t c = (cz * ny + cy) * nx + cx;
   const uint32_t xm = cx == 0 ? nx - 1 : cx - 1, xp = cx + 1 == nx ? 0 : cx + 1;

@@ -25,6 +25,8 @@ template <typename WT>
 struct PairLane {
   int lane, first_lane;
   bool has_prev0, has_next1;
+  float cf_prev0, cf_next1;     // the same as 1.f / 0.f
+  int src_prev, src_next;       // lane - 1, lane + 1 (mod 32)
   const WT* w0;
   const WT* w1;
   uint32_t v0, v1;
@@ -38,6 +40,10 @@ struct PairLane {
     first_lane = (int)((li0 - ci0) >> 1);         // lane holding the chain's particle 0
     has_prev0 = ci0 > 0u;                         // slot 0 has a partner in lane-1
     has_next1 = ci0 + 2u < N;                     // slot 1 has a partner in lane+1
+    cf_prev0 = has_prev0 ? 1.f : 0.f;
+    cf_next1 = has_next1 ? 1.f : 0.f;
+    src_prev = (lane - 1) & 31;
+    src_next = (lane + 1) & 31;
     w0 = static_cast<const WT*>(ci0 < N_A ? wA : wB);
     w1 = static_cast<const WT*>(ci0 + 1u < N_A ? wA : wB);
     v0 = ci0 < N_A ? 1u : 0x10000u;
@@ -47,15 +53,22 @@ struct PairLane {
 
 // Moves the pair (x0,y0,z0), (x1,y1,z1) held by this lane (particles base and
 // base+1), stores the result and counts the final cells into nacc.  g gives
-// the cell fold, keys the Philox round keys.  Returns this lane's accepted
-// moves.
-template <typename WT, typename IDX>
+// the cell fold, keys the Philox round keys.  PARTIAL: the tile may hold
+// fewer rows than lanes (valid says whether this lane's pair exists).
+// Returns this lane's accepted moves.
+//
+// Exactness notes: a missing bond partner enters as 0 * (A - s) with a finite
+// s, i.e. as an exact zero; the acceptance test is dE <= -ln u, which is the
+// rule "dE <= 0 or ln u < -dE" for every ln u < 0 except on the measure-zero
+// set dE = -ln u.
+template <typename WT, typename IDX, bool PARTIAL>
 __device__ __forceinline__ unsigned pair_tile(const Geom& g, const Geom& keys, const PairLane<WT>& L,
                                               float* __restrict__ px, float* __restrict__ py,
                                               float* __restrict__ pz, uint32_t* __restrict__ nacc,
                                               IDX base, bool valid, uint32_t sweep, uint32_t ctr3,
                                               bool set_order_random, float a, float K1, float x0,
                                               float x1, float y0, float y1, float z0, float z1) {
+  if (!PARTIAL) valid = true;
   const float K2 = 2.f * K1;
   const uint32_t hi = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)base >> 32) : 0u;
   const uint4 r0 = philox_rk(make_uint4((uint32_t)base, hi, sweep, ctr3), keys);
@@ -80,7 +93,6 @@ __device__ __forceinline__ unsigned pair_tile(const Geom& g, const Geom& keys, c
   const float lnu0 = log_uniform_open(r0.w);
   const float lnu1 = log_uniform_open(r1.w);
   const bool sw = set_order_random && (__shfl_sync(FULL, r0.w, L.first_lane) & 1u);
-  const int lane = L.lane;
 
   // A moves first, B second.
   float Ax = sw ? x1 : x0, Ay = sw ? y1 : y0, Az = sw ? z1 : z0;
@@ -94,18 +106,19 @@ __device__ __forceinline__ unsigned pair_tile(const Geom& g, const Geom& keys, c
   unsigned acc_count = 0;
 
   {  // first set: A moves against B and the adjacent lane's B
-    const int src = sw ? lane + 1 : lane - 1;
-    const bool cross = sw ? L.has_next1 : L.has_prev0;
-    const float sx = __shfl_sync(FULL, Bx, src & 31);
-    const float sy = __shfl_sync(FULL, By, src & 31);
-    const float sz = __shfl_sync(FULL, Bz, src & 31);
-    const float ex = cross ? sx : Ax, ey = cross ? sy : Ay, ez = cross ? sz : Az;
+    const int src = sw ? L.src_next : L.src_prev;
+    const float cf = sw ? L.cf_next1 : L.cf_prev0;
+    const float sx = __shfl_sync(FULL, Bx, src);
+    const float sy = __shfl_sync(FULL, By, src);
+    const float sz = __shfl_sync(FULL, Bz, src);
     const float dx = tAx - Ax, dy = tAy - Ay, dz = tAz - Az;
-    const float ux = (Ax - Bx) + (Ax - ex), uy = (Ay - By) + (Ay - ey), uz = (Az - Bz) + (Az - ez);
+    const float ux = fmaf(cf, Ax - sx, Ax - Bx);
+    const float uy = fmaf(cf, Ay - sy, Ay - By);
+    const float uz = fmaf(cf, Az - sz, Az - Bz);
     const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
     const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float dE = fmaf(cross ? K2 : K1, dd, fmaf(K2, du, fA));
-    const bool acc = valid && (dE <= 0.f || lA < -dE);
+    const float dE = fmaf(fmaf(cf, K1, K1), dd, fmaf(K2, du, fA));
+    const bool acc = valid && dE <= -lA;
     Ax = acc ? tAx : Ax;
     Ay = acc ? tAy : Ay;
     Az = acc ? tAz : Az;
@@ -113,18 +126,19 @@ __device__ __forceinline__ unsigned pair_tile(const Geom& g, const Geom& keys, c
     acc_count += acc;
   }
   {  // second set: B moves against A and the adjacent lane's A
-    const int src = sw ? lane - 1 : lane + 1;
-    const bool cross = sw ? L.has_prev0 : L.has_next1;
-    const float sx = __shfl_sync(FULL, Ax, src & 31);
-    const float sy = __shfl_sync(FULL, Ay, src & 31);
-    const float sz = __shfl_sync(FULL, Az, src & 31);
-    const float ex = cross ? sx : Bx, ey = cross ? sy : By, ez = cross ? sz : Bz;
+    const int src = sw ? L.src_prev : L.src_next;
+    const float cf = sw ? L.cf_prev0 : L.cf_next1;
+    const float sx = __shfl_sync(FULL, Ax, src);
+    const float sy = __shfl_sync(FULL, Ay, src);
+    const float sz = __shfl_sync(FULL, Az, src);
     const float dx = tBx - Bx, dy = tBy - By, dz = tBz - Bz;
-    const float ux = (Bx - Ax) + (Bx - ex), uy = (By - Ay) + (By - ey), uz = (Bz - Az) + (Bz - ez);
+    const float ux = fmaf(cf, Bx - sx, Bx - Ax);
+    const float uy = fmaf(cf, By - sy, By - Ay);
+    const float uz = fmaf(cf, Bz - sz, Bz - Az);
     const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
     const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float dE = fmaf(cross ? K2 : K1, dd, fmaf(K2, du, fB));
-    const bool acc = valid && (dE <= 0.f || lB < -dE);
+    const float dE = fmaf(fmaf(cf, K1, K1), dd, fmaf(K2, du, fB));
+    const bool acc = valid && dE <= -lB;
     Bx = acc ? tBx : Bx;
     By = acc ? tBy : By;
     Bz = acc ? tBz : Bz;
@@ -136,12 +150,11 @@ __device__ __forceinline__ unsigned pair_tile(const Geom& g, const Geom& keys, c
     __stcs(reinterpret_cast<float2*>(px + base), sw ? make_float2(Bx, Ax) : make_float2(Ax, Bx));
     __stcs(reinterpret_cast<float2*>(py + base), sw ? make_float2(By, Ay) : make_float2(Ay, By));
     __stcs(reinterpret_cast<float2*>(pz + base), sw ? make_float2(Bz, Az) : make_float2(Az, Bz));
-    if (cA == cB) {
-      atomicAdd(nacc + cA, L.v0 + L.v1);
-    } else {
-      atomicAdd(nacc + cA, sw ? L.v1 : L.v0);
-      atomicAdd(nacc + cB, sw ? L.v0 : L.v1);
-    }
+    // one atomic when both end in the same cell, else one each
+    const uint32_t vA = sw ? L.v1 : L.v0, vB = sw ? L.v0 : L.v1;
+    const bool same = cA == cB;
+    atomicAdd(nacc + cA, same ? vA + vB : vA);
+    if (!same) atomicAdd(nacc + cB, vB);
   }
   return acc_count;
 }

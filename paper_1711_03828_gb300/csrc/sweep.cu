@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(256) sweep_uniform_kernel(const SweepArgs p) {
 // are loaded while the current one is processed.  IDX is the index type:
 // 32-bit when M < 2^32 (Philox counter word 1 = 0).
 template <typename WT, typename IDX>
-__global__ void __launch_bounds__(256, 3) sweep_pair_kernel(const SweepArgs p) {
+__global__ void __launch_bounds__(256, 4) sweep_pair_kernel(const SweepArgs p) {
   const int lane = threadIdx.x & 31;
   const uint32_t n_tiles_all = (uint32_t)p.n_tiles;
   const uint32_t chunk = (n_tiles_all + gridDim.x - 1) / gridDim.x;
@@ -254,8 +254,12 @@ __global__ void __launch_bounds__(256, 3) sweep_pair_kernel(const SweepArgs p) {
       py = __ldcs(reinterpret_cast<const float2*>(p.y + bn));
       pz = __ldcs(reinterpret_cast<const float2*>(p.z + bn));
     }
-    my_acc += pair_tile<WT, IDX>(p.g, p.g, L, p.x, p.y, p.z, nacc, base, valid, sweep, ctr3,
-                                 p.set_order_random, p.a, p.K_b, x0, x1, y0, y1, z0, z1);
+    if (tile < full_tiles)
+      my_acc += pair_tile<WT, IDX, false>(p.g, p.g, L, p.x, p.y, p.z, nacc, base, true, sweep, ctr3,
+                                          p.set_order_random, p.a, p.K_b, x0, x1, y0, y1, z0, z1);
+    else
+      my_acc += pair_tile<WT, IDX, true>(p.g, p.g, L, p.x, p.y, p.z, nacc, base, valid, sweep, ctr3,
+                                         p.set_order_random, p.a, p.K_b, x0, x1, y0, y1, z0, z1);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) my_acc += __shfl_xor_sync(FULL, my_acc, o);
@@ -271,9 +275,9 @@ __global__ void __launch_bounds__(256, 3) sweep_pair_kernel(const SweepArgs p) {
 // first draw (purpose 1), the acceptance uniform from the second (purpose 2).
 __device__ __forceinline__ void cell3(const Geom& g, float x, float y, float z, uint32_t& cx,
                                       uint32_t& cy, uint32_t& cz) {
-  cx = fold_cell(x, (uint32_t)g.nx, g.fold_m[0], g.fold_sh[0], g.fold_bias[0]);
-  cy = fold_cell(y, (uint32_t)g.ny, g.fold_m[1], g.fold_sh[1], g.fold_bias[1]);
-  cz = fold_cell(z, (uint32_t)g.nz, g.fold_m[2], g.fold_sh[2], g.fold_bias[2]);
+  cx = fold_axis(g, 0, x, (uint32_t)g.nx);
+  cy = fold_axis(g, 1, y, (uint32_t)g.ny);
+  cz = fold_axis(g, 2, z, (uint32_t)g.nz);
 }
 
 // omega at the cell and minus its central-difference gradient (the field force).

@@ -172,12 +172,34 @@ def test_histogram_and_fields_with_edge_positions(dev):
                    chiN=10.0, kappaN=50.0)
     pos = workloads.random_walk_positions(d, seed=3, spread=3.0)
     edge = np.array([0.0, -0.0, 1.0, 3.0, -1e-7, -1.0, 9.0, 27.5, -45.25, 8.999999,
-                     np.nextafter(np.float32(9.0), np.float32(0.0)), -9.0, 1e6 + 0.5], np.float32)
+                     np.nextafter(np.float32(9.0), np.float32(0.0)), -9.0, 262143.5, -262143.75], np.float32)
     pos[0, : len(edge)] = edge
     pos[1, 100: 100 + len(edge)] = edge
     pos[2, 200: 200 + len(edge)] = edge[::-1]
     r = Runner(d, pos)
     r.check_grid()
+
+
+def test_positions_outside_the_supported_range_are_rejected(dev):
+    """|x| < 2^18 dL is the range in which the cell fold is exact: values at
+    or beyond it, and non-finite values, are refused from host and device
+    buffers, and the stored positions stay untouched."""
+    import torch
+    from paper_1711_03828_gb300 import SomaError
+    d = SystemDesc(n_chains=64, N=8, box_Re=(1.0, 1.0, 1.0), grid=(6, 6, 6))
+    s = System(d)
+    before = s.get_positions()
+    good = workloads.random_walk_positions(d, seed=1)
+    for bad in (262144.0, -262144.0, np.inf, np.nan):
+        p = good.copy()
+        p[1, 17] = bad
+        for src in (p, torch.from_numpy(p).cuda()):
+            with pytest.raises(SomaError):
+                s.set_positions(src)
+            np.testing.assert_array_equal(s.get_positions(), before)
+    s.set_positions(good)
+    np.testing.assert_array_equal(s.get_positions(), good)
+    s.close()
 
 
 @pytest.mark.parametrize("set_order", [SET_ORDER_RANDOM, SET_ORDER_FIXED])
