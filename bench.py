@@ -203,6 +203,18 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+def kernel_source_hash():
+    """sha256 over the sources of the sweep kernel (sweep.cu, pair_body.cuh,
+    common.cuh), so that a stored traffic figure is used only while the
+    kernel it was taken on is unchanged."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("sweep.cu", "pair_body.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1711_03828_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def measured_traffic(workload_name):
     """DRAM bytes per sweep launch from the committed ncu capture, if it was
     taken on this workload with the sweep kernel source as it is now."""
@@ -210,10 +222,8 @@ def measured_traffic(workload_name):
     try:
         with open(os.path.join(ROOT, "profiles", f"sweep_traffic_{workload_name}.json")) as f:
             t = json.load(f)
-        src = os.path.join(ROOT, "paper_1711_03828_gb300", "csrc", "sweep.cu")
-        with open(src, "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != t["sweep_cu_sha256"]:
-                return None
+        if kernel_source_hash() != t["kernel_src_sha256"]:
+            return None
         return t["dram_bytes_read"] + t["dram_bytes_write"]
     except (OSError, KeyError, ValueError):
         return None

@@ -125,8 +125,11 @@ struct Geom {
 };
 
 // Per-axis cell, clamped into [0, n) (exact inside the supported range).
+// The clamp already sends an n = 1 axis to 0, so the bias is added without
+// the multiplier s (an integer add instead of a multiply-add).
 __device__ __forceinline__ uint32_t fold_axis(const Geom& g, int k, float x, uint32_t n) {
-  return min(fold_raw(x, n, g.fold_m[k], g.fold_s[k], g.fold_b[k]), n - 1u);
+  const uint32_t c = __float_as_uint(__fadd_rd(x, 12582912.0f)) + g.fold_b[k];
+  return min(c - __umulhi(c, g.fold_m[k]) * n, n - 1u);
 }
 
 // Linear cell index (x fastest), clamped into the grid as a whole: one min

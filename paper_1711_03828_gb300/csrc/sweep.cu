@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(256) sweep_uniform_kernel(const SweepArgs p) {
 // are loaded while the current one is processed.  IDX is the index type:
 // 32-bit when M < 2^32 (Philox counter word 1 = 0).
 template <typename WT, typename IDX>
-__global__ void __launch_bounds__(256, 4) sweep_pair_kernel(const SweepArgs p) {
+__global__ void __launch_bounds__(256, 3) sweep_pair_kernel(const SweepArgs p) {
   const int lane = threadIdx.x & 31;
   const uint32_t n_tiles_all = (uint32_t)p.n_tiles;
   const uint32_t chunk = (n_tiles_all + gridDim.x - 1) / gridDim.x;
