@@ -38,6 +38,9 @@ def parse():
                              "batch64", "decorrelation"])
     ap.add_argument("--move", default="uniform", choices=["uniform", "smc", "learned"],
                     help="trial moves: uniform displacement or smart Monte Carlo")
+    ap.add_argument("--learned-net", default="mma_sync", choices=["mma_sync", "umma", "fp32"],
+                    help="network evaluator of the learned move: warp-level mma.sync (default), "
+                         "tcgen05 with the accumulator in tensor memory, or FP32 on the CUDA cores")
     ap.add_argument("--grid-dtype", default="f32", choices=["f32", "bf16", "f16"],
                     help="storage type of the omega grids (energies stay FP32)")
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -54,12 +57,13 @@ def dist_env():
 GRID_DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
 
 
-def workload(name, replica=0, grid_dtype="f32", move="uniform"):
+def workload(name, replica=0, grid_dtype="f32", move="uniform", learned_net="mma_sync"):
     from paper_1711_03828_gb300 import workloads
     d = getattr(workloads, name)(seed=1)
     d.replica_id = replica
     d.grid_dtype = GRID_DTYPES[grid_dtype]
     d.move = {"uniform": 0, "smc": 1, "learned": 2}[move]
+    d.flags |= {"mma_sync": 0, "umma": 4, "fp32": 2}[learned_net] if d.move == 2 else 0
     return d
 
 
@@ -229,6 +233,18 @@ def measured_traffic(workload_name):
         return None
 
 
+def sweep_kernel_name(d):
+    """The sweep kernel libsoma launches for this description."""
+    pair = d.N % 2 == 0 and d.N <= 64
+    if d.move == 1:
+        return "sweep_smc_kernel"
+    if d.move == 2:
+        if not pair or d.flags & 2:
+            return "sweep_learned_kernel"
+        return "sweep_learned_umma_kernel" if d.flags & 4 else "sweep_learned_tc_kernel"
+    return "sweep_pair_kernel" if pair else "sweep_uniform_kernel"
+
+
 def sweep_kernel_bytes(d):
     """Algorithmic bytes of one sweep-kernel launch: every position read and
     written once (24 B per particle), each omega plane read once and the
@@ -254,7 +270,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     from paper_1711_03828_gb300 import System, _abi
 
-    d = workload(args.workload, replica=rank, grid_dtype=args.grid_dtype, move=args.move)
+    d = workload(args.workload, replica=rank, grid_dtype=args.grid_dtype, move=args.move,
+                 learned_net=args.learned_net)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     s = System(d, stream=stream)
@@ -333,9 +350,7 @@ def run_ours(args):
         "config": config_of(d, args.workload,
                             f"inputs larger than L2 ({12 * d.M / 1e9:.2f} GB of positions)"),
         "roofline": {"bound": "hbm",
-                     "kernel": {1: "sweep_smc_kernel", 2: "sweep_learned_kernel"}.get(
-                         d.move, "sweep_pair_kernel" if d.N % 2 == 0 and d.N <= 64
-                         else "sweep_uniform_kernel"),
+                     "kernel": sweep_kernel_name(d),
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": measured_traffic(args.workload)
                      if args.grid_dtype == "f32" and args.move == "uniform" else None,

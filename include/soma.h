@@ -80,9 +80,15 @@ typedef enum { SOMA_GRID_F32 = 0, SOMA_GRID_BF16 = 1, SOMA_GRID_F16 = 2 } soma_g
  * SOMA_FLAG_NO_SORT keeps the drawing order (chain k = k-th draw). */
 #define SOMA_FLAG_NO_SORT 1
 /* The learned proposal's network runs on the tensor cores (BF16 operands and
- * activations, FP32 accumulation) for even N <= 64; this flag evaluates it on
- * the CUDA cores in FP32 instead (the precision the parity tests use). */
+ * activations, FP32 accumulation) for even N <= 64: by default as warp-level
+ * mma.sync products (32 feature rows per warp, weights held in registers).
+ * SOMA_FLAG_LEARNED_UMMA evaluates it as one tcgen05.mma product per layer
+ * over a 4-warp block's 128 rows with the accumulator in tensor memory
+ * (correct, but slower here: the block's warps must meet for every one of the
+ * twelve dependent products of a tile).  SOMA_FLAG_LEARNED_FP32 evaluates it
+ * on the CUDA cores in FP32 (the precision the parity tests use). */
 #define SOMA_FLAG_LEARNED_FP32 2
+#define SOMA_FLAG_LEARNED_UMMA 4
 
 /* Description of one system: a melt of n_chains linear A-B diblock chains.
  * struct_size must be sizeof(soma_system_desc) (ABI versioning). */

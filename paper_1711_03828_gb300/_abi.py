@@ -20,6 +20,7 @@ SET_ORDER_RANDOM, SET_ORDER_FIXED = 0, 1
 GRID_F32, GRID_BF16, GRID_F16 = 0, 1, 2
 FLAG_NO_SORT = 1
 FLAG_LEARNED_FP32 = 2
+FLAG_LEARNED_UMMA = 4
 
 
 class SomaSystemDesc(ctypes.Structure):

@@ -142,7 +142,7 @@ soma_status validate(const soma_system_desc* d) {
     return fail(SOMA_EINVAL, "set_order=%d unknown", d->set_order);
   if (d->grid_dtype < 0 || d->grid_dtype > 2)
     return fail(SOMA_EINVAL, "grid_dtype=%d unknown", d->grid_dtype);
-  if (d->flags & ~(SOMA_FLAG_NO_SORT | SOMA_FLAG_LEARNED_FP32))
+  if (d->flags & ~(SOMA_FLAG_NO_SORT | SOMA_FLAG_LEARNED_FP32 | SOMA_FLAG_LEARNED_UMMA))
     return fail(SOMA_EINVAL, "unknown flags 0x%x", d->flags);
   if (d->replica_id > 0xFFFFFFu) return fail(SOMA_EINVAL, "replica_id must be < 2^24");
   return SOMA_OK;
@@ -252,6 +252,7 @@ SweepArgs sweep_args(soma_t* h) {
   s.smc_s2A = (float)std::sqrt(2.0 * A);
   s.smc_inv4A = (float)(1.0 / (4.0 * A));
   s.learned_sigma0 = (float)(h->a64 / std::sqrt(3.0));
+  s.err = h->d_err;
   return s;
 }
 
@@ -417,7 +418,8 @@ soma_status soma_create(const soma_system_desc* desc, soma_t** out) {
 #undef ALLOC
   h->d_out = h->d_scratch + h->scratch_doubles;
   h->shape = sweep_shape(h->g.n_chains, h->g.N, h->sm_count, h->grid_dtype, desc->move,
-                         (desc->flags & SOMA_FLAG_LEARNED_FP32) != 0);
+                         (desc->flags & SOMA_FLAG_LEARNED_FP32) != 0,
+                         (desc->flags & SOMA_FLAG_LEARNED_UMMA) != 0);
   h->plain_shape = sweep_shape(h->g.n_chains, h->g.N, h->sm_count, h->grid_dtype, SOMA_MOVE_UNIFORM);
 #define CK(call) do { e = (call); if (e != cudaSuccess) { release(h); return cuda_fail(e, #call); } } while (0)
   CK(cudaMemsetAsync(h->n[0], 0, sizeof(uint32_t) * cells, h->stream));

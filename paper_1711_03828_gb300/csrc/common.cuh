@@ -176,6 +176,7 @@ struct SweepArgs {
   // smart Monte Carlo: A = a^2/6, sqrt(2A), 1/(4A)
   float smc_A, smc_s2A, smc_inv4A;
   float learned_sigma0;     // a/sqrt(3): scale of the learned proposal
+  unsigned* err;            // sticky error bits (a bounded wait that gave up)
 };
 
 // Training of the learned proposal: one expected-squared-jump sample per thread.

@@ -16,12 +16,13 @@ struct SweepShape {
   bool big;   // 64-bit particle indices (M >= 2^32)
   int move;   // 0 uniform, 1 smart Monte Carlo, 2 learned
   bool learned_tc;  // learned move with the network on the tensor cores
+  bool learned_umma;  // ... through tcgen05 (else warp-level mma.sync)
   int block;
   int grid;
 };
 
 SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dtype, int move,
-                       bool learned_fp32 = false);
+                       bool learned_fp32 = false, bool learned_umma = false);
 cudaError_t launch_sweep_uniform(const SweepArgs& a, const SweepShape& s, int grid_dtype,
                                  cudaStream_t st);
 
@@ -75,7 +76,7 @@ cudaError_t launch_adam(float* w, float* m, float* v, const float* grad, void* w
                         float b1, float b2, float eps, int step, float inv_n, cudaStream_t st);
 cudaError_t launch_quantize(const float* w, void* wq, cudaStream_t st);
 const void* learned_kernel_ptr(int Q, int grid_dtype);
-const void* learned_tc_kernel_ptr(int grid_dtype);
+const void* learned_tc_kernel_ptr(int grid_dtype, bool umma);
 
 // Entry-point helpers implemented in api.cu (messages go to soma_last_error).
 }  // namespace soma

@@ -238,7 +238,8 @@ const void* learned_kernel_ptr(int Q, int grid_dtype) {
 cudaError_t launch_sweep_learned(const SweepArgs& a, const SweepShape& s, int grid_dtype,
                                  const void* wq, cudaStream_t st) {
   void* args[] = {const_cast<SweepArgs*>(&a), const_cast<void**>(&wq)};
-  const void* fn = s.learned_tc ? learned_tc_kernel_ptr(grid_dtype) : learned_kernel_ptr(s.Q, grid_dtype);
+  const void* fn = s.learned_tc ? learned_tc_kernel_ptr(grid_dtype, s.learned_umma)
+                                : learned_kernel_ptr(s.Q, grid_dtype);
   return cudaLaunchKernel(fn, dim3(s.grid), dim3(s.block), args, 0, st);
 }
 

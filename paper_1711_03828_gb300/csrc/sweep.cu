@@ -489,10 +489,11 @@ static const void* sweep_kernel_ptr(int Q, bool vec, int grid_dtype, bool pair, 
 }
 
 SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dtype, int move,
-                       bool learned_fp32) {
+                       bool learned_fp32, bool learned_umma) {
   SweepShape s;
   s.move = move;
   s.learned_tc = false;
+  s.learned_umma = false;
   s.Q = (N <= 64) ? 1 : (N <= 128 ? 2 : 4);
   s.G = (uint32_t)(64 * s.Q) / N;
   s.n_tiles = (n_chains + s.G - 1) / s.G;
@@ -505,8 +506,9 @@ SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dty
   const void* fn = sweep_kernel_ptr(s.Q, s.vec, grid_dtype, s.pair, s.big, s.move);
   if (move == 2 && s.pair && !s.big && !learned_fp32) {
     s.learned_tc = true;
+    s.learned_umma = learned_umma;
     s.block = 128;
-    fn = learned_tc_kernel_ptr(grid_dtype);
+    fn = learned_tc_kernel_ptr(grid_dtype, s.learned_umma);
   }
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, s.block, 0);

@@ -47,7 +47,7 @@ def test_invalid_geometry_is_rejected_without_gpu(soma_lib, mutate):
     if mutate == "struct_size":
         c.struct_size = 8
     elif mutate == "flags":
-        c.flags = 6
+        c.flags = 8
     elif mutate == "box":
         c.box_Re[1] = -1.0
     elif mutate == "grid":

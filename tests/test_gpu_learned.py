@@ -19,8 +19,8 @@ import numpy as np
 import pytest
 
 from oracle import Positions
-from paper_1711_03828_gb300 import (FLAG_LEARNED_FP32, MOVE_LEARNED, MOVE_SMC, System, SystemDesc,
-                                    workloads)
+from paper_1711_03828_gb300 import (FLAG_LEARNED_FP32, FLAG_LEARNED_UMMA, MOVE_LEARNED,
+                                    MOVE_SMC, System, SystemDesc, workloads)
 from tests.conftest import oracle_system
 from tests.test_gpu_parity import _pos
 from tests.test_gpu_smc import _near_face, _tol
@@ -135,6 +135,43 @@ def test_learned_one_cycle_matches_oracle(cuda_device, N, n_chains, grid, box):
     assert mism <= max(3, 5e-4 * moves)
 
 
+@pytest.mark.parametrize("N,n_chains", [(32, 1000), (2, 4099), (64, 257)])
+def test_tcgen05_network_matches_mma_sync_network(cuda_device, N, n_chains):
+    """The tcgen05 evaluator (one M = 128 product per layer over a 4-warp
+    block, accumulator in tensor memory) and the warp-level mma.sync evaluator
+    take the same BF16 operands and accumulate in FP32; only the summation
+    order inside the tensor cores differs.  One cycle from the same state and
+    weights: every decision agrees except at near-ties, and every position
+    agrees to 2e-6 dL (a few FP32 ulps of the network output).  Chain counts
+    leave ragged last tiles and blocks with fewer than four tiles."""
+    box = (2.0, 2.0, 1.5) if N > 2 else (1.0, 1.0, 1.0)
+    grid = (12, 12, 9) if N > 2 else (6, 6, 6)
+    W = workloads.random_mlp(9, scale=0.2).astype(np.float32)
+    out = []
+    for flags in (FLAG_LEARNED_UMMA, 0):
+        d = SystemDesc(n_chains=n_chains, N=N, f=0.5, box_Re=box, grid=grid, chiN=30.0,
+                       kappaN=50.0, move=MOVE_LEARNED, seed=13, flags=flags)
+        pos0 = workloads.random_walk_positions(d, seed=77)
+        s = System(d)
+        s.set_proposal_weights(W)
+        s.set_positions(pos0)
+        s.update_fields()
+        s.sweep(1)
+        out.append((pos0, s.get_positions(), s.observables()["accepted"]))
+        s.close()
+    (p0, a, na), (_, b, nb) = out
+    moved_a, moved_b = np.any(a != p0, axis=0), np.any(b != p0, axis=0)
+    differ = np.nonzero(moved_a != moved_b)[0]
+    close = np.all(np.abs(a.astype(np.float64) - b) <= 2e-6 * np.maximum(1.0, np.abs(a)), axis=0)
+    print(f"N={N}: {a.shape[1]} moves, accepted {na} / {nb}, decisions differ {len(differ)}, "
+          f"positions beyond 2e-6: {int((~close).sum())}")
+    assert len(differ) <= max(2, 2e-4 * a.shape[1])
+    # a different decision changes that particle and, through its new position,
+    # at most the later move of its bonded partners
+    assert (~close).sum() <= 3 * len(differ) + max(2, 2e-4 * a.shape[1])
+    assert na > 0.05 * a.shape[1]
+
+
 def _pair_probabilities(K, L):
     from tests.test_oracle_pins import _pair_cell_probabilities
     z = np.zeros(L**3)
@@ -142,6 +179,7 @@ def _pair_probabilities(K, L):
 
 
 @pytest.mark.parametrize("move,flags", [(0, 0), (MOVE_SMC, 0), (MOVE_LEARNED, 0),
+                                        (MOVE_LEARNED, FLAG_LEARNED_UMMA),
                                         (MOVE_LEARNED, FLAG_LEARNED_FP32)])
 def test_gpu_two_particle_balance_brute_force(cuda_device, move, flags):
     """Dimers with chiN = kappaN = 0 on a periodic 2^3 grid: the visited cell
