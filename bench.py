@@ -237,7 +237,7 @@ def sweep_kernel_name(d):
     """The sweep kernel libsoma launches for this description."""
     pair = d.N % 2 == 0 and d.N <= 64
     if d.move == 1:
-        return "sweep_smc_kernel"
+        return "sweep_smc_pair_kernel" if pair else "sweep_smc_kernel"
     if d.move == 2:
         if not pair or d.flags & 2:
             return "sweep_learned_kernel"
