@@ -523,7 +523,7 @@ __device__ __forceinline__ bool smc_move(const SweepArgs& p, const WT* wt, SmcSl
 }
 
 template <typename WT>
-__global__ void __launch_bounds__(256) sweep_smc_pair_kernel(const SweepArgs p) {
+__global__ void __launch_bounds__(256, 3) sweep_smc_pair_kernel(const SweepArgs p) {
   const int lane = threadIdx.x & 31;
   const uint32_t n_tiles_all = (uint32_t)p.n_tiles;
   const uint32_t chunk = (n_tiles_all + gridDim.x - 1) / gridDim.x;
