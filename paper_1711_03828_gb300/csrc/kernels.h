@@ -77,6 +77,8 @@ cudaError_t launch_adam(float* w, float* m, float* v, const float* grad, void* w
 cudaError_t launch_quantize(const float* w, void* wq, cudaStream_t st);
 const void* learned_kernel_ptr(int Q, int grid_dtype);
 const void* learned_tc_kernel_ptr(int grid_dtype, bool umma);
+// smart Monte Carlo sweep kernel: paired layout (even N <= 64, 32-bit indices) or general
+const void* smc_kernel_ptr(int Q, bool pair, int grid_dtype);
 
 // Entry-point helpers implemented in api.cu (messages go to soma_last_error).
 }  // namespace soma

@@ -266,338 +266,6 @@ __global__ void __launch_bounds__(256, 3) sweep_pair_kernel(const SweepArgs p) {
   if (lane == 0 && my_acc) atomicAdd(p.acc, (unsigned long long)my_acc);
 }
 
-// ---------------------------------------------------------------------------
-// Smart Monte Carlo (force-biased) step, any N (the tiling of
-// sweep_uniform_kernel).  Trial move dr = A F(r) + sqrt(2A) xi, F = bonded
-// force minus the central-difference gradient of omega_t over the six
-// neighbouring cells; accepted with min(1, exp(-dE) T(r'->r)/T(r->r')),
-// T(r->r') = exp(-|r'-r-A F(r)|^2/(4A)).  Normals by Box-Muller from the
-// first draw (purpose 1), the acceptance uniform from the second (purpose 2).
-__device__ __forceinline__ void cell3(const Geom& g, float x, float y, float z, uint32_t& cx,
-                                      uint32_t& cy, uint32_t& cz) {
-  cx = fold_axis(g, 0, x, (uint32_t)g.nx);
-  cy = fold_axis(g, 1, y, (uint32_t)g.ny);
-  cz = fold_axis(g, 2, z, (uint32_t)g.nz);
-}
-
-// omega at the cell and minus its central-difference gradient (the field force).
-template <typename WT>
-__device__ __forceinline__ float field_and_force(const Geom& g, const WT* w, uint32_t cx, uint32_t cy,
-                                                 uint32_t cz, float& fx, float& fy, float& fz) {
-  const uint32_t nx = g.nx, ny = g.ny, nz = g.nz;
-  const uint32_t row = (cz * ny + cy) * nx;
-  const uint32_t xm = cx == 0 ? nx - 1 : cx - 1, xp = cx + 1 == nx ? 0 : cx + 1;
-  const uint32_t ym = cy == 0 ? ny - 1 : cy - 1, yp = cy + 1 == ny ? 0 : cy + 1;
-  const uint32_t zm = cz == 0 ? nz - 1 : cz - 1, zp = cz + 1 == nz ? 0 : cz + 1;
-  fx = -0.5f * (load_w<WT>(w, row + xp) - load_w<WT>(w, row + xm));
-  fy = -0.5f * (load_w<WT>(w, (cz * ny + yp) * nx + cx) - load_w<WT>(w, (cz * ny + ym) * nx + cx));
-  fz = -0.5f * (load_w<WT>(w, (zp * ny + cy) * nx + cx) - load_w<WT>(w, (zm * ny + cy) * nx + cx));
-  return load_w<WT>(w, row + cx);
-}
-
-template <int Q, typename WT>
-__global__ void __launch_bounds__(256) sweep_smc_kernel(const SweepArgs p) {
-  constexpr int S = 2 * Q;
-  const int lane = threadIdx.x & 31;
-  const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  const unsigned long long s64 = *p.d_sweep;
-  const uint32_t sweep = (uint32_t)s64;
-  uint32_t* __restrict__ nacc = ((s64 + 1ull) & 1ull) ? p.n1 : p.n0;
-  const WT* __restrict__ wA = static_cast<const WT*>(p.wA);
-  const WT* __restrict__ wB = static_cast<const WT*>(p.wB);
-  const uint32_t N = p.g.N, N_A = p.g.N_A;
-  const uint32_t ctr3a = (PURPOSE_MOVE << 24) | (p.g.replica & 0xFFFFFFu);
-  const uint32_t ctr3b = (PURPOSE_MOVE2 << 24) | (p.g.replica & 0xFFFFFFu);
-  const uint32_t li0 = (uint32_t)lane * S;
-  const float A = p.smc_A, s2A = p.smc_s2A, inv4A = p.smc_inv4A, K2 = 2.f * p.K_b;
-
-  uint32_t ci[S], src_lane[S], src_slot[S];
-  {
-    uint32_t g = li0 / N, i = li0 - g * N;
-#pragma unroll
-    for (int j = 0; j < S; ++j) {
-      ci[j] = i;
-      const uint32_t first = g * N;
-      src_lane[j] = (first / S) & 31u;
-      src_slot[j] = first % S;
-      if (++i == N) { i = 0; ++g; }
-    }
-  }
-
-  unsigned my_acc = 0;
-  for (uint64_t tile = warp0; tile < p.n_tiles; tile += nwarps) {
-    const uint64_t chain0 = tile * p.G;
-    const uint64_t rem = p.g.n_chains - chain0;
-    const uint32_t nmono = (rem < p.G ? (uint32_t)rem : p.G) * N;
-    const uint64_t base = chain0 * N + li0;
-
-    float x[S], y[S], z[S];
-#pragma unroll
-    for (int j = 0; j < S; ++j) {
-      const bool ok = li0 + j < nmono;
-      x[j] = ok ? __ldcs(p.x + base + j) : 0.f;
-      y[j] = ok ? __ldcs(p.y + base + j) : 0.f;
-      z[j] = ok ? __ldcs(p.z + base + j) : 0.f;
-    }
-
-    // configuration-independent part: normals, acceptance uniform, old cell,
-    // field and field force at the old cell
-    float gx[S], gy[S], gz[S], lnu[S], w_old[S], fox[S], foy[S], foz[S];
-    uint32_t co[S];
-    uint32_t lowbits = 0;
-#pragma unroll
-    for (int j = 0; j < S; ++j) {
-      const uint64_t m = base + j;
-      const uint4 r1 = philox_rk(make_uint4((uint32_t)m, (uint32_t)(m >> 32), sweep, ctr3a), p.g);
-      const uint4 r2 = philox_rk(make_uint4((uint32_t)m, (uint32_t)(m >> 32), sweep, ctr3b), p.g);
-      lowbits |= (r1.w & 1u) << j;
-      float sn, cs;
-      const float rad0 = sqrtf(-2.f * log_uniform_open_accurate(r1.x));
-      sincos_2pi_uniform(r1.y, &sn, &cs);
-      gx[j] = rad0 * cs;
-      gy[j] = rad0 * sn;
-      const float rad1 = sqrtf(-2.f * log_uniform_open_accurate(r1.z));
-      sincos_2pi_uniform(r1.w, &sn, &cs);
-      gz[j] = rad1 * cs;
-      lnu[j] = log_uniform_open_accurate(r2.x);
-      uint32_t cx, cy, cz;
-      cell3(p.g, x[j], y[j], z[j], cx, cy, cz);
-      co[j] = (cz * (uint32_t)p.g.ny + cy) * (uint32_t)p.g.nx + cx;
-      const WT* wt = (ci[j] < N_A) ? wA : wB;
-      w_old[j] = 0.f;
-      fox[j] = foy[j] = foz[j] = 0.f;
-      if (li0 + j < nmono) w_old[j] = field_and_force<WT>(p.g, wt, cx, cy, cz, fox[j], foy[j], foz[j]);
-    }
-
-    uint32_t phase[S];
-#pragma unroll
-    for (int j = 0; j < S; ++j) {
-      uint32_t b = 0;
-      if (p.set_order_random) b = (__shfl_sync(FULL, lowbits, src_lane[j]) >> src_slot[j]) & 1u;
-      phase[j] = (ci[j] & 1u) ^ b;
-    }
-
-#pragma unroll
-    for (uint32_t ph = 0; ph < 2; ++ph) {
-      const float pxl = __shfl_up_sync(FULL, x[S - 1], 1);
-      const float pyl = __shfl_up_sync(FULL, y[S - 1], 1);
-      const float pzl = __shfl_up_sync(FULL, z[S - 1], 1);
-      const float nxl = __shfl_down_sync(FULL, x[0], 1);
-      const float nyl = __shfl_down_sync(FULL, y[0], 1);
-      const float nzl = __shfl_down_sync(FULL, z[0], 1);
-#pragma unroll
-      for (int j = 0; j < S; ++j) {
-        if (li0 + j >= nmono || phase[j] != ph) continue;
-        const bool hp = ci[j] > 0, hn = ci[j] + 1 < N;
-        const float qx = (j > 0) ? x[j - 1] : pxl, qy = (j > 0) ? y[j - 1] : pyl,
-                    qz = (j > 0) ? z[j - 1] : pzl;
-        const float rx = (j < S - 1) ? x[j + 1] : nxl, ry = (j < S - 1) ? y[j + 1] : nyl,
-                    rz = (j < S - 1) ? z[j + 1] : nzl;
-        // U = sum over bonded partners of (r - n); bonded force = -2 K_b U
-        float ux = 0.f, uy = 0.f, uz = 0.f;
-        if (hp) { ux += x[j] - qx; uy += y[j] - qy; uz += z[j] - qz; }
-        if (hn) { ux += x[j] - rx; uy += y[j] - ry; uz += z[j] - rz; }
-        const float k = (float)((int)hp + (int)hn);
-        const float Fx = fmaf(-K2, ux, fox[j]), Fy = fmaf(-K2, uy, foy[j]), Fz = fmaf(-K2, uz, foz[j]);
-        const float tx = __fadd_rn(x[j], fmaf(s2A, gx[j], A * Fx));
-        const float ty = __fadd_rn(y[j], fmaf(s2A, gy[j], A * Fy));
-        const float tz = __fadd_rn(z[j], fmaf(s2A, gz[j], A * Fz));
-        uint32_t cx, cy, cz;
-        cell3(p.g, tx, ty, tz, cx, cy, cz);
-        const WT* wt = (ci[j] < N_A) ? wA : wB;
-        float fnx, fny, fnz;
-        const float w_new = field_and_force<WT>(p.g, wt, cx, cy, cz, fnx, fny, fnz);
-        const float dx = tx - x[j], dy = ty - y[j], dz = tz - z[j];
-        // bonded energy change d.(2U + k d); partners' new U' = U + k d
-        const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
-        const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float dE = fmaf(p.K_b, fmaf(2.f, du, k * dd), w_new - w_old[j]);
-        const float Gx = fmaf(-K2, fmaf(k, dx, ux), fnx), Gy = fmaf(-K2, fmaf(k, dy, uy), fny),
-                    Gz = fmaf(-K2, fmaf(k, dz, uz), fnz);
-        const float ax = dx - A * Fx, ay = dy - A * Fy, az = dz - A * Fz;   // forward residual
-        const float bx = -dx - A * Gx, by = -dy - A * Gy, bz = -dz - A * Gz;  // reverse residual
-        const float fwd = fmaf(ax, ax, fmaf(ay, ay, az * az));
-        const float rev = fmaf(bx, bx, fmaf(by, by, bz * bz));
-        const float log_alpha = fmaf(fwd - rev, inv4A, -dE);
-        if (log_alpha >= 0.f || lnu[j] < log_alpha) {
-          x[j] = tx;
-          y[j] = ty;
-          z[j] = tz;
-          co[j] = (cz * (uint32_t)p.g.ny + cy) * (uint32_t)p.g.nx + cx;
-          ++my_acc;
-        }
-      }
-    }
-
-#pragma unroll
-    for (int j = 0; j < S; ++j) {
-      if (li0 + j < nmono) {
-        __stcs(p.x + base + j, x[j]);
-        __stcs(p.y + base + j, y[j]);
-        __stcs(p.z + base + j, z[j]);
-        atomicAdd(nacc + co[j], (ci[j] < N_A) ? 1u : 0x10000u);
-      }
-    }
-  }
-
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) my_acc += __shfl_xor_sync(FULL, my_acc, o);
-  if (lane == 0 && my_acc) atomicAdd(p.acc, (unsigned long long)my_acc);
-}
-
-// ---------------------------------------------------------------------------
-// Smart Monte Carlo step for even N <= 64 in the paired layout of
-// pair_body.cuh: lane l holds the even particle 2l and the odd particle 2l+1
-// of one chain; after the draws the pair is relabelled with the chain's
-// set-order bit into A (moves in the first set) and B (second set), so that
-// every lane moves one particle per set without divergent branches.  The move
-// is the one of sweep_smc_kernel (same draws, same arithmetic per particle).
-struct SmcSlot {
-  float x, y, z;      // position
-  float gx, gy, gz;   // standard normals
-  float lnu;          // log of the acceptance uniform
-  float w;            // omega at the old cell
-  float fx, fy, fz;   // field force at the old cell
-  uint32_t c;         // old cell
-};
-
-template <typename WT>
-__device__ __forceinline__ SmcSlot smc_slot(const Geom& g, const WT* wt, float x, float y, float z,
-                                            uint32_t m, uint32_t sweep, uint32_t ctr3a,
-                                            uint32_t ctr3b, bool valid, uint32_t* first_word) {
-  SmcSlot q;
-  q.x = x; q.y = y; q.z = z;
-  const uint4 r1 = philox_rk(make_uint4(m, 0u, sweep, ctr3a), g);
-  const uint4 r2 = philox_rk(make_uint4(m, 0u, sweep, ctr3b), g);
-  *first_word = r1.w;
-  float sn, cs;
-  const float rad0 = sqrtf(-2.f * log_uniform_open_accurate(r1.x));
-  sincos_2pi_uniform(r1.y, &sn, &cs);
-  q.gx = rad0 * cs;
-  q.gy = rad0 * sn;
-  const float rad1 = sqrtf(-2.f * log_uniform_open_accurate(r1.z));
-  sincos_2pi_uniform(r1.w, &sn, &cs);
-  q.gz = rad1 * cs;
-  q.lnu = log_uniform_open_accurate(r2.x);
-  uint32_t cx, cy, cz;
-  cell3(g, x, y, z, cx, cy, cz);
-  q.c = (cz * (uint32_t)g.ny + cy) * (uint32_t)g.nx + cx;
-  q.w = 0.f;
-  q.fx = q.fy = q.fz = 0.f;
-  if (valid) q.w = field_and_force<WT>(g, wt, cx, cy, cz, q.fx, q.fy, q.fz);
-  return q;
-}
-
-// One smart Monte Carlo move of M against the fixed partner sum
-// U = sum (r - n) over its k bonded partners; returns acceptance.
-template <typename WT>
-__device__ __forceinline__ bool smc_move(const SweepArgs& p, const WT* wt, SmcSlot& M, float ux,
-                                         float uy, float uz, float k, bool valid) {
-  const float A = p.smc_A, s2A = p.smc_s2A, K2 = 2.f * p.K_b;
-  const float Fx = fmaf(-K2, ux, M.fx), Fy = fmaf(-K2, uy, M.fy), Fz = fmaf(-K2, uz, M.fz);
-  const float tx = __fadd_rn(M.x, fmaf(s2A, M.gx, A * Fx));
-  const float ty = __fadd_rn(M.y, fmaf(s2A, M.gy, A * Fy));
-  const float tz = __fadd_rn(M.z, fmaf(s2A, M.gz, A * Fz));
-  uint32_t cx, cy, cz;
-  cell3(p.g, tx, ty, tz, cx, cy, cz);
-  float fnx = 0.f, fny = 0.f, fnz = 0.f, w_new = 0.f;
-  if (valid) w_new = field_and_force<WT>(p.g, wt, cx, cy, cz, fnx, fny, fnz);
-  const float dx = tx - M.x, dy = ty - M.y, dz = tz - M.z;
-  const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
-  const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-  const float dE = fmaf(p.K_b, fmaf(2.f, du, k * dd), w_new - M.w);
-  const float Gx = fmaf(-K2, fmaf(k, dx, ux), fnx), Gy = fmaf(-K2, fmaf(k, dy, uy), fny),
-              Gz = fmaf(-K2, fmaf(k, dz, uz), fnz);
-  const float ax = dx - A * Fx, ay = dy - A * Fy, az = dz - A * Fz;
-  const float bx = -dx - A * Gx, by = -dy - A * Gy, bz = -dz - A * Gz;
-  const float fwd = fmaf(ax, ax, fmaf(ay, ay, az * az));
-  const float rev = fmaf(bx, bx, fmaf(by, by, bz * bz));
-  const float log_alpha = fmaf(fwd - rev, p.smc_inv4A, -dE);
-  const bool acc = valid && (log_alpha >= 0.f || M.lnu < log_alpha);
-  M.x = acc ? tx : M.x;
-  M.y = acc ? ty : M.y;
-  M.z = acc ? tz : M.z;
-  M.c = acc ? (cz * (uint32_t)p.g.ny + cy) * (uint32_t)p.g.nx + cx : M.c;
-  return acc;
-}
-
-template <typename WT>
-__global__ void __launch_bounds__(256, 3) sweep_smc_pair_kernel(const SweepArgs p) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t n_tiles_all = (uint32_t)p.n_tiles;
-  const uint32_t chunk = (n_tiles_all + gridDim.x - 1) / gridDim.x;
-  const uint32_t t_begin = blockIdx.x * chunk;
-  const uint32_t t_end = min(t_begin + chunk, n_tiles_all);
-  const uint32_t nwarps = blockDim.x >> 5;
-  const unsigned long long s64 = *p.d_sweep;
-  const uint32_t sweep = (uint32_t)s64;
-  uint32_t* __restrict__ nacc = ((s64 + 1ull) & 1ull) ? p.n1 : p.n0;
-  const uint32_t ctr3a = (PURPOSE_MOVE << 24) | (p.g.replica & 0xFFFFFFu);
-  const uint32_t ctr3b = (PURPOSE_MOVE2 << 24) | (p.g.replica & 0xFFFFFFu);
-  PairLane<WT> L;
-  L.init(lane, p.g.N, p.g.N_A, p.wA, p.wB);
-  const uint32_t TN = p.G * p.g.N;
-  unsigned my_acc = 0;
-  for (uint32_t tile = t_begin + (threadIdx.x >> 5); tile < t_end; tile += nwarps) {
-    const bool valid = tile < (uint32_t)p.full_tiles || L.li0 < p.last_rows;
-    const uint32_t base = tile * TN + L.li0;
-    float2 px = make_float2(0.f, 0.f), py = px, pz = px;
-    if (valid) {
-      px = __ldcs(reinterpret_cast<const float2*>(p.x + base));
-      py = __ldcs(reinterpret_cast<const float2*>(p.y + base));
-      pz = __ldcs(reinterpret_cast<const float2*>(p.z + base));
-    }
-    uint32_t w0, w1;
-    const SmcSlot s0 = smc_slot<WT>(p.g, L.w0, px.x, py.x, pz.x, base, sweep, ctr3a, ctr3b, valid, &w0);
-    const SmcSlot s1 = smc_slot<WT>(p.g, L.w1, px.y, py.y, pz.y, base + 1u, sweep, ctr3a, ctr3b,
-                                    valid, &w1);
-    const bool sw = p.set_order_random && (__shfl_sync(FULL, w0, L.first_lane) & 1u);
-    SmcSlot A = sw ? s1 : s0, B = sw ? s0 : s1;
-    const WT* wA = sw ? L.w1 : L.w0;
-    const WT* wB = sw ? L.w0 : L.w1;
-    {  // first set: A moves against B and the adjacent lane's B
-      const int src = sw ? L.src_next : L.src_prev;
-      const float cf = sw ? L.cf_next1 : L.cf_prev0;
-      const float sx = __shfl_sync(FULL, B.x, src);
-      const float sy = __shfl_sync(FULL, B.y, src);
-      const float sz = __shfl_sync(FULL, B.z, src);
-      my_acc += smc_move<WT>(p, wA, A, fmaf(cf, A.x - sx, A.x - B.x), fmaf(cf, A.y - sy, A.y - B.y),
-                             fmaf(cf, A.z - sz, A.z - B.z), 1.f + cf, valid);
-    }
-    {  // second set: B moves against A and the adjacent lane's A
-      const int src = sw ? L.src_prev : L.src_next;
-      const float cf = sw ? L.cf_prev0 : L.cf_next1;
-      const float sx = __shfl_sync(FULL, A.x, src);
-      const float sy = __shfl_sync(FULL, A.y, src);
-      const float sz = __shfl_sync(FULL, A.z, src);
-      my_acc += smc_move<WT>(p, wB, B, fmaf(cf, B.x - sx, B.x - A.x), fmaf(cf, B.y - sy, B.y - A.y),
-                             fmaf(cf, B.z - sz, B.z - A.z), 1.f + cf, valid);
-    }
-    if (valid) {
-      __stcs(reinterpret_cast<float2*>(p.x + base), sw ? make_float2(B.x, A.x) : make_float2(A.x, B.x));
-      __stcs(reinterpret_cast<float2*>(p.y + base), sw ? make_float2(B.y, A.y) : make_float2(A.y, B.y));
-      __stcs(reinterpret_cast<float2*>(p.z + base), sw ? make_float2(B.z, A.z) : make_float2(A.z, B.z));
-      const uint32_t vA = sw ? L.v1 : L.v0, vB = sw ? L.v0 : L.v1;
-      const bool same = A.c == B.c;
-      atomicAdd(nacc + A.c, same ? vA + vB : vA);
-      if (!same) atomicAdd(nacc + B.c, vB);
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) my_acc += __shfl_xor_sync(FULL, my_acc, o);
-  if (lane == 0 && my_acc) atomicAdd(p.acc, (unsigned long long)my_acc);
-}
-
-template <int Q>
-static const void* pick_smc(int grid_dtype) {
-  switch (grid_dtype) {
-    case 1: return (const void*)sweep_smc_kernel<Q, __nv_bfloat16>;
-    case 2: return (const void*)sweep_smc_kernel<Q, __half>;
-    default: return (const void*)sweep_smc_kernel<Q, float>;
-  }
-}
-
 template <int Q, bool VEC>
 static const void* pick_kernel(int grid_dtype) {
   switch (grid_dtype) {
@@ -609,16 +277,7 @@ static const void* pick_kernel(int grid_dtype) {
 
 static const void* sweep_kernel_ptr(int Q, bool vec, int grid_dtype, bool pair, bool big,
                                     int move) {
-  if (move == 1) {
-    if (pair && !big) {
-      switch (grid_dtype) {
-        case 1: return (const void*)sweep_smc_pair_kernel<__nv_bfloat16>;
-        case 2: return (const void*)sweep_smc_pair_kernel<__half>;
-        default: return (const void*)sweep_smc_pair_kernel<float>;
-      }
-    }
-    return Q == 1 ? pick_smc<1>(grid_dtype) : (Q == 2 ? pick_smc<2>(grid_dtype) : pick_smc<4>(grid_dtype));
-  }
+  if (move == 1) return smc_kernel_ptr(Q, pair && !big, grid_dtype);
   if (move == 2) return learned_kernel_ptr(Q, grid_dtype);
   if (pair) {
     if (big) {
