@@ -68,6 +68,7 @@ class OrSystem(ctypes.Structure):
         ("set_order", ctypes.c_int),
         ("move", ctypes.c_int),
         ("mlp", ctypes.c_void_p),
+        ("chosen", ctypes.c_void_p),
     ]
 
 
@@ -272,21 +273,32 @@ class System:
         return wA, wB
 
     def sweep(self, pos, wA, wB, sweep, c0=0, c1=None, want_margin=False, want_acc=False,
-              want_trial=False):
-        """One SET sweep in place; returns (stats, margin or None, accepted or
-        None), plus the (3, M) trial positions when want_trial."""
+              want_trial=False, want_chosen=False):
+        """One MC step in place; returns (stats, margin or None, accepted or
+        None), plus the (3, M) trial positions when want_trial and the chosen
+        particle of every attempt when want_chosen (molecule-parallel
+        iteration, set_order 2; margin, accepted and trial are then indexed by
+        attempt k*N + j instead of by particle)."""
         c1 = self.n_chains if c1 is None else c1
         margin = np.full(self.M, np.nan) if want_margin else None
         acc = np.zeros(self.M, np.uint8) if want_acc else None
         trial = np.full(3 * self.M, np.nan, np.float32) if want_trial else None
+        chosen = np.zeros(self.M, np.uint32) if want_chosen else None
+        self.s.chosen = chosen.ctypes.data if want_chosen else None
         st = OrSweepStats()
-        self.L.or_sweep_trial(ctypes.byref(self.s), _ptr(pos.x, f32p), _ptr(pos.y, f32p),
-                              _ptr(pos.z, f32p), _ptr(wA, f64p), _ptr(wB, f64p), int(sweep),
-                              int(c0), int(c1), _ptr(margin, f64p), _ptr(acc, u8p),
-                              _ptr(trial, f32p), ctypes.byref(st))
+        try:
+            self.L.or_sweep_trial(ctypes.byref(self.s), _ptr(pos.x, f32p), _ptr(pos.y, f32p),
+                                  _ptr(pos.z, f32p), _ptr(wA, f64p), _ptr(wB, f64p), int(sweep),
+                                  int(c0), int(c1), _ptr(margin, f64p), _ptr(acc, u8p),
+                                  _ptr(trial, f32p), ctypes.byref(st))
+        finally:
+            self.s.chosen = None
+        out = (st, margin, acc)
         if want_trial:
-            return st, margin, acc, trial.reshape(3, self.M)
-        return st, margin, acc
+            out = out + (trial.reshape(3, self.M),)
+        if want_chosen:
+            out = out + (chosen,)
+        return out
 
     def observables(self, pos, nA, nB):
         o = OrObs()

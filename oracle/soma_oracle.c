@@ -73,6 +73,7 @@ int or_system_init(or_system* s, uint64_t n_chains, uint32_t N, double f,
                    uint32_t replica, int set_order, int move) {
   memset(s, 0, sizeof(*s));
   if (n_chains == 0 || N == 0) return -1;
+  if (set_order == 2 && (move != 0 || N > 256)) return -1;  /* uniform moves, N <= 256 */
   s->n_chains = n_chains;
   s->N = N;
   s->N_A = (uint32_t)floor(f * (double)N + 0.5);
@@ -268,14 +269,16 @@ void or_fields(const or_system* s, const uint32_t* nA, const uint32_t* nB,
 /* field change omega_t(c') - omega_t(c) (Eq. delta-e); Metropolis acceptance    */
 /* min(1, exp(-dE)), taken as: accept iff dE <= 0 or ln u < -dE.                 */
 /* ------------------------------------------------------------------------- */
-static void or_move_uniform(const or_system* s, float* x, float* y, float* z,
-                            const double* wA, const double* wB, uint32_t sweep,
-                            uint64_t chain, uint32_t i, double* margin, uint8_t* accepted,
-                            float* trial, uint64_t* acc, uint64_t* ties) {
+/* Uniform move of particle i of chain with the draw w (words 0-2: the
+ * displacement, word 3: the acceptance uniform).  Diagnostics are stored at
+ * index rec (the particle for the SET sweep, the attempt for the molecule-
+ * parallel sweep). */
+static void or_move_uniform_w(const or_system* s, float* x, float* y, float* z,
+                              const double* wA, const double* wB, uint64_t chain, uint32_t i,
+                              const uint32_t w[4], uint64_t rec, double* margin, uint8_t* accepted,
+                              float* trial, uint64_t* acc, uint64_t* ties) {
   const uint32_t N = s->N;
   const uint64_t m = chain * N + i;
-  uint32_t w[4];
-  or_draw(s, OR_PURPOSE_MOVE, m, sweep, w);
   /* trial position: each displacement component a*v rounded to FP32, then the
    * sum rounded to FP32 (the stored precision of positions) */
   double r_old[3] = { x[m], y[m], z[m] };
@@ -287,7 +290,7 @@ static void or_move_uniform(const or_system* s, float* x, float* y, float* z,
   double u = or_uniform_open(w[3]);
   if (trial) {
     const uint64_t M = s->n_chains * N;
-    for (int d = 0; d < 3; ++d) trial[d * M + m] = (float)r_new[d];
+    for (int d = 0; d < 3; ++d) trial[d * M + rec] = (float)r_new[d];
   }
   /* bonded energy change: neighbours i-1 and i+1 of the linear chain */
   double dEb = 0.0;
@@ -310,13 +313,43 @@ static void or_move_uniform(const or_system* s, float* x, float* y, float* z,
   double dE = dEb + (w_t[c_new] - w_t[c_old]);
   double lnu = log(u);
   int acc_move = (dE <= 0.0) || (lnu < -dE);
-  if (margin) margin[m] = dE + lnu;
+  if (margin) margin[rec] = dE + lnu;
   if (fabs(dE + lnu) < 1e-4) (*ties)++;
   if (acc_move) {
     x[m] = (float)r_new[0]; y[m] = (float)r_new[1]; z[m] = (float)r_new[2];
     (*acc)++;
   }
-  if (accepted) accepted[m] = (uint8_t)acc_move;
+  if (accepted) accepted[rec] = (uint8_t)acc_move;
+}
+
+static void or_move_uniform(const or_system* s, float* x, float* y, float* z,
+                            const double* wA, const double* wB, uint32_t sweep,
+                            uint64_t chain, uint32_t i, double* margin, uint8_t* accepted,
+                            float* trial, uint64_t* acc, uint64_t* ties) {
+  const uint64_t m = chain * s->N + i;
+  uint32_t w[4];
+  or_draw(s, OR_PURPOSE_MOVE, m, sweep, w);
+  or_move_uniform_w(s, x, y, z, wA, wB, chain, i, w, m, margin, accepted, trial, acc, ties);
+}
+
+/* Molecule-parallel iteration (Sec. 3.1.2, the first scheme): the chain's N
+ * attempts of one MC step are made one after another, each on a particle of
+ * the chain chosen at random, so each particle is attempted once per step on
+ * average.  Attempt j of chain k draws Philox purpose 3 with id k*N + j: the
+ * particle is ((word 3 & 0xFF) * N) >> 8 (the low byte, which the acceptance
+ * uniform of the top 24 bits does not use; a state-independent choice, so
+ * balance holds for any choice probabilities), the move is the uniform move
+ * with that draw.  Diagnostics (margin, accepted, trial) are per attempt. */
+static void or_move_attempt(const or_system* s, float* x, float* y, float* z,
+                            const double* wA, const double* wB, uint32_t sweep,
+                            uint64_t chain, uint32_t j, double* margin, uint8_t* accepted,
+                            float* trial, uint32_t* chosen, uint64_t* acc, uint64_t* ties) {
+  const uint64_t a = chain * s->N + j;
+  uint32_t w[4];
+  or_draw(s, OR_PURPOSE_ATTEMPT, a, sweep, w);
+  const uint32_t i = (uint32_t)(((uint64_t)(w[3] & 0xFFu) * s->N) >> 8);
+  if (chosen) chosen[a] = i;
+  or_move_uniform_w(s, x, y, z, wA, wB, chain, i, w, a, margin, accepted, trial, acc, ties);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -722,6 +755,16 @@ void or_sweep_trial(const or_system* s, float* x, float* y, float* z,
 #pragma omp parallel for schedule(static) reduction(+ : acc, ties)
   for (long long cc = i0; cc < i1; ++cc) {
     uint64_t chain = (uint64_t)cc;
+    if (s->set_order == 2) {
+      for (uint32_t j = 0; j < N; ++j) {
+        uint64_t a1 = 0, t1 = 0;
+        or_move_attempt(s, x, y, z, wA, wB, sweep, chain, j, margin, accepted, trial,
+                        s->chosen, &a1, &t1);
+        acc += a1;
+        ties += t1;
+      }
+      continue;
+    }
     uint32_t first = or_first_set(s, chain, sweep);
     for (uint32_t k = 0; k < 2; ++k) {
       uint32_t set = first ^ k;

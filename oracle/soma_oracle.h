@@ -32,7 +32,7 @@ extern "C" {
 
 /* Philox stream purposes (the fourth counter word holds purpose<<24 | replica). */
 enum { OR_PURPOSE_INIT = 0, OR_PURPOSE_MOVE = 1, OR_PURPOSE_MOVE2 = 2,
-       OR_PURPOSE_CONFIG = 4, OR_PURPOSE_TRAIN = 5 };
+       OR_PURPOSE_ATTEMPT = 3, OR_PURPOSE_CONFIG = 4, OR_PURPOSE_TRAIN = 5 };
 
 typedef struct {
   uint64_t n_chains;
@@ -47,9 +47,12 @@ typedef struct {
   double   rho_cell; /* rho_0 dL^3 = M / n_cells */
   uint64_t seed;
   uint32_t replica;
-  int      set_order;  /* 0: random per (chain, sweep); 1: fixed even->odd */
+  int      set_order;  /* 0: random per (chain, sweep); 1: fixed even->odd;
+                          2: molecule-parallel iteration (no sets, below) */
   int      move;       /* 0 uniform (Metropolis), 1 smart MC (force biased), 2 learned */
   const double* mlp;   /* learned proposal parameters (move 2), OR_MLP_PARAMS doubles */
+  uint32_t* chosen;    /* optional: particle chosen by each attempt of the
+                          molecule-parallel iteration (set_order 2), M entries */
 } or_system;
 
 typedef struct {

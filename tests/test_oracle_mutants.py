@@ -82,6 +82,9 @@ MUTANTS = [
      PIN.check_learned_features_hand_values),
     ("gradient_interpolation_reversed", "g[d] = (1.0 - t) * lo + t * hi;", "g[d] = t * lo + (1.0 - t) * hi;",
      PIN.check_learned_features_hand_values),
+    ("molecule_choice_half", "const uint32_t i = (uint32_t)(((uint64_t)(w[3] & 0xFFu) * s->N) >> 8);",
+     "const uint32_t i = (uint32_t)(((uint64_t)(w[3] & 0xFFu) * s->N) >> 9);",
+     PIN.check_molecule_iteration_attempts),
     ("sort_key_axis", "for (int d = 0; d < 3; ++d) key |= ((b[d] >> bit) & 1u) << (3 * bit + d);",
      "for (int d = 0; d < 3; ++d) key |= ((b[2 - d] >> bit) & 1u) << (3 * bit + d);",
      PIN.check_sort_chains_is_a_spatial_permutation),

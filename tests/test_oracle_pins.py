@@ -157,13 +157,13 @@ def check_field_rounding_modes(lib=None):
 # --------------------------------------------------------------------------
 # Moves: ideal chains (chiN = kappaN = 0) relax to the Gaussian closed forms
 # --------------------------------------------------------------------------
-def check_ideal_chain_relaxes_to_gaussian_statistics(lib=None, move=0):
+def check_ideal_chain_relaxes_to_gaussian_statistics(lib=None, move=0, set_order=0):
     """With chiN = kappaN = 0 every field vanishes and the Metropolis chain
     samples exp(-K_b sum b^2): <b^2> = R_e0^2/(N-1) and, the bonds being
     independent, <R_e^2> = R_e0^2.  Start from bonds stretched by 1.6x so
     the test sees the sweep relax the bond length."""
     d = workloads.melt_small(n_chains=1024, N=8, chiN=0.0, kappaN=0.0, box_Re=(2.0, 2.0, 1.0),
-                             grid=(12, 12, 6), move=move)
+                             grid=(12, 12, 6), move=move, set_order=set_order)
     s = oracle_system(d, lib)
     if move == 2:
         s.set_mlp(workloads.random_mlp(7, scale=0.1))
@@ -297,6 +297,55 @@ def check_sweep_moves_follow_the_draws(lib=None):
 
 
 # --------------------------------------------------------------------------
+# Molecule-parallel iteration (Sec. 3.1.2, first scheme): N attempts per chain
+# and step, each on a particle chosen at random, every particle attempted once
+# per step on average; an attempt moves only its chosen particle, onto the
+# trial position of its own draw, or leaves the chain unchanged.
+# --------------------------------------------------------------------------
+def check_molecule_iteration_attempts(lib=None):
+    from oracle import Positions
+    for N, n_chains in ((32, 512), (7, 1500)):
+        d = SystemDesc(n_chains=n_chains, N=N, f=0.5, box_Re=(2.0, 2.0, 2.0), grid=(12, 12, 12),
+                       chiN=20.0, kappaN=50.0, set_order=2)
+        s = oracle_system(d, lib)
+        p = s.init_chains()
+        nA, nB = s.histogram(p)
+        wA, wB = s.fields(nA, nB)
+        counts = np.zeros(N)
+        for sweep in range(6):
+            before = p.copy()
+            st, margin, acc, trial, chosen = s.sweep(p, wA, wB, sweep, want_margin=True,
+                                                     want_acc=True, want_trial=True,
+                                                     want_chosen=True)
+            assert st.attempted == d.M and st.accepted == int(acc.sum())
+            assert chosen.max() < N
+            counts += np.bincount(chosen, minlength=N)
+            B = before.stacked().reshape(3, n_chains, N)
+            A = p.stacked().reshape(3, n_chains, N)
+            T = trial.reshape(3, n_chains, N)
+            C = chosen.reshape(n_chains, N)
+            ACC = acc.reshape(n_chains, N)
+            for k in range(0, n_chains, 37):   # replay chains attempt by attempt
+                cur = B[:, k, :].copy()
+                for j in range(N):
+                    if ACC[k, j]:
+                        cur[:, C[k, j]] = T[:, k, j]
+                np.testing.assert_array_equal(cur, A[:, k, :])
+            moved = np.any(A != B, axis=0)
+            assert moved.mean() > 0.2
+        # the choice is uniform over the chain (exact for N = 2^k, within 1/256 otherwise)
+        tot = counts.sum()
+        expect = tot / N
+        chi2 = float(((counts - expect) ** 2 / expect).sum())
+        assert chi2 < (N - 1) + 6 * math.sqrt(2 * (N - 1)) + (tot / 256**2 * N if N & (N - 1) else 0), chi2
+        assert counts.min() > 0
+
+
+def test_molecule_iteration_attempts(oracle_lib):
+    check_molecule_iteration_attempts()
+
+
+# --------------------------------------------------------------------------
 # Observables
 # --------------------------------------------------------------------------
 def check_observables_hand_values(lib=None):
@@ -353,13 +402,13 @@ def test_field_rounding_modes(oracle_lib):
     check_field_rounding_modes()
 
 
-@pytest.mark.parametrize("move", [0, 1, 2])
-def test_ideal_chain_relaxes_to_gaussian_statistics(oracle_lib, move):
-    check_ideal_chain_relaxes_to_gaussian_statistics(move=move)
+@pytest.mark.parametrize("move,set_order", [(0, 0), (1, 0), (2, 0), (0, 2)])
+def test_ideal_chain_relaxes_to_gaussian_statistics(oracle_lib, move, set_order):
+    check_ideal_chain_relaxes_to_gaussian_statistics(move=move, set_order=set_order)
 
 
-@pytest.mark.parametrize("set_order", [0, 1])
-@pytest.mark.parametrize("move", [0, 1, 2])
+@pytest.mark.parametrize("set_order,move", [(0, 0), (0, 1), (0, 2), (1, 0), (1, 1), (1, 2),
+                                            (2, 0)])
 def test_two_particle_balance_brute_force(oracle_lib, set_order, move):
     check_two_particle_balance_brute_force(set_order, move=move)
 
