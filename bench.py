@@ -38,6 +38,9 @@ def parse():
                              "batch64", "decorrelation"])
     ap.add_argument("--move", default="uniform", choices=["uniform", "smc", "learned"],
                     help="trial moves: uniform displacement or smart Monte Carlo")
+    ap.add_argument("--iteration", default="set", choices=["set", "molecule"],
+                    help="particle visiting scheme: independent sets (even/odd chain positions) "
+                         "or molecule-parallel with random particle choice")
     ap.add_argument("--learned-net", default="mma_sync", choices=["mma_sync", "umma", "fp32"],
                     help="network evaluator of the learned move: warp-level mma.sync (default), "
                          "tcgen05 with the accumulator in tensor memory, or FP32 on the CUDA cores")
@@ -57,13 +60,16 @@ def dist_env():
 GRID_DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
 
 
-def workload(name, replica=0, grid_dtype="f32", move="uniform", learned_net="mma_sync"):
+def workload(name, replica=0, grid_dtype="f32", move="uniform", learned_net="mma_sync",
+             iteration="set"):
     from paper_1711_03828_gb300 import workloads
     d = getattr(workloads, name)(seed=1)
     d.replica_id = replica
     d.grid_dtype = GRID_DTYPES[grid_dtype]
     d.move = {"uniform": 0, "smc": 1, "learned": 2}[move]
     d.flags |= {"mma_sync": 0, "umma": 4, "fp32": 2}[learned_net] if d.move == 2 else 0
+    if iteration == "molecule":
+        d.set_order = 2
     return d
 
 
@@ -73,7 +79,8 @@ def config_of(d, name, l2_note):
             "n_chains": d.n_chains, "N": d.N, "particles": d.M, "grid": list(d.grid),
             "box_Re": list(d.box_Re), "chiN": d.chiN, "kappaN": d.kappaN,
             "move": {0: "uniform", 1: "smart Monte Carlo", 2: "learned MH proposal"}[d.move],
-            "set_order": "random per chain and sweep",
+            "set_order": {0: "random per chain and sweep", 1: "even first",
+                          2: "molecule-parallel, random particle per attempt"}[d.set_order],
             "grid_dtype": {0: "f32", 1: "bf16", 2: "f16"}[d.grid_dtype], "l2": l2_note}
 
 
@@ -242,6 +249,8 @@ def sweep_kernel_name(d):
         if not pair or d.flags & 2:
             return "sweep_learned_kernel"
         return "sweep_learned_umma_kernel" if d.flags & 4 else "sweep_learned_tc_kernel"
+    if d.set_order == 2:
+        return "sweep_molecule_kernel"
     return "sweep_pair_kernel" if pair else "sweep_uniform_kernel"
 
 
@@ -271,7 +280,7 @@ def run_ours(args):
     from paper_1711_03828_gb300 import System, _abi
 
     d = workload(args.workload, replica=rank, grid_dtype=args.grid_dtype, move=args.move,
-                 learned_net=args.learned_net)
+                 learned_net=args.learned_net, iteration=args.iteration)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     s = System(d, stream=stream)

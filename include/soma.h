@@ -68,7 +68,16 @@ typedef enum {
 } soma_status;
 
 typedef enum { SOMA_MOVE_UNIFORM = 0, SOMA_MOVE_SMC = 1, SOMA_MOVE_LEARNED = 2 } soma_move;
-typedef enum { SOMA_SET_ORDER_RANDOM = 0, SOMA_SET_ORDER_FIXED = 1 } soma_set_order;
+/* How a sweep visits the particles (Sec. 3.1.2).  The SET scheme moves the
+ * even and then the odd chain positions (or the reverse) as two sets of
+ * independent particles: the order is drawn per chain and step (RANDOM) or
+ * always even first (FIXED).  SOMA_ITERATION_MOLECULE is the molecule-
+ * parallel scheme: one thread per chain makes the chain's N attempts one after
+ * another, each on a particle chosen at random (Philox purpose 3, id
+ * chain*N + attempt; the particle is ((word 3 & 0xFF) * N) >> 8, the
+ * acceptance uniform the top 24 bits of word 3); uniform moves only. */
+typedef enum { SOMA_SET_ORDER_RANDOM = 0, SOMA_SET_ORDER_FIXED = 1,
+               SOMA_ITERATION_MOLECULE = 2 } soma_set_order;
 typedef enum { SOMA_GRID_F32 = 0, SOMA_GRID_BF16 = 1, SOMA_GRID_F16 = 2 } soma_grid_dtype;
 
 /* desc.flags bits.  By default soma_create labels the chains in spatial order:

@@ -16,10 +16,11 @@ import numpy as np
 
 from . import _abi
 from ._abi import (FLAG_LEARNED_FP32, FLAG_LEARNED_UMMA, FLAG_NO_SORT, GRID_BF16, GRID_F16, GRID_F32, MLP_PARAMS, MOVE_LEARNED,
-                   MOVE_SMC, MOVE_UNIFORM, SET_ORDER_FIXED, SET_ORDER_RANDOM, SomaError)
+                   MOVE_SMC, MOVE_UNIFORM, SET_ORDER_FIXED, SET_ORDER_RANDOM, ITERATION_MOLECULE,
+                   SomaError)
 
 __all__ = ["SystemDesc", "System", "Batch", "SomaError", "FLAG_NO_SORT", "FLAG_LEARNED_FP32", "FLAG_LEARNED_UMMA", "MOVE_UNIFORM", "MOVE_SMC", "MOVE_LEARNED", "MLP_PARAMS", "SET_ORDER_RANDOM",
-           "SET_ORDER_FIXED", "GRID_F32", "GRID_BF16", "GRID_F16"]
+           "SET_ORDER_FIXED", "ITERATION_MOLECULE", "GRID_F32", "GRID_BF16", "GRID_F16"]
 
 
 @dataclass

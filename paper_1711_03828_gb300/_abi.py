@@ -16,7 +16,7 @@ SOMA_OK, SOMA_EINVAL, SOMA_ENOMEM, SOMA_ECUDA, SOMA_EOVERFLOW, SOMA_ETIMEOUT, SO
     0, -1, -2, -3, -4, -5, -6)
 MOVE_UNIFORM, MOVE_SMC, MOVE_LEARNED = 0, 1, 2
 MLP_PARAMS = 1604
-SET_ORDER_RANDOM, SET_ORDER_FIXED = 0, 1
+SET_ORDER_RANDOM, SET_ORDER_FIXED, ITERATION_MOLECULE = 0, 1, 2
 GRID_F32, GRID_BF16, GRID_F16 = 0, 1, 2
 FLAG_NO_SORT = 1
 FLAG_LEARNED_FP32 = 2

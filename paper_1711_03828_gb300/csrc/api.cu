@@ -138,8 +138,11 @@ soma_status validate(const soma_system_desc* d) {
     return fail(SOMA_EINVAL, "chiN, kappaN and a_Re must be finite");
   if (d->move != SOMA_MOVE_UNIFORM && d->move != SOMA_MOVE_SMC && d->move != SOMA_MOVE_LEARNED)
     return fail(SOMA_EINVAL, "move=%d is not available", d->move);
-  if (d->set_order != SOMA_SET_ORDER_RANDOM && d->set_order != SOMA_SET_ORDER_FIXED)
+  if (d->set_order != SOMA_SET_ORDER_RANDOM && d->set_order != SOMA_SET_ORDER_FIXED &&
+      d->set_order != SOMA_ITERATION_MOLECULE)
     return fail(SOMA_EINVAL, "set_order=%d unknown", d->set_order);
+  if (d->set_order == SOMA_ITERATION_MOLECULE && d->move != SOMA_MOVE_UNIFORM)
+    return fail(SOMA_EINVAL, "the molecule-parallel iteration takes uniform moves");
   if (d->grid_dtype < 0 || d->grid_dtype > 2)
     return fail(SOMA_EINVAL, "grid_dtype=%d unknown", d->grid_dtype);
   if (d->flags & ~(SOMA_FLAG_NO_SORT | SOMA_FLAG_LEARNED_FP32 | SOMA_FLAG_LEARNED_UMMA))
@@ -419,7 +422,8 @@ soma_status soma_create(const soma_system_desc* desc, soma_t** out) {
   h->d_out = h->d_scratch + h->scratch_doubles;
   h->shape = sweep_shape(h->g.n_chains, h->g.N, h->sm_count, h->grid_dtype, desc->move,
                          (desc->flags & SOMA_FLAG_LEARNED_FP32) != 0,
-                         (desc->flags & SOMA_FLAG_LEARNED_UMMA) != 0);
+                         (desc->flags & SOMA_FLAG_LEARNED_UMMA) != 0,
+                         desc->set_order == SOMA_ITERATION_MOLECULE);
   h->plain_shape = sweep_shape(h->g.n_chains, h->g.N, h->sm_count, h->grid_dtype, SOMA_MOVE_UNIFORM);
 #define CK(call) do { e = (call); if (e != cudaSuccess) { release(h); return cuda_fail(e, #call); } } while (0)
   CK(cudaMemsetAsync(h->n[0], 0, sizeof(uint32_t) * cells, h->stream));

@@ -17,12 +17,15 @@ struct SweepShape {
   int move;   // 0 uniform, 1 smart Monte Carlo, 2 learned
   bool learned_tc;  // learned move with the network on the tensor cores
   bool learned_umma;  // ... through tcgen05 (else warp-level mma.sync)
+  bool molecule;      // molecule-parallel iteration (one thread per chain)
+  size_t smem;        // dynamic shared memory of the sweep kernel
   int block;
   int grid;
 };
 
 SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dtype, int move,
-                       bool learned_fp32 = false, bool learned_umma = false);
+                       bool learned_fp32 = false, bool learned_umma = false,
+                       bool molecule = false);
 cudaError_t launch_sweep_uniform(const SweepArgs& a, const SweepShape& s, int grid_dtype,
                                  cudaStream_t st);
 
@@ -77,6 +80,9 @@ cudaError_t launch_adam(float* w, float* m, float* v, const float* grad, void* w
 cudaError_t launch_quantize(const float* w, void* wq, cudaStream_t st);
 const void* learned_kernel_ptr(int Q, int grid_dtype);
 const void* learned_tc_kernel_ptr(int grid_dtype, bool umma);
+// molecule-parallel sweep kernel for chains of N particles; *smem receives its
+// dynamic shared memory (prepare: allow the kernel that much, once at create)
+const void* molecule_kernel_ptr(uint32_t N, int grid_dtype, size_t* smem, bool prepare);
 // smart Monte Carlo sweep kernel: paired layout (even N <= 64, 32-bit indices) or general
 const void* smc_kernel_ptr(int Q, bool pair, int grid_dtype);
 

@@ -1,0 +1,124 @@
+// molecule.cu -- the molecule-parallel iteration (Sec. 3.1.2, first scheme).
+//
+// One thread per chain: the chain's N attempts of one MC step run one after
+// another, each on a particle of the chain chosen at random, so every particle
+// is attempted once per step on average and a move always sees the current
+// positions of its bonded partners.  Attempt j of chain k draws Philox purpose
+// 3 with id k*N + j: words 0-2 give the uniform displacement, the top 24 bits
+// of word 3 the acceptance uniform and its low byte the particle,
+// ((word3 & 0xFF) * N) >> 8.  A block stages its 128 chains in shared memory
+// (coalesced in and out) when they fit (N <= 64), then counts the final cells
+// while writing them back.
+#include "kernels.h"
+
+namespace soma {
+
+constexpr uint32_t PURPOSE_ATTEMPT = 3;
+constexpr int MOL_BLOCK = 128;
+
+template <typename WT, bool STAGE>
+__global__ void __launch_bounds__(MOL_BLOCK) sweep_molecule_kernel(const SweepArgs p) {
+  extern __shared__ float sm[];
+  const uint32_t N = p.g.N, N_A = p.g.N_A;
+  const uint32_t t = threadIdx.x;
+  const unsigned long long s64 = *p.d_sweep;
+  const uint32_t sweep = (uint32_t)s64;
+  uint32_t* __restrict__ nacc = ((s64 + 1ull) & 1ull) ? p.n1 : p.n0;
+  const uint32_t ctr3 = (PURPOSE_ATTEMPT << 24) | (p.g.replica & 0xFFFFFFu);
+  const WT* __restrict__ wA = static_cast<const WT*>(p.wA);
+  const WT* __restrict__ wB = static_cast<const WT*>(p.wB);
+  const float a = p.a, K1 = p.K_b, K2 = 2.f * p.K_b;
+  const uint64_t n_blocks = (p.g.n_chains + MOL_BLOCK - 1) / MOL_BLOCK;
+  unsigned my_acc = 0;
+  for (uint64_t cb = blockIdx.x; cb < n_blocks; cb += gridDim.x) {
+    const uint64_t chain0 = cb * MOL_BLOCK;
+    const uint64_t rem = p.g.n_chains - chain0;
+    const uint32_t nch = rem < (uint64_t)MOL_BLOCK ? (uint32_t)rem : (uint32_t)MOL_BLOCK;
+    const uint32_t cnt = nch * N;       // particles of this block
+    const uint64_t m0 = chain0 * N;
+    float* sx = sm;
+    float* sy = sm + MOL_BLOCK * N;
+    float* sz = sm + 2 * MOL_BLOCK * N;
+    if (STAGE) {
+      for (uint32_t q = t; q < cnt; q += MOL_BLOCK) {
+        sx[q] = __ldcs(p.x + m0 + q);
+        sy[q] = __ldcs(p.y + m0 + q);
+        sz[q] = __ldcs(p.z + m0 + q);
+      }
+      __syncthreads();
+    }
+    if (t < nch) {
+      const uint64_t chain = chain0 + t;
+      float* X = STAGE ? sx + t * N : p.x + chain * N;
+      float* Y = STAGE ? sy + t * N : p.y + chain * N;
+      float* Z = STAGE ? sz + t * N : p.z + chain * N;
+      for (uint32_t j = 0; j < N; ++j) {
+        const uint64_t id = chain * N + j;
+        const uint4 r = philox_rk(make_uint4((uint32_t)id, (uint32_t)(id >> 32), sweep, ctr3), p.g);
+        const uint32_t i = ((r.w & 0xFFu) * N) >> 8;
+        const float xo = X[i], yo = Y[i], zo = Z[i];
+        const float xn = __fadd_rn(xo, __fmul_rn(a, uniform_sym(r.x)));
+        const float yn = __fadd_rn(yo, __fmul_rn(a, uniform_sym(r.y)));
+        const float zn = __fadd_rn(zo, __fmul_rn(a, uniform_sym(r.z)));
+        const WT* w = i < N_A ? wA : wB;
+        const float dEf = load_w<WT>(w, cell_of(p.g, xn, yn, zn)) - load_w<WT>(w, cell_of(p.g, xo, yo, zo));
+        // U = sum over bonded partners of (r - n), k partners
+        float ux = 0.f, uy = 0.f, uz = 0.f, k = 0.f;
+        if (i > 0) { ux += xo - X[i - 1]; uy += yo - Y[i - 1]; uz += zo - Z[i - 1]; k += 1.f; }
+        if (i + 1 < N) { ux += xo - X[i + 1]; uy += yo - Y[i + 1]; uz += zo - Z[i + 1]; k += 1.f; }
+        const float dx = xn - xo, dy = yn - yo, dz = zn - zo;
+        const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+        const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float dE = fmaf(k * K1, dd, fmaf(K2, du, dEf));
+        if (dE <= -log_uniform_open(r.w)) {
+          X[i] = xn;
+          Y[i] = yn;
+          Z[i] = zn;
+          ++my_acc;
+        }
+      }
+    }
+    __syncthreads();
+    // write back (staged) and count the final cells
+    uint32_t ci = t % N;
+    const uint32_t step = MOL_BLOCK % N;
+    for (uint32_t q = t; q < cnt; q += MOL_BLOCK) {
+      float x, y, z;
+      if (STAGE) {
+        x = sx[q]; y = sy[q]; z = sz[q];
+        __stcs(p.x + m0 + q, x);
+        __stcs(p.y + m0 + q, y);
+        __stcs(p.z + m0 + q, z);
+      } else {
+        x = p.x[m0 + q]; y = p.y[m0 + q]; z = p.z[m0 + q];
+      }
+      atomicAdd(nacc + cell_of(p.g, x, y, z), ci < N_A ? 1u : 0x10000u);
+      ci += step;
+      if (ci >= N) ci -= N;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) my_acc += __shfl_xor_sync(FULL, my_acc, o);
+  if ((t & 31u) == 0 && my_acc) atomicAdd(p.acc, (unsigned long long)my_acc);
+}
+
+template <bool STAGE>
+static const void* pick_molecule(int grid_dtype) {
+  switch (grid_dtype) {
+    case 1: return (const void*)sweep_molecule_kernel<__nv_bfloat16, STAGE>;
+    case 2: return (const void*)sweep_molecule_kernel<__half, STAGE>;
+    default: return (const void*)sweep_molecule_kernel<float, STAGE>;
+  }
+}
+
+const void* molecule_kernel_ptr(uint32_t N, int grid_dtype, size_t* smem, bool prepare) {
+  const bool stage = N <= 64;
+  *smem = stage ? (size_t)3 * MOL_BLOCK * N * sizeof(float) : 0;
+  const void* fn = stage ? pick_molecule<true>(grid_dtype) : pick_molecule<false>(grid_dtype);
+  if (prepare && *smem > 48 * 1024)
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+  return fn;
+}
+
+}  // namespace soma

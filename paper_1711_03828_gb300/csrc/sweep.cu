@@ -299,11 +299,13 @@ static const void* sweep_kernel_ptr(int Q, bool vec, int grid_dtype, bool pair, 
 }
 
 SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dtype, int move,
-                       bool learned_fp32, bool learned_umma) {
+                       bool learned_fp32, bool learned_umma, bool molecule) {
   SweepShape s;
   s.move = move;
   s.learned_tc = false;
   s.learned_umma = false;
+  s.molecule = false;
+  s.smem = 0;
   s.Q = (N <= 64) ? 1 : (N <= 128 ? 2 : 4);
   s.G = (uint32_t)(64 * s.Q) / N;
   s.n_tiles = (n_chains + s.G - 1) / s.G;
@@ -320,11 +322,17 @@ SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dty
     s.block = 128;
     fn = learned_tc_kernel_ptr(grid_dtype, s.learned_umma);
   }
+  if (molecule && move == 0) {
+    s.molecule = true;
+    s.block = 128;
+    fn = molecule_kernel_ptr(N, grid_dtype, &s.smem, true);
+  }
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, s.block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, s.block, s.smem);
   if (per_sm < 1) per_sm = 1;
   const uint64_t warps_per_block = (uint64_t)s.block / 32;
-  const uint64_t need = (s.n_tiles + warps_per_block - 1) / warps_per_block;
+  const uint64_t need = s.molecule ? (n_chains + s.block - 1) / s.block
+                                   : (s.n_tiles + warps_per_block - 1) / warps_per_block;
   const uint64_t cap = (uint64_t)sm_count * (uint64_t)per_sm;
   s.grid = (int)(need < cap ? need : cap);
   if (s.grid < 1) s.grid = 1;
@@ -333,9 +341,11 @@ SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dty
 
 cudaError_t launch_sweep_uniform(const SweepArgs& a, const SweepShape& s, int grid_dtype,
                                  cudaStream_t st) {
-  const void* fn = sweep_kernel_ptr(s.Q, s.vec, grid_dtype, s.pair, s.big, s.move);
+  size_t smem = 0;
+  const void* fn = s.molecule ? molecule_kernel_ptr(a.g.N, grid_dtype, &smem, false)
+                              : sweep_kernel_ptr(s.Q, s.vec, grid_dtype, s.pair, s.big, s.move);
   void* args[] = {const_cast<SweepArgs*>(&a)};
-  return cudaLaunchKernel(fn, dim3(s.grid), dim3(s.block), args, 0, st);
+  return cudaLaunchKernel(fn, dim3(s.grid), dim3(s.block), args, smem, st);
 }
 
 }  // namespace soma

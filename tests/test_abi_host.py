@@ -41,6 +41,14 @@ def test_invalid_description_is_rejected_without_gpu(soma_lib, field, value):
     assert _abi.soma_last_error()
 
 
+def test_molecule_iteration_takes_uniform_moves_only(soma_lib):
+    for move in (1, 2):
+        d = _valid()
+        d.set_order, d.move = 2, move
+        st, h = _create_status(d.to_c())
+        assert st == _abi.SOMA_EINVAL and h.value is None
+
+
 @pytest.mark.parametrize("mutate", ["struct_size", "flags", "box", "grid", "noncubic", "cells"])
 def test_invalid_geometry_is_rejected_without_gpu(soma_lib, mutate):
     c = _valid().to_c()
