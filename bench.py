@@ -35,6 +35,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="melt_large",
                     choices=["melt_large", "melt_mid", "melt_small", "melt_slow", "melt_subbox",
+                             "melt_tiny",
                              "batch64", "decorrelation"])
     ap.add_argument("--move", default="uniform", choices=["uniform", "smc", "learned"],
                     help="trial moves: uniform displacement or smart Monte Carlo")
@@ -357,7 +358,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_of(d, args.workload,
-                            f"inputs larger than L2 ({12 * d.M / 1e9:.2f} GB of positions)"),
+                            f"inputs larger than L2 ({12 * d.M / 1e9:.2f} GB of positions)"
+                            if 12 * d.M > 129e6 else
+                            f"inputs L2-resident ({12 * d.M / 1e6:.2f} MB of positions): a "
+                            "latency figure, not a bandwidth one"),
         "roofline": {"bound": "hbm",
                      "kernel": sweep_kernel_name(d),
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -505,9 +509,10 @@ def run_decorrelation(args):
     ms_all = [(i, j, k) for i in range(-4, 5) for j in range(-4, 5) for k in range(0, 3)
               if 0 < i * i + j * j + k * k <= 16]
     res = {}
-    for name, move in (("uniform", 0), ("smc", 1), ("learned", 2)):
+    for name, move, order in (("uniform", 0, 0), ("smc", 1, 0), ("learned", 2, 0),
+                              ("uniform_molecule", 0, 2)):
         d = workloads.melt_slow(n_chains=16384, box_Re=(8.0, 8.0, 4.0), grid=(48, 48, 24),
-                                move=move)
+                                move=move, set_order=order)
         s = System(d)
         if move == 2:
             s.set_proposal_weights(W)
@@ -527,7 +532,7 @@ def run_decorrelation(args):
         tau_re, w_re = tau_int(np.asarray(re2))
         tau_sq, w_sq = tau_int(np.asarray(sqs))
         # wall time per cycle at scale
-        b = System(workloads.melt_slow(move=move))
+        b = System(workloads.melt_slow(move=move, set_order=order))
         if move == 2:
             b.set_proposal_weights(W)
         b.sweep(3)

@@ -55,6 +55,16 @@ def melt_mid(seed=1, **kw):
     return SystemDesc(**d)
 
 
+def melt_tiny(seed=1, **kw):
+    """The smallest system of the paper's weak-scaling series (n = 2^7 chains
+    of N = 64, sqrt(Nbar) = 128, dL = R_e0/6): 8192 particles in a 2x1x1 R_e0
+    box, 12x6x6 grid, homopolymer-like (chiN = 0), kappaN = 50."""
+    d = dict(n_chains=128, N=64, f=0.5, box_Re=(2.0, 1.0, 1.0), grid=(12, 6, 6), chiN=0.0,
+             kappaN=50.0, seed=seed)
+    d.update(kw)
+    return SystemDesc(**d)
+
+
 def melt_slow(seed=1, **kw):
     """Slow melt: 1,048,576 chains of N=64 in a 32x32x16 R_e0 box, 192x192x96
     grid, chiN=40, kappaN=50.  67,108,864 particles."""
