@@ -69,6 +69,9 @@ class OrSystem(ctypes.Structure):
         ("move", ctypes.c_int),
         ("mlp", ctypes.c_void_p),
         ("chosen", ctypes.c_void_p),
+        ("hamiltonian", ctypes.c_int),
+        ("ext", ctypes.c_void_p),
+        ("forbidden", ctypes.c_void_p),
     ]
 
 
@@ -79,7 +82,7 @@ class OrSweepStats(ctypes.Structure):
 
 class OrObs(ctypes.Structure):
     _fields_ = [("E_b", ctypes.c_double), ("E_nb", ctypes.c_double),
-                ("Re2", ctypes.c_double), ("b2", ctypes.c_double)]
+                ("Re2", ctypes.c_double), ("b2", ctypes.c_double), ("E_ext", ctypes.c_double)]
 
 
 def lib():
@@ -265,6 +268,21 @@ class System:
                            _ptr(pos.z, f32p), _ptr(nA, u32p), _ptr(nB, u32p))
         return nA, nB
 
+    def set_hamiltonian(self, k):
+        """0: K^0_inter, 1: K^1_inter (Eq. hamil-pair)."""
+        self.s.hamiltonian = int(k)
+
+    def set_external(self, ext=None, forbidden=None):
+        """External field per type and cell ((2, cells) kT per particle, added
+        to omega) and cells no particle may enter (nonzero entries); None
+        removes either.  Kept alive here."""
+        self._ext = None if ext is None else np.ascontiguousarray(ext, np.float64).reshape(-1)
+        self._forbidden = None if forbidden is None else np.ascontiguousarray(forbidden, np.uint8)
+        assert self._ext is None or self._ext.size == 2 * self.cells
+        assert self._forbidden is None or self._forbidden.size == self.cells
+        self.s.ext = None if self._ext is None else self._ext.ctypes.data
+        self.s.forbidden = None if self._forbidden is None else self._forbidden.ctypes.data
+
     def fields(self, nA, nB, round_mode=0):
         wA = np.zeros(self.cells, np.float64)
         wB = np.zeros(self.cells, np.float64)
@@ -305,8 +323,8 @@ class System:
         self.L.or_observables(ctypes.byref(self.s), _ptr(pos.x, f32p), _ptr(pos.y, f32p),
                              _ptr(pos.z, f32p), _ptr(nA, u32p), _ptr(nB, u32p),
                              ctypes.byref(o))
-        return {"E_b": o.E_b, "E_nb": o.E_nb, "E_tot": o.E_b + o.E_nb,
-                "Re2": o.Re2, "b2": o.b2}
+        return {"E_b": o.E_b, "E_nb": o.E_nb, "E_ext": o.E_ext,
+                "E_tot": o.E_b + o.E_nb + o.E_ext, "Re2": o.Re2, "b2": o.b2}
 
     def structure_factor(self, nA, nB, m):
         mm = np.ascontiguousarray(np.asarray(m, dtype=np.int32).reshape(-1, 3))

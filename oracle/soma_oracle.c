@@ -238,8 +238,11 @@ static double or_round_fp16(float f) {
 }
 
 /* a4: omega_i(c) = kappa_0 (sum_k phi_k(c) - 1) - sum_{k != i} chi_0/2 (phi_i - phi_k)  */
+/* (option K^0) or kappa_0 (sum_k phi_k(c) - 1) + sum_{k != i} chi_0 phi_k (option K^1), */
 /* with phi_k = n_k / (rho_0 dL^3), kappa_0 = kappaN/N, chi_0 = chiN/N            */
-/* (Eq. omega-fields, option K^0; two types A, B).                                */
+/* (Eq. omega-fields; two types A, B).  The external fields of Sec. 4 are added:   */
+/* a per-type, per-cell potential, and cells no particle may enter (omega = +inf, */
+/* so that every move into them is rejected).                                      */
 void or_fields(const or_system* s, const uint32_t* nA, const uint32_t* nB,
                double* wA, double* wB, int round_mode) {
   const uint64_t cells = (uint64_t)s->grid[0] * s->grid[1] * s->grid[2];
@@ -249,8 +252,16 @@ void or_fields(const or_system* s, const uint32_t* nA, const uint32_t* nB,
     double phiA = (double)nA[c] / s->rho_cell;
     double phiB = (double)nB[c] / s->rho_cell;
     double comp = kappa0 * (phiA + phiB - 1.0);
-    double a = comp - 0.5 * chi0 * (phiA - phiB);
-    double b = comp - 0.5 * chi0 * (phiB - phiA);
+    double a, b;
+    if (s->hamiltonian == 1) {       /* K^1: + sum_{k != i} chi0 phi_k */
+      a = comp + chi0 * phiB;
+      b = comp + chi0 * phiA;
+    } else {                         /* K^0: - sum_{k != i} chi0/2 (phi_i - phi_k) */
+      a = comp - 0.5 * chi0 * (phiA - phiB);
+      b = comp - 0.5 * chi0 * (phiB - phiA);
+    }
+    if (s->ext) { a += s->ext[c]; b += s->ext[cells + c]; }
+    if (s->forbidden && s->forbidden[c]) { a = INFINITY; b = INFINITY; }
     if (round_mode == 1) { a = (double)(float)a; b = (double)(float)b; }
     else if (round_mode == 2) { a = or_round_bf16((float)a); b = or_round_bf16((float)b); }
     else if (round_mode == 3) { a = or_round_fp16((float)a); b = or_round_fp16((float)b); }
@@ -826,16 +837,21 @@ void or_observables(const or_system* s, const float* x, const float* y, const fl
     Re2 += ex * ex + ey * ey + ez * ez;
   }
   const uint64_t cells = (uint64_t)s->grid[0] * s->grid[1] * s->grid[2];
-  double K = 0.0;
+  double K = 0.0, Eext = 0.0;
   for (uint64_t c = 0; c < cells; ++c) {
     double phiA = (double)nA[c] / s->rho_cell;
     double phiB = (double)nB[c] / s->rho_cell;
     double fl = phiA + phiB - 1.0;
     double df = phiA - phiB;
-    K += 0.5 * s->kappaN * fl * fl - 0.25 * s->chiN * df * df;
+    if (s->hamiltonian == 1)
+      K += 0.5 * s->kappaN * fl * fl + s->chiN * phiA * phiB;
+    else
+      K += 0.5 * s->kappaN * fl * fl - 0.25 * s->chiN * df * df;
+    if (s->ext) Eext += (double)nA[c] * s->ext[c] + (double)nB[c] * s->ext[cells + c];
   }
   out->E_b = Eb;
   out->E_nb = s->rho_cell / (double)N * K;
+  out->E_ext = Eext;
   out->Re2 = Re2 / (double)s->n_chains;
   out->b2 = (N > 1) ? b2 / ((double)s->n_chains * (double)(N - 1)) : 0.0;
 }

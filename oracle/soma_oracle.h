@@ -53,6 +53,10 @@ typedef struct {
   const double* mlp;   /* learned proposal parameters (move 2), OR_MLP_PARAMS doubles */
   uint32_t* chosen;    /* optional: particle chosen by each attempt of the
                           molecule-parallel iteration (set_order 2), M entries */
+  int hamiltonian;     /* 0: K^0_inter (default), 1: K^1_inter (Eq. hamil-pair) */
+  const double* ext;   /* optional external field per type and cell (cells of A,
+                          then cells of B), kT per particle, added to omega */
+  const uint8_t* forbidden;  /* optional: nonzero cells no particle may enter */
 } or_system;
 
 typedef struct {
@@ -154,9 +158,10 @@ void or_cycle(const or_system* s, float* x, float* y, float* z,
 /* --- a5: observables --------------------------------------------------------- */
 typedef struct {
   double E_b;     /* sum over bonds of K_b |b|^2, Eq. (h-bond)+(V-harmonic) */
-  double E_nb;    /* Eq. (discrete-ham) with K_fluc + K^0_inter */
+  double E_nb;    /* Eq. (discrete-ham) with K_fluc + K^0_inter (or K^1_inter) */
   double Re2;     /* mean |r_{N-1} - r_0|^2 over chains, dL^2 */
   double b2;      /* mean |r_{i+1} - r_i|^2 over bonds, dL^2 */
+  double E_ext;   /* sum over cells and types of n_t(c) * ext_t(c) */
 } or_obs;
 void or_observables(const or_system* s, const float* x, const float* y, const float* z,
                     const uint32_t* nA, const uint32_t* nB, or_obs* out);

@@ -2,6 +2,7 @@
 the oracle source (a dropped term, a wrong sign, a wrong index, a swapped
 operand) makes at least one pin fail.  Mistakes are planted on the CPU only,
 in a temporary build of ``oracle/soma_oracle.c``; no GPU code is involved."""
+import functools
 import os
 import subprocess
 
@@ -31,7 +32,7 @@ MUTANTS = [
      "    long long jn = (long long)i + side;\n    if (jn < 0 || jn >= (long long)N) continue;\n"
      "    uint64_t n = chain * N + (uint64_t)jn;\n    double rn[3] = { x[n], y[n], z[n] };\n    double d_new",
      PIN.check_ideal_chain_relaxes_to_gaussian_statistics),
-    ("chi_sign", "double a = comp - 0.5 * chi0 * (phiA - phiB);", "double a = comp + 0.5 * chi0 * (phiA - phiB);",
+    ("chi_sign", "      a = comp - 0.5 * chi0 * (phiA - phiB);", "      a = comp + 0.5 * chi0 * (phiA - phiB);",
      PIN.check_fields_closed_forms),
     ("kappa_dropped_minus_one", "kappa0 * (phiA + phiB - 1.0)", "kappa0 * (phiA + phiB)",
      PIN.check_fields_closed_forms),
@@ -85,6 +86,13 @@ MUTANTS = [
     ("molecule_choice_half", "const uint32_t i = (uint32_t)(((uint64_t)(w[3] & 0xFFu) * s->N) >> 8);",
      "const uint32_t i = (uint32_t)(((uint64_t)(w[3] & 0xFFu) * s->N) >> 9);",
      PIN.check_molecule_iteration_attempts),
+    ("k1_coupling_sign", "      a = comp + chi0 * phiB;", "      a = comp - chi0 * phiB;",
+     functools.partial(PIN.check_fields_are_the_energy_derivative, hamiltonian=1)),
+    ("external_types_swapped", "if (s->ext) { a += s->ext[c]; b += s->ext[cells + c]; }",
+     "if (s->ext) { a += s->ext[cells + c]; b += s->ext[c]; }",
+     functools.partial(PIN.check_fields_are_the_energy_derivative, external=True)),
+    ("forbidden_cells_ignored", "if (s->forbidden && s->forbidden[c]) { a = INFINITY; b = INFINITY; }",
+     "", PIN.check_walls_and_external_field_balance),
     ("sort_key_axis", "for (int d = 0; d < 3; ++d) key |= ((b[d] >> bit) & 1u) << (3 * bit + d);",
      "for (int d = 0; d < 3; ++d) key |= ((b[2 - d] >> bit) & 1u) << (3 * bit + d);",
      PIN.check_sort_chains_is_a_spatial_permutation),

@@ -113,13 +113,17 @@ def check_fields_closed_forms(lib=None):
     assert wA[2] == pytest.approx(kappa0) and wB[2] == pytest.approx(kappa0)
 
 
-def check_fields_are_the_energy_derivative(lib=None):
-    """omega_i(c) = d(H_nb/kT)/d n_i(c): Eq. (omega-fields) first line with
-    phi = n/(rho_0 dL^3).  H_nb is quadratic, so the central difference in the
-    integer count is exact."""
+def check_fields_are_the_energy_derivative(lib=None, hamiltonian=0, external=False):
+    """omega_i(c) = d(H_nb/kT + E_ext)/d n_i(c): Eq. (omega-fields) with
+    phi = n/(rho_0 dL^3), for either interaction option, plus the external
+    potential.  The energy is quadratic in the counts, so the central
+    difference in the integer count is exact."""
     d = SystemDesc(n_chains=300, N=10, f=0.4, box_Re=(1.5, 1.5, 1.0), grid=(3, 3, 2),
                    chiN=27.0, kappaN=35.0)
     s = oracle_system(d, lib)
+    s.set_hamiltonian(hamiltonian)
+    if external:
+        s.set_external(np.random.default_rng(3).normal(size=(2, s.cells)))
     rng = np.random.default_rng(7)
     nA = rng.integers(5, 40, s.cells).astype(np.uint32)
     nB = rng.integers(5, 40, s.cells).astype(np.uint32)
@@ -131,8 +135,8 @@ def check_fields_are_the_energy_derivative(lib=None):
             dn = [nA.copy(), nB.copy()]
             up[which][c] += 1
             dn[which][c] -= 1
-            Eu = s.observables(pos, *up)["E_nb"]
-            Ed = s.observables(pos, *dn)["E_nb"]
+            ou, od = s.observables(pos, *up), s.observables(pos, *dn)
+            Eu, Ed = ou["E_nb"] + ou["E_ext"], od["E_nb"] + od["E_ext"]
             assert (Eu - Ed) / 2 == pytest.approx(w[c], rel=1e-9, abs=1e-9)
 
 
@@ -267,6 +271,50 @@ def check_two_particle_balance_brute_force(set_order, lib=None, move=0):
     assert chi2 < 64 + 8 * math.sqrt(2 * 64)  # 64 bins, loose upper bound
 
 
+def check_walls_and_external_field_balance(lib=None, move=0):
+    """Dimers in an external potential with two forbidden cells (chiN = kappaN
+    = 0, so omega is the external field, +inf in the forbidden cells): the
+    stationary cell-pair distribution is the exact one with weight 0 in the
+    forbidden cells (exp(-inf)), and no particle ever enters one."""
+    L, Re = 2, 1.5
+    d = SystemDesc(n_chains=4096, N=2, f=0.5, box_Re=(L / Re,) * 3, grid=(L,) * 3,
+                   chiN=0.0, kappaN=0.0, seed=23, move=move)
+    s = oracle_system(d, lib)
+    rng = np.random.default_rng(9)
+    ext = rng.normal(size=(2, L**3))
+    forbidden = np.zeros(L**3, np.uint8)
+    forbidden[[2, 5]] = 1
+    s.set_external(ext, forbidden)
+    nA, nB = s.histogram(s.empty_positions())
+    wA, wB = s.fields(nA, nB)
+    assert np.all(np.isinf(wA[[2, 5]])) and np.all(np.isinf(wB[[2, 5]]))
+    np.testing.assert_array_equal(wA[forbidden == 0], ext[0][forbidden == 0])
+    K = s.params.K_b
+    Pex = _pair_cell_probabilities(K, L, wA, wB)
+    p = s.init_chains()
+    for sweep in range(100):
+        s.sweep(p, wA, wB, sweep)
+    T = 1500
+    counts = np.zeros((d.n_chains, L**6))
+    for sweep in range(100, 100 + T):
+        s.sweep(p, wA, wB, sweep)
+        P = p.stacked().reshape(3, d.n_chains, 2)
+        c0 = _cells_of(P[:, :, 0], L)
+        c1 = _cells_of(P[:, :, 1], L)
+        assert not forbidden[c0].any() and not forbidden[c1].any()
+        counts[np.arange(d.n_chains), c0 * L**3 + c1] += 1
+    freq = counts / T
+    est = freq.mean(0)
+    se = freq.std(0) / math.sqrt(d.n_chains)
+    z = (est - Pex.reshape(-1)) / np.maximum(se, 1e-12)
+    z[(Pex.reshape(-1) == 0) & (est == 0)] = 0.0
+    assert np.max(np.abs(z)) < 5.0, (np.max(np.abs(z)), np.argmax(np.abs(z)))
+
+
+def test_walls_and_external_field_balance(oracle_lib):
+    check_walls_and_external_field_balance()
+
+
 # --------------------------------------------------------------------------
 # Sweep mechanics: displacements bounded by a, accepted moves land on the draw
 # --------------------------------------------------------------------------
@@ -394,8 +442,30 @@ def test_fields_closed_forms(oracle_lib):
     check_fields_closed_forms()
 
 
-def test_fields_are_the_energy_derivative(oracle_lib):
-    check_fields_are_the_energy_derivative()
+@pytest.mark.parametrize("hamiltonian,external", [(0, False), (1, False), (0, True), (1, True)])
+def test_fields_are_the_energy_derivative(oracle_lib, hamiltonian, external):
+    check_fields_are_the_energy_derivative(hamiltonian=hamiltonian, external=external)
+
+
+def check_k1_fields_closed_forms(lib=None):
+    """Option K^1: a pure A cell at the mean density has omega_A = 0 and
+    omega_B = chi_0 (the cost of one B among A); a symmetric cell at the mean
+    density has omega_A = omega_B = chi_0 / 2."""
+    d = SystemDesc(n_chains=40, N=4, f=0.5, box_Re=(2.0, 2.0, 2.0), grid=(2, 2, 2),
+                   chiN=20.0, kappaN=50.0)
+    s = oracle_system(d, lib)
+    s.set_hamiltonian(1)
+    nA = np.full(8, 10, np.uint32)
+    nB = np.full(8, 10, np.uint32)
+    nA[0], nB[0] = 20, 0
+    wA, wB = s.fields(nA, nB)
+    chi0 = 20.0 / 4
+    assert wA[0] == pytest.approx(0.0, abs=1e-12) and wB[0] == pytest.approx(chi0)
+    assert wA[1] == pytest.approx(chi0 / 2) and wB[1] == pytest.approx(chi0 / 2)
+
+
+def test_k1_fields_closed_forms(oracle_lib):
+    check_k1_fields_closed_forms()
 
 
 def test_field_rounding_modes(oracle_lib):
