@@ -108,7 +108,9 @@ typedef struct soma_system_desc {
   double f;              /* A fraction of a chain, 0..1 */
   double box_Re[3];      /* box edges in units of R_e0 (> 0) */
   uint32_t grid[3];      /* cells per axis, 1..4096; dL = box/grid equal on all axes */
-  uint32_t reserved0;
+  uint32_t hamiltonian;  /* interaction option of Eq. (hamil-pair): 0 K^0_inter,
+                            1 K^1_inter (omega_A/B = kappa_0 (phi_A + phi_B - 1)
+                            + chi_0 phi_B/A, Eq. omega-fields second line) */
   double chiN;           /* Flory-Huggins chi_0 N (Eq. hamil-pair) */
   double kappaN;         /* inverse compressibility kappa_0 N (Eq. hamil-comp) */
   double a_Re;           /* maximal trial displacement per axis in R_e0;
@@ -128,8 +130,8 @@ typedef struct soma_t soma_t;
 /* Observables, reduced in FP64 on the device.  Energies in kT, lengths in dL. */
 typedef struct soma_obs {
   double E_b;        /* sum over bonds of (k0/2)|b|^2, Eq. (h-bond), (V-harmonic) */
-  double E_nb;       /* Eq. (discrete-ham) with K_fluc + K^0_inter of the current n */
-  double E_tot;      /* E_b + E_nb */
+  double E_nb;       /* Eq. (discrete-ham) with K_fluc + K_inter of the current n */
+  double E_tot;      /* E_b + E_nb + E_ext */
   double Re2;        /* mean over chains of |r_{N-1} - r_0|^2 */
   double Re2_rel;    /* Re2 / R_e0^2 */
   double b2;         /* mean over bonds of |r_{i+1} - r_i|^2 */
@@ -138,6 +140,8 @@ typedef struct soma_obs {
   uint64_t sweeps;   /* completed SCMF cycles since creation */
   uint32_t max_cell; /* largest n_A + n_B of any cell */
   uint32_t reserved;
+  double E_ext;      /* sum over cells of n_A ext_A + n_B ext_B (soma_set_external);
+                        E_tot = E_b + E_nb + E_ext */
 } soma_obs;
 
 /* Accumulated device time per kernel while timing is on (soma_set_timing). */
@@ -189,6 +193,20 @@ soma_status soma_get_positions(soma_t* h, float* dst, size_t n, int dst_on_devic
  * SOMA_EINVAL and nothing is copied.  Synchronises (the range check of a
  * device source runs on the device first). */
 soma_status soma_set_positions(soma_t* h, const float* src, size_t n, int src_on_device);
+
+/* External fields (Sec. 4): ext (2*cells floats: the potential of an A
+ * particle in each cell, then of a B particle, kT per particle) is added to
+ * omega at every field update, e.g. a linear attraction of one type to a
+ * surface; forbidden (cells bytes, nonzero = no particle may enter the cell,
+ * e.g. a confining wall) makes omega +inf there, so every move into such a
+ * cell is rejected.  Either pointer may be NULL (that field is removed).
+ * Forbidden cells take uniform moves only (SOMA_EINVAL otherwise: the smart
+ * Monte Carlo and learned proposals use field gradients).  A particle already
+ * inside a forbidden cell may leave it but none enters one.  Takes effect at
+ * the next field update (soma_update_fields applies it at once); the
+ * handle keeps its own copies.  Synchronises. */
+soma_status soma_set_external(soma_t* h, const float* ext, const uint8_t* forbidden,
+                              int src_on_device);
 
 /* FP64 observables of the current state (Eq. h-bond, Eq. discrete-ham).
  * Synchronises. */

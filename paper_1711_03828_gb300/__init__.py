@@ -40,6 +40,7 @@ class SystemDesc:
     seed: int = 1
     replica_id: int = 0
     flags: int = 0
+    hamiltonian: int = 0
 
     @property
     def M(self):
@@ -65,6 +66,7 @@ class SystemDesc:
         d.set_order = int(self.set_order)
         d.grid_dtype = int(self.grid_dtype)
         d.flags = int(self.flags)
+        d.hamiltonian = int(self.hamiltonian)
         d.seed = int(self.seed)
         d.replica_id = int(self.replica_id)
         d.stream = stream
@@ -143,6 +145,30 @@ class System:
             assert pos.is_contiguous() and pos.numel() == 3 * M
             _abi.soma_set_positions(self.h, ctypes.c_void_p(pos.data_ptr()), pos.numel(),
                                     1 if pos.is_cuda else 0)
+
+    def set_external(self, ext=None, forbidden=None):
+        """External potential ext ((2, cells) float32: A then B, kT per
+        particle) and forbidden cells ((cells,) nonzero = closed); numpy
+        arrays or CUDA tensors; None removes that field."""
+        cells = self.desc.cells
+        keep = []
+
+        def arg(a, dtype, n):
+            if a is None:
+                return None, 0
+            if isinstance(a, np.ndarray):
+                b = np.ascontiguousarray(a, dtype=dtype).reshape(-1)
+                assert b.size == n
+                keep.append(b)
+                return ctypes.c_void_p(b.ctypes.data), 0
+            assert a.is_contiguous() and a.numel() == n
+            return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+
+        e, on_e = arg(ext, np.float32, 2 * cells)
+        f, on_f = arg(forbidden, np.uint8, cells)
+        if e is not None and f is not None:
+            assert on_e == on_f, "ext and forbidden must both be host or both device arrays"
+        _abi.soma_set_external(self.h, e, f, on_e or on_f)
 
     def get_density(self, out=None):
         """Packed occupation numbers (cells,) uint32: n_A | n_B << 16."""

@@ -31,7 +31,7 @@ class SomaSystemDesc(ctypes.Structure):
         ("f", ctypes.c_double),
         ("box_Re", ctypes.c_double * 3),
         ("grid", ctypes.c_uint32 * 3),
-        ("reserved0", ctypes.c_uint32),
+        ("hamiltonian", ctypes.c_uint32),
         ("chiN", ctypes.c_double),
         ("kappaN", ctypes.c_double),
         ("a_Re", ctypes.c_double),
@@ -52,7 +52,7 @@ class SomaObs(ctypes.Structure):
         ("Re2", ctypes.c_double), ("Re2_rel", ctypes.c_double), ("b2", ctypes.c_double),
         ("accepted", ctypes.c_uint64), ("attempted", ctypes.c_uint64),
         ("sweeps", ctypes.c_uint64), ("max_cell", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32), ("E_ext", ctypes.c_double),
     ]
 
 
@@ -103,6 +103,7 @@ _SIGS = {
     "soma_get_fields": ([_P, _P, _c.c_size_t, _c.c_int], _c.c_int),
     "soma_get_positions": ([_P, _P, _c.c_size_t, _c.c_int], _c.c_int),
     "soma_set_positions": ([_P, _P, _c.c_size_t, _c.c_int], _c.c_int),
+    "soma_set_external": ([_P, _P, _P, _c.c_int], _c.c_int),
     "soma_observables": ([_P, _c.POINTER(SomaObs)], _c.c_int),
     "soma_structure_factor": ([_P, _P, _c.c_size_t, _P], _c.c_int),
     "soma_get_sweep": ([_P, _c.POINTER(_c.c_uint64)], _c.c_int),
@@ -172,6 +173,7 @@ soma_get_density = _wrap("soma_get_density")
 soma_get_fields = _wrap("soma_get_fields")
 soma_get_positions = _wrap("soma_get_positions")
 soma_set_positions = _wrap("soma_set_positions")
+soma_set_external = _wrap("soma_set_external")
 soma_observables = _wrap("soma_observables")
 soma_structure_factor = _wrap("soma_structure_factor")
 soma_get_sweep = _wrap("soma_get_sweep")

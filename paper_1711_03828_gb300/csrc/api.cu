@@ -80,6 +80,9 @@ struct soma_t {
   unsigned* d_err = nullptr;                 // [0] error bits, [1] arrival counter,
                                              // [2] range flag of soma_set_positions
   double* d_scratch = nullptr;
+  float* d_ext = nullptr;                    // external potential, 2 * cells (lazy)
+  uint8_t* d_forbidden = nullptr;            // forbidden cells, cells bytes (lazy)
+  bool has_ext = false, has_forbidden = false;
   double* d_out = nullptr;
   size_t scratch_doubles = 0;
   double* d_tw = nullptr;
@@ -148,6 +151,7 @@ soma_status validate(const soma_system_desc* d) {
   if (d->flags & ~(SOMA_FLAG_NO_SORT | SOMA_FLAG_LEARNED_FP32 | SOMA_FLAG_LEARNED_UMMA))
     return fail(SOMA_EINVAL, "unknown flags 0x%x", d->flags);
   if (d->replica_id > 0xFFFFFFu) return fail(SOMA_EINVAL, "replica_id must be < 2^24");
+  if (d->hamiltonian > 1) return fail(SOMA_EINVAL, "hamiltonian=%u unknown", d->hamiltonian);
   return SOMA_OK;
 }
 
@@ -205,6 +209,8 @@ void release(soma_t* h) {
   cudaFree(h->d_counters);
   cudaFree(h->d_err);
   cudaFree(h->d_scratch);
+  cudaFree(h->d_ext);
+  cudaFree(h->d_forbidden);
   cudaFree(h->d_tw);
   cudaFree(h->mlp_w);
   cudaFree(h->mlp_q);
@@ -228,6 +234,9 @@ FieldArgs field_args(soma_t* h, int after_sweep) {
   f.kappa0 = (float)(h->desc.kappaN / (double)h->desc.N);
   f.half_chi0 = (float)(0.5 * h->desc.chiN / (double)h->desc.N);
   f.after_sweep = after_sweep;
+  f.hamiltonian = (int)h->desc.hamiltonian;
+  f.ext = h->has_ext ? h->d_ext : nullptr;
+  f.forbidden = h->has_forbidden ? h->d_forbidden : nullptr;
   return f;
 }
 
@@ -399,7 +408,7 @@ soma_status soma_create(const soma_system_desc* desc, soma_t** out) {
   const size_t cells = h->g.cells;
   const size_t wb = wbytes(h->grid_dtype);
   h->scratch_doubles = (size_t)SQ_BLOCKS * 2 * SQ_MAX;
-  if (h->scratch_doubles < 4 * (size_t)OBS_BLOCKS) h->scratch_doubles = 4 * (size_t)OBS_BLOCKS;
+  if (h->scratch_doubles < 5 * (size_t)OBS_BLOCKS) h->scratch_doubles = 5 * (size_t)OBS_BLOCKS;
 #define ALLOC(ptr, bytes)                                                   \
   do {                                                                      \
     e = cudaMalloc((void**)&(ptr), (bytes));                                \
@@ -573,13 +582,44 @@ soma_status soma_set_positions(soma_t* h, const float* src, size_t n, int src_on
   return SOMA_OK;
 }
 
+soma_status soma_set_external(soma_t* h, const float* ext, const uint8_t* forbidden,
+                              int src_on_device) {
+  if (!h) return fail(SOMA_EINVAL, "handle is NULL");
+  if (forbidden && h->desc.move != SOMA_MOVE_UNIFORM)
+    return fail(SOMA_EINVAL, "forbidden cells take uniform moves only");
+  if (h->batched) return fail(SOMA_ESTATE, "a batch member has no external fields");
+  const size_t cells = h->g.cells;
+  const cudaMemcpyKind k = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaError_t e;
+  if (ext) {
+    if (!h->d_ext) {
+      e = cudaMalloc((void**)&h->d_ext, sizeof(float) * 2 * cells);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc ext");
+    }
+    SOMA_CUDA(cudaMemcpyAsync(h->d_ext, ext, sizeof(float) * 2 * cells, k, h->stream));
+  }
+  if (forbidden) {
+    if (!h->d_forbidden) {
+      e = cudaMalloc((void**)&h->d_forbidden, cells);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc forbidden");
+    }
+    SOMA_CUDA(cudaMemcpyAsync(h->d_forbidden, forbidden, cells, k, h->stream));
+  }
+  h->has_ext = ext != nullptr;
+  h->has_forbidden = forbidden != nullptr;
+  // the captured cycle holds the old field-kernel arguments
+  if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+  return sync(h);
+}
+
 soma_status soma_observables(soma_t* h, soma_obs* out) {
   if (!h || !out) return fail(SOMA_EINVAL, "NULL argument");
   const uint32_t* nn = h->n[h->host_sweep & 1];
   SOMA_CUDA(launch_observables(h->g, h->x(), h->y(), h->z(), nn, 1.0 / h->rho_cell,
-                               h->desc.kappaN, h->desc.chiN, h->d_scratch, h->d_out, h->stream));
+                               h->desc.kappaN, h->desc.chiN, (int)h->desc.hamiltonian,
+                               h->has_ext ? h->d_ext : nullptr, h->d_scratch, h->d_out, h->stream));
   h->launches += 3;
-  double r[4];
+  double r[5];
   unsigned long long c[2];
   SOMA_CUDA(cudaMemcpyAsync(r, h->d_out, sizeof r, cudaMemcpyDeviceToHost, h->stream));
   SOMA_CUDA(cudaMemcpyAsync(c, h->d_counters, sizeof c, cudaMemcpyDeviceToHost, h->stream));
@@ -589,7 +629,8 @@ soma_status soma_observables(soma_t* h, soma_obs* out) {
   const double nb = nch * (double)(h->g.N > 1 ? h->g.N - 1 : 0);
   out->E_b = h->K_b * r[0];
   out->E_nb = h->rho_cell / (double)h->g.N * r[2];
-  out->E_tot = out->E_b + out->E_nb;
+  out->E_ext = r[4];
+  out->E_tot = out->E_b + out->E_nb + out->E_ext;
   out->Re2 = r[1] / nch;
   out->Re2_rel = out->Re2 / (h->Re * h->Re);
   out->b2 = nb > 0 ? r[0] / nb : 0.0;
@@ -966,6 +1007,8 @@ soma_status soma_batch_create(const soma_system_desc* descs, uint32_t n, void* s
       return fail(SOMA_EINVAL, "batch member %u: N=%u (a batch takes even N <= 64)", k, d.N);
     if (d.move != SOMA_MOVE_UNIFORM)
       return fail(SOMA_EINVAL, "batch member %u: only uniform moves are batched", k);
+    if (d.set_order == SOMA_ITERATION_MOLECULE)
+      return fail(SOMA_EINVAL, "batch member %u: a batch runs the SET scheme", k);
     if (d.seed != descs[0].seed)
       return fail(SOMA_EINVAL, "batch member %u: all members share one seed (use replica_id)", k);
     if (d.grid_dtype != descs[0].grid_dtype)
@@ -1021,6 +1064,7 @@ soma_status soma_batch_create(const soma_system_desc* descs, uint32_t n, void* s
     S.kappa0 = (float)(h->desc.kappaN / (double)h->desc.N);
     S.half_chi0 = (float)(0.5 * h->desc.chiN / (double)h->desc.N);
     S.set_order_random = h->desc.set_order == SOMA_SET_ORDER_RANDOM;
+    S.hamiltonian = (int)h->desc.hamiltonian;
     cells += h->g.cells;
     if (cells < h->g.cells) { batch_release(b); return fail(SOMA_EINVAL, "batch grids exceed 2^32 cells"); }
   }

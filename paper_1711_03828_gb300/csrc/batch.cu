@@ -113,9 +113,17 @@ __global__ void __launch_bounds__(256) fields_batch_kernel(const BatchArgs p, ui
     const float phiA = (float)a * S->inv_rho;
     const float phiB = (float)b * S->inv_rho;
     const float comp = S->kappa0 * (phiA + phiB - 1.f);
-    const float d = S->half_chi0 * (phiA - phiB);
-    static_cast<WT*>(const_cast<void*>(S->wA))[local] = store_cvt<WT>(comp - d);
-    static_cast<WT*>(const_cast<void*>(S->wB))[local] = store_cvt<WT>(comp + d);
+    float wa, wb;
+    if (S->hamiltonian) {
+      wa = fmaf(2.f * S->half_chi0, phiB, comp);
+      wb = fmaf(2.f * S->half_chi0, phiA, comp);
+    } else {
+      const float d = S->half_chi0 * (phiA - phiB);
+      wa = comp - d;
+      wb = comp + d;
+    }
+    static_cast<WT*>(const_cast<void*>(S->wA))[local] = store_cvt<WT>(wa);
+    static_cast<WT*>(const_cast<void*>(S->wB))[local] = store_cvt<WT>(wb);
     bad |= (a >= 0xC000u) | (b >= 0xC000u);
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, ERR_OVERFLOW);

@@ -211,6 +211,9 @@ struct FieldArgs {
   float half_chi0;          // chiN/(2N)
   int after_sweep;          // 1: read n[(s+1)&1], clear n[s&1], then s += 1
                             // 0: read n[s&1], clear n[(s+1)&1]
+  int hamiltonian;          // 0: K^0_inter, 1: K^1_inter
+  const float* ext;         // external potential, A cells then B cells (or NULL)
+  const uint8_t* forbidden; // cells no particle may enter (or NULL)
 };
 
 // One system of a batch (device table entry).
@@ -229,6 +232,7 @@ struct BatchSys {
   uint32_t cell_begin;             // offset of this grid in the concatenated cells
   float inv_rho, kappa0, half_chi0;
   int set_order_random;
+  int hamiltonian;                 // 0: K^0_inter, 1: K^1_inter
 };
 
 struct BatchItem {

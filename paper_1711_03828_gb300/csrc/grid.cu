@@ -75,9 +75,22 @@ __global__ void __launch_bounds__(256) fields_kernel(const FieldArgs p, unsigned
     const float phiA = (float)a * p.inv_rho;
     const float phiB = (float)b * p.inv_rho;
     const float comp = p.kappa0 * (phiA + phiB - 1.f);
-    const float d = p.half_chi0 * (phiA - phiB);
-    wA[c] = store_cvt<WT>(comp - d);
-    wB[c] = store_cvt<WT>(comp + d);
+    float wa, wb;
+    if (p.hamiltonian) {          // K^1: + chi_0 phi_k of the other type
+      wa = fmaf(2.f * p.half_chi0, phiB, comp);
+      wb = fmaf(2.f * p.half_chi0, phiA, comp);
+    } else {                      // K^0: -/+ chi_0/2 (phi_A - phi_B)
+      const float d = p.half_chi0 * (phiA - phiB);
+      wa = comp - d;
+      wb = comp + d;
+    }
+    if (p.ext) {
+      wa += p.ext[c];
+      wb += p.ext[p.g.cells + c];
+    }
+    if (p.forbidden && p.forbidden[c]) wa = wb = __int_as_float(0x7F800000);   // +inf
+    wA[c] = store_cvt<WT>(wa);
+    wB[c] = store_cvt<WT>(wb);
     bad |= (a >= 0xC000u) | (b >= 0xC000u);
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(p.err, ERR_OVERFLOW);
@@ -298,16 +311,19 @@ __global__ void __launch_bounds__(256) chain_obs_kernel(const Geom g, const floa
 
 __global__ void __launch_bounds__(256) grid_obs_kernel(const Geom g, const uint32_t* __restrict__ n,
                                                        double inv_rho, double kappaN, double chiN,
+                                                       int hamiltonian, const float* __restrict__ ext,
                                                        double* __restrict__ part) {
   __shared__ double sh[2 * 32];
-  double v[2] = {0.0, 0.0};
+  double v[2] = {0.0, 0.0}, e_ext = 0.0;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < g.cells; c += stride) {
     const uint32_t w = n[c];
     const double a = (double)(w & 0xFFFFu), b = (double)(w >> 16);
     const double phiA = a * inv_rho, phiB = b * inv_rho;
     const double fl = phiA + phiB - 1.0, df = phiA - phiB;
-    v[0] += 0.5 * kappaN * fl * fl - 0.25 * chiN * df * df;
+    v[0] += hamiltonian ? 0.5 * kappaN * fl * fl + chiN * phiA * phiB
+                        : 0.5 * kappaN * fl * fl - 0.25 * chiN * df * df;
+    if (ext) e_ext += a * (double)ext[c] + b * (double)ext[g.cells + c];
     v[1] = fmax(v[1], a + b);
   }
   // the max is folded by a second pass over the per-warp maxima
@@ -315,44 +331,49 @@ __global__ void __launch_bounds__(256) grid_obs_kernel(const Geom g, const uint3
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
   __shared__ double shm[32];
   if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = mx;
-  double s1[1] = {v[0]};
-  block_sum<1>(s1, sh);
+  double s1[2] = {v[0], e_ext};
+  block_sum<2>(s1, sh);
   if (threadIdx.x == 0) {
     double m2 = 0.0;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m2 = fmax(m2, shm[k]);
-    part[2 * OBS_BLOCKS + blockIdx.x * 2 + 0] = s1[0];
-    part[2 * OBS_BLOCKS + blockIdx.x * 2 + 1] = m2;
+    part[2 * OBS_BLOCKS + blockIdx.x * 3 + 0] = s1[0];
+    part[2 * OBS_BLOCKS + blockIdx.x * 3 + 1] = m2;
+    part[2 * OBS_BLOCKS + blockIdx.x * 3 + 2] = s1[1];
   }
 }
 
 __global__ void obs_final_kernel(const double* __restrict__ part, int nb_chain, int nb_grid,
                                  double* __restrict__ out) {
   if (threadIdx.x != 0) return;
-  double b2 = 0.0, re2 = 0.0, k = 0.0, mx = 0.0;
+  double b2 = 0.0, re2 = 0.0, k = 0.0, mx = 0.0, ee = 0.0;
   for (int i = 0; i < nb_chain; ++i) {
     b2 += part[2 * i];
     re2 += part[2 * i + 1];
   }
   for (int i = 0; i < nb_grid; ++i) {
-    k += part[2 * OBS_BLOCKS + 2 * i];
-    mx = fmax(mx, part[2 * OBS_BLOCKS + 2 * i + 1]);
+    k += part[2 * OBS_BLOCKS + 3 * i];
+    mx = fmax(mx, part[2 * OBS_BLOCKS + 3 * i + 1]);
+    ee += part[2 * OBS_BLOCKS + 3 * i + 2];
   }
   out[0] = b2;
   out[1] = re2;
   out[2] = k;
   out[3] = mx;
+  out[4] = ee;
 }
 
 cudaError_t launch_observables(const Geom& g, const float* x, const float* y, const float* z,
                                const uint32_t* n, double inv_rho, double kappaN, double chiN,
-                               double* part, double* out, cudaStream_t st) {
+                               int hamiltonian, const float* ext, double* part, double* out,
+                               cudaStream_t st) {
   const uint64_t M = g.n_chains * g.N;
   uint64_t nb1 = (M + 255) / 256;
   if (nb1 > OBS_BLOCKS) nb1 = OBS_BLOCKS;
   uint64_t nb2 = ((uint64_t)g.cells + 255) / 256;
   if (nb2 > OBS_BLOCKS) nb2 = OBS_BLOCKS;
   chain_obs_kernel<<<(unsigned)nb1, 256, 0, st>>>(g, x, y, z, part);
-  grid_obs_kernel<<<(unsigned)nb2, 256, 0, st>>>(g, n, inv_rho, kappaN, chiN, part);
+  grid_obs_kernel<<<(unsigned)nb2, 256, 0, st>>>(g, n, inv_rho, kappaN, chiN, hamiltonian, ext,
+                                                 part);
   obs_final_kernel<<<1, 32, 0, st>>>(part, (int)nb1, (int)nb2, out);
   return cudaGetLastError();
 }

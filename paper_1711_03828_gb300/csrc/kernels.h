@@ -52,9 +52,11 @@ cudaError_t launch_convert_fields(const void* w, int grid_dtype, float* dst, uin
 //   out[2] = sum over cells of K(c) (Eq. discrete-ham, without rho dL^3/N),
 //   out[3] = max over cells of n_A + n_B.
 constexpr int OBS_BLOCKS = 1024;
+// part: 5 * OBS_BLOCKS doubles; out: b2, Re2 sums, K sum, max cell, external energy
 cudaError_t launch_observables(const Geom& g, const float* x, const float* y, const float* z,
                                const uint32_t* n, double inv_rho, double kappaN, double chiN,
-                               double* part, double* out, cudaStream_t st);
+                               int hamiltonian, const float* ext, double* part, double* out,
+                               cudaStream_t st);
 
 // S(q) for k <= SQ_MAX wave vectors; tw holds per q the FP64 twiddles
 // (cos, sin) of the three axes, laid out [q][nx + ny + nz][2].

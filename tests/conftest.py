@@ -38,7 +38,9 @@ def oracle_system(desc, L=None, **over):
               chiN=desc.chiN, kappaN=desc.kappaN, a_Re=desc.a_Re, seed=desc.seed,
               replica=desc.replica_id, set_order=desc.set_order, move=desc.move)
     kw.update(over)
-    return oracle.System(L=L, **kw)
+    s = oracle.System(L=L, **kw)
+    s.set_hamiltonian(getattr(desc, "hamiltonian", 0))
+    return s
 
 
 @pytest.fixture(scope="session")
