@@ -8,7 +8,7 @@
  * shares no code, header, constant table or helper with the CUDA library under
  * paper_1711_03828_gb300/csrc; neither includes the other.
  *
- * Conventions (the readings of the paper are listed in the design doc):
+ * Conventions (where the paper leaves a choice open, the reading taken):
  *   - lengths in units of the grid spacing dL (cubic cells, Sec. 2.1), so the
  *     cell of a particle is floor(x) taken modulo the grid extent;
  *   - energies in kT; omega_t(c) is the per-particle field energy of Eq.
