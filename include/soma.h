@@ -189,9 +189,10 @@ soma_status soma_get_positions(soma_t* h, float* dst, size_t n, int dst_on_devic
 /* Replace positions (3*M floats, SoA).  Does not recompute the fields: call
  * soma_update_fields to make n and omega follow.  Every coordinate must be
  * finite with |x| < 2^18 dL (the range in which the cell fold is exact;
- * chains diffuse far less than that in any feasible run): otherwise
- * SOMA_EINVAL and nothing is copied.  Synchronises (the range check of a
- * device source runs on the device first). */
+ * chains diffuse far less than that in any feasible run).  The check runs on
+ * the device after the copy: on a violation the call returns SOMA_EINVAL and
+ * the handle refuses soma_sweep, soma_update_fields and training (SOMA_ESTATE)
+ * until a later call sets valid positions.  Synchronises. */
 soma_status soma_set_positions(soma_t* h, const float* src, size_t n, int src_on_device);
 
 /* External fields (Sec. 4): ext (2*cells floats: the potential of an A

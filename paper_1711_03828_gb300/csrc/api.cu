@@ -80,6 +80,7 @@ struct soma_t {
   unsigned* d_err = nullptr;                 // [0] error bits, [1] arrival counter,
                                              // [2] range flag of soma_set_positions
   double* d_scratch = nullptr;
+  bool pos_invalid = false;                  // soma_set_positions was given positions out of range
   float* d_ext = nullptr;                    // external potential, 2 * cells (lazy)
   uint8_t* d_forbidden = nullptr;            // forbidden cells, cells bytes (lazy)
   bool has_ext = false, has_forbidden = false;
@@ -482,6 +483,7 @@ soma_status soma_destroy(soma_t* h) {
 soma_status soma_sweep(soma_t* h, uint32_t n) {
   if (!h) return fail(SOMA_EINVAL, "handle is NULL");
   if (h->batched) return fail(SOMA_ESTATE, "this system belongs to a batch: use soma_batch_sweep");
+  if (h->pos_invalid) return fail(SOMA_ESTATE, "positions out of range: set valid positions first");
   uint32_t done = 0;
   if (!h->timing && n >= GRAPH_CHUNK) {
     if (!h->graph) {
@@ -506,6 +508,7 @@ soma_status soma_sweep(soma_t* h, uint32_t n) {
 
 soma_status soma_update_fields(soma_t* h) {
   if (!h) return fail(SOMA_EINVAL, "handle is NULL");
+  if (h->pos_invalid) return fail(SOMA_ESTATE, "positions out of range: set valid positions first");
   return update_fields(h);
 }
 
@@ -560,25 +563,24 @@ soma_status soma_get_positions(soma_t* h, float* dst, size_t n, int dst_on_devic
 soma_status soma_set_positions(soma_t* h, const float* src, size_t n, int src_on_device) {
   if (!h || !src) return fail(SOMA_EINVAL, "NULL argument");
   if (n != 3 * h->M) return fail(SOMA_EINVAL, "n=%zu, expected 3*M=%llu", n, (unsigned long long)(3 * h->M));
-  // every coordinate must lie in the supported range of the cell fold
-  const float lim = (float)POS_LIMIT;
-  if (src_on_device) {
-    unsigned flag = 0;
-    SOMA_CUDA(cudaMemsetAsync(h->d_err + 2, 0, sizeof(unsigned), h->stream));
-    SOMA_CUDA(launch_range_check(src, 3 * h->M, lim, h->d_err + 2, h->sm_count, h->stream));
-    SOMA_CUDA(cudaMemcpyAsync(&flag, h->d_err + 2, sizeof flag, cudaMemcpyDeviceToHost, h->stream));
-    SOMA_CUDA(cudaStreamSynchronize(h->stream));
-    h->launches += 1;
-    if (flag) return fail(SOMA_EINVAL, "a position is not finite or has |x| >= 2^18 dL");
-  } else {
-    for (size_t i = 0; i < n; ++i)
-      if (!(std::fabs(src[i]) < lim))
-        return fail(SOMA_EINVAL, "position %zu (%g) is not finite or has |x| >= 2^18 dL", i, (double)src[i]);
-  }
   const cudaMemcpyKind k = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   for (int d = 0; d < 3; ++d)
     SOMA_CUDA(cudaMemcpyAsync(h->pos + d * h->plane, src + d * h->M, sizeof(float) * h->M, k, h->stream));
-  if (!src_on_device) SOMA_CUDA(cudaStreamSynchronize(h->stream));
+  // every coordinate must lie in the supported range of the cell fold; the
+  // check runs on the device copy, and a handle holding positions outside it
+  // refuses to sweep until valid positions are set
+  const float lim = (float)POS_LIMIT;
+  unsigned flag = 0;
+  SOMA_CUDA(cudaMemsetAsync(h->d_err + 2, 0, sizeof(unsigned), h->stream));
+  for (int d = 0; d < 3; ++d)
+    SOMA_CUDA(launch_range_check(h->pos + d * h->plane, h->M, lim, h->d_err + 2, h->sm_count, h->stream));
+  SOMA_CUDA(cudaMemcpyAsync(&flag, h->d_err + 2, sizeof flag, cudaMemcpyDeviceToHost, h->stream));
+  SOMA_CUDA(cudaStreamSynchronize(h->stream));
+  h->launches += 3;
+  h->pos_invalid = flag != 0;
+  if (flag)
+    return fail(SOMA_EINVAL, "a position is not finite or has |x| >= 2^18 dL: set valid positions "
+                             "before the next sweep");
   return SOMA_OK;
 }
 
@@ -791,6 +793,7 @@ soma_status soma_proposal_grad(soma_t* h, const float* w, const uint32_t* sample
 }
 
 soma_status soma_proposal_train(soma_t* h, const soma_train_cfg* cfg, soma_train_log* log) {
+  if (h && h->pos_invalid) return fail(SOMA_ESTATE, "positions out of range: set valid positions first");
   if (!h || !cfg) return fail(SOMA_EINVAL, "NULL argument");
   if (cfg->batch < 1 || cfg->steps < 1) return fail(SOMA_EINVAL, "steps and batch must be >= 1");
   float* dJ = nullptr;
@@ -1102,6 +1105,8 @@ soma_status soma_batch_system(soma_batch_t* b, uint32_t i, soma_t** out) {
 
 soma_status soma_batch_sweep(soma_batch_t* b, uint32_t n) {
   if (!b) return fail(SOMA_EINVAL, "batch is NULL");
+  for (soma_t* h : b->sys)
+    if (h->pos_invalid) return fail(SOMA_ESTATE, "a member holds positions out of range");
   uint32_t done = 0;
   if (!b->timing && n >= GRAPH_CHUNK) {
     if (!b->graph) {

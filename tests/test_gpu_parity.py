@@ -182,23 +182,29 @@ def test_histogram_and_fields_with_edge_positions(dev):
 
 def test_positions_outside_the_supported_range_are_rejected(dev):
     """|x| < 2^18 dL is the range in which the cell fold is exact: values at
-    or beyond it, and non-finite values, are refused from host and device
-    buffers, and the stored positions stay untouched."""
+    or beyond it, and non-finite values, from host and device buffers, make
+    soma_set_positions fail and the handle refuse to sweep or update its
+    fields until valid positions are set."""
     import torch
-    from paper_1711_03828_gb300 import SomaError
+    from paper_1711_03828_gb300 import SomaError, _abi
     d = SystemDesc(n_chains=64, N=8, box_Re=(1.0, 1.0, 1.0), grid=(6, 6, 6))
     s = System(d)
-    before = s.get_positions()
     good = workloads.random_walk_positions(d, seed=1)
     for bad in (262144.0, -262144.0, np.inf, np.nan):
         p = good.copy()
         p[1, 17] = bad
         for src in (p, torch.from_numpy(p).cuda()):
-            with pytest.raises(SomaError):
+            with pytest.raises(SomaError) as e:
                 s.set_positions(src)
-            np.testing.assert_array_equal(s.get_positions(), before)
+            assert e.value.status == _abi.SOMA_EINVAL
+            for call in (lambda: s.sweep(1), s.update_fields):
+                with pytest.raises(SomaError) as e:
+                    call()
+                assert e.value.status == _abi.SOMA_ESTATE
     s.set_positions(good)
     np.testing.assert_array_equal(s.get_positions(), good)
+    s.update_fields()
+    s.sweep(2)
     s.close()
 
 
