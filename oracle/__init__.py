@@ -72,6 +72,8 @@ class OrSystem(ctypes.Structure):
         ("hamiltonian", ctypes.c_int),
         ("ext", ctypes.c_void_p),
         ("forbidden", ctypes.c_void_p),
+        ("seq", ctypes.c_void_p),
+        ("arch", ctypes.c_void_p),
     ]
 
 
@@ -282,6 +284,20 @@ class System:
         assert self._forbidden is None or self._forbidden.size == self.cells
         self.s.ext = None if self._ext is None else self._ext.ctypes.data
         self.s.forbidden = None if self._forbidden is None else self._forbidden.ctypes.data
+
+    def set_architectures(self, seq=None, arch=None):
+        """Mixture of linear architectures: seq (n_arch uint64, bit i = particle
+        i is B) and the architecture of every chain (n_chains uint8); None
+        restores the diblock of N_A A particles.  Kept alive here."""
+        if seq is None:
+            self._seq = self._arch = None
+            self.s.seq = self.s.arch = None
+            return
+        self._seq = np.ascontiguousarray(seq, np.uint64)
+        self._arch = np.ascontiguousarray(arch, np.uint8)
+        assert self._arch.size == self.n_chains and self._arch.max() < self._seq.size
+        self.s.seq = self._seq.ctypes.data
+        self.s.arch = self._arch.ctypes.data
 
     def fields(self, nA, nB, round_mode=0):
         wA = np.zeros(self.cells, np.float64)

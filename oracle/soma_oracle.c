@@ -205,6 +205,11 @@ void or_sort_chains(const or_system* s, float* x, float* y, float* z, uint64_t* 
   free(tmp);
 }
 
+int or_is_B(const or_system* s, uint64_t chain, uint32_t i) {
+  if (s->seq && s->arch) return (int)((s->seq[s->arch[chain]] >> i) & 1u);
+  return i >= s->N_A;
+}
+
 /* a3: n_i(c) = number of particles of type i in cell c (Eq.                    */
 /* density-characteristics times rho_0 dL^3; Sec. 3.1.1 occupation numbers).    */
 void or_histogram(const or_system* s, const float* x, const float* y, const float* z,
@@ -216,7 +221,7 @@ void or_histogram(const or_system* s, const float* x, const float* y, const floa
     for (uint32_t i = 0; i < s->N; ++i) {
       uint64_t m = k * s->N + i;
       uint64_t c = or_cell(s, x[m], y[m], z[m]);
-      if (i < s->N_A) nA[c] += 1u; else nB[c] += 1u;
+      if (!or_is_B(s, k, i)) nA[c] += 1u; else nB[c] += 1u;
     }
   }
 }
@@ -318,7 +323,7 @@ static void or_move_uniform_w(const or_system* s, float* x, float* y, float* z,
     dEb += s->K_b * (d_new - d_old);
   }
   /* field energy change, Eq. (delta-e) */
-  const double* w_t = (i < s->N_A) ? wA : wB;
+  const double* w_t = or_is_B(s, chain, i) ? wB : wA;
   uint64_t c_old = or_cell(s, r_old[0], r_old[1], r_old[2]);
   uint64_t c_new = or_cell(s, r_new[0], r_new[1], r_new[2]);
   double dE = dEb + (w_t[c_new] - w_t[c_old]);
@@ -406,7 +411,7 @@ static void or_move_smc(const or_system* s, float* x, float* y, float* z,
                         float* trial, uint64_t* acc, uint64_t* ties) {
   const uint32_t N = s->N;
   const uint64_t m = chain * N + i;
-  const double* w_t = (i < s->N_A) ? wA : wB;
+  const double* w_t = or_is_B(s, chain, i) ? wB : wA;
   uint32_t w1[4], w2[4];
   or_draw(s, OR_PURPOSE_MOVE, m, sweep, w1);
   or_draw(s, OR_PURPOSE_MOVE2, m, sweep, w2);
@@ -566,7 +571,7 @@ void or_learned_features(const or_system* s, const float* x, const float* y, con
     feat[3] = x[n] - r[0]; feat[4] = y[n] - r[1]; feat[5] = z[n] - r[2];
   }
   or_field_gradient(s, w_t, r, feat + 6, NULL);
-  feat[9] = (i < s->N_A) ? 1.0 : 0.0;
+  feat[9] = or_is_B(s, chain, i) ? 0.0 : 1.0;
   feat[10] = (i > 0) ? 1.0 : 0.0;
   feat[11] = (i + 1 < s->N) ? 1.0 : 0.0;
 }
@@ -605,7 +610,7 @@ static void or_move_learned(const or_system* s, float* x, float* y, float* z,
                             uint64_t chain, uint32_t i, double* margin, uint8_t* accepted,
                             float* trial, uint64_t* acc, uint64_t* ties) {
   const uint64_t m = chain * s->N + i;
-  const double* w_t = (i < s->N_A) ? wA : wB;
+  const double* w_t = or_is_B(s, chain, i) ? wB : wA;
   uint32_t w1[4], w2[4];
   or_draw(s, OR_PURPOSE_MOVE, m, sweep, w1);
   or_draw(s, OR_PURPOSE_MOVE2, m, sweep, w2);
@@ -655,7 +660,7 @@ double or_esjd_sample(const or_system* s, const double* W, const float* x, const
                       const float* z, const double* wA, const double* wB, uint64_t chain,
                       uint32_t i, const double xi[3], double* grad, double* log_alpha_out) {
   const uint64_t m = chain * s->N + i;
-  const double* w_t = (i < s->N_A) ? wA : wB;
+  const double* w_t = or_is_B(s, chain, i) ? wB : wA;
   const double r[3] = { x[m], y[m], z[m] };
   double f[12], fr[12];
   or_mlp_cache cf, cr;

@@ -57,7 +57,14 @@ typedef struct {
   const double* ext;   /* optional external field per type and cell (cells of A,
                           then cells of B), kT per particle, added to omega */
   const uint8_t* forbidden;  /* optional: nonzero cells no particle may enter */
+  const uint64_t* seq; /* optional mixture of linear architectures (N <= 64): bit i of
+                          seq[a] set means particle i of architecture a is type B */
+  const uint8_t* arch; /* architecture of every chain (with seq; n_chains entries) */
 } or_system;
+
+/* Type of particle i of a chain: 1 for B, 0 for A (the diblock boundary N_A,
+ * or the chain's architecture in a mixture). */
+int or_is_B(const or_system* s, uint64_t chain, uint32_t i);
 
 typedef struct {
   uint64_t attempted, accepted;

@@ -93,6 +93,9 @@ MUTANTS = [
      functools.partial(PIN.check_fields_are_the_energy_derivative, external=True)),
     ("forbidden_cells_ignored", "if (s->forbidden && s->forbidden[c]) { a = INFINITY; b = INFINITY; }",
      "", PIN.check_walls_and_external_field_balance),
+    ("architecture_bits_reversed", "if (s->seq && s->arch) return (int)((s->seq[s->arch[chain]] >> i) & 1u);",
+     "if (s->seq && s->arch) return (int)((s->seq[s->arch[chain]] >> (s->N - 1 - i)) & 1u);",
+     PIN.check_architecture_mixture),
     ("sort_key_axis", "for (int d = 0; d < 3; ++d) key |= ((b[d] >> bit) & 1u) << (3 * bit + d);",
      "for (int d = 0; d < 3; ++d) key |= ((b[2 - d] >> bit) & 1u) << (3 * bit + d);",
      PIN.check_sort_chains_is_a_spatial_permutation),

@@ -315,6 +315,49 @@ def test_walls_and_external_field_balance(oracle_lib):
     check_walls_and_external_field_balance()
 
 
+def check_architecture_mixture(lib=None):
+    """A mixture of linear architectures: the counts follow the per-chain type
+    sequences (numpy binning), and a blend of dimers AA, BB, AB and BA in
+    fixed random fields samples, for each architecture, the exact cell-pair
+    distribution with the fields of its own two types."""
+    L, Re = 2, 1.5
+    d = SystemDesc(n_chains=4096, N=2, f=0.5, box_Re=(L / Re,) * 3, grid=(L,) * 3,
+                   chiN=0.0, kappaN=0.0, seed=31)
+    s = oracle_system(d, lib)
+    seq = np.array([0b00, 0b11, 0b10, 0b01], np.uint64)    # AA, BB, AB, BA
+    arch = (np.arange(d.n_chains) % 4).astype(np.uint8)
+    s.set_architectures(seq, arch)
+    p = s.init_chains()
+    # counts: particle i of chain k is B iff bit i of seq[arch[k]]
+    nA, nB = s.histogram(p)
+    P3 = p.stacked().astype(np.float64)
+    c = _cells_of(P3, L)
+    isB = ((seq[arch][:, None] >> np.arange(d.N, dtype=np.uint64)[None, :]) & 1).reshape(-1)
+    np.testing.assert_array_equal(nA, np.bincount(c[isB == 0], minlength=L**3))
+    np.testing.assert_array_equal(nB, np.bincount(c[isB == 1], minlength=L**3))
+    wA, wB = workloads.random_fields(L**3, seed=5, scale=1.0)
+    K = s.params.K_b
+    for sweep in range(100):
+        s.sweep(p, wA, wB, sweep)
+    T = 1500
+    counts = np.zeros((d.n_chains, L**6))
+    for sweep in range(100, 100 + T):
+        s.sweep(p, wA, wB, sweep)
+        P = p.stacked().reshape(3, d.n_chains, 2)
+        counts[np.arange(d.n_chains), _cells_of(P[:, :, 0], L) * L**3 + _cells_of(P[:, :, 1], L)] += 1
+    fields = {0: wA, 1: wB}
+    for a in range(4):
+        t0, t1 = int(seq[a]) & 1, (int(seq[a]) >> 1) & 1
+        Pex = _pair_cell_probabilities(K, L, fields[t0], fields[t1]).reshape(-1)
+        freq = counts[arch == a] / T
+        z = (freq.mean(0) - Pex) / np.maximum(freq.std(0) / math.sqrt(len(freq)), 1e-12)
+        assert np.max(np.abs(z)) < 5.0, (a, np.max(np.abs(z)))
+
+
+def test_architecture_mixture(oracle_lib):
+    check_architecture_mixture()
+
+
 # --------------------------------------------------------------------------
 # Sweep mechanics: displacements bounded by a, accepted moves land on the draw
 # --------------------------------------------------------------------------
