@@ -18,8 +18,8 @@ SRC = os.path.join(os.path.dirname(oracle.__file__), "soma_oracle.c")
 MUTANTS = [
     ("field_sign", "(w_t[c_new] - w_t[c_old])", "(w_t[c_old] - w_t[c_new])",
      lambda L: PIN.check_two_particle_balance_brute_force(0, L)),
-    ("field_type_swapped", "const double* w_t = (i < s->N_A) ? wA : wB;\n  uint64_t c_old",
-     "const double* w_t = (i < s->N_A) ? wB : wA;\n  uint64_t c_old",
+    ("field_type_swapped", "const double* w_t = or_is_B(s, chain, i) ? wB : wA;\n  uint64_t c_old",
+     "const double* w_t = or_is_B(s, chain, i) ? wA : wB;\n  uint64_t c_old",
      lambda L: PIN.check_two_particle_balance_brute_force(0, L)),
     ("bond_half_strength", "dEb += s->K_b * (d_new - d_old);", "dEb += 0.5 * s->K_b * (d_new - d_old);",
      PIN.check_ideal_chain_relaxes_to_gaussian_statistics),
