@@ -38,7 +38,7 @@ MUTANTS = [
      PIN.check_fields_closed_forms),
     ("energy_pair_counted_twice", "0.25 * s->chiN * df * df", "0.5 * s->chiN * df * df",
      PIN.check_fields_are_the_energy_derivative),
-    ("type_boundary", "if (i < s->N_A) nA[c] += 1u;", "if (i <= s->N_A) nA[c] += 1u;",
+    ("type_boundary", "  return i >= s->N_A;\n}", "  return i > s->N_A;\n}",
      PIN.check_histogram_matches_numpy_binning_with_edge_cases),
     ("truncate_not_floor", "long long f = (long long)floor(p[d]);", "long long f = (long long)(p[d]);",
      PIN.check_histogram_matches_numpy_binning_with_edge_cases),
