@@ -209,6 +209,19 @@ soma_status soma_set_positions(soma_t* h, const float* src, size_t n, int src_on
 soma_status soma_set_external(soma_t* h, const float* ext, const uint8_t* forbidden,
                               int src_on_device);
 
+/* Mixture of linear architectures (Sec. 2.1: any mixture of molecular
+ * architectures; here linear chains of N particles with any A/B sequence,
+ * e.g. homopolymer blends or triblocks): seq holds n_arch (1..256) type
+ * sequences, bit i of seq[a] set meaning particle i of architecture a is B,
+ * and arch (n_chains bytes) the architecture of every chain.  Replaces the
+ * diblock derived from desc.f for the sweep and the occupation count; call
+ * soma_update_fields to recount at once.  N <= 64, uniform moves, even N
+ * for the SET scheme (any N <= 64 with SOMA_ITERATION_MOLECULE).  seq = NULL
+ * returns to the diblock.  Every arch entry is checked against n_arch
+ * (SOMA_EINVAL).  The handle keeps its own copies.  Synchronises. */
+soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_arch,
+                                   const uint8_t* arch, int src_on_device);
+
 /* FP64 observables of the current state (Eq. h-bond, Eq. discrete-ham).
  * Synchronises. */
 soma_status soma_observables(soma_t* h, soma_obs* out);

@@ -170,6 +170,18 @@ class System:
             assert on_e == on_f, "ext and forbidden must both be host or both device arrays"
         _abi.soma_set_external(self.h, e, f, on_e or on_f)
 
+    def set_architectures(self, seq=None, arch=None):
+        """Mixture of linear architectures: seq (n_arch uint64, bit i set =
+        particle i is B) and the architecture of every chain (n_chains uint8);
+        seq None returns to the diblock of the description."""
+        if seq is None:
+            _abi.soma_set_architectures(self.h, None, 0, None, 0)
+            return
+        q = np.ascontiguousarray(seq, dtype=np.uint64).reshape(-1)
+        a = np.ascontiguousarray(arch, dtype=np.uint8).reshape(-1)
+        assert a.size == self.desc.n_chains
+        _abi.soma_set_architectures(self.h, q.ctypes.data, q.size, a.ctypes.data, 0)
+
     def get_density(self, out=None):
         """Packed occupation numbers (cells,) uint32: n_A | n_B << 16."""
         cells = self.desc.cells

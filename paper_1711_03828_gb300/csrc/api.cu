@@ -84,6 +84,8 @@ struct soma_t {
   float* d_ext = nullptr;                    // external potential, 2 * cells (lazy)
   uint8_t* d_forbidden = nullptr;            // forbidden cells, cells bytes (lazy)
   bool has_ext = false, has_forbidden = false;
+  uint64_t* d_seq = nullptr;                 // mixture: type sequence per architecture
+  uint8_t* d_arch = nullptr;                 // mixture: architecture per chain
   double* d_out = nullptr;
   size_t scratch_doubles = 0;
   double* d_tw = nullptr;
@@ -212,6 +214,8 @@ void release(soma_t* h) {
   cudaFree(h->d_scratch);
   cudaFree(h->d_ext);
   cudaFree(h->d_forbidden);
+  cudaFree(h->d_seq);
+  cudaFree(h->d_arch);
   cudaFree(h->d_tw);
   cudaFree(h->mlp_w);
   cudaFree(h->mlp_q);
@@ -266,6 +270,8 @@ SweepArgs sweep_args(soma_t* h) {
   s.smc_inv4A = (float)(1.0 / (4.0 * A));
   s.learned_sigma0 = (float)(h->a64 / std::sqrt(3.0));
   s.err = h->d_err;
+  s.seq = h->d_seq;
+  s.arch = h->d_seq ? h->d_arch : nullptr;
   return s;
 }
 
@@ -353,7 +359,8 @@ soma_status update_fields(soma_t* h) {
   // count into n[s&1] (cleared first), then omega from it
   uint32_t* nn = h->n[h->host_sweep & 1];
   SOMA_CUDA(cudaMemsetAsync(nn, 0, sizeof(uint32_t) * h->g.cells, h->stream));
-  SOMA_CUDA(launch_histogram(h->g, h->x(), h->y(), h->z(), nn, h->sm_count, h->stream));
+  SOMA_CUDA(launch_histogram(h->g, h->x(), h->y(), h->z(), nn, h->sm_count, h->stream,
+                             h->d_seq, h->d_seq ? h->d_arch : nullptr));
   ++h->launches;
   const FieldArgs fa = field_args(h, 0);
   SOMA_CUDA(launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count, h->stream));
@@ -610,6 +617,47 @@ soma_status soma_set_external(soma_t* h, const float* ext, const uint8_t* forbid
   h->has_ext = ext != nullptr;
   h->has_forbidden = forbidden != nullptr;
   // the captured cycle holds the old field-kernel arguments
+  if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+  return sync(h);
+}
+
+soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_arch,
+                                   const uint8_t* arch, int src_on_device) {
+  if (!h) return fail(SOMA_EINVAL, "handle is NULL");
+  if (h->batched) return fail(SOMA_ESTATE, "a batch member runs the diblock of its description");
+  if (!seq) {   // back to the diblock of the description
+    cudaFree(h->d_seq);
+    cudaFree(h->d_arch);
+    h->d_seq = nullptr;
+    h->d_arch = nullptr;
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    return SOMA_OK;
+  }
+  if (!arch || n_arch < 1 || n_arch > 256) return fail(SOMA_EINVAL, "need 1..256 architectures and arch");
+  if (h->g.N > 64) return fail(SOMA_EINVAL, "mixtures take N <= 64");
+  if (h->desc.move != SOMA_MOVE_UNIFORM) return fail(SOMA_EINVAL, "mixtures take uniform moves");
+  if (h->desc.set_order != SOMA_ITERATION_MOLECULE && (h->g.N % 2 != 0 || h->shape.big))
+    return fail(SOMA_EINVAL, "mixtures take even N (SET) or the molecule-parallel iteration");
+  // every architecture index is checked on the host (it addresses seq)
+  std::vector<uint8_t> a((size_t)h->g.n_chains);
+  if (src_on_device)
+    SOMA_CUDA(cudaMemcpy(a.data(), arch, a.size(), cudaMemcpyDeviceToHost));
+  else
+    std::memcpy(a.data(), arch, a.size());
+  for (size_t k = 0; k < a.size(); ++k)
+    if (a[k] >= n_arch) return fail(SOMA_EINVAL, "arch[%zu] = %u >= n_arch = %u", k, a[k], n_arch);
+  cudaError_t e;
+  if (!h->d_seq) {
+    e = cudaMalloc((void**)&h->d_seq, sizeof(uint64_t) * 256);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc seq");
+  }
+  if (!h->d_arch) {
+    e = cudaMalloc((void**)&h->d_arch, a.size());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc arch");
+  }
+  SOMA_CUDA(cudaMemcpyAsync(h->d_seq, seq, sizeof(uint64_t) * n_arch,
+                            src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  SOMA_CUDA(cudaMemcpyAsync(h->d_arch, a.data(), a.size(), cudaMemcpyHostToDevice, h->stream));
   if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
   return sync(h);
 }

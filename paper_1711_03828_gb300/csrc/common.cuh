@@ -177,6 +177,8 @@ struct SweepArgs {
   float smc_A, smc_s2A, smc_inv4A;
   float learned_sigma0;     // a/sqrt(3): scale of the learned proposal
   unsigned* err;            // sticky error bits (a bounded wait that gave up)
+  const uint64_t* seq;      // mixture of linear architectures: bit i of seq[a] set =
+  const uint8_t* arch;      // particle i of architecture a is B; arch[chain] (or NULL)
 };
 
 // Training of the learned proposal: one expected-squared-jump sample per thread.

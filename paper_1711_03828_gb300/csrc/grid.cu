@@ -13,22 +13,26 @@ namespace soma {
 // epilogue counts on its own).  One thread per particle.
 __global__ void histogram_kernel(const Geom g, const float* __restrict__ x,
                                  const float* __restrict__ y, const float* __restrict__ z,
-                                 uint32_t* __restrict__ n) {
+                                 uint32_t* __restrict__ n, const uint64_t* __restrict__ seq,
+                                 const uint8_t* __restrict__ arch) {
   const uint64_t M = g.n_chains * g.N;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += stride) {
-    const uint32_t i = (uint32_t)(m % g.N);
-    atomicAdd(n + cell_of(g, x[m], y[m], z[m]), (i < g.N_A) ? 1u : 0x10000u);
+    const uint64_t chain = m / g.N;
+    const uint32_t i = (uint32_t)(m - chain * g.N);
+    const bool isB = seq ? ((seq[arch[chain]] >> i) & 1ull) != 0 : i >= g.N_A;
+    atomicAdd(n + cell_of(g, x[m], y[m], z[m]), isB ? 0x10000u : 1u);
   }
 }
 
 cudaError_t launch_histogram(const Geom& g, const float* x, const float* y, const float* z,
-                             uint32_t* n, int sm_count, cudaStream_t st) {
+                             uint32_t* n, int sm_count, cudaStream_t st, const uint64_t* seq,
+                             const uint8_t* arch) {
   const uint64_t M = g.n_chains * g.N;
   uint64_t blocks = (M + 255) / 256;
   const uint64_t cap = (uint64_t)sm_count * 8;
   if (blocks > cap) blocks = cap;
-  histogram_kernel<<<(unsigned)blocks, 256, 0, st>>>(g, x, y, z, n);
+  histogram_kernel<<<(unsigned)blocks, 256, 0, st>>>(g, x, y, z, n, seq, arch);
   return cudaGetLastError();
 }
 

@@ -37,8 +37,10 @@ cudaError_t launch_init(const Geom& g, float* x, float* y, float* z, double sigm
 cudaError_t launch_sort_chains(const Geom& g, const float* src, uint64_t src_plane, float* dst,
                                uint64_t dst_plane, uint64_t* keys, uint64_t n_pad, int sm_count,
                                cudaStream_t st);
+// seq/arch: the per-chain type sequences of a mixture (NULL: diblocks of N_A A particles)
 cudaError_t launch_histogram(const Geom& g, const float* x, const float* y, const float* z,
-                             uint32_t* n, int sm_count, cudaStream_t st);
+                             uint32_t* n, int sm_count, cudaStream_t st,
+                             const uint64_t* seq = nullptr, const uint8_t* arch = nullptr);
 cudaError_t launch_range_check(const float* p, uint64_t n, float lim, unsigned* flag, int sm_count,
                                cudaStream_t st);
 cudaError_t launch_fields(const FieldArgs& a, unsigned* arrive, int grid_dtype, int sm_count,

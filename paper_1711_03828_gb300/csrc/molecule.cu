@@ -49,6 +49,8 @@ __global__ void __launch_bounds__(MOL_BLOCK) sweep_molecule_kernel(const SweepAr
     }
     if (t < nch) {
       const uint64_t chain = chain0 + t;
+      // type sequence of this chain (bit i set: particle i is B)
+      const uint64_t seq = p.seq ? __ldg(p.seq + __ldg(p.arch + chain)) : 0ull;
       float* X = STAGE ? sx + t * N : p.x + chain * N;
       float* Y = STAGE ? sy + t * N : p.y + chain * N;
       float* Z = STAGE ? sz + t * N : p.z + chain * N;
@@ -60,7 +62,8 @@ __global__ void __launch_bounds__(MOL_BLOCK) sweep_molecule_kernel(const SweepAr
         const float xn = __fadd_rn(xo, __fmul_rn(a, uniform_sym(r.x)));
         const float yn = __fadd_rn(yo, __fmul_rn(a, uniform_sym(r.y)));
         const float zn = __fadd_rn(zo, __fmul_rn(a, uniform_sym(r.z)));
-        const WT* w = i < N_A ? wA : wB;
+        const bool isB = p.seq ? ((seq >> i) & 1ull) != 0 : i >= N_A;
+        const WT* w = isB ? wB : wA;
         const float dEf = load_w<WT>(w, cell_of(p.g, xn, yn, zn)) - load_w<WT>(w, cell_of(p.g, xo, yo, zo));
         // U = sum over bonded partners of (r - n), k partners
         float ux = 0.f, uy = 0.f, uz = 0.f, k = 0.f;
@@ -92,7 +95,9 @@ __global__ void __launch_bounds__(MOL_BLOCK) sweep_molecule_kernel(const SweepAr
       } else {
         x = p.x[m0 + q]; y = p.y[m0 + q]; z = p.z[m0 + q];
       }
-      atomicAdd(nacc + cell_of(p.g, x, y, z), ci < N_A ? 1u : 0x10000u);
+      const bool isB = p.seq ? ((__ldg(p.seq + __ldg(p.arch + chain0 + q / N)) >> ci) & 1ull) != 0
+                             : ci >= N_A;
+      atomicAdd(nacc + cell_of(p.g, x, y, z), isB ? 0x10000u : 1u);
       ci += step;
       if (ci >= N) ci -= N;
     }

@@ -31,12 +31,15 @@ struct PairLane {
   const WT* w1;
   uint32_t v0, v1;
   uint32_t li0;
+  uint32_t ci0;         // chain position of slot 0
+  uint32_t lane_chain;  // chain of this lane within the tile
 
   __device__ __forceinline__ void init(int lane_, uint32_t N, uint32_t N_A, const void* wA,
                                        const void* wB) {
     lane = lane_;
     li0 = 2u * (uint32_t)lane;
-    const uint32_t ci0 = li0 % N;                 // chain position of slot 0 (even)
+    ci0 = li0 % N;                                // chain position of slot 0 (even)
+    lane_chain = li0 / N;
     first_lane = (int)((li0 - ci0) >> 1);         // lane holding the chain's particle 0
     has_prev0 = ci0 > 0u;                         // slot 0 has a partner in lane-1
     has_next1 = ci0 + 2u < N;                     // slot 1 has a partner in lane+1
@@ -44,10 +47,15 @@ struct PairLane {
     cf_next1 = has_next1 ? 1.f : 0.f;
     src_prev = (lane - 1) & 31;
     src_next = (lane + 1) & 31;
-    w0 = static_cast<const WT*>(ci0 < N_A ? wA : wB);
-    w1 = static_cast<const WT*>(ci0 + 1u < N_A ? wA : wB);
-    v0 = ci0 < N_A ? 1u : 0x10000u;
-    v1 = ci0 + 1u < N_A ? 1u : 0x10000u;
+    set_types(ci0 >= N_A, ci0 + 1u >= N_A, wA, wB);
+  }
+
+  // Types of the two slots (true: B): field planes and count increments.
+  __device__ __forceinline__ void set_types(bool b0, bool b1, const void* wA, const void* wB) {
+    w0 = static_cast<const WT*>(b0 ? wB : wA);
+    w1 = static_cast<const WT*>(b1 ? wB : wA);
+    v0 = b0 ? 0x10000u : 1u;
+    v1 = b1 ? 0x10000u : 1u;
   }
 };
 

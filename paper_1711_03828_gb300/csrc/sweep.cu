@@ -216,7 +216,9 @@ __global__ void __launch_bounds__(256) sweep_uniform_kernel(const SweepArgs p) {
 // its warps in step, so field values repeat in L1; the next tile's positions
 // are loaded while the current one is processed.  IDX is the index type:
 // 32-bit when M < 2^32 (Philox counter word 1 = 0).
-template <typename WT, typename IDX>
+// MIXED: a mixture of linear architectures (the type sequence of each chain
+// is read per tile); otherwise every chain is the diblock of N_A A particles.
+template <typename WT, typename IDX, bool MIXED>
 __global__ void __launch_bounds__(256, 3) sweep_pair_kernel(const SweepArgs p) {
   const int lane = threadIdx.x & 31;
   const uint32_t n_tiles_all = (uint32_t)p.n_tiles;
@@ -254,11 +256,17 @@ __global__ void __launch_bounds__(256, 3) sweep_pair_kernel(const SweepArgs p) {
       py = __ldcs(reinterpret_cast<const float2*>(p.y + bn));
       pz = __ldcs(reinterpret_cast<const float2*>(p.z + bn));
     }
+    PairLane<WT> Lt = L;
+    if (MIXED) {
+      const uint64_t chain = (uint64_t)tile * p.G + L.lane_chain;
+      const uint64_t seq = chain < p.g.n_chains ? __ldg(p.seq + __ldg(p.arch + chain)) : 0ull;
+      Lt.set_types((seq >> L.ci0) & 1ull, (seq >> (L.ci0 + 1u)) & 1ull, p.wA, p.wB);
+    }
     if (tile < full_tiles)
-      my_acc += pair_tile<WT, IDX, false>(p.g, p.g, L, p.x, p.y, p.z, nacc, base, true, sweep, ctr3,
+      my_acc += pair_tile<WT, IDX, false>(p.g, p.g, Lt, p.x, p.y, p.z, nacc, base, true, sweep, ctr3,
                                           p.set_order_random, p.a, p.K_b, x0, x1, y0, y1, z0, z1);
     else
-      my_acc += pair_tile<WT, IDX, true>(p.g, p.g, L, p.x, p.y, p.z, nacc, base, valid, sweep, ctr3,
+      my_acc += pair_tile<WT, IDX, true>(p.g, p.g, Lt, p.x, p.y, p.z, nacc, base, valid, sweep, ctr3,
                                          p.set_order_random, p.a, p.K_b, x0, x1, y0, y1, z0, z1);
   }
 #pragma unroll
@@ -276,21 +284,28 @@ static const void* pick_kernel(int grid_dtype) {
 }
 
 static const void* sweep_kernel_ptr(int Q, bool vec, int grid_dtype, bool pair, bool big,
-                                    int move) {
+                                    int move, bool mixed) {
   if (move == 1) return smc_kernel_ptr(Q, pair && !big, grid_dtype);
   if (move == 2) return learned_kernel_ptr(Q, grid_dtype);
   if (pair) {
     if (big) {
       switch (grid_dtype) {
-        case 1: return (const void*)sweep_pair_kernel<__nv_bfloat16, uint64_t>;
-        case 2: return (const void*)sweep_pair_kernel<__half, uint64_t>;
-        default: return (const void*)sweep_pair_kernel<float, uint64_t>;
+        case 1: return (const void*)sweep_pair_kernel<__nv_bfloat16, uint64_t, false>;
+        case 2: return (const void*)sweep_pair_kernel<__half, uint64_t, false>;
+        default: return (const void*)sweep_pair_kernel<float, uint64_t, false>;
+      }
+    }
+    if (mixed) {
+      switch (grid_dtype) {
+        case 1: return (const void*)sweep_pair_kernel<__nv_bfloat16, uint32_t, true>;
+        case 2: return (const void*)sweep_pair_kernel<__half, uint32_t, true>;
+        default: return (const void*)sweep_pair_kernel<float, uint32_t, true>;
       }
     }
     switch (grid_dtype) {
-      case 1: return (const void*)sweep_pair_kernel<__nv_bfloat16, uint32_t>;
-      case 2: return (const void*)sweep_pair_kernel<__half, uint32_t>;
-      default: return (const void*)sweep_pair_kernel<float, uint32_t>;
+      case 1: return (const void*)sweep_pair_kernel<__nv_bfloat16, uint32_t, false>;
+      case 2: return (const void*)sweep_pair_kernel<__half, uint32_t, false>;
+      default: return (const void*)sweep_pair_kernel<float, uint32_t, false>;
     }
   }
   if (Q == 1) return vec ? pick_kernel<1, true>(grid_dtype) : pick_kernel<1, false>(grid_dtype);
@@ -315,7 +330,7 @@ SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dty
   s.pair = (s.Q == 1) && (N % 2 == 0);
   s.big = n_chains * N >= (1ull << 32) || s.n_tiles >= (1ull << 31);
   s.block = 256;
-  const void* fn = sweep_kernel_ptr(s.Q, s.vec, grid_dtype, s.pair, s.big, s.move);
+  const void* fn = sweep_kernel_ptr(s.Q, s.vec, grid_dtype, s.pair, s.big, s.move, false);
   if (move == 2 && s.pair && !s.big && !learned_fp32) {
     s.learned_tc = true;
     s.learned_umma = learned_umma;
@@ -343,7 +358,8 @@ cudaError_t launch_sweep_uniform(const SweepArgs& a, const SweepShape& s, int gr
                                  cudaStream_t st) {
   size_t smem = 0;
   const void* fn = s.molecule ? molecule_kernel_ptr(a.g.N, grid_dtype, &smem, false)
-                              : sweep_kernel_ptr(s.Q, s.vec, grid_dtype, s.pair, s.big, s.move);
+                              : sweep_kernel_ptr(s.Q, s.vec, grid_dtype, s.pair, s.big, s.move,
+                                                 a.seq != nullptr);
   void* args[] = {const_cast<SweepArgs*>(&a)};
   return cudaLaunchKernel(fn, dim3(s.grid), dim3(s.block), args, smem, st);
 }
