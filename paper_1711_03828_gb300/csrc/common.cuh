@@ -68,6 +68,16 @@ __device__ __forceinline__ void sincos_2pi_uniform(uint32_t r, float* s, float* 
   *c = -cv;
 }
 
+// The same with the hardware approximations (__sincosf of the phase reduced
+// to [-pi, pi)): absolute error about 2^-21, for proposals whose acceptance
+// uses the realised trial position rather than the draw.
+__device__ __forceinline__ void sincos_2pi_uniform_fast(uint32_t r, float* s, float* c) {
+  const float u = fmaf(__uint2float_rn(r >> 8), 5.9604644775390625e-8f, 2.98023223876953125e-8f);
+  __sincosf(fmaf(6.2831853071795865f, u, -3.1415926535897932f), s, c);
+  *s = -*s;
+  *c = -*c;
+}
+
 // Open uniform in FP64 (init path): (k + 1/2)/2^24, exact.
 __device__ __forceinline__ double uniform_open_f64(uint32_t r) {
   return ((double)(r >> 8) + 0.5) * 5.9604644775390625e-8;

@@ -448,6 +448,8 @@ __device__ __forceinline__ unsigned learned_pair_tile(const SweepArgs& p, const 
     const float2 c = __ldcs(reinterpret_cast<const float2*>(p.z + base));
     x0 = a.x; x1 = a.y; y0 = b.x; y1 = b.y; z0 = c.x; z1 = c.y;
   }
+  // normals by Box-Muller with the hardware log and sincos: the acceptance
+  // uses the realised trial position, so the move stays exact
   float xi0[3], xi1[3], lnu0, lnu1;
   uint32_t w3first;
   {
@@ -456,20 +458,20 @@ __device__ __forceinline__ unsigned learned_pair_tile(const SweepArgs& p, const 
     const uint4 s1 = philox_rk(make_uint4(base + 1u, 0u, sweep, ctr3a), p.g);
     const uint4 s2 = philox_rk(make_uint4(base + 1u, 0u, sweep, ctr3b), p.g);
     float sn, cs;
-    float rad = sqrtf(-2.f * log_uniform_open_accurate(r1.x));
-    sincos_2pi_uniform(r1.y, &sn, &cs);
+    float rad = sqrtf(-2.f * log_uniform_open(r1.x));
+    sincos_2pi_uniform_fast(r1.y, &sn, &cs);
     xi0[0] = rad * cs; xi0[1] = rad * sn;
-    rad = sqrtf(-2.f * log_uniform_open_accurate(r1.z));
-    sincos_2pi_uniform(r1.w, &sn, &cs);
+    rad = sqrtf(-2.f * log_uniform_open(r1.z));
+    sincos_2pi_uniform_fast(r1.w, &sn, &cs);
     xi0[2] = rad * cs;
-    lnu0 = log_uniform_open_accurate(r2.x);
-    rad = sqrtf(-2.f * log_uniform_open_accurate(s1.x));
-    sincos_2pi_uniform(s1.y, &sn, &cs);
+    lnu0 = log_uniform_open(r2.x);
+    rad = sqrtf(-2.f * log_uniform_open(s1.x));
+    sincos_2pi_uniform_fast(s1.y, &sn, &cs);
     xi1[0] = rad * cs; xi1[1] = rad * sn;
-    rad = sqrtf(-2.f * log_uniform_open_accurate(s1.z));
-    sincos_2pi_uniform(s1.w, &sn, &cs);
+    rad = sqrtf(-2.f * log_uniform_open(s1.z));
+    sincos_2pi_uniform_fast(s1.w, &sn, &cs);
     xi1[2] = rad * cs;
-    lnu1 = log_uniform_open_accurate(s2.x);
+    lnu1 = log_uniform_open(s2.x);
     w3first = r1.w;
   }
   const bool sw = p.set_order_random && (__shfl_sync(FULL, w3first, L.first_lane) & 1u);
