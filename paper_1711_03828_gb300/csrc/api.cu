@@ -1131,7 +1131,7 @@ soma_status soma_batch_create(const soma_system_desc* descs, uint32_t n, void* s
   b->args.keys = b->sys[0]->g;
   b->args.d_sweep = b->sys[0]->d_counters;
   const int fit = batch_kernel_blocks_per_sm(b->block, b->grid_dtype);
-  b->blocks_per_sm = fit < 1 ? 1 : (fit < 2 ? fit : 2);
+  b->blocks_per_sm = fit < 1 ? 1 : (fit < 3 ? fit : 3);
   soma_status st = batch_items(b, b->item_tiles);
   if (st != SOMA_OK) { std::string m = g_last_error; batch_release(b); g_last_error = m; return st; }
   *out = b;

@@ -16,7 +16,7 @@
 namespace soma {
 
 template <typename WT>
-__global__ void __launch_bounds__(512) sweep_batch_kernel(const BatchArgs p) {
+__global__ void __launch_bounds__(256, 3) sweep_batch_kernel(const BatchArgs p) {
   const int lane = threadIdx.x & 31;
   const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const unsigned long long s64 = *p.d_sweep;
@@ -163,11 +163,13 @@ cudaError_t launch_fields_batch(const BatchArgs& a, uint32_t total_cells, unsign
 }
 
 int batch_kernel_blocks_per_sm(int block, int grid_dtype) {
-  int n = 0;
   const void* fn = grid_dtype == 1 ? (const void*)sweep_batch_kernel<__nv_bfloat16>
                  : grid_dtype == 2 ? (const void*)sweep_batch_kernel<__half>
                                    : (const void*)sweep_batch_kernel<float>;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, 0);
+  cudaFuncAttributes attr;
+  if (cudaFuncGetAttributes(&attr, fn) != cudaSuccess || block > attr.maxThreadsPerBlock) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, 0) != cudaSuccess) return 0;
   return n;
 }
 
