@@ -226,6 +226,23 @@ soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_ar
  * Synchronises. */
 soma_status soma_observables(soma_t* h, soma_obs* out);
 
+/* Derived parameters of a system (Sec. 2.1), all in the units used by the
+ * library (lengths in dL, energies in kT). */
+typedef struct soma_params {
+  double Re;          /* R_e0 in dL */
+  double a;           /* maximal trial displacement per axis, dL */
+  double K_b;         /* k0/2 = 3(N-1)/(2 R_e0^2), kT/dL^2 */
+  double b0;          /* bond length R_e0/sqrt(N-1), dL */
+  double rho_cell;    /* rho_0 dL^3 = M / cells, particles per cell */
+  double sqrt_Nbar;   /* invariant degree of polymerisation: rho_0 R_e0^3 / N */
+  double epsilon;     /* SCMF accuracy (b0/dL)^3 / sqrt(N Nbar) (quasi-instantaneous
+                         field approximation; small is accurate, Sec. 2.2) */
+  uint64_t M;         /* particles */
+  uint32_t cells;     /* grid cells */
+  uint32_t N_A;       /* A particles of a diblock */
+} soma_params;
+soma_status soma_get_parameters(soma_t* h, soma_params* out);
+
 /* Composition structure factor S(q) = |sum_c (n_A - n_B)(c) e^{-i q.c}|^2 / M
  * at q = 2 pi (m_x/grid_x, m_y/grid_y, m_z/grid_z) for k integer triples m
  * (host array, k x 3); FP64 on the device; out is a host array of k doubles.

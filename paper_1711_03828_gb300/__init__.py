@@ -208,6 +208,13 @@ class System:
         _abi.soma_observables(self.h, ctypes.byref(o))
         return {k: getattr(o, k) for k, _ in _abi.SomaObs._fields_ if k != "reserved"}
 
+    def parameters(self):
+        """Derived parameters (lengths in dL, energies in kT), incl. the SCMF
+        accuracy parameter epsilon and sqrt(Nbar)."""
+        p = _abi.SomaParams()
+        _abi.soma_get_parameters(self.h, ctypes.byref(p))
+        return {k: getattr(p, k) for k, _ in _abi.SomaParams._fields_}
+
     def structure_factor(self, m):
         mm = np.ascontiguousarray(np.asarray(m, dtype=np.int32).reshape(-1, 3))
         out = np.zeros(len(mm), np.float64)

@@ -56,6 +56,15 @@ class SomaObs(ctypes.Structure):
     ]
 
 
+class SomaParams(ctypes.Structure):
+    _fields_ = [
+        ("Re", ctypes.c_double), ("a", ctypes.c_double), ("K_b", ctypes.c_double),
+        ("b0", ctypes.c_double), ("rho_cell", ctypes.c_double), ("sqrt_Nbar", ctypes.c_double),
+        ("epsilon", ctypes.c_double), ("M", ctypes.c_uint64), ("cells", ctypes.c_uint32),
+        ("N_A", ctypes.c_uint32),
+    ]
+
+
 class SomaTiming(ctypes.Structure):
     _fields_ = [
         ("ms_sweep", ctypes.c_double), ("ms_fields", ctypes.c_double),
@@ -105,6 +114,7 @@ _SIGS = {
     "soma_set_positions": ([_P, _P, _c.c_size_t, _c.c_int], _c.c_int),
     "soma_set_external": ([_P, _P, _P, _c.c_int], _c.c_int),
     "soma_set_architectures": ([_P, _P, _c.c_uint32, _P, _c.c_int], _c.c_int),
+    "soma_get_parameters": ([_P, _P], _c.c_int),
     "soma_observables": ([_P, _c.POINTER(SomaObs)], _c.c_int),
     "soma_structure_factor": ([_P, _P, _c.c_size_t, _P], _c.c_int),
     "soma_get_sweep": ([_P, _c.POINTER(_c.c_uint64)], _c.c_int),
@@ -176,6 +186,7 @@ soma_get_positions = _wrap("soma_get_positions")
 soma_set_positions = _wrap("soma_set_positions")
 soma_set_external = _wrap("soma_set_external")
 soma_set_architectures = _wrap("soma_set_architectures")
+soma_get_parameters = _wrap("soma_get_parameters")
 soma_observables = _wrap("soma_observables")
 soma_structure_factor = _wrap("soma_structure_factor")
 soma_get_sweep = _wrap("soma_get_sweep")

@@ -662,6 +662,23 @@ soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_ar
   return sync(h);
 }
 
+soma_status soma_get_parameters(soma_t* h, soma_params* out) {
+  if (!h || !out) return fail(SOMA_EINVAL, "NULL argument");
+  const double N = (double)h->g.N;
+  out->Re = h->Re;
+  out->a = h->a64;
+  out->K_b = h->K_b;
+  out->b0 = h->g.N > 1 ? h->Re / std::sqrt(N - 1.0) : 0.0;
+  out->rho_cell = h->rho_cell;
+  // rho_0 R_e0^3 = (M / cells) * Re^3 in dL units
+  out->sqrt_Nbar = h->rho_cell * h->Re * h->Re * h->Re / N;
+  out->epsilon = out->b0 * out->b0 * out->b0 / std::sqrt(N * out->sqrt_Nbar * out->sqrt_Nbar);
+  out->M = h->M;
+  out->cells = h->g.cells;
+  out->N_A = h->g.N_A;
+  return SOMA_OK;
+}
+
 soma_status soma_observables(soma_t* h, soma_obs* out) {
   if (!h || !out) return fail(SOMA_EINVAL, "NULL argument");
   const uint32_t* nn = h->n[h->host_sweep & 1];

@@ -85,6 +85,7 @@ def test_struct_layouts_match_header(soma_lib, tmp_path):
     if not os.path.exists(os.path.join(inc, "soma.h")):
         inc = os.path.join(os.path.dirname(_abi.HERE), "include")
     structs = {"soma_system_desc": _abi.SomaSystemDesc, "soma_obs": _abi.SomaObs,
+               "soma_params": _abi.SomaParams,
                "soma_timing": _abi.SomaTiming}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "soma.h"', "int main(void){"]
     for cname, py in structs.items():

@@ -208,6 +208,25 @@ def test_positions_outside_the_supported_range_are_rejected(dev):
     s.close()
 
 
+def test_parameters_closed_forms(dev):
+    """Derived parameters of the small melt (Sec. 2.1): R_e0 = 6 dL,
+    b0 = R_e0/sqrt(31), rho_0 dL^3 = 32768/1728, sqrt(Nbar) = rho_0 R_e0^3/N =
+    128, the SCMF accuracy (b0/dL)^3/sqrt(N Nbar) and a = 0.5 R_e0/sqrt(31)."""
+    d = workloads.melt_small()
+    s = System(d)
+    p = s.parameters()
+    s.close()
+    b0 = 6.0 / math.sqrt(31.0)
+    assert p["Re"] == pytest.approx(6.0, rel=1e-14)
+    assert p["b0"] == pytest.approx(b0, rel=1e-14)
+    assert p["a"] == pytest.approx(0.5 * b0, rel=1e-14)
+    assert p["K_b"] == pytest.approx(3.0 * 31 / (2 * 36.0), rel=1e-14)
+    assert p["rho_cell"] == pytest.approx(32768 / 1728, rel=1e-14)
+    assert p["sqrt_Nbar"] == pytest.approx(128.0, rel=1e-12)
+    assert p["epsilon"] == pytest.approx(b0**3 / (math.sqrt(32.0) * 128.0), rel=1e-12)
+    assert (p["M"], p["cells"], p["N_A"]) == (32768, 1728, 16)
+
+
 @pytest.mark.parametrize("set_order", [SET_ORDER_RANDOM, SET_ORDER_FIXED])
 def test_sweeps_match_oracle_small_melt(dev, set_order):
     """1024 chains of N=32, 12^3 grid, chiN=20: 30 single cycles, then a block
