@@ -243,6 +243,14 @@ typedef struct soma_params {
 } soma_params;
 soma_status soma_get_parameters(soma_t* h, soma_params* out);
 
+/* Diagnostic of the bounded device waits (the tcgen05 network evaluator waits
+ * for its tensor-core products on an mbarrier with an iteration limit and
+ * reports a wait that gives up as SOMA_ETIMEOUT instead of hanging): one warp
+ * waits, at most limit polls, for an mbarrier phase that nothing completes.
+ * Returns SOMA_ETIMEOUT (the expected outcome), after which the context stays
+ * usable.  No counterpart in the paper.  Synchronises stream (NULL: legacy). */
+soma_status soma_check_bounded_wait(uint32_t limit, void* stream);
+
 /* Composition structure factor S(q) = |sum_c (n_A - n_B)(c) e^{-i q.c}|^2 / M
  * at q = 2 pi (m_x/grid_x, m_y/grid_y, m_z/grid_z) for k integer triples m
  * (host array, k x 3); FP64 on the device; out is a host array of k doubles.

@@ -41,6 +41,9 @@ soma_status fail(soma_status st, const char* fmt, ...) {
 }
 
 soma_status cuda_fail(cudaError_t e, const char* what) {
+  // a failed call also leaves its error as the runtime's "last error"; clear
+  // it so that the next launch check reports only its own failure
+  (void)cudaGetLastError();
   return fail(e == cudaErrorMemoryAllocation ? SOMA_ENOMEM : SOMA_ECUDA, "%s: %s", what,
               cudaGetErrorString(e));
 }
@@ -676,6 +679,22 @@ soma_status soma_get_parameters(soma_t* h, soma_params* out) {
   out->M = h->M;
   out->cells = h->g.cells;
   out->N_A = h->g.N_A;
+  return SOMA_OK;
+}
+
+soma_status soma_check_bounded_wait(uint32_t limit, void* stream) {
+  if (limit < 1) return fail(SOMA_EINVAL, "limit must be >= 1");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned* d = nullptr;
+  SOMA_CUDA(cudaMalloc((void**)&d, sizeof(unsigned)));
+  unsigned e = 0;
+  cudaError_t c = cudaMemsetAsync(d, 0, sizeof(unsigned), st);
+  if (c == cudaSuccess) c = launch_wait_probe(limit, d, st);
+  if (c == cudaSuccess) c = cudaMemcpyAsync(&e, d, sizeof e, cudaMemcpyDeviceToHost, st);
+  if (c == cudaSuccess) c = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (c != cudaSuccess) return cuda_fail(c, "bounded-wait probe");
+  if (e & ERR_TIMEOUT) return fail(SOMA_ETIMEOUT, "the probe's wait gave up after %u polls (expected)", limit);
   return SOMA_OK;
 }
 

@@ -84,6 +84,8 @@ cudaError_t launch_adam(float* w, float* m, float* v, const float* grad, void* w
 cudaError_t launch_quantize(const float* w, void* wq, cudaStream_t st);
 const void* learned_kernel_ptr(int Q, int grid_dtype);
 const void* learned_tc_kernel_ptr(int grid_dtype, bool umma);
+// one warp waits (at most limit polls) for an mbarrier phase nobody completes
+cudaError_t launch_wait_probe(uint32_t limit, unsigned* err, cudaStream_t st);
 // molecule-parallel sweep kernel for chains of N particles; *smem receives its
 // dynamic shared memory (prepare: allow the kernel that much, once at create)
 const void* molecule_kernel_ptr(uint32_t N, int grid_dtype, size_t* smem, bool prepare);

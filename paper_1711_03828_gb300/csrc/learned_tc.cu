@@ -203,8 +203,9 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
                :: "r"(bar) : "memory");
 }
 // Bounded wait for the given phase parity of an mbarrier.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t it = 0; it < (1u << 22); ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          uint32_t limit = (1u << 22)) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile("{\n.reg .pred P;\nmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n"
                  "selp.u32 %0, 1, 0, P;\n}\n" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
@@ -626,6 +627,25 @@ __global__ void __launch_bounds__(128) sweep_learned_umma_kernel(const SweepArgs
   if (wib == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
                  :: "r"(net.tmem), "r"(UMMA_TMEM_COLS) : "memory");
+}
+
+// Diagnostic of the bounded waits: one warp waits, with the given iteration
+// limit, for an mbarrier phase that never completes, and records the timeout.
+__global__ void wait_probe_kernel(uint32_t limit, unsigned* err) {
+  __shared__ __align__(8) unsigned long long bar;
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool done = mbar_wait(b, 0u, limit);
+  if (!done && threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
+}
+
+cudaError_t launch_wait_probe(uint32_t limit, unsigned* err, cudaStream_t st) {
+  wait_probe_kernel<<<1, 32, 0, st>>>(limit, err);
+  return cudaGetLastError();
 }
 
 const void* learned_tc_kernel_ptr(int grid_dtype, bool umma) {
