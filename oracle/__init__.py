@@ -18,6 +18,9 @@ Functions and the paper passage each follows:
 * ``System.sweep``              -- one SET Monte-Carlo step (Sec. 2.2, Sec. 3.1.2).
 * ``System.observables``        -- E_b (Eq. h-bond), E_nb (Eq. discrete-ham), R_e^2.
 * ``System.structure_factor``   -- composition S(q) on the grid (Sec. 5.6).
+* ``System.set_topology``       -- molecular architectures in the array layout of
+  Sec. 3.2.1 with independent sets (Sec. 3.1.2); ``topology_sets``,
+  ``topo_partners``, ``topo_type``, ``System.set_order`` expose the steps.
 """
 from __future__ import annotations
 
@@ -38,6 +41,8 @@ u8p = ctypes.POINTER(ctypes.c_uint8)
 i32p = ctypes.POINTER(ctypes.c_int32)
 
 PURPOSE_INIT, PURPOSE_MOVE, PURPOSE_MOVE2, PURPOSE_CONFIG, PURPOSE_TRAIN = 0, 1, 2, 4, 5
+PURPOSE_SETS = 6
+TOPO_NO_BONDS = 0xFFFFFF
 MLP_PARAMS = 1604
 
 
@@ -74,6 +79,11 @@ class OrSystem(ctypes.Structure):
         ("forbidden", ctypes.c_void_p),
         ("seq", ctypes.c_void_p),
         ("arch", ctypes.c_void_p),
+        ("topo", ctypes.c_void_p),
+        ("topo_start", ctypes.c_void_p),
+        ("n_topo", ctypes.c_uint32),
+        ("topo_set", ctypes.c_void_p),
+        ("topo_nsets", ctypes.c_void_p),
     ]
 
 
@@ -136,6 +146,13 @@ def load(path):
     L.or_chain_key.argtypes = [P, ctypes.c_float, ctypes.c_float, ctypes.c_float]
     L.or_chain_key.restype = ctypes.c_uint64
     L.or_sort_chains.argtypes = [P, f32p, f32p, f32p, ctypes.POINTER(ctypes.c_uint64)]
+    L.or_topo_type.argtypes = [u32p, ctypes.c_uint32, ctypes.c_uint32]
+    L.or_topo_type.restype = ctypes.c_uint32
+    L.or_topo_partners.argtypes = [u32p, ctypes.c_uint32, ctypes.c_uint32, u32p, ctypes.c_uint32]
+    L.or_topo_partners.restype = ctypes.c_uint32
+    L.or_topology_sets.argtypes = [u32p, ctypes.c_uint32, u8p]
+    L.or_topology_sets.restype = ctypes.c_uint32
+    L.or_set_order.argtypes = [P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, u32p]
     return L
 
 
@@ -158,6 +175,29 @@ def uniform_sym(r, L=None):
 
 def uniform_open(r, L=None):
     return (L or lib()).or_uniform_open(int(r))
+
+
+def topo_type(words, start, i, L=None):
+    """Type (0 A, 1 B) of particle i of the architecture block at start."""
+    w = np.ascontiguousarray(words, np.uint32)
+    return int((L or lib()).or_topo_type(_ptr(w, u32p), int(start), int(i)))
+
+
+def topo_partners(words, start, i, L=None):
+    """Bond partners of particle i of the block at start, in list order."""
+    w = np.ascontiguousarray(words, np.uint32)
+    out = np.zeros(256, np.uint32)
+    k = (L or lib()).or_topo_partners(_ptr(w, u32p), int(start), int(i), _ptr(out, u32p), 256)
+    return [int(v) for v in out[:k]]
+
+
+def topology_sets(words, start, L=None):
+    """(set of every particle, number of sets) of the block at start."""
+    w = np.ascontiguousarray(words, np.uint32)
+    N = int(w[start])
+    out = np.zeros(max(N, 1), np.uint8)
+    n = (L or lib()).or_topology_sets(_ptr(w, u32p), int(start), _ptr(out, u8p))
+    return out[:N], int(n)
 
 
 def num_threads():
@@ -293,11 +333,53 @@ class System:
             self._seq = self._arch = None
             self.s.seq = self.s.arch = None
             return
+        self.s.topo = None
         self._seq = np.ascontiguousarray(seq, np.uint64)
         self._arch = np.ascontiguousarray(arch, np.uint8)
         assert self._arch.size == self.n_chains and self._arch.max() < self._seq.size
         self.s.seq = self._seq.ctypes.data
         self.s.arch = self._arch.ctypes.data
+
+    def set_topology(self, words=None, starts=None, arch=None):
+        """Molecular architectures in the array layout of Sec. 3.2.1: words
+        (uint32), the first word of each architecture's block (starts), and the
+        architecture of every molecule (n_chains uint8).  The independent sets
+        are generated here by the oracle's own heuristic.  None restores the
+        diblock.  Kept alive here."""
+        if words is None:
+            self._topo = self._topo_start = self._arch = self._topo_set = self._topo_nsets = None
+            self.s.topo = self.s.topo_start = self.s.arch = None
+            self.s.topo_set = self.s.topo_nsets = None
+            self.s.n_topo = 0
+            return
+        self._topo = np.ascontiguousarray(words, np.uint32)
+        self._topo_start = np.ascontiguousarray(starts, np.uint32)
+        self._arch = np.ascontiguousarray(arch, np.uint8)
+        na = self._topo_start.size
+        assert self._arch.size == self.n_chains and int(self._arch.max()) < na
+        self._topo_set = np.zeros(na * self.N, np.uint8)
+        self._topo_nsets = np.zeros(na, np.uint8)
+        for a in range(na):
+            assert int(self._topo[self._topo_start[a]]) == self.N
+            sets, n = topology_sets(self._topo, self._topo_start[a], self.L)
+            assert 1 <= n <= 8
+            self._topo_set[a * self.N:(a + 1) * self.N] = sets
+            self._topo_nsets[a] = n
+        self.s.seq = None
+        self._seq = None
+        self.s.topo = self._topo.ctypes.data
+        self.s.topo_start = self._topo_start.ctypes.data
+        self.s.n_topo = na
+        self.s.topo_set = self._topo_set.ctypes.data
+        self.s.topo_nsets = self._topo_nsets.ctypes.data
+        self.s.arch = self._arch.ctypes.data
+
+    def set_order(self, chain, sweep, n_sets):
+        """Order in which molecule chain visits its n_sets sets in a sweep."""
+        out = np.zeros(8, np.uint32)
+        self.L.or_set_order(ctypes.byref(self.s), int(chain), int(sweep), int(n_sets),
+                            _ptr(out, u32p))
+        return [int(v) for v in out[:n_sets]]
 
     def fields(self, nA, nB, round_mode=0):
         wA = np.zeros(self.cells, np.float64)

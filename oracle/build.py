@@ -12,12 +12,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 def build(verbose: bool = False) -> str:
     src = os.path.join(_HERE, "soma_oracle.c")
     out = os.path.join(_HERE, "liboracle.so")
+    tmp = f"{out}.tmp{os.getpid()}"   # concurrent builds (parallel test workers) do not collide
     cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-           "-fPIC", "-shared", "-o", out + ".tmp", src, "-lm"]
+           "-fPIC", "-shared", "-o", tmp, src, "-lm"]
     if verbose:
         print(" ".join(cmd))
     subprocess.run(cmd, check=True)
-    os.replace(out + ".tmp", out)
+    os.replace(tmp, out)
     return out
 
 

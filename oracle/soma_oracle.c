@@ -206,8 +206,82 @@ void or_sort_chains(const or_system* s, float* x, float* y, float* z, uint64_t* 
 }
 
 int or_is_B(const or_system* s, uint64_t chain, uint32_t i) {
+  if (s->topo && s->arch) return or_topo_type(s->topo, s->topo_start[s->arch[chain]], i) == 1u;
   if (s->seq && s->arch) return (int)((s->seq[s->arch[chain]] >> i) & 1u);
   return i >= s->N_A;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Molecular architectures in the array layout of Sec. 3.2.1.                  */
+/* ------------------------------------------------------------------------- */
+uint32_t or_topo_type(const uint32_t* topo, uint32_t start, uint32_t i) {
+  return topo[start + 1u + i] & 0xFFu;
+}
+
+uint32_t or_topo_partners(const uint32_t* topo, uint32_t start, uint32_t i, uint32_t* out,
+                          uint32_t cap) {
+  const uint32_t first = topo[start + 1u + i] >> 8;
+  if (first == OR_TOPO_NO_BONDS) return 0u;
+  uint32_t k = 0;
+  for (uint32_t b = first;; ++b) {
+    const uint32_t w = topo[b];
+    /* the top 27 bits are the signed offset to the partner */
+    const int32_t off = (int32_t)w >> 5;
+    if (k < cap) out[k] = (uint32_t)((int64_t)i + off);
+    ++k;
+    if (w & 1u) break;
+  }
+  return k < cap ? k : cap;
+}
+
+uint32_t or_topology_sets(const uint32_t* topo, uint32_t start, uint8_t* set_of) {
+  const uint32_t N = topo[start];
+  uint32_t partners[256];
+  uint32_t n_sets = 0;
+  for (uint32_t i = 0; i < N; ++i) {
+    const uint32_t k = or_topo_partners(topo, start, i, partners, 256u);
+    uint32_t taken = 0;   /* bit c: a partner already placed holds set c */
+    for (uint32_t b = 0; b < k; ++b)
+      if (partners[b] < i) taken |= 1u << set_of[partners[b]];
+    uint32_t c = 0;
+    while (taken & (1u << c)) ++c;
+    set_of[i] = (uint8_t)c;
+    if (c + 1u > n_sets) n_sets = c + 1u;
+  }
+  return n_sets;
+}
+
+void or_set_order(const or_system* s, uint64_t chain, uint32_t sweep, uint32_t n_sets,
+                  uint32_t* order) {
+  for (uint32_t k = 0; k < n_sets; ++k) order[k] = k;
+  if (s->set_order != 0 || n_sets < 2) return;
+  uint32_t w[4];
+  if (n_sets == 2) {
+    or_draw(s, OR_PURPOSE_MOVE, chain * s->N, sweep, w);
+    const uint32_t first = w[3] & 1u;
+    order[0] = first;
+    order[1] = 1u - first;
+    return;
+  }
+  or_draw(s, OR_PURPOSE_SETS, chain, sweep, w);
+  order[0] = 0;
+  for (uint32_t k = 1; k < n_sets; ++k) {
+    const uint32_t h = (w[(k - 1u) / 2u] >> (16u * ((k - 1u) % 2u))) & 0xFFFFu;
+    const uint32_t j = (h * (k + 1u)) >> 16;
+    order[k] = order[j];
+    order[j] = k;
+  }
+}
+
+/* Bond partners of particle i of a chain: the linear neighbours i-1, i+1, or
+ * the bond list of the molecule's architecture. */
+static uint32_t or_partners(const or_system* s, uint64_t chain, uint32_t i, uint32_t* out) {
+  if (s->topo && s->arch)
+    return or_topo_partners(s->topo, s->topo_start[s->arch[chain]], i, out, 256u);
+  uint32_t k = 0;
+  if (i > 0) out[k++] = i - 1u;
+  if (i + 1u < s->N) out[k++] = i + 1u;
+  return k;
 }
 
 /* a3: n_i(c) = number of particles of type i in cell c (Eq.                    */
@@ -308,12 +382,13 @@ static void or_move_uniform_w(const or_system* s, float* x, float* y, float* z,
     const uint64_t M = s->n_chains * N;
     for (int d = 0; d < 3; ++d) trial[d * M + rec] = (float)r_new[d];
   }
-  /* bonded energy change: neighbours i-1 and i+1 of the linear chain */
+  /* bonded energy change over the bond partners (i-1 and i+1 of a linear
+   * chain, in that order) */
+  uint32_t partners[256];
+  const uint32_t n_partners = or_partners(s, chain, i, partners);
   double dEb = 0.0;
-  for (int side = -1; side <= 1; side += 2) {
-    long long jn = (long long)i + side;
-    if (jn < 0 || jn >= (long long)N) continue;
-    uint64_t n = chain * N + (uint64_t)jn;
+  for (uint32_t b = 0; b < n_partners; ++b) {
+    uint64_t n = chain * N + partners[b];
     double rn[3] = { x[n], y[n], z[n] };
     double d_new = 0.0, d_old = 0.0;
     for (int d = 0; d < 3; ++d) {
@@ -781,6 +856,23 @@ void or_sweep_trial(const or_system* s, float* x, float* y, float* z,
       }
       continue;
     }
+    if (s->topo && s->arch) {
+      /* sets of the molecule's architecture in this sweep's order; within a
+       * set the particles are independent, so their order does not matter */
+      const uint32_t a = s->arch[chain];
+      const uint32_t n_sets = s->topo_nsets[a];
+      uint32_t order[8];
+      or_set_order(s, chain, sweep, n_sets, order);
+      for (uint32_t k = 0; k < n_sets; ++k)
+        for (uint32_t i = 0; i < N; ++i) {
+          if (s->topo_set[(uint64_t)a * N + i] != order[k]) continue;
+          uint64_t a1 = 0, t1 = 0;
+          or_move_uniform(s, x, y, z, wA, wB, sweep, chain, i, margin, accepted, trial, &a1, &t1);
+          acc += a1;
+          ties += t1;
+        }
+      continue;
+    }
     uint32_t first = or_first_set(s, chain, sweep);
     for (uint32_t k = 0; k < 2; ++k) {
       uint32_t set = first ^ k;
@@ -826,9 +918,28 @@ void or_observables(const or_system* s, const float* x, const float* y, const fl
                     const uint32_t* nA, const uint32_t* nB, or_obs* out) {
   const uint32_t N = s->N;
   double Eb = 0.0, Re2 = 0.0, b2 = 0.0;
+  double n_bonds = 0.0;
   for (uint64_t k = 0; k < s->n_chains; ++k) {
     uint64_t m0 = k * N;
-    for (uint32_t i = 0; i + 1 < N; ++i) {
+    if (s->topo && s->arch) {
+      /* every bond once: from the particle with the smaller index */
+      uint32_t partners[256];
+      for (uint32_t i = 0; i < N; ++i) {
+        const uint32_t np = or_partners(s, k, i, partners);
+        for (uint32_t b = 0; b < np; ++b) {
+          const uint32_t j = partners[b];
+          if (j <= i) continue;
+          double dx = (double)x[m0 + j] - (double)x[m0 + i];
+          double dy = (double)y[m0 + j] - (double)y[m0 + i];
+          double dz = (double)z[m0 + j] - (double)z[m0 + i];
+          double bb = dx * dx + dy * dy + dz * dz;
+          b2 += bb;
+          Eb += s->K_b * bb;
+          n_bonds += 1.0;
+        }
+      }
+    }
+    for (uint32_t i = 0; i + 1 < N && !(s->topo && s->arch); ++i) {
       double dx = (double)x[m0 + i + 1] - (double)x[m0 + i];
       double dy = (double)y[m0 + i + 1] - (double)y[m0 + i];
       double dz = (double)z[m0 + i + 1] - (double)z[m0 + i];
@@ -858,7 +969,8 @@ void or_observables(const or_system* s, const float* x, const float* y, const fl
   out->E_nb = s->rho_cell / (double)N * K;
   out->E_ext = Eext;
   out->Re2 = Re2 / (double)s->n_chains;
-  out->b2 = (N > 1) ? b2 / ((double)s->n_chains * (double)(N - 1)) : 0.0;
+  if (!(s->topo && s->arch)) n_bonds = (double)s->n_chains * (double)(N > 1 ? N - 1 : 0);
+  out->b2 = n_bonds > 0.0 ? b2 / n_bonds : 0.0;
 }
 
 /* Composition structure factor on the collocation grid (the radial S(q) of

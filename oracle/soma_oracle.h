@@ -32,7 +32,8 @@ extern "C" {
 
 /* Philox stream purposes (the fourth counter word holds purpose<<24 | replica). */
 enum { OR_PURPOSE_INIT = 0, OR_PURPOSE_MOVE = 1, OR_PURPOSE_MOVE2 = 2,
-       OR_PURPOSE_ATTEMPT = 3, OR_PURPOSE_CONFIG = 4, OR_PURPOSE_TRAIN = 5 };
+       OR_PURPOSE_ATTEMPT = 3, OR_PURPOSE_CONFIG = 4, OR_PURPOSE_TRAIN = 5,
+       OR_PURPOSE_SETS = 6 };
 
 typedef struct {
   uint64_t n_chains;
@@ -59,8 +60,46 @@ typedef struct {
   const uint8_t* forbidden;  /* optional: nonzero cells no particle may enter */
   const uint64_t* seq; /* optional mixture of linear architectures (N <= 64): bit i of
                           seq[a] set means particle i of architecture a is type B */
-  const uint8_t* arch; /* architecture of every chain (with seq; n_chains entries) */
+  const uint8_t* arch; /* architecture of every chain (with seq or topo; n_chains entries) */
+  /* optional molecular architectures in the array layout of Sec. 3.2.1 (below);
+     arch[] then gives the architecture of every molecule and seq must be NULL */
+  const uint32_t* topo;       /* the architecture array */
+  const uint32_t* topo_start; /* index of the first word of each architecture's block */
+  uint32_t n_topo;            /* architectures */
+  const uint8_t* topo_set;    /* independent set of particle i of architecture a: [a*N + i] */
+  const uint8_t* topo_nsets;  /* number of independent sets of each architecture */
 } or_system;
+
+/* --- Molecular architectures (Sec. 3.2.1, Fig. polyarch) ---------------------
+ * One block per architecture: word 0 = N; word 1 + i = (offset << 8) | type of
+ * particle i, where offset is the index in the whole array of the particle's
+ * first bond word (OR_TOPO_NO_BONDS: no bonds) and type 0 = A, 1 = B; bond
+ * words = (signed 27-bit partner offset j - i) << 5 | (bond type << 1) | last,
+ * the list of a particle ending at the word whose last bit is 1.  Bond type 0
+ * is the harmonic bond of the system (the only one).  Readings where the
+ * figure is silent: "first bytes / bits" are the most significant ones, and
+ * a particle without bonds carries the offset 0xFFFFFF. */
+#define OR_TOPO_NO_BONDS 0xFFFFFFu
+/* type (0 A, 1 B) of particle i of the block starting at start */
+uint32_t or_topo_type(const uint32_t* topo, uint32_t start, uint32_t i);
+/* bond partners of particle i in list order into out (cap entries at most);
+ * returns their number */
+uint32_t or_topo_partners(const uint32_t* topo, uint32_t start, uint32_t i, uint32_t* out,
+                          uint32_t cap);
+/* Independent sets of one architecture (Sec. 3.1.2, set generation by a simple
+ * heuristic): particles in index order each take the smallest set index that
+ * none of their already placed bond partners holds.  Writes set_of[0..N) and
+ * returns the number of sets. */
+uint32_t or_topology_sets(const uint32_t* topo, uint32_t start, uint8_t* set_of);
+/* Order in which a molecule visits its n_sets sets in one sweep (Sec. 3.1.2:
+ * a random permutation per molecule and sweep).  Two sets: the linear-chain
+ * rule (bit 0 of the fourth word of the move draw of particle 0 puts set 1
+ * first).  More sets (up to 8): an inside-out Fisher-Yates shuffle whose k-th
+ * step (k = 1..n-1) takes j = (h_k (k+1)) >> 16, h_k the k-th 16-bit half
+ * (low half first) of the words of the draw (OR_PURPOSE_SETS, molecule,
+ * sweep).  set_order 1: sets in index order. */
+void or_set_order(const or_system* s, uint64_t chain, uint32_t sweep, uint32_t n_sets,
+                  uint32_t* order);
 
 /* Type of particle i of a chain: 1 for B, 0 for A (the diblock boundary N_A,
  * or the chain's architecture in a mixture). */

@@ -144,3 +144,125 @@ def random_mlp(seed, scale=0.3):
     w = np.concatenate(parts).astype(np.float32)
     bits = w.view(np.uint32) & np.uint32(0xFFFF0000)  # truncate to a BF16 value
     return bits.view(np.float32).astype(np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Molecular architectures: a molecule is (types, bonds) with types a list of 0
+# (A) / 1 (B) per particle and bonds a list of (i, j) pairs.  encode_architectures
+# writes them in the array layout of Sec. 3.2.1 that soma_set_topology reads.
+
+def linear_architecture(N, N_A=None):
+    """Linear chain i - (i+1); the first N_A particles are A (default N/2)."""
+    N_A = N // 2 if N_A is None else N_A
+    return [0 if i < N_A else 1 for i in range(N)], [(i, i + 1) for i in range(N - 1)]
+
+
+def star_architecture(arms, arm_len, arm_types=None):
+    """Star: particle 0 is the centre (type A), then each arm's particles from
+    the centre outwards; arm_types[k] is the type of arm k (default
+    alternating A, B)."""
+    types, bonds = [0], []
+    for k in range(arms):
+        t = (k % 2) if arm_types is None else arm_types[k]
+        prev = 0
+        for _ in range(arm_len):
+            i = len(types)
+            types.append(t)
+            bonds.append((prev, i))
+            prev = i
+    return types, bonds
+
+
+def ring_architecture(N, N_A=None):
+    """Ring i - (i+1) mod N; the first N_A particles are A (default N/2)."""
+    N_A = N // 2 if N_A is None else N_A
+    return [0 if i < N_A else 1 for i in range(N)], [(i, (i + 1) % N) for i in range(N)]
+
+
+def comb_architecture(backbone, teeth, tooth_len):
+    """Comb: an A backbone of the given length with `teeth` B side chains of
+    tooth_len particles grafted at evenly spaced backbone particles.  Each
+    tooth follows its graft point in the particle order."""
+    types, bonds = [], []
+    graft = set(int(round((k + 0.5) * backbone / teeth)) for k in range(teeth))
+    prev_bb = None
+    for b in range(backbone):
+        i = len(types)
+        types.append(0)
+        if prev_bb is not None:
+            bonds.append((prev_bb, i))
+        prev_bb = i
+        if b in graft:
+            prev = i
+            for _ in range(tooth_len):
+                j = len(types)
+                types.append(1)
+                bonds.append((prev, j))
+                prev = j
+    return types, bonds
+
+
+def encode_architectures(molecules):
+    """Architecture array (uint32) and the first word of each block, for a
+    list of (types, bonds).  Block: N; per particle (first bond word << 8) |
+    type (0xFFFFFF: no bonds); then per particle its bonds in the order given
+    (both directions of every bond), each ((j - i) << 5) | (bond type 0 << 1) |
+    last."""
+    words, starts = [], []
+    for types, bonds in molecules:
+        N = len(types)
+        partners = [[] for _ in range(N)]
+        for i, j in bonds:
+            partners[i].append(j)
+            partners[j].append(i)
+        start = len(words)
+        starts.append(start)
+        words.append(N)
+        mono = len(words)
+        words.extend([0] * N)
+        for i in range(N):
+            if not partners[i]:
+                words[mono + i] = (0xFFFFFF << 8) | types[i]
+                continue
+            words[mono + i] = (len(words) << 8) | types[i]
+            for k, j in enumerate(partners[i]):
+                last = 1 if k == len(partners[i]) - 1 else 0
+                words.append((((j - i) & 0x7FFFFFF) << 5) | last)
+    return np.asarray(words, np.uint32), np.asarray(starts, np.uint32)
+
+
+def architecture_positions(desc: SystemDesc, molecules, arch, seed: int,
+                           bond_sigma: float = None) -> np.ndarray:
+    """Seeded synthetic input for molecules of the given architectures
+    (arch[k] indexes molecules): particle 0 uniform in the box, every later
+    particle at its lowest-index bonded partner before it plus a normal
+    displacement of standard deviation bond_sigma per axis (default
+    R_e0/sqrt(3(N-1))); a particle with no earlier partner is placed uniformly
+    in the box.  Ring closures start stretched.  Returns (3, M) float32."""
+    rng = np.random.default_rng(seed)
+    Re = desc.grid[0] / desc.box_Re[0]
+    N = desc.N
+    if bond_sigma is None:
+        bond_sigma = Re / math.sqrt(3.0 * max(N - 1, 1))
+    box = np.asarray(desc.grid, dtype=np.float64)
+    parent = []
+    for types, bonds in molecules:
+        p = [-1] * N
+        for i, j in bonds:
+            a, b = min(i, j), max(i, j)
+            if p[b] < 0 or a < p[b]:
+                p[b] = a
+        parent.append(p)
+    n = desc.n_chains
+    arch = np.asarray(arch)
+    out = np.zeros((3, n, N))
+    free = rng.random((3, n, N)) * box[:, None, None]
+    steps = rng.normal(0.0, bond_sigma, size=(3, n, N))
+    for a, p in enumerate(parent):
+        sel = np.nonzero(arch == a)[0]
+        for i in range(N):
+            if p[i] < 0:
+                out[:, sel, i] = free[:, sel, i]
+            else:
+                out[:, sel, i] = out[:, sel, p[i]] + steps[:, sel, i]
+    return out.reshape(3, n * N).astype(np.float32)

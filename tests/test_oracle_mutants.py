@@ -11,6 +11,7 @@ import pytest
 import oracle
 from tests import test_oracle_philox as PH
 from tests import test_oracle_pins as PIN
+from tests import test_oracle_topology as TOPO
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "soma_oracle.c")
 
@@ -25,12 +26,7 @@ MUTANTS = [
      PIN.check_ideal_chain_relaxes_to_gaussian_statistics),
     ("metropolis_sign", "(lnu < -dE)", "(lnu < dE)",
      PIN.check_ideal_chain_relaxes_to_gaussian_statistics),
-    ("one_sided_bonds", "  double dEb = 0.0;\n  for (int side = -1; side <= 1; side += 2) {\n"
-     "    long long jn = (long long)i + side;\n    if (jn < 0 || jn >= (long long)N) continue;\n"
-     "    uint64_t n = chain * N + (uint64_t)jn;\n    double rn[3] = { x[n], y[n], z[n] };\n    double d_new",
-     "  double dEb = 0.0;\n  for (int side = -1; side < 1; side += 2) {\n"
-     "    long long jn = (long long)i + side;\n    if (jn < 0 || jn >= (long long)N) continue;\n"
-     "    uint64_t n = chain * N + (uint64_t)jn;\n    double rn[3] = { x[n], y[n], z[n] };\n    double d_new",
+    ("one_sided_bonds", "  if (i + 1u < s->N) out[k++] = i + 1u;\n", "",
      PIN.check_ideal_chain_relaxes_to_gaussian_statistics),
     ("chi_sign", "      a = comp - 0.5 * chi0 * (phiA - phiB);", "      a = comp + 0.5 * chi0 * (phiA - phiB);",
      PIN.check_fields_closed_forms),
@@ -55,7 +51,8 @@ MUTANTS = [
      lambda L: PH.check_philox_matches_curand_host_generator(1, L)),
     ("sq_wrong_axis", "(double)m[3 * q + 1] * cy / s->grid[1]", "(double)m[3 * q + 1] * cy / s->grid[0]",
      PIN.check_structure_factor_matches_numpy_fft),
-    ("bond_energy_observable", "Eb += s->K_b * bb;", "Eb += 2.0 * s->K_b * bb;",
+    ("bond_energy_observable", "      b2 += bb;\n      Eb += s->K_b * bb;",
+     "      b2 += bb;\n      Eb += 2.0 * s->K_b * bb;",
      PIN.check_observables_hand_values),
     ("smc_reverse_density_dropped", "const double log_alpha = -dE - rev / (4.0 * A) + fwd / (4.0 * A);",
      "const double log_alpha = -dE;",
@@ -99,6 +96,26 @@ MUTANTS = [
     ("sort_key_axis", "for (int d = 0; d < 3; ++d) key |= ((b[d] >> bit) & 1u) << (3 * bit + d);",
      "for (int d = 0; d < 3; ++d) key |= ((b[2 - d] >> bit) & 1u) << (3 * bit + d);",
      PIN.check_sort_chains_is_a_spatial_permutation),
+    # molecular architectures (Sec. 3.2.1) and independent sets (Sec. 3.1.2)
+    ("topo_offset_sign", "const int32_t off = (int32_t)w >> 5;", "const int32_t off = -((int32_t)w >> 5);",
+     TOPO.check_architecture_words_decode),
+    ("topo_type_byte", "return topo[start + 1u + i] & 0xFFu;", "return (topo[start + 1u + i] >> 24) & 0xFFu;",
+     TOPO.check_architecture_words_decode),
+    ("topo_first_bond_only", "if (w & 1u) break;", "if ((w & 1u) || k >= 1u) break;",
+     TOPO.check_architecture_words_decode),
+    ("topo_types_ignored",
+     "if (s->topo && s->arch) return or_topo_type(s->topo, s->topo_start[s->arch[chain]], i) == 1u;",
+     "if (s->topo && s->arch) return i >= s->N_A;", TOPO.check_linear_topology_is_the_linear_chain),
+    ("sets_see_later_partners", "if (partners[b] < i) taken |= 1u << set_of[partners[b]];",
+     "if (partners[b] != i) taken |= 1u << set_of[partners[b]];", TOPO.check_sets_hand_values),
+    ("set_shuffle_cyclic", "const uint32_t j = (h * (k + 1u)) >> 16;", "const uint32_t j = (h * k) >> 16;",
+     TOPO.check_set_order_is_a_uniform_permutation),
+    ("set_order_ignored", "if (s->topo_set[(uint64_t)a * N + i] != order[k]) continue;",
+     "if (s->topo_set[(uint64_t)a * N + i] != k) continue;", TOPO.check_linear_topology_is_the_linear_chain),
+    ("two_set_rule_reversed", "order[0] = first;\n    order[1] = 1u - first;",
+     "order[0] = 1u - first;\n    order[1] = first;", TOPO.check_linear_topology_is_the_linear_chain),
+    ("topo_bond_counted_twice", "if (j <= i) continue;", "if (j == i) continue;",
+     TOPO.check_topology_observables_hand_values),
 ]
 
 
