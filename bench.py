@@ -35,7 +35,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="melt_large",
                     choices=["melt_large", "melt_mid", "melt_small", "melt_slow", "melt_subbox",
-                             "melt_tiny",
+                             "melt_tiny", "arch_large",
                              "batch64", "decorrelation"])
     ap.add_argument("--move", default="uniform", choices=["uniform", "smc", "learned"],
                     help="trial moves: uniform displacement or smart Monte Carlo")
@@ -74,8 +74,25 @@ def workload(name, replica=0, grid_dtype="f32", move="uniform", learned_net="mma
     return d
 
 
+def setup_architectures(target, d, seed=1):
+    """Molecules of the four architectures of workloads.arch_large, one drawn
+    per molecule, on a library System or an oracle System (the same arrays)."""
+    import numpy as np
+    from paper_1711_03828_gb300 import workloads
+    mols = workloads.arch_large_molecules()
+    words, starts = workloads.encode_architectures(mols)
+    arch = np.random.default_rng(seed + 17).integers(0, len(mols), d.n_chains).astype(np.uint8)
+    pos = workloads.architecture_positions(d, mols, arch, seed=seed + 29)
+    target.set_topology(words, starts, arch)
+    return pos
+
+
 def config_of(d, name, l2_note):
-    return {"workload": f"{name}: {d.n_chains} chains x N={d.N}, box {d.box_Re} R_e0, grid "
+    extra = {}
+    if name == "arch_large":
+        extra["architectures"] = ("three-arm star (11,10,10), comb (16 + 4x4), ring (32), "
+                                  "linear diblock; one drawn per molecule")
+    return {**extra,"workload": f"{name}: {d.n_chains} chains x N={d.N}, box {d.box_Re} R_e0, grid "
                         f"{d.grid}, chiN={d.chiN}, kappaN={d.kappaN}",
             "n_chains": d.n_chains, "N": d.N, "particles": d.M, "grid": list(d.grid),
             "box_Re": list(d.box_Re), "chiN": d.chiN, "kappaN": d.kappaN,
@@ -98,7 +115,11 @@ def oracle_rate(name, seconds, max_steps=None):
     sub = workloads.scaled(d, (4.0, 4.0, 4.0))
     o = oracle.System(sub.n_chains, sub.N, sub.f, sub.box_Re, sub.grid, sub.chiN, sub.kappaN,
                       seed=sub.seed)
-    p = o.init_chains()
+    if name == "arch_large":
+        pos = setup_architectures(o, sub)
+        p = oracle.Positions(pos[0].copy(), pos[1].copy(), pos[2].copy())
+    else:
+        p = o.init_chains()
     nA, nB = o.histogram(p)
     wA, wB = o.fields(nA, nB)
     steps = 0
@@ -215,13 +236,16 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
-    """sha256 over the sources of the sweep kernel (sweep.cu, pair_body.cuh,
-    common.cuh), so that a stored traffic figure is used only while the
-    kernel it was taken on is unchanged."""
+SWEEP_SOURCES = ("sweep.cu", "pair_body.cuh", "common.cuh")
+
+
+def kernel_source_hash(sources=SWEEP_SOURCES):
+    """sha256 over the sources of a sweep kernel (by default the pair kernel's
+    sweep.cu, pair_body.cuh, common.cuh), so that a stored traffic figure is
+    used only while the kernel it was taken on is unchanged."""
     import hashlib
     h = hashlib.sha256()
-    for name in ("sweep.cu", "pair_body.cuh", "common.cuh"):
+    for name in sources:
         with open(os.path.join(ROOT, "paper_1711_03828_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -234,15 +258,17 @@ def measured_traffic(workload_name):
     try:
         with open(os.path.join(ROOT, "profiles", f"sweep_traffic_{workload_name}.json")) as f:
             t = json.load(f)
-        if kernel_source_hash() != t["kernel_src_sha256"]:
+        if kernel_source_hash(tuple(t.get("sources", SWEEP_SOURCES))) != t["kernel_src_sha256"]:
             return None
         return t["dram_bytes_read"] + t["dram_bytes_write"]
     except (OSError, KeyError, ValueError):
         return None
 
 
-def sweep_kernel_name(d):
+def sweep_kernel_name(d, architectures=False):
     """The sweep kernel libsoma launches for this description."""
+    if architectures:
+        return "sweep_topology_kernel"
     pair = d.N % 2 == 0 and d.N <= 64
     if d.move == 1:
         return "sweep_smc_pair_kernel" if pair else "sweep_smc_kernel"
@@ -285,6 +311,9 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     s = System(d, stream=stream)
+    if args.workload == "arch_large":
+        s.set_positions(setup_architectures(s, d))
+        s.update_fields()
     train_log = None
     if d.move == 2:  # train the proposal on this system's plain-method configurations
         train_log = s.train_proposal(steps=200, batch=16384, sweeps_between=1, lr=3e-3)
@@ -368,7 +397,7 @@ def run_ours(args):
                             f"inputs L2-resident ({12 * d.M / 1e6:.2f} MB of positions): a "
                             "latency figure, not a bandwidth one"),
         "roofline": {"bound": "hbm",
-                     "kernel": sweep_kernel_name(d),
+                     "kernel": sweep_kernel_name(d, args.workload == "arch_large"),
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": measured_traffic(args.workload)
                      if args.grid_dtype == "f32" and args.move == "uniform" else None,

@@ -222,6 +222,39 @@ soma_status soma_set_external(soma_t* h, const float* ext, const uint8_t* forbid
 soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_arch,
                                    const uint8_t* arch, int src_on_device);
 
+/* Molecules of any architecture (Sec. 2.1: branched molecules, rings, any
+ * mixture; Sec. 3.2.1: the architecture array; Sec. 3.1.2: independent sets).
+ *   words (n_words uint32): one block per architecture, starting at
+ *     start[a] (n_arch = 1..256 entries): word 0 = N (the system's N, <= 64);
+ *     word 1 + i = (index in words of particle i's first bond word << 8) |
+ *     type (0 A, 1 B), index 0xFFFFFF for a particle without bonds; a bond
+ *     word = (signed 27-bit offset j - i of the partner j << 5) | (bond type
+ *     << 1) | last, where bond type 0 (harmonic, the system's spring) is the
+ *     only one and the list of a particle ends at the word with last = 1.
+ *     Every bond is listed at both ends, once.
+ *   mol_arch (n_chains bytes): the architecture of every molecule.
+ * The independent sets are derived here: particles in index order take the
+ * smallest set index that none of their earlier partners holds (at most 8
+ * sets).  Each sweep a molecule visits its sets in a random order: two sets
+ * as the linear chain (bit 0 of the acceptance word of particle 0's move
+ * draw puts set 1 first), more by an inside-out Fisher-Yates shuffle whose
+ * k-th step (k = 1..n-1) takes j = (h_k (k+1)) >> 16, h_k the k-th 16-bit half
+ * (low half first) of the words of the Philox draw with counter (molecule lo,
+ * molecule hi, sweep, 6 << 24 | replica_id); SOMA_SET_ORDER_FIXED visits them
+ * in index order.  Replaces the diblock (and any mixture) for the sweep, the
+ * occupation count and the bond observables (E_b and b2 over the listed
+ * bonds; Re2 stays |r_{N-1} - r_0|^2); call soma_update_fields to recount at
+ * once.  Uniform moves and the SET scheme only.  src_on_device: all three
+ * arrays are device memory (else host).  SOMA_EINVAL, with the reason in
+ * soma_last_error, for a block that does not fit the array, a type other than
+ * 0/1, a bond type other than 0, a partner outside the molecule or listed
+ * twice, a bond listed at one end only, more than 8 sets, or a mol_arch entry
+ * >= n_arch.  words = NULL returns to the diblock.  The handle keeps its own
+ * copies.  Synchronises. */
+soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words,
+                              const uint32_t* start, uint32_t n_arch, const uint8_t* mol_arch,
+                              int src_on_device);
+
 /* FP64 observables of the current state (Eq. h-bond, Eq. discrete-ham).
  * Synchronises. */
 soma_status soma_observables(soma_t* h, soma_obs* out);

@@ -182,6 +182,21 @@ class System:
         assert a.size == self.desc.n_chains
         _abi.soma_set_architectures(self.h, q.ctypes.data, q.size, a.ctypes.data, 0)
 
+    def set_topology(self, words=None, starts=None, mol_arch=None):
+        """Molecules of any architecture: the architecture array of Sec. 3.2.1
+        (words, uint32; see workloads.encode_architectures), the first word
+        of each architecture's block (starts) and the architecture of every
+        molecule (n_chains uint8); words None returns to the diblock."""
+        if words is None:
+            _abi.soma_set_topology(self.h, None, 0, None, 0, None, 0)
+            return
+        w = np.ascontiguousarray(words, dtype=np.uint32).reshape(-1)
+        st = np.ascontiguousarray(starts, dtype=np.uint32).reshape(-1)
+        a = np.ascontiguousarray(mol_arch, dtype=np.uint8).reshape(-1)
+        assert a.size == self.desc.n_chains
+        _abi.soma_set_topology(self.h, w.ctypes.data, w.size, st.ctypes.data, st.size,
+                               a.ctypes.data, 0)
+
     def get_density(self, out=None):
         """Packed occupation numbers (cells,) uint32: n_A | n_B << 16."""
         cells = self.desc.cells

@@ -89,6 +89,15 @@ struct soma_t {
   bool has_ext = false, has_forbidden = false;
   uint64_t* d_seq = nullptr;                 // mixture: type sequence per architecture
   uint8_t* d_arch = nullptr;                 // mixture: architecture per chain
+  // molecular architectures of Sec. 3.2.1 (types in d_seq, molecules in d_arch)
+  bool has_topo = false;
+  uint32_t* d_topo_words = nullptr;
+  uint32_t* d_topo_start = nullptr;
+  uint8_t* d_topo_sets = nullptr;            // 256 * 64
+  uint8_t* d_topo_nsets = nullptr;           // 256
+  size_t topo_words_cap = 0;
+  double topo_bonds = 0.0;                   // bonds in the system
+  int topo_grid = 1;
   double* d_out = nullptr;
   size_t scratch_doubles = 0;
   double* d_tw = nullptr;
@@ -219,6 +228,10 @@ void release(soma_t* h) {
   cudaFree(h->d_forbidden);
   cudaFree(h->d_seq);
   cudaFree(h->d_arch);
+  cudaFree(h->d_topo_words);
+  cudaFree(h->d_topo_start);
+  cudaFree(h->d_topo_sets);
+  cudaFree(h->d_topo_nsets);
   cudaFree(h->d_tw);
   cudaFree(h->mlp_w);
   cudaFree(h->mlp_q);
@@ -309,7 +322,19 @@ soma_status timed(soma_t* h, int kind, F&& launch) {
   return SOMA_OK;
 }
 
+TopoArgs topo_args(soma_t* h, const SweepArgs& sa) {
+  TopoArgs t;
+  t.s = sa;
+  t.words = h->d_topo_words;
+  t.start = h->d_topo_start;
+  t.sets = h->d_topo_sets;
+  t.nsets = h->d_topo_nsets;
+  t.mol_arch = h->d_arch;
+  return t;
+}
+
 cudaError_t launch_sweep_any(soma_t* h, const SweepArgs& sa) {
+  if (h->has_topo) return launch_sweep_topology(topo_args(h, sa), h->topo_grid, h->grid_dtype, h->stream);
   if (h->desc.move == SOMA_MOVE_LEARNED)
     return launch_sweep_learned(sa, h->shape, h->grid_dtype, h->mlp_q, h->stream);
   return launch_sweep_uniform(sa, h->shape, h->grid_dtype, h->stream);
@@ -628,6 +653,7 @@ soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_ar
                                    const uint8_t* arch, int src_on_device) {
   if (!h) return fail(SOMA_EINVAL, "handle is NULL");
   if (h->batched) return fail(SOMA_ESTATE, "a batch member runs the diblock of its description");
+  h->has_topo = false;
   if (!seq) {   // back to the diblock of the description
     cudaFree(h->d_seq);
     cudaFree(h->d_arch);
@@ -663,6 +689,71 @@ soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_ar
   SOMA_CUDA(cudaMemcpyAsync(h->d_arch, a.data(), a.size(), cudaMemcpyHostToDevice, h->stream));
   if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
   return sync(h);
+}
+
+soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words,
+                              const uint32_t* start, uint32_t n_arch, const uint8_t* mol_arch,
+                              int src_on_device) {
+  if (!h) return fail(SOMA_EINVAL, "handle is NULL");
+  if (h->batched) return fail(SOMA_ESTATE, "a batch member runs the diblock of its description");
+  if (!words) return soma_set_architectures(h, nullptr, 0, nullptr, 0);
+  if (!start || !mol_arch || n_arch < 1 || n_arch > 256 || n_words < 2 || n_words > (1ull << 24))
+    return fail(SOMA_EINVAL, "need 1..256 architectures in 2..2^24 words, start and mol_arch");
+  if (h->g.N > 64) return fail(SOMA_EINVAL, "architectures take N <= 64");
+  if (h->desc.move != SOMA_MOVE_UNIFORM) return fail(SOMA_EINVAL, "architectures take uniform moves");
+  if (h->desc.set_order == SOMA_ITERATION_MOLECULE)
+    return fail(SOMA_EINVAL, "architectures take the SET scheme");
+  const cudaMemcpyKind k = src_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+  std::vector<uint32_t> w((size_t)n_words), st(n_arch);
+  std::vector<uint8_t> a((size_t)h->g.n_chains);
+  SOMA_CUDA(cudaMemcpy(w.data(), words, sizeof(uint32_t) * w.size(), k));
+  SOMA_CUDA(cudaMemcpy(st.data(), start, sizeof(uint32_t) * st.size(), k));
+  SOMA_CUDA(cudaMemcpy(a.data(), mol_arch, a.size(), k));
+  TopologyTables T;
+  const std::string why = topology_tables(w.data(), n_words, st.data(), n_arch, h->g.N, &T);
+  if (!why.empty()) return fail(SOMA_EINVAL, "%s", why.c_str());
+  double bonds = 0.0;
+  for (size_t m = 0; m < a.size(); ++m) {
+    if (a[m] >= n_arch) return fail(SOMA_EINVAL, "mol_arch[%zu] = %u >= n_arch = %u", m, a[m], n_arch);
+    bonds += (double)T.bonds[a[m]];
+  }
+  cudaError_t e;
+  if (h->topo_words_cap < n_words) {
+    cudaFree(h->d_topo_words);
+    h->d_topo_words = nullptr;
+    h->topo_words_cap = 0;
+    e = cudaMalloc((void**)&h->d_topo_words, sizeof(uint32_t) * n_words);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc architecture words");
+    h->topo_words_cap = n_words;
+  }
+  if (!h->d_topo_start) {
+    e = cudaMalloc((void**)&h->d_topo_start, sizeof(uint32_t) * 256);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_topo_sets, 256 * 64);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_topo_nsets, 256);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc architecture tables");
+  }
+  if (!h->d_seq) {
+    e = cudaMalloc((void**)&h->d_seq, sizeof(uint64_t) * 256);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc seq");
+  }
+  if (!h->d_arch) {
+    e = cudaMalloc((void**)&h->d_arch, a.size());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc arch");
+  }
+  const cudaMemcpyKind up = cudaMemcpyHostToDevice;
+  SOMA_CUDA(cudaMemcpyAsync(h->d_topo_words, w.data(), sizeof(uint32_t) * n_words, up, h->stream));
+  SOMA_CUDA(cudaMemcpyAsync(h->d_topo_start, st.data(), sizeof(uint32_t) * n_arch, up, h->stream));
+  SOMA_CUDA(cudaMemcpyAsync(h->d_topo_sets, T.sets.data(), T.sets.size(), up, h->stream));
+  SOMA_CUDA(cudaMemcpyAsync(h->d_topo_nsets, T.nsets.data(), T.nsets.size(), up, h->stream));
+  SOMA_CUDA(cudaMemcpyAsync(h->d_seq, T.seq.data(), sizeof(uint64_t) * n_arch, up, h->stream));
+  SOMA_CUDA(cudaMemcpyAsync(h->d_arch, a.data(), a.size(), up, h->stream));
+  soma_status s2 = sync(h);   // the host vectors are released on return
+  if (s2 != SOMA_OK) return s2;
+  h->topo_bonds = bonds;
+  h->topo_grid = topology_grid(h->grid_dtype, h->sm_count, h->shape.n_tiles);
+  h->has_topo = true;
+  if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+  return SOMA_OK;
 }
 
 soma_status soma_get_parameters(soma_t* h, soma_params* out) {
@@ -705,6 +796,11 @@ soma_status soma_observables(soma_t* h, soma_obs* out) {
                                h->desc.kappaN, h->desc.chiN, (int)h->desc.hamiltonian,
                                h->has_ext ? h->d_ext : nullptr, h->d_scratch, h->d_out, h->stream));
   h->launches += 3;
+  if (h->has_topo) {   // the bonds of the architectures replace those of the linear chain
+    SOMA_CUDA(launch_topology_bonds(h->g, h->x(), h->y(), h->z(), h->d_topo_words,
+                                    h->d_topo_start, h->d_arch, h->d_scratch, h->d_out, h->stream));
+    h->launches += 2;
+  }
   double r[5];
   unsigned long long c[2];
   SOMA_CUDA(cudaMemcpyAsync(r, h->d_out, sizeof r, cudaMemcpyDeviceToHost, h->stream));
@@ -712,7 +808,7 @@ soma_status soma_observables(soma_t* h, soma_obs* out) {
   soma_status st = sync(h);
   if (st != SOMA_OK) return st;
   const double nch = (double)h->g.n_chains;
-  const double nb = nch * (double)(h->g.N > 1 ? h->g.N - 1 : 0);
+  const double nb = h->has_topo ? h->topo_bonds : nch * (double)(h->g.N > 1 ? h->g.N - 1 : 0);
   out->E_b = h->K_b * r[0];
   out->E_nb = h->rho_cell / (double)h->g.N * r[2];
   out->E_ext = r[4];

@@ -1,6 +1,9 @@
 // kernels.h -- host-side launchers of the libsoma kernels (internal).
 #pragma once
 
+#include <string>
+#include <vector>
+
 #include "common.cuh"
 
 namespace soma {
@@ -91,6 +94,34 @@ cudaError_t launch_wait_probe(uint32_t limit, unsigned* err, cudaStream_t st);
 const void* molecule_kernel_ptr(uint32_t N, int grid_dtype, size_t* smem, bool prepare);
 // smart Monte Carlo sweep kernel: paired layout (even N <= 64, 32-bit indices) or general
 const void* smc_kernel_ptr(int Q, bool pair, int grid_dtype);
+
+// Molecules of any architecture (topology.cu): the architecture array of
+// Sec. 3.2.1 and the independent sets derived from it.
+struct TopoArgs {
+  SweepArgs s;               // geometry, positions, fields, tile shape (G = 64/N)
+  const uint32_t* words;     // architecture array
+  const uint32_t* start;     // first word of each architecture's block
+  const uint8_t* sets;       // independent set of particle i of architecture a: [a*64 + i]
+  const uint8_t* nsets;      // sets per architecture
+  const uint8_t* mol_arch;   // architecture of every molecule
+};
+struct TopologyTables {
+  std::vector<uint8_t> sets;     // n_arch * 64
+  std::vector<uint8_t> nsets;    // n_arch
+  std::vector<uint64_t> seq;     // type bits (bit i: particle i is B)
+  std::vector<uint32_t> bonds;   // bonds per architecture
+};
+// Checks an architecture array against a system of N particles per molecule
+// and derives the tables; returns an empty string or what is wrong.
+std::string topology_tables(const uint32_t* words, uint64_t n_words, const uint32_t* start,
+                            uint32_t n_arch, uint32_t N, TopologyTables* out);
+int topology_grid(int grid_dtype, int sm_count, uint64_t n_tiles);
+cudaError_t launch_sweep_topology(const TopoArgs& a, int grid, int grid_dtype, cudaStream_t st);
+// out[0] = sum over the bonds of the architectures of |b|^2 (FP64); part: OBS_BLOCKS doubles
+cudaError_t launch_topology_bonds(const Geom& g, const float* x, const float* y, const float* z,
+                                  const uint32_t* words, const uint32_t* start,
+                                  const uint8_t* mol_arch, double* part, double* out,
+                                  cudaStream_t st);
 
 // Entry-point helpers implemented in api.cu (messages go to soma_last_error).
 }  // namespace soma

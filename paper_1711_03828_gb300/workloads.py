@@ -159,13 +159,14 @@ def linear_architecture(N, N_A=None):
 
 def star_architecture(arms, arm_len, arm_types=None):
     """Star: particle 0 is the centre (type A), then each arm's particles from
-    the centre outwards; arm_types[k] is the type of arm k (default
-    alternating A, B)."""
+    the centre outwards; arm_len is one length for every arm or a list of
+    lengths; arm_types[k] is the type of arm k (default alternating A, B)."""
+    lens = [arm_len] * arms if isinstance(arm_len, int) else list(arm_len)
     types, bonds = [0], []
     for k in range(arms):
         t = (k % 2) if arm_types is None else arm_types[k]
         prev = 0
-        for _ in range(arm_len):
+        for _ in range(lens[k]):
             i = len(types)
             types.append(t)
             bonds.append((prev, i))
@@ -232,14 +233,15 @@ def encode_architectures(molecules):
 
 
 def architecture_positions(desc: SystemDesc, molecules, arch, seed: int,
-                           bond_sigma: float = None) -> np.ndarray:
+                           bond_sigma: float = None, chunk: int = 1 << 18) -> np.ndarray:
     """Seeded synthetic input for molecules of the given architectures
     (arch[k] indexes molecules): particle 0 uniform in the box, every later
-    particle at its lowest-index bonded partner before it plus a normal
-    displacement of standard deviation bond_sigma per axis (default
-    R_e0/sqrt(3(N-1))); a particle with no earlier partner is placed uniformly
-    in the box.  Ring closures start stretched.  Returns (3, M) float32."""
-    rng = np.random.default_rng(seed)
+    particle at its lowest-index bonded partner plus a normal displacement of
+    standard deviation bond_sigma per axis (default R_e0/sqrt(3(N-1))); a
+    particle with no earlier partner is placed uniformly in the box, so the
+    bonds that close rings start stretched.  Molecules are drawn in chunks of
+    `chunk` with the generator seeded by (seed, chunk index).  Returns (3, M)
+    float32."""
     Re = desc.grid[0] / desc.box_Re[0]
     N = desc.N
     if bond_sigma is None:
@@ -255,14 +257,33 @@ def architecture_positions(desc: SystemDesc, molecules, arch, seed: int,
         parent.append(p)
     n = desc.n_chains
     arch = np.asarray(arch)
-    out = np.zeros((3, n, N))
-    free = rng.random((3, n, N)) * box[:, None, None]
-    steps = rng.normal(0.0, bond_sigma, size=(3, n, N))
-    for a, p in enumerate(parent):
-        sel = np.nonzero(arch == a)[0]
-        for i in range(N):
-            if p[i] < 0:
-                out[:, sel, i] = free[:, sel, i]
-            else:
-                out[:, sel, i] = out[:, sel, p[i]] + steps[:, sel, i]
-    return out.reshape(3, n * N).astype(np.float32)
+    out = np.empty((3, n, N), np.float32)
+    for c, k0 in enumerate(range(0, n, chunk)):
+        k1 = min(n, k0 + chunk)
+        rng = np.random.default_rng([seed, c])
+        part = np.zeros((3, k1 - k0, N))
+        free = rng.random((3, k1 - k0, N)) * box[:, None, None]
+        steps = rng.normal(0.0, bond_sigma, size=(3, k1 - k0, N))
+        ar = arch[k0:k1]
+        for a, p in enumerate(parent):
+            sel = np.nonzero(ar == a)[0]
+            for i in range(N):
+                if p[i] < 0:
+                    part[:, sel, i] = free[:, sel, i]
+                else:
+                    part[:, sel, i] = part[:, sel, p[i]] + steps[:, sel, i]
+        out[:, k0:k1] = part
+    return out.reshape(3, n * N)
+
+
+def arch_large(seed=1, **kw):
+    """The 134M-particle melt of melt_large with molecules of four
+    architectures in equal numbers (random per molecule): a three-arm star
+    (arms 11, 10, 10; arms alternately A, B), a comb (A backbone of 16 with
+    four B teeth of 4), a ring (16 A, 16 B) and the linear diblock; N = 32."""
+    return melt_large(seed=seed, **kw)
+
+
+def arch_large_molecules():
+    return [star_architecture(3, [11, 10, 10]), comb_architecture(16, 4, 4),
+            ring_architecture(32), linear_architecture(32)]

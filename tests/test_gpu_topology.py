@@ -1,0 +1,237 @@
+"""Molecules of any architecture (the architecture array of Sec. 3.2.1, the
+independent sets of Sec. 3.1.2) on the GPU against the FP64 oracle, through
+the C ABI: stars, combs, rings (odd rings need three sets), chains with
+next-nearest bonds (triangles, three sets) and linear chains mixed in one
+system."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1711_03828_gb300 import (ITERATION_MOLECULE, MOVE_SMC, SomaError, System, SystemDesc,
+                                    _abi, workloads)
+from tests.conftest import oracle_system
+from tests.test_gpu_parity import TIE, _fields_tol, _pos
+
+pytestmark = pytest.mark.gpu
+
+
+def _triangles(N):
+    """Linear chain with next-nearest bonds i - (i+2): triangles, three sets."""
+    types = [0 if i < N // 2 else 1 for i in range(N)]
+    bonds = [(i, i + 1) for i in range(N - 1)] + [(i, i + 2) for i in range(N - 2)]
+    return types, bonds
+
+
+CASES = {
+    "N16_star_comb_ring_linear": (
+        dict(n_chains=2048, N=16, box_Re=(2.0, 2.0, 2.0), grid=(12, 12, 12)),
+        [workloads.star_architecture(3, 5), workloads.comb_architecture(8, 4, 2),
+         workloads.ring_architecture(16), workloads.linear_architecture(16)]),
+    "N9_odd_ring_star": (
+        dict(n_chains=3000, N=9, box_Re=(1.5, 1.5, 1.0), grid=(9, 9, 6)),
+        [workloads.ring_architecture(9), workloads.star_architecture(4, 2),
+         workloads.linear_architecture(9)]),
+    "N64_star_triangles_ring": (
+        dict(n_chains=512, N=64, box_Re=(2.0, 2.0, 1.0), grid=(12, 12, 6)),
+        [workloads.star_architecture(7, 9), _triangles(64), workloads.ring_architecture(64)]),
+    "N5_ring_star": (
+        dict(n_chains=6000, N=5, box_Re=(1.0, 1.0, 1.0), grid=(6, 6, 6)),
+        [workloads.ring_architecture(5), workloads.star_architecture(4, 1)]),
+}
+
+
+def _setup(name, set_order=0, seed=5, **over):
+    kw, mols = CASES[name]
+    kw = dict(kw, f=0.5, chiN=30.0, kappaN=50.0, seed=seed, set_order=set_order)
+    kw.update(over)
+    d = SystemDesc(**kw)
+    arch = np.random.default_rng(seed).integers(0, len(mols), d.n_chains).astype(np.uint8)
+    words, starts = workloads.encode_architectures(mols)
+    pos0 = workloads.architecture_positions(d, mols, arch, seed=seed + 100)
+    return d, mols, arch, words, starts, pos0
+
+
+def _check_decisions(bad, margin, N):
+    """Mismatched decisions only at near-ties and, downstream of a tie, in the
+    same molecule (its partners move later in the sweep against a different
+    position)."""
+    bad = np.asarray(bad)
+    tied = bad[np.abs(margin[bad]) < TIE]
+    tied_mol = set((tied // N).tolist())
+    for m in bad[np.abs(margin[bad]) >= TIE].tolist():
+        assert m // N in tied_mol, (m, margin[m])
+
+
+@pytest.mark.parametrize("name,set_order", [(n, 0) for n in CASES] +
+                         [("N16_star_comb_ring_linear", 1), ("N9_odd_ring_star", 1)])
+def test_topology_cycles_match_oracle(cuda_device, name, set_order):
+    d, mols, arch, words, starts, pos0 = _setup(name, set_order)
+    gpu = System(d)
+    gpu.set_topology(words, starts, arch)
+    gpu.set_positions(pos0)
+    gpu.update_fields()
+    orc = oracle_system(d)
+    orc.set_topology(words, starts, arch)
+    p = _pos(pos0)
+    nA, nB = orc.histogram(p)
+    wA, wB = orc.fields(nA, nB)
+    moves = mism = acc_tot = 0
+    for sweep in range(12):
+        n = gpu.get_density()
+        np.testing.assert_array_equal(n & 0xFFFF, nA)
+        np.testing.assert_array_equal(n >> 16, nB)
+        gA, gB = gpu.get_fields()
+        tol = _fields_tol(d, nA, nB, orc.params.rho_cell)
+        assert np.all(np.abs(gA - wA) <= tol) and np.all(np.abs(gB - wB) <= tol)
+        old = p.copy()
+        st, margin, acc = orc.sweep(p, wA, wB, sweep, want_margin=True, want_acc=True)
+        gpu.sweep(1)
+        g = gpu.get_positions()
+        gacc = ((g[0] != old.x) | (g[1] != old.y) | (g[2] != old.z)).astype(np.uint8)
+        bad = np.nonzero(gacc != acc)[0]
+        moves += d.M
+        acc_tot += int(acc.sum())
+        if len(bad):
+            _check_decisions(bad, margin, d.N)
+            mism += len(bad)
+            keep = np.ones(d.n_chains, bool)
+            keep[np.unique(bad // d.N)] = False
+            keep = np.repeat(keep, d.N)
+            np.testing.assert_array_equal(g[:, keep], p.stacked()[:, keep])
+            break
+        np.testing.assert_array_equal(g, p.stacked())
+        nA, nB = orc.histogram(p)
+        wA, wB = orc.fields(nA, nB)
+    o = gpu.observables()
+    gpu.close()
+    print(f"{name} set_order={set_order}: {moves} moves, acceptance {acc_tot / moves:.3f}, "
+          f"tolerated mismatches {mism}")
+    assert moves >= 6 * d.M
+    assert 0.2 < acc_tot / moves < 0.95
+    assert o["sweeps"] == moves // d.M
+
+
+def test_topology_observables_match_oracle(cuda_device):
+    d, mols, arch, words, starts, pos0 = _setup("N16_star_comb_ring_linear")
+    gpu = System(d)
+    gpu.set_topology(words, starts, arch)
+    gpu.set_positions(pos0)
+    gpu.update_fields()
+    o = gpu.observables()
+    gpu.close()
+    orc = oracle_system(d)
+    orc.set_topology(words, starts, arch)
+    p = _pos(pos0)
+    nA, nB = orc.histogram(p)
+    ref = orc.observables(p, nA, nB)
+    for k in ("E_b", "E_nb", "Re2", "b2", "E_tot"):
+        assert o[k] == pytest.approx(ref[k], rel=1e-9), k
+
+
+def test_topology_graph_replay_is_identical(cuda_device):
+    """soma_sweep(32) replays the captured cycle graph; 32 single cycles give
+    the same positions bit for bit."""
+    d, mols, arch, words, starts, pos0 = _setup("N9_odd_ring_star")
+    out = []
+    for chunked in (True, False):
+        s = System(d)
+        s.set_topology(words, starts, arch)
+        s.set_positions(pos0)
+        s.update_fields()
+        if chunked:
+            s.sweep(32)
+        else:
+            for _ in range(32):
+                s.sweep(1)
+        out.append(s.get_positions())
+        s.close()
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+def test_ideal_star_and_ring_statistics(cuda_device):
+    """chiN = kappaN = 0: <|r_i - r_j|^2> = d_ij b0^2 on a star (graph distance
+    d_ij) and b0^2 d (N - d)/N on an odd ring (three sets), b0^2 = R_e0^2/(N-1),
+    over 16384 molecules and 1500 cycles."""
+    Re = 6.0
+    for mol in (workloads.star_architecture(3, 5), workloads.ring_architecture(15)):
+        N = len(mol[0])
+        d = SystemDesc(n_chains=16384, N=N, f=0.5, box_Re=(4.0, 4.0, 2.0), grid=(24, 24, 12),
+                       chiN=0.0, kappaN=0.0, seed=9)
+        words, starts = workloads.encode_architectures([mol])
+        arch = np.zeros(d.n_chains, np.uint8)
+        s = System(d)
+        s.set_topology(words, starts, arch)
+        s.set_positions(workloads.architecture_positions(d, [mol], arch, seed=4))
+        s.update_fields()
+        s.sweep(500)
+        acc = np.zeros((d.n_chains, N, N))
+        k = 0
+        for _ in range(50):
+            s.sweep(20)
+            P = s.get_positions().astype(np.float64).reshape(3, d.n_chains, N)
+            acc += ((P[:, :, :, None] - P[:, :, None, :]) ** 2).sum(0)
+            k += 1
+        s.close()
+        r2 = acc / k
+        D = np.full((N, N), 10**6)
+        np.fill_diagonal(D, 0)
+        for i, j in mol[1]:
+            D[i, j] = D[j, i] = 1
+        for m in range(N):
+            D = np.minimum(D, D[:, m:m + 1] + D[m:m + 1, :])
+        b02 = Re**2 / (N - 1)
+        ring = len(mol[1]) == N
+        for dist in range(1, int(D.max()) + 1):
+            per_mol = r2[:, np.triu(D == dist, 1)].mean(axis=1)
+            want = b02 * dist * (N - dist) / N if ring else dist * b02
+            se = per_mol.std() / math.sqrt(len(per_mol))
+            assert abs(per_mol.mean() - want) < 5 * se, (ring, dist, per_mol.mean(), want, se)
+
+
+def test_topology_arguments_are_checked(cuda_device):
+    d, mols, arch, words, starts, pos0 = _setup("N9_odd_ring_star")
+    s = System(d)
+
+    def expect_einval(w, st, a):
+        with pytest.raises(SomaError) as e:
+            s.set_topology(w, st, a)
+        assert e.value.status == _abi.SOMA_EINVAL, _abi.soma_last_error()
+
+    ring = workloads.ring_architecture(9)
+    good, gst = workloads.encode_architectures([ring])
+    a0 = np.zeros(d.n_chains, np.uint8)
+    s.set_topology(good, gst, a0)                       # valid
+    bad = good.copy()
+    bad[gst[0] + 1 + 3] = (int(bad[gst[0] + 1 + 3]) & 0xFFFFFF00) | 2      # type 2
+    expect_einval(bad, gst, a0)
+    first = int(good[gst[0] + 1] >> 8)                   # particle 0's first bond word
+    bad = good.copy()
+    bad[first] |= 1 << 1                                 # bond type 1
+    expect_einval(bad, gst, a0)
+    bad = good.copy()
+    bad[first] = (int(bad[first]) & 0x1F) | (40 << 5)            # partner outside
+    expect_einval(bad, gst, a0)
+    bad = good.copy()
+    bad[first] = (int(bad[first]) & 0x1F) | (4 << 5)             # 0-4 listed at 0 only
+    expect_einval(bad, gst, a0)
+    expect_einval(good, np.array([len(good) - 2], np.uint32), a0)   # block past the end
+    lin8, st8 = workloads.encode_architectures([workloads.linear_architecture(8)])
+    expect_einval(lin8, st8, a0)                         # N = 8 in a system of N = 9
+    K9 = ([0] * 9, [(i, j) for i in range(9) for j in range(i + 1, 9)])
+    k9, k9s = workloads.encode_architectures([K9])
+    expect_einval(k9, k9s, a0)                           # nine sets
+    two, two_st = workloads.encode_architectures([ring, ring])
+    a_bad = a0.copy()
+    a_bad[17] = 2
+    expect_einval(two, two_st, a_bad)                    # mol_arch >= n_arch
+    s.set_topology(None)                                 # back to the diblock
+    s.sweep(2)
+    s.close()
+    for kw in (dict(move=MOVE_SMC), dict(set_order=ITERATION_MOLECULE)):
+        s = System(SystemDesc(**dict(CASES["N9_odd_ring_star"][0], f=0.5, chiN=10.0, kappaN=50.0,
+                                     **kw)))
+        with pytest.raises(SomaError) as e:
+            s.set_topology(good, gst, a0)
+        assert e.value.status == _abi.SOMA_EINVAL
+        s.close()
