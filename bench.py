@@ -35,7 +35,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="melt_large",
                     choices=["melt_large", "melt_mid", "melt_small", "melt_slow", "melt_subbox",
-                             "melt_tiny", "arch_large",
+                             "melt_tiny", "arch_large", "arch_mid",
                              "batch64", "decorrelation"])
     ap.add_argument("--move", default="uniform", choices=["uniform", "smc", "learned"],
                     help="trial moves: uniform displacement or smart Monte Carlo")
@@ -89,7 +89,7 @@ def setup_architectures(target, d, seed=1):
 
 def config_of(d, name, l2_note):
     extra = {}
-    if name == "arch_large":
+    if name.startswith("arch_"):
         extra["architectures"] = ("three-arm star (11,10,10), comb (16 + 4x4), ring (32), "
                                   "linear diblock; one drawn per molecule")
     return {**extra,"workload": f"{name}: {d.n_chains} chains x N={d.N}, box {d.box_Re} R_e0, grid "
@@ -115,7 +115,7 @@ def oracle_rate(name, seconds, max_steps=None):
     sub = workloads.scaled(d, (4.0, 4.0, 4.0))
     o = oracle.System(sub.n_chains, sub.N, sub.f, sub.box_Re, sub.grid, sub.chiN, sub.kappaN,
                       seed=sub.seed)
-    if name == "arch_large":
+    if name.startswith("arch_"):
         pos = setup_architectures(o, sub)
         p = oracle.Positions(pos[0].copy(), pos[1].copy(), pos[2].copy())
     else:
@@ -311,7 +311,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     s = System(d, stream=stream)
-    if args.workload == "arch_large":
+    if args.workload.startswith("arch_"):
         s.set_positions(setup_architectures(s, d))
         s.update_fields()
     train_log = None
@@ -397,7 +397,7 @@ def run_ours(args):
                             f"inputs L2-resident ({12 * d.M / 1e6:.2f} MB of positions): a "
                             "latency figure, not a bandwidth one"),
         "roofline": {"bound": "hbm",
-                     "kernel": sweep_kernel_name(d, args.workload == "arch_large"),
+                     "kernel": sweep_kernel_name(d, args.workload.startswith("arch_")),
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": measured_traffic(args.workload)
                      if args.grid_dtype == "f32" and args.move == "uniform" else None,

@@ -91,11 +91,8 @@ struct soma_t {
   uint8_t* d_arch = nullptr;                 // mixture: architecture per chain
   // molecular architectures of Sec. 3.2.1 (types in d_seq, molecules in d_arch)
   bool has_topo = false;
-  uint32_t* d_topo_words = nullptr;
-  uint32_t* d_topo_start = nullptr;
-  uint8_t* d_topo_sets = nullptr;            // 256 * 64
-  uint8_t* d_topo_nsets = nullptr;           // 256
-  size_t topo_words_cap = 0;
+  uint64_t* d_topo_pmask = nullptr;          // 256 * 64 partner masks
+  uint32_t* d_topo_ptab = nullptr;           // 256 * 64 per-particle table words
   double topo_bonds = 0.0;                   // bonds in the system
   int topo_grid = 1;
   double* d_out = nullptr;
@@ -228,10 +225,8 @@ void release(soma_t* h) {
   cudaFree(h->d_forbidden);
   cudaFree(h->d_seq);
   cudaFree(h->d_arch);
-  cudaFree(h->d_topo_words);
-  cudaFree(h->d_topo_start);
-  cudaFree(h->d_topo_sets);
-  cudaFree(h->d_topo_nsets);
+  cudaFree(h->d_topo_pmask);
+  cudaFree(h->d_topo_ptab);
   cudaFree(h->d_tw);
   cudaFree(h->mlp_w);
   cudaFree(h->mlp_q);
@@ -325,16 +320,16 @@ soma_status timed(soma_t* h, int kind, F&& launch) {
 TopoArgs topo_args(soma_t* h, const SweepArgs& sa) {
   TopoArgs t;
   t.s = sa;
-  t.words = h->d_topo_words;
-  t.start = h->d_topo_start;
-  t.sets = h->d_topo_sets;
-  t.nsets = h->d_topo_nsets;
+  t.pmask = h->d_topo_pmask;
+  t.ptab = h->d_topo_ptab;
   t.mol_arch = h->d_arch;
   return t;
 }
 
 cudaError_t launch_sweep_any(soma_t* h, const SweepArgs& sa) {
-  if (h->has_topo) return launch_sweep_topology(topo_args(h, sa), h->topo_grid, h->grid_dtype, h->stream);
+  if (h->has_topo)
+    return launch_sweep_topology(topo_args(h, sa), h->topo_grid, h->grid_dtype, h->shape.big,
+                                 h->stream);
   if (h->desc.move == SOMA_MOVE_LEARNED)
     return launch_sweep_learned(sa, h->shape, h->grid_dtype, h->mlp_q, h->stream);
   return launch_sweep_uniform(sa, h->shape, h->grid_dtype, h->stream);
@@ -718,18 +713,9 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
     bonds += (double)T.bonds[a[m]];
   }
   cudaError_t e;
-  if (h->topo_words_cap < n_words) {
-    cudaFree(h->d_topo_words);
-    h->d_topo_words = nullptr;
-    h->topo_words_cap = 0;
-    e = cudaMalloc((void**)&h->d_topo_words, sizeof(uint32_t) * n_words);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc architecture words");
-    h->topo_words_cap = n_words;
-  }
-  if (!h->d_topo_start) {
-    e = cudaMalloc((void**)&h->d_topo_start, sizeof(uint32_t) * 256);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_topo_sets, 256 * 64);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_topo_nsets, 256);
+  if (!h->d_topo_pmask) {
+    e = cudaMalloc((void**)&h->d_topo_pmask, sizeof(uint64_t) * 256 * 64);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_topo_ptab, sizeof(uint32_t) * 256 * 64);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc architecture tables");
   }
   if (!h->d_seq) {
@@ -741,16 +727,16 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc arch");
   }
   const cudaMemcpyKind up = cudaMemcpyHostToDevice;
-  SOMA_CUDA(cudaMemcpyAsync(h->d_topo_words, w.data(), sizeof(uint32_t) * n_words, up, h->stream));
-  SOMA_CUDA(cudaMemcpyAsync(h->d_topo_start, st.data(), sizeof(uint32_t) * n_arch, up, h->stream));
-  SOMA_CUDA(cudaMemcpyAsync(h->d_topo_sets, T.sets.data(), T.sets.size(), up, h->stream));
-  SOMA_CUDA(cudaMemcpyAsync(h->d_topo_nsets, T.nsets.data(), T.nsets.size(), up, h->stream));
+  SOMA_CUDA(cudaMemcpyAsync(h->d_topo_pmask, T.pmask.data(), sizeof(uint64_t) * T.pmask.size(), up,
+                            h->stream));
+  SOMA_CUDA(cudaMemcpyAsync(h->d_topo_ptab, T.ptab.data(), sizeof(uint32_t) * T.ptab.size(), up,
+                            h->stream));
   SOMA_CUDA(cudaMemcpyAsync(h->d_seq, T.seq.data(), sizeof(uint64_t) * n_arch, up, h->stream));
   SOMA_CUDA(cudaMemcpyAsync(h->d_arch, a.data(), a.size(), up, h->stream));
   soma_status s2 = sync(h);   // the host vectors are released on return
   if (s2 != SOMA_OK) return s2;
   h->topo_bonds = bonds;
-  h->topo_grid = topology_grid(h->grid_dtype, h->sm_count, h->shape.n_tiles);
+  h->topo_grid = topology_grid(h->grid_dtype, h->shape.big, h->sm_count, h->shape.n_tiles);
   h->has_topo = true;
   if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
   return SOMA_OK;
@@ -797,8 +783,8 @@ soma_status soma_observables(soma_t* h, soma_obs* out) {
                                h->has_ext ? h->d_ext : nullptr, h->d_scratch, h->d_out, h->stream));
   h->launches += 3;
   if (h->has_topo) {   // the bonds of the architectures replace those of the linear chain
-    SOMA_CUDA(launch_topology_bonds(h->g, h->x(), h->y(), h->z(), h->d_topo_words,
-                                    h->d_topo_start, h->d_arch, h->d_scratch, h->d_out, h->stream));
+    SOMA_CUDA(launch_topology_bonds(h->g, h->x(), h->y(), h->z(), h->d_topo_pmask, h->d_arch,
+                                    h->d_scratch, h->d_out, h->stream));
     h->launches += 2;
   }
   double r[5];

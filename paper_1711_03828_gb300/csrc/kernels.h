@@ -97,16 +97,19 @@ const void* smc_kernel_ptr(int Q, bool pair, int grid_dtype);
 
 // Molecules of any architecture (topology.cu): the architecture array of
 // Sec. 3.2.1 and the independent sets derived from it.
+// The bond lists of the array are re-encoded per particle: one 32-bit word
+// with its degree, its first three partners, type, set and the number of sets,
+// and a 64-bit mask of all its partners (bit j: bonded to particle j of the
+// molecule) read only for particles with more than three.
 struct TopoArgs {
   SweepArgs s;               // geometry, positions, fields, tile shape (G = 64/N)
-  const uint32_t* words;     // architecture array
-  const uint32_t* start;     // first word of each architecture's block
-  const uint8_t* sets;       // independent set of particle i of architecture a: [a*64 + i]
-  const uint8_t* nsets;      // sets per architecture
+  const uint64_t* pmask;     // partners of particle i of architecture a: [a*64 + i]
+  const uint32_t* ptab;      // [a*64 + i]: degree, first three partners, type, set, sets
   const uint8_t* mol_arch;   // architecture of every molecule
 };
 struct TopologyTables {
-  std::vector<uint8_t> sets;     // n_arch * 64
+  std::vector<uint64_t> pmask;   // n_arch * 64
+  std::vector<uint32_t> ptab;    // n_arch * 64
   std::vector<uint8_t> nsets;    // n_arch
   std::vector<uint64_t> seq;     // type bits (bit i: particle i is B)
   std::vector<uint32_t> bonds;   // bonds per architecture
@@ -115,13 +118,13 @@ struct TopologyTables {
 // and derives the tables; returns an empty string or what is wrong.
 std::string topology_tables(const uint32_t* words, uint64_t n_words, const uint32_t* start,
                             uint32_t n_arch, uint32_t N, TopologyTables* out);
-int topology_grid(int grid_dtype, int sm_count, uint64_t n_tiles);
-cudaError_t launch_sweep_topology(const TopoArgs& a, int grid, int grid_dtype, cudaStream_t st);
+int topology_grid(int grid_dtype, bool big, int sm_count, uint64_t n_tiles);
+cudaError_t launch_sweep_topology(const TopoArgs& a, int grid, int grid_dtype, bool big,
+                                  cudaStream_t st);
 // out[0] = sum over the bonds of the architectures of |b|^2 (FP64); part: OBS_BLOCKS doubles
 cudaError_t launch_topology_bonds(const Geom& g, const float* x, const float* y, const float* z,
-                                  const uint32_t* words, const uint32_t* start,
-                                  const uint8_t* mol_arch, double* part, double* out,
-                                  cudaStream_t st);
+                                  const uint64_t* pmask, const uint8_t* mol_arch, double* part,
+                                  double* out, cudaStream_t st);
 
 // Entry-point helpers implemented in api.cu (messages go to soma_last_error).
 }  // namespace soma

@@ -7,6 +7,12 @@
 // (0xFFFFFF: no bonds), the bond words holding (signed 27-bit partner offset
 // << 5) | (bond type << 1) | last.  Every molecule of a system has the
 // system's N <= 64 particles; mol_arch gives each molecule's architecture.
+// The array is checked and re-encoded on the host when it is set: per
+// particle one 32-bit word with its number of partners, its first three
+// partners, its type, its set and the number of sets (L1-resident: 256 bytes
+// per architecture), and a 64-bit mask of all its partners that the kernel
+// reads only for a particle with more than three; no list of dependent loads
+// is walked on the device.
 //
 // Independent sets: generated on the host when the architectures are set
 // (particles in index order take the smallest set index that none of their
@@ -17,7 +23,8 @@
 // one Philox draw (purpose 6, counter = molecule, sweep).
 //
 // Work decomposition.  A warp owns a tile of G = floor(64/N) whole molecules;
-// lane l holds tile particles l and l + 32 (coalesced 4-byte loads for any N).
+// lane l holds tile particles l and l + 32 (coalesced 4-byte loads for any N);
+// the next tile's positions and architectures are loaded during the current.
 // The tile's positions are staged in shared memory, where a moving particle
 // reads its bond partners (any partner in its molecule, wherever its lane).
 // Draws, trial positions, cells and both field values are computed before
@@ -71,118 +78,165 @@ __device__ __forceinline__ uint32_t set_steps(uint32_t n_sets, bool random, uint
   return steps;
 }
 
-template <typename WT>
-__global__ void __launch_bounds__(256) sweep_topology_kernel(const TopoArgs t) {
+// Per-particle word of the architecture table: bits 0-5 number of partners,
+// 6-11 / 12-17 / 18-23 the first three partners (index in the molecule),
+// bit 24 type (1 = B), 25-27 set, 28-31 number of sets of the architecture.
+__device__ __forceinline__ uint32_t pw_degree(uint32_t w) { return w & 63u; }
+__device__ __forceinline__ uint32_t pw_partner(uint32_t w, int k) { return (w >> (6 + 6 * k)) & 63u; }
+__device__ __forceinline__ bool pw_is_B(uint32_t w) { return (w >> 24) & 1u; }
+__device__ __forceinline__ uint32_t pw_set(uint32_t w) { return (w >> 25) & 7u; }
+__device__ __forceinline__ uint32_t pw_sets(uint32_t w) { return w >> 28; }
+
+// IDX: particle index type (32-bit when M < 2^32: Philox counter word 1 = 0).
+template <typename WT, typename IDX>
+__global__ void __launch_bounds__(256, 2) sweep_topology_kernel(const TopoArgs t) {
   __shared__ float sh[TOPO_WARPS][3][TOPO_TILE];
   const SweepArgs& p = t.s;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* sx = sh[wib][0];
   float* sy = sh[wib][1];
   float* sz = sh[wib][2];
-  const uint64_t nwarps = (uint64_t)gridDim.x * TOPO_WARPS;
+  const IDX nwarps = (IDX)gridDim.x * TOPO_WARPS;
+  const IDX n_tiles = (IDX)p.n_tiles;
+  const IDX n_mol = (IDX)p.g.n_chains;
   const unsigned long long s64 = *p.d_sweep;
   const uint32_t sweep = (uint32_t)s64;
   uint32_t* __restrict__ nacc = ((s64 + 1ull) & 1ull) ? p.n1 : p.n0;
   const WT* __restrict__ wA = static_cast<const WT*>(p.wA);
   const WT* __restrict__ wB = static_cast<const WT*>(p.wB);
-  const uint32_t N = p.g.N;
+  const uint32_t N = p.g.N, G = p.G;
   const uint32_t ctr3 = (PURPOSE_MOVE << 24) | (p.g.replica & 0xFFFFFFu);
-  const uint32_t ctr3s = (PURPOSE_SETS << 24) | (p.g.replica & 0xFFFFFFu);
   const bool random = p.set_order_random != 0;
 
-  // Tile-invariant slot data: tile index, molecule in the tile, position in
-  // the molecule, and (lane, slot) holding the molecule's particle 0.
-  uint32_t tl[2], gm[2], ci[2], src_lane[2], src_slot[2];
+  // Tile-invariant slot data, one register per slot: molecule in the tile
+  // (bits 0-7) and position in the molecule (bits 8-15).  Slot j of lane l is
+  // tile particle l + 32 j.
+  uint32_t gc[2];
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
-    tl[j] = (uint32_t)lane + 32u * (uint32_t)j;
-    gm[j] = tl[j] / N;
-    ci[j] = tl[j] - gm[j] * N;
-    const uint32_t first = gm[j] * N;
-    src_lane[j] = first & 31u;
-    src_slot[j] = first >> 5;
+    const uint32_t tl = (uint32_t)lane + 32u * (uint32_t)j;
+    const uint32_t g = tl / N;
+    gc[j] = g | (tl - g * N) << 8;
   }
+  auto tile_rows = [&](IDX tile) {
+    const IDX rem = n_mol - tile * G;
+    return (rem < (IDX)G ? (uint32_t)rem : G) * N;
+  };
 
-  unsigned my_acc = 0;
-  for (uint64_t tile = (uint64_t)blockIdx.x * TOPO_WARPS + wib; tile < p.n_tiles; tile += nwarps) {
-    const uint64_t chain0 = tile * p.G;
-    const uint64_t rem = p.g.n_chains - chain0;
-    const uint32_t nmono = (rem < p.G ? (uint32_t)rem : p.G) * N;
-    const uint64_t base = chain0 * N;
-
-    float x[2], y[2], z[2], xn[2], yn[2], zn[2], lnu[2], dEf[2];
-    uint32_t co[2], cn[2], boff[2], inc[2], set_of[2], own[2], n_sets[2];
-    bool valid[2];
+  // positions and architectures (a0 | a1 << 8) of the next tile, loaded
+  // while the current one is processed
+  float px[2] = {0.f, 0.f}, py[2] = {0.f, 0.f}, pz[2] = {0.f, 0.f};
+  uint32_t pa = 0u;
+  auto prefetch = [&](IDX tile) {
+    if (tile >= n_tiles) return;
+    const uint32_t rows = tile_rows(tile);
+    pa = 0u;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      valid[j] = tl[j] < nmono;
-      const uint64_t m = base + tl[j];
-      x[j] = valid[j] ? __ldcs(p.x + m) : 0.f;
-      y[j] = valid[j] ? __ldcs(p.y + m) : 0.f;
-      z[j] = valid[j] ? __ldcs(p.z + m) : 0.f;
-      sx[tl[j]] = x[j];
-      sy[tl[j]] = y[j];
-      sz[tl[j]] = z[j];
-      const uint64_t mol = chain0 + gm[j];
-      const uint32_t a = valid[j] ? __ldg(t.mol_arch + mol) : 0u;
-      const uint32_t mw = __ldg(t.words + __ldg(t.start + a) + 1u + ci[j]);
-      const bool isB = (mw & 0xFFu) != 0u;
-      boff[j] = mw >> 8;
-      inc[j] = isB ? 0x10000u : 1u;
-      set_of[j] = __ldg(t.sets + a * TOPO_TILE + ci[j]);
-      n_sets[j] = valid[j] ? __ldg(t.nsets + a) : 0u;
-      const uint4 r = philox_rk(make_uint4((uint32_t)m, (uint32_t)(m >> 32), sweep, ctr3), p.g);
+      const uint32_t tl = (uint32_t)lane + 32u * (uint32_t)j;
+      if (tl >= rows) continue;
+      const IDX m = tile * (G * N) + tl;
+      px[j] = __ldcs(p.x + m);
+      py[j] = __ldcs(p.y + m);
+      pz[j] = __ldcs(p.z + m);
+      pa |= (uint32_t)__ldg(t.mol_arch + (tile * G + (gc[j] & 0xFFu))) << (8 * j);
+    }
+  };
+  IDX tile = (IDX)blockIdx.x * TOPO_WARPS + wib;
+  prefetch(tile);
+
+  unsigned my_acc = 0;
+  for (; tile < n_tiles; tile += nwarps) {
+    const IDX chain0 = tile * G;
+    const uint32_t nmono = tile_rows(tile);
+    const IDX base = chain0 * N;
+    float x[2] = {px[0], px[1]}, y[2] = {py[0], py[1]}, z[2] = {pz[0], pz[1]};
+    const uint32_t a2 = pa;
+    prefetch(tile + nwarps);
+
+    // per slot: trial position, acceptance threshold -ln u - (field change),
+    // cells, table word, and the step at which the slot's set moves
+    float xn[2], yn[2], zn[2], thr[2];
+    uint32_t co[2], cn[2], pw[2], own[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const uint32_t tl = (uint32_t)lane + 32u * (uint32_t)j;
+      const bool valid = tl < nmono;
+      const uint32_t ci = gc[j] >> 8;
+      const IDX m = base + tl;
+      sx[tl] = x[j];
+      sy[tl] = y[j];
+      sz[tl] = z[j];
+      pw[j] = valid ? __ldg(t.ptab + ((a2 >> (8 * j)) & 0xFFu) * TOPO_TILE + ci) : 0u;
+      const uint32_t hi = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)m >> 32) : 0u;
+      const uint4 r = philox_rk(make_uint4((uint32_t)m, hi, sweep, ctr3), p.g);
       xn[j] = __fadd_rn(x[j], __fmul_rn(p.a, uniform_sym(r.x)));
       yn[j] = __fadd_rn(y[j], __fmul_rn(p.a, uniform_sym(r.y)));
       zn[j] = __fadd_rn(z[j], __fmul_rn(p.a, uniform_sym(r.z)));
-      lnu[j] = log_uniform_open(r.w);
       co[j] = cell_of(p.g, x[j], y[j], z[j]);
       cn[j] = cell_of(p.g, xn[j], yn[j], zn[j]);
-      const WT* wt = isB ? wB : wA;
-      dEf[j] = valid[j] ? load_w<WT>(wt, cn[j]) - load_w<WT>(wt, co[j]) : 0.f;
-      own[j] = (valid[j] && ci[j] == 0u)
-                   ? set_steps(n_sets[j], random, r.w & 1u, mol, sweep, ctr3s, p.g) : 0u;
+      const WT* wt = pw_is_B(pw[j]) ? wB : wA;
+      const float dEf = valid ? load_w<WT>(wt, cn[j]) - load_w<WT>(wt, co[j]) : 0.f;
+      thr[j] = -log_uniform_open(r.w) - dEf;
+      own[j] = (valid && ci == 0u)
+                   ? set_steps(pw_sets(pw[j]), random, r.w & 1u, (uint64_t)(chain0 + (gc[j] & 0xFFu)),
+                               sweep, (PURPOSE_SETS << 24) | (p.g.replica & 0xFFFFFFu), p.g)
+                   : 0u;
     }
-    uint32_t step[2];
+    uint32_t n_steps = 0, step[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      const uint32_t v0 = __shfl_sync(FULL, own[0], (int)src_lane[j]);
-      const uint32_t v1 = __shfl_sync(FULL, own[1], (int)src_lane[j]);
-      step[j] = ((src_slot[j] ? v1 : v0) >> (4u * set_of[j])) & 15u;
+      const uint32_t first = (gc[j] & 0xFFu) * N;   // tile index of the molecule's particle 0
+      const uint32_t v0 = __shfl_sync(FULL, own[0], (int)(first & 31u));
+      const uint32_t v1 = __shfl_sync(FULL, own[1], (int)(first & 31u));
+      const uint32_t ns = pw_sets(pw[j]);           // 0 for an empty slot
+      step[j] = ns ? (((first >> 5) ? v1 : v0) >> (4u * pw_set(pw[j]))) & 15u : 15u;
+      n_steps = max(n_steps, ns);
     }
-    const uint32_t n_steps = __reduce_max_sync(FULL, max(n_sets[0], n_sets[1]));
+    n_steps = __reduce_max_sync(FULL, n_steps);
     __syncwarp();
 
     for (uint32_t k = 0; k < n_steps; ++k) {
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        if (!valid[j] || step[j] != k) continue;
-        float ux = 0.f, uy = 0.f, uz = 0.f, nb = 0.f;
-        if (boff[j] != TOPO_NO_BONDS) {
-          const int mol0 = (int)(gm[j] * N) + (int)ci[j];
-          // a validated list has at most N - 1 < 64 entries
-          for (uint32_t b = boff[j], e = boff[j] + TOPO_TILE; b < e; ++b) {
-            const uint32_t w = __ldg(t.words + b);
-            const uint32_t q = (uint32_t)(mol0 + ((int32_t)w >> 5));
+        if (step[j] != k) continue;
+        const uint32_t mol0 = (gc[j] & 0xFFu) * N;
+        const uint32_t deg = pw_degree(pw[j]);
+        float ux = 0.f, uy = 0.f, uz = 0.f;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          if ((uint32_t)b < deg) {
+            const uint32_t q = mol0 + pw_partner(pw[j], b);
             ux += x[j] - sx[q];
             uy += y[j] - sy[q];
             uz += z[j] - sz[q];
-            nb += 1.f;
-            if (w & 1u) break;
+          }
+        }
+        if (deg > 3u) {   // the partners after the third, from the full mask
+          const uint32_t ci = gc[j] >> 8;
+          uint64_t mk = __ldg(t.pmask + ((a2 >> (8 * j)) & 0xFFu) * TOPO_TILE + ci);
+          mk &= mk - 1ull;
+          mk &= mk - 1ull;
+          mk &= mk - 1ull;
+          for (; mk; mk &= mk - 1ull) {
+            const uint32_t q = mol0 + (uint32_t)__ffsll((long long)mk) - 1u;
+            ux += x[j] - sx[q];
+            uy += y[j] - sy[q];
+            uz += z[j] - sz[q];
           }
         }
         const float dx = xn[j] - x[j], dy = yn[j] - y[j], dz = zn[j] - z[j];
         const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
         const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float dE = fmaf(p.K_b, fmaf(2.f, du, nb * dd), dEf[j]);
-        if (dE <= -lnu[j]) {
+        if (p.K_b * fmaf(2.f, du, (float)deg * dd) <= thr[j]) {
+          const uint32_t tl = (uint32_t)lane + 32u * (uint32_t)j;
           x[j] = xn[j];
           y[j] = yn[j];
           z[j] = zn[j];
           co[j] = cn[j];
-          sx[tl[j]] = x[j];
-          sy[tl[j]] = y[j];
-          sz[tl[j]] = z[j];
+          sx[tl] = x[j];
+          sy[tl] = y[j];
+          sz[tl] = z[j];
           ++my_acc;
         }
       }
@@ -191,12 +245,13 @@ __global__ void __launch_bounds__(256) sweep_topology_kernel(const TopoArgs t) {
 
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      if (!valid[j]) continue;
-      const uint64_t m = base + tl[j];
+      const uint32_t tl = (uint32_t)lane + 32u * (uint32_t)j;
+      if (tl >= nmono) continue;
+      const IDX m = base + tl;
       __stcs(p.x + m, x[j]);
       __stcs(p.y + m, y[j]);
       __stcs(p.z + m, z[j]);
-      atomicAdd(nacc + co[j], inc[j]);
+      atomicAdd(nacc + co[j], pw_is_B(pw[j]) ? 0x10000u : 1u);
     }
     __syncwarp();
   }
@@ -205,20 +260,26 @@ __global__ void __launch_bounds__(256) sweep_topology_kernel(const TopoArgs t) {
   if (lane == 0 && my_acc) atomicAdd(p.acc, (unsigned long long)my_acc);
 }
 
-const void* topology_kernel_ptr(int grid_dtype) {
+const void* topology_kernel_ptr(int grid_dtype, bool big) {
+  if (big) {
+    switch (grid_dtype) {
+      case 1: return (const void*)sweep_topology_kernel<__nv_bfloat16, uint64_t>;
+      case 2: return (const void*)sweep_topology_kernel<__half, uint64_t>;
+      default: return (const void*)sweep_topology_kernel<float, uint64_t>;
+    }
+  }
   switch (grid_dtype) {
-    case 1: return (const void*)sweep_topology_kernel<__nv_bfloat16>;
-    case 2: return (const void*)sweep_topology_kernel<__half>;
-    default: return (const void*)sweep_topology_kernel<float>;
+    case 1: return (const void*)sweep_topology_kernel<__nv_bfloat16, uint32_t>;
+    case 2: return (const void*)sweep_topology_kernel<__half, uint32_t>;
+    default: return (const void*)sweep_topology_kernel<float, uint32_t>;
   }
 }
 
 // Sum over bonds of |r_i - r_j|^2 (each bond once, from its lower index), FP64.
 __global__ void __launch_bounds__(256) topology_bonds_kernel(
     const Geom g, const float* __restrict__ x, const float* __restrict__ y,
-    const float* __restrict__ z, const uint32_t* __restrict__ words,
-    const uint32_t* __restrict__ start, const uint8_t* __restrict__ mol_arch,
-    double* __restrict__ part) {
+    const float* __restrict__ z, const uint64_t* __restrict__ pmask,
+    const uint8_t* __restrict__ mol_arch, double* __restrict__ part) {
   __shared__ double sh[32];
   double v = 0.0;
   const uint64_t M = g.n_chains * g.N;
@@ -226,20 +287,14 @@ __global__ void __launch_bounds__(256) topology_bonds_kernel(
   for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += stride) {
     const uint64_t mol = m / g.N;
     const uint32_t i = (uint32_t)(m - mol * g.N);
-    const uint32_t mw = __ldg(words + __ldg(start + __ldg(mol_arch + mol)) + 1u + i);
-    const uint32_t b0 = mw >> 8;
-    if (b0 == TOPO_NO_BONDS) continue;
-    for (uint32_t b = b0, e = b0 + TOPO_TILE; b < e; ++b) {
-      const uint32_t w = __ldg(words + b);
-      const int32_t off = (int32_t)w >> 5;
-      if (off > 0) {
-        const uint64_t q = m + (uint64_t)off;
-        const double dx = (double)x[q] - (double)x[m];
-        const double dy = (double)y[q] - (double)y[m];
-        const double dz = (double)z[q] - (double)z[m];
-        v += dx * dx + dy * dy + dz * dz;
-      }
-      if (w & 1u) break;
+    const uint64_t pm = __ldg(pmask + (uint32_t)__ldg(mol_arch + mol) * TOPO_TILE + i);
+    // partners above i
+    for (uint64_t mk = i < 63u ? pm >> (i + 1u) : 0ull; mk; mk &= mk - 1ull) {
+      const uint64_t q = m + (uint64_t)__ffsll((long long)mk);
+      const double dx = (double)x[q] - (double)x[m];
+      const double dy = (double)y[q] - (double)y[m];
+      const double dz = (double)z[q] - (double)z[m];
+      v += dx * dx + dy * dy + dz * dz;
     }
   }
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -266,8 +321,10 @@ std::string topology_tables(const uint32_t* w, uint64_t n_words, const uint32_t*
                             uint32_t n_arch, uint32_t N, TopologyTables* T) {
   char msg[256];
   if (N > (uint32_t)TOPO_TILE) return "architectures take N <= 64";
-  T->sets.assign((size_t)n_arch * TOPO_TILE, 0);
+  T->pmask.assign((size_t)n_arch * TOPO_TILE, 0);
+  T->ptab.assign((size_t)n_arch * TOPO_TILE, 0);
   T->nsets.assign(n_arch, 0);
+  std::vector<uint8_t> set_of(TOPO_TILE);
   T->seq.assign(n_arch, 0);
   T->bonds.assign(n_arch, 0);
   for (uint32_t a = 0; a < n_arch; ++a) {
@@ -329,7 +386,7 @@ std::string topology_tables(const uint32_t* w, uint64_t n_words, const uint32_t*
       if (i + 1u < 64u) T->bonds[a] += (uint32_t)__builtin_popcountll(partners[i] >> (i + 1u));
       uint32_t taken = 0;
       for (uint32_t j = 0; j < i; ++j)
-        if (partners[i] >> j & 1ull) taken |= 1u << T->sets[(size_t)a * TOPO_TILE + j];
+        if (partners[i] >> j & 1ull) taken |= 1u << set_of[j];
       uint32_t c = 0;
       while (taken >> c & 1u) ++c;
       if (c >= (uint32_t)TOPO_MAX_SETS) {
@@ -337,17 +394,27 @@ std::string topology_tables(const uint32_t* w, uint64_t n_words, const uint32_t*
                  TOPO_MAX_SETS);
         return msg;
       }
-      T->sets[(size_t)a * TOPO_TILE + i] = (uint8_t)c;
+      set_of[i] = (uint8_t)c;
       n_sets = std::max(n_sets, c + 1u);
     }
     T->nsets[a] = (uint8_t)n_sets;
+    for (uint32_t i = 0; i < N; ++i) {
+      T->pmask[(size_t)a * TOPO_TILE + i] = partners[i];
+      // degree, first three partners, type, set, sets (see pw_* above)
+      uint32_t w = (uint32_t)__builtin_popcountll(partners[i]);
+      uint64_t mk = partners[i];
+      for (int b = 0; b < 3 && mk; ++b, mk &= mk - 1ull)
+        w |= (uint32_t)__builtin_ctzll(mk) << (6 + 6 * b);
+      w |= (uint32_t)(T->seq[a] >> i & 1ull) << 24 | (uint32_t)set_of[i] << 25 | n_sets << 28;
+      T->ptab[(size_t)a * TOPO_TILE + i] = w;
+    }
   }
   return std::string();
 }
 
-int topology_grid(int grid_dtype, int sm_count, uint64_t n_tiles) {
+int topology_grid(int grid_dtype, bool big, int sm_count, uint64_t n_tiles) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topology_kernel_ptr(grid_dtype),
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topology_kernel_ptr(grid_dtype, big),
                                                 TOPO_WARPS * 32, 0);
   if (per_sm < 1) per_sm = 1;
   const uint64_t need = (n_tiles + TOPO_WARPS - 1) / TOPO_WARPS;
@@ -355,20 +422,20 @@ int topology_grid(int grid_dtype, int sm_count, uint64_t n_tiles) {
   return (int)std::max<uint64_t>(1, std::min(need, cap));
 }
 
-cudaError_t launch_sweep_topology(const TopoArgs& a, int grid, int grid_dtype, cudaStream_t st) {
+cudaError_t launch_sweep_topology(const TopoArgs& a, int grid, int grid_dtype, bool big,
+                                  cudaStream_t st) {
   void* args[] = {const_cast<TopoArgs*>(&a)};
-  return cudaLaunchKernel(topology_kernel_ptr(grid_dtype), dim3(grid), dim3(TOPO_WARPS * 32), args,
-                          0, st);
+  return cudaLaunchKernel(topology_kernel_ptr(grid_dtype, big), dim3(grid), dim3(TOPO_WARPS * 32),
+                          args, 0, st);
 }
 
 cudaError_t launch_topology_bonds(const Geom& g, const float* x, const float* y, const float* z,
-                                  const uint32_t* words, const uint32_t* start,
-                                  const uint8_t* mol_arch, double* part, double* out,
-                                  cudaStream_t st) {
+                                  const uint64_t* pmask, const uint8_t* mol_arch, double* part,
+                                  double* out, cudaStream_t st) {
   const uint64_t M = g.n_chains * g.N;
   uint64_t nb = (M + 255) / 256;
   if (nb > OBS_BLOCKS) nb = OBS_BLOCKS;
-  topology_bonds_kernel<<<(unsigned)nb, 256, 0, st>>>(g, x, y, z, words, start, mol_arch, part);
+  topology_bonds_kernel<<<(unsigned)nb, 256, 0, st>>>(g, x, y, z, pmask, mol_arch, part);
   topology_bonds_final_kernel<<<1, 32, 0, st>>>(part, (int)nb, out);
   return cudaGetLastError();
 }

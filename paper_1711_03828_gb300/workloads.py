@@ -284,6 +284,12 @@ def arch_large(seed=1, **kw):
     return melt_large(seed=seed, **kw)
 
 
+def arch_mid(seed=1, **kw):
+    """arch_large in the 16^3 R_e0 box of melt_mid (16,777,216 particles):
+    the profiling case of the architecture sweep."""
+    return melt_mid(seed=seed, **kw)
+
+
 def arch_large_molecules():
     return [star_architecture(3, [11, 10, 10]), comb_architecture(16, 4, 4),
             ring_architecture(32), linear_architecture(32)]
