@@ -23,14 +23,17 @@
 // one Philox draw (purpose 6, counter = molecule, sweep).
 //
 // Work decomposition.  A warp owns a tile of G = floor(64/N) whole molecules;
-// lane l holds tile particles l and l + 32 (coalesced 4-byte loads for any N);
-// the next tile's positions and architectures are loaded during the current.
-// The tile's positions are staged in shared memory, where a moving particle
-// reads its bond partners (any partner in its molecule, wherever its lane).
-// Draws, trial positions, cells and both field values are computed before
-// the sets; then step k of the tile moves every particle whose set is visited
-// k-th in its molecule, with a __syncwarp between steps.  Bond energy change of
-// r -> r + d with partners q: K_b (2 d.U + k d.d), U = sum_q (r - r_q).
+// lane l draws for tile particles l and l + 32 (coalesced 4-byte loads for any
+// N); the next tile's positions and architectures are loaded during the
+// current.  Draws, trial positions, cells and both field values are computed
+// first and recorded, with the positions, in a per-warp shared-memory record.
+// Step k of the tile then moves every particle whose set its molecule visits
+// k-th: those particles are listed (ballot + prefix count) and taken one per
+// lane, so every lane is busy whatever the sizes and orders of the sets, and a
+// mover reads its bond partners from the record wherever they sit.  Bond
+// energy change of r -> r + d with partners q: K_b (2 d.U + k d.d),
+// U = sum_q (r - r_q).  256 threads, 3 blocks per SM (80 registers, 22 KB of
+// shared memory per block).
 #include <algorithm>
 
 #include "kernels.h"
@@ -87,15 +90,24 @@ __device__ __forceinline__ bool pw_is_B(uint32_t w) { return (w >> 24) & 1u; }
 __device__ __forceinline__ uint32_t pw_set(uint32_t w) { return (w >> 25) & 7u; }
 __device__ __forceinline__ uint32_t pw_sets(uint32_t w) { return w >> 28; }
 
+// Shared-memory record of one warp's tile: current and trial positions, the
+// acceptance threshold, trial and final cells, table word, molecule start and
+// architecture of every tile particle, and the list of this step's movers.
+struct TopoTile {
+  float x[TOPO_TILE], y[TOPO_TILE], z[TOPO_TILE];
+  float tx[TOPO_TILE], ty[TOPO_TILE], tz[TOPO_TILE];
+  float thr[TOPO_TILE];
+  uint32_t cn[TOPO_TILE], cell[TOPO_TILE], pw[TOPO_TILE];
+  uint8_t mol0[TOPO_TILE], arch[TOPO_TILE], movers[TOPO_TILE];
+};
+
 // IDX: particle index type (32-bit when M < 2^32: Philox counter word 1 = 0).
 template <typename WT, typename IDX>
-__global__ void __launch_bounds__(256, 2) sweep_topology_kernel(const TopoArgs t) {
-  __shared__ float sh[TOPO_WARPS][3][TOPO_TILE];
+__global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t) {
+  __shared__ TopoTile tiles[TOPO_WARPS];
   const SweepArgs& p = t.s;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  float* sx = sh[wib][0];
-  float* sy = sh[wib][1];
-  float* sz = sh[wib][2];
+  TopoTile& S = tiles[wib];
   const IDX nwarps = (IDX)gridDim.x * TOPO_WARPS;
   const IDX n_tiles = (IDX)p.n_tiles;
   const IDX n_mol = (IDX)p.g.n_chains;
@@ -107,6 +119,7 @@ __global__ void __launch_bounds__(256, 2) sweep_topology_kernel(const TopoArgs t
   const uint32_t N = p.g.N, G = p.G;
   const uint32_t ctr3 = (PURPOSE_MOVE << 24) | (p.g.replica & 0xFFFFFFu);
   const bool random = p.set_order_random != 0;
+  const uint32_t below = (1u << lane) - 1u;
 
   // Tile-invariant slot data, one register per slot: molecule in the tile
   // (bits 0-7) and position in the molecule (bits 8-15).  Slot j of lane l is
@@ -150,93 +163,108 @@ __global__ void __launch_bounds__(256, 2) sweep_topology_kernel(const TopoArgs t
     const IDX chain0 = tile * G;
     const uint32_t nmono = tile_rows(tile);
     const IDX base = chain0 * N;
-    float x[2] = {px[0], px[1]}, y[2] = {py[0], py[1]}, z[2] = {pz[0], pz[1]};
+    const float x[2] = {px[0], px[1]}, y[2] = {py[0], py[1]}, z[2] = {pz[0], pz[1]};
     const uint32_t a2 = pa;
     prefetch(tile + nwarps);
 
-    // per slot: trial position, acceptance threshold -ln u - (field change),
-    // cells, table word, and the step at which the slot's set moves
-    float xn[2], yn[2], zn[2], thr[2];
-    uint32_t co[2], cn[2], pw[2], own[2];
+    // Draws, trial positions, cells and field changes of the natural slots,
+    // recorded in the tile record.
+    uint32_t own[2], step[2], n_steps = 0;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const uint32_t tl = (uint32_t)lane + 32u * (uint32_t)j;
       const bool valid = tl < nmono;
       const uint32_t ci = gc[j] >> 8;
+      const uint32_t a = (a2 >> (8 * j)) & 0xFFu;
       const IDX m = base + tl;
-      sx[tl] = x[j];
-      sy[tl] = y[j];
-      sz[tl] = z[j];
-      pw[j] = valid ? __ldg(t.ptab + ((a2 >> (8 * j)) & 0xFFu) * TOPO_TILE + ci) : 0u;
+      const uint32_t pw = valid ? __ldg(t.ptab + a * TOPO_TILE + ci) : 0u;
       const uint32_t hi = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)m >> 32) : 0u;
       const uint4 r = philox_rk(make_uint4((uint32_t)m, hi, sweep, ctr3), p.g);
-      xn[j] = __fadd_rn(x[j], __fmul_rn(p.a, uniform_sym(r.x)));
-      yn[j] = __fadd_rn(y[j], __fmul_rn(p.a, uniform_sym(r.y)));
-      zn[j] = __fadd_rn(z[j], __fmul_rn(p.a, uniform_sym(r.z)));
-      co[j] = cell_of(p.g, x[j], y[j], z[j]);
-      cn[j] = cell_of(p.g, xn[j], yn[j], zn[j]);
-      const WT* wt = pw_is_B(pw[j]) ? wB : wA;
-      const float dEf = valid ? load_w<WT>(wt, cn[j]) - load_w<WT>(wt, co[j]) : 0.f;
-      thr[j] = -log_uniform_open(r.w) - dEf;
+      const float xn = __fadd_rn(x[j], __fmul_rn(p.a, uniform_sym(r.x)));
+      const float yn = __fadd_rn(y[j], __fmul_rn(p.a, uniform_sym(r.y)));
+      const float zn = __fadd_rn(z[j], __fmul_rn(p.a, uniform_sym(r.z)));
+      const uint32_t co = cell_of(p.g, x[j], y[j], z[j]);
+      const uint32_t cn = cell_of(p.g, xn, yn, zn);
+      const WT* wt = pw_is_B(pw) ? wB : wA;
+      const float dEf = valid ? load_w<WT>(wt, cn) - load_w<WT>(wt, co) : 0.f;
+      S.x[tl] = x[j];
+      S.y[tl] = y[j];
+      S.z[tl] = z[j];
+      S.tx[tl] = xn;
+      S.ty[tl] = yn;
+      S.tz[tl] = zn;
+      S.thr[tl] = -log_uniform_open(r.w) - dEf;
+      S.cn[tl] = cn;
+      S.cell[tl] = co;
+      S.pw[tl] = pw;
+      S.mol0[tl] = (uint8_t)((gc[j] & 0xFFu) * N);
+      S.arch[tl] = (uint8_t)a;
       own[j] = (valid && ci == 0u)
-                   ? set_steps(pw_sets(pw[j]), random, r.w & 1u, (uint64_t)(chain0 + (gc[j] & 0xFFu)),
+                   ? set_steps(pw_sets(pw), random, r.w & 1u, (uint64_t)(chain0 + (gc[j] & 0xFFu)),
                                sweep, (PURPOSE_SETS << 24) | (p.g.replica & 0xFFFFFFu), p.g)
                    : 0u;
+      step[j] = pw;   // resolved below, once every slot's own steps exist
     }
-    uint32_t n_steps = 0, step[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const uint32_t first = (gc[j] & 0xFFu) * N;   // tile index of the molecule's particle 0
       const uint32_t v0 = __shfl_sync(FULL, own[0], (int)(first & 31u));
       const uint32_t v1 = __shfl_sync(FULL, own[1], (int)(first & 31u));
-      const uint32_t ns = pw_sets(pw[j]);           // 0 for an empty slot
-      step[j] = ns ? (((first >> 5) ? v1 : v0) >> (4u * pw_set(pw[j]))) & 15u : 15u;
+      const uint32_t pw = step[j];
+      const uint32_t ns = pw_sets(pw);             // 0 for an empty slot
+      step[j] = ns ? (((first >> 5) ? v1 : v0) >> (4u * pw_set(pw))) & 15u : 15u;
       n_steps = max(n_steps, ns);
     }
     n_steps = __reduce_max_sync(FULL, n_steps);
     __syncwarp();
 
+    // Step k: the particles whose set moves k-th are listed and taken one per
+    // lane (all lanes busy whatever the sets' sizes and orders).
     for (uint32_t k = 0; k < n_steps; ++k) {
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        if (step[j] != k) continue;
-        const uint32_t mol0 = (gc[j] & 0xFFu) * N;
-        const uint32_t deg = pw_degree(pw[j]);
+      const bool m0 = step[0] == k, m1 = step[1] == k;
+      const uint32_t b0 = __ballot_sync(FULL, m0), b1 = __ballot_sync(FULL, m1);
+      const uint32_t c0 = __popc(b0);
+      if (m0) S.movers[__popc(b0 & below)] = (uint8_t)lane;
+      if (m1) S.movers[c0 + __popc(b1 & below)] = (uint8_t)(32 + lane);
+      __syncwarp();
+      const uint32_t count = c0 + __popc(b1);
+      for (uint32_t r = (uint32_t)lane; r < count; r += 32u) {
+        const uint32_t q = S.movers[r];
+        const uint32_t pw = S.pw[q];
+        const uint32_t mol0 = S.mol0[q];
+        const uint32_t deg = pw_degree(pw);
+        const float rx = S.x[q], ry = S.y[q], rz = S.z[q];
         float ux = 0.f, uy = 0.f, uz = 0.f;
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
           if ((uint32_t)b < deg) {
-            const uint32_t q = mol0 + pw_partner(pw[j], b);
-            ux += x[j] - sx[q];
-            uy += y[j] - sy[q];
-            uz += z[j] - sz[q];
+            const uint32_t n = mol0 + pw_partner(pw, b);
+            ux += rx - S.x[n];
+            uy += ry - S.y[n];
+            uz += rz - S.z[n];
           }
         }
         if (deg > 3u) {   // the partners after the third, from the full mask
-          const uint32_t ci = gc[j] >> 8;
-          uint64_t mk = __ldg(t.pmask + ((a2 >> (8 * j)) & 0xFFu) * TOPO_TILE + ci);
+          uint64_t mk = __ldg(t.pmask + (uint32_t)S.arch[q] * TOPO_TILE + (q - mol0));
           mk &= mk - 1ull;
           mk &= mk - 1ull;
           mk &= mk - 1ull;
           for (; mk; mk &= mk - 1ull) {
-            const uint32_t q = mol0 + (uint32_t)__ffsll((long long)mk) - 1u;
-            ux += x[j] - sx[q];
-            uy += y[j] - sy[q];
-            uz += z[j] - sz[q];
+            const uint32_t n = mol0 + (uint32_t)__ffsll((long long)mk) - 1u;
+            ux += rx - S.x[n];
+            uy += ry - S.y[n];
+            uz += rz - S.z[n];
           }
         }
-        const float dx = xn[j] - x[j], dy = yn[j] - y[j], dz = zn[j] - z[j];
+        const float tx = S.tx[q], ty = S.ty[q], tz = S.tz[q];
+        const float dx = tx - rx, dy = ty - ry, dz = tz - rz;
         const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
         const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (p.K_b * fmaf(2.f, du, (float)deg * dd) <= thr[j]) {
-          const uint32_t tl = (uint32_t)lane + 32u * (uint32_t)j;
-          x[j] = xn[j];
-          y[j] = yn[j];
-          z[j] = zn[j];
-          co[j] = cn[j];
-          sx[tl] = x[j];
-          sy[tl] = y[j];
-          sz[tl] = z[j];
+        if (p.K_b * fmaf(2.f, du, (float)deg * dd) <= S.thr[q]) {
+          S.x[q] = tx;
+          S.y[q] = ty;
+          S.z[q] = tz;
+          S.cell[q] = S.cn[q];
           ++my_acc;
         }
       }
@@ -248,10 +276,10 @@ __global__ void __launch_bounds__(256, 2) sweep_topology_kernel(const TopoArgs t
       const uint32_t tl = (uint32_t)lane + 32u * (uint32_t)j;
       if (tl >= nmono) continue;
       const IDX m = base + tl;
-      __stcs(p.x + m, x[j]);
-      __stcs(p.y + m, y[j]);
-      __stcs(p.z + m, z[j]);
-      atomicAdd(nacc + co[j], pw_is_B(pw[j]) ? 0x10000u : 1u);
+      __stcs(p.x + m, S.x[tl]);
+      __stcs(p.y + m, S.y[tl]);
+      __stcs(p.z + m, S.z[tl]);
+      atomicAdd(nacc + S.cell[tl], pw_is_B(S.pw[tl]) ? 0x10000u : 1u);
     }
     __syncwarp();
   }
