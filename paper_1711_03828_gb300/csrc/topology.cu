@@ -32,7 +32,7 @@
 // lane, so every lane is busy whatever the sizes and orders of the sets, and a
 // mover reads its bond partners from the record wherever they sit.  Bond
 // energy change of r -> r + d with partners q: K_b (2 d.U + k d.d),
-// U = sum_q (r - r_q).  256 threads, 3 blocks per SM (80 registers, 22 KB of
+// U = sum_q (r - r_q).  256 threads, 3 blocks per SM (80 registers, 25 KB of
 // shared memory per block).
 #include <algorithm>
 
@@ -90,15 +90,16 @@ __device__ __forceinline__ bool pw_is_B(uint32_t w) { return (w >> 24) & 1u; }
 __device__ __forceinline__ uint32_t pw_set(uint32_t w) { return (w >> 25) & 7u; }
 __device__ __forceinline__ uint32_t pw_sets(uint32_t w) { return w >> 28; }
 
-// Shared-memory record of one warp's tile: current and trial positions, the
-// acceptance threshold, trial and final cells, table word, molecule start and
-// architecture of every tile particle, and the list of this step's movers.
+// Shared-memory record of one warp's tile, one 16-byte entry per particle and
+// array (a mover reads each with one 128-bit access): P = current position and
+// final cell, T = trial position and acceptance threshold, Q = table word,
+// trial cell, molecule start | architecture << 8; and the list of this step's
+// movers.
 struct TopoTile {
-  float x[TOPO_TILE], y[TOPO_TILE], z[TOPO_TILE];
-  float tx[TOPO_TILE], ty[TOPO_TILE], tz[TOPO_TILE];
-  float thr[TOPO_TILE];
-  uint32_t cn[TOPO_TILE], cell[TOPO_TILE], pw[TOPO_TILE];
-  uint8_t mol0[TOPO_TILE], arch[TOPO_TILE], movers[TOPO_TILE];
+  float4 P[TOPO_TILE];
+  float4 T[TOPO_TILE];
+  uint4 Q[TOPO_TILE];
+  uint8_t movers[TOPO_TILE];
 };
 
 // IDX: particle index type (32-bit when M < 2^32: Philox counter word 1 = 0).
@@ -187,18 +188,9 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
       const uint32_t cn = cell_of(p.g, xn, yn, zn);
       const WT* wt = pw_is_B(pw) ? wB : wA;
       const float dEf = valid ? load_w<WT>(wt, cn) - load_w<WT>(wt, co) : 0.f;
-      S.x[tl] = x[j];
-      S.y[tl] = y[j];
-      S.z[tl] = z[j];
-      S.tx[tl] = xn;
-      S.ty[tl] = yn;
-      S.tz[tl] = zn;
-      S.thr[tl] = -log_uniform_open(r.w) - dEf;
-      S.cn[tl] = cn;
-      S.cell[tl] = co;
-      S.pw[tl] = pw;
-      S.mol0[tl] = (uint8_t)((gc[j] & 0xFFu) * N);
-      S.arch[tl] = (uint8_t)a;
+      S.P[tl] = make_float4(x[j], y[j], z[j], __uint_as_float(co));
+      S.T[tl] = make_float4(xn, yn, zn, -log_uniform_open(r.w) - dEf);
+      S.Q[tl] = make_uint4(pw, cn, (gc[j] & 0xFFu) * N | a << 8, 0u);
       own[j] = (valid && ci == 0u)
                    ? set_steps(pw_sets(pw), random, r.w & 1u, (uint64_t)(chain0 + (gc[j] & 0xFFu)),
                                sweep, (PURPOSE_SETS << 24) | (p.g.replica & 0xFFFFFFu), p.g)
@@ -212,7 +204,8 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
       const uint32_t v1 = __shfl_sync(FULL, own[1], (int)(first & 31u));
       const uint32_t pw = step[j];
       const uint32_t ns = pw_sets(pw);             // 0 for an empty slot
-      step[j] = ns ? (((first >> 5) ? v1 : v0) >> (4u * pw_set(pw))) & 15u : 15u;
+      step[j] = (ns ? (((first >> 5) ? v1 : v0) >> (4u * pw_set(pw))) & 15u : 15u) |
+                (uint32_t)pw_is_B(pw) << 4;
       n_steps = max(n_steps, ns);
     }
     n_steps = __reduce_max_sync(FULL, n_steps);
@@ -221,7 +214,7 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
     // Step k: the particles whose set moves k-th are listed and taken one per
     // lane (all lanes busy whatever the sets' sizes and orders).
     for (uint32_t k = 0; k < n_steps; ++k) {
-      const bool m0 = step[0] == k, m1 = step[1] == k;
+      const bool m0 = (step[0] & 15u) == k, m1 = (step[1] & 15u) == k;
       const uint32_t b0 = __ballot_sync(FULL, m0), b1 = __ballot_sync(FULL, m1);
       const uint32_t c0 = __popc(b0);
       if (m0) S.movers[__popc(b0 & below)] = (uint8_t)lane;
@@ -230,41 +223,38 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
       const uint32_t count = c0 + __popc(b1);
       for (uint32_t r = (uint32_t)lane; r < count; r += 32u) {
         const uint32_t q = S.movers[r];
-        const uint32_t pw = S.pw[q];
-        const uint32_t mol0 = S.mol0[q];
+        const uint4 Qq = S.Q[q];
+        const float4 Pq = S.P[q];
+        const uint32_t pw = Qq.x, mol0 = Qq.z & 0xFFu;
         const uint32_t deg = pw_degree(pw);
-        const float rx = S.x[q], ry = S.y[q], rz = S.z[q];
         float ux = 0.f, uy = 0.f, uz = 0.f;
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
           if ((uint32_t)b < deg) {
-            const uint32_t n = mol0 + pw_partner(pw, b);
-            ux += rx - S.x[n];
-            uy += ry - S.y[n];
-            uz += rz - S.z[n];
+            const float4 Pn = S.P[mol0 + pw_partner(pw, b)];
+            ux += Pq.x - Pn.x;
+            uy += Pq.y - Pn.y;
+            uz += Pq.z - Pn.z;
           }
         }
         if (deg > 3u) {   // the partners after the third, from the full mask
-          uint64_t mk = __ldg(t.pmask + (uint32_t)S.arch[q] * TOPO_TILE + (q - mol0));
+          uint64_t mk = __ldg(t.pmask + (Qq.z >> 8) * TOPO_TILE + (q - mol0));
           mk &= mk - 1ull;
           mk &= mk - 1ull;
           mk &= mk - 1ull;
           for (; mk; mk &= mk - 1ull) {
-            const uint32_t n = mol0 + (uint32_t)__ffsll((long long)mk) - 1u;
-            ux += rx - S.x[n];
-            uy += ry - S.y[n];
-            uz += rz - S.z[n];
+            const float4 Pn = S.P[mol0 + (uint32_t)__ffsll((long long)mk) - 1u];
+            ux += Pq.x - Pn.x;
+            uy += Pq.y - Pn.y;
+            uz += Pq.z - Pn.z;
           }
         }
-        const float tx = S.tx[q], ty = S.ty[q], tz = S.tz[q];
-        const float dx = tx - rx, dy = ty - ry, dz = tz - rz;
+        const float4 Tq = S.T[q];
+        const float dx = Tq.x - Pq.x, dy = Tq.y - Pq.y, dz = Tq.z - Pq.z;
         const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
         const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (p.K_b * fmaf(2.f, du, (float)deg * dd) <= S.thr[q]) {
-          S.x[q] = tx;
-          S.y[q] = ty;
-          S.z[q] = tz;
-          S.cell[q] = S.cn[q];
+        if (p.K_b * fmaf(2.f, du, (float)deg * dd) <= Tq.w) {
+          S.P[q] = make_float4(Tq.x, Tq.y, Tq.z, __uint_as_float(Qq.y));
           ++my_acc;
         }
       }
@@ -276,10 +266,11 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
       const uint32_t tl = (uint32_t)lane + 32u * (uint32_t)j;
       if (tl >= nmono) continue;
       const IDX m = base + tl;
-      __stcs(p.x + m, S.x[tl]);
-      __stcs(p.y + m, S.y[tl]);
-      __stcs(p.z + m, S.z[tl]);
-      atomicAdd(nacc + S.cell[tl], pw_is_B(S.pw[tl]) ? 0x10000u : 1u);
+      const float4 Pf = S.P[tl];
+      __stcs(p.x + m, Pf.x);
+      __stcs(p.y + m, Pf.y);
+      __stcs(p.z + m, Pf.z);
+      atomicAdd(nacc + __float_as_uint(Pf.w), (step[j] >> 4) ? 0x10000u : 1u);
     }
     __syncwarp();
   }
