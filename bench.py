@@ -268,7 +268,7 @@ def measured_traffic(workload_name):
 def sweep_kernel_name(d, architectures=False):
     """The sweep kernel libsoma launches for this description."""
     if architectures:
-        return "sweep_topology_kernel"
+        return "sweep_molecule_topology_kernel" if d.set_order == 2 else "sweep_topology_kernel"
     pair = d.N % 2 == 0 and d.N <= 64
     if d.move == 1:
         return "sweep_smc_pair_kernel" if pair else "sweep_smc_kernel"

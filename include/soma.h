@@ -244,7 +244,9 @@ soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_ar
  * in index order.  Replaces the diblock (and any mixture) for the sweep, the
  * occupation count and the bond observables (E_b and b2 over the listed
  * bonds; Re2 stays |r_{N-1} - r_0|^2); call soma_update_fields to recount at
- * once.  Uniform moves and the SET scheme only.  src_on_device: all three
+ * once.  Uniform moves, in the SET scheme or the molecule-parallel iteration
+ * (SOMA_ITERATION_MOLECULE: random particles, partners from the same
+ * tables).  src_on_device: all three
  * arrays are device memory (else host).  SOMA_EINVAL, with the reason in
  * soma_last_error, for a block that does not fit the array, a type other than
  * 0/1, a bond type other than 0, a partner outside the molecule or listed

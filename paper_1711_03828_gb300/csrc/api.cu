@@ -327,6 +327,8 @@ TopoArgs topo_args(soma_t* h, const SweepArgs& sa) {
 }
 
 cudaError_t launch_sweep_any(soma_t* h, const SweepArgs& sa) {
+  if (h->has_topo && h->shape.molecule)
+    return launch_molecule_topology(topo_args(h, sa), h->topo_grid, h->grid_dtype, h->stream);
   if (h->has_topo)
     return launch_sweep_topology(topo_args(h, sa), h->topo_grid, h->grid_dtype, h->shape.big,
                                  h->stream);
@@ -696,8 +698,6 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
     return fail(SOMA_EINVAL, "need 1..256 architectures in 2..2^24 words, start and mol_arch");
   if (h->g.N > 64) return fail(SOMA_EINVAL, "architectures take N <= 64");
   if (h->desc.move != SOMA_MOVE_UNIFORM) return fail(SOMA_EINVAL, "architectures take uniform moves");
-  if (h->desc.set_order == SOMA_ITERATION_MOLECULE)
-    return fail(SOMA_EINVAL, "architectures take the SET scheme");
   const cudaMemcpyKind k = src_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
   std::vector<uint32_t> w((size_t)n_words), st(n_arch);
   std::vector<uint8_t> a((size_t)h->g.n_chains);
@@ -736,7 +736,9 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
   soma_status s2 = sync(h);   // the host vectors are released on return
   if (s2 != SOMA_OK) return s2;
   h->topo_bonds = bonds;
-  h->topo_grid = topology_grid(h->grid_dtype, h->shape.big, h->sm_count, h->shape.n_tiles);
+  h->topo_grid = h->shape.molecule
+                     ? molecule_topology_grid(h->g.N, h->grid_dtype, h->sm_count, h->g.n_chains)
+                     : topology_grid(h->grid_dtype, h->shape.big, h->sm_count, h->shape.n_tiles);
   h->has_topo = true;
   if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
   return SOMA_OK;

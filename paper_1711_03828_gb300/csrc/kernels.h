@@ -121,6 +121,11 @@ std::string topology_tables(const uint32_t* words, uint64_t n_words, const uint3
 int topology_grid(int grid_dtype, bool big, int sm_count, uint64_t n_tiles);
 cudaError_t launch_sweep_topology(const TopoArgs& a, int grid, int grid_dtype, bool big,
                                   cudaStream_t st);
+// the molecule-parallel iteration for molecules of any architecture (N <= 64);
+// the grid helper also allows the kernel its shared memory (call it before
+// the first launch, outside stream capture)
+int molecule_topology_grid(uint32_t N, int grid_dtype, int sm_count, uint64_t n_chains);
+cudaError_t launch_molecule_topology(const TopoArgs& a, int grid, int grid_dtype, cudaStream_t st);
 // out[0] = sum over the bonds of the architectures of |b|^2 (FP64); part: OBS_BLOCKS doubles
 cudaError_t launch_topology_bonds(const Geom& g, const float* x, const float* y, const float* z,
                                   const uint64_t* pmask, const uint8_t* mol_arch, double* part,

@@ -8,7 +8,10 @@
 // of word 3 the acceptance uniform and its low byte the particle,
 // ((word3 & 0xFF) * N) >> 8.  A block stages its 128 chains in shared memory
 // (coalesced in and out) when they fit (N <= 64), then counts the final cells
-// while writing them back.
+// while writing them back.  Molecules of any architecture (the architecture
+// array of Sec. 3.2.1, re-encoded per particle as for the SET kernel of
+// topology.cu) take the same body with their bond partners and types from
+// the per-particle table words.
 #include "kernels.h"
 
 namespace soma {
@@ -16,8 +19,14 @@ namespace soma {
 constexpr uint32_t PURPOSE_ATTEMPT = 3;
 constexpr int MOL_BLOCK = 128;
 
-template <typename WT, bool STAGE>
-__global__ void __launch_bounds__(MOL_BLOCK) sweep_molecule_kernel(const SweepArgs p) {
+// Table word of the architecture path (see topology.cu): bits 0-5 number of
+// partners, 6-23 the first three partners, bit 24 type.
+__device__ __forceinline__ uint32_t mol_partner(uint32_t w, int k) { return (w >> (6 + 6 * k)) & 63u; }
+
+// TOPO: molecules of any architecture (t holds the tables); else linear chains
+// (the diblock, or a mixture through p.seq / p.arch).
+template <typename WT, bool STAGE, bool TOPO>
+__device__ __forceinline__ void molecule_body(const SweepArgs& p, const TopoArgs& tp) {
   extern __shared__ float sm[];
   const uint32_t N = p.g.N, N_A = p.g.N_A;
   const uint32_t t = threadIdx.x;
@@ -51,6 +60,7 @@ __global__ void __launch_bounds__(MOL_BLOCK) sweep_molecule_kernel(const SweepAr
       const uint64_t chain = chain0 + t;
       // type sequence of this chain (bit i set: particle i is B)
       const uint64_t seq = p.seq ? __ldg(p.seq + __ldg(p.arch + chain)) : 0ull;
+      const uint32_t* tab = TOPO ? tp.ptab + (uint32_t)__ldg(tp.mol_arch + chain) * 64u : nullptr;
       float* X = STAGE ? sx + t * N : p.x + chain * N;
       float* Y = STAGE ? sy + t * N : p.y + chain * N;
       float* Z = STAGE ? sz + t * N : p.z + chain * N;
@@ -62,13 +72,41 @@ __global__ void __launch_bounds__(MOL_BLOCK) sweep_molecule_kernel(const SweepAr
         const float xn = __fadd_rn(xo, __fmul_rn(a, uniform_sym(r.x)));
         const float yn = __fadd_rn(yo, __fmul_rn(a, uniform_sym(r.y)));
         const float zn = __fadd_rn(zo, __fmul_rn(a, uniform_sym(r.z)));
-        const bool isB = p.seq ? ((seq >> i) & 1ull) != 0 : i >= N_A;
+        const bool isB = TOPO ? ((__ldg(tab + i) >> 24) & 1u) != 0
+                              : (p.seq ? ((seq >> i) & 1ull) != 0 : i >= N_A);
         const WT* w = isB ? wB : wA;
         const float dEf = load_w<WT>(w, cell_of(p.g, xn, yn, zn)) - load_w<WT>(w, cell_of(p.g, xo, yo, zo));
         // U = sum over bonded partners of (r - n), k partners
         float ux = 0.f, uy = 0.f, uz = 0.f, k = 0.f;
-        if (i > 0) { ux += xo - X[i - 1]; uy += yo - Y[i - 1]; uz += zo - Z[i - 1]; k += 1.f; }
-        if (i + 1 < N) { ux += xo - X[i + 1]; uy += yo - Y[i + 1]; uz += zo - Z[i + 1]; k += 1.f; }
+        if (TOPO) {
+          const uint32_t pw = __ldg(tab + i);
+          const uint32_t deg = pw & 63u;
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            if ((uint32_t)b < deg) {
+              const uint32_t n = mol_partner(pw, b);
+              ux += xo - X[n];
+              uy += yo - Y[n];
+              uz += zo - Z[n];
+            }
+          }
+          if (deg > 3u) {   // the partners after the third, from the full mask
+            uint64_t mk = __ldg(tp.pmask + (uint32_t)__ldg(tp.mol_arch + chain) * 64u + i);
+            mk &= mk - 1ull;
+            mk &= mk - 1ull;
+            mk &= mk - 1ull;
+            for (; mk; mk &= mk - 1ull) {
+              const uint32_t n = (uint32_t)__ffsll((long long)mk) - 1u;
+              ux += xo - X[n];
+              uy += yo - Y[n];
+              uz += zo - Z[n];
+            }
+          }
+          k = (float)deg;
+        } else {
+          if (i > 0) { ux += xo - X[i - 1]; uy += yo - Y[i - 1]; uz += zo - Z[i - 1]; k += 1.f; }
+          if (i + 1 < N) { ux += xo - X[i + 1]; uy += yo - Y[i + 1]; uz += zo - Z[i + 1]; k += 1.f; }
+        }
         const float dx = xn - xo, dy = yn - yo, dz = zn - zo;
         const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
         const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -95,8 +133,13 @@ __global__ void __launch_bounds__(MOL_BLOCK) sweep_molecule_kernel(const SweepAr
       } else {
         x = p.x[m0 + q]; y = p.y[m0 + q]; z = p.z[m0 + q];
       }
-      const bool isB = p.seq ? ((__ldg(p.seq + __ldg(p.arch + chain0 + q / N)) >> ci) & 1ull) != 0
-                             : ci >= N_A;
+      bool isB;
+      if (TOPO)
+        isB = ((__ldg(tp.ptab + (uint32_t)__ldg(tp.mol_arch + chain0 + q / N) * 64u + ci) >> 24) &
+               1u) != 0;
+      else
+        isB = p.seq ? ((__ldg(p.seq + __ldg(p.arch + chain0 + q / N)) >> ci) & 1ull) != 0
+                    : ci >= N_A;
       atomicAdd(nacc + cell_of(p.g, x, y, z), isB ? 0x10000u : 1u);
       ci += step;
       if (ci >= N) ci -= N;
@@ -106,6 +149,43 @@ __global__ void __launch_bounds__(MOL_BLOCK) sweep_molecule_kernel(const SweepAr
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) my_acc += __shfl_xor_sync(FULL, my_acc, o);
   if ((t & 31u) == 0 && my_acc) atomicAdd(p.acc, (unsigned long long)my_acc);
+}
+
+template <typename WT, bool STAGE>
+__global__ void __launch_bounds__(MOL_BLOCK) sweep_molecule_kernel(const SweepArgs p) {
+  molecule_body<WT, STAGE, false>(p, TopoArgs{});
+}
+
+template <typename WT>
+__global__ void __launch_bounds__(MOL_BLOCK) sweep_molecule_topology_kernel(const TopoArgs t) {
+  molecule_body<WT, true, true>(t.s, t);
+}
+
+static const void* molecule_topology_ptr(int grid_dtype) {
+  switch (grid_dtype) {
+    case 1: return (const void*)sweep_molecule_topology_kernel<__nv_bfloat16>;
+    case 2: return (const void*)sweep_molecule_topology_kernel<__half>;
+    default: return (const void*)sweep_molecule_topology_kernel<float>;
+  }
+}
+
+int molecule_topology_grid(uint32_t N, int grid_dtype, int sm_count, uint64_t n_chains) {
+  const void* fn = molecule_topology_ptr(grid_dtype);
+  const size_t smem = (size_t)3 * MOL_BLOCK * N * sizeof(float);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, MOL_BLOCK, smem);
+  if (per_sm < 1) per_sm = 1;
+  const uint64_t need = (n_chains + MOL_BLOCK - 1) / MOL_BLOCK;
+  const uint64_t cap = (uint64_t)sm_count * (uint64_t)per_sm;
+  return (int)(need < cap ? need : cap);
+}
+
+cudaError_t launch_molecule_topology(const TopoArgs& a, int grid, int grid_dtype, cudaStream_t st) {
+  void* args[] = {const_cast<TopoArgs*>(&a)};
+  const size_t smem = (size_t)3 * MOL_BLOCK * a.s.g.N * sizeof(float);
+  return cudaLaunchKernel(molecule_topology_ptr(grid_dtype), dim3(grid), dim3(MOL_BLOCK), args,
+                          smem, st);
 }
 
 template <bool STAGE>

@@ -131,12 +131,14 @@ def _cycle_both(a, b, p, q, sweeps):
     assert a.observables(p, nA, nB) == b.observables(q, nA, nB)
 
 
-def check_linear_topology_is_the_linear_chain(lib=None):
+def check_linear_topology_is_the_linear_chain(lib=None, set_order=0):
     """The diblock written as an architecture array gives bit for bit the
     sweeps, occupation numbers and observables of the linear-chain path, and
-    a mixture of two linear architectures those of the mixture path."""
+    a mixture of two linear architectures those of the mixture path (SET
+    scheme, or the molecule-parallel iteration with set_order 2)."""
     L = _L(lib)
-    d = workloads.melt_small(n_chains=512, chiN=30.0, box_Re=(2.0, 2.0, 1.0), grid=(12, 12, 6))
+    d = workloads.melt_small(n_chains=512, chiN=30.0, box_Re=(2.0, 2.0, 1.0), grid=(12, 12, 6),
+                             set_order=set_order)
     pos0 = workloads.random_walk_positions(d, seed=3)
     lin = oracle_system(d, L)
     top = oracle_system(d, L)
@@ -247,8 +249,9 @@ def test_set_order_is_a_uniform_permutation(oracle_lib):
     check_set_order_is_a_uniform_permutation()
 
 
-def test_linear_topology_is_the_linear_chain(oracle_lib):
-    check_linear_topology_is_the_linear_chain()
+@pytest.mark.parametrize("set_order", [0, 1, 2])
+def test_linear_topology_is_the_linear_chain(oracle_lib, set_order):
+    check_linear_topology_is_the_linear_chain(set_order=set_order)
 
 
 def test_ideal_star_and_ring_closed_forms(oracle_lib):
