@@ -257,6 +257,15 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
                               const uint32_t* start, uint32_t n_arch, const uint8_t* mol_arch,
                               int src_on_device);
 
+/* The check and the independent sets of soma_set_topology on their own, on
+ * the host (no handle, no device): words / start / n_arch as there (host
+ * memory), N the particles per molecule; writes the set of particle i of
+ * architecture a to sets[a*N + i] (n_arch*N bytes) and the number of sets of
+ * each architecture to n_sets (n_arch bytes).  SOMA_EINVAL for an array
+ * soma_set_topology would refuse, with the reason in soma_last_error. */
+soma_status soma_topology_sets(const uint32_t* words, uint64_t n_words, const uint32_t* start,
+                               uint32_t n_arch, uint32_t N, uint8_t* sets, uint8_t* n_sets);
+
 /* FP64 observables of the current state (Eq. h-bond, Eq. discrete-ham).
  * Synchronises. */
 soma_status soma_observables(soma_t* h, soma_obs* out);

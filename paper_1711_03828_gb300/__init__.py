@@ -20,7 +20,8 @@ from ._abi import (FLAG_LEARNED_FP32, FLAG_LEARNED_UMMA, FLAG_NO_SORT, GRID_BF16
                    SomaError)
 
 __all__ = ["SystemDesc", "System", "Batch", "SomaError", "FLAG_NO_SORT", "FLAG_LEARNED_FP32", "FLAG_LEARNED_UMMA", "MOVE_UNIFORM", "MOVE_SMC", "MOVE_LEARNED", "MLP_PARAMS", "SET_ORDER_RANDOM",
-           "SET_ORDER_FIXED", "ITERATION_MOLECULE", "GRID_F32", "GRID_BF16", "GRID_F16"]
+           "SET_ORDER_FIXED", "ITERATION_MOLECULE", "GRID_F32", "GRID_BF16", "GRID_F16",
+           "topology_sets"]
 
 
 @dataclass
@@ -77,6 +78,20 @@ def _torch_stream_handle(stream):
     if stream is None:
         return None
     return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def topology_sets(words, starts, N):
+    """The library's check and independent sets of an architecture array
+    (soma_topology_sets, host only): returns (sets (n_arch, N) uint8, number
+    of sets per architecture); raises SomaError for an array soma_set_topology
+    would refuse."""
+    w = np.ascontiguousarray(words, dtype=np.uint32).reshape(-1)
+    st = np.ascontiguousarray(starts, dtype=np.uint32).reshape(-1)
+    sets = np.zeros((st.size, N), np.uint8)
+    ns = np.zeros(st.size, np.uint8)
+    _abi.soma_topology_sets(w.ctypes.data, w.size, st.ctypes.data, st.size, N, sets.ctypes.data,
+                            ns.ctypes.data)
+    return sets, ns
 
 
 class System:

@@ -744,6 +744,21 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
   return SOMA_OK;
 }
 
+soma_status soma_topology_sets(const uint32_t* words, uint64_t n_words, const uint32_t* start,
+                               uint32_t n_arch, uint32_t N, uint8_t* sets, uint8_t* n_sets) {
+  if (!words || !start || !sets || !n_sets) return fail(SOMA_EINVAL, "NULL argument");
+  if (n_arch < 1 || n_arch > 256 || n_words < 2 || n_words > (1ull << 24) || N < 1)
+    return fail(SOMA_EINVAL, "need 1..256 architectures in 2..2^24 words and N >= 1");
+  TopologyTables T;
+  const std::string why = topology_tables(words, n_words, start, n_arch, N, &T);
+  if (!why.empty()) return fail(SOMA_EINVAL, "%s", why.c_str());
+  for (uint32_t a = 0; a < n_arch; ++a) {
+    n_sets[a] = T.nsets[a];
+    for (uint32_t i = 0; i < N; ++i) sets[(size_t)a * N + i] = (uint8_t)((T.ptab[(size_t)a * 64 + i] >> 25) & 7u);
+  }
+  return SOMA_OK;
+}
+
 soma_status soma_get_parameters(soma_t* h, soma_params* out) {
   if (!h || !out) return fail(SOMA_EINVAL, "NULL argument");
   const double N = (double)h->g.N;
