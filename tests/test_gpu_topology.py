@@ -275,3 +275,49 @@ def test_topology_arguments_are_checked(cuda_device):
             s.set_topology(good, gst, a0)
         assert e.value.status == _abi.SOMA_EINVAL
         s.close()
+
+
+@pytest.mark.parametrize("dtype", [1, 2])
+def test_topology_reduced_precision_grids(cuda_device, dtype):
+    """BF16 / FP16 omega with molecules of any architecture: decisions agree
+    with the oracle's omega rounded to the same type except at near-ties, at
+    particles whose old or new cell holds a value one storage ulp apart (FP32
+    rounding boundary), and downstream of those in the same molecule."""
+    from tests.test_gpu_precision import ROUND_MODE, _cells, _differing_cells, _trial_positions
+    d, mols, arch, words, starts, pos0 = _setup("N16_star_comb_ring_linear", grid_dtype=dtype)
+    s = System(d)
+    s.set_topology(words, starts, arch)
+    s.set_positions(pos0)
+    s.update_fields()
+    orc = oracle_system(d)
+    orc.set_topology(words, starts, arch)
+    p = _pos(pos0)
+    compared = 0
+    for sweep in range(4):
+        nA, nB = orc.histogram(p)
+        n = s.get_density()
+        np.testing.assert_array_equal(n & 0xFFFF, nA)
+        np.testing.assert_array_equal(n >> 16, nB)
+        wA, wB = orc.fields(nA, nB, ROUND_MODE[dtype])
+        gA, gB = s.get_fields()
+        odd = _differing_cells(gA, wA, dtype) | _differing_cells(gB, wB, dtype)
+        old = p.copy()
+        _, margin, acc = orc.sweep(p, wA, wB, sweep, want_margin=True, want_acc=True)
+        s.sweep(1)
+        g = s.get_positions()
+        gacc = (g != old.stacked()).any(axis=0).astype(np.uint8)
+        bad = np.nonzero(gacc != acc)[0]
+        compared += d.M
+        if len(bad):
+            trial = _trial_positions(orc, old, sweep, bad)
+            c_old = _cells(d, old.stacked()[:, bad])
+            c_new = _cells(d, trial)
+            excused = (np.abs(margin[bad]) < TIE) | np.isin(c_old, list(odd)) | \
+                np.isin(c_new, list(odd))
+            mols_ok = set((bad[excused] // d.N).tolist())
+            assert all(m // d.N in mols_ok for m in bad.tolist())
+            break
+        np.testing.assert_array_equal(g, p.stacked())
+    s.close()
+    print(f"architectures, grid dtype {dtype}: {compared} moves compared")
+    assert compared >= 2 * d.M
