@@ -313,6 +313,7 @@ def run_ours(args):
     s = System(d, stream=stream)
     if args.workload.startswith("arch_"):
         s.set_positions(setup_architectures(s, d))
+        s.sort_molecules()   # the generator's molecules are in random spatial order
         s.update_fields()
     train_log = None
     if d.move == 2:  # train the proposal on this system's plain-method configurations

@@ -257,6 +257,19 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
                               const uint32_t* start, uint32_t n_arch, const uint8_t* mol_arch,
                               int src_on_device);
 
+/* Relabels the molecules in the order soma_create gives its own chains: by
+ * the Morton (Z-curve) code of the 8^3-cell block holding each molecule's
+ * particle 0, ties by the previous label (the labels of molecules are
+ * arbitrary, Sec. 3.1.1).  Positions and the architectures of
+ * soma_set_architectures / soma_set_topology follow their molecules; the
+ * occupation numbers and fields do not change.  Molecules that are neighbours
+ * in space then share warps, so the field gathers and count atomics of a warp
+ * hit nearby cells: call it after soma_set_positions with positions in an
+ * arbitrary order.  perm (optional, host, n_chains entries) receives the
+ * previous label of each new label.  SOMA_EINVAL for n_chains >= 2^32,
+ * SOMA_ESTATE for a batch member.  Synchronises. */
+soma_status soma_sort_molecules(soma_t* h, uint64_t* perm);
+
 /* The check and the independent sets of soma_set_topology on their own, on
  * the host (no handle, no device): words / start / n_arch as there (host
  * memory), N the particles per molecule; writes the set of particle i of

@@ -212,6 +212,13 @@ class System:
         _abi.soma_set_topology(self.h, w.ctypes.data, w.size, st.ctypes.data, st.size,
                                a.ctypes.data, 0)
 
+    def sort_molecules(self):
+        """Relabel the molecules in spatial (Morton) order of their particle 0;
+        returns the previous label of each new label (n_chains uint64)."""
+        perm = np.zeros(self.desc.n_chains, np.uint64)
+        _abi.soma_sort_molecules(self.h, perm.ctypes.data)
+        return perm
+
     def get_density(self, out=None):
         """Packed occupation numbers (cells,) uint32: n_A | n_B << 16."""
         cells = self.desc.cells

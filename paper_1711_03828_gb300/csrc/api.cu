@@ -744,6 +744,46 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
   return SOMA_OK;
 }
 
+soma_status soma_sort_molecules(soma_t* h, uint64_t* perm) {
+  if (!h) return fail(SOMA_EINVAL, "handle is NULL");
+  if (h->batched) return fail(SOMA_ESTATE, "a batch member keeps its labels");
+  if (h->g.n_chains >= (1ull << 32)) return fail(SOMA_EINVAL, "labels need n_chains < 2^32");
+  uint64_t n_pad = 1;
+  while (n_pad < h->g.n_chains) n_pad <<= 1;
+  float* stage = nullptr;
+  uint64_t* keys = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&stage, sizeof(float) * 3 * h->plane, h->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&keys, sizeof(uint64_t) * n_pad, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(stage, h->pos, sizeof(float) * 3 * h->plane, cudaMemcpyDeviceToDevice,
+                        h->stream);
+  if (e == cudaSuccess)
+    e = launch_sort_chains(h->g, stage, h->plane, h->pos, h->plane, keys, n_pad, h->sm_count,
+                           h->stream);
+  std::vector<uint64_t> k;
+  if (e == cudaSuccess && (perm || h->d_arch)) {
+    k.resize((size_t)h->g.n_chains);
+    e = cudaMemcpyAsync(k.data(), keys, sizeof(uint64_t) * k.size(), cudaMemcpyDeviceToHost,
+                        h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  if (stage) cudaFreeAsync(stage, h->stream);
+  if (keys) cudaFreeAsync(keys, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "molecule sort");
+  h->launches += 3;
+  if (h->d_arch) {   // the architectures follow their molecules
+    std::vector<uint8_t> a((size_t)h->g.n_chains), b(a.size());
+    SOMA_CUDA(cudaMemcpyAsync(a.data(), h->d_arch, a.size(), cudaMemcpyDeviceToHost, h->stream));
+    SOMA_CUDA(cudaStreamSynchronize(h->stream));
+    for (size_t j = 0; j < b.size(); ++j) b[j] = a[k[j] & 0xFFFFFFFFull];
+    SOMA_CUDA(cudaMemcpyAsync(h->d_arch, b.data(), b.size(), cudaMemcpyHostToDevice, h->stream));
+    SOMA_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  if (perm)
+    for (size_t j = 0; j < k.size(); ++j) perm[j] = k[j] & 0xFFFFFFFFull;
+  return sync(h);
+}
+
 soma_status soma_topology_sets(const uint32_t* words, uint64_t n_words, const uint32_t* start,
                                uint32_t n_arch, uint32_t N, uint8_t* sets, uint8_t* n_sets) {
   if (!words || !start || !sets || !n_sets) return fail(SOMA_EINVAL, "NULL argument");

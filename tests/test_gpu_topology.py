@@ -63,24 +63,16 @@ def _check_decisions(bad, margin, N):
         assert m // N in tied_mol, (m, margin[m])
 
 
-@pytest.mark.parametrize("name,set_order", [(n, 0) for n in CASES] +
-                         [("N16_star_comb_ring_linear", 1), ("N9_odd_ring_star", 1)])
-def test_topology_cycles_match_oracle(cuda_device, name, set_order):
-    d, mols, arch, words, starts, pos0 = _setup(name, set_order)
-    gpu = System(d)
-    gpu.set_topology(words, starts, arch)
-    gpu.set_positions(pos0)
-    gpu.update_fields()
-    orc = oracle_system(d)
-    orc.set_topology(words, starts, arch)
-    p = _pos(pos0)
+def _cycles(d, gpu, orc, p, n):
+    """n cycles on both sides from the same state; returns (moves compared,
+    tolerated mismatches, oracle acceptances)."""
     nA, nB = orc.histogram(p)
     wA, wB = orc.fields(nA, nB)
     moves = mism = acc_tot = 0
-    for sweep in range(12):
-        n = gpu.get_density()
-        np.testing.assert_array_equal(n & 0xFFFF, nA)
-        np.testing.assert_array_equal(n >> 16, nB)
+    for sweep in range(n):
+        n_gpu = gpu.get_density()
+        np.testing.assert_array_equal(n_gpu & 0xFFFF, nA)
+        np.testing.assert_array_equal(n_gpu >> 16, nB)
         gA, gB = gpu.get_fields()
         tol = _fields_tol(d, nA, nB, orc.params.rho_cell)
         assert np.all(np.abs(gA - wA) <= tol) and np.all(np.abs(gB - wB) <= tol)
@@ -103,6 +95,20 @@ def test_topology_cycles_match_oracle(cuda_device, name, set_order):
         np.testing.assert_array_equal(g, p.stacked())
         nA, nB = orc.histogram(p)
         wA, wB = orc.fields(nA, nB)
+    return moves, mism, acc_tot
+
+
+@pytest.mark.parametrize("name,set_order", [(n, 0) for n in CASES] +
+                         [("N16_star_comb_ring_linear", 1), ("N9_odd_ring_star", 1)])
+def test_topology_cycles_match_oracle(cuda_device, name, set_order):
+    d, mols, arch, words, starts, pos0 = _setup(name, set_order)
+    gpu = System(d)
+    gpu.set_topology(words, starts, arch)
+    gpu.set_positions(pos0)
+    gpu.update_fields()
+    orc = oracle_system(d)
+    orc.set_topology(words, starts, arch)
+    moves, mism, acc_tot = _cycles(d, gpu, orc, _pos(pos0), 12)
     o = gpu.observables()
     gpu.close()
     print(f"{name} set_order={set_order}: {moves} moves, acceptance {acc_tot / moves:.3f}, "
@@ -110,6 +116,31 @@ def test_topology_cycles_match_oracle(cuda_device, name, set_order):
     assert moves >= 6 * d.M
     assert 0.2 < acc_tot / moves < 0.95
     assert o["sweeps"] == moves // d.M
+
+
+def test_sort_molecules_relabels_like_the_oracle(cuda_device):
+    """soma_sort_molecules gives the oracle's spatial labelling of the same
+    positions, the architectures follow their molecules (cycles after the sort
+    match the oracle run with the permuted architectures), and the counts do
+    not change."""
+    d, mols, arch, words, starts, pos0 = _setup("N16_star_comb_ring_linear")
+    gpu = System(d)
+    gpu.set_topology(words, starts, arch)
+    gpu.set_positions(pos0)
+    gpu.update_fields()
+    n0 = gpu.get_density()
+    perm = gpu.sort_molecules()
+    np.testing.assert_array_equal(gpu.get_density(), n0)
+    orc = oracle_system(d)
+    p = _pos(pos0)
+    operm = orc.sort_chains(p)
+    np.testing.assert_array_equal(perm, operm)
+    np.testing.assert_array_equal(gpu.get_positions(), p.stacked())
+    assert sorted(perm.tolist()) == list(range(d.n_chains))
+    orc.set_topology(words, starts, arch[perm.astype(np.int64)])
+    moves, mism, _ = _cycles(d, gpu, orc, p, 6)
+    gpu.close()
+    assert moves >= 3 * d.M
 
 
 @pytest.mark.parametrize("name", ["N16_star_comb_ring_linear", "N9_odd_ring_star",
