@@ -84,6 +84,9 @@ class OrSystem(ctypes.Structure):
         ("n_topo", ctypes.c_uint32),
         ("topo_set", ctypes.c_void_p),
         ("topo_nsets", ctypes.c_void_p),
+        ("n_types", ctypes.c_uint32),
+        ("chi_types", ctypes.c_double * 64),
+        ("w_types", ctypes.c_void_p),
     ]
 
 
@@ -153,6 +156,12 @@ def load(path):
     L.or_topology_sets.argtypes = [u32p, ctypes.c_uint32, u8p]
     L.or_topology_sets.restype = ctypes.c_uint32
     L.or_set_order.argtypes = [P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, u32p]
+    L.or_type.argtypes = [P, ctypes.c_uint64, ctypes.c_uint32]
+    L.or_type.restype = ctypes.c_uint32
+    L.or_histogram_types.argtypes = [P, f32p, f32p, f32p, u32p]
+    L.or_fields_types.argtypes = [P, u32p, f64p, ctypes.c_int]
+    L.or_energy_types.argtypes = [P, u32p]
+    L.or_energy_types.restype = ctypes.c_double
     return L
 
 
@@ -374,6 +383,49 @@ class System:
         self.s.topo_nsets = self._topo_nsets.ctypes.data
         self.s.arch = self._arch.ctypes.data
 
+    def set_types(self, n_types=0, chiN=None):
+        """n_t particle types (types from the architecture array's type
+        bytes): chiN is the n_t x n_t matrix of chi_ij N (symmetric, zero
+        diagonal).  n_types 0 returns to the two types A, B."""
+        self.s.n_types = int(n_types)
+        for k in range(64):
+            self.s.chi_types[k] = 0.0
+        if n_types:
+            c = np.asarray(chiN, np.float64).reshape(n_types, n_types)
+            assert 2 <= n_types <= 8 and np.allclose(c, c.T) and np.all(np.diag(c) == 0)
+            for i in range(n_types):
+                for j in range(n_types):
+                    self.s.chi_types[i * 8 + j] = float(c[i, j])
+
+    def type_of(self, chain, i):
+        return int(self.L.or_type(ctypes.byref(self.s), int(chain), int(i)))
+
+    def histogram_types(self, pos):
+        n = np.zeros((self.s.n_types, self.cells), np.uint32)
+        self.L.or_histogram_types(ctypes.byref(self.s), _ptr(pos.x, f32p), _ptr(pos.y, f32p),
+                                  _ptr(pos.z, f32p), _ptr(n, u32p))
+        return n
+
+    def fields_types(self, n, round_mode=0):
+        nn = np.ascontiguousarray(n, np.uint32)
+        w = np.zeros((self.s.n_types, self.cells), np.float64)
+        self.L.or_fields_types(ctypes.byref(self.s), _ptr(nn, u32p), _ptr(w, f64p), int(round_mode))
+        return w
+
+    def energy_types(self, n):
+        nn = np.ascontiguousarray(n, np.uint32)
+        return float(self.L.or_energy_types(ctypes.byref(self.s), _ptr(nn, u32p)))
+
+    def observables_types(self, pos, n):
+        """Observables with n_t types: the bond part as observables(), E_nb of
+        the types' energy, no external energy."""
+        z = np.zeros(self.cells, np.uint32)
+        o = self.observables(pos, z, z)
+        o["E_nb"] = self.energy_types(n)
+        o["E_ext"] = 0.0
+        o["E_tot"] = o["E_b"] + o["E_nb"]
+        return o
+
     def set_order(self, chain, sweep, n_sets):
         """Order in which molecule chain visits its n_sets sets in a sweep."""
         out = np.zeros(8, np.uint32)
@@ -389,7 +441,7 @@ class System:
         return wA, wB
 
     def sweep(self, pos, wA, wB, sweep, c0=0, c1=None, want_margin=False, want_acc=False,
-              want_trial=False, want_chosen=False):
+              want_trial=False, want_chosen=False, w_types=None):
         """One MC step in place; returns (stats, margin or None, accepted or
         None), plus the (3, M) trial positions when want_trial and the chosen
         particle of every attempt when want_chosen (molecule-parallel
@@ -401,6 +453,12 @@ class System:
         trial = np.full(3 * self.M, np.nan, np.float32) if want_trial else None
         chosen = np.zeros(self.M, np.uint32) if want_chosen else None
         self.s.chosen = chosen.ctypes.data if want_chosen else None
+        if w_types is not None:   # the n_t field planes, (n_types, cells)
+            planes = [np.ascontiguousarray(w_types[t], np.float64) for t in range(len(w_types))]
+            ptrs = (ctypes.c_void_p * len(planes))(*[q.ctypes.data for q in planes])
+            self.s.w_types = ctypes.cast(ptrs, ctypes.c_void_p)
+            if wA is None:
+                wA = wB = planes[0]
         st = OrSweepStats()
         try:
             self.L.or_sweep_trial(ctypes.byref(self.s), _ptr(pos.x, f32p), _ptr(pos.y, f32p),
@@ -409,6 +467,7 @@ class System:
                                   _ptr(trial, f32p), ctypes.byref(st))
         finally:
             self.s.chosen = None
+            self.s.w_types = None
         out = (st, margin, acc)
         if want_trial:
             out = out + (trial.reshape(3, self.M),)

@@ -211,6 +211,11 @@ int or_is_B(const or_system* s, uint64_t chain, uint32_t i) {
   return i >= s->N_A;
 }
 
+uint32_t or_type(const or_system* s, uint64_t chain, uint32_t i) {
+  if (s->topo && s->arch) return or_topo_type(s->topo, s->topo_start[s->arch[chain]], i);
+  return (uint32_t)or_is_B(s, chain, i);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Molecular architectures in the array layout of Sec. 3.2.1.                  */
 /* ------------------------------------------------------------------------- */
@@ -349,6 +354,69 @@ void or_fields(const or_system* s, const uint32_t* nA, const uint32_t* nB,
   }
 }
 
+/* n_t particle types: occupation numbers and fields per type (Sec. 2.1, Eq.    */
+/* density-characteristics, hamil-comp, hamil-pair and omega-fields).          */
+void or_histogram_types(const or_system* s, const float* x, const float* y, const float* z,
+                        uint32_t* n) {
+  const uint64_t cells = (uint64_t)s->grid[0] * s->grid[1] * s->grid[2];
+  memset(n, 0, (size_t)s->n_types * cells * sizeof(uint32_t));
+  for (uint64_t k = 0; k < s->n_chains; ++k)
+    for (uint32_t i = 0; i < s->N; ++i) {
+      const uint64_t m = k * s->N + i;
+      n[(uint64_t)or_type(s, k, i) * cells + or_cell(s, x[m], y[m], z[m])] += 1u;
+    }
+}
+
+void or_fields_types(const or_system* s, const uint32_t* n, double* w, int round_mode) {
+  const uint64_t cells = (uint64_t)s->grid[0] * s->grid[1] * s->grid[2];
+  const uint32_t T = s->n_types;
+  const double kappa0 = s->kappaN / (double)s->N;
+  for (uint64_t c = 0; c < cells; ++c) {
+    double phi[8], total = 0.0;
+    for (uint32_t t = 0; t < T; ++t) {
+      phi[t] = (double)n[t * cells + c] / s->rho_cell;
+      total += phi[t];
+    }
+    const double comp = kappa0 * (total - 1.0);
+    for (uint32_t i = 0; i < T; ++i) {
+      double v = comp;
+      for (uint32_t k = 0; k < T; ++k) {
+        if (k == i) continue;
+        const double chi0 = s->chi_types[i * 8 + k] / (double)s->N;
+        if (s->hamiltonian == 1) v = v + chi0 * phi[k];
+        else v = v - 0.5 * chi0 * (phi[i] - phi[k]);
+      }
+      if (round_mode == 1) v = (double)(float)v;
+      else if (round_mode == 2) v = or_round_bf16((float)v);
+      else if (round_mode == 3) v = or_round_fp16((float)v);
+      w[i * cells + c] = v;
+    }
+  }
+}
+
+double or_energy_types(const or_system* s, const uint32_t* n) {
+  const uint64_t cells = (uint64_t)s->grid[0] * s->grid[1] * s->grid[2];
+  const uint32_t T = s->n_types;
+  double K = 0.0;
+  for (uint64_t c = 0; c < cells; ++c) {
+    double phi[8], total = 0.0;
+    for (uint32_t t = 0; t < T; ++t) {
+      phi[t] = (double)n[t * cells + c] / s->rho_cell;
+      total += phi[t];
+    }
+    const double fl = total - 1.0;
+    double k = 0.5 * s->kappaN * fl * fl;
+    for (uint32_t i = 0; i < T; ++i)
+      for (uint32_t j = i + 1; j < T; ++j) {
+        const double chi = s->chi_types[i * 8 + j];
+        if (s->hamiltonian == 1) k += chi * phi[i] * phi[j];
+        else k -= 0.25 * chi * (phi[i] - phi[j]) * (phi[i] - phi[j]);
+      }
+    K += k;
+  }
+  return s->rho_cell / (double)s->N * K;
+}
+
 /* ------------------------------------------------------------------------- */
 /* a2: one Monte-Carlo step with the fields frozen (second stage of the SCMF    */
 /* cycle, Sec. 2.2), iterating each molecule's independent sets in a random     */
@@ -399,6 +467,7 @@ static void or_move_uniform_w(const or_system* s, float* x, float* y, float* z,
   }
   /* field energy change, Eq. (delta-e) */
   const double* w_t = or_is_B(s, chain, i) ? wB : wA;
+  if (s->n_types && s->w_types) w_t = s->w_types[or_type(s, chain, i)];
   uint64_t c_old = or_cell(s, r_old[0], r_old[1], r_old[2]);
   uint64_t c_new = or_cell(s, r_new[0], r_new[1], r_new[2]);
   double dE = dEb + (w_t[c_new] - w_t[c_old]);

@@ -68,6 +68,13 @@ typedef struct {
   uint32_t n_topo;            /* architectures */
   const uint8_t* topo_set;    /* independent set of particle i of architecture a: [a*N + i] */
   const uint8_t* topo_nsets;  /* number of independent sets of each architecture */
+  /* optional n_t particle types (Sec. 2.1, Eq. hamil-pair and omega-fields for
+     n_t types): with topo, particle types are the architecture's type bytes
+     0..n_types-1; chi_types[i*8 + j] = chi_ij N (symmetric, zero diagonal);
+     the sweep then takes the field of type t from w_types[t] */
+  uint32_t n_types;           /* 0: the two types A, B of wA / wB */
+  double chi_types[64];
+  const double* const* w_types;
 } or_system;
 
 /* --- Molecular architectures (Sec. 3.2.1, Fig. polyarch) ---------------------
@@ -104,6 +111,9 @@ void or_set_order(const or_system* s, uint64_t chain, uint32_t sweep, uint32_t n
 /* Type of particle i of a chain: 1 for B, 0 for A (the diblock boundary N_A,
  * or the chain's architecture in a mixture). */
 int or_is_B(const or_system* s, uint64_t chain, uint32_t i);
+/* Type 0..n_t-1 of particle i of a chain (the architecture's type byte, else
+ * or_is_B). */
+uint32_t or_type(const or_system* s, uint64_t chain, uint32_t i);
 
 typedef struct {
   uint64_t attempted, accepted;
@@ -149,6 +159,22 @@ void or_histogram(const or_system* s, const float* x, const float* y, const floa
  * For 2/3 the value is first rounded to FP32 (the storage path of the GPU). */
 void or_fields(const or_system* s, const uint32_t* nA, const uint32_t* nB,
                double* wA, double* wB, int round_mode);
+
+/* --- n_t particle types (Sec. 2.1) ------------------------------------------
+ * Occupation numbers per type, n[t*cells + c]; fields per type,
+ * w[t*cells + c]:
+ *   K^0: omega_i = kappa_0 (sum_k phi_k - 1) - sum_{k != i} chi_0ik/2 (phi_i - phi_k)
+ *   K^1: omega_i = kappa_0 (sum_k phi_k - 1) + sum_{k != i} chi_0ik phi_k
+ * (Eq. omega-fields), the derivatives of the energy per cell
+ *   kappaN/2 (sum phi - 1)^2 - sum_{i<j} chi_ij N/4 (phi_i - phi_j)^2   (K^0)
+ *   kappaN/2 (sum phi - 1)^2 + sum_{i<j} chi_ij N phi_i phi_j           (K^1)
+ * counting every pair of types once (as for two types); or_energy_types
+ * returns E_nb = rho_0 dL^3 / N times its sum over cells.  round_mode as for
+ * or_fields (no external potential). */
+void or_histogram_types(const or_system* s, const float* x, const float* y, const float* z,
+                        uint32_t* n);
+void or_fields_types(const or_system* s, const uint32_t* n, double* w, int round_mode);
+double or_energy_types(const or_system* s, const uint32_t* n);
 
 /* --- a2: one SET sweep with frozen fields (Sec. 3.1.2, Listing 2 scheme) --- */
 /* margin (optional, M doubles): ln u - ln(acceptance ratio) of each attempted

@@ -12,6 +12,7 @@ import oracle
 from tests import test_oracle_philox as PH
 from tests import test_oracle_pins as PIN
 from tests import test_oracle_topology as TOPO
+from tests import test_oracle_types as TYPES
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "soma_oracle.c")
 
@@ -19,8 +20,8 @@ SRC = os.path.join(os.path.dirname(oracle.__file__), "soma_oracle.c")
 MUTANTS = [
     ("field_sign", "(w_t[c_new] - w_t[c_old])", "(w_t[c_old] - w_t[c_new])",
      lambda L: PIN.check_two_particle_balance_brute_force(0, L)),
-    ("field_type_swapped", "const double* w_t = or_is_B(s, chain, i) ? wB : wA;\n  uint64_t c_old",
-     "const double* w_t = or_is_B(s, chain, i) ? wA : wB;\n  uint64_t c_old",
+    ("field_type_swapped", "const double* w_t = or_is_B(s, chain, i) ? wB : wA;\n  if (s->n_types",
+     "const double* w_t = or_is_B(s, chain, i) ? wA : wB;\n  if (s->n_types",
      lambda L: PIN.check_two_particle_balance_brute_force(0, L)),
     ("bond_half_strength", "dEb += s->K_b * (d_new - d_old);", "dEb += 0.5 * s->K_b * (d_new - d_old);",
      PIN.check_ideal_chain_relaxes_to_gaussian_statistics),
@@ -116,6 +117,22 @@ MUTANTS = [
      "order[0] = 1u - first;\n    order[1] = first;", TOPO.check_linear_topology_is_the_linear_chain),
     ("topo_bond_counted_twice", "if (j <= i) continue;", "if (j == i) continue;",
      TOPO.check_topology_observables_hand_values),
+    # n_t particle types
+    ("types_K0_sign", "else v = v - 0.5 * chi0 * (phi[i] - phi[k]);",
+     "else v = v + 0.5 * chi0 * (phi[i] - phi[k]);",
+     lambda L: TYPES.check_type_fields_are_the_energy_derivative(L, 0)),
+    ("types_K1_own_density", "if (s->hamiltonian == 1) v = v + chi0 * phi[k];",
+     "if (s->hamiltonian == 1) v = v + chi0 * phi[i];", lambda L: TYPES.check_two_types_equal_the_AB_path(L, 1)),
+    ("types_kappa_minus_one", "const double comp = kappa0 * (total - 1.0);",
+     "const double comp = kappa0 * total;", lambda L: TYPES.check_type_fields_are_the_energy_derivative(L, 1)),
+    ("types_energy_pair_weight", "else k -= 0.25 * chi * (phi[i] - phi[j]) * (phi[i] - phi[j]);",
+     "else k -= 0.5 * chi * (phi[i] - phi[j]) * (phi[i] - phi[j]);",
+     lambda L: TYPES.check_type_fields_are_the_energy_derivative(L, 0)),
+    ("types_sweep_plane", "if (s->n_types && s->w_types) w_t = s->w_types[or_type(s, chain, i)];",
+     "if (s->n_types && s->w_types) w_t = s->w_types[0];", TYPES.check_identical_types_collapse_under_K1),
+    ("types_histogram_plane", "n[(uint64_t)or_type(s, k, i) * cells + or_cell(s, x[m], y[m], z[m])] += 1u;",
+     "n[(uint64_t)(or_type(s, k, i) & 1u) * cells + or_cell(s, x[m], y[m], z[m])] += 1u;",
+     TYPES.check_type_histogram_matches_numpy),
 ]
 
 
