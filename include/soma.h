@@ -257,6 +257,29 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
                               const uint32_t* start, uint32_t n_arch, const uint8_t* mol_arch,
                               int src_on_device);
 
+/* n_t particle types (Sec. 2.1: Eq. hamil-comp, hamil-pair, omega-fields for
+ * n_t types).  n_types = 2..8 with chiN[i*n_types + j] = chi_ij N (finite,
+ * symmetric, zero diagonal); the option K^0 / K^1 is desc.hamiltonian:
+ *   K^0: omega_i = kappa_0 (sum_k phi_k - 1) - sum_{k != i} chi_ik/(2N) (phi_i - phi_k)
+ *   K^1: omega_i = kappa_0 (sum_k phi_k - 1) + sum_{k != i} chi_ik/N phi_k
+ * and E_nb per cell kappaN/2 (sum phi - 1)^2 - sum_{i<j} chi_ij N/4 (phi_i -
+ * phi_j)^2 (K^0) or + sum_{i<j} chi_ij N phi_i phi_j (K^1), every pair of
+ * types counted once.  Particle types are the type bytes of the architecture
+ * array (soma_set_topology, types < n_types), so the system runs the
+ * architecture path (SET or molecule-parallel, uniform moves, FP32 fields, no
+ * external fields); the occupation numbers become one 32-bit plane per type.
+ * soma_get_density, soma_get_fields and soma_structure_factor then refuse
+ * (SOMA_EINVAL): use soma_get_type_counts / soma_get_type_fields.  Recomputes
+ * counts and fields when architectures are set.  n_types = 0 returns to the
+ * two types A, B (SOMA_ESTATE while the architectures use a type >= 2).
+ * SOMA_EINVAL for a bad n_types or chiN or an incompatible description.
+ * Synchronises. */
+soma_status soma_set_types(soma_t* h, uint32_t n_types, const double* chiN);
+/* Occupation numbers per type, n[t*cells + c] (n = n_types*cells), and the
+ * FP32 fields per type, w[t*cells + c], of the current state.  Synchronise. */
+soma_status soma_get_type_counts(soma_t* h, uint32_t* dst, size_t n, int dst_on_device);
+soma_status soma_get_type_fields(soma_t* h, float* dst, size_t n, int dst_on_device);
+
 /* Relabels the molecules in the order soma_create gives its own chains: by
  * the Morton (Z-curve) code of the 8^3-cell block holding each molecule's
  * particle 0, ties by the previous label (the labels of molecules are
@@ -274,8 +297,10 @@ soma_status soma_sort_molecules(soma_t* h, uint64_t* perm);
  * the host (no handle, no device): words / start / n_arch as there (host
  * memory), N the particles per molecule; writes the set of particle i of
  * architecture a to sets[a*N + i] (n_arch*N bytes) and the number of sets of
- * each architecture to n_sets (n_arch bytes).  SOMA_EINVAL for an array
- * soma_set_topology would refuse, with the reason in soma_last_error. */
+ * each architecture to n_sets (n_arch bytes).  Types 0..7 are accepted (the
+ * sets do not depend on them; soma_set_topology checks them against the
+ * system's types).  SOMA_EINVAL for an array soma_set_topology would refuse
+ * otherwise, with the reason in soma_last_error. */
 soma_status soma_topology_sets(const uint32_t* words, uint64_t n_words, const uint32_t* start,
                                uint32_t n_arch, uint32_t N, uint8_t* sets, uint8_t* n_sets);
 

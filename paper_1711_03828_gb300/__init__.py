@@ -100,6 +100,7 @@ class System:
     def __init__(self, desc: SystemDesc, stream=None, _borrowed=None):
         self.desc = desc
         self._stream_obj = stream
+        self.n_types = 0
         if _borrowed is not None:
             self.h = _borrowed
             self._owner = False
@@ -211,6 +212,29 @@ class System:
         assert a.size == self.desc.n_chains
         _abi.soma_set_topology(self.h, w.ctypes.data, w.size, st.ctypes.data, st.size,
                                a.ctypes.data, 0)
+
+    def set_types(self, n_types=0, chiN=None):
+        """n_t particle types (2..8) with the n_t x n_t matrix chiN of chi_ij N;
+        types come from the architecture array.  0 returns to A, B."""
+        if not n_types:
+            _abi.soma_set_types(self.h, 0, None)
+            self.n_types = 0
+            return
+        c = np.ascontiguousarray(chiN, dtype=np.float64).reshape(n_types, n_types)
+        _abi.soma_set_types(self.h, int(n_types), c.ctypes.data)
+        self.n_types = int(n_types)
+
+    def get_type_counts(self):
+        """Occupation numbers per type, (n_types, cells) uint32."""
+        out = np.empty((self.n_types, self.desc.cells), np.uint32)
+        _abi.soma_get_type_counts(self.h, out.ctypes.data, out.size, 0)
+        return out
+
+    def get_type_fields(self):
+        """Fields per type, (n_types, cells) float32."""
+        out = np.empty((self.n_types, self.desc.cells), np.float32)
+        _abi.soma_get_type_fields(self.h, out.ctypes.data, out.size, 0)
+        return out
 
     def sort_molecules(self):
         """Relabel the molecules in spatial (Morton) order of their particle 0;

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsoma.so")
-SOURCES = ["sweep.cu", "smc.cu", "molecule.cu", "grid.cu", "api.cu", "noalloc.cu", "batch.cu", "learned.cu", "learned_tc.cu", "topology.cu"]
+SOURCES = ["sweep.cu", "smc.cu", "molecule.cu", "grid.cu", "api.cu", "noalloc.cu", "batch.cu", "learned.cu", "learned_tc.cu", "topology.cu", "types.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

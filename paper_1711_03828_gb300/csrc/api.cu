@@ -94,6 +94,13 @@ struct soma_t {
   uint64_t* d_topo_pmask = nullptr;          // 256 * 64 partner masks
   uint32_t* d_topo_ptab = nullptr;           // 256 * 64 per-particle table words
   double topo_bonds = 0.0;                   // bonds in the system
+  uint8_t* d_topo_ttab = nullptr;            // 256 * 64 particle types
+  uint32_t topo_max_type = 0;                // largest type of the current architectures
+  // n_t particle types (0: the two types A, B of the packed grid)
+  uint32_t n_types = 0;
+  double chiN_types[TYPES_MAX * TYPES_MAX] = {};
+  uint32_t* nt[2] = {nullptr, nullptr};      // count planes, n_types * cells each
+  float* wt = nullptr;                       // field planes, n_types * cells
   int topo_grid = 1;
   double* d_out = nullptr;
   size_t scratch_doubles = 0;
@@ -227,6 +234,10 @@ void release(soma_t* h) {
   cudaFree(h->d_arch);
   cudaFree(h->d_topo_pmask);
   cudaFree(h->d_topo_ptab);
+  cudaFree(h->d_topo_ttab);
+  cudaFree(h->nt[0]);
+  cudaFree(h->nt[1]);
+  cudaFree(h->wt);
   cudaFree(h->d_tw);
   cudaFree(h->mlp_w);
   cudaFree(h->mlp_q);
@@ -323,15 +334,47 @@ TopoArgs topo_args(soma_t* h, const SweepArgs& sa) {
   t.pmask = h->d_topo_pmask;
   t.ptab = h->d_topo_ptab;
   t.mol_arch = h->d_arch;
+  t.ttab = h->d_topo_ttab;
+  t.wt = h->wt;
+  t.nt0 = h->nt[0];
+  t.nt1 = h->nt[1];
   return t;
 }
 
+TypesArgs types_args(soma_t* h, int after_sweep) {
+  TypesArgs a;
+  a.g = h->g;
+  a.n0 = h->nt[0];
+  a.n1 = h->nt[1];
+  a.w = h->wt;
+  a.d_sweep = h->d_counters;
+  a.n_types = h->n_types;
+  a.after_sweep = after_sweep;
+  a.hamiltonian = (int)h->desc.hamiltonian;
+  a.inv_rho = (float)(1.0 / h->rho_cell);
+  a.inv_rho_f64 = 1.0 / h->rho_cell;
+  a.kappa0 = (float)(h->desc.kappaN / (double)h->desc.N);
+  for (int k = 0; k < TYPES_MAX * TYPES_MAX; ++k) {
+    a.chiN[k] = h->chiN_types[k];
+    a.chi0[k] = (float)(h->chiN_types[k] / (double)h->desc.N);
+  }
+  return a;
+}
+
+// the field update of one cycle: the packed A | B grid or the type planes
+cudaError_t launch_fields_any(soma_t* h, const FieldArgs& fa, const TypesArgs& ta) {
+  if (h->n_types) return launch_fields_types(ta, h->d_err + 1, h->sm_count, h->stream);
+  return launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count, h->stream);
+}
+
 cudaError_t launch_sweep_any(soma_t* h, const SweepArgs& sa) {
+  const bool types = h->n_types != 0;
   if (h->has_topo && h->shape.molecule)
-    return launch_molecule_topology(topo_args(h, sa), h->topo_grid, h->grid_dtype, h->stream);
+    return launch_molecule_topology(topo_args(h, sa), h->topo_grid, h->grid_dtype, h->stream,
+                                    types);
   if (h->has_topo)
     return launch_sweep_topology(topo_args(h, sa), h->topo_grid, h->grid_dtype, h->shape.big,
-                                 h->stream);
+                                 h->stream, types);
   if (h->desc.move == SOMA_MOVE_LEARNED)
     return launch_sweep_learned(sa, h->shape, h->grid_dtype, h->mlp_q, h->stream);
   return launch_sweep_uniform(sa, h->shape, h->grid_dtype, h->stream);
@@ -342,7 +385,8 @@ soma_status one_cycle(soma_t* h) {
   soma_status st = timed(h, 0, [&] { return launch_sweep_any(h, sa); });
   if (st != SOMA_OK) return st;
   const FieldArgs fa = field_args(h, 1);
-  st = timed(h, 1, [&] { return launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count, h->stream); });
+  const TypesArgs ta = types_args(h, 1);
+  st = timed(h, 1, [&] { return launch_fields_any(h, fa, ta); });
   if (st != SOMA_OK) return st;
   ++h->host_sweep;
   return SOMA_OK;
@@ -353,10 +397,11 @@ soma_status build_graph(soma_t* h) {
   SOMA_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   const SweepArgs sa = sweep_args(h);
   const FieldArgs fa = field_args(h, 1);
+  const TypesArgs ta = types_args(h, 1);
   cudaError_t e = cudaSuccess;
   for (uint32_t k = 0; k < GRAPH_CHUNK && e == cudaSuccess; ++k) {
     e = launch_sweep_any(h, sa);
-    if (e == cudaSuccess) e = launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count, h->stream);
+    if (e == cudaSuccess) e = launch_fields_any(h, fa, ta);
   }
   cudaError_t e2 = cudaStreamEndCapture(h->stream, &gr);
   if (e != cudaSuccess) { if (gr) cudaGraphDestroy(gr); return cuda_fail(e, "graph capture"); }
@@ -381,6 +426,17 @@ soma_status sync(soma_t* h) {
 }
 
 soma_status update_fields(soma_t* h) {
+  if (h->n_types && !h->has_topo)
+    return fail(SOMA_ESTATE, "n_t types take the architecture path: call soma_set_topology");
+  if (h->n_types) {   // count into the type planes nt[s&1], then the fields
+    uint32_t* nn = h->nt[h->host_sweep & 1];
+    SOMA_CUDA(cudaMemsetAsync(nn, 0, sizeof(uint32_t) * h->n_types * h->g.cells, h->stream));
+    SOMA_CUDA(launch_histogram_types(h->g, h->x(), h->y(), h->z(), h->d_topo_ttab, h->d_arch, nn,
+                                     h->sm_count, h->stream));
+    SOMA_CUDA(launch_fields_types(types_args(h, 0), h->d_err + 1, h->sm_count, h->stream));
+    h->launches += 2;
+    return SOMA_OK;
+  }
   // count into n[s&1] (cleared first), then omega from it
   uint32_t* nn = h->n[h->host_sweep & 1];
   SOMA_CUDA(cudaMemsetAsync(nn, 0, sizeof(uint32_t) * h->g.cells, h->stream));
@@ -516,6 +572,8 @@ soma_status soma_sweep(soma_t* h, uint32_t n) {
   if (!h) return fail(SOMA_EINVAL, "handle is NULL");
   if (h->batched) return fail(SOMA_ESTATE, "this system belongs to a batch: use soma_batch_sweep");
   if (h->pos_invalid) return fail(SOMA_ESTATE, "positions out of range: set valid positions first");
+  if (h->n_types && !h->has_topo)
+    return fail(SOMA_ESTATE, "n_t types take the architecture path: call soma_set_topology");
   uint32_t done = 0;
   if (!h->timing && n >= GRAPH_CHUNK) {
     if (!h->graph) {
@@ -553,6 +611,7 @@ void* soma_stream(soma_t* h) { return h ? (void*)h->stream : nullptr; }
 
 soma_status soma_get_density(soma_t* h, uint32_t* dst, size_t n_cells, int dst_on_device) {
   if (!h || !dst) return fail(SOMA_EINVAL, "NULL argument");
+  if (h->n_types) return fail(SOMA_EINVAL, "n_t types: use soma_get_type_counts");
   if (n_cells != h->g.cells) return fail(SOMA_EINVAL, "n_cells=%zu, grid has %u", n_cells, h->g.cells);
   const uint32_t* src = h->n[h->host_sweep & 1];
   SOMA_CUDA(cudaMemcpyAsync(dst, src, sizeof(uint32_t) * n_cells,
@@ -563,6 +622,7 @@ soma_status soma_get_density(soma_t* h, uint32_t* dst, size_t n_cells, int dst_o
 
 soma_status soma_get_fields(soma_t* h, float* dst, size_t n, int dst_on_device) {
   if (!h || !dst) return fail(SOMA_EINVAL, "NULL argument");
+  if (h->n_types) return fail(SOMA_EINVAL, "n_t types: use soma_get_type_fields");
   const size_t cells = h->g.cells;
   if (n != 2 * cells) return fail(SOMA_EINVAL, "n=%zu, expected 2*cells=%zu", n, 2 * cells);
   if (h->grid_dtype == 0) {
@@ -621,6 +681,8 @@ soma_status soma_set_external(soma_t* h, const float* ext, const uint8_t* forbid
   if (!h) return fail(SOMA_EINVAL, "handle is NULL");
   if (forbidden && h->desc.move != SOMA_MOVE_UNIFORM)
     return fail(SOMA_EINVAL, "forbidden cells take uniform moves only");
+  if (h->n_types && (ext || forbidden))
+    return fail(SOMA_EINVAL, "external fields take the two types A, B");
   if (h->batched) return fail(SOMA_ESTATE, "a batch member has no external fields");
   const size_t cells = h->g.cells;
   const cudaMemcpyKind k = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -650,7 +712,9 @@ soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_ar
                                    const uint8_t* arch, int src_on_device) {
   if (!h) return fail(SOMA_EINVAL, "handle is NULL");
   if (h->batched) return fail(SOMA_ESTATE, "a batch member runs the diblock of its description");
+  if (h->n_types) return fail(SOMA_ESTATE, "n_t types take architectures: call soma_set_types(h, 0, NULL) first");
   h->has_topo = false;
+  h->topo_max_type = 0;
   if (!seq) {   // back to the diblock of the description
     cudaFree(h->d_seq);
     cudaFree(h->d_arch);
@@ -705,7 +769,8 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
   SOMA_CUDA(cudaMemcpy(st.data(), start, sizeof(uint32_t) * st.size(), k));
   SOMA_CUDA(cudaMemcpy(a.data(), mol_arch, a.size(), k));
   TopologyTables T;
-  const std::string why = topology_tables(w.data(), n_words, st.data(), n_arch, h->g.N, &T);
+  const std::string why = topology_tables(w.data(), n_words, st.data(), n_arch, h->g.N, &T,
+                                          h->n_types ? h->n_types : 2u);
   if (!why.empty()) return fail(SOMA_EINVAL, "%s", why.c_str());
   double bonds = 0.0;
   for (size_t m = 0; m < a.size(); ++m) {
@@ -716,6 +781,7 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
   if (!h->d_topo_pmask) {
     e = cudaMalloc((void**)&h->d_topo_pmask, sizeof(uint64_t) * 256 * 64);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_topo_ptab, sizeof(uint32_t) * 256 * 64);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_topo_ttab, 256 * 64);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc architecture tables");
   }
   if (!h->d_seq) {
@@ -731,17 +797,106 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
                             h->stream));
   SOMA_CUDA(cudaMemcpyAsync(h->d_topo_ptab, T.ptab.data(), sizeof(uint32_t) * T.ptab.size(), up,
                             h->stream));
+  SOMA_CUDA(cudaMemcpyAsync(h->d_topo_ttab, T.ttab.data(), T.ttab.size(), up, h->stream));
   SOMA_CUDA(cudaMemcpyAsync(h->d_seq, T.seq.data(), sizeof(uint64_t) * n_arch, up, h->stream));
   SOMA_CUDA(cudaMemcpyAsync(h->d_arch, a.data(), a.size(), up, h->stream));
   soma_status s2 = sync(h);   // the host vectors are released on return
   if (s2 != SOMA_OK) return s2;
   h->topo_bonds = bonds;
+  h->topo_max_type = T.max_type;
   h->topo_grid = h->shape.molecule
                      ? molecule_topology_grid(h->g.N, h->grid_dtype, h->sm_count, h->g.n_chains)
                      : topology_grid(h->grid_dtype, h->shape.big, h->sm_count, h->shape.n_tiles);
   h->has_topo = true;
   if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
   return SOMA_OK;
+}
+
+soma_status soma_set_types(soma_t* h, uint32_t n_types, const double* chiN) {
+  if (!h) return fail(SOMA_EINVAL, "handle is NULL");
+  if (h->batched) return fail(SOMA_ESTATE, "a batch member has the two types A, B");
+  if (n_types == 0) {   // back to the packed A | B grid
+    if (h->topo_max_type > 1)
+      return fail(SOMA_ESTATE, "the architectures use type %u: set two-type architectures first",
+                  h->topo_max_type);
+    cudaFree(h->nt[0]);
+    cudaFree(h->nt[1]);
+    cudaFree(h->wt);
+    h->nt[0] = h->nt[1] = nullptr;
+    h->wt = nullptr;
+    h->n_types = 0;
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    const soma_status st = update_fields(h);
+    return st == SOMA_OK ? sync(h) : st;
+  }
+  if (n_types < 2 || n_types > (uint32_t)TYPES_MAX || !chiN)
+    return fail(SOMA_EINVAL, "n_types=%u outside 2..%d, or chiN is NULL", n_types, TYPES_MAX);
+  for (uint32_t i = 0; i < n_types; ++i)
+    for (uint32_t j = 0; j < n_types; ++j) {
+      const double a = chiN[i * n_types + j], b = chiN[j * n_types + i];
+      if (!std::isfinite(a) || a != b || (i == j && a != 0.0))
+        return fail(SOMA_EINVAL, "chiN must be finite and symmetric with a zero diagonal (%u, %u)",
+                    i, j);
+    }
+  if (h->grid_dtype != 0) return fail(SOMA_EINVAL, "n_t types take FP32 fields");
+  if (h->desc.move != SOMA_MOVE_UNIFORM) return fail(SOMA_EINVAL, "n_t types take uniform moves");
+  if (h->has_ext || h->has_forbidden) return fail(SOMA_EINVAL, "n_t types take no external fields");
+  if (h->has_topo && h->topo_max_type >= n_types)
+    return fail(SOMA_EINVAL, "the architectures use type %u >= n_types", h->topo_max_type);
+  if (!h->has_topo && h->d_seq)
+    return fail(SOMA_ESTATE, "a mixture of linear architectures has the two types A, B");
+  const size_t bytes = sizeof(uint32_t) * n_types * h->g.cells;
+  cudaFree(h->nt[0]);
+  cudaFree(h->nt[1]);
+  cudaFree(h->wt);
+  h->nt[0] = h->nt[1] = nullptr;
+  h->wt = nullptr;
+  h->n_types = 0;
+  cudaError_t e = cudaMalloc((void**)&h->nt[0], bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->nt[1], bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->wt, sizeof(float) * n_types * h->g.cells);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->nt[0], 0, bytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->nt[1], 0, bytes, h->stream);
+  if (e != cudaSuccess) {
+    cudaFree(h->nt[0]);
+    cudaFree(h->nt[1]);
+    cudaFree(h->wt);
+    h->nt[0] = h->nt[1] = nullptr;
+    h->wt = nullptr;
+    return cuda_fail(e, "type planes");
+  }
+  for (int k = 0; k < TYPES_MAX * TYPES_MAX; ++k) h->chiN_types[k] = 0.0;
+  for (uint32_t i = 0; i < n_types; ++i)
+    for (uint32_t j = 0; j < n_types; ++j) h->chiN_types[i * TYPES_MAX + j] = chiN[i * n_types + j];
+  h->n_types = n_types;
+  if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+  if (h->has_topo) {   // the counts and fields of the current configuration
+    soma_status st = update_fields(h);
+    if (st != SOMA_OK) return st;
+  }
+  return sync(h);
+}
+
+soma_status soma_get_type_counts(soma_t* h, uint32_t* dst, size_t n, int dst_on_device) {
+  if (!h || !dst) return fail(SOMA_EINVAL, "NULL argument");
+  if (!h->n_types) return fail(SOMA_EINVAL, "no n_t types set: use soma_get_density");
+  if (n != (size_t)h->n_types * h->g.cells)
+    return fail(SOMA_EINVAL, "n=%zu, expected n_types*cells=%zu", n, (size_t)h->n_types * h->g.cells);
+  SOMA_CUDA(cudaMemcpyAsync(dst, h->nt[h->host_sweep & 1], sizeof(uint32_t) * n,
+                            dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            h->stream));
+  return sync(h);
+}
+
+soma_status soma_get_type_fields(soma_t* h, float* dst, size_t n, int dst_on_device) {
+  if (!h || !dst) return fail(SOMA_EINVAL, "NULL argument");
+  if (!h->n_types) return fail(SOMA_EINVAL, "no n_t types set: use soma_get_fields");
+  if (n != (size_t)h->n_types * h->g.cells)
+    return fail(SOMA_EINVAL, "n=%zu, expected n_types*cells=%zu", n, (size_t)h->n_types * h->g.cells);
+  SOMA_CUDA(cudaMemcpyAsync(dst, h->wt, sizeof(float) * n,
+                            dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            h->stream));
+  return sync(h);
 }
 
 soma_status soma_sort_molecules(soma_t* h, uint64_t* perm) {
@@ -790,7 +945,7 @@ soma_status soma_topology_sets(const uint32_t* words, uint64_t n_words, const ui
   if (n_arch < 1 || n_arch > 256 || n_words < 2 || n_words > (1ull << 24) || N < 1)
     return fail(SOMA_EINVAL, "need 1..256 architectures in 2..2^24 words and N >= 1");
   TopologyTables T;
-  const std::string why = topology_tables(words, n_words, start, n_arch, N, &T);
+  const std::string why = topology_tables(words, n_words, start, n_arch, N, &T, TYPES_MAX);
   if (!why.empty()) return fail(SOMA_EINVAL, "%s", why.c_str());
   for (uint32_t a = 0; a < n_arch; ++a) {
     n_sets[a] = T.nsets[a];
@@ -844,6 +999,11 @@ soma_status soma_observables(soma_t* h, soma_obs* out) {
                                     h->d_scratch, h->d_out, h->stream));
     h->launches += 2;
   }
+  if (h->n_types) {    // the non-bonded energy and largest count of the type planes
+    SOMA_CUDA(launch_observables_types(types_args(h, 0), h->desc.kappaN, h->nt[h->host_sweep & 1],
+                                       h->d_scratch, h->d_out, h->stream));
+    h->launches += 2;
+  }
   double r[5];
   unsigned long long c[2];
   SOMA_CUDA(cudaMemcpyAsync(r, h->d_out, sizeof r, cudaMemcpyDeviceToHost, h->stream));
@@ -869,6 +1029,7 @@ soma_status soma_observables(soma_t* h, soma_obs* out) {
 
 soma_status soma_structure_factor(soma_t* h, const int32_t* m, size_t k, double* out) {
   if (!h || !m || !out) return fail(SOMA_EINVAL, "NULL argument");
+  if (h->n_types) return fail(SOMA_EINVAL, "S(q) of the A-B composition takes the two types A, B");
   if (k > 4096) return fail(SOMA_EINVAL, "k=%zu > 4096", k);
   if (k == 0) return SOMA_OK;
   const int nx = h->g.nx, ny = h->g.ny, nz = h->g.nz;
@@ -924,7 +1085,11 @@ soma_status soma_set_sweep(soma_t* h, uint64_t sweep) {
   SOMA_CUDA(cudaStreamSynchronize(h->stream));
   h->host_sweep = sweep;
   // the occupation buffer in use depends on the counter's parity
-  SOMA_CUDA(cudaMemsetAsync(h->n[(sweep + 1) & 1], 0, sizeof(uint32_t) * h->g.cells, h->stream));
+  if (h->n_types)
+    SOMA_CUDA(cudaMemsetAsync(h->nt[(sweep + 1) & 1], 0,
+                              sizeof(uint32_t) * h->n_types * h->g.cells, h->stream));
+  else
+    SOMA_CUDA(cudaMemsetAsync(h->n[(sweep + 1) & 1], 0, sizeof(uint32_t) * h->g.cells, h->stream));
   return update_fields(h);
 }
 

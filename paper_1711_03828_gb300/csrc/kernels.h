@@ -106,10 +106,18 @@ struct TopoArgs {
   const uint64_t* pmask;     // partners of particle i of architecture a: [a*64 + i]
   const uint32_t* ptab;      // [a*64 + i]: degree, first three partners, type, set, sets
   const uint8_t* mol_arch;   // architecture of every molecule
+  // n_t types: type of particle i of architecture a ([a*64 + i]), the field
+  // planes (n_types * cells) and the count planes of both parities
+  const uint8_t* ttab;
+  const float* wt;
+  uint32_t* nt0;
+  uint32_t* nt1;
 };
 struct TopologyTables {
   std::vector<uint64_t> pmask;   // n_arch * 64
   std::vector<uint32_t> ptab;    // n_arch * 64
+  std::vector<uint8_t> ttab;     // n_arch * 64, type of each particle
+  uint32_t max_type = 0;
   std::vector<uint8_t> nsets;    // n_arch
   std::vector<uint64_t> seq;     // type bits (bit i: particle i is B)
   std::vector<uint32_t> bonds;   // bonds per architecture
@@ -117,19 +125,48 @@ struct TopologyTables {
 // Checks an architecture array against a system of N particles per molecule
 // and derives the tables; returns an empty string or what is wrong.
 std::string topology_tables(const uint32_t* words, uint64_t n_words, const uint32_t* start,
-                            uint32_t n_arch, uint32_t N, TopologyTables* out);
+                            uint32_t n_arch, uint32_t N, TopologyTables* out,
+                            uint32_t n_types = 2);
 int topology_grid(int grid_dtype, bool big, int sm_count, uint64_t n_tiles);
 cudaError_t launch_sweep_topology(const TopoArgs& a, int grid, int grid_dtype, bool big,
-                                  cudaStream_t st);
+                                  cudaStream_t st, bool types = false);
 // the molecule-parallel iteration for molecules of any architecture (N <= 64);
 // the grid helper also allows the kernel its shared memory (call it before
 // the first launch, outside stream capture)
 int molecule_topology_grid(uint32_t N, int grid_dtype, int sm_count, uint64_t n_chains);
-cudaError_t launch_molecule_topology(const TopoArgs& a, int grid, int grid_dtype, cudaStream_t st);
+cudaError_t launch_molecule_topology(const TopoArgs& a, int grid, int grid_dtype, cudaStream_t st,
+                                     bool types = false);
 // out[0] = sum over the bonds of the architectures of |b|^2 (FP64); part: OBS_BLOCKS doubles
 cudaError_t launch_topology_bonds(const Geom& g, const float* x, const float* y, const float* z,
                                   const uint64_t* pmask, const uint8_t* mol_arch, double* part,
                                   double* out, cudaStream_t st);
+
+// n_t particle types (types.cu).
+constexpr int TYPES_MAX = 8;
+struct TypesArgs {
+  Geom g;
+  uint32_t* n0;              // count planes, n_types * cells each; the sweep of step s
+  uint32_t* n1;              // counts into planes (s+1)&1
+  float* w;                  // field planes, n_types * cells
+  unsigned long long* d_sweep;
+  uint32_t n_types;
+  int after_sweep;           // as FieldArgs
+  int hamiltonian;           // 0: K^0_inter, 1: K^1_inter
+  float inv_rho;             // 1/(rho_0 dL^3)
+  float kappa0;              // kappaN/N
+  double inv_rho_f64;
+  float chi0[TYPES_MAX * TYPES_MAX];    // chi_ij N / N
+  double chiN[TYPES_MAX * TYPES_MAX];   // chi_ij N
+};
+cudaError_t launch_fields_types(const TypesArgs& a, unsigned* arrive, int sm_count,
+                                cudaStream_t st);
+cudaError_t launch_histogram_types(const Geom& g, const float* x, const float* y, const float* z,
+                                   const uint8_t* ttab, const uint8_t* mol_arch, uint32_t* n,
+                                   int sm_count, cudaStream_t st);
+// out[2] = sum over cells of the energy per cell, out[3] = largest total count,
+// out[4] = 0 (no external potential); part: 2 * OBS_BLOCKS doubles
+cudaError_t launch_observables_types(const TypesArgs& a, double kappaN, const uint32_t* n,
+                                     double* part, double* out, cudaStream_t st);
 
 // Entry-point helpers implemented in api.cu (messages go to soma_last_error).
 }  // namespace soma

@@ -25,14 +25,17 @@ __device__ __forceinline__ uint32_t mol_partner(uint32_t w, int k) { return (w >
 
 // TOPO: molecules of any architecture (t holds the tables); else linear chains
 // (the diblock, or a mixture through p.seq / p.arch).
-template <typename WT, bool STAGE, bool TOPO>
+// MULTI (with TOPO): n_t particle types, the type from the type table, one
+// FP32 field plane and one count plane per type.
+template <typename WT, bool STAGE, bool TOPO, bool MULTI = false>
 __device__ __forceinline__ void molecule_body(const SweepArgs& p, const TopoArgs& tp) {
   extern __shared__ float sm[];
   const uint32_t N = p.g.N, N_A = p.g.N_A;
   const uint32_t t = threadIdx.x;
   const unsigned long long s64 = *p.d_sweep;
   const uint32_t sweep = (uint32_t)s64;
-  uint32_t* __restrict__ nacc = ((s64 + 1ull) & 1ull) ? p.n1 : p.n0;
+  uint32_t* __restrict__ nacc = MULTI ? (((s64 + 1ull) & 1ull) ? tp.nt1 : tp.nt0)
+                                      : (((s64 + 1ull) & 1ull) ? p.n1 : p.n0);
   const uint32_t ctr3 = (PURPOSE_ATTEMPT << 24) | (p.g.replica & 0xFFFFFFu);
   const WT* __restrict__ wA = static_cast<const WT*>(p.wA);
   const WT* __restrict__ wB = static_cast<const WT*>(p.wB);
@@ -72,10 +75,17 @@ __device__ __forceinline__ void molecule_body(const SweepArgs& p, const TopoArgs
         const float xn = __fadd_rn(xo, __fmul_rn(a, uniform_sym(r.x)));
         const float yn = __fadd_rn(yo, __fmul_rn(a, uniform_sym(r.y)));
         const float zn = __fadd_rn(zo, __fmul_rn(a, uniform_sym(r.z)));
-        const bool isB = TOPO ? ((__ldg(tab + i) >> 24) & 1u) != 0
-                              : (p.seq ? ((seq >> i) & 1ull) != 0 : i >= N_A);
-        const WT* w = isB ? wB : wA;
-        const float dEf = load_w<WT>(w, cell_of(p.g, xn, yn, zn)) - load_w<WT>(w, cell_of(p.g, xo, yo, zo));
+        float dEf;
+        if (MULTI) {
+          const uint32_t ty = __ldg(tp.ttab + (uint32_t)__ldg(tp.mol_arch + chain) * 64u + i);
+          const float* w = tp.wt + (size_t)ty * p.g.cells;
+          dEf = __ldg(w + cell_of(p.g, xn, yn, zn)) - __ldg(w + cell_of(p.g, xo, yo, zo));
+        } else {
+          const bool isB = TOPO ? ((__ldg(tab + i) >> 24) & 1u) != 0
+                                : (p.seq ? ((seq >> i) & 1ull) != 0 : i >= N_A);
+          const WT* w = isB ? wB : wA;
+          dEf = load_w<WT>(w, cell_of(p.g, xn, yn, zn)) - load_w<WT>(w, cell_of(p.g, xo, yo, zo));
+        }
         // U = sum over bonded partners of (r - n), k partners
         float ux = 0.f, uy = 0.f, uz = 0.f, k = 0.f;
         if (TOPO) {
@@ -133,14 +143,19 @@ __device__ __forceinline__ void molecule_body(const SweepArgs& p, const TopoArgs
       } else {
         x = p.x[m0 + q]; y = p.y[m0 + q]; z = p.z[m0 + q];
       }
-      bool isB;
-      if (TOPO)
-        isB = ((__ldg(tp.ptab + (uint32_t)__ldg(tp.mol_arch + chain0 + q / N) * 64u + ci) >> 24) &
-               1u) != 0;
-      else
-        isB = p.seq ? ((__ldg(p.seq + __ldg(p.arch + chain0 + q / N)) >> ci) & 1ull) != 0
-                    : ci >= N_A;
-      atomicAdd(nacc + cell_of(p.g, x, y, z), isB ? 0x10000u : 1u);
+      if (MULTI) {
+        const uint32_t ty = __ldg(tp.ttab + (uint32_t)__ldg(tp.mol_arch + chain0 + q / N) * 64u + ci);
+        atomicAdd(nacc + (size_t)ty * p.g.cells + cell_of(p.g, x, y, z), 1u);
+      } else {
+        bool isB;
+        if (TOPO)
+          isB = ((__ldg(tp.ptab + (uint32_t)__ldg(tp.mol_arch + chain0 + q / N) * 64u + ci) >> 24) &
+                 1u) != 0;
+        else
+          isB = p.seq ? ((__ldg(p.seq + __ldg(p.arch + chain0 + q / N)) >> ci) & 1ull) != 0
+                      : ci >= N_A;
+        atomicAdd(nacc + cell_of(p.g, x, y, z), isB ? 0x10000u : 1u);
+      }
       ci += step;
       if (ci >= N) ci -= N;
     }
@@ -156,23 +171,28 @@ __global__ void __launch_bounds__(MOL_BLOCK) sweep_molecule_kernel(const SweepAr
   molecule_body<WT, STAGE, false>(p, TopoArgs{});
 }
 
-template <typename WT>
+template <typename WT, bool MULTI>
 __global__ void __launch_bounds__(MOL_BLOCK) sweep_molecule_topology_kernel(const TopoArgs t) {
-  molecule_body<WT, true, true>(t.s, t);
+  molecule_body<WT, true, true, MULTI>(t.s, t);
 }
 
-static const void* molecule_topology_ptr(int grid_dtype) {
+static const void* molecule_topology_ptr(int grid_dtype, bool types = false) {
+  if (types) return (const void*)sweep_molecule_topology_kernel<float, true>;   // FP32 fields
   switch (grid_dtype) {
-    case 1: return (const void*)sweep_molecule_topology_kernel<__nv_bfloat16>;
-    case 2: return (const void*)sweep_molecule_topology_kernel<__half>;
-    default: return (const void*)sweep_molecule_topology_kernel<float>;
+    case 1: return (const void*)sweep_molecule_topology_kernel<__nv_bfloat16, false>;
+    case 2: return (const void*)sweep_molecule_topology_kernel<__half, false>;
+    default: return (const void*)sweep_molecule_topology_kernel<float, false>;
   }
 }
 
 int molecule_topology_grid(uint32_t N, int grid_dtype, int sm_count, uint64_t n_chains) {
   const void* fn = molecule_topology_ptr(grid_dtype);
   const size_t smem = (size_t)3 * MOL_BLOCK * N * sizeof(float);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 48 * 1024) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(molecule_topology_ptr(0, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  }
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, MOL_BLOCK, smem);
   if (per_sm < 1) per_sm = 1;
@@ -181,11 +201,12 @@ int molecule_topology_grid(uint32_t N, int grid_dtype, int sm_count, uint64_t n_
   return (int)(need < cap ? need : cap);
 }
 
-cudaError_t launch_molecule_topology(const TopoArgs& a, int grid, int grid_dtype, cudaStream_t st) {
+cudaError_t launch_molecule_topology(const TopoArgs& a, int grid, int grid_dtype, cudaStream_t st,
+                                     bool types) {
   void* args[] = {const_cast<TopoArgs*>(&a)};
   const size_t smem = (size_t)3 * MOL_BLOCK * a.s.g.N * sizeof(float);
-  return cudaLaunchKernel(molecule_topology_ptr(grid_dtype), dim3(grid), dim3(MOL_BLOCK), args,
-                          smem, st);
+  return cudaLaunchKernel(molecule_topology_ptr(grid_dtype, types), dim3(grid), dim3(MOL_BLOCK),
+                          args, smem, st);
 }
 
 template <bool STAGE>

@@ -103,7 +103,9 @@ struct TopoTile {
 };
 
 // IDX: particle index type (32-bit when M < 2^32: Philox counter word 1 = 0).
-template <typename WT, typename IDX>
+// MULTI: n_t particle types (type table, one field and one count plane per
+// type; FP32 fields); else the two types A, B of the packed grid.
+template <typename WT, typename IDX, bool MULTI>
 __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t) {
   __shared__ TopoTile tiles[TOPO_WARPS];
   const SweepArgs& p = t.s;
@@ -114,7 +116,8 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
   const IDX n_mol = (IDX)p.g.n_chains;
   const unsigned long long s64 = *p.d_sweep;
   const uint32_t sweep = (uint32_t)s64;
-  uint32_t* __restrict__ nacc = ((s64 + 1ull) & 1ull) ? p.n1 : p.n0;
+  uint32_t* __restrict__ nacc = MULTI ? (((s64 + 1ull) & 1ull) ? t.nt1 : t.nt0)
+                                      : (((s64 + 1ull) & 1ull) ? p.n1 : p.n0);
   const WT* __restrict__ wA = static_cast<const WT*>(p.wA);
   const WT* __restrict__ wB = static_cast<const WT*>(p.wB);
   const uint32_t N = p.g.N, G = p.G;
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
 
     // Draws, trial positions, cells and field changes of the natural slots,
     // recorded in the tile record.
-    uint32_t own[2], step[2], n_steps = 0;
+    uint32_t own[2], step[2], ty[2], n_steps = 0;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const uint32_t tl = (uint32_t)lane + 32u * (uint32_t)j;
@@ -186,11 +189,21 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
       const float zn = __fadd_rn(z[j], __fmul_rn(p.a, uniform_sym(r.z)));
       const uint32_t co = cell_of(p.g, x[j], y[j], z[j]);
       const uint32_t cn = cell_of(p.g, xn, yn, zn);
-      const WT* wt = pw_is_B(pw) ? wB : wA;
-      const float dEf = valid ? load_w<WT>(wt, cn) - load_w<WT>(wt, co) : 0.f;
+      // type: the architecture's type byte (n_t types) or the A/B bit
+      const uint32_t type = MULTI ? (valid ? __ldg(t.ttab + a * TOPO_TILE + ci) : 0u)
+                                  : (uint32_t)pw_is_B(pw);
+      float dEf = 0.f;
+      if (MULTI) {
+        const float* wt = t.wt + (size_t)type * p.g.cells;
+        if (valid) dEf = __ldg(wt + cn) - __ldg(wt + co);
+      } else {
+        const WT* wt = type ? wB : wA;
+        if (valid) dEf = load_w<WT>(wt, cn) - load_w<WT>(wt, co);
+      }
       S.P[tl] = make_float4(x[j], y[j], z[j], __uint_as_float(co));
       S.T[tl] = make_float4(xn, yn, zn, -log_uniform_open(r.w) - dEf);
-      S.Q[tl] = make_uint4(pw, cn, (gc[j] & 0xFFu) * N | a << 8, 0u);
+      S.Q[tl] = make_uint4(pw, cn, (gc[j] & 0xFFu) * N | a << 8, type);
+      ty[j] = type;
       own[j] = (valid && ci == 0u)
                    ? set_steps(pw_sets(pw), random, r.w & 1u, (uint64_t)(chain0 + (gc[j] & 0xFFu)),
                                sweep, (PURPOSE_SETS << 24) | (p.g.replica & 0xFFFFFFu), p.g)
@@ -205,7 +218,7 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
       const uint32_t pw = step[j];
       const uint32_t ns = pw_sets(pw);             // 0 for an empty slot
       step[j] = (ns ? (((first >> 5) ? v1 : v0) >> (4u * pw_set(pw))) & 15u : 15u) |
-                (uint32_t)pw_is_B(pw) << 4;
+                ty[j] << 4;
       n_steps = max(n_steps, ns);
     }
     n_steps = __reduce_max_sync(FULL, n_steps);
@@ -270,7 +283,10 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
       __stcs(p.x + m, Pf.x);
       __stcs(p.y + m, Pf.y);
       __stcs(p.z + m, Pf.z);
-      atomicAdd(nacc + __float_as_uint(Pf.w), (step[j] >> 4) ? 0x10000u : 1u);
+      if (MULTI)
+        atomicAdd(nacc + (size_t)(step[j] >> 4) * p.g.cells + __float_as_uint(Pf.w), 1u);
+      else
+        atomicAdd(nacc + __float_as_uint(Pf.w), (step[j] >> 4) ? 0x10000u : 1u);
     }
     __syncwarp();
   }
@@ -279,18 +295,21 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
   if (lane == 0 && my_acc) atomicAdd(p.acc, (unsigned long long)my_acc);
 }
 
-const void* topology_kernel_ptr(int grid_dtype, bool big) {
+const void* topology_kernel_ptr(int grid_dtype, bool big, bool types) {
+  if (types)   // FP32 fields only
+    return big ? (const void*)sweep_topology_kernel<float, uint64_t, true>
+               : (const void*)sweep_topology_kernel<float, uint32_t, true>;
   if (big) {
     switch (grid_dtype) {
-      case 1: return (const void*)sweep_topology_kernel<__nv_bfloat16, uint64_t>;
-      case 2: return (const void*)sweep_topology_kernel<__half, uint64_t>;
-      default: return (const void*)sweep_topology_kernel<float, uint64_t>;
+      case 1: return (const void*)sweep_topology_kernel<__nv_bfloat16, uint64_t, false>;
+      case 2: return (const void*)sweep_topology_kernel<__half, uint64_t, false>;
+      default: return (const void*)sweep_topology_kernel<float, uint64_t, false>;
     }
   }
   switch (grid_dtype) {
-    case 1: return (const void*)sweep_topology_kernel<__nv_bfloat16, uint32_t>;
-    case 2: return (const void*)sweep_topology_kernel<__half, uint32_t>;
-    default: return (const void*)sweep_topology_kernel<float, uint32_t>;
+    case 1: return (const void*)sweep_topology_kernel<__nv_bfloat16, uint32_t, false>;
+    case 2: return (const void*)sweep_topology_kernel<__half, uint32_t, false>;
+    default: return (const void*)sweep_topology_kernel<float, uint32_t, false>;
   }
 }
 
@@ -337,11 +356,13 @@ __global__ void topology_bonds_final_kernel(const double* __restrict__ part, int
 }  // namespace
 
 std::string topology_tables(const uint32_t* w, uint64_t n_words, const uint32_t* start,
-                            uint32_t n_arch, uint32_t N, TopologyTables* T) {
+                            uint32_t n_arch, uint32_t N, TopologyTables* T, uint32_t n_types) {
   char msg[256];
   if (N > (uint32_t)TOPO_TILE) return "architectures take N <= 64";
   T->pmask.assign((size_t)n_arch * TOPO_TILE, 0);
   T->ptab.assign((size_t)n_arch * TOPO_TILE, 0);
+  T->ttab.assign((size_t)n_arch * TOPO_TILE, 0);
+  T->max_type = 0;
   T->nsets.assign(n_arch, 0);
   std::vector<uint8_t> set_of(TOPO_TILE);
   T->seq.assign(n_arch, 0);
@@ -361,11 +382,14 @@ std::string topology_tables(const uint32_t* w, uint64_t n_words, const uint32_t*
     for (uint32_t i = 0; i < N; ++i) {
       const uint32_t mw = w[s + 1u + i];
       const uint32_t type = mw & 0xFFu;
-      if (type > 1u) {
-        snprintf(msg, sizeof msg, "architecture %u particle %u: type %u (0 A, 1 B only)", a, i, type);
+      if (type >= n_types) {
+        snprintf(msg, sizeof msg, "architecture %u particle %u: type %u (the system has %u types)",
+                 a, i, type, n_types);
         return msg;
       }
-      if (type) T->seq[a] |= 1ull << i;
+      if (type == 1u) T->seq[a] |= 1ull << i;
+      T->ttab[(size_t)a * TOPO_TILE + i] = (uint8_t)type;
+      T->max_type = std::max(T->max_type, type);
       const uint32_t off = mw >> 8;
       if (off == TOPO_NO_BONDS) continue;
       for (uint64_t b = off;; ++b) {
@@ -433,7 +457,7 @@ std::string topology_tables(const uint32_t* w, uint64_t n_words, const uint32_t*
 
 int topology_grid(int grid_dtype, bool big, int sm_count, uint64_t n_tiles) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topology_kernel_ptr(grid_dtype, big),
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topology_kernel_ptr(grid_dtype, big, false),
                                                 TOPO_WARPS * 32, 0);
   if (per_sm < 1) per_sm = 1;
   const uint64_t need = (n_tiles + TOPO_WARPS - 1) / TOPO_WARPS;
@@ -442,10 +466,10 @@ int topology_grid(int grid_dtype, bool big, int sm_count, uint64_t n_tiles) {
 }
 
 cudaError_t launch_sweep_topology(const TopoArgs& a, int grid, int grid_dtype, bool big,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, bool types) {
   void* args[] = {const_cast<TopoArgs*>(&a)};
-  return cudaLaunchKernel(topology_kernel_ptr(grid_dtype, big), dim3(grid), dim3(TOPO_WARPS * 32),
-                          args, 0, st);
+  return cudaLaunchKernel(topology_kernel_ptr(grid_dtype, big, types), dim3(grid),
+                          dim3(TOPO_WARPS * 32), args, 0, st);
 }
 
 cudaError_t launch_topology_bonds(const Geom& g, const float* x, const float* y, const float* z,
