@@ -35,7 +35,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="melt_large",
                     choices=["melt_large", "melt_mid", "melt_small", "melt_slow", "melt_subbox",
-                             "melt_tiny", "arch_large", "arch_mid",
+                             "melt_tiny", "arch_large", "arch_mid", "abc_large",
                              "batch64", "decorrelation"])
     ap.add_argument("--move", default="uniform", choices=["uniform", "smc", "learned"],
                     help="trial moves: uniform displacement or smart Monte Carlo")
@@ -74,12 +74,18 @@ def workload(name, replica=0, grid_dtype="f32", move="uniform", learned_net="mma
     return d
 
 
-def setup_architectures(target, d, seed=1):
-    """Molecules of the four architectures of workloads.arch_large, one drawn
-    per molecule, on a library System or an oracle System (the same arrays)."""
+def setup_architectures(target, d, seed=1, name="arch_large"):
+    """Molecules of the architectures of workloads.arch_large (or, for
+    abc_large, the three-type molecules of workloads.abc_molecules with their
+    chi matrix), one drawn per molecule, on a library System or an oracle
+    System (the same arrays)."""
     import numpy as np
     from paper_1711_03828_gb300 import workloads
-    mols = workloads.arch_large_molecules()
+    if name.startswith("abc_"):
+        mols = workloads.abc_molecules()
+        target.set_types(3, workloads.ABC_CHI_N)
+    else:
+        mols = workloads.arch_large_molecules()
     words, starts = workloads.encode_architectures(mols)
     arch = np.random.default_rng(seed + 17).integers(0, len(mols), d.n_chains).astype(np.uint8)
     pos = workloads.architecture_positions(d, mols, arch, seed=seed + 29)
@@ -87,11 +93,19 @@ def setup_architectures(target, d, seed=1):
     return pos
 
 
+def uses_architectures(name):
+    return name.startswith("arch_") or name.startswith("abc_")
+
+
 def config_of(d, name, l2_note):
     extra = {}
     if name.startswith("arch_"):
         extra["architectures"] = ("three-arm star (11,10,10), comb (16 + 4x4), ring (32), "
                                   "linear diblock; one drawn per molecule")
+    if name.startswith("abc_"):
+        extra["architectures"] = ("three types A, B, C (chi N: AB 30, AC 15, BC 40): ABC "
+                                  "triblock, three-arm star with one arm per type, ABC ring; "
+                                  "one drawn per molecule")
     return {**extra,"workload": f"{name}: {d.n_chains} chains x N={d.N}, box {d.box_Re} R_e0, grid "
                         f"{d.grid}, chiN={d.chiN}, kappaN={d.kappaN}",
             "n_chains": d.n_chains, "N": d.N, "particles": d.M, "grid": list(d.grid),
@@ -115,19 +129,24 @@ def oracle_rate(name, seconds, max_steps=None):
     sub = workloads.scaled(d, (4.0, 4.0, 4.0))
     o = oracle.System(sub.n_chains, sub.N, sub.f, sub.box_Re, sub.grid, sub.chiN, sub.kappaN,
                       seed=sub.seed)
-    if name.startswith("arch_"):
-        pos = setup_architectures(o, sub)
+    if uses_architectures(name):
+        pos = setup_architectures(o, sub, name=name)
         p = oracle.Positions(pos[0].copy(), pos[1].copy(), pos[2].copy())
     else:
         p = o.init_chains()
-    nA, nB = o.histogram(p)
-    wA, wB = o.fields(nA, nB)
+    types = name.startswith("abc_")
+
+    def fields():
+        if types:
+            return None, None, o.fields_types(o.histogram_types(p))
+        return (*o.fields(*o.histogram(p)), None)
+
+    wA, wB, wT = fields()
     steps = 0
     t0 = time.perf_counter()
     while True:
-        o.sweep(p, wA, wB, steps)
-        nA, nB = o.histogram(p)
-        wA, wB = o.fields(nA, nB)
+        o.sweep(p, wA, wB, steps, w_types=wT)
+        wA, wB, wT = fields()
         steps += 1
         el = time.perf_counter() - t0
         if (max_steps is not None and steps >= max_steps) or (max_steps is None and el >= seconds):
@@ -281,17 +300,23 @@ def sweep_kernel_name(d, architectures=False):
     return "sweep_pair_kernel" if pair else "sweep_uniform_kernel"
 
 
-def sweep_kernel_bytes(d):
+def sweep_kernel_bytes(d, n_types=0):
     """Algorithmic bytes of one sweep-kernel launch: every position read and
     written once (24 B per particle), each omega plane read once and the
-    occupation grid written once (12 B per cell for FP32 omega)."""
+    occupation grid written once (12 B per cell for FP32 omega; with n_t
+    types one FP32 field plane and one 32-bit count plane per type)."""
     cells = d.grid[0] * d.grid[1] * d.grid[2]
+    if n_types:
+        return 24 * d.M + cells * 8 * n_types
     wb = 4 if d.grid_dtype == 0 else 2
     return 24 * d.M + cells * (2 * wb + 4)
 
 
-def field_kernel_bytes(d):
+def field_kernel_bytes(d, n_types=0):
+    """Counts read, the next sweep's counts cleared, fields written."""
     cells = d.grid[0] * d.grid[1] * d.grid[2]
+    if n_types:
+        return cells * 12 * n_types
     wb = 4 if d.grid_dtype == 0 else 2
     return cells * (4 + 4 + 2 * wb)
 
@@ -311,8 +336,8 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     s = System(d, stream=stream)
-    if args.workload.startswith("arch_"):
-        s.set_positions(setup_architectures(s, d))
+    if uses_architectures(args.workload):
+        s.set_positions(setup_architectures(s, d, name=args.workload))
         s.sort_molecules()   # the generator's molecules are in random spatial order
         s.update_fields()
     train_log = None
@@ -355,7 +380,8 @@ def run_ours(args):
     field_ms = tk["ms_fields"] / max(tk["field_launches"], 1)
     s.set_timing(False)
     peak, peak_kind = measured_peak_hbm()
-    achieved = sweep_kernel_bytes(d) / (sweep_ms * 1e-3) / 1e9
+    n_types = 3 if args.workload.startswith("abc_") else 0
+    achieved = sweep_kernel_bytes(d, n_types) / (sweep_ms * 1e-3) / 1e9
 
     # end to end through the C ABI with host buffers: every step copies the
     # positions in from pinned memory, runs one cycle and reads the occupation
@@ -363,7 +389,9 @@ def run_ours(args):
     host_pos = torch.empty(3 * d.M, dtype=torch.float32, pin_memory=True)
     import ctypes
     _abi.soma_get_positions(s.h, ctypes.c_void_p(host_pos.data_ptr()), 3 * d.M, 0)
-    host_n = torch.empty(d.cells, dtype=torch.int32, pin_memory=True)
+    n_words = d.cells * (n_types or 1)   # the packed A | B grid, or one plane per type
+    host_n = torch.empty(n_words, dtype=torch.int32, pin_memory=True)
+    read_counts = _abi.soma_get_type_counts if n_types else _abi.soma_get_density
     e2e_steps = max(1, min(args.e2e_steps, args.steps))
     barrier()
     torch.cuda.synchronize()
@@ -371,7 +399,7 @@ def run_ours(args):
     for _ in range(e2e_steps):
         _abi.soma_set_positions(s.h, ctypes.c_void_p(host_pos.data_ptr()), 3 * d.M, 0)
         _abi.soma_sweep(s.h, 1)
-        _abi.soma_get_density(s.h, ctypes.c_void_p(host_n.data_ptr()), d.cells, 0)
+        read_counts(s.h, ctypes.c_void_p(host_n.data_ptr()), n_words, 0)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     if world > 1:
@@ -379,7 +407,7 @@ def run_ours(args):
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e = {"value": d.M * e2e_steps * world / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": 12 * d.M, "d2h_bytes_per_step": 4 * d.cells,
+           "h2d_bytes_per_step": 12 * d.M, "d2h_bytes_per_step": 4 * n_words,
            "steps": e2e_steps}
     obs = s.observables()
     s.close()
@@ -398,13 +426,13 @@ def run_ours(args):
                             f"inputs L2-resident ({12 * d.M / 1e6:.2f} MB of positions): a "
                             "latency figure, not a bandwidth one"),
         "roofline": {"bound": "hbm",
-                     "kernel": sweep_kernel_name(d, args.workload.startswith("arch_")),
+                     "kernel": sweep_kernel_name(d, uses_architectures(args.workload)),
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": measured_traffic(args.workload)
                      if args.grid_dtype == "f32" and args.move == "uniform" else None,
-                     "bytes_per_launch": sweep_kernel_bytes(d), "ms_per_launch": sweep_ms,
+                     "bytes_per_launch": sweep_kernel_bytes(d, n_types), "ms_per_launch": sweep_ms,
                      "field_kernel_ms": field_ms,
-                     "field_kernel_gbs": field_kernel_bytes(d) / (field_ms * 1e-3) / 1e9},
+                     "field_kernel_gbs": field_kernel_bytes(d, n_types) / (field_ms * 1e-3) / 1e9},
         "e2e": e2e,
         "clocks": clk.out,
         "gpu_launches": int(launches),

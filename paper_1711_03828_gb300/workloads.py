@@ -290,6 +290,27 @@ def arch_mid(seed=1, **kw):
     return melt_mid(seed=seed, **kw)
 
 
+def abc_large(seed=1, **kw):
+    """The 134M-particle melt of melt_large with three particle types A, B, C
+    (chi_AB N = 30, chi_AC N = 15, chi_BC N = 40, kappaN = 50): molecules of
+    abc_molecules(), one drawn per molecule."""
+    return melt_large(seed=seed, **kw)
+
+
+ABC_CHI_N = [[0.0, 30.0, 15.0], [30.0, 0.0, 40.0], [15.0, 40.0, 0.0]]
+
+
+def abc_molecules():
+    """Three architectures of N = 32 with types 0 (A), 1 (B), 2 (C): a linear
+    ABC triblock (11, 11, 10), a three-arm star with one arm of each type
+    (arms 11, 10, 10; centre A) and a ring of A, B and C blocks (11, 11, 10)."""
+    tri = [0] * 11 + [1] * 11 + [2] * 10
+    star_types = [0] + [0] * 11 + [1] * 10 + [2] * 10
+    return [(tri, linear_architecture(32)[1]),
+            (star_types, star_architecture(3, [11, 10, 10])[1]),
+            (tri, ring_architecture(32)[1])]
+
+
 def arch_large_molecules():
     return [star_architecture(3, [11, 10, 10]), comb_architecture(16, 4, 4),
             ring_architecture(32), linear_architecture(32)]
