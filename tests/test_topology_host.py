@@ -57,6 +57,8 @@ def test_malformed_arrays_are_refused(soma_lib):
 
     bad = good.copy()
     bad[gst[0] + 4] = (int(bad[gst[0] + 4]) & 0xFFFFFF00) | 2
+    topology_sets(bad, gst, 9)                      # types 0..7: the sets take any of them
+    bad[gst[0] + 4] = (int(bad[gst[0] + 4]) & 0xFFFFFF00) | 8
     assert "type" in refused(bad, gst)
     bad = good.copy()
     bad[first] |= 1 << 1
