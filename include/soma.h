@@ -227,7 +227,8 @@ soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_ar
  *   words (n_words uint32): one block per architecture, starting at
  *     start[a] (n_arch = 1..256 entries): word 0 = N (the system's N, <= 64);
  *     word 1 + i = (index in words of particle i's first bond word << 8) |
- *     type (0 A, 1 B), index 0xFFFFFF for a particle without bonds; a bond
+ *     type (0 A, 1 B; 0..n_types-1 after soma_set_types), index 0xFFFFFF for
+ *     a particle without bonds; a bond
  *     word = (signed 27-bit offset j - i of the partner j << 5) | (bond type
  *     << 1) | last, where bond type 0 (harmonic, the system's spring) is the
  *     only one and the list of a particle ends at the word with last = 1.
@@ -248,8 +249,9 @@ soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_ar
  * (SOMA_ITERATION_MOLECULE: random particles, partners from the same
  * tables).  src_on_device: all three
  * arrays are device memory (else host).  SOMA_EINVAL, with the reason in
- * soma_last_error, for a block that does not fit the array, a type other than
- * 0/1, a bond type other than 0, a partner outside the molecule or listed
+ * soma_last_error, for a block that does not fit the array, a type outside
+ * 0/1 (0..n_types-1 with n_t types), a bond type other than 0, a partner
+ * outside the molecule or listed
  * twice, a bond listed at one end only, more than 8 sets, or a mol_arch entry
  * >= n_arch.  words = NULL returns to the diblock.  The handle keeps its own
  * copies.  Synchronises. */
