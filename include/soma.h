@@ -271,12 +271,20 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
  * architecture path (SET or molecule-parallel, uniform moves, FP32 fields, no
  * external fields); the occupation numbers become one 32-bit plane per type.
  * soma_get_density, soma_get_fields and soma_structure_factor then refuse
- * (SOMA_EINVAL): use soma_get_type_counts / soma_get_type_fields.  Recomputes
+ * (SOMA_EINVAL): use soma_get_type_counts / soma_get_type_fields /
+ * soma_structure_factor_types.  Recomputes
  * counts and fields when architectures are set.  n_types = 0 returns to the
  * two types A, B (SOMA_ESTATE while the architectures use a type >= 2).
  * SOMA_EINVAL for a bad n_types or chiN or an incompatible description.
  * Synchronises. */
 soma_status soma_set_types(soma_t* h, uint32_t n_types, const double* chiN);
+/* Composition structure factor of types ti and tj (Sec. 5.6 for A, B):
+ * S_ij(q) = |sum_c (n_ti(c) - n_tj(c)) exp(-i q.c)|^2 / M on grid wave vectors
+ * q = 2 pi m / n (m: k x 3 int32, k <= 4096); with the two types A, B it is
+ * soma_structure_factor.  SOMA_EINVAL for equal or out-of-range types;
+ * SOMA_EOVERFLOW if a count exceeds 65535.  Synchronises. */
+soma_status soma_structure_factor_types(soma_t* h, uint32_t ti, uint32_t tj, const int32_t* m,
+                                        size_t k, double* out);
 /* Occupation numbers per type, n[t*cells + c] (n = n_types*cells), and the
  * FP32 fields per type, w[t*cells + c], of the current state.  Synchronise. */
 soma_status soma_get_type_counts(soma_t* h, uint32_t* dst, size_t n, int dst_on_device);

@@ -224,6 +224,15 @@ class System:
         _abi.soma_set_types(self.h, int(n_types), c.ctypes.data)
         self.n_types = int(n_types)
 
+    def structure_factor_types(self, ti, tj, m):
+        """S_ij(q) of the composition n_ti - n_tj for wave-vector indices m
+        (k x 3)."""
+        mm = np.ascontiguousarray(np.asarray(m, dtype=np.int32).reshape(-1, 3))
+        out = np.zeros(len(mm), np.float64)
+        _abi.soma_structure_factor_types(self.h, int(ti), int(tj), mm.ctypes.data, len(mm),
+                                         out.ctypes.data)
+        return out
+
     def get_type_counts(self):
         """Occupation numbers per type, (n_types, cells) uint32."""
         out = np.empty((self.n_types, self.desc.cells), np.uint32)

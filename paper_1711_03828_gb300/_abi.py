@@ -118,6 +118,7 @@ _SIGS = {
     "soma_topology_sets": ([_P, _c.c_uint64, _P, _c.c_uint32, _c.c_uint32, _P, _P], _c.c_int),
     "soma_sort_molecules": ([_P, _P], _c.c_int),
     "soma_set_types": ([_P, _c.c_uint32, _P], _c.c_int),
+    "soma_structure_factor_types": ([_P, _c.c_uint32, _c.c_uint32, _P, _c.c_size_t, _P], _c.c_int),
     "soma_get_type_counts": ([_P, _P, _c.c_size_t, _c.c_int], _c.c_int),
     "soma_get_type_fields": ([_P, _P, _c.c_size_t, _c.c_int], _c.c_int),
     "soma_get_parameters": ([_P, _P], _c.c_int),
@@ -197,6 +198,7 @@ soma_set_topology = _wrap("soma_set_topology")
 soma_topology_sets = _wrap("soma_topology_sets")
 soma_sort_molecules = _wrap("soma_sort_molecules")
 soma_set_types = _wrap("soma_set_types")
+soma_structure_factor_types = _wrap("soma_structure_factor_types")
 soma_get_type_counts = _wrap("soma_get_type_counts")
 soma_get_type_fields = _wrap("soma_get_type_fields")
 soma_get_parameters = _wrap("soma_get_parameters")

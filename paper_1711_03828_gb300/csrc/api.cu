@@ -1027,11 +1027,48 @@ soma_status soma_observables(soma_t* h, soma_obs* out) {
   return SOMA_OK;
 }
 
+namespace {
+// S(q) of the composition held in a packed grid (first type in bits 0-15,
+// second in 16-31).
+soma_status structure_factor_of(soma_t* h, const uint32_t* nn, const int32_t* m, size_t k,
+                                double* out);
+}  // namespace
+
 soma_status soma_structure_factor(soma_t* h, const int32_t* m, size_t k, double* out) {
   if (!h || !m || !out) return fail(SOMA_EINVAL, "NULL argument");
-  if (h->n_types) return fail(SOMA_EINVAL, "S(q) of the A-B composition takes the two types A, B");
+  if (h->n_types) return fail(SOMA_EINVAL, "n_t types: use soma_structure_factor_types");
   if (k > 4096) return fail(SOMA_EINVAL, "k=%zu > 4096", k);
   if (k == 0) return SOMA_OK;
+  return structure_factor_of(h, h->n[h->host_sweep & 1], m, k, out);
+}
+
+soma_status soma_structure_factor_types(soma_t* h, uint32_t ti, uint32_t tj, const int32_t* m,
+                                        size_t k, double* out) {
+  if (!h || !m || !out) return fail(SOMA_EINVAL, "NULL argument");
+  const uint32_t T = h->n_types ? h->n_types : 2u;
+  if (ti >= T || tj >= T || ti == tj)
+    return fail(SOMA_EINVAL, "types %u, %u: need two different types below %u", ti, tj, T);
+  if (k > 4096) return fail(SOMA_EINVAL, "k=%zu > 4096", k);
+  if (k == 0) return SOMA_OK;
+  // two types: the packed A | B grid (S of B - A equals S of A - B)
+  if (!h->n_types) return structure_factor_of(h, h->n[h->host_sweep & 1], m, k, out);
+  uint32_t* packed = nullptr;
+  SOMA_CUDA(cudaMallocAsync((void**)&packed, sizeof(uint32_t) * h->g.cells, h->stream));
+  cudaError_t e = launch_pack_type_pair(h->nt[h->host_sweep & 1], h->g.cells, ti, tj, packed,
+                                        h->d_err, h->sm_count, h->stream);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(packed, h->stream);
+    return cuda_fail(e, "pack type pair");
+  }
+  soma_status st = structure_factor_of(h, packed, m, k, out);
+  cudaFreeAsync(packed, h->stream);
+  if (st != SOMA_OK) return st;
+  return sync(h);
+}
+
+namespace {
+soma_status structure_factor_of(soma_t* h, const uint32_t* nn, const int32_t* m, size_t k,
+                                double* out) {
   const int nx = h->g.nx, ny = h->g.ny, nz = h->g.nz;
   const size_t T = (size_t)nx + ny + nz;
   const size_t need = (size_t)SQ_MAX * T * 2;
@@ -1042,7 +1079,6 @@ soma_status soma_structure_factor(soma_t* h, const int32_t* m, size_t k, double*
     h->tw_doubles = need;
   }
   std::vector<double> tw(need);
-  const uint32_t* nn = h->n[h->host_sweep & 1];
   const double two_pi = 6.283185307179586;
   for (size_t q0 = 0; q0 < k; q0 += SQ_MAX) {
     const int kk = (int)((k - q0) < (size_t)SQ_MAX ? (k - q0) : (size_t)SQ_MAX);
@@ -1071,6 +1107,7 @@ soma_status soma_structure_factor(soma_t* h, const int32_t* m, size_t k, double*
   }
   return SOMA_OK;
 }
+}  // namespace
 
 soma_status soma_get_sweep(soma_t* h, uint64_t* out) {
   if (!h || !out) return fail(SOMA_EINVAL, "NULL argument");

@@ -163,6 +163,9 @@ cudaError_t launch_fields_types(const TypesArgs& a, unsigned* arrive, int sm_cou
 cudaError_t launch_histogram_types(const Geom& g, const float* x, const float* y, const float* z,
                                    const uint8_t* ttab, const uint8_t* mol_arch, uint32_t* n,
                                    int sm_count, cudaStream_t st);
+// n_i | n_j << 16 per cell from the type planes n (for the composition S(q))
+cudaError_t launch_pack_type_pair(const uint32_t* n, uint32_t cells, uint32_t ti, uint32_t tj,
+                                  uint32_t* out, unsigned* err, int sm_count, cudaStream_t st);
 // out[2] = sum over cells of the energy per cell, out[3] = largest total count,
 // out[4] = 0 (no external potential); part: 2 * OBS_BLOCKS doubles
 cudaError_t launch_observables_types(const TypesArgs& a, double kappaN, const uint32_t* n,

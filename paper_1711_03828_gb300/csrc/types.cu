@@ -145,7 +145,32 @@ __global__ void obs_types_final_kernel(const double* __restrict__ part, int nb,
   out[4] = 0.0;
 }
 
+// Packs the counts of types i and j into one grid, n_i | n_j << 16, for the
+// composition structure factor; a count that does not fit 16 bits sets the
+// overflow bit of the error word.
+__global__ void __launch_bounds__(256) pack_pair_kernel(const uint32_t* __restrict__ n,
+                                                        uint32_t cells, uint32_t ti, uint32_t tj,
+                                                        uint32_t* __restrict__ out,
+                                                        unsigned* __restrict__ err) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += stride) {
+    const uint32_t a = n[(size_t)ti * cells + c], b = n[(size_t)tj * cells + c];
+    if ((a | b) >> 16) atomicOr(err, ERR_OVERFLOW);
+    out[c] = (a & 0xFFFFu) | (b << 16);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_pack_type_pair(const uint32_t* n, uint32_t cells, uint32_t ti, uint32_t tj,
+                                  uint32_t* out, unsigned* err, int sm_count, cudaStream_t st) {
+  uint64_t blocks = ((uint64_t)cells + 255) / 256;
+  const uint64_t cap = (uint64_t)sm_count * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  pack_pair_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, cells, ti, tj, out, err);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_fields_types(const TypesArgs& a, unsigned* arrive, int sm_count,
                                 cudaStream_t st) {

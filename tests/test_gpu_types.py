@@ -164,3 +164,25 @@ def test_types_arguments_are_checked(cuda_device):
                           grid_dtype=GRID_BF16))
     refused(_abi.SOMA_EINVAL, s.set_types, 3, CHI3)
     s.close()
+
+
+def test_type_structure_factors_match_oracle(cuda_device):
+    """S_ij(q) of the composition n_i - n_j for each pair of three types, and
+    the two-type case through the packed grid, against the oracle's DFT."""
+    m = [(1, 0, 0), (0, 1, 0), (1, 1, 0), (2, 0, 1), (0, 0, 3), (-1, 2, 1)]
+    d, gpu, orc, p = _setup(3, CHI3, 0, n_chains=1024)
+    gpu.sweep(5)
+    n = gpu.get_type_counts()
+    for i, j in ((0, 1), (1, 2), (0, 2), (2, 0)):
+        got = gpu.structure_factor_types(i, j, m)
+        want = orc.structure_factor(n[i], n[j], m)
+        np.testing.assert_allclose(got, want, rtol=1e-9, atol=1e-9)
+    gpu.close()
+    s = System(SystemDesc(n_chains=1024, N=16, box_Re=(2.0, 2.0, 2.0), grid=(12, 12, 12)))
+    s.sweep(3)
+    ab = s.structure_factor(m)
+    np.testing.assert_array_equal(s.structure_factor_types(0, 1, m), ab)
+    np.testing.assert_array_equal(s.structure_factor_types(1, 0, m), ab)
+    with pytest.raises(SomaError):
+        s.structure_factor_types(0, 0, m)
+    s.close()
