@@ -21,6 +21,9 @@ Functions and the paper passage each follows:
 * ``System.set_topology``       -- molecular architectures in the array layout of
   Sec. 3.2.1 with independent sets (Sec. 3.1.2); ``topology_sets``,
   ``topo_partners``, ``topo_type``, ``System.set_order`` expose the steps.
+* ``System.set_types``          -- n_t particle types (Sec. 2.1): ``histogram_types``,
+  ``fields_types`` (Eq. omega-fields for n_t types), ``energy_types`` (Eq.
+  discrete-ham with Eq. hamil-pair), ``observables_types``.
 """
 from __future__ import annotations
 
