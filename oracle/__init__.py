@@ -24,6 +24,11 @@ Functions and the paper passage each follows:
 * ``System.set_types``          -- n_t particle types (Sec. 2.1): ``histogram_types``,
   ``fields_types`` (Eq. omega-fields for n_t types), ``energy_types`` (Eq.
   discrete-ham with Eq. hamil-pair), ``observables_types``.
+* ``mlp_forward`` / ``System.set_mlp`` -- the learned proposal's network (no
+  counterpart in the paper) in FP64, or with ``bf16=True`` in the BF16 reading
+  of the tensor-core evaluators (``mlp_forward_bf16``; ``bf16_slack`` and
+  ``System.sweep(want_slack=True)`` measure how near each rounding lies to a
+  BF16 rounding boundary).
 """
 from __future__ import annotations
 
@@ -58,6 +63,25 @@ def mlp_forward(W, x, L=None):
     return out
 
 
+def mlp_forward_bf16(W, x, Tx=None, L=None):
+    """Network outputs in the BF16 reading (inputs, weights, biases and hidden
+    activations rounded to BF16, sums exact) and the smallest slack of its
+    roundings (inf when Tx is None: only the activations count then)."""
+    Wd = np.ascontiguousarray(W, dtype=np.float64)
+    xd = np.ascontiguousarray(x, dtype=np.float64)
+    T = None if Tx is None else np.ascontiguousarray(Tx, dtype=np.float64)
+    out = np.zeros(4)
+    sl = np.full(1, np.inf)
+    (L or lib()).or_mlp_forward_bf16(_ptr(Wd, f64p), _ptr(xd, f64p), _ptr(T, f64p),
+                                     _ptr(out, f64p), _ptr(sl, f64p))
+    return out, float(sl[0])
+
+
+def bf16_slack(v, T, L=None):
+    """Distance of v from its nearest BF16 rounding boundary, in units of T."""
+    return float((L or lib()).or_bf16_slack(float(v), float(T)))
+
+
 class OrSystem(ctypes.Structure):
     _fields_ = [
         ("n_chains", ctypes.c_uint64),
@@ -90,6 +114,8 @@ class OrSystem(ctypes.Structure):
         ("n_types", ctypes.c_uint32),
         ("chi_types", ctypes.c_double * 64),
         ("w_types", ctypes.c_void_p),
+        ("mlp_bf16", ctypes.c_int),
+        ("mlp_slack", ctypes.c_void_p),
     ]
 
 
@@ -144,6 +170,9 @@ def load(path):
     L.or_num_threads.restype = ctypes.c_int
     L.or_mlp_forward.argtypes = [f64p, f64p, f64p]
     L.or_set_mlp.argtypes = [P, f64p]
+    L.or_mlp_forward_bf16.argtypes = [f64p, f64p, f64p, f64p, f64p]
+    L.or_bf16_slack.argtypes = [ctypes.c_double, ctypes.c_double]
+    L.or_bf16_slack.restype = ctypes.c_double
     L.or_learned_features.argtypes = [P, f32p, f32p, f32p, f64p, ctypes.c_uint64,
                                       ctypes.c_uint32, f64p, f64p]
     L.or_esjd_sample.argtypes = [P, f64p, f32p, f32p, f32p, f64p, f64p, ctypes.c_uint64,
@@ -270,11 +299,14 @@ class System:
                                   _ptr(pos.x, f32p), _ptr(pos.y, f32p), _ptr(pos.z, f32p))
         return pos
 
-    def set_mlp(self, W):
-        """Parameters of the learned proposal (move 2); kept alive here."""
+    def set_mlp(self, W, bf16=False):
+        """Parameters of the learned proposal (move 2); kept alive here.
+        bf16: evaluate the network in the BF16 reading of the tensor-core
+        evaluators instead of in FP64."""
         self._mlp = np.ascontiguousarray(W, dtype=np.float64)
         assert self._mlp.size == MLP_PARAMS
         self.L.or_set_mlp(ctypes.byref(self.s), _ptr(self._mlp, f64p))
+        self.s.mlp_bf16 = 1 if bf16 else 0
 
     def learned_features(self, pos, w_t, chain, i, r):
         f = np.zeros(12)
@@ -444,7 +476,7 @@ class System:
         return wA, wB
 
     def sweep(self, pos, wA, wB, sweep, c0=0, c1=None, want_margin=False, want_acc=False,
-              want_trial=False, want_chosen=False, w_types=None):
+              want_trial=False, want_chosen=False, w_types=None, want_slack=False):
         """One MC step in place; returns (stats, margin or None, accepted or
         None), plus the (3, M) trial positions when want_trial and the chosen
         particle of every attempt when want_chosen (molecule-parallel
@@ -456,6 +488,8 @@ class System:
         trial = np.full(3 * self.M, np.nan, np.float32) if want_trial else None
         chosen = np.zeros(self.M, np.uint32) if want_chosen else None
         self.s.chosen = chosen.ctypes.data if want_chosen else None
+        slack = np.full(self.M, np.inf) if want_slack else None
+        self.s.mlp_slack = slack.ctypes.data if want_slack else None
         if w_types is not None:   # the n_t field planes, (n_types, cells)
             planes = [np.ascontiguousarray(w_types[t], np.float64) for t in range(len(w_types))]
             ptrs = (ctypes.c_void_p * len(planes))(*[q.ctypes.data for q in planes])
@@ -471,11 +505,14 @@ class System:
         finally:
             self.s.chosen = None
             self.s.w_types = None
+            self.s.mlp_slack = None
         out = (st, margin, acc)
         if want_trial:
             out = out + (trial.reshape(3, self.M),)
         if want_chosen:
             out = out + (chosen,)
+        if want_slack:
+            out = out + (slack,)
         return out
 
     def observables(self, pos, nA, nB):

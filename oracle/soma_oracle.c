@@ -647,6 +647,82 @@ void or_mlp_forward(const double* W, const double x[12], double out[4]) {
   for (int j = 0; j < 4; ++j) out[j] = c.o[j];
 }
 
+/* BF16 reading of the network (the tensor-core evaluators of the library):
+ * every operand of a product is a BF16 value -- the inputs, the weights and
+ * biases (rounded from their FP32 value) and the hidden activations (the ReLU
+ * of the exact sum, rounded) -- while the sums themselves are exact here (the
+ * GPU accumulates in FP32, so a rounded value near a BF16 rounding boundary
+ * may round the other way there: or_bf16_slack measures how near). */
+double or_bf16_slack(double v, double T) {
+  if (v == 0.0 || !(T > 0.0) || !isfinite(v)) return INFINITY;
+  if (ldexp(1.0, ilogb(v) - 7) < ldexp(T, -16)) return INFINITY;
+  const float f = (float)v;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  const uint32_t sign = u & 0x80000000u, mag = u & 0x7FFF0000u;
+  double best = INFINITY;
+  /* the boundaries below, inside and above the BF16 interval holding f */
+  for (int k = -1; k <= 1; ++k) {
+    const int64_t b = (int64_t)mag + 0x8000 + (int64_t)k * 0x10000;
+    if (b < 0 || b >= 0x7F800000) continue;
+    const uint32_t bu = sign | (uint32_t)b;
+    float bf;
+    memcpy(&bf, &bu, 4);
+    const double d = fabs(v - (double)bf);
+    if (d < best) best = d;
+  }
+  return best / T;
+}
+
+static double or_wbf(const double* W, int k) { return or_round_bf16((float)W[k]); }
+
+/* T3 (optional, 4): magnitude of the terms of each output's sum */
+static void or_mlp_bf16_run(const double* W, const double x[12], const double* Tx,
+                            double out[4], double* T3, double* slack) {
+  double sl = slack ? *slack : INFINITY;
+  double xb[12], h1[32], h2[32];
+  for (int k = 0; k < 12; ++k) {
+    xb[k] = or_round_bf16((float)x[k]);
+    if (Tx) sl = fmin(sl, or_bf16_slack(x[k], Tx[k]));
+  }
+  for (int j = 0; j < 32; ++j) {
+    double a = or_wbf(W, L_B1 + j), T = fabs(a);
+    for (int k = 0; k < 12; ++k) {
+      const double t = or_wbf(W, L_W1 + 12 * j + k) * xb[k];
+      a += t;
+      T += fabs(t);
+    }
+    h1[j] = a > 0.0 ? or_round_bf16((float)a) : 0.0;
+    if (a > 0.0) sl = fmin(sl, or_bf16_slack(a, T));
+  }
+  for (int j = 0; j < 32; ++j) {
+    double a = or_wbf(W, L_B2 + j), T = fabs(a);
+    for (int k = 0; k < 32; ++k) {
+      const double t = or_wbf(W, L_W2 + 32 * j + k) * h1[k];
+      a += t;
+      T += fabs(t);
+    }
+    h2[j] = a > 0.0 ? or_round_bf16((float)a) : 0.0;
+    if (a > 0.0) sl = fmin(sl, or_bf16_slack(a, T));
+  }
+  for (int j = 0; j < 4; ++j) {
+    double a = or_wbf(W, L_B3 + j), T = fabs(a);
+    for (int k = 0; k < 32; ++k) {
+      const double t = or_wbf(W, L_W3 + 32 * j + k) * h2[k];
+      a += t;
+      T += fabs(t);
+    }
+    out[j] = a;
+    if (T3) T3[j] = T;
+  }
+  if (slack) *slack = sl;
+}
+
+void or_mlp_forward_bf16(const double* W, const double x[12], const double* Tx,
+                         double out[4], double* slack) {
+  or_mlp_bf16_run(W, x, Tx, out, NULL, slack);
+}
+
 /* Back-propagation of output gradients go[4] through the cached run: adds
  * the parameter gradients to gW (optional) and returns input gradients gx. */
 static void or_mlp_backward(const double* W, const or_mlp_cache* c, const double go[4],
@@ -720,6 +796,28 @@ void or_learned_features(const or_system* s, const float* x, const float* y, con
   feat[11] = (i + 1 < s->N) ? 1.0 : 0.0;
 }
 
+/* Magnitudes of the terms each feature at r is formed from, for the slack of
+ * its BF16 rounding: dr[d] bounds (as a magnitude) how far the GPU's r may
+ * lie from r -- 0 at the particle's own stored position, which both sides
+ * hold exactly, so that its bond vectors (one FP32 rounding of an exact
+ * difference on both sides) are reproduced exactly; the field gradient is
+ * formed from three field values (and r when dr > 0); the flags are exact. */
+static void or_feature_terms(const or_system* s, const double* w_t, uint32_t i,
+                             const double r[3], const double dr[3], const double feat[12],
+                             double T[12]) {
+  for (int k = 0; k < 12; ++k) T[k] = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    if (i > 0 && dr[d] > 0.0) T[d] = dr[d] + fabs(feat[d]);
+    if (i + 1 < s->N && dr[d] > 0.0) T[3 + d] = dr[d] + fabs(feat[3 + d]);
+  }
+  const uint64_t c = or_cell(s, r[0], r[1], r[2]);
+  for (int d = 0; d < 3; ++d) {
+    const double wm = w_t[or_cell_shift(s, c, d, -1)], wp = w_t[or_cell_shift(s, c, d, +1)];
+    const double lo = w_t[c] - wm, hi = wp - w_t[c];
+    T[6 + d] = fabs(w_t[c]) + fabs(wm) + fabs(wp) + fabs(hi - lo) * dr[d];
+  }
+}
+
 /* proposal parameters of the network outputs */
 static double or_sigma0(const or_system* s) { return s->a / sqrt(3.0); }
 static double or_logsig(const double o3) { return 2.0 * tanh(0.5 * o3); }
@@ -766,8 +864,15 @@ static void or_move_learned(const or_system* s, float* x, float* y, float* z,
     xi[2 * p + 1] = rad * sin(th);
   }
   double r_old[3] = { x[m], y[m], z[m] }, r_new[3], f[12], o[4], o_rev[4];
+  double T[12], T3[4], slack = INFINITY;
+  const double dr0[3] = { 0.0, 0.0, 0.0 };
   or_learned_features(s, x, y, z, w_t, chain, i, r_old, f);
-  or_mlp_forward(s->mlp, f, o);
+  if (s->mlp_bf16) {
+    or_feature_terms(s, w_t, i, r_old, dr0, f, T);
+    or_mlp_bf16_run(s->mlp, f, T, o, T3, &slack);
+  } else {
+    or_mlp_forward(s->mlp, f, o);
+  }
   const double sig = or_sigma0(s) * exp(or_logsig(o[3]));
   for (int d = 0; d < 3; ++d) {
     float dx = (float)(o[d] + sig * xi[d]);
@@ -778,7 +883,17 @@ static void or_move_learned(const or_system* s, float* x, float* y, float* z,
     for (int d = 0; d < 3; ++d) trial[d * M + m] = (float)r_new[d];
   }
   or_learned_features(s, x, y, z, w_t, chain, i, r_new, f);
-  or_mlp_forward(s->mlp, f, o_rev);
+  if (s->mlp_bf16) {
+    /* the trial position inherits the rounding of the outputs, the step
+       scale and the normals on the GPU */
+    double dr[3];
+    for (int d = 0; d < 3; ++d) dr[d] = fabs(r_new[d]) + fabs(o[d]) + sig * fabs(xi[d]) + T3[d];
+    or_feature_terms(s, w_t, i, r_new, dr, f, T);
+    or_mlp_bf16_run(s->mlp, f, T, o_rev, NULL, &slack);
+    if (s->mlp_slack) s->mlp_slack[m] = slack;
+  } else {
+    or_mlp_forward(s->mlp, f, o_rev);
+  }
   double dE = or_bond_energy(s, x, y, z, chain, i, r_new) - or_bond_energy(s, x, y, z, chain, i, r_old)
               + (w_t[or_cell(s, r_new[0], r_new[1], r_new[2])] - w_t[or_cell(s, r_old[0], r_old[1], r_old[2])]);
   const double log_alpha = -dE + or_log_q(s, o_rev, r_new, r_old) - or_log_q(s, o, r_old, r_new);

@@ -75,6 +75,14 @@ typedef struct {
   uint32_t n_types;           /* 0: the two types A, B of wA / wB */
   double chi_types[64];
   const double* const* w_types;
+  /* learned proposal in the tensor-core reading (mlp_bf16 = 1): features,
+     weights, biases and the two hidden layers' activations rounded to BF16
+     (nearest, ties to even) where the GPU's tensor-core evaluators round them,
+     sums exact (FP64); mlp_slack (optional, M doubles) receives per move the
+     smallest distance of a rounded value to a BF16 rounding boundary in units
+     of the magnitude of the terms that formed it (or_bf16_slack) */
+  int mlp_bf16;
+  double* mlp_slack;
 } or_system;
 
 /* --- Molecular architectures (Sec. 3.2.1, Fig. polyarch) ---------------------
@@ -215,6 +223,20 @@ void or_learned_features(const or_system* s, const float* x, const float* y, con
                          const double* w_t, uint64_t chain, uint32_t i, const double r[3],
                          double feat[12]);
 void or_set_mlp(or_system* s, const double* W);
+/* The network in the BF16 reading (see mlp_bf16): x rounded to BF16, weights
+ * and biases rounded FP64 -> FP32 -> BF16, each hidden pre-activation summed
+ * exactly, passed through the ReLU and rounded to BF16, outputs summed
+ * exactly.  Tx (optional, 12): magnitude of the terms each input was formed
+ * from (0: the input is reproduced exactly); *slack (optional) is lowered to
+ * the smallest or_bf16_slack of the rounded inputs and activations. */
+void or_mlp_forward_bf16(const double* W, const double x[12], const double* Tx,
+                         double out[4], double* slack);
+/* Distance of v from the nearest BF16 rounding boundary (the midpoint of two
+ * adjacent BF16 values, applied to the FP32 value of v) divided by T: how far,
+ * in units of T, v may move before its BF16 value changes.  +inf for v = 0,
+ * T <= 0, or where the BF16 spacing at v is below 2^-16 T (a change of the
+ * rounded value there is negligible). */
+double or_bf16_slack(double v, double T);
 /* Expected-squared-jump objective of one sample (chain, i) with normals xi:
  * J = alpha |r'-r|^2, alpha = min(1, exp(log_alpha)); returns J and adds dJ/dW
  * to grad (1604, optional).  Fields frozen, neighbours at their positions. */

@@ -13,6 +13,7 @@ from tests import test_oracle_philox as PH
 from tests import test_oracle_pins as PIN
 from tests import test_oracle_topology as TOPO
 from tests import test_oracle_types as TYPES
+from tests import test_oracle_learned_bf16 as BF16
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "soma_oracle.c")
 
@@ -117,6 +118,19 @@ MUTANTS = [
      "order[0] = 1u - first;\n    order[1] = first;", TOPO.check_linear_topology_is_the_linear_chain),
     ("topo_bond_counted_twice", "if (j <= i) continue;", "if (j == i) continue;",
      TOPO.check_topology_observables_hand_values),
+    # the BF16 reading of the learned proposal's network
+    ("bf16_inputs_not_rounded", "xb[k] = or_round_bf16((float)x[k]);", "xb[k] = x[k];",
+     BF16.check_bf16_network_closed_form),
+    ("bf16_weights_not_rounded", "static double or_wbf(const double* W, int k) { return or_round_bf16((float)W[k]); }",
+     "static double or_wbf(const double* W, int k) { return W[k]; }", BF16.check_bf16_network_closed_form),
+    ("bf16_first_hidden_not_rounded", "h1[j] = a > 0.0 ? or_round_bf16((float)a) : 0.0;",
+     "h1[j] = a > 0.0 ? a : 0.0;", BF16.check_bf16_network_closed_form),
+    ("bf16_second_hidden_not_rounded", "h2[j] = a > 0.0 ? or_round_bf16((float)a) : 0.0;",
+     "h2[j] = a > 0.0 ? a : 0.0;", BF16.check_bf16_network_closed_form),
+    ("bf16_reverse_density_in_fp64", "or_mlp_bf16_run(s->mlp, f, T, o_rev, NULL, &slack);",
+     "or_mlp_forward(s->mlp, f, o_rev);", BF16.check_bf16_move_uses_the_bf16_network),
+    ("bf16_slack_inner_boundary_only", "for (int k = -1; k <= 1; ++k) {", "for (int k = 0; k <= 0; ++k) {",
+     BF16.check_bf16_slack_values),
     # n_t particle types
     ("types_K0_sign", "else v = v - 0.5 * chi0 * (phi[i] - phi[k]);",
      "else v = v + 0.5 * chi0 * (phi[i] - phi[k]);",

@@ -239,14 +239,14 @@ def _cells_of(P3, L):
     return (c[2] * L + c[1]) * L + c[0]
 
 
-def check_two_particle_balance_brute_force(set_order, lib=None, move=0):
+def check_two_particle_balance_brute_force(set_order, lib=None, move=0, bf16=False):
     L = 2
     Re = 1.5
     d = SystemDesc(n_chains=4096, N=2, f=0.5, box_Re=(L / Re,) * 3, grid=(L,) * 3,
                    chiN=0.0, kappaN=0.0, set_order=set_order, seed=17, move=move)
     s = oracle_system(d, lib)
     if move == 2:
-        s.set_mlp(workloads.random_mlp(7, scale=0.1))
+        s.set_mlp(workloads.random_mlp(7, scale=0.1), bf16=bf16)
     K = s.params.K_b
     assert K == pytest.approx(3.0 / (2 * Re * Re))
     wA, wB = workloads.random_fields(L**3, seed=5, scale=1.0)
