@@ -885,9 +885,11 @@ static void or_move_learned(const or_system* s, float* x, float* y, float* z,
   or_learned_features(s, x, y, z, w_t, chain, i, r_new, f);
   if (s->mlp_bf16) {
     /* the trial position inherits the rounding of the outputs, the step
-       scale and the normals on the GPU */
+       scale and the normals on the GPU, and one rounding of the position
+       itself (2^-4 |r'| carries it at the 2^-19 relative level of the rest) */
     double dr[3];
-    for (int d = 0; d < 3; ++d) dr[d] = fabs(r_new[d]) + fabs(o[d]) + sig * fabs(xi[d]) + T3[d];
+    for (int d = 0; d < 3; ++d)
+      dr[d] = fabs(o[d]) + sig * fabs(xi[d]) + T3[d] + ldexp(fabs(r_new[d]), -4);
     or_feature_terms(s, w_t, i, r_new, dr, f, T);
     or_mlp_bf16_run(s->mlp, f, T, o_rev, NULL, &slack);
     if (s->mlp_slack) s->mlp_slack[m] = slack;

@@ -9,9 +9,10 @@ and FP64 evaluations may take different branches).
 Sweep: one cycle from the same positions and BF16-exact random weights, the
 tolerances of the smart Monte Carlo move (the network and the normals are
 evaluated in FP32 on the GPU, in FP64 in the oracle), with the FP32 network
-(SOMA_FLAG_LEARNED_FP32).  The tensor-core network (BF16 operands and
-activations) is checked for exactness by brute force and against the FP32
-network by the jump statistics it produces.
+(SOMA_FLAG_LEARNED_FP32).  The tensor-core networks (the default mma.sync one
+and the tcgen05 one; BF16 operands and activations, FP32 sums) against the
+oracle's BF16 reading of the network, one cycle element by element; they are
+also checked for exactness by brute force and against each other.
 """
 import math
 
@@ -133,6 +134,92 @@ def test_learned_one_cycle_matches_oracle(cuda_device, N, n_chains, grid, box):
         accepted += int(acc.sum())
     print(f"learned N={N}: {moves} moves, acceptance {accepted / moves:.3f}, mismatches {mism}")
     assert mism <= max(3, 5e-4 * moves)
+
+
+# A BF16 rounding of the tensor-core network may round the other way on the
+# GPU, whose sums are FP32 in the tensor cores' own order, when the oracle's
+# exact value lies within this fraction of the magnitude of its terms from a
+# rounding boundary (FP32 sums of at most 33 terms err by a few 2^-24 of it).
+SLACK_BF16 = 2.0**-19
+
+
+@pytest.mark.parametrize("flags", [0, FLAG_LEARNED_UMMA], ids=["mma_sync", "tcgen05"])
+@pytest.mark.parametrize("N,n_chains,grid,box", [
+    (32, 1001, (12, 12, 12), (2.0, 2.0, 2.0)),
+    (64, 257, (12, 12, 9), (2.0, 2.0, 1.5)),
+    (2, 4099, (6, 6, 6), (1.0, 1.0, 1.0)),
+    (8, 1003, (12, 12, 12), (2.0, 2.0, 2.0)),
+])
+def test_learned_tensor_core_one_cycle_matches_bf16_oracle(cuda_device, N, n_chains, grid, box,
+                                                           flags):
+    """The default learned sweep (BF16 network on the tensor cores, mma.sync)
+    and the tcgen05 one against the oracle's BF16 reading of the network, one
+    cycle from the same state, element by element.  Weights that BF16 must
+    round.  Tolerances of the smart Monte Carlo move, except that a move
+    whose oracle evaluation has a rounding within SLACK_BF16 of a BF16
+    boundary (or whose bonded partner's has) may round differently and so
+    propose up to 1e-2 dL elsewhere; such deviations must stay rare.  Chain
+    counts leave ragged last tiles and blocks with fewer than four tiles."""
+    d = SystemDesc(n_chains=n_chains, N=N, f=0.5, box_Re=box, grid=grid, chiN=30.0,
+                   kappaN=50.0, move=MOVE_LEARNED, seed=11, flags=flags)
+    W = workloads.random_mlp(5, scale=0.2) * (1.0 + 2.0**-10)
+    moves = mism = accepted = flagged = deviating = 0
+    for k, sweep in enumerate((0, 3, 1000)):
+        pos0 = workloads.random_walk_positions(d, seed=300 + k)
+        orc = oracle_system(d)
+        orc.set_mlp(W, bf16=True)
+        s = System(d)
+        s.set_proposal_weights(W.astype(np.float32))
+        s.set_positions(pos0)
+        s.set_sweep(sweep)
+        p = _pos(pos0)
+        nA, nB = orc.histogram(p)
+        wA, wB = orc.fields(nA, nB)
+        _, margin, acc, trial, slack = orc.sweep(p, wA, wB, sweep, want_margin=True,
+                                                 want_acc=True, want_trial=True, want_slack=True)
+        s.sweep(1)
+        g = s.get_positions()
+        s.close()
+        near = slack < SLACK_BF16
+        same_chain = lambda a, b: a // N == b // N  # noqa: E731
+        expl = near.copy()
+        expl[1:] |= near[:-1] & same_chain(np.arange(1, d.M), np.arange(d.M - 1))
+        expl[:-1] |= near[1:] & same_chain(np.arange(d.M - 1), np.arange(1, d.M))
+        gacc = np.any(g != pos0, axis=0).astype(np.uint8)
+        bad = np.nonzero(gacc != acc)[0]
+        ok = set(bad[np.abs(margin[bad]) < TIE_LEARNED].tolist())
+        face = _near_face(trial)
+        ok |= {int(m) for m in bad if face[m] or expl[m]}
+        for m in bad.tolist():
+            if m not in ok:
+                assert any(k2 in ok and k2 // N == m // N for k2 in (m - 1, m + 1)), \
+                    (m, margin[m], slack[m])
+        keep = np.ones(d.n_chains, bool)
+        keep[np.unique(bad // N)] = False
+        keep = np.repeat(keep, N)
+        np.testing.assert_array_equal(g[:, keep & (acc == 0)], pos0[:, keep & (acc == 0)])
+        sel = keep & (acc == 1)
+        dev = np.max(np.abs(g.astype(np.float64) - trial), axis=0)
+        # the normals (hardware log and sincos) err by ~2^-21 of the step, so
+        # the SMC tolerance grows with the step where it exceeds 3 dL (N = 2:
+        # steps up to ~13 dL)
+        step = np.max(np.abs(trial - pos0.astype(np.float64)), axis=0)
+        strict = dev <= np.maximum(_tol(trial[0]), 2e-6 * step)
+        off = np.nonzero(sel & ~strict)[0]
+        unexplained = off[~expl[off]]
+        assert len(unexplained) == 0, (unexplained[:10], dev[unexplained[:10]], slack[unexplained[:10]])
+        assert dev[off].max(initial=0) <= 1e-2, dev[off].max()
+        moves += d.M
+        mism += len(bad)
+        accepted += int(acc.sum())
+        flagged += int(near.sum())
+        deviating += len(off)
+    print(f"learned tensor-core network (flags={flags}) N={N}: {moves} moves, acceptance "
+          f"{accepted / moves:.3f}, decision mismatches {mism}, moves near a BF16 boundary "
+          f"{flagged}, proposals off by more than 1e-6 R_e0 {deviating}")
+    assert accepted > 0.05 * moves
+    assert mism <= max(3, 1e-3 * moves)
+    assert deviating <= max(3, 1e-2 * moves)
 
 
 @pytest.mark.parametrize("N,n_chains", [(32, 1000), (2, 4099), (64, 257)])
