@@ -7,8 +7,11 @@ kappaN=50.  One step = one SCMF cycle of every particle.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line (rank 0).  Under torchrun every rank runs an independent
-replica of the workload (weak scaling, no collective on the data path).
+Prints one JSON line (rank 0).  Under torchrun (N > 1) the workload's chains
+are sharded over the ranks (strong scaling: the same 134 M-particle system on
+N GPUs) and every cycle sums the occupation numbers over the ranks with one
+NCCL all-reduce before each rank's field update, the one exchange of the
+method (Sec. 3.1.1).
 """
 from __future__ import annotations
 
@@ -321,6 +324,102 @@ def field_kernel_bytes(d, n_types=0):
     return cells * (4 + 4 + 2 * wb)
 
 
+def run_sharded(args, rank, world):
+    """One rank of the chain-sharded cycle: this rank's share of the
+    workload's chains, one NCCL all-reduce of the packed counts per cycle."""
+    import ctypes
+
+    import torch
+    import torch.distributed as tdist
+    from paper_1711_03828_gb300 import System, _abi
+    from paper_1711_03828_gb300.shard import ShardedRun, shard_desc
+
+    if uses_architectures(args.workload) or args.move == "learned":
+        raise SystemExit("bench.py --gpus N > 1 shards the linear-chain workloads with uniform "
+                         "or smart Monte Carlo moves")
+    whole = workload(args.workload, grid_dtype=args.grid_dtype, move=args.move,
+                     iteration=args.iteration)
+    d = shard_desc(whole, world, rank)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    s = System(d, stream=stream)
+    run = ShardedRun(s, d.cells, "cuda")
+    run.start()
+    run.cycle(args.warmup)
+    s.sync()
+    t_before = s.timing()
+    tdist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record(stream)
+        run.cycle(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    tdist.barrier()
+    t = torch.tensor([ev0.elapsed_time(ev1)], device="cuda")
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    ms = float(t.item())
+    launches = s.timing()["kernel_launches"] - t_before["kernel_launches"]
+    value = whole.M * args.steps / (ms * 1e-3)
+    s.set_timing(True)
+    run.cycle(min(args.steps, 100))
+    tk = s.timing()
+    s.set_timing(False)
+    sweep_ms = tk["ms_sweep"] / max(tk["sweep_launches"], 1)
+    field_ms = tk["ms_fields"] / max(tk["field_launches"], 1)
+    peak, peak_kind = measured_peak_hbm()
+    achieved = sweep_kernel_bytes(d) / (sweep_ms * 1e-3) / 1e9
+    # end to end: every step uploads this rank's positions from pinned host
+    # memory, runs one sharded cycle (exchange included) and reads the summed
+    # occupation numbers back
+    host_pos = torch.empty(3 * d.M, dtype=torch.float32, pin_memory=True)
+    _abi.soma_get_positions(s.h, ctypes.c_void_p(host_pos.data_ptr()), 3 * d.M, 0)
+    host_n = torch.empty(d.cells, dtype=torch.int32, pin_memory=True)
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    tdist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        _abi.soma_set_positions(s.h, ctypes.c_void_p(host_pos.data_ptr()), 3 * d.M, 0)
+        run.start()
+        run.cycle(1)
+        _abi.soma_get_density(s.h, ctypes.c_void_p(host_n.data_ptr()), d.cells, 0)
+    torch.cuda.synchronize()
+    t = torch.tensor([time.perf_counter() - t0], device="cuda")
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    e2e = {"value": whole.M * e2e_steps / float(t.item()), "unit": UNIT,
+           "h2d_bytes_per_step": 12 * d.M, "d2h_bytes_per_step": 4 * d.cells,
+           "steps": e2e_steps, "per_rank": True}
+    obs = s.observables()
+    acc = torch.tensor([float(obs["accepted"]), float(obs["attempted"])], device="cuda",
+                       dtype=torch.float64)
+    tdist.all_reduce(acc)
+    s.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {**config_of(whole, args.workload,
+                                   f"inputs larger than L2 ({12 * d.M / 1e9:.2f} GB of positions "
+                                   "per rank)" if 12 * d.M > 129e6 else
+                                   f"inputs L2-resident ({12 * d.M / 1e6:.1f} MB per rank)"),
+                       "parallelism": f"chains sharded over {world} ranks, one NCCL all-reduce "
+                                      f"of the {4 * d.cells / 1e6:.1f} MB count grid per cycle"},
+            "roofline": {"bound": "hbm", "kernel": sweep_kernel_name(d), "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "traffic": None,
+                         "bytes_per_launch": sweep_kernel_bytes(d), "ms_per_launch": sweep_ms,
+                         "field_kernel_ms": field_ms},
+            "e2e": e2e, "clocks": clk.out, "gpu_launches": int(launches),
+            "acceptance": float(acc[0].item()) / max(float(acc[1].item()), 1.0),
+        }
+        print(json.dumps(line), flush=True)
+    tdist.destroy_process_group()
+
+
 def run_ours(args):
     import torch
     import torch.distributed as tdist
@@ -329,6 +428,8 @@ def run_ours(args):
     if world > 1:
         tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
+    if world > 1:
+        return run_sharded(args, rank, world)
     from paper_1711_03828_gb300 import System, _abi
 
     d = workload(args.workload, replica=rank, grid_dtype=args.grid_dtype, move=args.move,

@@ -55,7 +55,7 @@
 extern "C" {
 #endif
 
-#define SOMA_ABI_VERSION 1
+#define SOMA_ABI_VERSION 2
 
 typedef enum {
   SOMA_OK = 0,
@@ -123,6 +123,12 @@ typedef struct soma_system_desc {
   uint32_t replica_id;   /* Philox counter word 3, low 24 bits */
   uint32_t reserved1;
   void* stream;          /* cudaStream_t to run on; NULL: the handle creates its own */
+  /* Chain sharding (see soma_shard_sweep): this handle holds chains
+     [chain_offset, chain_offset + n_chains) of a system of n_chains_total
+     chains.  n_chains_total = 0: the handle holds the whole system
+     (chain_offset must then be 0). */
+  uint64_t chain_offset;
+  uint64_t n_chains_total;
 } soma_system_desc;
 
 typedef struct soma_t soma_t;
@@ -173,6 +179,47 @@ soma_status soma_sweep(soma_t* h, uint32_t n);
 /* Recompute n and omega from the current positions (first stage of the SCMF
  * cycle, Eqs. density-characteristics and omega-fields).  Asynchronous. */
 soma_status soma_update_fields(soma_t* h);
+
+/* Chain sharding over ranks (Sec. 3.1.1: whole molecules are distributed over
+ * the ranks, every rank moves its own molecules against the same fields, and
+ * the one exchange of a cycle is the sum of the occupation numbers over the
+ * ranks before each rank computes the fields itself).
+ *
+ * A shard is a handle whose desc has n_chains_total > 0: it holds chains
+ * [chain_offset, chain_offset + n_chains) of a system of n_chains_total
+ * chains (n_chains_total * N < 2^32) on the whole system's box and grid.
+ * Every random number is keyed on the whole system's chain and particle
+ * indices and rho_0 dL^3 counts all n_chains_total * N particles, so shards
+ * that hold every chain once, driven through the three calls below with
+ * their counts summed, reproduce bit for bit the handle that holds the whole
+ * system (given the same positions: soma_create labels each shard's chains
+ * in spatial order by itself, which is a different labelling of the same
+ * system; soma_set_positions gives any other).  A shard takes the uniform,
+ * smart Monte Carlo and learned moves, the SET and the molecule-parallel
+ * iterations and molecular architectures (soma_set_topology); not n_t types
+ * nor batches.  soma_sweep and soma_update_fields refuse a shard
+ * (SOMA_ESTATE): they would use its own particles' counts alone.
+ *
+ * One cycle of a shard h, on h's stream:
+ *   soma_shard_sweep(h, buf, cells)     MC step of h's particles; their packed
+ *                                       occupation numbers are copied to buf
+ *   <sum buf over all shards, in place> e.g. ncclAllReduce(buf, buf, cells,
+ *                                       ncclUint32, ncclSum, comm, stream): the
+ *                                       packed A | B<<16 halves add exactly
+ *                                       while every global count is < 2^16
+ *   soma_shard_fields(h, buf, cells)    n := buf, omega from it, cycle done
+ * After soma_create or soma_set_positions the fields are those of h's own
+ * particles; start with soma_shard_counts(h, buf, cells), the sum, and
+ * soma_shard_fields(h, buf, cells).  The calls must alternate in that order
+ * (a counts or sweep call, then a fields call): SOMA_ESTATE otherwise.
+ * buf holds cells = grid cells uint32 entries, device or host memory (the
+ * copies use cudaMemcpyDefault; with host memory the call returns after its
+ * copy); it is borrowed for the call only.  SOMA_EINVAL: NULL argument or
+ * cells differs from the grid size.  Overflow of a summed count is reported
+ * as for soma_sweep (SOMA_EOVERFLOW, sticky). */
+soma_status soma_shard_counts(soma_t* h, uint32_t* counts, size_t cells);
+soma_status soma_shard_sweep(soma_t* h, uint32_t* counts, size_t cells);
+soma_status soma_shard_fields(soma_t* h, const uint32_t* summed, size_t cells);
 
 /* Copy the packed occupation numbers (n_cells = grid cells entries; bits 0..15
  * n_A, 16..31 n_B) to dst (device pointer if dst_on_device, else host).
@@ -315,7 +362,10 @@ soma_status soma_topology_sets(const uint32_t* words, uint64_t n_words, const ui
                                uint32_t n_arch, uint32_t N, uint8_t* sets, uint8_t* n_sets);
 
 /* FP64 observables of the current state (Eq. h-bond, Eq. discrete-ham).
- * Synchronises. */
+ * Synchronises.  For a shard, E_b, Re2, b2 and the move counts cover its own
+ * chains (sum E_b and the counts over the shards, weight Re2 and b2 by the
+ * chains and bonds); E_nb, E_ext and max_cell are those of the current
+ * occupation numbers, i.e. of the whole system after soma_shard_fields. */
 soma_status soma_observables(soma_t* h, soma_obs* out);
 
 /* Derived parameters of a system (Sec. 2.1), all in the units used by the

@@ -42,6 +42,8 @@ class SystemDesc:
     replica_id: int = 0
     flags: int = 0
     hamiltonian: int = 0
+    chain_offset: int = 0      # chain sharding: this handle holds chains
+    n_chains_total: int = 0    # [chain_offset, chain_offset + n_chains) of n_chains_total
 
     @property
     def M(self):
@@ -71,6 +73,8 @@ class SystemDesc:
         d.seed = int(self.seed)
         d.replica_id = int(self.replica_id)
         d.stream = stream
+        d.chain_offset = int(self.chain_offset)
+        d.n_chains_total = int(self.n_chains_total)
         return d
 
 
@@ -138,6 +142,28 @@ class System:
 
     def sync(self):
         _abi.soma_sync(self.h)
+
+    # -- chain sharding (one exchange of occupation numbers per cycle) -----
+    def _counts_arg(self, buf):
+        cells = self.desc.cells
+        if isinstance(buf, np.ndarray):
+            assert buf.dtype == np.uint32 and buf.size == cells and buf.flags.c_contiguous
+            return ctypes.c_void_p(buf.ctypes.data), cells
+        assert buf.is_contiguous() and buf.numel() == cells and buf.element_size() == 4
+        return ctypes.c_void_p(buf.data_ptr()), cells
+
+    def shard_counts(self, buf):
+        """Packed occupation numbers of this shard's particles into buf
+        (cells uint32/int32: numpy array or tensor); soma_shard_counts."""
+        _abi.soma_shard_counts(self.h, *self._counts_arg(buf))
+
+    def shard_sweep(self, buf):
+        """MC step of this shard's particles; their packed counts into buf."""
+        _abi.soma_shard_sweep(self.h, *self._counts_arg(buf))
+
+    def shard_fields(self, summed):
+        """Fields from the counts summed over every shard; ends the cycle."""
+        _abi.soma_shard_fields(self.h, *self._counts_arg(summed))
 
     # -- state access -----------------------------------------------------
     def get_positions(self, out=None):

@@ -43,6 +43,8 @@ class SomaSystemDesc(ctypes.Structure):
         ("replica_id", ctypes.c_uint32),
         ("reserved1", ctypes.c_uint32),
         ("stream", ctypes.c_void_p),
+        ("chain_offset", ctypes.c_uint64),
+        ("n_chains_total", ctypes.c_uint64),
     ]
 
 
@@ -108,6 +110,9 @@ _SIGS = {
     "soma_destroy": ([_P], _c.c_int),
     "soma_sweep": ([_P, _c.c_uint32], _c.c_int),
     "soma_update_fields": ([_P], _c.c_int),
+    "soma_shard_counts": ([_P, _P, _c.c_size_t], _c.c_int),
+    "soma_shard_sweep": ([_P, _P, _c.c_size_t], _c.c_int),
+    "soma_shard_fields": ([_P, _P, _c.c_size_t], _c.c_int),
     "soma_get_density": ([_P, _P, _c.c_size_t, _c.c_int], _c.c_int),
     "soma_get_fields": ([_P, _P, _c.c_size_t, _c.c_int], _c.c_int),
     "soma_get_positions": ([_P, _P, _c.c_size_t, _c.c_int], _c.c_int),
@@ -188,6 +193,9 @@ soma_create = _wrap("soma_create")
 soma_destroy = _wrap("soma_destroy")
 soma_sweep = _wrap("soma_sweep")
 soma_update_fields = _wrap("soma_update_fields")
+soma_shard_counts = _wrap("soma_shard_counts")
+soma_shard_sweep = _wrap("soma_shard_sweep")
+soma_shard_fields = _wrap("soma_shard_fields")
 soma_get_density = _wrap("soma_get_density")
 soma_get_fields = _wrap("soma_get_fields")
 soma_get_positions = _wrap("soma_get_positions")

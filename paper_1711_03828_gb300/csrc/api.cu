@@ -109,6 +109,9 @@ struct soma_t {
   SweepShape shape;
   uint64_t host_sweep = 0;
   uint64_t launches = 0;
+  // chain sharding: 0 no exchange pending, 1 soma_shard_counts done, 2
+  // soma_shard_sweep done (soma_shard_fields comes next in both cases)
+  int shard_phase = 0;
   bool timing = false;
   struct EvPair { cudaEvent_t a, b; int kind; };
   std::vector<EvPair> ev_pending;
@@ -171,6 +174,18 @@ soma_status validate(const soma_system_desc* d) {
     return fail(SOMA_EINVAL, "unknown flags 0x%x", d->flags);
   if (d->replica_id > 0xFFFFFFu) return fail(SOMA_EINVAL, "replica_id must be < 2^24");
   if (d->hamiltonian > 1) return fail(SOMA_EINVAL, "hamiltonian=%u unknown", d->hamiltonian);
+  if (d->n_chains_total == 0 && d->chain_offset != 0)
+    return fail(SOMA_EINVAL, "chain_offset=%llu needs n_chains_total (the whole system's chains)",
+                (unsigned long long)d->chain_offset);
+  if (d->n_chains_total != 0) {
+    if (d->chain_offset > d->n_chains_total || d->n_chains > d->n_chains_total - d->chain_offset)
+      return fail(SOMA_EINVAL, "chains [%llu, %llu) lie outside the %llu chains of the system",
+                  (unsigned long long)d->chain_offset,
+                  (unsigned long long)(d->chain_offset + d->n_chains),
+                  (unsigned long long)d->n_chains_total);
+    if (d->n_chains_total >= (1ull << 32) / d->N)
+      return fail(SOMA_EINVAL, "a sharded system needs n_chains_total*N < 2^32");
+  }
   return SOMA_OK;
 }
 
@@ -185,7 +200,9 @@ void derive(soma_t* h) {
   h->sigma = (d.N > 1) ? h->Re / std::sqrt(3.0 * (double)(d.N - 1)) : 0.0;
   h->M = d.n_chains * d.N;
   const double cells = (double)d.grid[0] * (double)d.grid[1] * (double)d.grid[2];
-  h->rho_cell = (double)h->M / cells;
+  // rho_0 dL^3 of the whole system (a shard holds part of its particles)
+  const uint64_t M_all = (d.n_chains_total ? d.n_chains_total : d.n_chains) * d.N;
+  h->rho_cell = (double)M_all / cells;
   h->grid_dtype = d.grid_dtype;
   Geom& g = h->g;
   g.n_chains = d.n_chains;
@@ -211,6 +228,8 @@ void derive(soma_t* h) {
     g.rk1[r] = g.key1 + (uint32_t)r * 0xBB67AE85u;
   }
   g.replica = d.replica_id;
+  g.chain_base = d.n_chains_total ? d.chain_offset : 0;
+  g.id_base = g.chain_base * d.N;
 }
 
 size_t wbytes(int dtype) { return dtype == 0 ? 4 : 2; }
@@ -571,6 +590,8 @@ soma_status soma_destroy(soma_t* h) {
 soma_status soma_sweep(soma_t* h, uint32_t n) {
   if (!h) return fail(SOMA_EINVAL, "handle is NULL");
   if (h->batched) return fail(SOMA_ESTATE, "this system belongs to a batch: use soma_batch_sweep");
+  if (h->desc.n_chains_total)
+    return fail(SOMA_ESTATE, "a shard exchanges counts every cycle: use soma_shard_sweep");
   if (h->pos_invalid) return fail(SOMA_ESTATE, "positions out of range: set valid positions first");
   if (h->n_types && !h->has_topo)
     return fail(SOMA_ESTATE, "n_t types take the architecture path: call soma_set_topology");
@@ -599,7 +620,65 @@ soma_status soma_sweep(soma_t* h, uint32_t n) {
 soma_status soma_update_fields(soma_t* h) {
   if (!h) return fail(SOMA_EINVAL, "handle is NULL");
   if (h->pos_invalid) return fail(SOMA_ESTATE, "positions out of range: set valid positions first");
+  if (h->desc.n_chains_total)
+    return fail(SOMA_ESTATE, "a shard's fields need every shard's counts: use soma_shard_counts");
   return update_fields(h);
+}
+
+namespace {
+soma_status shard_check(soma_t* h, const void* buf, size_t cells) {
+  if (!h || !buf) return fail(SOMA_EINVAL, "NULL argument");
+  if (!h->desc.n_chains_total) return fail(SOMA_ESTATE, "not a shard (desc.n_chains_total is 0)");
+  if (cells != h->g.cells) return fail(SOMA_EINVAL, "cells=%zu, the grid has %u", cells, h->g.cells);
+  if (h->pos_invalid) return fail(SOMA_ESTATE, "positions out of range: set valid positions first");
+  return SOMA_OK;
+}
+}  // namespace
+
+soma_status soma_shard_counts(soma_t* h, uint32_t* counts, size_t cells) {
+  soma_status st = shard_check(h, counts, cells);
+  if (st != SOMA_OK) return st;
+  if (h->shard_phase != 0) return fail(SOMA_ESTATE, "soma_shard_fields must come first");
+  uint32_t* nn = h->n[h->host_sweep & 1];
+  SOMA_CUDA(cudaMemsetAsync(nn, 0, sizeof(uint32_t) * cells, h->stream));
+  SOMA_CUDA(launch_histogram(h->g, h->x(), h->y(), h->z(), nn, h->sm_count, h->stream,
+                             h->d_seq, h->d_seq ? h->d_arch : nullptr));
+  ++h->launches;
+  SOMA_CUDA(cudaMemcpyAsync(counts, nn, sizeof(uint32_t) * cells, cudaMemcpyDefault, h->stream));
+  h->shard_phase = 1;
+  return SOMA_OK;
+}
+
+soma_status soma_shard_sweep(soma_t* h, uint32_t* counts, size_t cells) {
+  soma_status st = shard_check(h, counts, cells);
+  if (st != SOMA_OK) return st;
+  if (h->shard_phase != 0) return fail(SOMA_ESTATE, "soma_shard_fields must come first");
+  const SweepArgs sa = sweep_args(h);
+  st = timed(h, 0, [&] { return launch_sweep_any(h, sa); });
+  if (st != SOMA_OK) return st;
+  SOMA_CUDA(cudaMemcpyAsync(counts, h->n[(h->host_sweep + 1) & 1], sizeof(uint32_t) * cells,
+                            cudaMemcpyDefault, h->stream));
+  h->shard_phase = 2;
+  return SOMA_OK;
+}
+
+soma_status soma_shard_fields(soma_t* h, const uint32_t* summed, size_t cells) {
+  soma_status st = shard_check(h, summed, cells);
+  if (st != SOMA_OK) return st;
+  if (h->shard_phase == 0)
+    return fail(SOMA_ESTATE, "soma_shard_counts or soma_shard_sweep must come first");
+  const int after_sweep = h->shard_phase == 2;
+  // the summed counts take the place of the shard's own in the buffer the
+  // field kernel reads: n[(s+1)&1] after a sweep, n[s&1] otherwise
+  uint32_t* nn = h->n[(h->host_sweep + (after_sweep ? 1 : 0)) & 1];
+  SOMA_CUDA(cudaMemcpyAsync(nn, summed, sizeof(uint32_t) * cells, cudaMemcpyDefault, h->stream));
+  const FieldArgs fa = field_args(h, after_sweep);
+  st = timed(h, 1, [&] { return launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count,
+                                              h->stream); });
+  if (st != SOMA_OK) return st;
+  if (after_sweep) ++h->host_sweep;
+  h->shard_phase = 0;
+  return SOMA_OK;
 }
 
 soma_status soma_sync(soma_t* h) {
@@ -670,6 +749,7 @@ soma_status soma_set_positions(soma_t* h, const float* src, size_t n, int src_on
   SOMA_CUDA(cudaStreamSynchronize(h->stream));
   h->launches += 3;
   h->pos_invalid = flag != 0;
+  h->shard_phase = 0;
   if (flag)
     return fail(SOMA_EINVAL, "a position is not finite or has |x| >= 2^18 dL: set valid positions "
                              "before the next sweep");
@@ -815,6 +895,8 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
 soma_status soma_set_types(soma_t* h, uint32_t n_types, const double* chiN) {
   if (!h) return fail(SOMA_EINVAL, "handle is NULL");
   if (h->batched) return fail(SOMA_ESTATE, "a batch member has the two types A, B");
+  if (h->desc.n_chains_total && n_types)
+    return fail(SOMA_ESTATE, "a shard exchanges the packed A | B counts: n_t types are not sharded");
   if (n_types == 0) {   // back to the packed A | B grid
     if (h->topo_max_type > 1)
       return fail(SOMA_ESTATE, "the architectures use type %u: set two-type architectures first",
@@ -1121,6 +1203,7 @@ soma_status soma_set_sweep(soma_t* h, uint64_t sweep) {
   SOMA_CUDA(cudaMemcpyAsync(h->d_counters, &v, sizeof v, cudaMemcpyHostToDevice, h->stream));
   SOMA_CUDA(cudaStreamSynchronize(h->stream));
   h->host_sweep = sweep;
+  h->shard_phase = 0;
   // the occupation buffer in use depends on the counter's parity
   if (h->n_types)
     SOMA_CUDA(cudaMemsetAsync(h->nt[(sweep + 1) & 1], 0,
@@ -1442,6 +1525,7 @@ soma_status soma_batch_create(const soma_system_desc* descs, uint32_t n, void* s
     if (d.grid_dtype != descs[0].grid_dtype)
       return fail(SOMA_EINVAL, "batch member %u: all members share one grid_dtype", k);
     if (d.n_chains * d.N >= (1ull << 32)) return fail(SOMA_EINVAL, "batch member %u: M >= 2^32", k);
+    if (d.n_chains_total) return fail(SOMA_EINVAL, "batch member %u: a batch holds whole systems", k);
   }
   soma_batch_t* b = new (std::nothrow) soma_batch_t();
   if (!b) return fail(SOMA_ENOMEM, "host allocation failed");

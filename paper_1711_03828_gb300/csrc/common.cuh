@@ -132,6 +132,13 @@ struct Geom {
   uint32_t key0, key1;
   uint32_t rk0[10], rk1[10];  // Philox round keys: key + r * (Weyl constant)
   uint32_t replica;
+  // One shard of a larger system (chains distributed over ranks, Sec. 3.1.1):
+  // its chain k is chain chain_base + k of the whole system, and every draw
+  // is keyed on the whole system's chain and particle indices (id_base =
+  // chain_base * N), so that the shards together draw what one handle holding
+  // every chain draws.  Both 0 for a system held whole.  A sharded system has
+  // fewer than 2^32 particles, so 32-bit counters stay exact.
+  uint64_t chain_base, id_base;
 };
 
 // Per-axis cell, clamped into [0, n) (exact inside the supported range).

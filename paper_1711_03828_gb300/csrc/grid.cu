@@ -152,7 +152,8 @@ __global__ void init_kernel(const Geom g, float* __restrict__ x, float* __restri
   const double two_pi = 6.283185307179586;  // 2*pi rounded to FP64
   for (uint64_t chain = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; chain < g.n_chains;
        chain += stride) {
-    const uint32_t lo = (uint32_t)chain, hi = (uint32_t)(chain >> 32);
+    const uint64_t gc = chain + g.chain_base;   // the chain's index in the whole system
+    const uint32_t lo = (uint32_t)gc, hi = (uint32_t)(gc >> 32);
     uint4 w = philox4x32_10(make_uint4(lo, hi, 0u, ctr3), g.key0, g.key1);
     double r[3] = {__dmul_rn(uniform_open_f64(w.x), (double)g.nx),
                    __dmul_rn(uniform_open_f64(w.y), (double)g.ny),

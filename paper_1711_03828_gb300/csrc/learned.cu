@@ -130,8 +130,9 @@ __global__ void __launch_bounds__(256) sweep_learned_kernel(const SweepArgs p,
 #pragma unroll
     for (int j = 0; j < S; ++j) {
       const uint64_t m = base + j;
-      const uint4 r1 = philox_rk(make_uint4((uint32_t)m, (uint32_t)(m >> 32), sweep, ctr3a), p.g);
-      const uint4 r2 = philox_rk(make_uint4((uint32_t)m, (uint32_t)(m >> 32), sweep, ctr3b), p.g);
+      const uint64_t mc = m + p.g.id_base;
+      const uint4 r1 = philox_rk(make_uint4((uint32_t)mc, (uint32_t)(mc >> 32), sweep, ctr3a), p.g);
+      const uint4 r2 = philox_rk(make_uint4((uint32_t)mc, (uint32_t)(mc >> 32), sweep, ctr3b), p.g);
       lowbits |= (r1.w & 1u) << j;
       float sn, cs;
       const float rad0 = sqrtf(-2.f * log_uniform_open_accurate(r1.x));

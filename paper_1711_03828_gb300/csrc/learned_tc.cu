@@ -454,10 +454,11 @@ __device__ __forceinline__ unsigned learned_pair_tile(const SweepArgs& p, const 
   float xi0[3], xi1[3], lnu0, lnu1;
   uint32_t w3first;
   {
-    const uint4 r1 = philox_rk(make_uint4(base, 0u, sweep, ctr3a), p.g);
-    const uint4 r2 = philox_rk(make_uint4(base, 0u, sweep, ctr3b), p.g);
-    const uint4 s1 = philox_rk(make_uint4(base + 1u, 0u, sweep, ctr3a), p.g);
-    const uint4 s2 = philox_rk(make_uint4(base + 1u, 0u, sweep, ctr3b), p.g);
+    const uint32_t cb = base + (uint32_t)p.g.id_base;
+    const uint4 r1 = philox_rk(make_uint4(cb, 0u, sweep, ctr3a), p.g);
+    const uint4 r2 = philox_rk(make_uint4(cb, 0u, sweep, ctr3b), p.g);
+    const uint4 s1 = philox_rk(make_uint4(cb + 1u, 0u, sweep, ctr3a), p.g);
+    const uint4 s2 = philox_rk(make_uint4(cb + 1u, 0u, sweep, ctr3b), p.g);
     float sn, cs;
     float rad = sqrtf(-2.f * log_uniform_open(r1.x));
     sincos_2pi_uniform_fast(r1.y, &sn, &cs);

@@ -68,7 +68,7 @@ __device__ __forceinline__ void molecule_body(const SweepArgs& p, const TopoArgs
       float* Y = STAGE ? sy + t * N : p.y + chain * N;
       float* Z = STAGE ? sz + t * N : p.z + chain * N;
       for (uint32_t j = 0; j < N; ++j) {
-        const uint64_t id = chain * N + j;
+        const uint64_t id = chain * N + j + p.g.id_base;
         const uint4 r = philox_rk(make_uint4((uint32_t)id, (uint32_t)(id >> 32), sweep, ctr3), p.g);
         const uint32_t i = ((r.w & 0xFFu) * N) >> 8;
         const float xo = X[i], yo = Y[i], zo = Z[i];

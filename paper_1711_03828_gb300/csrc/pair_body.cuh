@@ -60,8 +60,9 @@ struct PairLane {
 };
 
 // Moves the pair (x0,y0,z0), (x1,y1,z1) held by this lane (particles base and
-// base+1), stores the result and counts the final cells into nacc.  g gives
-// the cell fold, keys the Philox round keys.  PARTIAL: the tile may hold
+// base+1, drawing with the counter indices cbase and cbase+1), stores the
+// result and counts the final cells into nacc.  g gives the cell fold, keys
+// the Philox round keys.  PARTIAL: the tile may hold
 // fewer rows than lanes (valid says whether this lane's pair exists).
 // Returns this lane's accepted moves.
 //
@@ -73,14 +74,15 @@ template <typename WT, typename IDX, bool PARTIAL>
 __device__ __forceinline__ unsigned pair_tile(const Geom& g, const Geom& keys, const PairLane<WT>& L,
                                               float* __restrict__ px, float* __restrict__ py,
                                               float* __restrict__ pz, uint32_t* __restrict__ nacc,
-                                              IDX base, bool valid, uint32_t sweep, uint32_t ctr3,
+                                              IDX base, IDX cbase, bool valid, uint32_t sweep,
+                                              uint32_t ctr3,
                                               bool set_order_random, float a, float K1, float x0,
                                               float x1, float y0, float y1, float z0, float z1) {
   if (!PARTIAL) valid = true;
   const float K2 = 2.f * K1;
-  const uint32_t hi = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)base >> 32) : 0u;
-  const uint4 r0 = philox_rk(make_uint4((uint32_t)base, hi, sweep, ctr3), keys);
-  const IDX m1 = base + 1u;
+  const uint32_t hi = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)cbase >> 32) : 0u;
+  const uint4 r0 = philox_rk(make_uint4((uint32_t)cbase, hi, sweep, ctr3), keys);
+  const IDX m1 = cbase + 1u;
   const uint32_t hi1 = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)m1 >> 32) : 0u;
   const uint4 r1 = philox_rk(make_uint4((uint32_t)m1, hi1, sweep, ctr3), keys);
   const float xn0 = __fadd_rn(x0, __fmul_rn(a, uniform_sym(r0.x)));

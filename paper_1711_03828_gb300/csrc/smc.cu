@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256) sweep_smc_kernel(const SweepArgs p) {
     uint32_t lowbits = 0;
 #pragma unroll
     for (int j = 0; j < S; ++j) {
-      const uint64_t m = base + j;
+      const uint64_t m = base + j + p.g.id_base;
       const uint4 r1 = philox_rk(make_uint4((uint32_t)m, (uint32_t)(m >> 32), sweep, ctr3a), p.g);
       const uint4 r2 = philox_rk(make_uint4((uint32_t)m, (uint32_t)(m >> 32), sweep, ctr3b), p.g);
       lowbits |= (r1.w & 1u) << j;
@@ -300,8 +300,10 @@ __global__ void __launch_bounds__(256, 3) sweep_smc_pair_kernel(const SweepArgs 
       pz = __ldcs(reinterpret_cast<const float2*>(p.z + base));
     }
     uint32_t w0, w1;
-    const SmcSlot s0 = smc_slot<WT>(p.g, L.w0, px.x, py.x, pz.x, base, sweep, ctr3a, ctr3b, valid, &w0);
-    const SmcSlot s1 = smc_slot<WT>(p.g, L.w1, px.y, py.y, pz.y, base + 1u, sweep, ctr3a, ctr3b,
+    const uint32_t cbase = base + (uint32_t)p.g.id_base;
+    const SmcSlot s0 = smc_slot<WT>(p.g, L.w0, px.x, py.x, pz.x, cbase, sweep, ctr3a, ctr3b, valid,
+                                    &w0);
+    const SmcSlot s1 = smc_slot<WT>(p.g, L.w1, px.y, py.y, pz.y, cbase + 1u, sweep, ctr3a, ctr3b,
                                     valid, &w1);
     const bool sw = p.set_order_random && (__shfl_sync(FULL, w0, L.first_lane) & 1u);
     SmcSlot A = sw ? s1 : s0, B = sw ? s0 : s1;

@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256) sweep_uniform_kernel(const SweepArgs p) {
     uint32_t lowbits = 0;
 #pragma unroll
     for (int j = 0; j < S; ++j) {
-      const uint64_t m = base + j;
+      const uint64_t m = base + j + p.g.id_base;
       const uint4 r = philox_rk(make_uint4((uint32_t)m, (uint32_t)(m >> 32), sweep, ctr3), p.g);
       xn[j] = __fadd_rn(x[j], __fmul_rn(p.a, uniform_sym(r.x)));
       yn[j] = __fadd_rn(y[j], __fmul_rn(p.a, uniform_sym(r.y)));
@@ -262,12 +262,15 @@ __global__ void __launch_bounds__(256, 3) sweep_pair_kernel(const SweepArgs p) {
       const uint64_t seq = chain < p.g.n_chains ? __ldg(p.seq + __ldg(p.arch + chain)) : 0ull;
       Lt.set_types((seq >> L.ci0) & 1ull, (seq >> (L.ci0 + 1u)) & 1ull, p.wA, p.wB);
     }
+    const IDX cbase = base + (IDX)p.g.id_base;
     if (tile < full_tiles)
-      my_acc += pair_tile<WT, IDX, false>(p.g, p.g, Lt, p.x, p.y, p.z, nacc, base, true, sweep, ctr3,
-                                          p.set_order_random, p.a, p.K_b, x0, x1, y0, y1, z0, z1);
+      my_acc += pair_tile<WT, IDX, false>(p.g, p.g, Lt, p.x, p.y, p.z, nacc, base, cbase, true, sweep,
+                                          ctr3, p.set_order_random, p.a, p.K_b, x0, x1, y0, y1, z0,
+                                          z1);
     else
-      my_acc += pair_tile<WT, IDX, true>(p.g, p.g, Lt, p.x, p.y, p.z, nacc, base, valid, sweep, ctr3,
-                                         p.set_order_random, p.a, p.K_b, x0, x1, y0, y1, z0, z1);
+      my_acc += pair_tile<WT, IDX, true>(p.g, p.g, Lt, p.x, p.y, p.z, nacc, base, cbase, valid, sweep,
+                                         ctr3, p.set_order_random, p.a, p.K_b, x0, x1, y0, y1, z0,
+                                         z1);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) my_acc += __shfl_xor_sync(FULL, my_acc, o);

@@ -62,7 +62,8 @@ __device__ __forceinline__ uint32_t set_steps(uint32_t n_sets, bool random, uint
     return s;
   }
   if (n_sets == 2) return first_bit ? 0x01u : 0x10u;
-  const uint4 r = philox_rk(make_uint4((uint32_t)mol, (uint32_t)(mol >> 32), sweep, ctr3), g);
+  const uint64_t gm = mol + g.chain_base;
+  const uint4 r = philox_rk(make_uint4((uint32_t)gm, (uint32_t)(gm >> 32), sweep, ctr3), g);
   const uint32_t w[4] = {r.x, r.y, r.z, r.w};
   uint32_t order = 0;  // nibble k: the set visited at step k
 #pragma unroll
@@ -182,8 +183,9 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
       const uint32_t a = (a2 >> (8 * j)) & 0xFFu;
       const IDX m = base + tl;
       const uint32_t pw = valid ? __ldg(t.ptab + a * TOPO_TILE + ci) : 0u;
-      const uint32_t hi = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)m >> 32) : 0u;
-      const uint4 r = philox_rk(make_uint4((uint32_t)m, hi, sweep, ctr3), p.g);
+      const IDX mc = m + (IDX)p.g.id_base;
+      const uint32_t hi = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)mc >> 32) : 0u;
+      const uint4 r = philox_rk(make_uint4((uint32_t)mc, hi, sweep, ctr3), p.g);
       const float xn = __fadd_rn(x[j], __fmul_rn(p.a, uniform_sym(r.x)));
       const float yn = __fadd_rn(y[j], __fmul_rn(p.a, uniform_sym(r.y)));
       const float zn = __fadd_rn(z[j], __fmul_rn(p.a, uniform_sym(r.z)));

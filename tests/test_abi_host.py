@@ -14,7 +14,13 @@ def test_library_exports_every_declared_symbol(soma_lib):
     L = soma_lib.lib()
     missing = [n for n in names if not hasattr(L, n)]
     assert not missing, missing
-    assert L.soma_abi_version() == 1
+    assert L.soma_abi_version() == 2
+
+
+def test_binding_wraps_every_declared_symbol():
+    """The Python binding has one function per declared entry point."""
+    missing = [n for n in _abi.declared_symbols() if not callable(getattr(_abi, n, None))]
+    assert not missing, missing
 
 
 def _create_status(desc_c):
@@ -124,3 +130,18 @@ def test_invalid_batch_is_rejected_without_gpu(soma_lib, bad):
     n = 0 if bad == "empty" else 2
     assert _abi.lib().soma_batch_create(arr, n, None, ctypes.byref(h)) == _abi.SOMA_EINVAL
     assert h.value is None
+
+
+@pytest.mark.parametrize("offset,count,total", [
+    (1, 16, 0),            # an offset without the whole system's chain count
+    (10, 16, 20),          # chains beyond the whole system
+    (0, 16, 8),            # more chains than the whole system
+    (0, 16, 1 << 29),      # a sharded system of 2^32 particles (N = 8)
+])
+def test_invalid_shard_is_rejected_without_gpu(soma_lib, offset, count, total):
+    d = _valid()
+    d.chain_offset, d.n_chains, d.n_chains_total = offset, count, total
+    st, h = _create_status(d.to_c())
+    assert st == _abi.SOMA_EINVAL and h.value is None
+    msg = _abi.soma_last_error()
+    assert "chain" in msg or "2^32" in msg

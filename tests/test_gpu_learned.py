@@ -139,8 +139,10 @@ def test_learned_one_cycle_matches_oracle(cuda_device, N, n_chains, grid, box):
 # A BF16 rounding of the tensor-core network may round the other way on the
 # GPU, whose sums are FP32 in the tensor cores' own order, when the oracle's
 # exact value lies within this fraction of the magnitude of its terms from a
-# rounding boundary (FP32 sums of at most 33 terms err by a few 2^-24 of it).
-SLACK_BF16 = 2.0**-19
+# rounding boundary: a sum of K <= 32 products and the accumulator whose
+# alignment truncates errs by at most (K + 1) 2^-23 of the terms' magnitude,
+# below 2^-17 (and the trial position, fed back as features, inherits it).
+SLACK_BF16 = 2.0**-17
 
 
 @pytest.mark.parametrize("flags", [0, FLAG_LEARNED_UMMA], ids=["mma_sync", "tcgen05"])
