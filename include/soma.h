@@ -524,11 +524,12 @@ soma_status soma_batch_get_timing(soma_batch_t* b, soma_timing* out);
 /* S(q) for callers that cannot allocate device memory.
  *
  * The paper has no counterpart: this is a library convenience.  It computes
- * exactly what soma_structure_factor computes, but allocates nothing: no
- * cudaMalloc, no cudaFree, no host heap.  It is meant for code that cannot
- * allocate at the moment it wants S(q), e.g. an analysis hook inside a host
- * application whose memory pool owns all free device memory, or code that
- * must not synchronise the device (cudaMalloc and cudaFree may).
+ * exactly what soma_structure_factor computes, but allocates nothing after
+ * its first call on a device (below): no cudaMalloc, no cudaFree, no host
+ * heap, on success or failure.  It is meant for code that cannot allocate at
+ * the moment it wants S(q), e.g. an analysis hook inside a host application
+ * whose memory pool owns all free device memory, or code that must not
+ * synchronise the device (cudaMalloc and cudaFree may).
  *
  * desc:     the system (validated like soma_create; desc->stream is ignored).
  * density:  device pointer to the packed occupation numbers of that system
@@ -538,12 +539,20 @@ soma_status soma_batch_get_timing(soma_batch_t* b, soma_timing* out);
  * stream:   cudaStream_t to run on (NULL: legacy default stream).
  *
  * Scratch (twiddle tables and block partial sums, about 768 KB) lives in one
- * file-scope device array of libsoma, which every GPU that loads the library
- * holds until the process exits.  The first call on a device looks up that
- * array's device address (once per device); make it before any stream
- * capture.  All calls share the array: two calls that overlap on the GPU
- * (different streams, or different host threads without ordering) race and
- * may return wrong values.  Every call overwrites all of the scratch it reads.
+ * file-scope device array of libsoma.  The first call on each device sets it
+ * up: it looks up the array's device address, and with CUDA's lazy module
+ * loading (the default) that lookup is what loads this part of the library
+ * onto the device and allocates the array there -- so make the first call
+ * at a time when device memory can still be allocated (for instance right
+ * after soma_create) and before any stream capture.  The address is kept for
+ * the rest of the process: after a cudaDeviceReset of that device the kept
+ * address is stale and this entry point must not be called on it again.  The
+ * array stays allocated on every device that made a call until the process
+ * exits.  Every call synchronises its stream before returning (the results
+ * are copied to the host array out).  All calls share the array: two calls
+ * that overlap on the GPU (different streams, or different host threads
+ * without ordering) race and may return wrong values.  Every call overwrites
+ * all of the scratch it reads.
  * Returns SOMA_EINVAL when k exceeds SOMA_SQ_NOALLOC_MAX_K or grid_x + grid_y +
  * grid_z exceeds SOMA_SQ_NOALLOC_MAX_AXES, and SOMA_ECUDA on a CUDA error. */
 #define SOMA_SQ_NOALLOC_MAX_K 32

@@ -27,18 +27,29 @@ using namespace soma;
 
 namespace {
 
-thread_local std::string g_last_error;
+// Message of the last failing call on this thread: a fixed buffer, so that
+// reporting an error allocates nothing either.
+constexpr size_t ERR_LEN = 512;
+thread_local char g_last_error[ERR_LEN] = "";
 
 soma_status fail(soma_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
 soma_status fail(soma_status st, const char* fmt, ...) {
-  char buf[512];
+  char buf[ERR_LEN];
   va_list ap;
   va_start(ap, fmt);
   vsnprintf(buf, sizeof buf, fmt, ap);
   va_end(ap);
-  g_last_error = buf;
+  memcpy(g_last_error, buf, ERR_LEN);
   return st;
 }
+
+// Keeps the current message across cleanup calls that may report errors of
+// their own (restored when the guard goes out of scope).
+struct KeepError {
+  char saved[ERR_LEN];
+  KeepError() { memcpy(saved, g_last_error, ERR_LEN); }
+  ~KeepError() { memcpy(g_last_error, saved, ERR_LEN); }
+};
 
 soma_status cuda_fail(cudaError_t e, const char* what) {
   // a failed call also leaves its error as the runtime's "last error"; clear
@@ -490,7 +501,7 @@ extern "C" {
 
 int soma_abi_version(void) { return SOMA_ABI_VERSION; }
 
-const char* soma_last_error(void) { return g_last_error.c_str(); }
+const char* soma_last_error(void) { return g_last_error; }
 
 soma_status soma_create(const soma_system_desc* desc, soma_t** out) {
   if (!out) return fail(SOMA_EINVAL, "out is NULL");
@@ -576,7 +587,7 @@ soma_status soma_create(const soma_system_desc* desc, soma_t** out) {
 #undef CK
   st = update_fields(h);
   if (st == SOMA_OK) st = sync(h);
-  if (st != SOMA_OK) { std::string m = g_last_error; release(h); g_last_error = m; return st; }
+  if (st != SOMA_OK) { KeepError keep; release(h); return st; }
   *out = h;
   return SOMA_OK;
 }
@@ -1549,10 +1560,10 @@ soma_status soma_batch_create(const soma_system_desc* descs, uint32_t n, void* s
     soma_t* h = nullptr;
     soma_status st = soma_create(&d, &h);
     if (st != SOMA_OK) {
-      std::string m = g_last_error;
+      char m[ERR_LEN];
+      memcpy(m, g_last_error, ERR_LEN);
       batch_release(b);
-      g_last_error = "batch member " + std::to_string(k) + ": " + m;
-      return st;
+      return fail(st, "batch member %u: %s", k, m);
     }
     h->batched = true;
     b->sys.push_back(h);
@@ -1594,7 +1605,7 @@ soma_status soma_batch_create(const soma_system_desc* descs, uint32_t n, void* s
   const int fit = batch_kernel_blocks_per_sm(b->block, b->grid_dtype);
   b->blocks_per_sm = fit < 1 ? 1 : (fit < 3 ? fit : 3);
   soma_status st = batch_items(b, b->item_tiles);
-  if (st != SOMA_OK) { std::string m = g_last_error; batch_release(b); g_last_error = m; return st; }
+  if (st != SOMA_OK) { KeepError keep; batch_release(b); return st; }
   *out = b;
   return SOMA_OK;
 }

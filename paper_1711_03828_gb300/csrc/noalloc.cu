@@ -6,9 +6,11 @@
 // application whose memory pool already owns the GPU's free memory, or code
 // that must not synchronise the device (cudaMalloc and cudaFree may).  For
 // them, soma_structure_factor_noalloc keeps that scratch in one file-scope
-// device array (allocated by the CUDA runtime when the library is loaded,
-// held by every GPU that loads the library until the process exits) and
-// takes every input and output from the caller.
+// device array and takes every input and output from the caller.  The CUDA
+// runtime allocates the array on a device when this module is loaded there:
+// with lazy module loading (the default) that happens in the first call on
+// the device, through cudaGetSymbolAddress, so the first call per device is
+// the one that may allocate; the array is then held until the process exits.
 #include <mutex>
 
 #include "kernels.h"
@@ -57,6 +59,8 @@ double* g_scratch_ptr[64] = {nullptr};
 
 // Device address of the scratch array for the current device, looked up once
 // per device (the name is only a host-side stand-in for the device symbol).
+// The address is kept for the life of the process: a cudaDeviceReset of the
+// device would make it stale (the entry point's documentation excludes that).
 cudaError_t scratch_for_current_device(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -46,6 +46,28 @@ def test_noalloc_structure_factor_matches_allocating_entry_point(cuda_device):
     s.close()
 
 
+def test_noalloc_calls_after_the_first_allocate_no_device_memory(cuda_device):
+    """The first call on a device loads the scratch array (lazy module
+    loading); every later call leaves the device's free memory unchanged."""
+    import torch
+    d = workloads.melt_small(chiN=30.0)
+    s = System(d)
+    s.sweep(5)
+    dens = torch.empty(d.cells, dtype=torch.int32, device=cuda_device)
+    s.get_density(out=dens)
+    torch.cuda.synchronize()
+    c = d.to_c()
+    ms = np.random.default_rng(5).integers(-6, 7, (32, 3))
+    first = _noalloc(c, dens, ms)
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        again = _noalloc(c, dens, ms)
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    np.testing.assert_array_equal(again, first)
+    s.close()
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(cuda_device):
     import torch
     d = workloads.melt_small()
