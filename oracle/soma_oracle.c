@@ -437,14 +437,13 @@ static void or_move_uniform_w(const or_system* s, float* x, float* y, float* z,
                               float* trial, uint64_t* acc, uint64_t* ties) {
   const uint32_t N = s->N;
   const uint64_t m = chain * N + i;
-  /* trial position: each displacement component a*v rounded to FP32, then the
-   * sum rounded to FP32 (the stored precision of positions) */
+  /* trial position: r + a*v rounded once to FP32 (the stored precision of
+   * positions); fmaf rounds the exact value of the fused multiply-add */
   double r_old[3] = { x[m], y[m], z[m] };
   double r_new[3];
-  for (int d = 0; d < 3; ++d) {
-    float dx = (float)((double)s->a32 * or_uniform_sym(w[d]));
-    r_new[d] = (double)(float)(r_old[d] + (double)dx);
-  }
+  const float pos[3] = { x[m], y[m], z[m] };
+  for (int d = 0; d < 3; ++d)
+    r_new[d] = (double)fmaf(s->a32, (float)or_uniform_sym(w[d]), pos[d]);
   double u = or_uniform_open(w[3]);
   if (trial) {
     const uint64_t M = s->n_chains * N;

@@ -67,11 +67,11 @@ __global__ void __launch_bounds__(256, 3) sweep_batch_kernel(const BatchArgs p) 
         pz = __ldcs(reinterpret_cast<const float2*>(S.z + bn));
       }
       if (tile < S.full_tiles)
-        my_acc += pair_tile<WT, uint32_t, false>(S.g, p.keys, L, S.x, S.y, S.z, nacc, base, base,
+        my_acc += pair_tile<WT, uint32_t, false, false>(S.g, p.keys, L, S.x, S.y, S.z, nacc, base, base,
                                                  true, sweep, ctr3, S.set_order_random, S.a, S.K_b, x0,
                                                  x1, y0, y1, z0, z1);
       else
-        my_acc += pair_tile<WT, uint32_t, true>(S.g, p.keys, L, S.x, S.y, S.z, nacc, base, base,
+        my_acc += pair_tile<WT, uint32_t, true, false>(S.g, p.keys, L, S.x, S.y, S.z, nacc, base, base,
                                                 valid, sweep, ctr3, S.set_order_random, S.a, S.K_b, x0,
                                                 x1, y0, y1, z0, z1);
     }

@@ -158,6 +158,47 @@ __device__ __forceinline__ uint32_t cell_of(const Geom& g, float x, float y, flo
   return min((cz * (uint32_t)g.ny + cy) * (uint32_t)g.nx + cx, g.cells - 1u);
 }
 
+// Cell of the floor bits fb = bits of __fadd_rd(x, 1.5*2^23) per axis (the
+// first step of fold_raw done by the caller).  WIDE: every axis has at least
+// two cells, so the bias is added without the multiplier s (an integer add on
+// the ALU instead of a multiply-add on the FMA pipe); otherwise as fold_raw.
+template <bool WIDE>
+__device__ __forceinline__ uint32_t cell_of_floor_bits(const Geom& g, uint32_t fbx, uint32_t fby,
+                                                       uint32_t fbz) {
+  uint32_t c[3];
+  const uint32_t fb[3] = {fbx, fby, fbz};
+  const uint32_t n[3] = {(uint32_t)g.nx, (uint32_t)g.ny, (uint32_t)g.nz};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const uint32_t b = WIDE ? fb[k] + g.fold_b[k] : fb[k] * g.fold_s[k] + g.fold_b[k];
+    c[k] = b - __umulhi(b, g.fold_m[k]) * n[k];
+  }
+  return min((c[2] * n[1] + c[1]) * n[0] + c[0], g.cells - 1u);
+}
+
+// Two FP32 values in one 64-bit register pair for the packed FP32x2
+// instructions of sm_100 and later: each half is rounded exactly as the
+// scalar instruction with the same rounding mode rounds it.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_add_rm(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_fma_rn(unsigned long long a, unsigned long long b,
+                                                        unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // Philox4x32-10 with the round keys taken from the kernel parameters (the
 // key schedule is the same for every thread, so it is computed once on the
 // host and read from the constant bank).

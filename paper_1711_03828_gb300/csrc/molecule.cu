@@ -72,9 +72,9 @@ __device__ __forceinline__ void molecule_body(const SweepArgs& p, const TopoArgs
         const uint4 r = philox_rk(make_uint4((uint32_t)id, (uint32_t)(id >> 32), sweep, ctr3), p.g);
         const uint32_t i = ((r.w & 0xFFu) * N) >> 8;
         const float xo = X[i], yo = Y[i], zo = Z[i];
-        const float xn = __fadd_rn(xo, __fmul_rn(a, uniform_sym(r.x)));
-        const float yn = __fadd_rn(yo, __fmul_rn(a, uniform_sym(r.y)));
-        const float zn = __fadd_rn(zo, __fmul_rn(a, uniform_sym(r.z)));
+        const float xn = __fmaf_rn(a, uniform_sym(r.x), xo);
+        const float yn = __fmaf_rn(a, uniform_sym(r.y), yo);
+        const float zn = __fmaf_rn(a, uniform_sym(r.z), zo);
         float dEf;
         if (MULTI) {
           const uint32_t ty = __ldg(tp.ttab + (uint32_t)__ldg(tp.mol_arch + chain) * 64u + i);

@@ -70,7 +70,7 @@ struct PairLane {
 // s, i.e. as an exact zero; the acceptance test is dE <= -ln u, which is the
 // rule "dE <= 0 or ln u < -dE" for every ln u < 0 except on the measure-zero
 // set dE = -ln u.
-template <typename WT, typename IDX, bool PARTIAL>
+template <typename WT, typename IDX, bool PARTIAL, bool WIDE>
 __device__ __forceinline__ unsigned pair_tile(const Geom& g, const Geom& keys, const PairLane<WT>& L,
                                               float* __restrict__ px, float* __restrict__ py,
                                               float* __restrict__ pz, uint32_t* __restrict__ nacc,
@@ -85,23 +85,55 @@ __device__ __forceinline__ unsigned pair_tile(const Geom& g, const Geom& keys, c
   const IDX m1 = cbase + 1u;
   const uint32_t hi1 = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)m1 >> 32) : 0u;
   const uint4 r1 = philox_rk(make_uint4((uint32_t)m1, hi1, sweep, ctr3), keys);
-  const float xn0 = __fadd_rn(x0, __fmul_rn(a, uniform_sym(r0.x)));
-  const float yn0 = __fadd_rn(y0, __fmul_rn(a, uniform_sym(r0.y)));
-  const float zn0 = __fadd_rn(z0, __fmul_rn(a, uniform_sym(r0.z)));
-  const float xn1 = __fadd_rn(x1, __fmul_rn(a, uniform_sym(r1.x)));
-  const float yn1 = __fadd_rn(y1, __fmul_rn(a, uniform_sym(r1.y)));
-  const float zn1 = __fadd_rn(z1, __fmul_rn(a, uniform_sym(r1.z)));
-  const uint32_t c0 = cell_of(g, x0, y0, z0);
-  const uint32_t c1 = cell_of(g, x1, y1, z1);
-  const uint32_t cn0 = cell_of(g, xn0, yn0, zn0);
-  const uint32_t cn1 = cell_of(g, xn1, yn1, zn1);
+  // Both slots at once with the packed FP32x2 instructions: the symmetric
+  // uniforms k 2^-23 + (2^-24 - 1) (one rounding), the trial positions
+  // r + a v (one rounding, a fused multiply-add), and the floor bits of the
+  // cell fold (sum with 1.5 2^23 rounded toward -inf) -- bit for bit the
+  // scalar arithmetic of uniform_sym, __fmaf_rn and fold_raw.
+  const unsigned long long S = f2_pack(1.1920928955078125e-7f, 1.1920928955078125e-7f);
+  const unsigned long long C = f2_pack(-0.99999994039535522461f, -0.99999994039535522461f);
+  const unsigned long long A2 = f2_pack(a, a);
+  const unsigned long long MAG = f2_pack(12582912.0f, 12582912.0f);
+  const unsigned long long X = f2_pack(x0, x1), Y = f2_pack(y0, y1), Z = f2_pack(z0, z1);
+  const unsigned long long XN = f2_fma_rn(
+      A2, f2_fma_rn(f2_pack(__uint2float_rn(r0.x >> 8), __uint2float_rn(r1.x >> 8)), S, C), X);
+  const unsigned long long YN = f2_fma_rn(
+      A2, f2_fma_rn(f2_pack(__uint2float_rn(r0.y >> 8), __uint2float_rn(r1.y >> 8)), S, C), Y);
+  const unsigned long long ZN = f2_fma_rn(
+      A2, f2_fma_rn(f2_pack(__uint2float_rn(r0.z >> 8), __uint2float_rn(r1.z >> 8)), S, C), Z);
+  float xn0, xn1, yn0, yn1, zn0, zn1;
+  f2_unpack(XN, xn0, xn1);
+  f2_unpack(YN, yn0, yn1);
+  f2_unpack(ZN, zn0, zn1);
+  float fx0, fx1, fy0, fy1, fz0, fz1, gx0, gx1, gy0, gy1, gz0, gz1;
+  f2_unpack(f2_add_rm(X, MAG), fx0, fx1);
+  f2_unpack(f2_add_rm(Y, MAG), fy0, fy1);
+  f2_unpack(f2_add_rm(Z, MAG), fz0, fz1);
+  f2_unpack(f2_add_rm(XN, MAG), gx0, gx1);
+  f2_unpack(f2_add_rm(YN, MAG), gy0, gy1);
+  f2_unpack(f2_add_rm(ZN, MAG), gz0, gz1);
+  const uint32_t c0 = cell_of_floor_bits<WIDE>(g, __float_as_uint(fx0), __float_as_uint(fy0),
+                                               __float_as_uint(fz0));
+  const uint32_t c1 = cell_of_floor_bits<WIDE>(g, __float_as_uint(fx1), __float_as_uint(fy1),
+                                               __float_as_uint(fz1));
+  const uint32_t cn0 = cell_of_floor_bits<WIDE>(g, __float_as_uint(gx0), __float_as_uint(gy0),
+                                                __float_as_uint(gz0));
+  const uint32_t cn1 = cell_of_floor_bits<WIDE>(g, __float_as_uint(gx1), __float_as_uint(gy1),
+                                                __float_as_uint(gz1));
   float dEf0 = 0.f, dEf1 = 0.f;
   if (valid) {
     dEf0 = load_w<WT>(L.w0, cn0) - load_w<WT>(L.w0, c0);
     dEf1 = load_w<WT>(L.w1, cn1) - load_w<WT>(L.w1, c1);
   }
-  const float lnu0 = log_uniform_open(r0.w);
-  const float lnu1 = log_uniform_open(r1.w);
+  float lnu0, lnu1;
+  {  // ln of the open uniforms (k + 1/2) 2^-24 of both slots
+    float u0, u1;
+    f2_unpack(f2_fma_rn(f2_pack(__uint2float_rn(r0.w >> 8), __uint2float_rn(r1.w >> 8)),
+                        f2_pack(5.9604644775390625e-8f, 5.9604644775390625e-8f),
+                        f2_pack(2.98023223876953125e-8f, 2.98023223876953125e-8f)), u0, u1);
+    lnu0 = __logf(u0);
+    lnu1 = __logf(u1);
+  }
   const bool sw = set_order_random && (__shfl_sync(FULL, r0.w, L.first_lane) & 1u);
 
   // A moves first, B second.

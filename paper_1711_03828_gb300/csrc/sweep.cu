@@ -12,8 +12,8 @@
 // Per particle: one Philox4x32-10 draw (counter = particle, sweep) gives the
 // three displacement uniforms and the acceptance uniform; the set order of a
 // chain is bit 0 of the acceptance word of its first particle.  The trial
-// position is rounded exactly like the stored FP32 state (mul then add, both
-// round-to-nearest, no contraction).  The two field values omega_t(c) and
+// position r + a v is rounded once to the stored FP32 precision (a fused
+// multiply-add, round-to-nearest).  The two field values omega_t(c) and
 // omega_t(c') are gathered from the L2-resident omega planes before the set
 // loop since c' does not depend on the neighbours.  After both sets the final
 // cells are added to the packed occupation grid n[(s+1)&1] with 32-bit
@@ -122,9 +122,9 @@ __global__ void __launch_bounds__(256) sweep_uniform_kernel(const SweepArgs p) {
     for (int j = 0; j < S; ++j) {
       const uint64_t m = base + j + p.g.id_base;
       const uint4 r = philox_rk(make_uint4((uint32_t)m, (uint32_t)(m >> 32), sweep, ctr3), p.g);
-      xn[j] = __fadd_rn(x[j], __fmul_rn(p.a, uniform_sym(r.x)));
-      yn[j] = __fadd_rn(y[j], __fmul_rn(p.a, uniform_sym(r.y)));
-      zn[j] = __fadd_rn(z[j], __fmul_rn(p.a, uniform_sym(r.z)));
+      xn[j] = __fmaf_rn(p.a, uniform_sym(r.x), x[j]);
+      yn[j] = __fmaf_rn(p.a, uniform_sym(r.y), y[j]);
+      zn[j] = __fmaf_rn(p.a, uniform_sym(r.z), z[j]);
       lnu[j] = log_uniform_open(r.w);
       lowbits |= (r.w & 1u) << j;
       co[j] = cell_of(p.g, x[j], y[j], z[j]);
@@ -236,6 +236,7 @@ __global__ void __launch_bounds__(256, 3) sweep_pair_kernel(const SweepArgs p) {
   const uint32_t TN = p.G * p.g.N;
   const uint32_t full_tiles = (uint32_t)p.full_tiles;
   auto lane_ok = [&](uint32_t t) { return t < full_tiles || L.li0 < p.last_rows; };
+  const bool wide = p.g.nx > 1 && p.g.ny > 1 && p.g.nz > 1;
 
   float2 px = make_float2(0.f, 0.f), py = px, pz = px;
   if (warp0 < t_end && lane_ok(warp0)) {
@@ -263,14 +264,18 @@ __global__ void __launch_bounds__(256, 3) sweep_pair_kernel(const SweepArgs p) {
       Lt.set_types((seq >> L.ci0) & 1ull, (seq >> (L.ci0 + 1u)) & 1ull, p.wA, p.wB);
     }
     const IDX cbase = base + (IDX)p.g.id_base;
-    if (tile < full_tiles)
-      my_acc += pair_tile<WT, IDX, false>(p.g, p.g, Lt, p.x, p.y, p.z, nacc, base, cbase, true, sweep,
-                                          ctr3, p.set_order_random, p.a, p.K_b, x0, x1, y0, y1, z0,
-                                          z1);
+    if (tile < full_tiles && wide)
+      my_acc += pair_tile<WT, IDX, false, true>(p.g, p.g, Lt, p.x, p.y, p.z, nacc, base, cbase, true,
+                                                sweep, ctr3, p.set_order_random, p.a, p.K_b, x0, x1,
+                                                y0, y1, z0, z1);
+    else if (tile < full_tiles)
+      my_acc += pair_tile<WT, IDX, false, false>(p.g, p.g, Lt, p.x, p.y, p.z, nacc, base, cbase, true,
+                                                 sweep, ctr3, p.set_order_random, p.a, p.K_b, x0,
+                                                 x1, y0, y1, z0, z1);
     else
-      my_acc += pair_tile<WT, IDX, true>(p.g, p.g, Lt, p.x, p.y, p.z, nacc, base, cbase, valid, sweep,
-                                         ctr3, p.set_order_random, p.a, p.K_b, x0, x1, y0, y1, z0,
-                                         z1);
+      my_acc += pair_tile<WT, IDX, true, false>(p.g, p.g, Lt, p.x, p.y, p.z, nacc, base, cbase, valid,
+                                                sweep, ctr3, p.set_order_random, p.a, p.K_b, x0, x1,
+                                                y0, y1, z0, z1);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) my_acc += __shfl_xor_sync(FULL, my_acc, o);

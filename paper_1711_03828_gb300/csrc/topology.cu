@@ -186,9 +186,9 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
       const IDX mc = m + (IDX)p.g.id_base;
       const uint32_t hi = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)mc >> 32) : 0u;
       const uint4 r = philox_rk(make_uint4((uint32_t)mc, hi, sweep, ctr3), p.g);
-      const float xn = __fadd_rn(x[j], __fmul_rn(p.a, uniform_sym(r.x)));
-      const float yn = __fadd_rn(y[j], __fmul_rn(p.a, uniform_sym(r.y)));
-      const float zn = __fadd_rn(z[j], __fmul_rn(p.a, uniform_sym(r.z)));
+      const float xn = __fmaf_rn(p.a, uniform_sym(r.x), x[j]);
+      const float yn = __fmaf_rn(p.a, uniform_sym(r.y), y[j]);
+      const float zn = __fmaf_rn(p.a, uniform_sym(r.z), z[j]);
       const uint32_t co = cell_of(p.g, x[j], y[j], z[j]);
       const uint32_t cn = cell_of(p.g, xn, yn, zn);
       // type: the architecture's type byte (n_t types) or the A/B bit

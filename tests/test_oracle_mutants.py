@@ -118,6 +118,9 @@ MUTANTS = [
      "order[0] = 1u - first;\n    order[1] = first;", TOPO.check_linear_topology_is_the_linear_chain),
     ("topo_bond_counted_twice", "if (j <= i) continue;", "if (j == i) continue;",
      TOPO.check_topology_observables_hand_values),
+    ("trial_rounded_twice", "r_new[d] = (double)fmaf(s->a32, (float)or_uniform_sym(w[d]), pos[d]);",
+     "r_new[d] = (double)(float)(r_old[d] + (double)(float)((double)s->a32 * or_uniform_sym(w[d])));",
+     PIN.check_sweep_moves_follow_the_draws),
     # the BF16 reading of the learned proposal's network
     ("bf16_inputs_not_rounded", "xb[k] = or_round_bf16((float)x[k]);", "xb[k] = x[k];",
      BF16.check_bf16_network_closed_form),

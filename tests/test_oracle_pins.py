@@ -361,7 +361,22 @@ def test_architecture_mixture(oracle_lib):
 # --------------------------------------------------------------------------
 # Sweep mechanics: displacements bounded by a, accepted moves land on the draw
 # --------------------------------------------------------------------------
+def _f32_nearest(q):
+    """The FP32 value nearest to the rational q (ties to the even significand),
+    found from exact rational distances rather than by floating-point rounding."""
+    from fractions import Fraction
+    t = np.float32(float(q))
+    best = None
+    for c in (np.nextafter(t, np.float32(-np.inf)), t, np.nextafter(t, np.float32(np.inf))):
+        dist = abs(Fraction(float(c)) - q)
+        even = (int(np.array(c, np.float32).view(np.uint32)) & 1) == 0
+        if best is None or dist < best[0] or (dist == best[0] and even):
+            best = (dist, c)
+    return best[1]
+
+
 def check_sweep_moves_follow_the_draws(lib=None):
+    from fractions import Fraction
     d = workloads.melt_small(n_chains=64)
     s = oracle_system(d, lib)
     p = s.init_chains()
@@ -372,8 +387,9 @@ def check_sweep_moves_follow_the_draws(lib=None):
     a32 = float(np.float32(s.params.a32))
     for k in range(d.M):
         w = s.draw(1, k, 3)
-        prop = [np.float32(np.float64(getattr(before, ax)[k]) +
-                           np.float64(np.float32(a32 * (((int(w[j]) >> 8) * 2 + 1) / 2**24 - 1))))
+        # r + a v rounded once: the exact rational sum, rounded to FP32
+        prop = [_f32_nearest(Fraction(float(getattr(before, ax)[k])) + Fraction(a32) *
+                             (Fraction((int(w[j]) >> 8) * 2 + 1, 2**24) - 1))
                 for j, ax in enumerate("xyz")]
         now = [getattr(p, ax)[k] for ax in "xyz"]
         old = [getattr(before, ax)[k] for ax in "xyz"]
