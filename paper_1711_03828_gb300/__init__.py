@@ -99,7 +99,12 @@ def topology_sets(words, starts, N):
 
 
 class System:
-    """One SCMF system on the GPU (owns a ``soma_t``, or borrows one from a Batch)."""
+    """One SCMF system on the GPU (owns a ``soma_t``, or borrows one from a Batch).
+
+    stream: the torch CUDA stream the handle runs on.  None -- or torch's
+    default stream, whose handle is NULL -- gives the handle a stream of its
+    own, which torch's operations are not ordered with: synchronise (or pass
+    a stream of your own) before torch reads what the handle wrote."""
 
     def __init__(self, desc: SystemDesc, stream=None, _borrowed=None):
         self.desc = desc

@@ -59,27 +59,35 @@ struct PairLane {
   }
 };
 
-// Moves the pair (x0,y0,z0), (x1,y1,z1) held by this lane (particles base and
-// base+1, drawing with the counter indices cbase and cbase+1), stores the
-// result and counts the final cells into nacc.  g gives the cell fold, keys
-// the Philox round keys.  PARTIAL: the tile may hold
-// fewer rows than lanes (valid says whether this lane's pair exists).
-// Returns this lane's accepted moves.
+// One tile of the paired sweep in two stages, so that a warp can issue the
+// field gathers of its next tile before it finishes the current one:
+//   pair_prepare: the draws of the pair (particles base and base+1, counter
+//     indices cbase and cbase+1), its trial positions and the cells of the old
+//     and trial positions, and the loads of the four field values (issued
+//     here, used in pair_finish);
+//   pair_finish: the acceptance uniforms, the chain's set order, both SET
+//     phases, the stores and the occupation count.
+// pair_tile runs both back to back.  valid says whether this lane's pair
+// exists (the tile may hold fewer rows than lanes).
 //
 // Exactness notes: a missing bond partner enters as 0 * (A - s) with a finite
 // s, i.e. as an exact zero; the acceptance test is dE <= -ln u, which is the
 // rule "dE <= 0 or ln u < -dE" for every ln u < 0 except on the measure-zero
 // set dE = -ln u.
-template <typename WT, typename IDX, bool PARTIAL, bool WIDE>
-__device__ __forceinline__ unsigned pair_tile(const Geom& g, const Geom& keys, const PairLane<WT>& L,
-                                              float* __restrict__ px, float* __restrict__ py,
-                                              float* __restrict__ pz, uint32_t* __restrict__ nacc,
-                                              IDX base, IDX cbase, bool valid, uint32_t sweep,
-                                              uint32_t ctr3,
-                                              bool set_order_random, float a, float K1, float x0,
-                                              float x1, float y0, float y1, float z0, float z1) {
-  if (!PARTIAL) valid = true;
-  const float K2 = 2.f * K1;
+struct PairState {
+  float x0, x1, y0, y1, z0, z1;        // positions
+  float xn0, xn1, yn0, yn1, zn0, zn1;  // trial positions
+  uint32_t c0, c1, cn0, cn1;           // old and trial cells
+  float wn0, wo0, wn1, wo1;            // omega at the trial and old cells
+  uint32_t u0, u1;                     // draw words of the acceptance uniforms
+  bool valid;
+};
+
+template <typename WT, typename IDX, bool WIDE>
+__device__ __forceinline__ void pair_prepare(const Geom& g, const Geom& keys, const PairLane<WT>& L,
+                                             IDX cbase, bool valid, uint32_t sweep, uint32_t ctr3,
+                                             float a, float x0, float x1, float y0, float y1,
+                                             float z0, float z1, PairState& P) {
   const uint32_t hi = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)cbase >> 32) : 0u;
   const uint4 r0 = philox_rk(make_uint4((uint32_t)cbase, hi, sweep, ctr3), keys);
   const IDX m1 = cbase + 1u;
@@ -101,10 +109,9 @@ __device__ __forceinline__ unsigned pair_tile(const Geom& g, const Geom& keys, c
       A2, f2_fma_rn(f2_pack(__uint2float_rn(r0.y >> 8), __uint2float_rn(r1.y >> 8)), S, C), Y);
   const unsigned long long ZN = f2_fma_rn(
       A2, f2_fma_rn(f2_pack(__uint2float_rn(r0.z >> 8), __uint2float_rn(r1.z >> 8)), S, C), Z);
-  float xn0, xn1, yn0, yn1, zn0, zn1;
-  f2_unpack(XN, xn0, xn1);
-  f2_unpack(YN, yn0, yn1);
-  f2_unpack(ZN, zn0, zn1);
+  f2_unpack(XN, P.xn0, P.xn1);
+  f2_unpack(YN, P.yn0, P.yn1);
+  f2_unpack(ZN, P.zn0, P.zn1);
   float fx0, fx1, fy0, fy1, fz0, fz1, gx0, gx1, gy0, gy1, gz0, gz1;
   f2_unpack(f2_add_rm(X, MAG), fx0, fx1);
   f2_unpack(f2_add_rm(Y, MAG), fy0, fy1);
@@ -112,29 +119,46 @@ __device__ __forceinline__ unsigned pair_tile(const Geom& g, const Geom& keys, c
   f2_unpack(f2_add_rm(XN, MAG), gx0, gx1);
   f2_unpack(f2_add_rm(YN, MAG), gy0, gy1);
   f2_unpack(f2_add_rm(ZN, MAG), gz0, gz1);
-  const uint32_t c0 = cell_of_floor_bits<WIDE>(g, __float_as_uint(fx0), __float_as_uint(fy0),
-                                               __float_as_uint(fz0));
-  const uint32_t c1 = cell_of_floor_bits<WIDE>(g, __float_as_uint(fx1), __float_as_uint(fy1),
-                                               __float_as_uint(fz1));
-  const uint32_t cn0 = cell_of_floor_bits<WIDE>(g, __float_as_uint(gx0), __float_as_uint(gy0),
-                                                __float_as_uint(gz0));
-  const uint32_t cn1 = cell_of_floor_bits<WIDE>(g, __float_as_uint(gx1), __float_as_uint(gy1),
-                                                __float_as_uint(gz1));
-  float dEf0 = 0.f, dEf1 = 0.f;
+  P.c0 = cell_of_floor_bits<WIDE>(g, __float_as_uint(fx0), __float_as_uint(fy0), __float_as_uint(fz0));
+  P.c1 = cell_of_floor_bits<WIDE>(g, __float_as_uint(fx1), __float_as_uint(fy1), __float_as_uint(fz1));
+  P.cn0 = cell_of_floor_bits<WIDE>(g, __float_as_uint(gx0), __float_as_uint(gy0), __float_as_uint(gz0));
+  P.cn1 = cell_of_floor_bits<WIDE>(g, __float_as_uint(gx1), __float_as_uint(gy1), __float_as_uint(gz1));
+  P.wn0 = P.wo0 = P.wn1 = P.wo1 = 0.f;
   if (valid) {
-    dEf0 = load_w<WT>(L.w0, cn0) - load_w<WT>(L.w0, c0);
-    dEf1 = load_w<WT>(L.w1, cn1) - load_w<WT>(L.w1, c1);
+    P.wn0 = load_w<WT>(L.w0, P.cn0);
+    P.wo0 = load_w<WT>(L.w0, P.c0);
+    P.wn1 = load_w<WT>(L.w1, P.cn1);
+    P.wo1 = load_w<WT>(L.w1, P.c1);
   }
+  P.x0 = x0; P.x1 = x1; P.y0 = y0; P.y1 = y1; P.z0 = z0; P.z1 = z1;
+  P.u0 = r0.w;
+  P.u1 = r1.w;
+  P.valid = valid;
+}
+
+// Returns this lane's accepted moves.
+template <typename WT, typename IDX>
+__device__ __forceinline__ unsigned pair_finish(const PairLane<WT>& L, float* __restrict__ px,
+                                                float* __restrict__ py, float* __restrict__ pz,
+                                                uint32_t* __restrict__ nacc, IDX base,
+                                                const PairState& P, bool set_order_random,
+                                                float K1) {
+  const bool valid = P.valid;
+  const float K2 = 2.f * K1;
+  const float x0 = P.x0, x1 = P.x1, y0 = P.y0, y1 = P.y1, z0 = P.z0, z1 = P.z1;
+  const float xn0 = P.xn0, xn1 = P.xn1, yn0 = P.yn0, yn1 = P.yn1, zn0 = P.zn0, zn1 = P.zn1;
+  const uint32_t c0 = P.c0, c1 = P.c1, cn0 = P.cn0, cn1 = P.cn1;
+  const float dEf0 = P.wn0 - P.wo0, dEf1 = P.wn1 - P.wo1;
   float lnu0, lnu1;
   {  // ln of the open uniforms (k + 1/2) 2^-24 of both slots
     float u0, u1;
-    f2_unpack(f2_fma_rn(f2_pack(__uint2float_rn(r0.w >> 8), __uint2float_rn(r1.w >> 8)),
+    f2_unpack(f2_fma_rn(f2_pack(__uint2float_rn(P.u0 >> 8), __uint2float_rn(P.u1 >> 8)),
                         f2_pack(5.9604644775390625e-8f, 5.9604644775390625e-8f),
                         f2_pack(2.98023223876953125e-8f, 2.98023223876953125e-8f)), u0, u1);
     lnu0 = __logf(u0);
     lnu1 = __logf(u1);
   }
-  const bool sw = set_order_random && (__shfl_sync(FULL, r0.w, L.first_lane) & 1u);
+  const bool sw = set_order_random && (__shfl_sync(FULL, P.u0, L.first_lane) & 1u);
 
   // A moves first, B second.
   float Ax = sw ? x1 : x0, Ay = sw ? y1 : y0, Az = sw ? z1 : z0;
@@ -199,6 +223,20 @@ __device__ __forceinline__ unsigned pair_tile(const Geom& g, const Geom& keys, c
     if (!same) atomicAdd(nacc + cB, vB);
   }
   return acc_count;
+}
+
+template <typename WT, typename IDX, bool PARTIAL, bool WIDE>
+__device__ __forceinline__ unsigned pair_tile(const Geom& g, const Geom& keys, const PairLane<WT>& L,
+                                              float* __restrict__ px, float* __restrict__ py,
+                                              float* __restrict__ pz, uint32_t* __restrict__ nacc,
+                                              IDX base, IDX cbase, bool valid, uint32_t sweep,
+                                              uint32_t ctr3, bool set_order_random, float a,
+                                              float K1, float x0, float x1, float y0, float y1,
+                                              float z0, float z1) {
+  PairState P;
+  pair_prepare<WT, IDX, WIDE>(g, keys, L, cbase, PARTIAL ? valid : true, sweep, ctr3, a, x0, x1, y0,
+                              y1, z0, z1, P);
+  return pair_finish<WT, IDX>(L, px, py, pz, nacc, base, P, set_order_random, K1);
 }
 
 }  // namespace soma

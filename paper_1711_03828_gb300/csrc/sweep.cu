@@ -239,24 +239,21 @@ __global__ void __launch_bounds__(256, 3) sweep_pair_kernel(const SweepArgs p) {
   const bool wide = p.g.nx > 1 && p.g.ny > 1 && p.g.nz > 1;
 
   float2 px = make_float2(0.f, 0.f), py = px, pz = px;
-  if (warp0 < t_end && lane_ok(warp0)) {
-    const IDX b0 = (IDX)warp0 * TN + L.li0;
-    px = __ldcs(reinterpret_cast<const float2*>(p.x + b0));
-    py = __ldcs(reinterpret_cast<const float2*>(p.y + b0));
-    pz = __ldcs(reinterpret_cast<const float2*>(p.z + b0));
-  }
+  auto load_pos = [&](uint32_t t) {
+    if (t < t_end && lane_ok(t)) {
+      const IDX b = (IDX)t * TN + L.li0;
+      px = __ldcs(reinterpret_cast<const float2*>(p.x + b));
+      py = __ldcs(reinterpret_cast<const float2*>(p.y + b));
+      pz = __ldcs(reinterpret_cast<const float2*>(p.z + b));
+    }
+  };
+  load_pos(warp0);
   unsigned my_acc = 0;
   for (uint32_t tile = warp0; tile < t_end; tile += nwarps) {
     const bool valid = lane_ok(tile);
     const IDX base = (IDX)tile * TN + L.li0;
     const float x0 = px.x, x1 = px.y, y0 = py.x, y1 = py.y, z0 = pz.x, z1 = pz.y;
-    const uint32_t nt = tile + nwarps;
-    if (nt < t_end && lane_ok(nt)) {
-      const IDX bn = (IDX)nt * TN + L.li0;
-      px = __ldcs(reinterpret_cast<const float2*>(p.x + bn));
-      py = __ldcs(reinterpret_cast<const float2*>(p.y + bn));
-      pz = __ldcs(reinterpret_cast<const float2*>(p.z + bn));
-    }
+    load_pos(tile + nwarps);
     PairLane<WT> Lt = L;
     if (MIXED) {
       const uint64_t chain = (uint64_t)tile * p.G + L.lane_chain;

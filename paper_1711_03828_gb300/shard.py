@@ -50,9 +50,11 @@ class ShardedRun:
     ``shard_sweep`` and ``shard_fields`` taking the count buffer); cells: grid
     cells; device: where the count buffer lives (the device of the exchange);
     allreduce: sums the buffer over the ranks in place (default:
-    ``torch.distributed.all_reduce`` on the default group).  For a ``System``
-    on the GPU the shard must run on torch's current stream, so that the
-    collective is ordered after the count copy and before the field update.
+    ``torch.distributed.all_reduce`` on the default group).  When the system
+    runs on a CUDA stream of its own (``stream_handle()``), torch's current
+    stream waits for it before the collective and it waits for torch's stream
+    after, so the exchange is ordered after the count copy and before the
+    field update whichever stream the caller uses.
     """
 
     def __init__(self, system, cells: int, device="cpu", allreduce=None):
@@ -66,17 +68,31 @@ class ShardedRun:
                 dist.all_reduce(t, op=dist.ReduceOp.SUM)
         self.allreduce = allreduce
         self.cycles = 0
+        self._ext = None
+        handle = getattr(system, "stream_handle", None)
+        if self.buf.is_cuda and handle is not None and handle():
+            self._ext = torch.cuda.ExternalStream(int(handle()), device=self.buf.device)
+
+    def _exchange(self):
+        if self._ext is None:
+            self.allreduce(self.buf)
+            return
+        import torch
+        cur = torch.cuda.current_stream(self.buf.device)
+        cur.wait_stream(self._ext)
+        self.allreduce(self.buf)
+        self._ext.wait_stream(cur)
 
     def start(self):
         """Fields of the whole system from the shards' current positions."""
         self.system.shard_counts(self.buf)
-        self.allreduce(self.buf)
+        self._exchange()
         self.system.shard_fields(self.buf)
 
     def cycle(self, n: int = 1):
         """n SCMF cycles, each with its one exchange of counts."""
         for _ in range(int(n)):
             self.system.shard_sweep(self.buf)
-            self.allreduce(self.buf)
+            self._exchange()
             self.system.shard_fields(self.buf)
             self.cycles += 1

@@ -26,6 +26,17 @@ from tests.test_gpu_parity import _pos, check_decisions
 pytestmark = pytest.mark.gpu
 
 
+@pytest.fixture
+def on_stream(cuda_device):
+    """A stream of its own, current for torch during the test: the handles
+    run on it (a NULL stream would give each handle a private stream that
+    torch's operations are not ordered with)."""
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        yield st
+    st.synchronize()
+
+
 def _arch_setup(d):
     mols = [workloads.star_architecture(3, 5), workloads.ring_architecture(16),
             workloads.comb_architecture(8, 4, 2), workloads.linear_architecture(16)]
@@ -66,6 +77,7 @@ CASES = {
 
 def _shards_from_whole(d, world, setup_factory):
     st = torch.cuda.current_stream()
+    assert st.cuda_stream != 0
     setup = setup_factory(d) if setup_factory else None
     whole = System(d, stream=st)
     if setup:
@@ -97,7 +109,7 @@ def _exchange(shards, call, cells):
 
 
 @pytest.mark.parametrize("case", list(CASES))
-def test_shards_equal_the_whole_system_bit_for_bit(cuda_device, case):
+def test_shards_equal_the_whole_system_bit_for_bit(on_stream, case):
     d, setup_factory, world = CASES[case]
     whole, shards = _shards_from_whole(d, world, setup_factory)
     _exchange(shards, lambda s, b: s.shard_counts(b), d.cells)
@@ -126,7 +138,7 @@ def test_shards_equal_the_whole_system_bit_for_bit(cuda_device, case):
     whole.close()
 
 
-def test_sharded_run_one_cycle_matches_oracle(cuda_device):
+def test_sharded_run_one_cycle_matches_oracle(on_stream):
     """Two shards driven by ShardedRun (the summing done by a device add in
     place of the all-reduce) against the oracle's whole-system cycle from the
     same positions: counts bit-exact, decisions equal except at near-ties,
@@ -190,7 +202,7 @@ def test_sharded_run_one_cycle_matches_oracle(cuda_device):
         s.close()
 
 
-def test_shard_calls_are_refused_out_of_order(cuda_device):
+def test_shard_calls_are_refused_out_of_order(on_stream):
     d = workloads.melt_small(n_chains=64)
     sd = shard_desc(d, 2, 1)
     s = System(sd, stream=torch.cuda.current_stream())
