@@ -94,6 +94,7 @@ struct soma_t {
   unsigned* d_err = nullptr;                 // [0] error bits, [1] arrival counter,
                                              // [2] range flag of soma_set_positions
   double* d_scratch = nullptr;
+  float4* d_smc = nullptr;                   // smart Monte Carlo table (2 * cells), SMC only
   bool pos_invalid = false;                  // soma_set_positions was given positions out of range
   float* d_ext = nullptr;                    // external potential, 2 * cells (lazy)
   uint8_t* d_forbidden = nullptr;            // forbidden cells, cells bytes (lazy)
@@ -258,6 +259,7 @@ void release(soma_t* h) {
   cudaFree(h->d_counters);
   cudaFree(h->d_err);
   cudaFree(h->d_scratch);
+  cudaFree(h->d_smc);
   cudaFree(h->d_ext);
   cudaFree(h->d_forbidden);
   cudaFree(h->d_seq);
@@ -321,6 +323,7 @@ SweepArgs sweep_args(soma_t* h) {
   s.smc_s2A = (float)std::sqrt(2.0 * A);
   s.smc_inv4A = (float)(1.0 / (4.0 * A));
   s.learned_sigma0 = (float)(h->a64 / std::sqrt(3.0));
+  s.smc_tab = h->d_smc;
   s.err = h->d_err;
   s.seq = h->d_seq;
   s.arch = h->d_seq ? h->d_arch : nullptr;
@@ -391,10 +394,20 @@ TypesArgs types_args(soma_t* h, int after_sweep) {
   return a;
 }
 
+// the table of fields and field forces that smart Monte Carlo sweeps read,
+// after every field update of such a system
+cudaError_t launch_smc_table_of(soma_t* h) {
+  if (!h->d_smc) return cudaSuccess;
+  ++h->launches;
+  return launch_smc_table(h->g, h->w[0], h->w[1], h->d_smc, h->grid_dtype, h->sm_count, h->stream);
+}
+
 // the field update of one cycle: the packed A | B grid or the type planes
 cudaError_t launch_fields_any(soma_t* h, const FieldArgs& fa, const TypesArgs& ta) {
   if (h->n_types) return launch_fields_types(ta, h->d_err + 1, h->sm_count, h->stream);
-  return launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count, h->stream);
+  cudaError_t e = launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count, h->stream);
+  if (e == cudaSuccess) e = launch_smc_table_of(h);
+  return e;
 }
 
 cudaError_t launch_sweep_any(soma_t* h, const SweepArgs& sa) {
@@ -476,6 +489,7 @@ soma_status update_fields(soma_t* h) {
   const FieldArgs fa = field_args(h, 0);
   SOMA_CUDA(launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count, h->stream));
   ++h->launches;
+  SOMA_CUDA(launch_smc_table_of(h));
   return SOMA_OK;
 }
 
@@ -546,6 +560,7 @@ soma_status soma_create(const soma_system_desc* desc, soma_t** out) {
   ALLOC(h->mlp_m, sizeof(float) * SOMA_MLP_PARAMS);
   ALLOC(h->mlp_v, sizeof(float) * SOMA_MLP_PARAMS);
   ALLOC(h->mlp_g, sizeof(float) * SOMA_MLP_PARAMS);
+  if (desc->move == SOMA_MOVE_SMC) ALLOC(h->d_smc, sizeof(float4) * 2 * cells);
 #undef ALLOC
   h->d_out = h->d_scratch + h->scratch_doubles;
   h->shape = sweep_shape(h->g.n_chains, h->g.N, h->sm_count, h->grid_dtype, desc->move,
@@ -614,7 +629,7 @@ soma_status soma_sweep(soma_t* h, uint32_t n) {
     }
     while (n - done >= GRAPH_CHUNK) {
       SOMA_CUDA(cudaGraphLaunch(h->graph, h->stream));
-      h->launches += 2 * GRAPH_CHUNK;
+      h->launches += (h->d_smc ? 3 : 2) * GRAPH_CHUNK;
       h->t.sweep_launches += GRAPH_CHUNK;
       h->t.field_launches += GRAPH_CHUNK;
       h->host_sweep += GRAPH_CHUNK;
@@ -684,8 +699,10 @@ soma_status soma_shard_fields(soma_t* h, const uint32_t* summed, size_t cells) {
   uint32_t* nn = h->n[(h->host_sweep + (after_sweep ? 1 : 0)) & 1];
   SOMA_CUDA(cudaMemcpyAsync(nn, summed, sizeof(uint32_t) * cells, cudaMemcpyDefault, h->stream));
   const FieldArgs fa = field_args(h, after_sweep);
-  st = timed(h, 1, [&] { return launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count,
-                                              h->stream); });
+  st = timed(h, 1, [&] {
+    cudaError_t e = launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count, h->stream);
+    return e == cudaSuccess ? launch_smc_table_of(h) : e;
+  });
   if (st != SOMA_OK) return st;
   if (after_sweep) ++h->host_sweep;
   h->shard_phase = 0;

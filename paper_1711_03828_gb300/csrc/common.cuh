@@ -234,6 +234,7 @@ struct SweepArgs {
   // smart Monte Carlo: A = a^2/6, sqrt(2A), 1/(4A)
   float smc_A, smc_s2A, smc_inv4A;
   float learned_sigma0;     // a/sqrt(3): scale of the learned proposal
+  const float4* smc_tab;    // smart Monte Carlo: omega and field force per cell, A then B
   unsigned* err;            // sticky error bits (a bounded wait that gave up)
   const uint64_t* seq;      // mixture of linear architectures: bit i of seq[a] set =
   const uint8_t* arch;      // particle i of architecture a is B; arch[chain] (or NULL)

@@ -94,6 +94,11 @@ cudaError_t launch_wait_probe(uint32_t limit, unsigned* err, cudaStream_t st);
 const void* molecule_kernel_ptr(uint32_t N, int grid_dtype, size_t* smem, bool prepare);
 // smart Monte Carlo sweep kernel: paired layout (even N <= 64, 32-bit indices) or general
 const void* smc_kernel_ptr(int Q, bool pair, int grid_dtype);
+// Smart Monte Carlo table (omega and the central-difference field force per
+// type and cell, float4, A then B) from the omega planes of storage type
+// grid_dtype; rebuilt after every field update of a smart Monte Carlo system.
+cudaError_t launch_smc_table(const Geom& g, const void* wA, const void* wB, float4* tab,
+                             int grid_dtype, int sm_count, cudaStream_t st);
 
 // Molecules of any architecture (topology.cu): the architecture array of
 // Sec. 3.2.1 and the independent sets derived from it.

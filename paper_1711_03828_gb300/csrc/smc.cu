@@ -46,7 +46,56 @@ __device__ __forceinline__ float field_and_force(const Geom& g, const WT* w, uin
   return load_w<WT>(w, row + cx);
 }
 
-template <int Q, typename WT>
+// The smart Monte Carlo table, rebuilt after every field update: per type and
+// cell, omega_t(c) and minus its central difference along each axis (the
+// field force of field_and_force, bit for bit), one float4 per cell, A then
+// B.  A move reads it with one 16-byte load at its old and one at its trial
+// cell instead of gathering seven field values at each.
+template <typename WT>
+__global__ void smc_table_kernel(const Geom g, const WT* __restrict__ wA, const WT* __restrict__ wB,
+                                 float4* __restrict__ tab) {
+  const uint32_t nx = g.nx, ny = g.ny;
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < g.cells;
+       c += gridDim.x * blockDim.x) {
+    const uint32_t cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+    float fx, fy, fz;
+    float w = field_and_force<WT>(g, wA, cx, cy, cz, fx, fy, fz);
+    tab[c] = make_float4(w, fx, fy, fz);
+    w = field_and_force<WT>(g, wB, cx, cy, cz, fx, fy, fz);
+    tab[g.cells + c] = make_float4(w, fx, fy, fz);
+  }
+}
+
+cudaError_t launch_smc_table(const Geom& g, const void* wA, const void* wB, float4* tab,
+                             int grid_dtype, int sm_count, cudaStream_t st) {
+  const int grid = 4 * sm_count;
+  switch (grid_dtype) {
+    case 1:
+      smc_table_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(
+          g, static_cast<const __nv_bfloat16*>(wA), static_cast<const __nv_bfloat16*>(wB), tab);
+      break;
+    case 2:
+      smc_table_kernel<__half><<<grid, 256, 0, st>>>(g, static_cast<const __half*>(wA),
+                                                     static_cast<const __half*>(wB), tab);
+      break;
+    default:
+      smc_table_kernel<float><<<grid, 256, 0, st>>>(g, static_cast<const float*>(wA),
+                                                    static_cast<const float*>(wB), tab);
+  }
+  return cudaGetLastError();
+}
+
+// omega and field force of a cell from the table plane of the particle's type.
+__device__ __forceinline__ float smc_field(const float4* __restrict__ tab, uint32_t c, float& fx,
+                                           float& fy, float& fz) {
+  const float4 q = __ldg(tab + c);
+  fx = q.y;
+  fy = q.z;
+  fz = q.w;
+  return q.x;
+}
+
+template <int Q>
 __global__ void __launch_bounds__(256) sweep_smc_kernel(const SweepArgs p) {
   constexpr int S = 2 * Q;
   const int lane = threadIdx.x & 31;
@@ -55,8 +104,8 @@ __global__ void __launch_bounds__(256) sweep_smc_kernel(const SweepArgs p) {
   const unsigned long long s64 = *p.d_sweep;
   const uint32_t sweep = (uint32_t)s64;
   uint32_t* __restrict__ nacc = ((s64 + 1ull) & 1ull) ? p.n1 : p.n0;
-  const WT* __restrict__ wA = static_cast<const WT*>(p.wA);
-  const WT* __restrict__ wB = static_cast<const WT*>(p.wB);
+  const float4* __restrict__ tabA = p.smc_tab;
+  const float4* __restrict__ tabB = p.smc_tab + p.g.cells;
   const uint32_t N = p.g.N, N_A = p.g.N_A;
   const uint32_t ctr3a = (PURPOSE_MOVE << 24) | (p.g.replica & 0xFFFFFFu);
   const uint32_t ctr3b = (PURPOSE_MOVE2 << 24) | (p.g.replica & 0xFFFFFFu);
@@ -115,10 +164,10 @@ __global__ void __launch_bounds__(256) sweep_smc_kernel(const SweepArgs p) {
       uint32_t cx, cy, cz;
       cell3(p.g, x[j], y[j], z[j], cx, cy, cz);
       co[j] = (cz * (uint32_t)p.g.ny + cy) * (uint32_t)p.g.nx + cx;
-      const WT* wt = (ci[j] < N_A) ? wA : wB;
+      const float4* tab = (ci[j] < N_A) ? tabA : tabB;
       w_old[j] = 0.f;
       fox[j] = foy[j] = foz[j] = 0.f;
-      if (li0 + j < nmono) w_old[j] = field_and_force<WT>(p.g, wt, cx, cy, cz, fox[j], foy[j], foz[j]);
+      if (li0 + j < nmono) w_old[j] = smc_field(tab, co[j], fox[j], foy[j], foz[j]);
     }
 
     uint32_t phase[S];
@@ -156,9 +205,10 @@ __global__ void __launch_bounds__(256) sweep_smc_kernel(const SweepArgs p) {
         const float tz = __fadd_rn(z[j], fmaf(s2A, gz[j], A * Fz));
         uint32_t cx, cy, cz;
         cell3(p.g, tx, ty, tz, cx, cy, cz);
-        const WT* wt = (ci[j] < N_A) ? wA : wB;
+        const float4* tab = (ci[j] < N_A) ? tabA : tabB;
+        const uint32_t cn = (cz * (uint32_t)p.g.ny + cy) * (uint32_t)p.g.nx + cx;
         float fnx, fny, fnz;
-        const float w_new = field_and_force<WT>(p.g, wt, cx, cy, cz, fnx, fny, fnz);
+        const float w_new = smc_field(tab, cn, fnx, fny, fnz);
         const float dx = tx - x[j], dy = ty - y[j], dz = tz - z[j];
         // bonded energy change d.(2U + k d); partners' new U' = U + k d
         const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
@@ -175,7 +225,7 @@ __global__ void __launch_bounds__(256) sweep_smc_kernel(const SweepArgs p) {
           x[j] = tx;
           y[j] = ty;
           z[j] = tz;
-          co[j] = (cz * (uint32_t)p.g.ny + cy) * (uint32_t)p.g.nx + cx;
+          co[j] = cn;
           ++my_acc;
         }
       }
@@ -213,8 +263,7 @@ struct SmcSlot {
   uint32_t c;         // old cell
 };
 
-template <typename WT>
-__device__ __forceinline__ SmcSlot smc_slot(const Geom& g, const WT* wt, float x, float y, float z,
+__device__ __forceinline__ SmcSlot smc_slot(const Geom& g, const float4* tab, float x, float y, float z,
                                             uint32_t m, uint32_t sweep, uint32_t ctr3a,
                                             uint32_t ctr3b, bool valid, uint32_t* first_word) {
   SmcSlot q;
@@ -236,14 +285,13 @@ __device__ __forceinline__ SmcSlot smc_slot(const Geom& g, const WT* wt, float x
   q.c = (cz * (uint32_t)g.ny + cy) * (uint32_t)g.nx + cx;
   q.w = 0.f;
   q.fx = q.fy = q.fz = 0.f;
-  if (valid) q.w = field_and_force<WT>(g, wt, cx, cy, cz, q.fx, q.fy, q.fz);
+  if (valid) q.w = smc_field(tab, q.c, q.fx, q.fy, q.fz);
   return q;
 }
 
 // One smart Monte Carlo move of M against the fixed partner sum
 // U = sum (r - n) over its k bonded partners; returns acceptance.
-template <typename WT>
-__device__ __forceinline__ bool smc_move(const SweepArgs& p, const WT* wt, SmcSlot& M, float ux,
+__device__ __forceinline__ bool smc_move(const SweepArgs& p, const float4* tab, SmcSlot& M, float ux,
                                          float uy, float uz, float k, bool valid) {
   const float A = p.smc_A, s2A = p.smc_s2A, K2 = 2.f * p.K_b;
   const float Fx = fmaf(-K2, ux, M.fx), Fy = fmaf(-K2, uy, M.fy), Fz = fmaf(-K2, uz, M.fz);
@@ -252,8 +300,9 @@ __device__ __forceinline__ bool smc_move(const SweepArgs& p, const WT* wt, SmcSl
   const float tz = __fadd_rn(M.z, fmaf(s2A, M.gz, A * Fz));
   uint32_t cx, cy, cz;
   cell3(p.g, tx, ty, tz, cx, cy, cz);
+  const uint32_t cn = (cz * (uint32_t)p.g.ny + cy) * (uint32_t)p.g.nx + cx;
   float fnx = 0.f, fny = 0.f, fnz = 0.f, w_new = 0.f;
-  if (valid) w_new = field_and_force<WT>(p.g, wt, cx, cy, cz, fnx, fny, fnz);
+  if (valid) w_new = smc_field(tab, cn, fnx, fny, fnz);
   const float dx = tx - M.x, dy = ty - M.y, dz = tz - M.z;
   const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
   const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -269,11 +318,10 @@ __device__ __forceinline__ bool smc_move(const SweepArgs& p, const WT* wt, SmcSl
   M.x = acc ? tx : M.x;
   M.y = acc ? ty : M.y;
   M.z = acc ? tz : M.z;
-  M.c = acc ? (cz * (uint32_t)p.g.ny + cy) * (uint32_t)p.g.nx + cx : M.c;
+  M.c = acc ? cn : M.c;
   return acc;
 }
 
-template <typename WT>
 __global__ void __launch_bounds__(256, 3) sweep_smc_pair_kernel(const SweepArgs p) {
   const int lane = threadIdx.x & 31;
   const uint32_t n_tiles_all = (uint32_t)p.n_tiles;
@@ -286,8 +334,10 @@ __global__ void __launch_bounds__(256, 3) sweep_smc_pair_kernel(const SweepArgs 
   uint32_t* __restrict__ nacc = ((s64 + 1ull) & 1ull) ? p.n1 : p.n0;
   const uint32_t ctr3a = (PURPOSE_MOVE << 24) | (p.g.replica & 0xFFFFFFu);
   const uint32_t ctr3b = (PURPOSE_MOVE2 << 24) | (p.g.replica & 0xFFFFFFu);
-  PairLane<WT> L;
+  PairLane<float> L;
   L.init(lane, p.g.N, p.g.N_A, p.wA, p.wB);
+  const float4* tab0 = p.smc_tab + (L.v0 == 1u ? 0u : p.g.cells);   // table plane of slot 0
+  const float4* tab1 = p.smc_tab + (L.v1 == 1u ? 0u : p.g.cells);
   const uint32_t TN = p.G * p.g.N;
   unsigned my_acc = 0;
   for (uint32_t tile = t_begin + (threadIdx.x >> 5); tile < t_end; tile += nwarps) {
@@ -301,21 +351,20 @@ __global__ void __launch_bounds__(256, 3) sweep_smc_pair_kernel(const SweepArgs 
     }
     uint32_t w0, w1;
     const uint32_t cbase = base + (uint32_t)p.g.id_base;
-    const SmcSlot s0 = smc_slot<WT>(p.g, L.w0, px.x, py.x, pz.x, cbase, sweep, ctr3a, ctr3b, valid,
-                                    &w0);
-    const SmcSlot s1 = smc_slot<WT>(p.g, L.w1, px.y, py.y, pz.y, cbase + 1u, sweep, ctr3a, ctr3b,
-                                    valid, &w1);
+    const SmcSlot s0 = smc_slot(p.g, tab0, px.x, py.x, pz.x, cbase, sweep, ctr3a, ctr3b, valid, &w0);
+    const SmcSlot s1 = smc_slot(p.g, tab1, px.y, py.y, pz.y, cbase + 1u, sweep, ctr3a, ctr3b, valid,
+                                &w1);
     const bool sw = p.set_order_random && (__shfl_sync(FULL, w0, L.first_lane) & 1u);
     SmcSlot A = sw ? s1 : s0, B = sw ? s0 : s1;
-    const WT* wA = sw ? L.w1 : L.w0;
-    const WT* wB = sw ? L.w0 : L.w1;
+    const float4* tA = sw ? tab1 : tab0;
+    const float4* tB = sw ? tab0 : tab1;
     {  // first set: A moves against B and the adjacent lane's B
       const int src = sw ? L.src_next : L.src_prev;
       const float cf = sw ? L.cf_next1 : L.cf_prev0;
       const float sx = __shfl_sync(FULL, B.x, src);
       const float sy = __shfl_sync(FULL, B.y, src);
       const float sz = __shfl_sync(FULL, B.z, src);
-      my_acc += smc_move<WT>(p, wA, A, fmaf(cf, A.x - sx, A.x - B.x), fmaf(cf, A.y - sy, A.y - B.y),
+      my_acc += smc_move(p, tA, A, fmaf(cf, A.x - sx, A.x - B.x), fmaf(cf, A.y - sy, A.y - B.y),
                              fmaf(cf, A.z - sz, A.z - B.z), 1.f + cf, valid);
     }
     {  // second set: B moves against A and the adjacent lane's A
@@ -324,7 +373,7 @@ __global__ void __launch_bounds__(256, 3) sweep_smc_pair_kernel(const SweepArgs 
       const float sx = __shfl_sync(FULL, A.x, src);
       const float sy = __shfl_sync(FULL, A.y, src);
       const float sz = __shfl_sync(FULL, A.z, src);
-      my_acc += smc_move<WT>(p, wB, B, fmaf(cf, B.x - sx, B.x - A.x), fmaf(cf, B.y - sy, B.y - A.y),
+      my_acc += smc_move(p, tB, B, fmaf(cf, B.x - sx, B.x - A.x), fmaf(cf, B.y - sy, B.y - A.y),
                              fmaf(cf, B.z - sz, B.z - A.z), 1.f + cf, valid);
     }
     if (valid) {
@@ -342,24 +391,10 @@ __global__ void __launch_bounds__(256, 3) sweep_smc_pair_kernel(const SweepArgs 
   if (lane == 0 && my_acc) atomicAdd(p.acc, (unsigned long long)my_acc);
 }
 
-template <int Q>
-static const void* pick_smc(int grid_dtype) {
-  switch (grid_dtype) {
-    case 1: return (const void*)sweep_smc_kernel<Q, __nv_bfloat16>;
-    case 2: return (const void*)sweep_smc_kernel<Q, __half>;
-    default: return (const void*)sweep_smc_kernel<Q, float>;
-  }
-}
-
-const void* smc_kernel_ptr(int Q, bool pair, int grid_dtype) {
-  if (pair) {
-    switch (grid_dtype) {
-      case 1: return (const void*)sweep_smc_pair_kernel<__nv_bfloat16>;
-      case 2: return (const void*)sweep_smc_pair_kernel<__half>;
-      default: return (const void*)sweep_smc_pair_kernel<float>;
-    }
-  }
-  return Q == 1 ? pick_smc<1>(grid_dtype) : (Q == 2 ? pick_smc<2>(grid_dtype) : pick_smc<4>(grid_dtype));
+const void* smc_kernel_ptr(int Q, bool pair, int /*grid_dtype: the table is FP32*/) {
+  if (pair) return (const void*)sweep_smc_pair_kernel;
+  return Q == 1 ? (const void*)sweep_smc_kernel<1>
+                : (Q == 2 ? (const void*)sweep_smc_kernel<2> : (const void*)sweep_smc_kernel<4>);
 }
 
 }  // namespace soma
