@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--workload", default="melt_large",
                     choices=["melt_large", "melt_mid", "melt_small", "melt_slow", "melt_subbox",
                              "melt_tiny", "arch_large", "arch_mid", "abc_large",
-                             "batch64", "decorrelation"])
+                             "batch64", "decorrelation", "precision"])
     ap.add_argument("--move", default="uniform", choices=["uniform", "smc", "learned"],
                     help="trial moves: uniform displacement or smart Monte Carlo")
     ap.add_argument("--iteration", default="set", choices=["set", "molecule"],
@@ -659,42 +659,50 @@ def run_decorrelation(args):
 
     torch.cuda.set_device(0)
     dev = torch.device("cuda")
-    small = workloads.melt_slow(n_chains=16384, box_Re=(8.0, 8.0, 4.0), grid=(48, 48, 24))
     big = workloads.melt_slow()
     every, T, equil = 10, max(args.steps, 400), 1000
-    # train the learned proposal on plain-method configurations of the small box
+    seeds = (1, 2)
+    # train the learned proposal on plain-method configurations of the small
+    # box: 2000 Adam steps, five plain sweeps between steps (10^4 sweeps of
+    # plain-method trajectories)
     tr = System(workloads.melt_slow(n_chains=16384, box_Re=(8.0, 8.0, 4.0), grid=(48, 48, 24),
-                                    move=2))
+                                    move=2, seed=101))
     tr.sweep(200)
-    train_log = tr.train_proposal(steps=600, batch=16384, sweeps_between=1, lr=3e-3)
+    train_log = tr.train_proposal(steps=2000, batch=16384, sweeps_between=5, lr=3e-3)
     W = tr.get_proposal_weights()
     tr.close()
     # q*: the strongest low-q shell after equilibration (uniform moves)
     ms_all = [(i, j, k) for i in range(-4, 5) for j in range(-4, 5) for k in range(0, 3)
               if 0 < i * i + j * j + k * k <= 16]
     res = {}
+    q_star = None
     for name, move, order in (("uniform", 0, 0), ("smc", 1, 0), ("learned", 2, 0),
                               ("uniform_molecule", 0, 2)):
-        d = workloads.melt_slow(n_chains=16384, box_Re=(8.0, 8.0, 4.0), grid=(48, 48, 24),
-                                move=move, set_order=order)
-        s = System(d)
-        if move == 2:
-            s.set_proposal_weights(W)
-        s.sweep(equil)
-        if name == "uniform":
-            sq = s.structure_factor(ms_all)
-            q_star = [ms_all[int(np.argmax(sq))]]
-        pos = torch.empty(3 * d.M, dtype=torch.float32, device=dev)
-        re2, sqs = [], []
-        for t in range(T):
-            s.sweep(every)
-            s.get_positions(out=pos)
-            P = pos.view(3, d.n_chains, d.N)
-            re2.append(((P[:, :, -1] - P[:, :, 0]) ** 2).sum(0).double().cpu().numpy())
-            sqs.append(float(s.structure_factor(q_star)[0]))
-        s.close()
-        tau_re, w_re = tau_int(np.asarray(re2))
-        tau_sq, w_sq = tau_int(np.asarray(sqs))
+        taus_re, taus_sq = [], []
+        for seed in seeds:
+            d = workloads.melt_slow(n_chains=16384, box_Re=(8.0, 8.0, 4.0), grid=(48, 48, 24),
+                                    move=move, set_order=order, seed=seed)
+            s = System(d)
+            if move == 2:
+                s.set_proposal_weights(W)
+            s.sweep(equil)
+            if q_star is None:
+                sq = s.structure_factor(ms_all)
+                q_star = [ms_all[int(np.argmax(sq))]]
+            pos = torch.empty(3 * d.M, dtype=torch.float32, device=dev)
+            re2, sqs = [], []
+            for t in range(T):
+                s.sweep(every)
+                s.get_positions(out=pos)
+                P = pos.view(3, d.n_chains, d.N)
+                re2.append(((P[:, :, -1] - P[:, :, 0]) ** 2).sum(0).double().cpu().numpy())
+                sqs.append(float(s.structure_factor(q_star)[0]))
+            s.close()
+            tr_, w_ = tau_int(np.asarray(re2))
+            taus_re.append(tr_)
+            taus_sq.append(tau_int(np.asarray(sqs))[0])
+        tau_re, w_re = float(np.mean(taus_re)), w_
+        tau_sq = float(np.mean(taus_sq))
         # wall time per cycle at scale
         b = System(workloads.melt_slow(move=move, set_order=order))
         if move == 2:
@@ -708,18 +716,93 @@ def run_decorrelation(args):
         ms_cycle = (_t.perf_counter() - t0) * 1e3 / 20
         b.close()
         tau_sweeps = tau_re * every
-        res[name] = {"tau_int_Re2_sweeps": tau_sweeps, "window": w_re * every,
-                     "tau_int_Sq_sweeps": tau_sq * every, "ms_per_cycle_67M": ms_cycle,
-                     "decorrelations_per_s": big.n_chains * (1e3 / ms_cycle) / (2 * tau_sweeps)}
+        # error of the seed mean from the seeds' spread (the autocorrelation is
+        # averaged over 16,384 chains, so one run's estimate scatters far less
+        # than a single series' would)
+        err = float(np.std(taus_re, ddof=1) / np.sqrt(len(seeds))) * every
+        dps = big.n_chains * (1e3 / ms_cycle) / (2 * tau_sweeps)
+        res[name] = {"tau_int_Re2_sweeps": tau_sweeps, "tau_int_Re2_err": err,
+                     "tau_int_Re2_per_seed": [t * every for t in taus_re], "window": w_re * every,
+                     "tau_int_Sq_sweeps": tau_sq * every,
+                     "tau_int_Sq_per_seed": [t * every for t in taus_sq],
+                     "ms_per_cycle_67M": ms_cycle,
+                     "decorrelations_per_s": dps, "decorrelations_per_s_err": dps * err / tau_sweeps}
     line = {"metric": "R_e^2 decorrelations/s (learned vs plain)", "unit": "decorrelations/s",
             "value": res["learned"]["decorrelations_per_s"], "higher_is_better": True,
             "n_gpus": 1, "data": "synthetic", "dtype": "f32",
             "config": {"workload": "slow melt: tau_int on 16,384 chains x N=64 in 8x8x4 R_e0 "
                                    "(48x48x24 grid), wall time on 1,048,576 chains in 32x32x16 R_e0 "
                                    "(192x192x96 grid), chiN=40, kappaN=50",
-                       "sampling": f"every {every} cycles, {T} samples after {equil} cycles",
+                       "sampling": f"every {every} cycles, {T} samples after {equil} cycles, "
+                                   f"seeds {list(seeds)}",
                        "q_star": q_star[0]},
             "moves": res, "training": train_log}
+    print(json.dumps(line), flush=True)
+
+
+def batch_means(x, n_batches=8):
+    """Mean and standard error of a time series by batch means."""
+    import numpy as np
+    x = np.asarray(x, dtype=np.float64)
+    b = len(x) // n_batches
+    m = x[:b * n_batches].reshape(n_batches, b).mean(1)
+    return float(x.mean()), float(m.std(ddof=1) / np.sqrt(n_batches))
+
+
+def run_precision(args):
+    """Precision of the 16-bit field grids at scale: the 134M-particle lamellar
+    melt from one seed with FP32, BF16 and FP16 omega, 1000 SCMF cycles each;
+    time averages over the last 800 cycles (a sample every 10 cycles, batch
+    means over 8 batches) of the total energy per particle (FP64 on the GPU),
+    <R_e^2>/R_e0^2 and S(q*), q* the shell |m| (grid wave vectors) with the
+    largest S averaged over up to 32 wave vectors of the shell, chosen on the
+    FP32 run after 200 cycles and used for all three."""
+    import numpy as np
+    import torch
+    from paper_1711_03828_gb300 import System
+
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(7)
+    shells = {}
+    for r in range(4, 33):
+        # wave vectors of the shell |m| = r (rounded), half space, up to 32 of them
+        ms = [(i, j, k) for i in range(-r, r + 1) for j in range(-r, r + 1) for k in range(0, r + 1)
+              if round(np.sqrt(i * i + j * j + k * k)) == r and (k > 0 or j > 0 or (j == 0 and i > 0))]
+        idx = rng.choice(len(ms), size=min(32, len(ms)), replace=False)
+        shells[r] = [ms[i] for i in sorted(idx)]
+    equil, total, every = 200, 1000, 10
+    res, q_shell = {}, None
+    for name in ("f32", "bf16", "f16"):
+        d = workload("melt_large", grid_dtype=name)
+        s = System(d)
+        s.sweep(equil)
+        if q_shell is None:
+            avg = {r: float(np.mean(s.structure_factor(m))) for r, m in shells.items()}
+            q_shell = max(avg, key=avg.get)
+        E, R, S = [], [], []
+        t0 = time.perf_counter()
+        for _ in range((total - equil) // every):
+            s.sweep(every)
+            o = s.observables()
+            E.append(o["E_tot"] / d.M)
+            R.append(o["Re2_rel"])
+            S.append(float(np.mean(s.structure_factor(shells[q_shell]))))
+        wall = time.perf_counter() - t0
+        s.close()
+        res[name] = {"E_per_particle": batch_means(E), "Re2_rel": batch_means(R),
+                     "S_qstar": batch_means(S), "samples": len(E), "wall_s": wall}
+    for name in ("bf16", "f16"):
+        for k in ("E_per_particle", "Re2_rel", "S_qstar"):
+            m0, e0 = res["f32"][k]
+            m1, e1 = res[name][k]
+            res[name][k + "_vs_f32_sigma"] = (m1 - m0) / max(np.hypot(e0, e1), 1e-300)
+    line = {"metric": "observables with 16-bit field grids vs FP32 (config 4)",
+            "n_gpus": 1, "data": "synthetic", "dtype": "f32 positions and energies",
+            "config": {"workload": "melt_large: 4194304 chains x N=32, box 32^3 R_e0, grid 192^3, "
+                                   "chiN=30, kappaN=50, seed 1",
+                       "cycles": total, "averaged": f"cycles {equil}..{total}, every {every}",
+                       "q_star_shell": q_shell},
+            "results": res}
     print(json.dumps(line), flush=True)
 
 
@@ -731,6 +814,8 @@ def main():
         run_batch(args)
     elif args.workload == "decorrelation":
         run_decorrelation(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_ours(args)
 
