@@ -395,19 +395,24 @@ class System:
             self.s.topo = self.s.topo_start = self.s.arch = None
             self.s.topo_set = self.s.topo_nsets = None
             self.s.n_topo = 0
+            self.s.rho_cell = float(self.M) / self.cells
             return
         self._topo = np.ascontiguousarray(words, np.uint32)
         self._topo_start = np.ascontiguousarray(starts, np.uint32)
         self._arch = np.ascontiguousarray(arch, np.uint8)
         na = self._topo_start.size
         assert self._arch.size == self.n_chains and int(self._arch.max()) < na
-        self._topo_set = np.zeros(na * self.N, np.uint8)
+        # absent slots (past an architecture's n particles) belong to no set
+        self._topo_set = np.full(na * self.N, 0xFF, np.uint8)
         self._topo_nsets = np.zeros(na, np.uint8)
+        lengths = np.zeros(na, np.int64)
         for a in range(na):
-            assert int(self._topo[self._topo_start[a]]) == self.N
+            n_a = int(self._topo[self._topo_start[a]])
+            assert 1 <= n_a <= self.N
+            lengths[a] = n_a
             sets, n = topology_sets(self._topo, self._topo_start[a], self.L)
             assert 1 <= n <= 8
-            self._topo_set[a * self.N:(a + 1) * self.N] = sets
+            self._topo_set[a * self.N:a * self.N + n_a] = sets
             self._topo_nsets[a] = n
         self.s.seq = None
         self._seq = None
@@ -417,6 +422,8 @@ class System:
         self.s.topo_set = self._topo_set.ctypes.data
         self.s.topo_nsets = self._topo_nsets.ctypes.data
         self.s.arch = self._arch.ctypes.data
+        # rho_0 dL^3 counts the molecules' particles, absent slots excluded
+        self.s.rho_cell = float(lengths[self._arch].sum()) / self.cells
 
     def set_types(self, n_types=0, chiN=None):
         """n_t particle types (types from the architecture array's type

@@ -211,6 +211,21 @@ int or_is_B(const or_system* s, uint64_t chain, uint32_t i) {
   return i >= s->N_A;
 }
 
+/* Particles of a molecule: its architecture's count (the first word of the
+ * block, at most N; the slots from there to N-1 are absent), else N. */
+uint32_t or_length(const or_system* s, uint64_t chain) {
+  if (s->topo && s->arch) return s->topo[s->topo_start[s->arch[chain]]];
+  return s->N;
+}
+
+/* Particles of the system: the molecules' counts summed. */
+double or_particles(const or_system* s) {
+  if (!(s->topo && s->arch)) return (double)s->n_chains * (double)s->N;
+  double n = 0.0;
+  for (uint64_t k = 0; k < s->n_chains; ++k) n += (double)or_length(s, k);
+  return n;
+}
+
 uint32_t or_type(const or_system* s, uint64_t chain, uint32_t i) {
   if (s->topo && s->arch) return or_topo_type(s->topo, s->topo_start[s->arch[chain]], i);
   return (uint32_t)or_is_B(s, chain, i);
@@ -297,7 +312,8 @@ void or_histogram(const or_system* s, const float* x, const float* y, const floa
   memset(nA, 0, cells * sizeof(uint32_t));
   memset(nB, 0, cells * sizeof(uint32_t));
   for (uint64_t k = 0; k < s->n_chains; ++k) {
-    for (uint32_t i = 0; i < s->N; ++i) {
+    const uint32_t n_k = or_length(s, k);
+    for (uint32_t i = 0; i < n_k; ++i) {
       uint64_t m = k * s->N + i;
       uint64_t c = or_cell(s, x[m], y[m], z[m]);
       if (!or_is_B(s, k, i)) nA[c] += 1u; else nB[c] += 1u;
@@ -361,7 +377,7 @@ void or_histogram_types(const or_system* s, const float* x, const float* y, cons
   const uint64_t cells = (uint64_t)s->grid[0] * s->grid[1] * s->grid[2];
   memset(n, 0, (size_t)s->n_types * cells * sizeof(uint32_t));
   for (uint64_t k = 0; k < s->n_chains; ++k)
-    for (uint32_t i = 0; i < s->N; ++i) {
+    for (uint32_t i = 0; i < or_length(s, k); ++i) {
       const uint64_t m = k * s->N + i;
       n[(uint64_t)or_type(s, k, i) * cells + or_cell(s, x[m], y[m], z[m])] += 1u;
     }
@@ -495,7 +511,7 @@ static void or_move_uniform(const or_system* s, float* x, float* y, float* z,
  * attempts of one MC step are made one after another, each on a particle of
  * the chain chosen at random, so each particle is attempted once per step on
  * average.  Attempt j of chain k draws Philox purpose 3 with id k*N + j: the
- * particle is ((word 3 & 0xFF) * N) >> 8 (the low byte, which the acceptance
+ * particle is ((word 3 & 0xFF) * n) >> 8, n the molecule's particles (the low byte, which the acceptance
  * uniform of the top 24 bits does not use; a state-independent choice, so
  * balance holds for any choice probabilities), the move is the uniform move
  * with that draw.  Diagnostics (margin, accepted, trial) are per attempt. */
@@ -506,7 +522,7 @@ static void or_move_attempt(const or_system* s, float* x, float* y, float* z,
   const uint64_t a = chain * s->N + j;
   uint32_t w[4];
   or_draw(s, OR_PURPOSE_ATTEMPT, a, sweep, w);
-  const uint32_t i = (uint32_t)(((uint64_t)(w[3] & 0xFFu) * s->N) >> 8);
+  const uint32_t i = (uint32_t)(((uint64_t)(w[3] & 0xFFu) * or_length(s, chain)) >> 8);
   if (chosen) chosen[a] = i;
   or_move_uniform_w(s, x, y, z, wA, wB, chain, i, w, a, margin, accepted, trial, acc, ties);
 }
@@ -1032,7 +1048,7 @@ void or_sweep_trial(const or_system* s, float* x, float* y, float* z,
   for (long long cc = i0; cc < i1; ++cc) {
     uint64_t chain = (uint64_t)cc;
     if (s->set_order == 2) {
-      for (uint32_t j = 0; j < N; ++j) {
+      for (uint32_t j = 0; j < or_length(s, chain); ++j) {
         uint64_t a1 = 0, t1 = 0;
         or_move_attempt(s, x, y, z, wA, wB, sweep, chain, j, margin, accepted, trial,
                         s->chosen, &a1, &t1);
@@ -1075,7 +1091,9 @@ void or_sweep_trial(const or_system* s, float* x, float* y, float* z,
     }
   }
   if (st) {
-    st->attempted += (c1 - c0) * N;
+    uint64_t att = 0;
+    for (uint64_t k = c0; k < c1; ++k) att += or_length(s, k);
+    st->attempted += att;
     st->accepted += acc;
     st->near_ties += ties;
   }
@@ -1109,7 +1127,7 @@ void or_observables(const or_system* s, const float* x, const float* y, const fl
     if (s->topo && s->arch) {
       /* every bond once: from the particle with the smaller index */
       uint32_t partners[256];
-      for (uint32_t i = 0; i < N; ++i) {
+      for (uint32_t i = 0; i < or_length(s, k); ++i) {
         const uint32_t np = or_partners(s, k, i, partners);
         for (uint32_t b = 0; b < np; ++b) {
           const uint32_t j = partners[b];
@@ -1132,9 +1150,10 @@ void or_observables(const or_system* s, const float* x, const float* y, const fl
       b2 += bb;
       Eb += s->K_b * bb;
     }
-    double ex = (double)x[m0 + N - 1] - (double)x[m0];
-    double ey = (double)y[m0 + N - 1] - (double)y[m0];
-    double ez = (double)z[m0 + N - 1] - (double)z[m0];
+    const uint32_t last = or_length(s, k) - 1u;   /* the molecule's last particle */
+    double ex = (double)x[m0 + last] - (double)x[m0];
+    double ey = (double)y[m0 + last] - (double)y[m0];
+    double ez = (double)z[m0 + last] - (double)z[m0];
     Re2 += ex * ex + ey * ey + ez * ez;
   }
   const uint64_t cells = (uint64_t)s->grid[0] * s->grid[1] * s->grid[2];
@@ -1162,7 +1181,7 @@ void or_observables(const or_system* s, const float* x, const float* y, const fl
  * Sec. 5.6 is the shell average of this quantity).  Direct DFT. */
 void or_structure_factor(const or_system* s, const uint32_t* nA, const uint32_t* nB,
                          const int32_t* m, size_t k, double* out) {
-  const double M = (double)s->n_chains * (double)s->N;
+  const double M = or_particles(s);
   for (size_t q = 0; q < k; ++q) {
     double re = 0.0, im = 0.0;
     for (uint32_t cz = 0; cz < s->grid[2]; ++cz)

@@ -86,7 +86,10 @@ typedef struct {
 } or_system;
 
 /* --- Molecular architectures (Sec. 3.2.1, Fig. polyarch) ---------------------
- * One block per architecture: word 0 = N; word 1 + i = (offset << 8) | type of
+ * One block per architecture: word 0 = n, its number of particles (1 <= n <=
+ * N: molecules of several lengths in one system; a molecule of n < N
+ * particles occupies the first n of its N slots, the others are absent --
+ * never moved, counted or bonded); word 1 + i = (offset << 8) | type of
  * particle i, where offset is the index in the whole array of the particle's
  * first bond word (OR_TOPO_NO_BONDS: no bonds) and type 0 = A, 1 = B; bond
  * words = (signed 27-bit partner offset j - i) << 5 | (bond type << 1) | last,
@@ -116,6 +119,9 @@ uint32_t or_topology_sets(const uint32_t* topo, uint32_t start, uint8_t* set_of)
 void or_set_order(const or_system* s, uint64_t chain, uint32_t sweep, uint32_t n_sets,
                   uint32_t* order);
 
+/* Particles of a molecule (its architecture's n, else N) and of the system. */
+uint32_t or_length(const or_system* s, uint64_t chain);
+double or_particles(const or_system* s);
 /* Type of particle i of a chain: 1 for B, 0 for A (the diblock boundary N_A,
  * or the chain's architecture in a mixture). */
 int or_is_B(const or_system* s, uint64_t chain, uint32_t i);

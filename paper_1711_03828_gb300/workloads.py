@@ -239,7 +239,8 @@ def architecture_positions(desc: SystemDesc, molecules, arch, seed: int,
     particle at its lowest-index bonded partner plus a normal displacement of
     standard deviation bond_sigma per axis (default R_e0/sqrt(3(N-1))); a
     particle with no earlier partner is placed uniformly in the box, so the
-    bonds that close rings start stretched.  Molecules are drawn in chunks of
+    bonds that close rings start stretched; the absent slots of a molecule of
+    fewer than N particles are placed uniformly too.  Molecules are drawn in chunks of
     `chunk` with the generator seeded by (seed, chunk index).  Returns (3, M)
     float32."""
     Re = desc.grid[0] / desc.box_Re[0]

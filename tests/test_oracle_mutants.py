@@ -134,6 +134,13 @@ MUTANTS = [
      "or_mlp_forward(s->mlp, f, o_rev);", BF16.check_bf16_move_uses_the_bf16_network),
     ("bf16_slack_inner_boundary_only", "for (int k = -1; k <= 1; ++k) {", "for (int k = 0; k <= 0; ++k) {",
      BF16.check_bf16_slack_values),
+    # molecules of several lengths
+    ("blend_histogram_counts_absent_slots", "const uint32_t n_k = or_length(s, k);",
+     "const uint32_t n_k = s->N;", TOPO.check_blend_histogram_and_density),
+    ("blend_end_to_end_to_last_slot", "const uint32_t last = or_length(s, k) - 1u;",
+     "const uint32_t last = s->N - 1u;", TOPO.check_blend_ideal_statistics),
+    ("blend_sq_over_all_slots", "  const double M = or_particles(s);",
+     "  const double M = (double)s->n_chains * (double)s->N;", TOPO.check_blend_histogram_and_density),
     # n_t particle types
     ("types_K0_sign", "else v = v - 0.5 * chi0 * (phi[i] - phi[k]);",
      "else v = v + 0.5 * chi0 * (phi[i] - phi[k]);",

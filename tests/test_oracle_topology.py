@@ -260,3 +260,141 @@ def test_ideal_star_and_ring_closed_forms(oracle_lib):
 
 def test_topology_observables_hand_values(oracle_lib):
     check_topology_observables_hand_values()
+
+
+# --------------------------------------------------------------------------
+# Molecules of several lengths in one system (Sec. 2.1 mixtures, one
+# architecture per molecule type, Sec. 3.2.1): an architecture of n < N
+# particles fills the first n of a molecule's N slots, the rest are absent.
+# --------------------------------------------------------------------------
+def _blend(N, lengths, n_mol, L, chiN=0.0, kappaN=0.0, set_order=0, seed=7):
+    mols = [workloads.linear_architecture(n, n) for n in lengths]   # homopolymers of A
+    d = SystemDesc(n_chains=n_mol, N=N, f=0.5, box_Re=(2.0, 2.0, 1.0), grid=(12, 12, 6),
+                   chiN=chiN, kappaN=kappaN, seed=seed, set_order=set_order)
+    s = oracle_system(d, L)
+    words, starts = workloads.encode_architectures(mols)
+    arch = (np.arange(n_mol) % len(lengths)).astype(np.uint8)
+    s.set_topology(words, starts, arch)
+    pos0 = workloads.architecture_positions(d, mols, arch, seed=13)
+    return d, s, arch, Positions(*[pos0[k].copy() for k in range(3)])
+
+
+def check_blend_ideal_statistics(lib=None, set_order=0):
+    """Ideal homopolymers of 8 and 4 particles in slots of N = 8 (chiN = kappaN
+    = 0): each keeps Gaussian bonds of b0^2 = R_e0^2/(N-1) (the spring constant
+    of the system), so <R_e^2> = (n-1) b0^2 per length, and the absent slots of
+    the short molecules never move.  Also under the molecule-parallel
+    iteration, whose attempts pick a particle of the molecule's own n."""
+    L = _L(lib)
+    N, lengths = 8, (8, 4)
+    d, s, arch, p = _blend(N, lengths, 1024, L, set_order=set_order)
+    absent = np.zeros((d.n_chains, N), bool)
+    absent[arch == 1, 4:] = True
+    absent = absent.reshape(-1)
+    frozen = p.stacked()[:, absent].copy()
+    nA, nB = s.histogram(p)
+    assert int(nA.sum()) == 512 * 8 + 512 * 4 and int(nB.sum()) == 0
+    wA, wB = s.fields(nA, nB)
+    Re = 6.0
+    b02 = Re**2 / (N - 1)
+    re2 = {8: [], 4: []}
+    att = 0
+    for sweep in range(1600):
+        st, _, _ = s.sweep(p, wA, wB, sweep)
+        att += st.attempted
+        if sweep >= 600 and sweep % 4 == 0:
+            P = p.stacked().astype(np.float64).reshape(3, d.n_chains, N)
+            for a, n in enumerate(lengths):
+                sel = arch == a
+                re2[n].append(((P[:, sel, n - 1] - P[:, sel, 0]) ** 2).sum(0))
+    assert att == 1600 * (512 * 8 + 512 * 4)
+    np.testing.assert_array_equal(p.stacked()[:, absent], frozen)
+    for n in lengths:
+        per = np.mean(re2[n], axis=0)
+        se = per.std() / math.sqrt(per.size)
+        assert abs(per.mean() - (n - 1) * b02) < 5 * se, (n, per.mean(), (n - 1) * b02, se)
+    o = s.observables(p, *s.histogram(p))
+    P = p.stacked().astype(np.float64).reshape(3, d.n_chains, N)
+    last = np.where(arch == 1, 3, 7)
+    want = ((P[:, np.arange(d.n_chains), last] - P[:, :, 0]) ** 2).sum(0).mean()
+    assert o["Re2"] == pytest.approx(want, rel=1e-12)
+
+
+def check_blend_monomer_dimer_balance(lib=None):
+    """Monomers (n = 1) and dimers (n = 2) in slots of N = 2 in fixed random
+    fields: a free A monomer visits cell c with probability exp(-wA(c)) / Z
+    (uniform inside each cell), the dimers follow the exact cell-pair
+    distribution of the two-particle test (erf quadrature)."""
+    from tests.test_oracle_pins import _cells_of, _pair_cell_probabilities
+    L = _L(lib)
+    Lg, Re = 2, 1.5
+    mols = [([0, 1], [(0, 1)]), ([0], [])]
+    d = SystemDesc(n_chains=4096, N=2, f=0.5, box_Re=(Lg / Re,) * 3, grid=(Lg,) * 3, chiN=0.0,
+                   kappaN=0.0, seed=19)
+    s = oracle_system(d, L)
+    words, starts = workloads.encode_architectures(mols)
+    arch = (np.arange(d.n_chains) % 2).astype(np.uint8)
+    s.set_topology(words, starts, arch)
+    wA, wB = workloads.random_fields(Lg**3, seed=5, scale=1.0)
+    p = Positions(*[a.copy() for a in workloads.architecture_positions(d, mols, arch, seed=3)])
+    for sweep in range(100):
+        s.sweep(p, wA, wB, sweep)
+    T = 1500
+    dim = np.nonzero(arch == 0)[0]
+    mono = np.nonzero(arch == 1)[0]
+    cpair = np.zeros((dim.size, Lg**6))
+    cmono = np.zeros((mono.size, Lg**3))
+    for sweep in range(100, 100 + T):
+        s.sweep(p, wA, wB, sweep)
+        P = p.stacked().reshape(3, d.n_chains, 2)
+        c0, c1 = _cells_of(P[:, dim, 0], Lg), _cells_of(P[:, dim, 1], Lg)
+        cpair[np.arange(dim.size), c0 * Lg**3 + c1] += 1
+        cmono[np.arange(mono.size), _cells_of(P[:, mono, 0], Lg)] += 1
+    K = s.params.K_b
+    for counts, want in ((cpair, _pair_cell_probabilities(K, Lg, wA, wB).reshape(-1)),
+                         (cmono, np.exp(-wA) / np.exp(-wA).sum())):
+        freq = counts / T
+        z = (freq.mean(0) - want) / np.maximum(freq.std(0) / math.sqrt(freq.shape[0]), 1e-12)
+        assert np.max(np.abs(z)) < 5.0, np.max(np.abs(z))
+
+
+def check_blend_histogram_and_density(lib=None):
+    """Occupation numbers count the molecules' particles only (numpy binning
+    of the present slots); S(q) divides by their number (numpy FFT); and
+    rho_0 dL^3 is their number per cell: with 1152 molecules of 8 and 4
+    particles in 864 cells it is 8, and counts of 4 A and 4 B in every cell
+    give omega = 0 exactly (the field vanishes at the melt density)."""
+    L = _L(lib)
+    d, s, arch, p = _blend(8, (8, 3, 5), 999, L, chiN=20.0, kappaN=50.0)
+    present = (np.arange(8)[None, :] < np.array([8, 3, 5])[arch][:, None]).reshape(-1)
+    P = p.stacked().astype(np.float64)
+    c = np.floor(P).astype(np.int64) % np.array(d.grid)[:, None]
+    ci = (c[2] * d.grid[1] + c[1]) * d.grid[0] + c[0]
+    nA, nB = s.histogram(p)
+    np.testing.assert_array_equal(nA, np.bincount(ci[present], minlength=d.cells))
+    assert int(nB.sum()) == 0
+    M_real = int(np.array([8, 3, 5])[arch].sum())
+    assert s.params.rho_cell == pytest.approx(M_real / d.cells, rel=1e-15)
+    m = [(1, 0, 0), (0, 2, 1), (3, 1, 2)]
+    grid = nA.reshape(d.grid[2], d.grid[1], d.grid[0]).astype(np.float64)
+    F = np.fft.fftn(grid)
+    want = [abs(F[k, j, i]) ** 2 / M_real for i, j, k in m]
+    np.testing.assert_allclose(s.structure_factor(nA, nB, m), want, rtol=1e-12)
+    d2, s2, arch2, _ = _blend(8, (8, 4), 1152, L, chiN=20.0, kappaN=50.0)
+    assert s2.params.rho_cell == 8.0
+    four = np.full(d2.cells, 4, np.uint32)
+    wA, wB = s2.fields(four, four)
+    assert np.all(wA == 0.0) and np.all(wB == 0.0)
+
+
+@pytest.mark.parametrize("set_order", [0, 2])
+def test_blend_ideal_statistics(oracle_lib, set_order):
+    check_blend_ideal_statistics(set_order=set_order)
+
+
+def test_blend_monomer_dimer_balance(oracle_lib):
+    check_blend_monomer_dimer_balance()
+
+
+def test_blend_histogram_and_density(oracle_lib):
+    check_blend_histogram_and_density()
