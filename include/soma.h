@@ -272,7 +272,11 @@ soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_ar
 /* Molecules of any architecture (Sec. 2.1: branched molecules, rings, any
  * mixture; Sec. 3.2.1: the architecture array; Sec. 3.1.2: independent sets).
  *   words (n_words uint32): one block per architecture, starting at
- *     start[a] (n_arch = 1..256 entries): word 0 = N (the system's N, <= 64);
+ *     start[a] (n_arch = 1..256 entries): word 0 = n, the architecture's
+ *     particles, 1 <= n <= N (the system's N, <= 64): a molecule of n < N
+ *     particles holds the first n of its N slots (molecules of several
+ *     lengths in one system, Sec. 2.1); its other slots are absent -- never
+ *     moved, counted or bonded, their positions kept as they are;
  *     word 1 + i = (index in words of particle i's first bond word << 8) |
  *     type (0 A, 1 B; 0..n_types-1 after soma_set_types), index 0xFFFFFF for
  *     a particle without bonds; a bond
@@ -291,10 +295,16 @@ soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_ar
  * molecule hi, sweep, 6 << 24 | replica_id); SOMA_SET_ORDER_FIXED visits them
  * in index order.  Replaces the diblock (and any mixture) for the sweep, the
  * occupation count and the bond observables (E_b and b2 over the listed
- * bonds; Re2 stays |r_{N-1} - r_0|^2); call soma_update_fields to recount at
+ * bonds; Re2 = |r_{n-1} - r_0|^2 with n the molecule's particles); rho_0 dL^3,
+ * the attempted moves and the normalisation of S(q) count the molecules'
+ * particles, while kappa_0 = kappaN/N and chi_0 = chiN/N keep the system's N
+ * as the reference length; call soma_update_fields to recount at
  * once.  Uniform moves, in the SET scheme or the molecule-parallel iteration
- * (SOMA_ITERATION_MOLECULE: random particles, partners from the same
- * tables).  src_on_device: all three
+ * (SOMA_ITERATION_MOLECULE: each molecule makes n attempts, on particles
+ * ((word 3 & 0xFF) * n) >> 8 of its own n; partners from the same tables).
+ * A shard (desc.n_chains_total > 0) takes only architectures of N particles
+ * (SOMA_EINVAL otherwise: its density counts the whole system).
+ * src_on_device: all three
  * arrays are device memory (else host).  SOMA_EINVAL, with the reason in
  * soma_last_error, for a block that does not fit the array, a type outside
  * 0/1 (0..n_types-1 with n_t types), a bond type other than 0, a partner
@@ -352,8 +362,9 @@ soma_status soma_sort_molecules(soma_t* h, uint64_t* perm);
 
 /* The check and the independent sets of soma_set_topology on their own, on
  * the host (no handle, no device): words / start / n_arch as there (host
- * memory), N the particles per molecule; writes the set of particle i of
- * architecture a to sets[a*N + i] (n_arch*N bytes) and the number of sets of
+ * memory), N the particle slots per molecule; writes the set of particle i of
+ * architecture a to sets[a*N + i] (n_arch*N bytes; 0xFF for the absent slots
+ * of an architecture of fewer than N particles) and the number of sets of
  * each architecture to n_sets (n_arch bytes).  Types 0..7 are accepted (the
  * sets do not depend on them; soma_set_topology checks them against the
  * system's types).  SOMA_EINVAL for an array soma_set_topology would refuse

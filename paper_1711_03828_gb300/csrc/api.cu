@@ -107,6 +107,8 @@ struct soma_t {
   uint32_t* d_topo_ptab = nullptr;           // 256 * 64 per-particle table words
   double topo_bonds = 0.0;                   // bonds in the system
   uint8_t* d_topo_ttab = nullptr;            // 256 * 64 particle types
+  uint8_t* d_topo_len = nullptr;             // 256 particle counts (the rest of N absent)
+  uint64_t M_real = 0;                       // particles present (M less absent slots)
   uint32_t topo_max_type = 0;                // largest type of the current architectures
   // n_t particle types (0: the two types A, B of the packed grid)
   uint32_t n_types = 0;
@@ -211,6 +213,7 @@ void derive(soma_t* h) {
   h->K_b = (d.N > 1) ? 3.0 * (double)(d.N - 1) / (2.0 * h->Re * h->Re) : 0.0;
   h->sigma = (d.N > 1) ? h->Re / std::sqrt(3.0 * (double)(d.N - 1)) : 0.0;
   h->M = d.n_chains * d.N;
+  h->M_real = h->M;
   const double cells = (double)d.grid[0] * (double)d.grid[1] * (double)d.grid[2];
   // rho_0 dL^3 of the whole system (a shard holds part of its particles)
   const uint64_t M_all = (d.n_chains_total ? d.n_chains_total : d.n_chains) * d.N;
@@ -242,6 +245,7 @@ void derive(soma_t* h) {
   g.replica = d.replica_id;
   g.chain_base = d.n_chains_total ? d.chain_offset : 0;
   g.id_base = g.chain_base * d.N;
+  g.particles = M_all;
 }
 
 size_t wbytes(int dtype) { return dtype == 0 ? 4 : 2; }
@@ -267,6 +271,7 @@ void release(soma_t* h) {
   cudaFree(h->d_topo_pmask);
   cudaFree(h->d_topo_ptab);
   cudaFree(h->d_topo_ttab);
+  cudaFree(h->d_topo_len);
   cudaFree(h->nt[0]);
   cudaFree(h->nt[1]);
   cudaFree(h->wt);
@@ -367,6 +372,7 @@ TopoArgs topo_args(soma_t* h, const SweepArgs& sa) {
   t.pmask = h->d_topo_pmask;
   t.ptab = h->d_topo_ptab;
   t.mol_arch = h->d_arch;
+  t.alen = h->d_topo_len;
   t.ttab = h->d_topo_ttab;
   t.wt = h->wt;
   t.nt0 = h->nt[0];
@@ -484,7 +490,8 @@ soma_status update_fields(soma_t* h) {
   uint32_t* nn = h->n[h->host_sweep & 1];
   SOMA_CUDA(cudaMemsetAsync(nn, 0, sizeof(uint32_t) * h->g.cells, h->stream));
   SOMA_CUDA(launch_histogram(h->g, h->x(), h->y(), h->z(), nn, h->sm_count, h->stream,
-                             h->d_seq, h->d_seq ? h->d_arch : nullptr));
+                             h->d_seq, h->d_seq ? h->d_arch : nullptr,
+                             h->has_topo ? h->d_topo_len : nullptr));
   ++h->launches;
   const FieldArgs fa = field_args(h, 0);
   SOMA_CUDA(launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count, h->stream));
@@ -668,7 +675,8 @@ soma_status soma_shard_counts(soma_t* h, uint32_t* counts, size_t cells) {
   uint32_t* nn = h->n[h->host_sweep & 1];
   SOMA_CUDA(cudaMemsetAsync(nn, 0, sizeof(uint32_t) * cells, h->stream));
   SOMA_CUDA(launch_histogram(h->g, h->x(), h->y(), h->z(), nn, h->sm_count, h->stream,
-                             h->d_seq, h->d_seq ? h->d_arch : nullptr));
+                             h->d_seq, h->d_seq ? h->d_arch : nullptr,
+                             h->has_topo ? h->d_topo_len : nullptr));
   ++h->launches;
   SOMA_CUDA(cudaMemcpyAsync(counts, nn, sizeof(uint32_t) * cells, cudaMemcpyDefault, h->stream));
   h->shard_phase = 1;
@@ -816,6 +824,19 @@ soma_status soma_set_external(soma_t* h, const float* ext, const uint8_t* forbid
   return sync(h);
 }
 
+namespace {
+// Every slot of every molecule present: the density and particle count of the
+// description (after architectures of fewer particles are replaced).
+void restore_particles(soma_t* h) {
+  soma_t tmp;
+  tmp.desc = h->desc;
+  derive(&tmp);
+  h->rho_cell = tmp.rho_cell;
+  h->g.particles = tmp.g.particles;
+  h->M_real = h->M;
+}
+}  // namespace
+
 soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_arch,
                                    const uint8_t* arch, int src_on_device) {
   if (!h) return fail(SOMA_EINVAL, "handle is NULL");
@@ -823,6 +844,7 @@ soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_ar
   if (h->n_types) return fail(SOMA_ESTATE, "n_t types take architectures: call soma_set_types(h, 0, NULL) first");
   h->has_topo = false;
   h->topo_max_type = 0;
+  restore_particles(h);
   if (!seq) {   // back to the diblock of the description
     cudaFree(h->d_seq);
     cudaFree(h->d_arch);
@@ -881,15 +903,21 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
                                           h->n_types ? h->n_types : 2u);
   if (!why.empty()) return fail(SOMA_EINVAL, "%s", why.c_str());
   double bonds = 0.0;
+  uint64_t present = 0;
   for (size_t m = 0; m < a.size(); ++m) {
     if (a[m] >= n_arch) return fail(SOMA_EINVAL, "mol_arch[%zu] = %u >= n_arch = %u", m, a[m], n_arch);
     bonds += (double)T.bonds[a[m]];
+    present += T.len[a[m]];
   }
+  if (h->desc.n_chains_total && present != h->M)
+    return fail(SOMA_EINVAL, "a shard takes architectures of N particles only (its density "
+                             "counts the whole system)");
   cudaError_t e;
   if (!h->d_topo_pmask) {
     e = cudaMalloc((void**)&h->d_topo_pmask, sizeof(uint64_t) * 256 * 64);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_topo_ptab, sizeof(uint32_t) * 256 * 64);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_topo_ttab, 256 * 64);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_topo_len, 256);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc architecture tables");
   }
   if (!h->d_seq) {
@@ -906,12 +934,20 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
   SOMA_CUDA(cudaMemcpyAsync(h->d_topo_ptab, T.ptab.data(), sizeof(uint32_t) * T.ptab.size(), up,
                             h->stream));
   SOMA_CUDA(cudaMemcpyAsync(h->d_topo_ttab, T.ttab.data(), T.ttab.size(), up, h->stream));
+  SOMA_CUDA(cudaMemcpyAsync(h->d_topo_len, T.len.data(), T.len.size(), up, h->stream));
   SOMA_CUDA(cudaMemcpyAsync(h->d_seq, T.seq.data(), sizeof(uint64_t) * n_arch, up, h->stream));
   SOMA_CUDA(cudaMemcpyAsync(h->d_arch, a.data(), a.size(), up, h->stream));
   soma_status s2 = sync(h);   // the host vectors are released on return
   if (s2 != SOMA_OK) return s2;
   h->topo_bonds = bonds;
   h->topo_max_type = T.max_type;
+  // rho_0 dL^3 and the particle count follow the molecules' particles (a
+  // shard holds molecules of N particles only and keeps the whole system's)
+  h->M_real = present;
+  if (!h->desc.n_chains_total) {
+    h->g.particles = present;
+    h->rho_cell = (double)present / (double)h->g.cells;
+  }
   h->topo_grid = h->shape.molecule
                      ? molecule_topology_grid(h->g.N, h->grid_dtype, h->sm_count, h->g.n_chains)
                      : topology_grid(h->grid_dtype, h->shape.big, h->sm_count, h->shape.n_tiles);
@@ -1059,7 +1095,9 @@ soma_status soma_topology_sets(const uint32_t* words, uint64_t n_words, const ui
   if (!why.empty()) return fail(SOMA_EINVAL, "%s", why.c_str());
   for (uint32_t a = 0; a < n_arch; ++a) {
     n_sets[a] = T.nsets[a];
-    for (uint32_t i = 0; i < N; ++i) sets[(size_t)a * N + i] = (uint8_t)((T.ptab[(size_t)a * 64 + i] >> 25) & 7u);
+    for (uint32_t i = 0; i < N; ++i)   // 0xFF: an absent slot (past the architecture's particles)
+      sets[(size_t)a * N + i] =
+          i < T.len[a] ? (uint8_t)((T.ptab[(size_t)a * 64 + i] >> 25) & 7u) : (uint8_t)0xFF;
   }
   return SOMA_OK;
 }
@@ -1106,7 +1144,7 @@ soma_status soma_observables(soma_t* h, soma_obs* out) {
   h->launches += 3;
   if (h->has_topo) {   // the bonds of the architectures replace those of the linear chain
     SOMA_CUDA(launch_topology_bonds(h->g, h->x(), h->y(), h->z(), h->d_topo_pmask, h->d_arch,
-                                    h->d_scratch, h->d_out, h->stream));
+                                    h->d_topo_len, h->d_scratch, h->d_out, h->stream));
     h->launches += 2;
   }
   if (h->n_types) {    // the non-bonded energy and largest count of the type planes
@@ -1131,7 +1169,7 @@ soma_status soma_observables(soma_t* h, soma_obs* out) {
   out->b2 = nb > 0 ? r[0] / nb : 0.0;
   out->accepted = c[1];
   out->sweeps = c[0];
-  out->attempted = c[0] * h->M;
+  out->attempted = c[0] * h->M_real;
   out->max_cell = (uint32_t)r[3];
   out->reserved = 0;
   return SOMA_OK;

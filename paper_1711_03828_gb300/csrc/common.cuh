@@ -139,6 +139,10 @@ struct Geom {
   // every chain draws.  Both 0 for a system held whole.  A sharded system has
   // fewer than 2^32 particles, so 32-bit counters stay exact.
   uint64_t chain_base, id_base;
+  // Particles the occupation numbers count: n_chains * N, less the absent
+  // slots of molecules with fewer particles than N; for a shard, those of the
+  // whole system (its grid holds the whole system's counts).
+  uint64_t particles;
 };
 
 // Per-axis cell, clamped into [0, n) (exact inside the supported range).

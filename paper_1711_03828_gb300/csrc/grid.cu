@@ -14,12 +14,14 @@ namespace soma {
 __global__ void histogram_kernel(const Geom g, const float* __restrict__ x,
                                  const float* __restrict__ y, const float* __restrict__ z,
                                  uint32_t* __restrict__ n, const uint64_t* __restrict__ seq,
-                                 const uint8_t* __restrict__ arch) {
+                                 const uint8_t* __restrict__ arch,
+                                 const uint8_t* __restrict__ alen) {
   const uint64_t M = g.n_chains * g.N;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += stride) {
     const uint64_t chain = m / g.N;
     const uint32_t i = (uint32_t)(m - chain * g.N);
+    if (alen && i >= alen[arch[chain]]) continue;   // an absent slot
     const bool isB = seq ? ((seq[arch[chain]] >> i) & 1ull) != 0 : i >= g.N_A;
     atomicAdd(n + cell_of(g, x[m], y[m], z[m]), isB ? 0x10000u : 1u);
   }
@@ -27,12 +29,12 @@ __global__ void histogram_kernel(const Geom g, const float* __restrict__ x,
 
 cudaError_t launch_histogram(const Geom& g, const float* x, const float* y, const float* z,
                              uint32_t* n, int sm_count, cudaStream_t st, const uint64_t* seq,
-                             const uint8_t* arch) {
+                             const uint8_t* arch, const uint8_t* alen) {
   const uint64_t M = g.n_chains * g.N;
   uint64_t blocks = (M + 255) / 256;
   const uint64_t cap = (uint64_t)sm_count * 8;
   if (blocks > cap) blocks = cap;
-  histogram_kernel<<<(unsigned)blocks, 256, 0, st>>>(g, x, y, z, n, seq, arch);
+  histogram_kernel<<<(unsigned)blocks, 256, 0, st>>>(g, x, y, z, n, seq, arch, alen);
   return cudaGetLastError();
 }
 
@@ -447,7 +449,7 @@ cudaError_t launch_structure_factor(const Geom& g, const uint32_t* n, const doub
   uint64_t nb = ((uint64_t)g.cells + 255) / 256;
   if (nb > SQ_BLOCKS) nb = SQ_BLOCKS;
   sq_kernel<<<(unsigned)nb, 256, 0, st>>>(g, n, tw, k, part);
-  const double invM = 1.0 / ((double)g.n_chains * (double)g.N);
+  const double invM = 1.0 / (double)g.particles;
   sq_final_kernel<<<1, SQ_MAX, 0, st>>>(part, (int)nb, k, invM, out);
   return cudaGetLastError();
 }

@@ -40,10 +40,12 @@ cudaError_t launch_init(const Geom& g, float* x, float* y, float* z, double sigm
 cudaError_t launch_sort_chains(const Geom& g, const float* src, uint64_t src_plane, float* dst,
                                uint64_t dst_plane, uint64_t* keys, uint64_t n_pad, int sm_count,
                                cudaStream_t st);
-// seq/arch: the per-chain type sequences of a mixture (NULL: diblocks of N_A A particles)
+// seq/arch: the per-chain type sequences of a mixture (NULL: diblocks of N_A A particles);
+// alen: particles of each architecture (NULL: all N), absent slots not counted
 cudaError_t launch_histogram(const Geom& g, const float* x, const float* y, const float* z,
                              uint32_t* n, int sm_count, cudaStream_t st,
-                             const uint64_t* seq = nullptr, const uint8_t* arch = nullptr);
+                             const uint64_t* seq = nullptr, const uint8_t* arch = nullptr,
+                             const uint8_t* alen = nullptr);
 cudaError_t launch_range_check(const float* p, uint64_t n, float lim, unsigned* flag, int sm_count,
                                cudaStream_t st);
 cudaError_t launch_fields(const FieldArgs& a, unsigned* arrive, int grid_dtype, int sm_count,
@@ -111,6 +113,7 @@ struct TopoArgs {
   const uint64_t* pmask;     // partners of particle i of architecture a: [a*64 + i]
   const uint32_t* ptab;      // [a*64 + i]: degree, first three partners, type, set, sets
   const uint8_t* mol_arch;   // architecture of every molecule
+  const uint8_t* alen;       // particles of each architecture (the slots past it are absent)
   // n_t types: type of particle i of architecture a ([a*64 + i]), the field
   // planes (n_types * cells) and the count planes of both parities
   const uint8_t* ttab;
@@ -126,9 +129,13 @@ struct TopologyTables {
   std::vector<uint8_t> nsets;    // n_arch
   std::vector<uint64_t> seq;     // type bits (bit i: particle i is B)
   std::vector<uint32_t> bonds;   // bonds per architecture
+  std::vector<uint8_t> len;      // particles per architecture (<= N; the rest absent)
 };
-// Checks an architecture array against a system of N particles per molecule
-// and derives the tables; returns an empty string or what is wrong.
+// Checks an architecture array against a system of N particle slots per
+// molecule (an architecture holds 1..N particles, the first slots of its
+// molecules) and derives the tables -- an absent slot has table word 0 (no
+// sets), no partners and type byte 0xFF; returns an empty string or what is
+// wrong.
 std::string topology_tables(const uint32_t* words, uint64_t n_words, const uint32_t* start,
                             uint32_t n_arch, uint32_t N, TopologyTables* out,
                             uint32_t n_types = 2);
@@ -141,10 +148,12 @@ cudaError_t launch_sweep_topology(const TopoArgs& a, int grid, int grid_dtype, b
 int molecule_topology_grid(uint32_t N, int grid_dtype, int sm_count, uint64_t n_chains);
 cudaError_t launch_molecule_topology(const TopoArgs& a, int grid, int grid_dtype, cudaStream_t st,
                                      bool types = false);
-// out[0] = sum over the bonds of the architectures of |b|^2 (FP64); part: OBS_BLOCKS doubles
+// out[0] = sum over the bonds of the architectures of |b|^2, out[1] = sum over
+// the molecules of |r_last - r_0|^2 with r_last the last particle of each
+// molecule's architecture (lengths alen) (FP64); part: 2 OBS_BLOCKS doubles
 cudaError_t launch_topology_bonds(const Geom& g, const float* x, const float* y, const float* z,
-                                  const uint64_t* pmask, const uint8_t* mol_arch, double* part,
-                                  double* out, cudaStream_t st);
+                                  const uint64_t* pmask, const uint8_t* mol_arch,
+                                  const uint8_t* alen, double* part, double* out, cudaStream_t st);
 
 // n_t particle types (types.cu).
 constexpr int TYPES_MAX = 8;

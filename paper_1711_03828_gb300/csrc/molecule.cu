@@ -63,14 +63,18 @@ __device__ __forceinline__ void molecule_body(const SweepArgs& p, const TopoArgs
       const uint64_t chain = chain0 + t;
       // type sequence of this chain (bit i set: particle i is B)
       const uint64_t seq = p.seq ? __ldg(p.seq + __ldg(p.arch + chain)) : 0ull;
-      const uint32_t* tab = TOPO ? tp.ptab + (uint32_t)__ldg(tp.mol_arch + chain) * 64u : nullptr;
+      const uint32_t arch_k = TOPO ? (uint32_t)__ldg(tp.mol_arch + chain) : 0u;
+      const uint32_t* tab = TOPO ? tp.ptab + arch_k * 64u : nullptr;
+      // particles of the molecule: its architecture's (the slots past them
+      // are absent), else N; it makes that many attempts on its own particles
+      const uint32_t len = TOPO ? (uint32_t)__ldg(tp.alen + arch_k) : N;
       float* X = STAGE ? sx + t * N : p.x + chain * N;
       float* Y = STAGE ? sy + t * N : p.y + chain * N;
       float* Z = STAGE ? sz + t * N : p.z + chain * N;
-      for (uint32_t j = 0; j < N; ++j) {
+      for (uint32_t j = 0; j < len; ++j) {
         const uint64_t id = chain * N + j + p.g.id_base;
         const uint4 r = philox_rk(make_uint4((uint32_t)id, (uint32_t)(id >> 32), sweep, ctr3), p.g);
-        const uint32_t i = ((r.w & 0xFFu) * N) >> 8;
+        const uint32_t i = ((r.w & 0xFFu) * len) >> 8;
         const float xo = X[i], yo = Y[i], zo = Z[i];
         const float xn = __fmaf_rn(a, uniform_sym(r.x), xo);
         const float yn = __fmaf_rn(a, uniform_sym(r.y), yo);
@@ -143,7 +147,9 @@ __device__ __forceinline__ void molecule_body(const SweepArgs& p, const TopoArgs
       } else {
         x = p.x[m0 + q]; y = p.y[m0 + q]; z = p.z[m0 + q];
       }
-      if (MULTI) {
+      if (TOPO && ci >= (uint32_t)__ldg(tp.alen + __ldg(tp.mol_arch + chain0 + q / N))) {
+        // an absent slot: written back unchanged, not counted
+      } else if (MULTI) {
         const uint32_t ty = __ldg(tp.ttab + (uint32_t)__ldg(tp.mol_arch + chain0 + q / N) * 64u + ci);
         atomicAdd(nacc + (size_t)ty * p.g.cells + cell_of(p.g, x, y, z), 1u);
       } else {

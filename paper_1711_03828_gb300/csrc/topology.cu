@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
       const uint32_t a = (a2 >> (8 * j)) & 0xFFu;
       const IDX m = base + tl;
       const uint32_t pw = valid ? __ldg(t.ptab + a * TOPO_TILE + ci) : 0u;
+      const bool present = pw_sets(pw) != 0u;   // false: empty slot or absent particle
       const IDX mc = m + (IDX)p.g.id_base;
       const uint32_t hi = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)mc >> 32) : 0u;
       const uint4 r = philox_rk(make_uint4((uint32_t)mc, hi, sweep, ctr3), p.g);
@@ -192,15 +193,15 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
       const uint32_t co = cell_of(p.g, x[j], y[j], z[j]);
       const uint32_t cn = cell_of(p.g, xn, yn, zn);
       // type: the architecture's type byte (n_t types) or the A/B bit
-      const uint32_t type = MULTI ? (valid ? __ldg(t.ttab + a * TOPO_TILE + ci) : 0u)
+      const uint32_t type = MULTI ? (present ? __ldg(t.ttab + a * TOPO_TILE + ci) : 0u)
                                   : (uint32_t)pw_is_B(pw);
       float dEf = 0.f;
       if (MULTI) {
         const float* wt = t.wt + (size_t)type * p.g.cells;
-        if (valid) dEf = __ldg(wt + cn) - __ldg(wt + co);
+        if (present) dEf = __ldg(wt + cn) - __ldg(wt + co);
       } else {
         const WT* wt = type ? wB : wA;
-        if (valid) dEf = load_w<WT>(wt, cn) - load_w<WT>(wt, co);
+        if (present) dEf = load_w<WT>(wt, cn) - load_w<WT>(wt, co);
       }
       S.P[tl] = make_float4(x[j], y[j], z[j], __uint_as_float(co));
       S.T[tl] = make_float4(xn, yn, zn, -log_uniform_open(r.w) - dEf);
@@ -282,6 +283,7 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
       if (tl >= nmono) continue;
       const IDX m = base + tl;
       const float4 Pf = S.P[tl];
+      if ((step[j] & 15u) == 15u) continue;   // an absent slot: kept, not counted
       __stcs(p.x + m, Pf.x);
       __stcs(p.y + m, Pf.y);
       __stcs(p.z + m, Pf.z);
@@ -319,15 +321,24 @@ const void* topology_kernel_ptr(int grid_dtype, bool big, bool types) {
 __global__ void __launch_bounds__(256) topology_bonds_kernel(
     const Geom g, const float* __restrict__ x, const float* __restrict__ y,
     const float* __restrict__ z, const uint64_t* __restrict__ pmask,
-    const uint8_t* __restrict__ mol_arch, double* __restrict__ part) {
-  __shared__ double sh[32];
-  double v = 0.0;
+    const uint8_t* __restrict__ mol_arch, const uint8_t* __restrict__ alen,
+    double* __restrict__ part) {
+  __shared__ double sh[2 * 32];
+  double v = 0.0, re = 0.0;
   const uint64_t M = g.n_chains * g.N;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += stride) {
     const uint64_t mol = m / g.N;
     const uint32_t i = (uint32_t)(m - mol * g.N);
-    const uint64_t pm = __ldg(pmask + (uint32_t)__ldg(mol_arch + mol) * TOPO_TILE + i);
+    const uint32_t a = __ldg(mol_arch + mol);
+    const uint64_t pm = __ldg(pmask + a * TOPO_TILE + i);
+    if (i == 0u) {   // end to end: particle 0 to the architecture's last particle
+      const uint64_t e = m + (uint64_t)__ldg(alen + a) - 1u;
+      const double dx = (double)x[e] - (double)x[m];
+      const double dy = (double)y[e] - (double)y[m];
+      const double dz = (double)z[e] - (double)z[m];
+      re += dx * dx + dy * dy + dz * dz;
+    }
     // partners above i
     for (uint64_t mk = i < 63u ? pm >> (i + 1u) : 0ull; mk; mk &= mk - 1ull) {
       const uint64_t q = m + (uint64_t)__ffsll((long long)mk);
@@ -337,22 +348,36 @@ __global__ void __launch_bounds__(256) topology_bonds_kernel(
       v += dx * dx + dy * dy + dz * dz;
     }
   }
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  for (int o = 16; o > 0; o >>= 1) {
+    v += __shfl_xor_sync(FULL, v, o);
+    re += __shfl_xor_sync(FULL, re, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[threadIdx.x >> 5] = v;
+    sh[32 + (threadIdx.x >> 5)] = re;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
-    part[blockIdx.x] = s;
+    double s = 0.0, r = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      s += sh[k];
+      r += sh[32 + k];
+    }
+    part[2 * blockIdx.x] = s;
+    part[2 * blockIdx.x + 1] = r;
   }
 }
 
 __global__ void topology_bonds_final_kernel(const double* __restrict__ part, int nb,
                                             double* __restrict__ out) {
   if (threadIdx.x != 0) return;
-  double s = 0.0;
-  for (int k = 0; k < nb; ++k) s += part[k];
+  double s = 0.0, r = 0.0;
+  for (int k = 0; k < nb; ++k) {
+    s += part[2 * k];
+    r += part[2 * k + 1];
+  }
   out[0] = s;
+  out[1] = r;
 }
 
 }  // namespace
@@ -369,19 +394,30 @@ std::string topology_tables(const uint32_t* w, uint64_t n_words, const uint32_t*
   std::vector<uint8_t> set_of(TOPO_TILE);
   T->seq.assign(n_arch, 0);
   T->bonds.assign(n_arch, 0);
+  T->len.assign(n_arch, 0);
+  // absent slots: no partners, no sets (table word 0), type byte 0xFF
+  std::fill(T->ttab.begin(), T->ttab.end(), (uint8_t)0xFF);
   for (uint32_t a = 0; a < n_arch; ++a) {
     const uint64_t s = start[a];
-    if (s >= n_words || s + 1u + N > n_words) {
+    if (s >= n_words) {
       snprintf(msg, sizeof msg, "architecture %u: block at word %llu runs past the %llu words", a,
                (unsigned long long)s, (unsigned long long)n_words);
       return msg;
     }
-    if (w[s] != N) {
-      snprintf(msg, sizeof msg, "architecture %u has %u particles, the system %u", a, w[s], N);
+    const uint32_t n_a = w[s];   // particles of this architecture, the first n_a slots
+    if (n_a < 1 || n_a > N) {
+      snprintf(msg, sizeof msg, "architecture %u has %u particles (1..%u, the system's N)", a, n_a,
+               N);
       return msg;
     }
+    if (s + 1u + n_a > n_words) {
+      snprintf(msg, sizeof msg, "architecture %u: block at word %llu runs past the %llu words", a,
+               (unsigned long long)s, (unsigned long long)n_words);
+      return msg;
+    }
+    T->len[a] = (uint8_t)n_a;
     uint64_t partners[TOPO_TILE] = {0};  // bit j of partners[i]: i and j are bonded
-    for (uint32_t i = 0; i < N; ++i) {
+    for (uint32_t i = 0; i < n_a; ++i) {
       const uint32_t mw = w[s + 1u + i];
       const uint32_t type = mw & 0xFFu;
       if (type >= n_types) {
@@ -407,7 +443,7 @@ std::string topology_tables(const uint32_t* w, uint64_t n_words, const uint32_t*
           return msg;
         }
         const int64_t j = (int64_t)i + ((int32_t)bw >> 5);
-        if (j < 0 || j >= (int64_t)N || j == (int64_t)i) {
+        if (j < 0 || j >= (int64_t)n_a || j == (int64_t)i) {
           snprintf(msg, sizeof msg, "architecture %u particle %u: partner %lld outside the molecule",
                    a, i, (long long)j);
           return msg;
@@ -422,8 +458,8 @@ std::string topology_tables(const uint32_t* w, uint64_t n_words, const uint32_t*
       }
     }
     uint32_t n_sets = 0;
-    for (uint32_t i = 0; i < N; ++i) {
-      for (uint32_t j = 0; j < N; ++j)
+    for (uint32_t i = 0; i < n_a; ++i) {
+      for (uint32_t j = 0; j < n_a; ++j)
         if ((partners[i] >> j & 1ull) != (partners[j] >> i & 1ull)) {
           snprintf(msg, sizeof msg, "architecture %u: bond %u-%u listed on one side only", a, i, j);
           return msg;
@@ -443,7 +479,7 @@ std::string topology_tables(const uint32_t* w, uint64_t n_words, const uint32_t*
       n_sets = std::max(n_sets, c + 1u);
     }
     T->nsets[a] = (uint8_t)n_sets;
-    for (uint32_t i = 0; i < N; ++i) {
+    for (uint32_t i = 0; i < n_a; ++i) {
       T->pmask[(size_t)a * TOPO_TILE + i] = partners[i];
       // degree, first three partners, type, set, sets (see pw_* above)
       uint32_t w = (uint32_t)__builtin_popcountll(partners[i]);
@@ -475,12 +511,13 @@ cudaError_t launch_sweep_topology(const TopoArgs& a, int grid, int grid_dtype, b
 }
 
 cudaError_t launch_topology_bonds(const Geom& g, const float* x, const float* y, const float* z,
-                                  const uint64_t* pmask, const uint8_t* mol_arch, double* part,
-                                  double* out, cudaStream_t st) {
+                                  const uint64_t* pmask, const uint8_t* mol_arch,
+                                  const uint8_t* alen, double* part, double* out,
+                                  cudaStream_t st) {
   const uint64_t M = g.n_chains * g.N;
   uint64_t nb = (M + 255) / 256;
   if (nb > OBS_BLOCKS) nb = OBS_BLOCKS;
-  topology_bonds_kernel<<<(unsigned)nb, 256, 0, st>>>(g, x, y, z, pmask, mol_arch, part);
+  topology_bonds_kernel<<<(unsigned)nb, 256, 0, st>>>(g, x, y, z, pmask, mol_arch, alen, part);
   topology_bonds_final_kernel<<<1, 32, 0, st>>>(part, (int)nb, out);
   return cudaGetLastError();
 }

@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(256) histogram_types_kernel(
     const uint64_t mol = m / g.N;
     const uint32_t i = (uint32_t)(m - mol * g.N);
     const uint32_t t = __ldg(ttab + (uint32_t)__ldg(mol_arch + mol) * 64u + i);
+    if (t == 0xFFu) continue;   // an absent slot
     atomicAdd(n + (size_t)t * g.cells + cell_of(g, x[m], y[m], z[m]), 1u);
   }
 }

@@ -226,5 +226,12 @@ def test_shard_calls_are_refused_out_of_order(on_stream):
     with pytest.raises(SomaError) as e:
         whole.shard_sweep(buf)        # not a shard
     assert e.value.status == _abi.SOMA_ESTATE
+    # molecules of fewer than N particles: a shard's density counts the whole system
+    mols = [workloads.linear_architecture(d.N), workloads.linear_architecture(d.N // 2, 0)]
+    words, starts = workloads.encode_architectures(mols)
+    with pytest.raises(SomaError) as e:
+        s.set_topology(words, starts, np.arange(sd.n_chains, dtype=np.uint8) % 2)
+    assert e.value.status == _abi.SOMA_EINVAL
+    s.set_topology(words, starts, np.zeros(sd.n_chains, np.uint8))   # all of N: taken
     s.close()
     whole.close()

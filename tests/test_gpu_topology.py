@@ -38,6 +38,17 @@ CASES = {
     "N5_ring_star": (
         dict(n_chains=6000, N=5, box_Re=(1.0, 1.0, 1.0), grid=(6, 6, 6)),
         [workloads.ring_architecture(5), workloads.star_architecture(4, 1)]),
+    # molecules of several lengths in slots of N (the rest of a molecule's
+    # slots absent): a diblock of 16, a B homopolymer of 8, a star of 10, a
+    # ring of 12 and A monomers
+    "N16_blend_lengths": (
+        dict(n_chains=2400, N=16, box_Re=(2.0, 2.0, 2.0), grid=(12, 12, 12)),
+        [workloads.linear_architecture(16), workloads.linear_architecture(8, 0),
+         workloads.star_architecture(3, 3), workloads.ring_architecture(12), ([0], [])]),
+    # a homopolymer blend of lengths 32 (A) and 11 (B)
+    "N32_homopolymer_blend": (
+        dict(n_chains=1500, N=32, box_Re=(2.0, 2.0, 2.0), grid=(12, 12, 12)),
+        [workloads.linear_architecture(32, 32), workloads.linear_architecture(11, 0)]),
 }
 
 
@@ -144,7 +155,7 @@ def test_sort_molecules_relabels_like_the_oracle(cuda_device):
 
 
 @pytest.mark.parametrize("name", ["N16_star_comb_ring_linear", "N9_odd_ring_star",
-                                  "N64_star_triangles_ring"])
+                                  "N64_star_triangles_ring", "N16_blend_lengths"])
 def test_topology_molecule_iteration_matches_oracle(cuda_device, name):
     """The molecule-parallel iteration (N attempts per molecule on random
     particles) with molecules of any architecture: one cycle per start,
@@ -183,14 +194,20 @@ def test_topology_molecule_iteration_matches_oracle(cuda_device, name):
     assert mism <= 3
 
 
-def test_topology_observables_match_oracle(cuda_device):
-    d, mols, arch, words, starts, pos0 = _setup("N16_star_comb_ring_linear")
+@pytest.mark.parametrize("name", ["N16_star_comb_ring_linear", "N16_blend_lengths"])
+def test_topology_observables_match_oracle(cuda_device, name):
+    """FP64 observables and S(q) against the oracle; with molecules of several
+    lengths also the density (rho_0 dL^3 of the present particles), R_e^2 to
+    each molecule's own last particle and the attempted moves."""
+    d, mols, arch, words, starts, pos0 = _setup(name)
     gpu = System(d)
     gpu.set_topology(words, starts, arch)
     gpu.set_positions(pos0)
     gpu.update_fields()
     o = gpu.observables()
-    gpu.close()
+    m = [(1, 0, 0), (0, 1, 2), (3, 2, 1), (5, 5, 5)]
+    sq = gpu.structure_factor(m)
+    par = gpu.parameters()
     orc = oracle_system(d)
     orc.set_topology(words, starts, arch)
     p = _pos(pos0)
@@ -198,6 +215,12 @@ def test_topology_observables_match_oracle(cuda_device):
     ref = orc.observables(p, nA, nB)
     for k in ("E_b", "E_nb", "Re2", "b2", "E_tot"):
         assert o[k] == pytest.approx(ref[k], rel=1e-9), k
+    np.testing.assert_allclose(sq, orc.structure_factor(nA, nB, m), rtol=1e-9)
+    assert par["rho_cell"] == pytest.approx(orc.params.rho_cell, rel=1e-15)
+    present = int(np.array([len(t) for t, _ in mols])[arch].sum())
+    gpu.sweep(2)
+    assert gpu.observables()["attempted"] == 2 * present
+    gpu.close()
 
 
 def test_topology_graph_replay_is_identical(cuda_device):
@@ -287,8 +310,10 @@ def test_topology_arguments_are_checked(cuda_device):
     bad[first] = (int(bad[first]) & 0x1F) | (4 << 5)             # 0-4 listed at 0 only
     expect_einval(bad, gst, a0)
     expect_einval(good, np.array([len(good) - 2], np.uint32), a0)   # block past the end
+    lin10, st10 = workloads.encode_architectures([workloads.linear_architecture(10)])
+    expect_einval(lin10, st10, a0)                       # 10 particles, more than N = 9
     lin8, st8 = workloads.encode_architectures([workloads.linear_architecture(8)])
-    expect_einval(lin8, st8, a0)                         # N = 8 in a system of N = 9
+    s.set_topology(lin8, st8, a0)                        # 8 of N = 9: the ninth slot absent
     K9 = ([0] * 9, [(i, j) for i in range(9) for j in range(i + 1, 9)])
     k9, k9s = workloads.encode_architectures([K9])
     expect_einval(k9, k9s, a0)                           # nine sets

@@ -69,7 +69,9 @@ def test_malformed_arrays_are_refused(soma_lib):
     bad = good.copy()
     bad[first] = (int(bad[first]) & 0x1F) | (4 << 5)
     assert "one side" in refused(bad, gst)
-    assert "runs past" in refused(good, np.array([len(good) - 2], np.uint32))
+    past = np.concatenate([good, np.array([9], np.uint32)])   # a block of 9 at the last word
+    assert "runs past" in refused(past, np.array([len(past) - 1], np.uint32))
+    assert "particles" in refused(good, np.array([len(good) - 2], np.uint32))  # count garbage
     assert "particles" in refused(good, gst, N=8)
     K9 = ([0] * 9, [(i, j) for i in range(9) for j in range(i + 1, 9)])
     w9, s9 = workloads.encode_architectures([K9])
@@ -81,3 +83,26 @@ def test_malformed_arrays_are_refused(soma_lib):
     ends = [k for k in range(first, len(good)) if good[k] & 1]
     last[ends[-1]] &= ~np.uint32(1)    # and the array's final list runs off the end
     refused(last, gst)
+
+
+def test_sets_of_architectures_shorter_than_N(soma_lib, oracle_lib):
+    """Molecules of several lengths: an architecture of n <= N particles fills
+    the first n slots; the library's sets equal the oracle's on them and mark
+    the absent slots 0xFF; more than N particles, or none, is refused."""
+    mols = [workloads.linear_architecture(16), workloads.linear_architecture(8, 0),
+            workloads.star_architecture(3, 3), workloads.ring_architecture(12), ([0], [])]
+    words, starts = workloads.encode_architectures(mols)
+    ls, ln = topology_sets(words, starts, 16)
+    for a, (types, _) in enumerate(mols):
+        os_, on = oracle.topology_sets(words, int(starts[a]))
+        n = len(types)
+        assert ln[a] == on
+        np.testing.assert_array_equal(ls[a, :n], os_)
+        assert np.all(ls[a, n:] == 0xFF)
+    with pytest.raises(SomaError) as e:
+        topology_sets(words, starts, 12)               # the diblock of 16 does not fit
+    assert e.value.status == _abi.SOMA_EINVAL and "particles" in _abi.soma_last_error()
+    empty = words.copy()
+    empty[starts[4]] = 0                               # an architecture of no particles
+    with pytest.raises(SomaError):
+        topology_sets(empty, starts, 16)
