@@ -82,8 +82,9 @@ MUTANTS = [
      PIN.check_learned_features_hand_values),
     ("gradient_interpolation_reversed", "g[d] = (1.0 - t) * lo + t * hi;", "g[d] = t * lo + (1.0 - t) * hi;",
      PIN.check_learned_features_hand_values),
-    ("molecule_choice_half", "const uint32_t i = (uint32_t)(((uint64_t)(w[3] & 0xFFu) * s->N) >> 8);",
-     "const uint32_t i = (uint32_t)(((uint64_t)(w[3] & 0xFFu) * s->N) >> 9);",
+    ("molecule_choice_half",
+     "const uint32_t i = (uint32_t)(((uint64_t)(w[3] & 0xFFu) * or_length(s, chain)) >> 8);",
+     "const uint32_t i = (uint32_t)(((uint64_t)(w[3] & 0xFFu) * or_length(s, chain)) >> 9);",
      PIN.check_molecule_iteration_attempts),
     ("k1_coupling_sign", "      a = comp + chi0 * phiB;", "      a = comp - chi0 * phiB;",
      functools.partial(PIN.check_fields_are_the_energy_derivative, hamiltonian=1)),
