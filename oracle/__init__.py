@@ -397,6 +397,8 @@ class System:
             self.s.n_topo = 0
             self.s.rho_cell = float(self.M) / self.cells
             return
+        # the learned proposal's features are those of a linear chain
+        assert int(self.s.move) != 2, "architectures take the uniform or smart Monte Carlo move"
         self._topo = np.ascontiguousarray(words, np.uint32)
         self._topo_start = np.ascontiguousarray(starts, np.uint32)
         self._arch = np.ascontiguousarray(arch, np.uint8)

@@ -531,7 +531,8 @@ static void or_move_attempt(const or_system* s, float* x, float* y, float* z,
 /* Smart Monte Carlo (force-biased) move of Sec. 2.2 (Rossky, Doll, Friedman;  */
 /* Pangali, Rao, Berne): trial displacement dr = A F(r) + sqrt(2A) xi with xi a */
 /* vector of standard normals and F the force on the particle: the bonded      */
-/* force -2 k0/2 sum_n (r - r_n) plus minus the field gradient, taken by        */
+/* force -2 k0/2 sum_n (r - r_n) over its bond partners n (of any architecture) */
+/* plus minus the field gradient of its type, taken by                          */
 /* central differences of omega_t over the neighbouring cells.  Accepted with   */
 /* min(1, exp(-dE) T(r'->r)/T(r->r')), T(r->r') = exp(-|r'-r-A F(r)|^2/(4A)),   */
 /* which keeps the move exact for any force.  A = a^2/6, so that the per-axis    */
@@ -548,14 +549,17 @@ static uint64_t or_cell_shift(const or_system* s, uint64_t c, int axis, int step
   return ((uint64_t)k[2] * s->grid[1] + (uint64_t)k[1]) * s->grid[0] + (uint64_t)k[0];
 }
 
+/* Force on particle i of chain at r: the harmonic bonds to its partners (the
+ * linear neighbours i-1, i+1, or the bond list of the molecule's
+ * architecture, Sec. 3.2.1) and the field force of its type's plane. */
 static void or_force(const or_system* s, const float* x, const float* y, const float* z,
                      const double* w_t, uint64_t chain, uint32_t i, const double r[3],
                      double F[3]) {
   for (int d = 0; d < 3; ++d) F[d] = 0.0;
-  for (int side = -1; side <= 1; side += 2) {
-    long long jn = (long long)i + side;
-    if (jn < 0 || jn >= (long long)s->N) continue;
-    uint64_t n = chain * s->N + (uint64_t)jn;
+  uint32_t fpart[256];
+  const uint32_t n_fpart = or_partners(s, chain, i, fpart);
+  for (uint32_t b = 0; b < n_fpart; ++b) {
+    uint64_t n = chain * s->N + fpart[b];
     double rn[3] = { x[n], y[n], z[n] };
     for (int d = 0; d < 3; ++d) F[d] -= 2.0 * s->K_b * (r[d] - rn[d]);
   }
@@ -570,7 +574,9 @@ static void or_move_smc(const or_system* s, float* x, float* y, float* z,
                         float* trial, uint64_t* acc, uint64_t* ties) {
   const uint32_t N = s->N;
   const uint64_t m = chain * N + i;
-  const double* w_t = or_is_B(s, chain, i) ? wB : wA;
+  /* the field plane of the particle's type (A / B, or one of n_t types) */
+  const double* w_t = (s->n_types && s->w_types) ? s->w_types[or_type(s, chain, i)]
+                                                  : (or_is_B(s, chain, i) ? wB : wA);
   uint32_t w1[4], w2[4];
   or_draw(s, OR_PURPOSE_MOVE, m, sweep, w1);
   or_draw(s, OR_PURPOSE_MOVE2, m, sweep, w2);
@@ -594,11 +600,12 @@ static void or_move_smc(const or_system* s, float* x, float* y, float* z,
     for (int d = 0; d < 3; ++d) trial[d * M + m] = (float)r_new[d];
   }
   or_force(s, x, y, z, w_t, chain, i, r_new, F_new);
+  /* bonded energy change over the partners, as in the uniform move */
+  uint32_t epart[256];
+  const uint32_t n_epart = or_partners(s, chain, i, epart);
   double dEb = 0.0;
-  for (int side = -1; side <= 1; side += 2) {
-    long long jn = (long long)i + side;
-    if (jn < 0 || jn >= (long long)N) continue;
-    uint64_t n = chain * N + (uint64_t)jn;
+  for (uint32_t b = 0; b < n_epart; ++b) {
+    uint64_t n = chain * N + epart[b];
     double rn[3] = { x[n], y[n], z[n] };
     for (int d = 0; d < 3; ++d)
       dEb += s->K_b * ((r_new[d] - rn[d]) * (r_new[d] - rn[d]) - (r_old[d] - rn[d]) * (r_old[d] - rn[d]));
@@ -1068,7 +1075,10 @@ void or_sweep_trial(const or_system* s, float* x, float* y, float* z,
         for (uint32_t i = 0; i < N; ++i) {
           if (s->topo_set[(uint64_t)a * N + i] != order[k]) continue;
           uint64_t a1 = 0, t1 = 0;
-          or_move_uniform(s, x, y, z, wA, wB, sweep, chain, i, margin, accepted, trial, &a1, &t1);
+          if (s->move == 1)
+            or_move_smc(s, x, y, z, wA, wB, sweep, chain, i, margin, accepted, trial, &a1, &t1);
+          else
+            or_move_uniform(s, x, y, z, wA, wB, sweep, chain, i, margin, accepted, trial, &a1, &t1);
           acc += a1;
           ties += t1;
         }

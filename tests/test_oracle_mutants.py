@@ -142,6 +142,19 @@ MUTANTS = [
      "const uint32_t last = s->N - 1u;", TOPO.check_blend_ideal_statistics),
     ("blend_sq_over_all_slots", "  const double M = or_particles(s);",
      "  const double M = (double)s->n_chains * (double)s->N;", TOPO.check_blend_histogram_and_density),
+    # smart Monte Carlo on molecules of any architecture and type
+    ("smc_force_linear_on_architectures", "  const uint32_t n_fpart = or_partners(s, chain, i, fpart);",
+     "  uint32_t n_fpart = 0;\n  if (i > 0) fpart[n_fpart++] = i - 1u;\n"
+     "  if (i + 1u < s->N) fpart[n_fpart++] = i + 1u;", TOPO.check_smc_force_follows_the_architecture),
+    ("smc_bond_energy_linear_on_architectures", "  const uint32_t n_epart = or_partners(s, chain, i, epart);",
+     "  uint32_t n_epart = 0;\n  if (i > 0) epart[n_epart++] = i - 1u;\n"
+     "  if (i + 1u < s->N) epart[n_epart++] = i + 1u;",
+     lambda L: TOPO.check_ideal_star_and_ring_closed_forms(L, move=1)),
+    ("smc_architectures_take_uniform_moves", "          if (s->move == 1)\n            or_move_smc(",
+     "          if (0)\n            or_move_smc(",
+     lambda L: TOPO.check_linear_topology_is_the_linear_chain(L, 0, 1)),
+    ("smc_types_field_plane", "? s->w_types[or_type(s, chain, i)]\n", "? s->w_types[0]\n",
+     lambda L: TYPES.check_two_types_equal_the_AB_path(L, 0, 1)),
     # n_t particle types
     ("types_K0_sign", "else v = v - 0.5 * chi0 * (phi[i] - phi[k]);",
      "else v = v + 0.5 * chi0 * (phi[i] - phi[k]);",

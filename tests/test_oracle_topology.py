@@ -131,14 +131,15 @@ def _cycle_both(a, b, p, q, sweeps):
     assert a.observables(p, nA, nB) == b.observables(q, nA, nB)
 
 
-def check_linear_topology_is_the_linear_chain(lib=None, set_order=0):
+def check_linear_topology_is_the_linear_chain(lib=None, set_order=0, move=0):
     """The diblock written as an architecture array gives bit for bit the
     sweeps, occupation numbers and observables of the linear-chain path, and
     a mixture of two linear architectures those of the mixture path (SET
-    scheme, or the molecule-parallel iteration with set_order 2)."""
+    scheme, or the molecule-parallel iteration with set_order 2; uniform or
+    smart Monte Carlo moves, move 1)."""
     L = _L(lib)
     d = workloads.melt_small(n_chains=512, chiN=30.0, box_Re=(2.0, 2.0, 1.0), grid=(12, 12, 6),
-                             set_order=set_order)
+                             set_order=set_order, move=move)
     pos0 = workloads.random_walk_positions(d, seed=3)
     lin = oracle_system(d, L)
     top = oracle_system(d, L)
@@ -161,10 +162,10 @@ def check_linear_topology_is_the_linear_chain(lib=None, set_order=0):
     _cycle_both(mix, top2, p, q, 3)
 
 
-def _ideal(molecule, n_mol, L, sweeps, first):
+def _ideal(molecule, n_mol, L, sweeps, first, move=0):
     N = len(molecule[0])
     d = SystemDesc(n_chains=n_mol, N=N, f=0.5, box_Re=(2.0, 2.0, 1.0), grid=(12, 12, 6),
-                   chiN=0.0, kappaN=0.0, seed=7)
+                   chiN=0.0, kappaN=0.0, seed=7, move=move)
     s = oracle_system(d, L)
     words, starts = workloads.encode_architectures([molecule])
     s.set_topology(words, starts, np.zeros(n_mol, np.uint8))
@@ -193,17 +194,19 @@ def _graph_distance(N, bonds):
     return D
 
 
-def check_ideal_star_and_ring_closed_forms(lib=None):
+def check_ideal_star_and_ring_closed_forms(lib=None, move=0):
     """chiN = kappaN = 0: the bonds of a tree are independent Gaussians, so
     <|r_i - r_j|^2> = d_ij b0^2 with d_ij the graph distance; on a ring of N
     bonds the constraint that they sum to zero gives b0^2 d (N - d) / N.
-    b0^2 = R_e0^2/(N-1) is the bond length the spring constant fixes."""
+    b0^2 = R_e0^2/(N-1) is the bond length the spring constant fixes.  Under
+    either move (uniform, or smart Monte Carlo: the bonded energy over the
+    architecture's partners decides the acceptance)."""
     L = _L(lib)
     Re = 6.0
     for molecule, closed in ((workloads.star_architecture(3, 5), "tree"),
                              (workloads.ring_architecture(9), "ring")):
         N = len(molecule[0])
-        d, r2 = _ideal(molecule, 1024, L, 1400, 400)
+        d, r2 = _ideal(molecule, 1024, L, 1400, 400, move)
         b02 = Re**2 / (N - 1)
         D = _graph_distance(N, molecule[1])
         for dist in range(1, int(D.max()) + 1):
@@ -212,6 +215,36 @@ def check_ideal_star_and_ring_closed_forms(lib=None):
             want = dist * b02 if closed == "tree" else b02 * dist * (N - dist) / N
             se = per_mol.std() / math.sqrt(len(per_mol))
             assert abs(per_mol.mean() - want) < 5 * se, (closed, dist, per_mol.mean(), want, se)
+
+
+def check_smc_force_follows_the_architecture(lib=None):
+    """Smart Monte Carlo on branched and cyclic molecules at chiN = kappaN =
+    0: any force keeps the move exact (the proposal densities enter the
+    acceptance), so the force is pinned by efficiency.  With the force of the
+    molecule's own bonds the drift follows the harmonic well and nearly every
+    move is accepted (0.94-0.95 at the default step); a force taken from the
+    linear neighbours i - 1, i + 1 instead pulls the star's centre, the comb's
+    teeth and the ring's closing particles the wrong way (0.62-0.89)."""
+    L = _L(lib)
+    for molecule in (workloads.star_architecture(3, 5), workloads.star_architecture(7, 2),
+                     workloads.ring_architecture(9), workloads.comb_architecture(8, 4, 2)):
+        N = len(molecule[0])
+        n_mol = 1024
+        d = SystemDesc(n_chains=n_mol, N=N, f=0.5, box_Re=(2.0, 2.0, 1.0), grid=(12, 12, 6),
+                       chiN=0.0, kappaN=0.0, move=1, seed=7)
+        s = oracle_system(d, L)
+        words, starts = workloads.encode_architectures([molecule])
+        s.set_topology(words, starts, np.zeros(n_mol, np.uint8))
+        pos0 = workloads.architecture_positions(d, [molecule], np.zeros(n_mol, np.uint8), seed=13)
+        p = Positions(*[pos0[k].copy() for k in range(3)])
+        w0 = np.zeros(s.cells)
+        acc = att = 0
+        for sweep in range(20):
+            st, _, _ = s.sweep(p, w0, w0, sweep)
+            acc += st.accepted
+            att += st.attempted
+        assert att == 20 * d.M
+        assert acc / att > 0.93, (N, acc / att)
 
 
 def check_topology_observables_hand_values(lib=None):
@@ -249,13 +282,18 @@ def test_set_order_is_a_uniform_permutation(oracle_lib):
     check_set_order_is_a_uniform_permutation()
 
 
-@pytest.mark.parametrize("set_order", [0, 1, 2])
-def test_linear_topology_is_the_linear_chain(oracle_lib, set_order):
-    check_linear_topology_is_the_linear_chain(set_order=set_order)
+@pytest.mark.parametrize("set_order,move", [(0, 0), (1, 0), (2, 0), (0, 1), (1, 1)])
+def test_linear_topology_is_the_linear_chain(oracle_lib, set_order, move):
+    check_linear_topology_is_the_linear_chain(set_order=set_order, move=move)
 
 
-def test_ideal_star_and_ring_closed_forms(oracle_lib):
-    check_ideal_star_and_ring_closed_forms()
+@pytest.mark.parametrize("move", [0, 1])
+def test_ideal_star_and_ring_closed_forms(oracle_lib, move):
+    check_ideal_star_and_ring_closed_forms(move=move)
+
+
+def test_smc_force_follows_the_architecture(oracle_lib):
+    check_smc_force_follows_the_architecture()
 
 
 def test_topology_observables_hand_values(oracle_lib):

@@ -11,11 +11,11 @@ from paper_1711_03828_gb300 import SystemDesc, workloads
 from tests.conftest import oracle_system
 
 
-def _system(L, hamiltonian, n_types, chiN, mols, n_chains=512, N=None, seed=3):
+def _system(L, hamiltonian, n_types, chiN, mols, n_chains=512, N=None, seed=3, move=0):
     N = N or len(mols[0][0])
     # the A/B path takes chi_01 N from the description
     d = SystemDesc(n_chains=n_chains, N=N, f=0.5, box_Re=(2.0, 2.0, 1.0), grid=(12, 12, 6),
-                   chiN=float(np.asarray(chiN)[0][1]), kappaN=40.0, seed=seed)
+                   chiN=float(np.asarray(chiN)[0][1]), kappaN=40.0, seed=seed, move=move)
     s = oracle_system(d, L)
     s.set_hamiltonian(hamiltonian)
     words, starts = workloads.encode_architectures(mols)
@@ -27,13 +27,15 @@ def _system(L, hamiltonian, n_types, chiN, mols, n_chains=512, N=None, seed=3):
     return d, s, words, starts, arch, Positions(*[pos[k].copy() for k in range(3)])
 
 
-def check_two_types_equal_the_AB_path(lib=None, hamiltonian=0):
+def check_two_types_equal_the_AB_path(lib=None, hamiltonian=0, move=0):
     """n_t = 2 through the type planes: the occupation numbers, fields (bit
-    for bit), energy and several cycles of sweeps of the A/B path."""
+    for bit), energy and several cycles of sweeps of the A/B path (uniform
+    or smart Monte Carlo moves: the field and its force come from the plane
+    of the particle's type)."""
     mols = [workloads.linear_architecture(16), workloads.star_architecture(3, 5)]
     chi = [[0.0, 27.0], [27.0, 0.0]]
-    d, t, words, starts, arch, p = _system(lib, hamiltonian, 2, chi, mols)
-    _, ab, _, _, _, q = _system(lib, hamiltonian, 0, chi, mols)
+    d, t, words, starts, arch, p = _system(lib, hamiltonian, 2, chi, mols, move=move)
+    _, ab, _, _, _, q = _system(lib, hamiltonian, 0, chi, mols, move=move)
     for sweep in range(3):
         n = t.histogram_types(p)
         nA, nB = ab.histogram(q)
@@ -120,9 +122,9 @@ def check_type_histogram_matches_numpy(lib=None):
     assert int(n.sum()) == d.M
 
 
-@pytest.mark.parametrize("hamiltonian", [0, 1])
-def test_two_types_equal_the_AB_path(oracle_lib, hamiltonian):
-    check_two_types_equal_the_AB_path(hamiltonian=hamiltonian)
+@pytest.mark.parametrize("hamiltonian,move", [(0, 0), (1, 0), (0, 1)])
+def test_two_types_equal_the_AB_path(oracle_lib, hamiltonian, move):
+    check_two_types_equal_the_AB_path(hamiltonian=hamiltonian, move=move)
 
 
 @pytest.mark.parametrize("hamiltonian", [0, 1])
