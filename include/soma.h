@@ -301,7 +301,11 @@ soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_ar
  * as the reference length; call soma_update_fields to recount at
  * once.  Uniform moves, in the SET scheme or the molecule-parallel iteration
  * (SOMA_ITERATION_MOLECULE: each molecule makes n attempts, on particles
- * ((word 3 & 0xFF) * n) >> 8 of its own n; partners from the same tables).
+ * ((word 3 & 0xFF) * n) >> 8 of its own n; partners from the same tables),
+ * or smart Monte Carlo moves in the SET scheme (Sec. 2.2; the draws and the
+ * acceptance of the linear chain's move, the bonded force -2 K_b sum_q (r -
+ * r_q) over the listed partners q at the time the particle's set moves); the
+ * learned proposal takes linear chains only (SOMA_EINVAL).
  * A shard (desc.n_chains_total > 0) takes only architectures of N particles
  * (SOMA_EINVAL otherwise: its density counts the whole system).
  * src_on_device: all three
@@ -325,8 +329,10 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
  * phi_j)^2 (K^0) or + sum_{i<j} chi_ij N phi_i phi_j (K^1), every pair of
  * types counted once.  Particle types are the type bytes of the architecture
  * array (soma_set_topology, types < n_types), so the system runs the
- * architecture path (SET or molecule-parallel, uniform moves, FP32 fields, no
- * external fields); the occupation numbers become one 32-bit plane per type.
+ * architecture path (SET or molecule-parallel, uniform moves, or SET with
+ * smart Monte Carlo moves whose field and field force come from the plane of
+ * the particle's type; FP32 fields, no external fields); the occupation
+ * numbers become one 32-bit plane per type.
  * soma_get_density, soma_get_fields and soma_structure_factor then refuse
  * (SOMA_EINVAL): use soma_get_type_counts / soma_get_type_fields /
  * soma_structure_factor_types.  Recomputes

@@ -94,7 +94,8 @@ struct soma_t {
   unsigned* d_err = nullptr;                 // [0] error bits, [1] arrival counter,
                                              // [2] range flag of soma_set_positions
   double* d_scratch = nullptr;
-  float4* d_smc = nullptr;                   // smart Monte Carlo table (2 * cells), SMC only
+  float4* d_smc = nullptr;                   // smart Monte Carlo table, smc_planes * cells, SMC only
+  uint32_t smc_planes = 0;                   // one float4 plane per type (A, B or n_t types)
   bool pos_invalid = false;                  // soma_set_positions was given positions out of range
   float* d_ext = nullptr;                    // external potential, 2 * cells (lazy)
   uint8_t* d_forbidden = nullptr;            // forbidden cells, cells bytes (lazy)
@@ -401,17 +402,19 @@ TypesArgs types_args(soma_t* h, int after_sweep) {
 }
 
 // the table of fields and field forces that smart Monte Carlo sweeps read,
-// after every field update of such a system
+// after every field update of such a system (A and B, or one plane per type)
 cudaError_t launch_smc_table_of(soma_t* h) {
   if (!h->d_smc) return cudaSuccess;
   ++h->launches;
+  if (h->n_types)
+    return launch_smc_table_planes(h->g, h->wt, h->n_types, h->d_smc, h->sm_count, h->stream);
   return launch_smc_table(h->g, h->w[0], h->w[1], h->d_smc, h->grid_dtype, h->sm_count, h->stream);
 }
 
 // the field update of one cycle: the packed A | B grid or the type planes
 cudaError_t launch_fields_any(soma_t* h, const FieldArgs& fa, const TypesArgs& ta) {
-  if (h->n_types) return launch_fields_types(ta, h->d_err + 1, h->sm_count, h->stream);
-  cudaError_t e = launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count, h->stream);
+  cudaError_t e = h->n_types ? launch_fields_types(ta, h->d_err + 1, h->sm_count, h->stream)
+                             : launch_fields(fa, h->d_err + 1, h->grid_dtype, h->sm_count, h->stream);
   if (e == cudaSuccess) e = launch_smc_table_of(h);
   return e;
 }
@@ -423,7 +426,7 @@ cudaError_t launch_sweep_any(soma_t* h, const SweepArgs& sa) {
                                     types);
   if (h->has_topo)
     return launch_sweep_topology(topo_args(h, sa), h->topo_grid, h->grid_dtype, h->shape.big,
-                                 h->stream, types);
+                                 h->stream, types, h->desc.move == SOMA_MOVE_SMC);
   if (h->desc.move == SOMA_MOVE_LEARNED)
     return launch_sweep_learned(sa, h->shape, h->grid_dtype, h->mlp_q, h->stream);
   return launch_sweep_uniform(sa, h->shape, h->grid_dtype, h->stream);
@@ -484,6 +487,7 @@ soma_status update_fields(soma_t* h) {
                                      h->sm_count, h->stream));
     SOMA_CUDA(launch_fields_types(types_args(h, 0), h->d_err + 1, h->sm_count, h->stream));
     h->launches += 2;
+    SOMA_CUDA(launch_smc_table_of(h));
     return SOMA_OK;
   }
   // count into n[s&1] (cleared first), then omega from it
@@ -567,7 +571,10 @@ soma_status soma_create(const soma_system_desc* desc, soma_t** out) {
   ALLOC(h->mlp_m, sizeof(float) * SOMA_MLP_PARAMS);
   ALLOC(h->mlp_v, sizeof(float) * SOMA_MLP_PARAMS);
   ALLOC(h->mlp_g, sizeof(float) * SOMA_MLP_PARAMS);
-  if (desc->move == SOMA_MOVE_SMC) ALLOC(h->d_smc, sizeof(float4) * 2 * cells);
+  if (desc->move == SOMA_MOVE_SMC) {
+    ALLOC(h->d_smc, sizeof(float4) * 2 * cells);
+    h->smc_planes = 2;
+  }
 #undef ALLOC
   h->d_out = h->d_scratch + h->scratch_doubles;
   h->shape = sweep_shape(h->g.n_chains, h->g.N, h->sm_count, h->grid_dtype, desc->move,
@@ -882,6 +889,16 @@ soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_ar
   return sync(h);
 }
 
+namespace {
+// launch grid of the architecture sweep for the handle's iteration, move and types
+void set_topo_grid(soma_t* h) {
+  h->topo_grid = h->shape.molecule
+                     ? molecule_topology_grid(h->g.N, h->grid_dtype, h->sm_count, h->g.n_chains)
+                     : topology_grid(h->grid_dtype, h->shape.big, h->sm_count, h->shape.n_tiles,
+                                     h->n_types != 0, h->desc.move == SOMA_MOVE_SMC);
+}
+}  // namespace
+
 soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words,
                               const uint32_t* start, uint32_t n_arch, const uint8_t* mol_arch,
                               int src_on_device) {
@@ -891,7 +908,8 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
   if (!start || !mol_arch || n_arch < 1 || n_arch > 256 || n_words < 2 || n_words > (1ull << 24))
     return fail(SOMA_EINVAL, "need 1..256 architectures in 2..2^24 words, start and mol_arch");
   if (h->g.N > 64) return fail(SOMA_EINVAL, "architectures take N <= 64");
-  if (h->desc.move != SOMA_MOVE_UNIFORM) return fail(SOMA_EINVAL, "architectures take uniform moves");
+  if (h->desc.move == SOMA_MOVE_LEARNED)
+    return fail(SOMA_EINVAL, "architectures take the uniform or smart Monte Carlo move");
   const cudaMemcpyKind k = src_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
   std::vector<uint32_t> w((size_t)n_words), st(n_arch);
   std::vector<uint8_t> a((size_t)h->g.n_chains);
@@ -948,10 +966,8 @@ soma_status soma_set_topology(soma_t* h, const uint32_t* words, uint64_t n_words
     h->g.particles = present;
     h->rho_cell = (double)present / (double)h->g.cells;
   }
-  h->topo_grid = h->shape.molecule
-                     ? molecule_topology_grid(h->g.N, h->grid_dtype, h->sm_count, h->g.n_chains)
-                     : topology_grid(h->grid_dtype, h->shape.big, h->sm_count, h->shape.n_tiles);
   h->has_topo = true;
+  set_topo_grid(h);
   if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
   return SOMA_OK;
 }
@@ -972,6 +988,7 @@ soma_status soma_set_types(soma_t* h, uint32_t n_types, const double* chiN) {
     h->wt = nullptr;
     h->n_types = 0;
     if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    if (h->has_topo) set_topo_grid(h);
     const soma_status st = update_fields(h);
     return st == SOMA_OK ? sync(h) : st;
   }
@@ -985,7 +1002,8 @@ soma_status soma_set_types(soma_t* h, uint32_t n_types, const double* chiN) {
                     i, j);
     }
   if (h->grid_dtype != 0) return fail(SOMA_EINVAL, "n_t types take FP32 fields");
-  if (h->desc.move != SOMA_MOVE_UNIFORM) return fail(SOMA_EINVAL, "n_t types take uniform moves");
+  if (h->desc.move == SOMA_MOVE_LEARNED)
+    return fail(SOMA_EINVAL, "n_t types take the uniform or smart Monte Carlo move");
   if (h->has_ext || h->has_forbidden) return fail(SOMA_EINVAL, "n_t types take no external fields");
   if (h->has_topo && h->topo_max_type >= n_types)
     return fail(SOMA_EINVAL, "the architectures use type %u >= n_types", h->topo_max_type);
@@ -1003,6 +1021,16 @@ soma_status soma_set_types(soma_t* h, uint32_t n_types, const double* chiN) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->wt, sizeof(float) * n_types * h->g.cells);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->nt[0], 0, bytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->nt[1], 0, bytes, h->stream);
+  if (e == cudaSuccess && h->d_smc && h->smc_planes < n_types) {
+    // smart Monte Carlo: one table plane per type (rebuilt with the fields)
+    float4* tab = nullptr;
+    e = cudaMalloc((void**)&tab, sizeof(float4) * n_types * h->g.cells);
+    if (e == cudaSuccess) {
+      cudaFree(h->d_smc);
+      h->d_smc = tab;
+      h->smc_planes = n_types;
+    }
+  }
   if (e != cudaSuccess) {
     cudaFree(h->nt[0]);
     cudaFree(h->nt[1]);
@@ -1016,6 +1044,7 @@ soma_status soma_set_types(soma_t* h, uint32_t n_types, const double* chiN) {
     for (uint32_t j = 0; j < n_types; ++j) h->chiN_types[i * TYPES_MAX + j] = chiN[i * n_types + j];
   h->n_types = n_types;
   if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+  if (h->has_topo) set_topo_grid(h);
   if (h->has_topo) {   // the counts and fields of the current configuration
     soma_status st = update_fields(h);
     if (st != SOMA_OK) return st;

@@ -244,6 +244,18 @@ struct SweepArgs {
   const uint8_t* arch;      // particle i of architecture a is B; arch[chain] (or NULL)
 };
 
+// Smart Monte Carlo: omega and the field force (minus the central difference
+// of omega along each axis) of cell c, one 16-byte entry of the table plane
+// of the particle's type.
+__device__ __forceinline__ float smc_field(const float4* __restrict__ tab, uint32_t c, float& fx,
+                                           float& fy, float& fz) {
+  const float4 q = __ldg(tab + c);
+  fx = q.y;
+  fy = q.z;
+  fz = q.w;
+  return q.x;
+}
+
 // Training of the learned proposal: one expected-squared-jump sample per thread.
 struct TrainArgs {
   Geom g;

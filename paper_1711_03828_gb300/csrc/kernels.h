@@ -101,6 +101,9 @@ const void* smc_kernel_ptr(int Q, bool pair, int grid_dtype);
 // grid_dtype; rebuilt after every field update of a smart Monte Carlo system.
 cudaError_t launch_smc_table(const Geom& g, const void* wA, const void* wB, float4* tab,
                              int grid_dtype, int sm_count, cudaStream_t st);
+// the same for n_t types: one float4 plane per type from the FP32 planes w
+cudaError_t launch_smc_table_planes(const Geom& g, const float* w, uint32_t planes, float4* tab,
+                                    int sm_count, cudaStream_t st);
 
 // Molecules of any architecture (topology.cu): the architecture array of
 // Sec. 3.2.1 and the independent sets derived from it.
@@ -139,9 +142,11 @@ struct TopologyTables {
 std::string topology_tables(const uint32_t* words, uint64_t n_words, const uint32_t* start,
                             uint32_t n_arch, uint32_t N, TopologyTables* out,
                             uint32_t n_types = 2);
-int topology_grid(int grid_dtype, bool big, int sm_count, uint64_t n_tiles);
+// smc: the smart Monte Carlo move (the table s.smc_tab holds one plane per type)
+int topology_grid(int grid_dtype, bool big, int sm_count, uint64_t n_tiles, bool types = false,
+                  bool smc = false);
 cudaError_t launch_sweep_topology(const TopoArgs& a, int grid, int grid_dtype, bool big,
-                                  cudaStream_t st, bool types = false);
+                                  cudaStream_t st, bool types = false, bool smc = false);
 // the molecule-parallel iteration for molecules of any architecture (N <= 64);
 // the grid helper also allows the kernel its shared memory (call it before
 // the first launch, outside stream capture)

@@ -66,6 +66,28 @@ __global__ void smc_table_kernel(const Geom g, const WT* __restrict__ wA, const 
   }
 }
 
+// The same table for n_t types: one plane of float4 per type from the FP32
+// field planes w (n_types * cells).
+__global__ void smc_table_planes_kernel(const Geom g, const float* __restrict__ w, uint32_t planes,
+                                        float4* __restrict__ tab) {
+  const uint32_t nx = g.nx, ny = g.ny;
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < g.cells;
+       c += gridDim.x * blockDim.x) {
+    const uint32_t cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+    for (uint32_t t = 0; t < planes; ++t) {
+      float fx, fy, fz;
+      const float v = field_and_force<float>(g, w + (size_t)t * g.cells, cx, cy, cz, fx, fy, fz);
+      tab[(size_t)t * g.cells + c] = make_float4(v, fx, fy, fz);
+    }
+  }
+}
+
+cudaError_t launch_smc_table_planes(const Geom& g, const float* w, uint32_t planes, float4* tab,
+                                    int sm_count, cudaStream_t st) {
+  smc_table_planes_kernel<<<4 * sm_count, 256, 0, st>>>(g, w, planes, tab);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_smc_table(const Geom& g, const void* wA, const void* wB, float4* tab,
                              int grid_dtype, int sm_count, cudaStream_t st) {
   const int grid = 4 * sm_count;
@@ -83,16 +105,6 @@ cudaError_t launch_smc_table(const Geom& g, const void* wA, const void* wB, floa
                                                     static_cast<const float*>(wB), tab);
   }
   return cudaGetLastError();
-}
-
-// omega and field force of a cell from the table plane of the particle's type.
-__device__ __forceinline__ float smc_field(const float4* __restrict__ tab, uint32_t c, float& fx,
-                                           float& fy, float& fz) {
-  const float4 q = __ldg(tab + c);
-  fx = q.y;
-  fy = q.z;
-  fz = q.w;
-  return q.x;
 }
 
 template <int Q>

@@ -5,8 +5,9 @@
 // Architecture array (Sec. 3.2.1, Fig. polyarch): per architecture a block of
 // N, then one word per particle, (index of its first bond word << 8) | type
 // (0xFFFFFF: no bonds), the bond words holding (signed 27-bit partner offset
-// << 5) | (bond type << 1) | last.  Every molecule of a system has the
-// system's N <= 64 particles; mol_arch gives each molecule's architecture.
+// << 5) | (bond type << 1) | last.  A molecule has the system's N <= 64
+// particle slots; its architecture (mol_arch) fills the first n <= N of them,
+// the others are absent (never moved or counted).
 // The array is checked and re-encoded on the host when it is set: per
 // particle one 32-bit word with its number of partners, its first three
 // partners, its type, its set and the number of sets (L1-resident: 256 bytes
@@ -93,25 +94,36 @@ __device__ __forceinline__ uint32_t pw_sets(uint32_t w) { return w >> 28; }
 
 // Shared-memory record of one warp's tile, one 16-byte entry per particle and
 // array (a mover reads each with one 128-bit access): P = current position and
-// final cell, T = trial position and acceptance threshold, Q = table word,
-// trial cell, molecule start | architecture << 8; and the list of this step's
-// movers.
+// final cell, T = trial position and acceptance threshold (smart Monte Carlo:
+// the three normals and ln u), Q = table word, trial cell, molecule start |
+// architecture << 8, type; W (smart Monte Carlo only) = omega and field force
+// at the current cell; and the list of this step's movers.
+template <bool SMC>
 struct TopoTile {
   float4 P[TOPO_TILE];
   float4 T[TOPO_TILE];
   uint4 Q[TOPO_TILE];
+  float4 W[SMC ? TOPO_TILE : 1];
   uint8_t movers[TOPO_TILE];
 };
 
 // IDX: particle index type (32-bit when M < 2^32: Philox counter word 1 = 0).
 // MULTI: n_t particle types (type table, one field and one count plane per
 // type; FP32 fields); else the two types A, B of the packed grid.
-template <typename WT, typename IDX, bool MULTI>
+// SMC: the smart Monte Carlo move (Sec. 2.2) in place of the uniform one.  Its
+// trial position depends on the force of the particle's partners, which may
+// have moved in an earlier step of the tile, so only the draws are made up
+// front (three Box-Muller normals from the move draw, purpose 1, and ln u from
+// the second draw, purpose 2, as for linear chains); the mover computes the
+// force U of its partners from the record, the field and field force at its
+// cell and at the trial cell from the per-type table, the trial position
+// r + A F + sqrt(2A) xi and the acceptance min(1, exp(-dE) T(r'->r)/T(r->r')).
+template <typename WT, typename IDX, bool MULTI, bool SMC>
 __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t) {
-  __shared__ TopoTile tiles[TOPO_WARPS];
+  __shared__ TopoTile<SMC> tiles[TOPO_WARPS];
   const SweepArgs& p = t.s;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  TopoTile& S = tiles[wib];
+  TopoTile<SMC>& S = tiles[wib];
   const IDX nwarps = (IDX)gridDim.x * TOPO_WARPS;
   const IDX n_tiles = (IDX)p.n_tiles;
   const IDX n_mol = (IDX)p.g.n_chains;
@@ -123,6 +135,7 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
   const WT* __restrict__ wB = static_cast<const WT*>(p.wB);
   const uint32_t N = p.g.N, G = p.G;
   const uint32_t ctr3 = (PURPOSE_MOVE << 24) | (p.g.replica & 0xFFFFFFu);
+  const uint32_t ctr3b = (PURPOSE_MOVE2 << 24) | (p.g.replica & 0xFFFFFFu);
   const bool random = p.set_order_random != 0;
   const uint32_t below = (1u << lane) - 1u;
 
@@ -187,25 +200,41 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
       const IDX mc = m + (IDX)p.g.id_base;
       const uint32_t hi = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)mc >> 32) : 0u;
       const uint4 r = philox_rk(make_uint4((uint32_t)mc, hi, sweep, ctr3), p.g);
-      const float xn = __fmaf_rn(p.a, uniform_sym(r.x), x[j]);
-      const float yn = __fmaf_rn(p.a, uniform_sym(r.y), y[j]);
-      const float zn = __fmaf_rn(p.a, uniform_sym(r.z), z[j]);
       const uint32_t co = cell_of(p.g, x[j], y[j], z[j]);
-      const uint32_t cn = cell_of(p.g, xn, yn, zn);
       // type: the architecture's type byte (n_t types) or the A/B bit
       const uint32_t type = MULTI ? (present ? __ldg(t.ttab + a * TOPO_TILE + ci) : 0u)
                                   : (uint32_t)pw_is_B(pw);
-      float dEf = 0.f;
-      if (MULTI) {
-        const float* wt = t.wt + (size_t)type * p.g.cells;
-        if (present) dEf = __ldg(wt + cn) - __ldg(wt + co);
-      } else {
-        const WT* wt = type ? wB : wA;
-        if (present) dEf = load_w<WT>(wt, cn) - load_w<WT>(wt, co);
-      }
       S.P[tl] = make_float4(x[j], y[j], z[j], __uint_as_float(co));
-      S.T[tl] = make_float4(xn, yn, zn, -log_uniform_open(r.w) - dEf);
-      S.Q[tl] = make_uint4(pw, cn, (gc[j] & 0xFFu) * N | a << 8, type);
+      if (SMC) {
+        const uint4 r2 = philox_rk(make_uint4((uint32_t)mc, hi, sweep, ctr3b), p.g);
+        float sn, cs;
+        const float rad0 = sqrtf(-2.f * log_uniform_open_accurate(r.x));
+        sincos_2pi_uniform_fast(r.y, &sn, &cs);
+        const float gx = rad0 * cs, gy = rad0 * sn;
+        const float rad1 = sqrtf(-2.f * log_uniform_open_accurate(r.z));
+        sincos_2pi_uniform_fast(r.w, &sn, &cs);
+        S.T[tl] = make_float4(gx, gy, rad1 * cs, log_uniform_open(r2.x));
+        S.Q[tl] = make_uint4(pw, 0u, (gc[j] & 0xFFu) * N | a << 8, type);
+        // the table entry of the current cell, gathered here for all slots at
+        // once rather than inside the mover's dependent chain
+        S.W[tl] = present ? __ldg(p.smc_tab + (size_t)type * p.g.cells + co)
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        const float xn = __fmaf_rn(p.a, uniform_sym(r.x), x[j]);
+        const float yn = __fmaf_rn(p.a, uniform_sym(r.y), y[j]);
+        const float zn = __fmaf_rn(p.a, uniform_sym(r.z), z[j]);
+        const uint32_t cn = cell_of(p.g, xn, yn, zn);
+        float dEf = 0.f;
+        if (MULTI) {
+          const float* wt = t.wt + (size_t)type * p.g.cells;
+          if (present) dEf = __ldg(wt + cn) - __ldg(wt + co);
+        } else {
+          const WT* wt = type ? wB : wA;
+          if (present) dEf = load_w<WT>(wt, cn) - load_w<WT>(wt, co);
+        }
+        S.T[tl] = make_float4(xn, yn, zn, -log_uniform_open(r.w) - dEf);
+        S.Q[tl] = make_uint4(pw, cn, (gc[j] & 0xFFu) * N | a << 8, type);
+      }
       ty[j] = type;
       own[j] = (valid && ci == 0u)
                    ? set_steps(pw_sets(pw), random, r.w & 1u, (uint64_t)(chain0 + (gc[j] & 0xFFu)),
@@ -266,12 +295,43 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
           }
         }
         const float4 Tq = S.T[q];
-        const float dx = Tq.x - Pq.x, dy = Tq.y - Pq.y, dz = Tq.z - Pq.z;
-        const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
-        const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (p.K_b * fmaf(2.f, du, (float)deg * dd) <= Tq.w) {
-          S.P[q] = make_float4(Tq.x, Tq.y, Tq.z, __uint_as_float(Qq.y));
-          ++my_acc;
+        if (SMC) {
+          // bonded force -2 K_b U plus the field force of the particle's type
+          const float4* __restrict__ tab = p.smc_tab + (size_t)Qq.w * p.g.cells;
+          const float A = p.smc_A, K2 = 2.f * p.K_b, k = (float)deg;
+          const float4 Wq = S.W[q];
+          const float w_old = Wq.x, fox = Wq.y, foy = Wq.z, foz = Wq.w;
+          float fnx, fny, fnz;
+          const float Fx = fmaf(-K2, ux, fox), Fy = fmaf(-K2, uy, foy), Fz = fmaf(-K2, uz, foz);
+          const float tx = __fadd_rn(Pq.x, fmaf(p.smc_s2A, Tq.x, A * Fx));
+          const float ty = __fadd_rn(Pq.y, fmaf(p.smc_s2A, Tq.y, A * Fy));
+          const float tz = __fadd_rn(Pq.z, fmaf(p.smc_s2A, Tq.z, A * Fz));
+          const uint32_t cn = cell_of(p.g, tx, ty, tz);
+          const float w_new = smc_field(tab, cn, fnx, fny, fnz);
+          const float dx = tx - Pq.x, dy = ty - Pq.y, dz = tz - Pq.z;
+          // bonded energy change d.(2U + k d); the force at r' uses U' = U + k d
+          const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+          const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const float dE = fmaf(p.K_b, fmaf(2.f, du, k * dd), w_new - w_old);
+          const float Gx = fmaf(-K2, fmaf(k, dx, ux), fnx), Gy = fmaf(-K2, fmaf(k, dy, uy), fny),
+                      Gz = fmaf(-K2, fmaf(k, dz, uz), fnz);
+          const float ax = dx - A * Fx, ay = dy - A * Fy, az = dz - A * Fz;     // forward residual
+          const float bx = -dx - A * Gx, by = -dy - A * Gy, bz = -dz - A * Gz;  // reverse residual
+          const float fwd = fmaf(ax, ax, fmaf(ay, ay, az * az));
+          const float rev = fmaf(bx, bx, fmaf(by, by, bz * bz));
+          const float log_alpha = fmaf(fwd - rev, p.smc_inv4A, -dE);
+          if (log_alpha >= 0.f || Tq.w < log_alpha) {
+            S.P[q] = make_float4(tx, ty, tz, __uint_as_float(cn));
+            ++my_acc;
+          }
+        } else {
+          const float dx = Tq.x - Pq.x, dy = Tq.y - Pq.y, dz = Tq.z - Pq.z;
+          const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+          const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          if (p.K_b * fmaf(2.f, du, (float)deg * dd) <= Tq.w) {
+            S.P[q] = make_float4(Tq.x, Tq.y, Tq.z, __uint_as_float(Qq.y));
+            ++my_acc;
+          }
         }
       }
       __syncwarp();
@@ -299,22 +359,30 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
   if (lane == 0 && my_acc) atomicAdd(p.acc, (unsigned long long)my_acc);
 }
 
-const void* topology_kernel_ptr(int grid_dtype, bool big, bool types) {
+template <bool SMC>
+const void* topology_kernel_ptr_of(int grid_dtype, bool big, bool types) {
+  // the smart Monte Carlo move reads the FP32 table, whatever the field storage
+  if (types || SMC) grid_dtype = 0;
   if (types)   // FP32 fields only
-    return big ? (const void*)sweep_topology_kernel<float, uint64_t, true>
-               : (const void*)sweep_topology_kernel<float, uint32_t, true>;
+    return big ? (const void*)sweep_topology_kernel<float, uint64_t, true, SMC>
+               : (const void*)sweep_topology_kernel<float, uint32_t, true, SMC>;
   if (big) {
     switch (grid_dtype) {
-      case 1: return (const void*)sweep_topology_kernel<__nv_bfloat16, uint64_t, false>;
-      case 2: return (const void*)sweep_topology_kernel<__half, uint64_t, false>;
-      default: return (const void*)sweep_topology_kernel<float, uint64_t, false>;
+      case 1: return (const void*)sweep_topology_kernel<__nv_bfloat16, uint64_t, false, SMC>;
+      case 2: return (const void*)sweep_topology_kernel<__half, uint64_t, false, SMC>;
+      default: return (const void*)sweep_topology_kernel<float, uint64_t, false, SMC>;
     }
   }
   switch (grid_dtype) {
-    case 1: return (const void*)sweep_topology_kernel<__nv_bfloat16, uint32_t, false>;
-    case 2: return (const void*)sweep_topology_kernel<__half, uint32_t, false>;
-    default: return (const void*)sweep_topology_kernel<float, uint32_t, false>;
+    case 1: return (const void*)sweep_topology_kernel<__nv_bfloat16, uint32_t, false, SMC>;
+    case 2: return (const void*)sweep_topology_kernel<__half, uint32_t, false, SMC>;
+    default: return (const void*)sweep_topology_kernel<float, uint32_t, false, SMC>;
   }
+}
+
+const void* topology_kernel_ptr(int grid_dtype, bool big, bool types, bool smc) {
+  return smc ? topology_kernel_ptr_of<true>(grid_dtype, big, types)
+             : topology_kernel_ptr_of<false>(grid_dtype, big, types);
 }
 
 // Sum over bonds of |r_i - r_j|^2 (each bond once, from its lower index), FP64.
@@ -493,9 +561,10 @@ std::string topology_tables(const uint32_t* w, uint64_t n_words, const uint32_t*
   return std::string();
 }
 
-int topology_grid(int grid_dtype, bool big, int sm_count, uint64_t n_tiles) {
+int topology_grid(int grid_dtype, bool big, int sm_count, uint64_t n_tiles, bool types, bool smc) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topology_kernel_ptr(grid_dtype, big, false),
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm,
+                                                topology_kernel_ptr(grid_dtype, big, types, smc),
                                                 TOPO_WARPS * 32, 0);
   if (per_sm < 1) per_sm = 1;
   const uint64_t need = (n_tiles + TOPO_WARPS - 1) / TOPO_WARPS;
@@ -504,9 +573,9 @@ int topology_grid(int grid_dtype, bool big, int sm_count, uint64_t n_tiles) {
 }
 
 cudaError_t launch_sweep_topology(const TopoArgs& a, int grid, int grid_dtype, bool big,
-                                  cudaStream_t st, bool types) {
+                                  cudaStream_t st, bool types, bool smc) {
   void* args[] = {const_cast<TopoArgs*>(&a)};
-  return cudaLaunchKernel(topology_kernel_ptr(grid_dtype, big, types), dim3(grid),
+  return cudaLaunchKernel(topology_kernel_ptr(grid_dtype, big, types, smc), dim3(grid),
                           dim3(TOPO_WARPS * 32), args, 0, st);
 }
 

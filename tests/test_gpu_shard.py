@@ -72,6 +72,9 @@ CASES = {
                                      set_order=ITERATION_MOLECULE), None, 2),
     "architectures": (SystemDesc(n_chains=2000, N=16, box_Re=(2.0, 2.0, 1.0), grid=(12, 12, 6),
                                  chiN=25.0, seed=13), _arch_setup, 2),
+    "architectures_smc": (SystemDesc(n_chains=2000, N=16, box_Re=(2.0, 2.0, 1.0),
+                                     grid=(12, 12, 6), chiN=25.0, move=MOVE_SMC, seed=15),
+                          _arch_setup, 2),
 }
 
 

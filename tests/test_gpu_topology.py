@@ -8,8 +8,8 @@ import math
 import numpy as np
 import pytest
 
-from paper_1711_03828_gb300 import (ITERATION_MOLECULE, MOVE_SMC, SomaError, System, SystemDesc,
-                                    _abi, workloads)
+from paper_1711_03828_gb300 import (ITERATION_MOLECULE, MOVE_LEARNED, SomaError, System,
+                                    SystemDesc, _abi, workloads)
 from tests.conftest import oracle_system
 from tests.test_gpu_parity import TIE, _fields_tol, _pos
 
@@ -243,15 +243,15 @@ def test_topology_graph_replay_is_identical(cuda_device):
     np.testing.assert_array_equal(out[0], out[1])
 
 
-def test_ideal_star_and_ring_statistics(cuda_device):
+def check_ideal_closed_forms(move=0):
     """chiN = kappaN = 0: <|r_i - r_j|^2> = d_ij b0^2 on a star (graph distance
     d_ij) and b0^2 d (N - d)/N on an odd ring (three sets), b0^2 = R_e0^2/(N-1),
-    over 16384 molecules and 1500 cycles."""
+    over 16384 molecules and 1500 cycles of the given move."""
     Re = 6.0
     for mol in (workloads.star_architecture(3, 5), workloads.ring_architecture(15)):
         N = len(mol[0])
         d = SystemDesc(n_chains=16384, N=N, f=0.5, box_Re=(4.0, 4.0, 2.0), grid=(24, 24, 12),
-                       chiN=0.0, kappaN=0.0, seed=9)
+                       chiN=0.0, kappaN=0.0, seed=9, move=move)
         words, starts = workloads.encode_architectures([mol])
         arch = np.zeros(d.n_chains, np.uint8)
         s = System(d)
@@ -281,6 +281,10 @@ def test_ideal_star_and_ring_statistics(cuda_device):
             want = b02 * dist * (N - dist) / N if ring else dist * b02
             se = per_mol.std() / math.sqrt(len(per_mol))
             assert abs(per_mol.mean() - want) < 5 * se, (ring, dist, per_mol.mean(), want, se)
+
+
+def test_ideal_star_and_ring_statistics(cuda_device):
+    check_ideal_closed_forms()
 
 
 def test_topology_arguments_are_checked(cuda_device):
@@ -324,7 +328,7 @@ def test_topology_arguments_are_checked(cuda_device):
     s.set_topology(None)                                 # back to the diblock
     s.sweep(2)
     s.close()
-    for kw in (dict(move=MOVE_SMC),):
+    for kw in (dict(move=MOVE_LEARNED),):     # the learned proposal takes linear chains
         s = System(SystemDesc(**dict(CASES["N9_odd_ring_star"][0], f=0.5, chiN=10.0, kappaN=50.0,
                                      **kw)))
         with pytest.raises(SomaError) as e:
