@@ -537,9 +537,10 @@ static void or_move_attempt(const or_system* s, float* x, float* y, float* z,
 /* min(1, exp(-dE) T(r'->r)/T(r->r')), T(r->r') = exp(-|r'-r-A F(r)|^2/(4A)),   */
 /* which keeps the move exact for any force.  A = a^2/6, so that the per-axis    */
 /* variance 2A equals that of the uniform move, a^2/3.                          */
-/* Random numbers: normals from the Box-Muller transform of words (0,1) and    */
-/* (2,3) of the move draw (purpose 1), the acceptance uniform from word 0 of    */
-/* the second draw (purpose 2).                                                 */
+/* Random numbers: one draw per move (purpose 1).  The normals come from the   */
+/* Box-Muller transform of the uniforms of the top 24 bits of words (0,1) and  */
+/* (2,3); the acceptance uniform from the 24 bits left over, the low bytes of   */
+/* words 0, 1, 2 (word 0's lowest).                                              */
 /* ------------------------------------------------------------------------- */
 static uint64_t or_cell_shift(const or_system* s, uint64_t c, int axis, int step) {
   long long n[3] = { s->grid[0], s->grid[1], s->grid[2] };
@@ -577,9 +578,10 @@ static void or_move_smc(const or_system* s, float* x, float* y, float* z,
   /* the field plane of the particle's type (A / B, or one of n_t types) */
   const double* w_t = (s->n_types && s->w_types) ? s->w_types[or_type(s, chain, i)]
                                                   : (or_is_B(s, chain, i) ? wB : wA);
-  uint32_t w1[4], w2[4];
+  uint32_t w1[4];
   or_draw(s, OR_PURPOSE_MOVE, m, sweep, w1);
-  or_draw(s, OR_PURPOSE_MOVE2, m, sweep, w2);
+  /* the acceptance uniform's 24 bits, as the top 24 bits of a word */
+  const uint32_t w_acc = ((w1[0] & 0xFFu) | (w1[1] & 0xFFu) << 8 | (w1[2] & 0xFFu) << 16) << 8;
   double xi[4];
   for (int p = 0; p < 2; ++p) {
     double u1 = or_uniform_open(w1[2 * p]), u2 = or_uniform_open(w1[2 * p + 1]);
@@ -620,7 +622,7 @@ static void or_move_smc(const or_system* s, float* x, float* y, float* z,
     rev += b * b;
   }
   const double log_alpha = -dE - rev / (4.0 * A) + fwd / (4.0 * A);
-  const double lnu = log(or_uniform_open(w2[0]));
+  const double lnu = log(or_uniform_open(w_acc));
   const int acc_move = (log_alpha >= 0.0) || (lnu < log_alpha);
   if (margin) margin[m] = lnu - log_alpha;
   if (fabs(lnu - log_alpha) < 1e-4) (*ties)++;

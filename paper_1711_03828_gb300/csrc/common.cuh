@@ -58,6 +58,13 @@ __device__ __forceinline__ float log_uniform_open_accurate(uint32_t r) {
   return log1pf(-one_minus_u);
 }
 
+// The 24 bits of a move draw r that its four top-24-bit uniforms leave over
+// (the low bytes of words x, y, z; x's lowest), as the top 24 bits of a word:
+// the acceptance uniform of a move whose four uniforms are all taken.
+__device__ __forceinline__ uint32_t spare_uniform_word(const uint4& r) {
+  return ((r.x & 0xFFu) | (r.y & 0xFFu) << 8 | (r.z & 0xFFu) << 16) << 8;
+}
+
 // cos and sin of 2 pi u for the open uniform u = (k + 1/2)/2^24: with the exact
 // symmetric uniform v = 2u - 1, 2 pi u = pi v + pi, so cos = -cospi(v) and
 // sin = -sinpi(v), evaluated without rounding the phase.

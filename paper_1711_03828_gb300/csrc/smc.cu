@@ -3,9 +3,10 @@
 // Trial move dr = A F(r) + sqrt(2A) xi with A = a^2/6, F the bonded force
 // minus the central-difference gradient of omega_t over the six neighbouring
 // cells, accepted with min(1, exp(-dE) T(r'->r)/T(r->r')) (Sec. 2.2 names the
-// force-biased proposal; the Rossky-Doll-Friedman form is used).  Normals by
-// Box-Muller from the first draw (purpose 1), the acceptance uniform from the
-// second (purpose 2).  The radius sqrt(-2 ln u) takes ln u accurate to about an
+// force-biased proposal; the Rossky-Doll-Friedman form is used).  One Philox
+// draw per move (purpose 1): normals by Box-Muller from the top 24 bits of its
+// four words, the acceptance uniform from the 24 bits they leave (the low
+// bytes of words 0-2).  The radius sqrt(-2 ln u) takes ln u accurate to about an
 // ulp (near u = 1 a small absolute error of ln u would be a large one of the
 // radius); the angle takes the hardware sincos (absolute error about 2^-21,
 // below 1e-6 dL in the displacement) and the acceptance test the hardware log,
@@ -22,8 +23,8 @@ namespace soma {
 // sweep_uniform_kernel).  Trial move dr = A F(r) + sqrt(2A) xi, F = bonded
 // force minus the central-difference gradient of omega_t over the six
 // neighbouring cells; accepted with min(1, exp(-dE) T(r'->r)/T(r->r')),
-// T(r->r') = exp(-|r'-r-A F(r)|^2/(4A)).  Normals by Box-Muller from the
-// first draw (purpose 1), the acceptance uniform from the second (purpose 2).
+// T(r->r') = exp(-|r'-r-A F(r)|^2/(4A)).  Normals and the acceptance uniform
+// from one draw (purpose 1), as above.
 __device__ __forceinline__ void cell3(const Geom& g, float x, float y, float z, uint32_t& cx,
                                       uint32_t& cy, uint32_t& cz) {
   cx = fold_axis(g, 0, x, (uint32_t)g.nx);
@@ -120,7 +121,6 @@ __global__ void __launch_bounds__(256) sweep_smc_kernel(const SweepArgs p) {
   const float4* __restrict__ tabB = p.smc_tab + p.g.cells;
   const uint32_t N = p.g.N, N_A = p.g.N_A;
   const uint32_t ctr3a = (PURPOSE_MOVE << 24) | (p.g.replica & 0xFFFFFFu);
-  const uint32_t ctr3b = (PURPOSE_MOVE2 << 24) | (p.g.replica & 0xFFFFFFu);
   const uint32_t li0 = (uint32_t)lane * S;
   const float A = p.smc_A, s2A = p.smc_s2A, inv4A = p.smc_inv4A, K2 = 2.f * p.K_b;
 
@@ -162,7 +162,6 @@ __global__ void __launch_bounds__(256) sweep_smc_kernel(const SweepArgs p) {
     for (int j = 0; j < S; ++j) {
       const uint64_t m = base + j + p.g.id_base;
       const uint4 r1 = philox_rk(make_uint4((uint32_t)m, (uint32_t)(m >> 32), sweep, ctr3a), p.g);
-      const uint4 r2 = philox_rk(make_uint4((uint32_t)m, (uint32_t)(m >> 32), sweep, ctr3b), p.g);
       lowbits |= (r1.w & 1u) << j;
       float sn, cs;
       const float rad0 = sqrtf(-2.f * log_uniform_open_accurate(r1.x));
@@ -172,7 +171,7 @@ __global__ void __launch_bounds__(256) sweep_smc_kernel(const SweepArgs p) {
       const float rad1 = sqrtf(-2.f * log_uniform_open_accurate(r1.z));
       sincos_2pi_uniform_fast(r1.w, &sn, &cs);
       gz[j] = rad1 * cs;
-      lnu[j] = log_uniform_open(r2.x);
+      lnu[j] = log_uniform_open(spare_uniform_word(r1));
       uint32_t cx, cy, cz;
       cell3(p.g, x[j], y[j], z[j], cx, cy, cz);
       co[j] = (cz * (uint32_t)p.g.ny + cy) * (uint32_t)p.g.nx + cx;
@@ -277,11 +276,10 @@ struct SmcSlot {
 
 __device__ __forceinline__ SmcSlot smc_slot(const Geom& g, const float4* tab, float x, float y, float z,
                                             uint32_t m, uint32_t sweep, uint32_t ctr3a,
-                                            uint32_t ctr3b, bool valid, uint32_t* first_word) {
+                                            bool valid, uint32_t* first_word) {
   SmcSlot q;
   q.x = x; q.y = y; q.z = z;
   const uint4 r1 = philox_rk(make_uint4(m, 0u, sweep, ctr3a), g);
-  const uint4 r2 = philox_rk(make_uint4(m, 0u, sweep, ctr3b), g);
   *first_word = r1.w;
   float sn, cs;
   const float rad0 = sqrtf(-2.f * log_uniform_open_accurate(r1.x));
@@ -291,7 +289,7 @@ __device__ __forceinline__ SmcSlot smc_slot(const Geom& g, const float4* tab, fl
   const float rad1 = sqrtf(-2.f * log_uniform_open_accurate(r1.z));
   sincos_2pi_uniform_fast(r1.w, &sn, &cs);
   q.gz = rad1 * cs;
-  q.lnu = log_uniform_open(r2.x);
+  q.lnu = log_uniform_open(spare_uniform_word(r1));
   uint32_t cx, cy, cz;
   cell3(g, x, y, z, cx, cy, cz);
   q.c = (cz * (uint32_t)g.ny + cy) * (uint32_t)g.nx + cx;
@@ -345,7 +343,6 @@ __global__ void __launch_bounds__(256, 3) sweep_smc_pair_kernel(const SweepArgs 
   const uint32_t sweep = (uint32_t)s64;
   uint32_t* __restrict__ nacc = ((s64 + 1ull) & 1ull) ? p.n1 : p.n0;
   const uint32_t ctr3a = (PURPOSE_MOVE << 24) | (p.g.replica & 0xFFFFFFu);
-  const uint32_t ctr3b = (PURPOSE_MOVE2 << 24) | (p.g.replica & 0xFFFFFFu);
   PairLane<float> L;
   L.init(lane, p.g.N, p.g.N_A, p.wA, p.wB);
   const float4* tab0 = p.smc_tab + (L.v0 == 1u ? 0u : p.g.cells);   // table plane of slot 0
@@ -363,9 +360,8 @@ __global__ void __launch_bounds__(256, 3) sweep_smc_pair_kernel(const SweepArgs 
     }
     uint32_t w0, w1;
     const uint32_t cbase = base + (uint32_t)p.g.id_base;
-    const SmcSlot s0 = smc_slot(p.g, tab0, px.x, py.x, pz.x, cbase, sweep, ctr3a, ctr3b, valid, &w0);
-    const SmcSlot s1 = smc_slot(p.g, tab1, px.y, py.y, pz.y, cbase + 1u, sweep, ctr3a, ctr3b, valid,
-                                &w1);
+    const SmcSlot s0 = smc_slot(p.g, tab0, px.x, py.x, pz.x, cbase, sweep, ctr3a, valid, &w0);
+    const SmcSlot s1 = smc_slot(p.g, tab1, px.y, py.y, pz.y, cbase + 1u, sweep, ctr3a, valid, &w1);
     const bool sw = p.set_order_random && (__shfl_sync(FULL, w0, L.first_lane) & 1u);
     SmcSlot A = sw ? s1 : s0, B = sw ? s0 : s1;
     const float4* tA = sw ? tab1 : tab0;

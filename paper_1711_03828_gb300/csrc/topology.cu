@@ -113,8 +113,8 @@ struct TopoTile {
 // SMC: the smart Monte Carlo move (Sec. 2.2) in place of the uniform one.  Its
 // trial position depends on the force of the particle's partners, which may
 // have moved in an earlier step of the tile, so only the draws are made up
-// front (three Box-Muller normals from the move draw, purpose 1, and ln u from
-// the second draw, purpose 2, as for linear chains); the mover computes the
+// front (three Box-Muller normals and ln u from the one move draw, purpose 1,
+// as for linear chains); the mover computes the
 // force U of its partners from the record, the field and field force at its
 // cell and at the trial cell from the per-type table, the trial position
 // r + A F + sqrt(2A) xi and the acceptance min(1, exp(-dE) T(r'->r)/T(r->r')).
@@ -135,7 +135,6 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
   const WT* __restrict__ wB = static_cast<const WT*>(p.wB);
   const uint32_t N = p.g.N, G = p.G;
   const uint32_t ctr3 = (PURPOSE_MOVE << 24) | (p.g.replica & 0xFFFFFFu);
-  const uint32_t ctr3b = (PURPOSE_MOVE2 << 24) | (p.g.replica & 0xFFFFFFu);
   const bool random = p.set_order_random != 0;
   const uint32_t below = (1u << lane) - 1u;
 
@@ -206,14 +205,13 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
                                   : (uint32_t)pw_is_B(pw);
       S.P[tl] = make_float4(x[j], y[j], z[j], __uint_as_float(co));
       if (SMC) {
-        const uint4 r2 = philox_rk(make_uint4((uint32_t)mc, hi, sweep, ctr3b), p.g);
         float sn, cs;
         const float rad0 = sqrtf(-2.f * log_uniform_open_accurate(r.x));
         sincos_2pi_uniform_fast(r.y, &sn, &cs);
         const float gx = rad0 * cs, gy = rad0 * sn;
         const float rad1 = sqrtf(-2.f * log_uniform_open_accurate(r.z));
         sincos_2pi_uniform_fast(r.w, &sn, &cs);
-        S.T[tl] = make_float4(gx, gy, rad1 * cs, log_uniform_open(r2.x));
+        S.T[tl] = make_float4(gx, gy, rad1 * cs, log_uniform_open(spare_uniform_word(r)));
         S.Q[tl] = make_uint4(pw, 0u, (gc[j] & 0xFFu) * N | a << 8, type);
         // the table entry of the current cell, gathered here for all slots at
         // once rather than inside the mover's dependent chain

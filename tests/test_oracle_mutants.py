@@ -142,6 +142,11 @@ MUTANTS = [
      "const uint32_t last = s->N - 1u;", TOPO.check_blend_ideal_statistics),
     ("blend_sq_over_all_slots", "  const double M = or_particles(s);",
      "  const double M = (double)s->n_chains * (double)s->N;", TOPO.check_blend_histogram_and_density),
+    ("smc_acceptance_from_the_angle_word", "(w1[1] & 0xFFu) << 8 | (w1[2] & 0xFFu) << 16) << 8;",
+     "(w1[1] & 0xFFu) << 8 | (w1[3] & 0xFFu) << 16) << 8;", PIN.check_smc_moves_follow_the_draws),
+    ("smc_normals_paired_wrongly", "double u1 = or_uniform_open(w1[2 * p]), u2 = or_uniform_open(w1[2 * p + 1]);\n    double rad = sqrt(-2.0 * log(u1)), th = 2.0 * M_PI * u2;\n    xi[2 * p] = rad * cos(th);\n    xi[2 * p + 1] = rad * sin(th);\n  }\n  const double A = s->a * s->a / 6.0;",
+     "double u1 = or_uniform_open(w1[p]), u2 = or_uniform_open(w1[p + 2]);\n    double rad = sqrt(-2.0 * log(u1)), th = 2.0 * M_PI * u2;\n    xi[2 * p] = rad * cos(th);\n    xi[2 * p + 1] = rad * sin(th);\n  }\n  const double A = s->a * s->a / 6.0;",
+     PIN.check_smc_moves_follow_the_draws),
     # smart Monte Carlo on molecules of any architecture and type
     ("smc_force_linear_on_architectures", "  const uint32_t n_fpart = or_partners(s, chain, i, fpart);",
      "  uint32_t n_fpart = 0;\n  if (i > 0) fpart[n_fpart++] = i - 1u;\n"

@@ -630,6 +630,57 @@ def test_smc_force_direction(oracle_lib):
     check_smc_force_direction()
 
 
+def check_smc_moves_follow_the_draws(lib=None):
+    """Free particles (N = 1) in a field ramp along x, away from its periodic
+    seam, so that the field force is the same constant F = (-0.8, 0, 0) at
+    the old and at the trial cell: every trial position is r + A F + sqrt(2A)
+    xi with xi the Box-Muller normals of the top 24 bits of words (0, 1) and
+    (2, 3) of the move draw, and the acceptance compares ln u, u the open
+    uniform of the low bytes of words 0, 1, 2, with ln alpha = -dE -
+    |r - r' - A F|^2/(4A) + |r' - r - A F|^2/(4A), all recomputed here in
+    FP64 from the Philox words."""
+    d = SystemDesc(n_chains=2000, N=1, f=1.0, box_Re=(64 / 6, 8 / 6, 8 / 6), grid=(64, 8, 8),
+                   chiN=0.0, kappaN=0.0, a_Re=0.15, move=1, seed=5)
+    s = oracle_system(d, lib)
+    p = s.empty_positions()
+    rng = np.random.default_rng(2)
+    p.x[:] = rng.uniform(20, 44, d.M)
+    p.y[:] = rng.uniform(0, 8, d.M)
+    p.z[:] = rng.uniform(0, 8, d.M)
+    before = p.copy()
+    ramp = 0.8 * (np.arange(s.cells) % 64).astype(np.float64)
+    sweep = 7
+    st, margin, acc, trial = s.sweep(p, ramp, ramp, sweep, want_margin=True, want_acc=True,
+                                     want_trial=True)
+    a = float(s.params.a)
+    A = a * a / 6.0
+    F = np.array([-0.8, 0.0, 0.0])
+    for k in range(d.M):
+        w = [int(v) for v in s.draw(1, k, sweep)]
+        u = [((v >> 8) + 0.5) / 2**24 for v in w]
+        r1, r2 = math.sqrt(-2 * math.log(u[0])), math.sqrt(-2 * math.log(u[2]))
+        xi = [r1 * math.cos(2 * math.pi * u[1]), r1 * math.sin(2 * math.pi * u[1]),
+              r2 * math.cos(2 * math.pi * u[3])]
+        r = np.array([before.x[k], before.y[k], before.z[k]], np.float64)
+        want = np.float32(r + np.float32(A * F + math.sqrt(2 * A) * np.array(xi)))
+        got = trial[:, k]
+        assert np.all(np.abs(got - want) <= np.spacing(np.abs(want).astype(np.float32))), (k, got, want)
+        rn = got.astype(np.float64)
+        dE = 0.8 * (math.floor(rn[0]) - math.floor(r[0]))
+        fwd = ((rn - r - A * F) ** 2).sum()
+        rev = ((r - rn - A * F) ** 2).sum()
+        log_alpha = -dE - rev / (4 * A) + fwd / (4 * A)
+        low = (w[0] & 0xFF) | (w[1] & 0xFF) << 8 | (w[2] & 0xFF) << 16
+        lnu = math.log((low + 0.5) / 2**24)
+        assert abs(margin[k] - (lnu - log_alpha)) < 1e-9, (k, margin[k], lnu - log_alpha)
+        assert bool(acc[k]) == (log_alpha >= 0 or lnu < log_alpha)
+    assert 0.5 < acc.mean() < 0.999
+
+
+def test_smc_moves_follow_the_draws(oracle_lib):
+    check_smc_moves_follow_the_draws()
+
+
 # --------------------------------------------------------------------------
 # Learned proposal: the gradient of the expected-squared-jump objective
 # (through both network evaluations) against central finite differences.
