@@ -33,7 +33,7 @@
 // lane, so every lane is busy whatever the sizes and orders of the sets, and a
 // mover reads its bond partners from the record wherever they sit.  Bond
 // energy change of r -> r + d with partners q: K_b (2 d.U + k d.d),
-// U = sum_q (r - r_q).  256 threads, 3 blocks per SM (80 registers, 25 KB of
+// U = sum_q (r - r_q).  256 threads, 3 blocks per SM (80 registers, 28 KB of
 // shared memory per block).
 #include <algorithm>
 
@@ -93,16 +93,23 @@ __device__ __forceinline__ uint32_t pw_set(uint32_t w) { return (w >> 25) & 7u; 
 __device__ __forceinline__ uint32_t pw_sets(uint32_t w) { return w >> 28; }
 
 // Shared-memory record of one warp's tile, one 16-byte entry per particle and
-// array (a mover reads each with one 128-bit access): P = current position and
+// array (a mover reads each with one 128-bit access), entry q at slot
+// rec(q) = q + q/8 for the uniform move: a quarter warp's 128-bit accesses
+// are conflict-free when its eight entries fall in distinct 16-byte bank
+// groups, and the movers of one set of a chain (every second particle) do
+// once each run of eight entries is shifted by one slot (the smart Monte Carlo
+// variant, whose time is set by its longer move body, keeps q).  P = current position and
 // final cell, T = trial position and acceptance threshold (smart Monte Carlo:
 // the three normals and ln u), Q = table word, trial cell, molecule start |
 // architecture << 8, type; W (smart Monte Carlo only) = omega and field force
 // at the current cell; and the list of this step's movers.
 template <bool SMC>
 struct TopoTile {
-  float4 P[TOPO_TILE];
-  float4 T[TOPO_TILE];
-  uint4 Q[TOPO_TILE];
+  static constexpr int REC = SMC ? TOPO_TILE : TOPO_TILE + TOPO_TILE / 8;
+  static __device__ __forceinline__ uint32_t rec(uint32_t q) { return SMC ? q : q + (q >> 3); }
+  float4 P[REC];
+  float4 T[REC];
+  uint4 Q[REC];
   float4 W[SMC ? TOPO_TILE : 1];
   uint8_t movers[TOPO_TILE];
 };
@@ -203,7 +210,7 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
       // type: the architecture's type byte (n_t types) or the A/B bit
       const uint32_t type = MULTI ? (present ? __ldg(t.ttab + a * TOPO_TILE + ci) : 0u)
                                   : (uint32_t)pw_is_B(pw);
-      S.P[tl] = make_float4(x[j], y[j], z[j], __uint_as_float(co));
+      S.P[S.rec(tl)] = make_float4(x[j], y[j], z[j], __uint_as_float(co));
       if (SMC) {
         float sn, cs;
         const float rad0 = sqrtf(-2.f * log_uniform_open_accurate(r.x));
@@ -211,11 +218,11 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
         const float gx = rad0 * cs, gy = rad0 * sn;
         const float rad1 = sqrtf(-2.f * log_uniform_open_accurate(r.z));
         sincos_2pi_uniform_fast(r.w, &sn, &cs);
-        S.T[tl] = make_float4(gx, gy, rad1 * cs, log_uniform_open(spare_uniform_word(r)));
-        S.Q[tl] = make_uint4(pw, 0u, (gc[j] & 0xFFu) * N | a << 8, type);
+        S.T[S.rec(tl)] = make_float4(gx, gy, rad1 * cs, log_uniform_open(spare_uniform_word(r)));
+        S.Q[S.rec(tl)] = make_uint4(pw, 0u, (gc[j] & 0xFFu) * N | a << 8, type);
         // the table entry of the current cell, gathered here for all slots at
         // once rather than inside the mover's dependent chain
-        S.W[tl] = present ? __ldg(p.smc_tab + (size_t)type * p.g.cells + co)
+        S.W[S.rec(tl)] = present ? __ldg(p.smc_tab + (size_t)type * p.g.cells + co)
                           : make_float4(0.f, 0.f, 0.f, 0.f);
       } else {
         const float xn = __fmaf_rn(p.a, uniform_sym(r.x), x[j]);
@@ -230,8 +237,8 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
           const WT* wt = type ? wB : wA;
           if (present) dEf = load_w<WT>(wt, cn) - load_w<WT>(wt, co);
         }
-        S.T[tl] = make_float4(xn, yn, zn, -log_uniform_open(r.w) - dEf);
-        S.Q[tl] = make_uint4(pw, cn, (gc[j] & 0xFFu) * N | a << 8, type);
+        S.T[S.rec(tl)] = make_float4(xn, yn, zn, -log_uniform_open(r.w) - dEf);
+        S.Q[S.rec(tl)] = make_uint4(pw, cn, (gc[j] & 0xFFu) * N | a << 8, type);
       }
       ty[j] = type;
       own[j] = (valid && ci == 0u)
@@ -266,15 +273,15 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
       const uint32_t count = c0 + __popc(b1);
       for (uint32_t r = (uint32_t)lane; r < count; r += 32u) {
         const uint32_t q = S.movers[r];
-        const uint4 Qq = S.Q[q];
-        const float4 Pq = S.P[q];
+        const uint4 Qq = S.Q[S.rec(q)];
+        const float4 Pq = S.P[S.rec(q)];
         const uint32_t pw = Qq.x, mol0 = Qq.z & 0xFFu;
         const uint32_t deg = pw_degree(pw);
         float ux = 0.f, uy = 0.f, uz = 0.f;
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
           if ((uint32_t)b < deg) {
-            const float4 Pn = S.P[mol0 + pw_partner(pw, b)];
+            const float4 Pn = S.P[S.rec(mol0 + pw_partner(pw, b))];
             ux += Pq.x - Pn.x;
             uy += Pq.y - Pn.y;
             uz += Pq.z - Pn.z;
@@ -286,18 +293,18 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
           mk &= mk - 1ull;
           mk &= mk - 1ull;
           for (; mk; mk &= mk - 1ull) {
-            const float4 Pn = S.P[mol0 + (uint32_t)__ffsll((long long)mk) - 1u];
+            const float4 Pn = S.P[S.rec(mol0 + (uint32_t)__ffsll((long long)mk) - 1u)];
             ux += Pq.x - Pn.x;
             uy += Pq.y - Pn.y;
             uz += Pq.z - Pn.z;
           }
         }
-        const float4 Tq = S.T[q];
+        const float4 Tq = S.T[S.rec(q)];
         if (SMC) {
           // bonded force -2 K_b U plus the field force of the particle's type
           const float4* __restrict__ tab = p.smc_tab + (size_t)Qq.w * p.g.cells;
           const float A = p.smc_A, K2 = 2.f * p.K_b, k = (float)deg;
-          const float4 Wq = S.W[q];
+          const float4 Wq = S.W[S.rec(q)];
           const float w_old = Wq.x, fox = Wq.y, foy = Wq.z, foz = Wq.w;
           float fnx, fny, fnz;
           const float Fx = fmaf(-K2, ux, fox), Fy = fmaf(-K2, uy, foy), Fz = fmaf(-K2, uz, foz);
@@ -319,7 +326,7 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
           const float rev = fmaf(bx, bx, fmaf(by, by, bz * bz));
           const float log_alpha = fmaf(fwd - rev, p.smc_inv4A, -dE);
           if (log_alpha >= 0.f || Tq.w < log_alpha) {
-            S.P[q] = make_float4(tx, ty, tz, __uint_as_float(cn));
+            S.P[S.rec(q)] = make_float4(tx, ty, tz, __uint_as_float(cn));
             ++my_acc;
           }
         } else {
@@ -327,7 +334,7 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
           const float du = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
           const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
           if (p.K_b * fmaf(2.f, du, (float)deg * dd) <= Tq.w) {
-            S.P[q] = make_float4(Tq.x, Tq.y, Tq.z, __uint_as_float(Qq.y));
+            S.P[S.rec(q)] = make_float4(Tq.x, Tq.y, Tq.z, __uint_as_float(Qq.y));
             ++my_acc;
           }
         }
@@ -340,7 +347,7 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
       const uint32_t tl = (uint32_t)lane + 32u * (uint32_t)j;
       if (tl >= nmono) continue;
       const IDX m = base + tl;
-      const float4 Pf = S.P[tl];
+      const float4 Pf = S.P[S.rec(tl)];
       if ((step[j] & 15u) == 15u) continue;   // an absent slot: kept, not counted
       __stcs(p.x + m, Pf.x);
       __stcs(p.y + m, Pf.y);
