@@ -160,10 +160,11 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
     return (rem < (IDX)G ? (uint32_t)rem : G) * N;
   };
 
-  // positions and architectures (a0 | a1 << 8) of the next tile, loaded
-  // while the current one is processed
+  // positions, architectures (a0 | a1 << 8) and table words of the next
+  // tile, loaded while the current one is processed (the field gathers of
+  // a tile then wait on nothing but its own draws)
   float px[2] = {0.f, 0.f}, py[2] = {0.f, 0.f}, pz[2] = {0.f, 0.f};
-  uint32_t pa = 0u;
+  uint32_t pa = 0u, ppw[2] = {0u, 0u};
   auto prefetch = [&](IDX tile) {
     if (tile >= n_tiles) return;
     const uint32_t rows = tile_rows(tile);
@@ -171,12 +172,15 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const uint32_t tl = (uint32_t)lane + 32u * (uint32_t)j;
+      ppw[j] = 0u;
       if (tl >= rows) continue;
       const IDX m = tile * (G * N) + tl;
       px[j] = __ldcs(p.x + m);
       py[j] = __ldcs(p.y + m);
       pz[j] = __ldcs(p.z + m);
-      pa |= (uint32_t)__ldg(t.mol_arch + (tile * G + (gc[j] & 0xFFu))) << (8 * j);
+      const uint32_t aj = __ldg(t.mol_arch + (tile * G + (gc[j] & 0xFFu)));
+      pa |= aj << (8 * j);
+      ppw[j] = __ldg(t.ptab + aj * TOPO_TILE + (gc[j] >> 8));
     }
   };
   IDX tile = (IDX)blockIdx.x * TOPO_WARPS + wib;
@@ -189,6 +193,7 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
     const IDX base = chain0 * N;
     const float x[2] = {px[0], px[1]}, y[2] = {py[0], py[1]}, z[2] = {pz[0], pz[1]};
     const uint32_t a2 = pa;
+    const uint32_t pw2[2] = {ppw[0], ppw[1]};
     prefetch(tile + nwarps);
 
     // Draws, trial positions, cells and field changes of the natural slots,
@@ -201,7 +206,7 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
       const uint32_t ci = gc[j] >> 8;
       const uint32_t a = (a2 >> (8 * j)) & 0xFFu;
       const IDX m = base + tl;
-      const uint32_t pw = valid ? __ldg(t.ptab + a * TOPO_TILE + ci) : 0u;
+      const uint32_t pw = pw2[j];
       const bool present = pw_sets(pw) != 0u;   // false: empty slot or absent particle
       const IDX mc = m + (IDX)p.g.id_base;
       const uint32_t hi = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)mc >> 32) : 0u;
@@ -229,13 +234,16 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
         const float yn = __fmaf_rn(p.a, uniform_sym(r.y), y[j]);
         const float zn = __fmaf_rn(p.a, uniform_sym(r.z), z[j]);
         const uint32_t cn = cell_of(p.g, xn, yn, zn);
-        float dEf = 0.f;
+        // the field change, gathered for every slot (an absent or empty
+        // slot's cells are in the grid, its value unused): no wait on the
+        // table word
+        float dEf;
         if (MULTI) {
           const float* wt = t.wt + (size_t)type * p.g.cells;
-          if (present) dEf = __ldg(wt + cn) - __ldg(wt + co);
+          dEf = __ldg(wt + cn) - __ldg(wt + co);
         } else {
           const WT* wt = type ? wB : wA;
-          if (present) dEf = load_w<WT>(wt, cn) - load_w<WT>(wt, co);
+          dEf = load_w<WT>(wt, cn) - load_w<WT>(wt, co);
         }
         S.T[S.rec(tl)] = make_float4(xn, yn, zn, -log_uniform_open(r.w) - dEf);
         S.Q[S.rec(tl)] = make_uint4(pw, cn, (gc[j] & 0xFFu) * N | a << 8, type);
