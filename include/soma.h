@@ -440,6 +440,18 @@ void* soma_stream(soma_t* h);
 soma_status soma_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
                         void* stream);
 
+/* What the smart Monte Carlo move (Sec. 2.2) makes of its Philox draw, for n
+ * draws of four words each (words, 4n uint32) into out (4n floats): the three
+ * standard normals of the Box-Muller transform of the uniforms (k + 1/2)/2^24
+ * of the top 24 bits k of words (0, 1) and (2, 3) -- radius sqrt(-2 ln u1)
+ * with ln u1 accurate to about an FP32 ulp, angle 2 pi u2 by the hardware
+ * sincos -- and ln u of the acceptance uniform, k = the low bytes of words 0,
+ * 1, 2 (word 0's lowest), by the hardware log.  The same device functions as
+ * the sweeps.  Both pointers device memory; asynchronous on stream.
+ * SOMA_EINVAL for a NULL pointer with n > 0.  Used to check the transforms
+ * against independent implementations. */
+soma_status soma_smc_draws(const uint32_t* words, float* out, size_t n, void* stream);
+
 /* ------------------------------------------------------------------------
  * Learned proposal (desc.move = SOMA_MOVE_LEARNED; no counterpart in the
  * paper, whose force-biased proposal is the smart Monte Carlo move, Sec. 2.2).

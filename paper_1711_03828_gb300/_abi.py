@@ -137,6 +137,7 @@ _SIGS = {
     "soma_sync": ([_P], _c.c_int),
     "soma_stream": ([_P], _P),
     "soma_philox": ([_P, _P, _P, _c.c_size_t, _P], _c.c_int),
+    "soma_smc_draws": ([_P, _P, _c.c_size_t, _P], _c.c_int),
     "soma_structure_factor_noalloc": ([_c.POINTER(SomaSystemDesc), _P, _P, _c.c_size_t, _P, _P],
                                       _c.c_int),
     "soma_proposal_set_weights": ([_P, _P, _c.c_size_t, _c.c_int], _c.c_int),
@@ -220,6 +221,7 @@ soma_get_timing = _wrap("soma_get_timing")
 soma_sync = _wrap("soma_sync")
 soma_stream = _wrap("soma_stream")
 soma_philox = _wrap("soma_philox")
+soma_smc_draws = _wrap("soma_smc_draws")
 soma_structure_factor_noalloc = _wrap("soma_structure_factor_noalloc")
 soma_proposal_set_weights = _wrap("soma_proposal_set_weights")
 soma_proposal_get_weights = _wrap("soma_proposal_get_weights")

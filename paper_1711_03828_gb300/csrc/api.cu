@@ -1462,6 +1462,15 @@ soma_status soma_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out,
   return SOMA_OK;
 }
 
+soma_status soma_smc_draws(const uint32_t* words, float* out, size_t n, void* stream) {
+  if (n && (!words || !out)) return fail(SOMA_EINVAL, "NULL argument");
+  int dev = 0, sms = 1;
+  SOMA_CUDA(cudaGetDevice(&dev));
+  SOMA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  SOMA_CUDA(launch_smc_draws(words, out, n, sms, (cudaStream_t)stream));
+  return SOMA_OK;
+}
+
 
 // ---------------------------------------------------------------------------
 // Batches of independent systems (one sweep launch + one field launch per cycle)

@@ -474,4 +474,29 @@ cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* ou
   return cudaGetLastError();
 }
 
+// What a smart Monte Carlo move makes of its draw (four words): the three
+// normals and ln u of the spare 24 bits, by the sweeps' own device functions.
+__global__ void smc_draws_kernel(const uint32_t* __restrict__ w, float* __restrict__ out,
+                                 size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const uint4 r = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+    float gx, gy, gz;
+    smc_normals(r, gx, gy, gz);
+    out[4 * i] = gx;
+    out[4 * i + 1] = gy;
+    out[4 * i + 2] = gz;
+    out[4 * i + 3] = log_uniform_open(spare_uniform_word(r));
+  }
+}
+
+cudaError_t launch_smc_draws(const uint32_t* words, float* out, size_t n, int sm_count,
+                             cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const size_t blocks = (n + 255) / 256;
+  const size_t cap = (size_t)8 * (size_t)(sm_count > 0 ? sm_count : 1);
+  smc_draws_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, st>>>(words, out, n);
+  return cudaGetLastError();
+}
+
 }  // namespace soma

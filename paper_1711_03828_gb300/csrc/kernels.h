@@ -74,6 +74,10 @@ cudaError_t launch_structure_factor(const Geom& g, const uint32_t* n, const doub
 
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
                           cudaStream_t st);
+// out[4i..4i+3] = the three normals and ln u a smart Monte Carlo move takes
+// from draw words[4i..4i+3]
+cudaError_t launch_smc_draws(const uint32_t* words, float* out, size_t n, int sm_count,
+                             cudaStream_t st);
 
 cudaError_t launch_sweep_batch(const BatchArgs& a, int grid, int block, int grid_dtype,
                                cudaStream_t st);

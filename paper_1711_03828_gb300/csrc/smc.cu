@@ -163,14 +163,7 @@ __global__ void __launch_bounds__(256) sweep_smc_kernel(const SweepArgs p) {
       const uint64_t m = base + j + p.g.id_base;
       const uint4 r1 = philox_rk(make_uint4((uint32_t)m, (uint32_t)(m >> 32), sweep, ctr3a), p.g);
       lowbits |= (r1.w & 1u) << j;
-      float sn, cs;
-      const float rad0 = sqrtf(-2.f * log_uniform_open_accurate(r1.x));
-      sincos_2pi_uniform_fast(r1.y, &sn, &cs);
-      gx[j] = rad0 * cs;
-      gy[j] = rad0 * sn;
-      const float rad1 = sqrtf(-2.f * log_uniform_open_accurate(r1.z));
-      sincos_2pi_uniform_fast(r1.w, &sn, &cs);
-      gz[j] = rad1 * cs;
+      smc_normals(r1, gx[j], gy[j], gz[j]);
       lnu[j] = log_uniform_open(spare_uniform_word(r1));
       uint32_t cx, cy, cz;
       cell3(p.g, x[j], y[j], z[j], cx, cy, cz);
@@ -281,14 +274,7 @@ __device__ __forceinline__ SmcSlot smc_slot(const Geom& g, const float4* tab, fl
   q.x = x; q.y = y; q.z = z;
   const uint4 r1 = philox_rk(make_uint4(m, 0u, sweep, ctr3a), g);
   *first_word = r1.w;
-  float sn, cs;
-  const float rad0 = sqrtf(-2.f * log_uniform_open_accurate(r1.x));
-  sincos_2pi_uniform_fast(r1.y, &sn, &cs);
-  q.gx = rad0 * cs;
-  q.gy = rad0 * sn;
-  const float rad1 = sqrtf(-2.f * log_uniform_open_accurate(r1.z));
-  sincos_2pi_uniform_fast(r1.w, &sn, &cs);
-  q.gz = rad1 * cs;
+  smc_normals(r1, q.gx, q.gy, q.gz);
   q.lnu = log_uniform_open(spare_uniform_word(r1));
   uint32_t cx, cy, cz;
   cell3(g, x, y, z, cx, cy, cz);

@@ -217,13 +217,9 @@ __global__ void __launch_bounds__(256, 3) sweep_topology_kernel(const TopoArgs t
                                   : (uint32_t)pw_is_B(pw);
       S.P[S.rec(tl)] = make_float4(x[j], y[j], z[j], __uint_as_float(co));
       if (SMC) {
-        float sn, cs;
-        const float rad0 = sqrtf(-2.f * log_uniform_open_accurate(r.x));
-        sincos_2pi_uniform_fast(r.y, &sn, &cs);
-        const float gx = rad0 * cs, gy = rad0 * sn;
-        const float rad1 = sqrtf(-2.f * log_uniform_open_accurate(r.z));
-        sincos_2pi_uniform_fast(r.w, &sn, &cs);
-        S.T[S.rec(tl)] = make_float4(gx, gy, rad1 * cs, log_uniform_open(spare_uniform_word(r)));
+        float gx, gy, gz;
+        smc_normals(r, gx, gy, gz);
+        S.T[S.rec(tl)] = make_float4(gx, gy, gz, log_uniform_open(spare_uniform_word(r)));
         S.Q[S.rec(tl)] = make_uint4(pw, 0u, (gc[j] & 0xFFu) * N | a << 8, type);
         // the table entry of the current cell, gathered here for all slots at
         // once rather than inside the mover's dependent chain

@@ -18,8 +18,8 @@ import pytest
 
 import oracle
 from oracle import Positions
-from paper_1711_03828_gb300 import (FLAG_NO_SORT, SET_ORDER_FIXED, SET_ORDER_RANDOM, System,
-                                    SystemDesc, _abi)
+from paper_1711_03828_gb300 import (FLAG_NO_SORT, SET_ORDER_FIXED, SET_ORDER_RANDOM, SomaError,
+                                    System, SystemDesc, _abi)
 from paper_1711_03828_gb300 import workloads
 from tests.conftest import oracle_system
 
@@ -146,6 +146,57 @@ def test_philox_matches_oracle_bit_exact(dev):
     out = o.cpu().numpy().view(np.uint32)
     for i in range(n):
         np.testing.assert_array_equal(out[i], oracle.philox(ctr[i], key[i]))
+
+
+def test_smc_draws_match_fp64(dev):
+    """What the smart Monte Carlo move makes of its draw, against FP64: the
+    radius sqrt(-2 ln u) of the Box-Muller normals for every one of the 2^24
+    uniforms u = (k + 1/2)/2^24 (angle words at u2 = 1/2 + 2^-25, where the
+    cosine rounds to -1 in FP32, so the first and third normals are minus the
+    radii) within 3 FP32 ulps; for random draws the three normals within the
+    hardware sincos's absolute error times the radius, and ln u of the spare
+    24 bits (the low bytes of words 0-2) within the hardware log's."""
+    import torch
+    n = 1 << 24
+    k = np.arange(n, dtype=np.uint64)
+    w = np.zeros((n, 4), np.uint32)
+    w[:, 0] = (k << 8).astype(np.uint32)
+    w[:, 2] = ((n - 1 - k) << 8).astype(np.uint32)
+    w[:, 1] = w[:, 3] = np.uint32((1 << 23) << 8)
+    src = torch.from_numpy(w.reshape(-1).view(np.int32)).to(dev)
+    out = torch.empty(4 * n, dtype=torch.float32, device=dev)
+    _abi.soma_smc_draws(src.data_ptr(), out.data_ptr(), n, None)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy().reshape(n, 4).astype(np.float64)
+    u = (np.arange(n, dtype=np.float64) + 0.5) / 2.0**24
+    rad = np.sqrt(-2.0 * np.log(u))
+    ulp = np.spacing(rad.astype(np.float32)).astype(np.float64)
+    err0 = np.abs(-o[:, 0] - rad) / ulp
+    err2 = np.abs(-o[:, 2] - rad[::-1]) / ulp[::-1]
+    print(f"radius: max error {err0.max():.2f} / {err2.max():.2f} ulps over all 2^24 uniforms")
+    assert err0.max() <= 3.0 and err2.max() <= 3.0
+    # random draws
+    rng = np.random.default_rng(7)
+    m = 1 << 20
+    w = rng.integers(0, 2**32, (m, 4), dtype=np.uint64).astype(np.uint32)
+    src = torch.from_numpy(w.reshape(-1).view(np.int32)).to(dev)
+    out = torch.empty(4 * m, dtype=torch.float32, device=dev)
+    _abi.soma_smc_draws(src.data_ptr(), out.data_ptr(), m, None)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy().reshape(m, 4).astype(np.float64)
+    uu = ((w.astype(np.uint64) >> 8).astype(np.float64) + 0.5) / 2.0**24
+    r0, r1 = np.sqrt(-2 * np.log(uu[:, 0])), np.sqrt(-2 * np.log(uu[:, 2]))
+    th0, th1 = 2 * np.pi * uu[:, 1], 2 * np.pi * uu[:, 3]
+    want = np.stack([r0 * np.cos(th0), r0 * np.sin(th0), r1 * np.cos(th1)], axis=1)
+    tol = np.stack([r0, r0, r1], axis=1) * 2.0**-20 + 1e-7
+    assert np.all(np.abs(o[:, :3] - want) <= tol), np.max(np.abs(o[:, :3] - want) / tol)
+    low = ((w[:, 0] & 0xFF) | (w[:, 1] & 0xFF).astype(np.uint64) << 8 |
+           (w[:, 2] & 0xFF).astype(np.uint64) << 16).astype(np.float64)
+    lnu = np.log((low + 0.5) / 2.0**24)
+    tol = np.maximum(2.0**-21, 4 * 2.0**-23 * np.abs(lnu))
+    assert np.all(np.abs(o[:, 3] - lnu) <= tol), np.max(np.abs(o[:, 3] - lnu) / tol)
+    with pytest.raises(SomaError):
+        _abi.soma_smc_draws(None, out.data_ptr(), 4, None)
 
 
 @pytest.mark.parametrize("flags", [0, FLAG_NO_SORT])
