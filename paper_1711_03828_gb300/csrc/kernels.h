@@ -95,8 +95,10 @@ const void* learned_kernel_ptr(int Q, int grid_dtype);
 const void* learned_tc_kernel_ptr(int grid_dtype, bool umma);
 // one warp waits (at most limit polls) for an mbarrier phase nobody completes
 cudaError_t launch_wait_probe(uint32_t limit, unsigned* err, cudaStream_t st);
-// molecule-parallel sweep kernel for chains of N particles; *smem receives its
-// dynamic shared memory (prepare: allow the kernel that much, once at create)
+// molecule-parallel sweep kernel for chains of N particles (one thread per
+// chain, MOL_BLOCK threads and chains per block); *smem receives its dynamic
+// shared memory (prepare: allow the kernel that much, once at create)
+constexpr int MOL_BLOCK = 128;
 const void* molecule_kernel_ptr(uint32_t N, int grid_dtype, size_t* smem, bool prepare);
 // smart Monte Carlo sweep kernel: paired layout (even N <= 64, 32-bit indices) or general
 const void* smc_kernel_ptr(int Q, bool pair, int grid_dtype);

@@ -17,7 +17,6 @@
 namespace soma {
 
 constexpr uint32_t PURPOSE_ATTEMPT = 3;
-constexpr int MOL_BLOCK = 128;
 
 // Table word of the architecture path (see topology.cu): bits 0-5 number of
 // partners, 6-23 the first three partners, bit 24 type.

@@ -344,7 +344,7 @@ SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dty
   }
   if (molecule && move == 0) {
     s.molecule = true;
-    s.block = 128;
+    s.block = MOL_BLOCK;
     fn = molecule_kernel_ptr(N, grid_dtype, &s.smem, true);
   }
   int per_sm = 0;
