@@ -5,6 +5,7 @@
 //   - initial chains: Sec. 2.1 (Gaussian bonds, b0 = sqrt(3/k0));
 //   - energies: Eq. (h-bond), (V-harmonic), (discrete-ham); S(q): Sec. 5.6.
 #include "kernels.h"
+#include "draws.cuh"
 
 namespace soma {
 

@@ -13,6 +13,7 @@
 //
 // Parameter layout (1604): W1[32][12] b1[32] W2[32][32] b2[32] W3[4][32] b3[4].
 #include "kernels.h"
+#include "draws.cuh"
 
 namespace soma {
 

@@ -22,6 +22,7 @@
 // of learned.cu and is shared by both.
 #include "kernels.h"
 #include "pair_body.cuh"
+#include "draws.cuh"
 
 namespace soma {
 

@@ -15,6 +15,7 @@
 // trial position.
 #include "kernels.h"
 #include "pair_body.cuh"
+#include "draws.cuh"
 
 namespace soma {
 

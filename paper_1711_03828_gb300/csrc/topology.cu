@@ -38,6 +38,7 @@
 #include <algorithm>
 
 #include "kernels.h"
+#include "draws.cuh"
 
 namespace soma {
 
