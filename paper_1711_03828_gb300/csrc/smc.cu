@@ -336,15 +336,27 @@ __global__ void __launch_bounds__(256, 3) sweep_smc_pair_kernel(const SweepArgs 
   const float4* tab1 = p.smc_tab + (L.v1 == 1u ? 0u : p.g.cells);
   const uint32_t TN = p.G * p.g.N;
   unsigned my_acc = 0;
+  // positions of the warp's next tile, loaded while the current one is moved
+  float2 nx = make_float2(0.f, 0.f), ny = nx, nz = nx;
+  auto load_pos = [&](uint32_t t) {
+    if (t < t_end && (t < (uint32_t)p.full_tiles || L.li0 < p.last_rows)) {
+      const uint32_t b = t * TN + L.li0;
+      nx = __ldcs(reinterpret_cast<const float2*>(p.x + b));
+      ny = __ldcs(reinterpret_cast<const float2*>(p.y + b));
+      nz = __ldcs(reinterpret_cast<const float2*>(p.z + b));
+    }
+  };
+  load_pos(t_begin + (threadIdx.x >> 5));
   for (uint32_t tile = t_begin + (threadIdx.x >> 5); tile < t_end; tile += nwarps) {
     const bool valid = tile < (uint32_t)p.full_tiles || L.li0 < p.last_rows;
     const uint32_t base = tile * TN + L.li0;
     float2 px = make_float2(0.f, 0.f), py = px, pz = px;
     if (valid) {
-      px = __ldcs(reinterpret_cast<const float2*>(p.x + base));
-      py = __ldcs(reinterpret_cast<const float2*>(p.y + base));
-      pz = __ldcs(reinterpret_cast<const float2*>(p.z + base));
+      px = nx;
+      py = ny;
+      pz = nz;
     }
+    load_pos(tile + nwarps);
     uint32_t w0, w1;
     const uint32_t cbase = base + (uint32_t)p.g.id_base;
     const SmcSlot s0 = smc_slot(p.g, tab0, px.x, py.x, pz.x, cbase, sweep, ctr3a, valid, &w0);
