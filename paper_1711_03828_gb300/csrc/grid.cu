@@ -41,18 +41,26 @@ cudaError_t launch_histogram(const Geom& g, const float* x, const float* y, cons
 
 // Range check of positions given by the caller: flag = 1 if any value is not
 // finite or has |v| >= lim (the supported range of the cell fold).
+// p starts 16-byte aligned (every position plane is 256-byte aligned): four
+// coordinates per 16-byte load, the last n mod 4 one by one.
 __global__ void __launch_bounds__(256) range_check_kernel(const float* __restrict__ p, uint64_t n,
                                                           float lim, unsigned* flag) {
   unsigned bad = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    bad |= !(fabsf(p[i]) < lim);
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t n4 = n / 4;
+  const float4* __restrict__ q = reinterpret_cast<const float4*>(p);
+  for (uint64_t i = tid; i < n4; i += stride) {
+    const float4 v = __ldg(q + i);
+    bad |= !(fabsf(v.x) < lim) | !(fabsf(v.y) < lim) | !(fabsf(v.z) < lim) | !(fabsf(v.w) < lim);
+  }
+  for (uint64_t i = 4 * n4 + tid; i < n; i += stride) bad |= !(fabsf(p[i]) < lim);
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1u);
 }
 
 cudaError_t launch_range_check(const float* p, uint64_t n, float lim, unsigned* flag, int sm_count,
                                cudaStream_t st) {
-  uint64_t blocks = (n + 255) / 256;
+  uint64_t blocks = (n / 4 + 255) / 256;
   const uint64_t cap = (uint64_t)sm_count * 8;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;

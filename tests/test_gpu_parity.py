@@ -257,6 +257,21 @@ def test_positions_outside_the_supported_range_are_rejected(dev):
     s.update_fields()
     s.sweep(2)
     s.close()
+    # every lane of the 16-byte loads and the scalar tail (M = 441: one
+    # coordinate past the last full group of four), in every plane
+    d = SystemDesc(n_chains=63, N=7, box_Re=(1.0, 1.0, 1.0), grid=(6, 6, 6))
+    s = System(d)
+    good = workloads.random_walk_positions(d, seed=2)
+    for plane in range(3):
+        for idx in (0, 1, 2, 3, 437, 439, d.M - 1):
+            p = good.copy()
+            p[plane, idx] = np.inf if idx % 2 else -262144.0
+            with pytest.raises(SomaError) as e:
+                s.set_positions(p)
+            assert e.value.status == _abi.SOMA_EINVAL, (plane, idx)
+    s.set_positions(good)
+    s.sweep(1)
+    s.close()
 
 
 def test_parameters_closed_forms(dev):
