@@ -95,23 +95,22 @@ __device__ __forceinline__ uint32_t pw_sets(uint32_t w) { return w >> 28; }
 
 // Shared-memory record of one warp's tile, one 16-byte entry per particle and
 // array (a mover reads each with one 128-bit access), entry q at slot
-// rec(q) = q + q/8 for the uniform move: a quarter warp's 128-bit accesses
-// are conflict-free when its eight entries fall in distinct 16-byte bank
-// groups, and the movers of one set of a chain (every second particle) do
-// once each run of eight entries is shifted by one slot (the smart Monte Carlo
-// variant, whose time is set by its longer move body, keeps q).  P = current position and
+// rec(q) = q + q/8: a quarter warp's 128-bit accesses are conflict-free when
+// its eight entries fall in distinct 16-byte bank groups, and the movers of
+// one set of a chain (every second particle) do once each run of eight
+// entries is shifted by one slot.  P = current position and
 // final cell, T = trial position and acceptance threshold (smart Monte Carlo:
 // the three normals and ln u), Q = table word, trial cell, molecule start |
 // architecture << 8, type; W (smart Monte Carlo only) = omega and field force
 // at the current cell; and the list of this step's movers.
 template <bool SMC>
 struct TopoTile {
-  static constexpr int REC = SMC ? TOPO_TILE : TOPO_TILE + TOPO_TILE / 8;
-  static __device__ __forceinline__ uint32_t rec(uint32_t q) { return SMC ? q : q + (q >> 3); }
+  static constexpr int REC = TOPO_TILE + TOPO_TILE / 8;
+  static __device__ __forceinline__ uint32_t rec(uint32_t q) { return q + (q >> 3); }
   float4 P[REC];
   float4 T[REC];
   uint4 Q[REC];
-  float4 W[SMC ? TOPO_TILE : 1];
+  float4 W[SMC ? REC : 1];
   uint8_t movers[TOPO_TILE];
 };
 
