@@ -273,16 +273,17 @@ __device__ __forceinline__ SmcSlot smc_slot(const Geom& g, const float4* tab, fl
                                             bool valid, uint32_t* first_word) {
   SmcSlot q;
   q.x = x; q.y = y; q.z = z;
-  const uint4 r1 = philox_rk(make_uint4(m, 0u, sweep, ctr3a), g);
-  *first_word = r1.w;
-  smc_normals(r1, q.gx, q.gy, q.gz);
-  q.lnu = log_uniform_open(spare_uniform_word(r1));
+  // the old cell's table entry first: in flight during the draw and normals
   uint32_t cx, cy, cz;
   cell3(g, x, y, z, cx, cy, cz);
   q.c = (cz * (uint32_t)g.ny + cy) * (uint32_t)g.nx + cx;
   q.w = 0.f;
   q.fx = q.fy = q.fz = 0.f;
   if (valid) q.w = smc_field(tab, q.c, q.fx, q.fy, q.fz);
+  const uint4 r1 = philox_rk(make_uint4(m, 0u, sweep, ctr3a), g);
+  *first_word = r1.w;
+  smc_normals(r1, q.gx, q.gy, q.gz);
+  q.lnu = log_uniform_open(spare_uniform_word(r1));
   return q;
 }
 
