@@ -88,6 +88,21 @@ __device__ __forceinline__ void pair_prepare(const Geom& g, const Geom& keys, co
                                              IDX cbase, bool valid, uint32_t sweep, uint32_t ctr3,
                                              float a, float x0, float x1, float y0, float y1,
                                              float z0, float z1, PairState& P) {
+  // the old cells and their field values first: they wait on nothing but the
+  // positions, so the gathers are in flight during the draws
+  const unsigned long long MAG = f2_pack(12582912.0f, 12582912.0f);
+  const unsigned long long X = f2_pack(x0, x1), Y = f2_pack(y0, y1), Z = f2_pack(z0, z1);
+  float fx0, fx1, fy0, fy1, fz0, fz1, gx0, gx1, gy0, gy1, gz0, gz1;
+  f2_unpack(f2_add_rm(X, MAG), fx0, fx1);
+  f2_unpack(f2_add_rm(Y, MAG), fy0, fy1);
+  f2_unpack(f2_add_rm(Z, MAG), fz0, fz1);
+  P.c0 = cell_of_floor_bits<WIDE>(g, __float_as_uint(fx0), __float_as_uint(fy0), __float_as_uint(fz0));
+  P.c1 = cell_of_floor_bits<WIDE>(g, __float_as_uint(fx1), __float_as_uint(fy1), __float_as_uint(fz1));
+  P.wo0 = P.wo1 = 0.f;
+  if (valid) {
+    P.wo0 = load_w<WT>(L.w0, P.c0);
+    P.wo1 = load_w<WT>(L.w1, P.c1);
+  }
   const uint32_t hi = sizeof(IDX) > 4 ? (uint32_t)((uint64_t)cbase >> 32) : 0u;
   const uint4 r0 = philox_rk(make_uint4((uint32_t)cbase, hi, sweep, ctr3), keys);
   const IDX m1 = cbase + 1u;
@@ -101,8 +116,6 @@ __device__ __forceinline__ void pair_prepare(const Geom& g, const Geom& keys, co
   const unsigned long long S = f2_pack(1.1920928955078125e-7f, 1.1920928955078125e-7f);
   const unsigned long long C = f2_pack(-0.99999994039535522461f, -0.99999994039535522461f);
   const unsigned long long A2 = f2_pack(a, a);
-  const unsigned long long MAG = f2_pack(12582912.0f, 12582912.0f);
-  const unsigned long long X = f2_pack(x0, x1), Y = f2_pack(y0, y1), Z = f2_pack(z0, z1);
   const unsigned long long XN = f2_fma_rn(
       A2, f2_fma_rn(f2_pack(__uint2float_rn(r0.x >> 8), __uint2float_rn(r1.x >> 8)), S, C), X);
   const unsigned long long YN = f2_fma_rn(
@@ -112,23 +125,15 @@ __device__ __forceinline__ void pair_prepare(const Geom& g, const Geom& keys, co
   f2_unpack(XN, P.xn0, P.xn1);
   f2_unpack(YN, P.yn0, P.yn1);
   f2_unpack(ZN, P.zn0, P.zn1);
-  float fx0, fx1, fy0, fy1, fz0, fz1, gx0, gx1, gy0, gy1, gz0, gz1;
-  f2_unpack(f2_add_rm(X, MAG), fx0, fx1);
-  f2_unpack(f2_add_rm(Y, MAG), fy0, fy1);
-  f2_unpack(f2_add_rm(Z, MAG), fz0, fz1);
   f2_unpack(f2_add_rm(XN, MAG), gx0, gx1);
   f2_unpack(f2_add_rm(YN, MAG), gy0, gy1);
   f2_unpack(f2_add_rm(ZN, MAG), gz0, gz1);
-  P.c0 = cell_of_floor_bits<WIDE>(g, __float_as_uint(fx0), __float_as_uint(fy0), __float_as_uint(fz0));
-  P.c1 = cell_of_floor_bits<WIDE>(g, __float_as_uint(fx1), __float_as_uint(fy1), __float_as_uint(fz1));
   P.cn0 = cell_of_floor_bits<WIDE>(g, __float_as_uint(gx0), __float_as_uint(gy0), __float_as_uint(gz0));
   P.cn1 = cell_of_floor_bits<WIDE>(g, __float_as_uint(gx1), __float_as_uint(gy1), __float_as_uint(gz1));
-  P.wn0 = P.wo0 = P.wn1 = P.wo1 = 0.f;
+  P.wn0 = P.wn1 = 0.f;
   if (valid) {
     P.wn0 = load_w<WT>(L.w0, P.cn0);
-    P.wo0 = load_w<WT>(L.w0, P.c0);
     P.wn1 = load_w<WT>(L.w1, P.cn1);
-    P.wo1 = load_w<WT>(L.w1, P.c1);
   }
   P.x0 = x0; P.x1 = x1; P.y0 = y0; P.y1 = y1; P.z0 = z0; P.z1 = z1;
   P.u0 = r0.w;
