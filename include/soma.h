@@ -262,8 +262,12 @@ soma_status soma_set_external(soma_t* h, const float* ext, const uint8_t* forbid
  * sequences, bit i of seq[a] set meaning particle i of architecture a is B,
  * and arch (n_chains bytes) the architecture of every chain.  Replaces the
  * diblock derived from desc.f for the sweep and the occupation count; call
- * soma_update_fields to recount at once.  N <= 64, uniform moves, even N
- * for the SET scheme (any N <= 64 with SOMA_ITERATION_MOLECULE).  seq = NULL
+ * soma_update_fields to recount at once.  N <= 64.  Uniform moves: even N
+ * for the SET scheme (any N <= 64 with SOMA_ITERATION_MOLECULE).  Smart
+ * Monte Carlo moves (any N <= 64): the mixture is set as linear
+ * architectures through soma_set_topology (particle i of type bit i, bonded
+ * to i - 1 and i + 1), whose sweep moves a linear chain as the linear path
+ * does.  The learned proposal: SOMA_EINVAL.  seq = NULL
  * returns to the diblock.  Every arch entry is checked against n_arch
  * (SOMA_EINVAL).  The handle keeps its own copies.  Synchronises. */
 soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_arch,

@@ -862,8 +862,9 @@ soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_ar
   }
   if (!arch || n_arch < 1 || n_arch > 256) return fail(SOMA_EINVAL, "need 1..256 architectures and arch");
   if (h->g.N > 64) return fail(SOMA_EINVAL, "mixtures take N <= 64");
-  if (h->desc.move != SOMA_MOVE_UNIFORM) return fail(SOMA_EINVAL, "mixtures take uniform moves");
-  if (h->desc.set_order != SOMA_ITERATION_MOLECULE && (h->g.N % 2 != 0 || h->shape.big))
+  if (h->desc.move == SOMA_MOVE_LEARNED) return fail(SOMA_EINVAL, "mixtures take uniform or smart Monte Carlo moves");
+  if (h->desc.move == SOMA_MOVE_UNIFORM && h->desc.set_order != SOMA_ITERATION_MOLECULE &&
+      (h->g.N % 2 != 0 || h->shape.big))
     return fail(SOMA_EINVAL, "mixtures take even N (SET) or the molecule-parallel iteration");
   // every architecture index is checked on the host (it addresses seq)
   std::vector<uint8_t> a((size_t)h->g.n_chains);
@@ -873,6 +874,33 @@ soma_status soma_set_architectures(soma_t* h, const uint64_t* seq, uint32_t n_ar
     std::memcpy(a.data(), arch, a.size());
   for (size_t k = 0; k < a.size(); ++k)
     if (a[k] >= n_arch) return fail(SOMA_EINVAL, "arch[%zu] = %u >= n_arch = %u", k, a[k], n_arch);
+  if (h->desc.move == SOMA_MOVE_SMC) {
+    // Smart Monte Carlo moves run on the architecture path: each linear
+    // architecture written in the array layout of Sec. 3.2.1 (particle i of
+    // type bit i of its sequence, bonded to i - 1 and i + 1).
+    const uint32_t N = h->g.N;
+    std::vector<uint64_t> sq(n_arch);
+    SOMA_CUDA(cudaMemcpy(sq.data(), seq, sizeof(uint64_t) * n_arch,
+                         src_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+    std::vector<uint32_t> words, start(n_arch);
+    for (uint32_t k = 0; k < n_arch; ++k) {
+      start[k] = (uint32_t)words.size();
+      words.push_back(N);
+      const size_t first = words.size();
+      words.resize(first + N);
+      for (uint32_t i = 0; i < N; ++i) {
+        const uint32_t type = (uint32_t)((sq[k] >> i) & 1ull);
+        if (N == 1) {
+          words[first + i] = 0xFFFFFFu << 8 | type;   // a lone particle: no bonds
+          continue;
+        }
+        words[first + i] = (uint32_t)words.size() << 8 | type;
+        if (i > 0) words.push_back(0x7FFFFFFu << 5 | (i + 1 < N ? 0u : 1u));   // offset -1
+        if (i + 1 < N) words.push_back(1u << 5 | 1u);                          // offset +1, last
+      }
+    }
+    return soma_set_topology(h, words.data(), words.size(), start.data(), n_arch, a.data(), 0);
+  }
   cudaError_t e;
   if (!h->d_seq) {
     e = cudaMalloc((void**)&h->d_seq, sizeof(uint64_t) * 256);
