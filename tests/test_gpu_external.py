@@ -56,6 +56,30 @@ def test_external_fields_and_k1_cycles_match_oracle(cuda_device, hamiltonian):
     assert r.moves >= 6 * d.M
 
 
+@pytest.mark.parametrize("hamiltonian", [0, 1])
+def test_external_potential_smc_matches_oracle(cuda_device, hamiltonian):
+    """Smart Monte Carlo in an external potential (no closed cells: their
+    infinite fields have no gradient): the field force includes the
+    potential's central difference; one cycle from each of three starts
+    against the oracle with the SMC tolerances."""
+    from paper_1711_03828_gb300 import MOVE_SMC
+    from tests.test_gpu_smc import compare_smc_cycle
+    moves = mism = 0
+    for k, sweep in enumerate((0, 7, 500)):
+        d = workloads.melt_small(hamiltonian=hamiltonian, chiN=25.0, move=MOVE_SMC, seed=41 + k)
+        ext, _ = _external(d, 5 + k)
+        s = System(d)
+        s.set_external(ext, None)
+        orc = oracle_system(d)
+        orc.set_external(ext.astype(np.float64), None)
+        m, b, _ = compare_smc_cycle(d, s, orc, workloads.random_walk_positions(d, seed=81 + k),
+                                    sweep)
+        moves += m
+        mism += b
+    print(f"SMC K{hamiltonian} with an external potential: {moves} moves, mismatches {mism}")
+    assert mism <= max(3, 2e-4 * moves)
+
+
 def _step(r, forbidden):
     """One cycle in both; positions compared as in Runner.step, the grid with
     the infinite walls taken into account."""

@@ -97,50 +97,22 @@ def test_mixture_smc_matches_oracle(cuda_device, N, n_chains, grid, box):
     """Smart Monte Carlo on a mixture (even and odd N): one cycle from each of
     three starts against the oracle's mixture path, with the tolerances of
     the SMC parity tests; the counts follow the sequences."""
-    from tests.test_gpu_smc import TIE_SMC, _near_face, _tol
+    from tests.test_gpu_smc import compare_smc_cycle
     moves = mism = accepted = 0
     for k, sweep in enumerate((0, 5, 300)):
         d = SystemDesc(n_chains=n_chains, N=N, f=0.5, box_Re=box, grid=grid, chiN=30.0,
                        kappaN=50.0, move=MOVE_SMC, seed=31 + k)
         seq = _sequences(N)
         arch = np.random.default_rng(9 + k).integers(0, len(seq), d.n_chains).astype(np.uint8)
-        pos0 = workloads.random_walk_positions(d, seed=71 + k)
         s = System(d)
         s.set_architectures(seq, arch)
-        s.set_positions(pos0)
-        s.set_sweep(sweep)
         orc = oracle_system(d)
         orc.set_architectures(seq, arch)
-        p = _pos(pos0)
-        nA, nB = orc.histogram(p)
-        n = s.get_density()
-        np.testing.assert_array_equal(n & 0xFFFF, nA)
-        np.testing.assert_array_equal(n >> 16, nB)
-        wA, wB = orc.fields(nA, nB)
-        st, margin, acc, trial = orc.sweep(p, wA, wB, sweep, want_margin=True, want_acc=True,
-                                           want_trial=True)
-        s.sweep(1)
-        g = s.get_positions()
-        s.close()
-        gacc = np.any(g != pos0, axis=0).astype(np.uint8)
-        bad = np.nonzero(gacc != acc)[0]
-        ok = set(bad[np.abs(margin[bad]) < TIE_SMC].tolist())
-        face = _near_face(trial)
-        ok |= {int(m) for m in bad if face[m]}
-        for m in bad.tolist():
-            if m not in ok:
-                assert any(q in ok for q in range(m - m % N, m - m % N + N)), (m, margin[m])
-        keep = np.ones(d.n_chains, bool)
-        keep[np.unique(bad // N)] = False
-        keep = np.repeat(keep, N)
-        rej = keep & (acc == 0)
-        np.testing.assert_array_equal(g[:, rej], pos0[:, rej])
-        accd = keep & (acc == 1)
-        err = np.abs(g[:, accd].astype(np.float64) - trial[:, accd]) / _tol(trial[:, accd])
-        assert err.max(initial=0) <= 1.0, err.max()
-        moves += d.M
-        mism += len(bad)
-        accepted += int(acc.sum())
+        m, b, a = compare_smc_cycle(d, s, orc, workloads.random_walk_positions(d, seed=71 + k),
+                                    sweep)
+        moves += m
+        mism += b
+        accepted += a
     print(f"SMC mixture N={N}: {moves} moves, acceptance {accepted / moves:.3f}, mismatches {mism}")
     assert mism <= max(3, 2e-4 * moves)
     assert 0.3 < accepted / moves < 0.999

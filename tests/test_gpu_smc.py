@@ -40,6 +40,44 @@ def _near_face(trial):
     return np.any(dist <= 1e-6 * RE + ULPS * _spacing(trial), axis=0)
 
 
+def compare_smc_cycle(d, s, orc, pos0, sweep):
+    """One SMC cycle of the configured System s and oracle orc from pos0 at
+    sweep number sweep (s is closed here): counts bit-exact; decisions equal
+    except near-ties, trials within 4 ulps of a cell face and the molecules of
+    those; rejected moves bit-identical, accepted ones within 1e-6 R_e0 of the
+    oracle's trial.  Returns (moves, mismatches, accepted)."""
+    s.set_positions(pos0)
+    s.set_sweep(sweep)
+    p = _pos(pos0)
+    nA, nB = orc.histogram(p)
+    n = s.get_density()
+    np.testing.assert_array_equal(n & 0xFFFF, nA)
+    np.testing.assert_array_equal(n >> 16, nB)
+    wA, wB = orc.fields(nA, nB)
+    st, margin, acc, trial = orc.sweep(p, wA, wB, sweep, want_margin=True, want_acc=True,
+                                       want_trial=True)
+    s.sweep(1)
+    g = s.get_positions()
+    s.close()
+    gacc = np.any(g != pos0, axis=0).astype(np.uint8)
+    bad = np.nonzero(gacc != acc)[0]
+    ok = set(bad[np.abs(margin[bad]) < TIE_SMC].tolist())
+    face = _near_face(np.nan_to_num(trial))
+    ok |= {int(m) for m in bad if face[m]}
+    ok_mol = {m // d.N for m in ok}
+    for m in bad.tolist():
+        assert m in ok or m // d.N in ok_mol, (m, margin[m])
+    keep = np.ones(d.n_chains, bool)
+    keep[np.unique(bad // d.N)] = False
+    keep = np.repeat(keep, d.N)
+    rej = keep & (acc == 0)
+    np.testing.assert_array_equal(g[:, rej], pos0[:, rej])
+    accd = keep & (acc == 1)
+    err = np.abs(g[:, accd].astype(np.float64) - trial[:, accd]) / _tol(trial[:, accd])
+    assert err.max(initial=0) <= 1.0, err.max()
+    return d.M, len(bad), int(acc.sum())
+
+
 def _one_cycle(d, pos0, sweep):
     orc = oracle_system(d)
     s = System(d)
