@@ -70,9 +70,24 @@ __device__ __forceinline__ void molecule_body(const SweepArgs& p, const TopoArgs
       float* X = STAGE ? sx + t * N : p.x + chain * N;
       float* Y = STAGE ? sy + t * N : p.y + chain * N;
       float* Z = STAGE ? sz + t * N : p.z + chain * N;
+      // linear chains: the next attempt's draw (independent of this attempt's
+      // outcome) is computed while this attempt's field gathers are in flight;
+      // for architectures that measured slower (more registers in the longer
+      // partner loop), so they draw in turn
+      const uint64_t id0 = chain * N + p.g.id_base;
+      uint4 rnext = make_uint4(0u, 0u, 0u, 0u);
+      if (!TOPO)
+        rnext = philox_rk(make_uint4((uint32_t)id0, (uint32_t)(id0 >> 32), sweep, ctr3), p.g);
       for (uint32_t j = 0; j < len; ++j) {
-        const uint64_t id = chain * N + j + p.g.id_base;
-        const uint4 r = philox_rk(make_uint4((uint32_t)id, (uint32_t)(id >> 32), sweep, ctr3), p.g);
+        uint4 r;
+        if (!TOPO) {
+          r = rnext;
+          const uint64_t idn = id0 + j + 1u;
+          rnext = philox_rk(make_uint4((uint32_t)idn, (uint32_t)(idn >> 32), sweep, ctr3), p.g);
+        } else {
+          const uint64_t id = id0 + j;
+          r = philox_rk(make_uint4((uint32_t)id, (uint32_t)(id >> 32), sweep, ctr3), p.g);
+        }
         const uint32_t i = ((r.w & 0xFFu) * len) >> 8;
         const float xo = X[i], yo = Y[i], zo = Z[i];
         const float xn = __fmaf_rn(a, uniform_sym(r.x), xo);
