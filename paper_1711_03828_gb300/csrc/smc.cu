@@ -154,18 +154,14 @@ __global__ void __launch_bounds__(256) sweep_smc_kernel(const SweepArgs p) {
       z[j] = ok ? __ldcs(p.z + base + j) : 0.f;
     }
 
-    // configuration-independent part: normals, acceptance uniform, old cell,
-    // field and field force at the old cell
+    // configuration-independent part: old cell, field and field force at the
+    // old cell (loaded first, so that the loads are in flight during the
+    // draws), normals, acceptance uniform
     float gx[S], gy[S], gz[S], lnu[S], w_old[S], fox[S], foy[S], foz[S];
     uint32_t co[S];
     uint32_t lowbits = 0;
 #pragma unroll
     for (int j = 0; j < S; ++j) {
-      const uint64_t m = base + j + p.g.id_base;
-      const uint4 r1 = philox_rk(make_uint4((uint32_t)m, (uint32_t)(m >> 32), sweep, ctr3a), p.g);
-      lowbits |= (r1.w & 1u) << j;
-      smc_normals(r1, gx[j], gy[j], gz[j]);
-      lnu[j] = log_uniform_open(spare_uniform_word(r1));
       uint32_t cx, cy, cz;
       cell3(p.g, x[j], y[j], z[j], cx, cy, cz);
       co[j] = (cz * (uint32_t)p.g.ny + cy) * (uint32_t)p.g.nx + cx;
@@ -173,6 +169,14 @@ __global__ void __launch_bounds__(256) sweep_smc_kernel(const SweepArgs p) {
       w_old[j] = 0.f;
       fox[j] = foy[j] = foz[j] = 0.f;
       if (li0 + j < nmono) w_old[j] = smc_field(tab, co[j], fox[j], foy[j], foz[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      const uint64_t m = base + j + p.g.id_base;
+      const uint4 r1 = philox_rk(make_uint4((uint32_t)m, (uint32_t)(m >> 32), sweep, ctr3a), p.g);
+      lowbits |= (r1.w & 1u) << j;
+      smc_normals(r1, gx[j], gy[j], gz[j]);
+      lnu[j] = log_uniform_open(spare_uniform_word(r1));
     }
 
     uint32_t phase[S];
