@@ -12,7 +12,9 @@ the rank's chain range.  After three cycles the positions of each shard and
 the all-reduced counts must equal the monolithic run bit for bit (chains are
 independent under frozen fields, integer addition is associative, and the
 random-number counters are global particle indices).  A third rank count
-(three ranks on 512 chains) leaves shards of unequal size.
+(three ranks on 512 chains) leaves shards of unequal size.  The same holds
+for molecules of several architectures under smart Monte Carlo moves (each
+rank holding its molecules' architecture bytes).
 """
 import os
 import socket
@@ -27,21 +29,38 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _desc():
+def _desc(case="diblock"):
+    from paper_1711_03828_gb300 import SystemDesc, workloads
+    if case == "diblock":
+        return workloads.melt_small(n_chains=512, chiN=25.0)
+    return SystemDesc(n_chains=600, N=16, f=0.5, box_Re=(2.0, 2.0, 1.0), grid=(12, 12, 6),
+                      chiN=25.0, kappaN=50.0, move=1, seed=5)
+
+
+def _setup(case, orc, c0, c1):
+    """The molecules' architectures of chains [c0, c1) for the architecture case."""
+    if case == "diblock":
+        return
     from paper_1711_03828_gb300 import workloads
-    return workloads.melt_small(n_chains=512, chiN=25.0)
+    mols = [workloads.star_architecture(3, 5), workloads.ring_architecture(16),
+            workloads.comb_architecture(8, 4, 2), workloads.linear_architecture(16)]
+    words, starts = workloads.encode_architectures(mols)
+    arch = np.random.default_rng(3).integers(0, len(mols), 600).astype(np.uint8)
+    orc.set_topology(words, starts, arch[c0:c1])
 
 
 class OracleShard:
     """The oracle behind the shard calls of ``System``: chains [c0, c1) of the
     whole system's positions move, their counts are packed A | B<<16."""
 
-    def __init__(self, d, c0, c1):
+    def __init__(self, d, c0, c1, case="diblock"):
         from tests.conftest import oracle_system
         self.d, self.c0, self.c1 = d, c0, c1
         self.full = oracle_system(d)
+        _setup(case, self.full, 0, d.n_chains)
         self.p = self.full.initial_state()
         self.own = oracle_system(type(d)(**{**d.__dict__, "n_chains": c1 - c0}))
+        _setup(case, self.own, c0, c1)
         self.sweep_no = 0
         self.wA = self.wB = None
 
@@ -67,15 +86,15 @@ class OracleShard:
         self.wA, self.wB = self.full.fields(self.nA, self.nB)
 
 
-def _rank_main(rank, world, port, out_dir):
+def _rank_main(rank, world, port, out_dir, case="diblock"):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     from paper_1711_03828_gb300.shard import ShardedRun, shard_desc
-    d = _desc()
+    d = _desc(case)
     sd = shard_desc(d, world, rank)
-    shard = OracleShard(d, sd.chain_offset, sd.chain_offset + sd.n_chains)
+    shard = OracleShard(d, sd.chain_offset, sd.chain_offset + sd.n_chains, case)
     run = ShardedRun(shard, d.cells, "cpu")
     run.start()
     run.cycle(3)
@@ -88,14 +107,15 @@ def _rank_main(rank, world, port, out_dir):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world", [2, 3])
-def test_sharded_cycle_equals_monolithic(oracle_lib, tmp_path, world):
+@pytest.mark.parametrize("world,case", [(2, "diblock"), (3, "diblock"), (2, "architectures_smc")])
+def test_sharded_cycle_equals_monolithic(oracle_lib, tmp_path, world, case):
     import torch.multiprocessing as mp
-    mp.start_processes(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world,
+    mp.start_processes(_rank_main, args=(world, _free_port(), str(tmp_path), case), nprocs=world,
                        join=True, start_method="spawn")
     from tests.conftest import oracle_system
-    d = _desc()
+    d = _desc(case)
     full = oracle_system(d)
+    _setup(case, full, 0, d.n_chains)
     p = full.initial_state()
     nA, nB = full.histogram(p)
     for sweep in range(3):
