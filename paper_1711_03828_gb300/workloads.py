@@ -57,9 +57,10 @@ def melt_mid(seed=1, **kw):
 
 def melt_tiny(seed=1, **kw):
     """The smallest system of the paper's weak-scaling series (n = 2^7 chains
-    of N = 64, sqrt(Nbar) = 128, dL = R_e0/6): 8192 particles in a 2x1x1 R_e0
-    box, 12x6x6 grid, homopolymer-like (chiN = 0), kappaN = 50."""
-    d = dict(n_chains=128, N=64, f=0.5, box_Re=(2.0, 1.0, 1.0), grid=(12, 6, 6), chiN=0.0,
+    of N = 64, sqrt(Nbar) = 128, dL = R_e0/6): 8192 particles in a 1x1x1 R_e0
+    box (rho_0 R_e0^3 = 128 N), 6x6x6 grid, homopolymer-like (chiN = 0),
+    kappaN = 50."""
+    d = dict(n_chains=128, N=64, f=0.5, box_Re=(1.0, 1.0, 1.0), grid=(6, 6, 6), chiN=0.0,
              kappaN=50.0, seed=seed)
     d.update(kw)
     return SystemDesc(**d)

@@ -14,6 +14,7 @@ from tests import test_oracle_pins as PIN
 from tests import test_oracle_topology as TOPO
 from tests import test_oracle_types as TYPES
 from tests import test_oracle_learned_bf16 as BF16
+from tests import test_oracle_golden as GOLD
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "soma_oracle.c")
 
@@ -147,6 +148,8 @@ MUTANTS = [
     ("smc_normals_paired_wrongly", "double u1 = or_uniform_open(w1[2 * p]), u2 = or_uniform_open(w1[2 * p + 1]);\n    double rad = sqrt(-2.0 * log(u1)), th = 2.0 * M_PI * u2;\n    xi[2 * p] = rad * cos(th);\n    xi[2 * p + 1] = rad * sin(th);\n  }\n  const double A = s->a * s->a / 6.0;",
      "double u1 = or_uniform_open(w1[p]), u2 = or_uniform_open(w1[p + 2]);\n    double rad = sqrt(-2.0 * log(u1)), th = 2.0 * M_PI * u2;\n    xi[2 * p] = rad * cos(th);\n    xi[2 * p + 1] = rad * sin(th);\n  }\n  const double A = s->a * s->a / 6.0;",
      PIN.check_smc_moves_follow_the_draws),
+    ("density_counts_bonds", "s->rho_cell = (double)n_chains * (double)N / cells;",
+     "s->rho_cell = (double)n_chains * (double)(N - 1) / cells;", GOLD.check_printed_systems),
     # smart Monte Carlo on molecules of any architecture and type
     ("smc_force_linear_on_architectures", "  const uint32_t n_fpart = or_partners(s, chain, i, fpart);",
      "  uint32_t n_fpart = 0;\n  if (i > 0) fpart[n_fpart++] = i - 1u;\n"
