@@ -577,12 +577,13 @@ soma_status soma_batch_get_timing(soma_batch_t* b, soma_timing* out);
  * loading (the default) that lookup is what loads this part of the library
  * onto the device and allocates the array there -- so make the first call
  * at a time when device memory can still be allocated (for instance right
- * after soma_create) and before any stream capture.  The address is kept for
+ * after soma_create).  The address is kept for
  * the rest of the process: after a cudaDeviceReset of that device the kept
  * address is stale and this entry point must not be called on it again.  The
  * array stays allocated on every device that made a call until the process
  * exits.  Every call synchronises its stream before returning (the results
- * are copied to the host array out).  All calls share the array: two calls
+ * are copied to the host array out), so no call may be made on a stream that
+ * is being captured into a graph.  All calls share the array: two calls
  * that overlap on the GPU (different streams, or different host threads
  * without ordering) race and may return wrong values.  Every call overwrites
  * all of the scratch it reads.
