@@ -532,7 +532,10 @@ typedef struct soma_batch_t soma_batch_t;
 typedef struct soma_tune_entry {
   int32_t block;          /* threads per block */
   int32_t blocks_per_sm;  /* resident blocks per SM (persistent grid) */
-  int32_t item_tiles;     /* 32-lane tiles per work item */
+  int32_t item_tiles;     /* 32-lane tiles per work item, taken by the blocks
+                             in turn; 0 (the default): every block takes one
+                             contiguous range of the members' concatenated
+                             tiles, equal to within a tile */
   int32_t reserved;
   double ms_per_cycle;    /* sweep + field update, CUDA events */
 } soma_tune_entry;
@@ -544,12 +547,19 @@ soma_status soma_batch_destroy(soma_batch_t* b);
 soma_status soma_batch_sweep(soma_batch_t* b, uint32_t n);
 soma_status soma_batch_sync(soma_batch_t* b);
 soma_status soma_batch_system(soma_batch_t* b, uint32_t i, soma_t** out);
-/* Time every launch shape (block 128/256/512 x resident blocks per SM x
- * work-item length 16/64/256 tiles) over cycles_per_candidate real cycles
+/* Time every launch shape (block 128/256/512 threads that fit the kernel x
+ * 1..8 resident blocks per SM that fit x work items of 16/64/256 tiles or the
+ * equal contiguous range per block) over cycles_per_candidate real cycles
  * (the members advance), keep the fastest.  table (optional) receives up to
- * table_len entries; *n_written the number of shapes tried. */
+ * table_len entries; *n_written the number of shapes tried.  The paper tunes
+ * its parallel regions the same way, by timing candidates (Sec. 3.2.2). */
 soma_status soma_batch_autotune(soma_batch_t* b, uint32_t cycles_per_candidate,
                                 soma_tune_entry* table, uint32_t table_len, uint32_t* n_written);
+/* Use a given launch shape (e.g. one tuned earlier; ms_per_cycle ignored).
+ * SOMA_EINVAL unless block is a multiple of 32 the kernel accepts,
+ * blocks_per_sm of that block fit on one SM and item_tiles >= 0.  Results do
+ * not depend on the shape: every member evolves as it would alone. */
+soma_status soma_batch_set_shape(soma_batch_t* b, const soma_tune_entry* shape);
 soma_status soma_batch_get_shape(soma_batch_t* b, soma_tune_entry* out);
 soma_status soma_batch_set_timing(soma_batch_t* b, int on);
 soma_status soma_batch_get_timing(soma_batch_t* b, soma_timing* out);

@@ -427,6 +427,13 @@ class Batch:
         return [dict(block=t.block, blocks_per_sm=t.blocks_per_sm, item_tiles=t.item_tiles,
                      ms_per_cycle=t.ms_per_cycle) for t in tab[:nw.value]]
 
+    def set_shape(self, block, blocks_per_sm, item_tiles):
+        """Launch shape of the batched sweep (item_tiles 0: one equal
+        contiguous range of tiles per block)."""
+        t = _abi.SomaTuneEntry(block=int(block), blocks_per_sm=int(blocks_per_sm),
+                               item_tiles=int(item_tiles))
+        _abi.soma_batch_set_shape(self.h, ctypes.byref(t))
+
     def shape(self):
         t = _abi.SomaTuneEntry()
         _abi.soma_batch_get_shape(self.h, ctypes.byref(t))

@@ -1517,7 +1517,7 @@ struct soma_batch_t {
   unsigned* d_aux = nullptr;  // [0] arrival counter, [1] error bits
   uint32_t total_cells = 0;
   BatchArgs args{};
-  int block = 256, blocks_per_sm = 2, item_tiles = 64;
+  int block = 256, blocks_per_sm = 2, item_tiles = 0;
   cudaGraphExec_t graph = nullptr;
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_sweep, ev_field;
@@ -1545,10 +1545,39 @@ void batch_release(soma_batch_t* b) {
 
 soma_status batch_items(soma_batch_t* b, int item_tiles) {
   std::vector<BatchItem> items;
-  for (uint32_t k = 0; k < b->sys.size(); ++k) {
-    const uint32_t nt = (uint32_t)b->sys[k]->shape.n_tiles;
-    for (uint32_t t0 = 0; t0 < nt; t0 += (uint32_t)item_tiles)
-      items.push_back({k, t0, std::min(nt, t0 + (uint32_t)item_tiles)});
+  if (item_tiles > 0) {
+    for (uint32_t k = 0; k < b->sys.size(); ++k) {
+      const uint32_t nt = (uint32_t)b->sys[k]->shape.n_tiles;
+      for (uint32_t t0 = 0; t0 < nt; t0 += (uint32_t)item_tiles)
+        items.push_back({k, t0, std::min(nt, t0 + (uint32_t)item_tiles)});
+    }
+  } else {
+    // One contiguous range of the members' concatenated tiles per block,
+    // equal to within a tile, cut at member boundaries into pieces; block j
+    // takes items j, j + grid, j + 2 grid, ... so piece r of block j sits at
+    // r * grid + j, and blocks with fewer pieces get empty ones.
+    const uint32_t grid = (uint32_t)(b->sm_count * b->blocks_per_sm);
+    std::vector<uint64_t> begin(b->sys.size() + 1, 0);
+    for (uint32_t k = 0; k < b->sys.size(); ++k)
+      begin[k + 1] = begin[k] + (uint64_t)b->sys[k]->shape.n_tiles;
+    const uint64_t total = begin.back();
+    std::vector<std::vector<BatchItem>> per(grid);
+    size_t rounds = 1;
+    uint32_t k = 0;
+    for (uint32_t j = 0; j < grid; ++j) {
+      uint64_t g0 = total * j / grid;
+      const uint64_t g1 = total * (j + 1) / grid;
+      while (g0 < g1) {
+        while (begin[k + 1] <= g0) ++k;
+        const uint64_t e = std::min(g1, begin[k + 1]);
+        per[j].push_back({k, (uint32_t)(g0 - begin[k]), (uint32_t)(e - begin[k])});
+        g0 = e;
+      }
+      rounds = std::max(rounds, per[j].size());
+    }
+    items.assign(rounds * grid, BatchItem{0u, 0u, 0u});
+    for (uint32_t j = 0; j < grid; ++j)
+      for (size_t r = 0; r < per[j].size(); ++r) items[r * grid + j] = per[j][r];
   }
   if (items.size() > b->items_cap) {
     cudaFree(b->d_items);
@@ -1804,7 +1833,7 @@ soma_status soma_batch_autotune(soma_batch_t* b, uint32_t cycles_per_candidate,
   if (!b) return fail(SOMA_EINVAL, "batch is NULL");
   if (cycles_per_candidate < 1) cycles_per_candidate = 1;
   const int blocks[3] = {128, 256, 512};
-  const int items[3] = {16, 64, 256};
+  const int items[4] = {16, 64, 256, 0};
   std::vector<soma_tune_entry> res;
   cudaEvent_t e0, e1;
   SOMA_CUDA(cudaEventCreate(&e0));
@@ -1818,9 +1847,13 @@ soma_status soma_batch_autotune(soma_batch_t* b, uint32_t cycles_per_candidate,
     if (st != SOMA_OK) return st;
     for (int blk : blocks) {
       const int fit = batch_kernel_blocks_per_sm(blk, b->grid_dtype);
-      for (int bps = 1; bps <= fit && bps <= 4; ++bps) {
+      for (int bps = 1; bps <= fit && bps <= 8; ++bps) {
         b->block = blk;
         b->blocks_per_sm = bps;
+        if (it == 0) {  // the balanced split depends on the grid
+          st = batch_items(b, 0);
+          if (st != SOMA_OK) return st;
+        }
         st = batch_cycle(b);  // warm-up with this shape
         if (st != SOMA_OK) return st;
         SOMA_CUDA(cudaEventRecord(e0, b->stream));
@@ -1849,6 +1882,20 @@ soma_status soma_batch_autotune(soma_batch_t* b, uint32_t cycles_per_candidate,
     for (uint32_t k = 0; k < table_len && k < res.size(); ++k) table[k] = res[k];
   if (n_written) *n_written = (uint32_t)res.size();
   return SOMA_OK;
+}
+
+soma_status soma_batch_set_shape(soma_batch_t* b, const soma_tune_entry* shape) {
+  if (!b || !shape) return fail(SOMA_EINVAL, "NULL argument");
+  if (shape->block < 32 || shape->block > 1024 || shape->block % 32 != 0)
+    return fail(SOMA_EINVAL, "block=%d: a multiple of 32 in 32..1024", (int)shape->block);
+  const int fit = batch_kernel_blocks_per_sm(shape->block, b->grid_dtype);
+  if (shape->blocks_per_sm < 1 || shape->blocks_per_sm > fit)
+    return fail(SOMA_EINVAL, "blocks_per_sm=%d: 1..%d fit on an SM with block=%d",
+                (int)shape->blocks_per_sm, fit, (int)shape->block);
+  if (shape->item_tiles < 0) return fail(SOMA_EINVAL, "item_tiles=%d < 0", (int)shape->item_tiles);
+  b->block = shape->block;
+  b->blocks_per_sm = shape->blocks_per_sm;
+  return batch_items(b, shape->item_tiles);
 }
 
 soma_status soma_batch_get_shape(soma_batch_t* b, soma_tune_entry* out) {

@@ -5,11 +5,15 @@
 // rank (Sec. 3.1, 3.2.2).  Here a batch of independent systems (different
 // sizes, chain lengths, compositions, chiN, replicas of one seed) shares a
 // single persistent launch: the tiles of all systems are cut into work items
-// of contiguous tiles of one system; blocks take items round-robin and their
-// warps walk an item's tiles with the same tile body as the single-system
+// of contiguous tiles of one system; block j takes items j, j + grid, ... and
+// its warps walk an item's tiles with the same tile body as the single-system
 // kernel (pair_body.cuh), so every system evolves bit-identically to the same
-// system run alone.  Launch shape (block size, blocks per SM, item length) is
-// picked by an autotuner that times the candidates during the run.
+// system run alone.  The host lays the items out either as fixed-length items
+// of each system in turn or as one equal contiguous range of the concatenated
+// tiles per block, cut at system boundaries (piece r of block j at item
+// r * grid + j, padded with empty items).  Launch shape (block size, blocks
+// per SM, split) is picked by an autotuner that times the candidates during
+// the run.
 #include "kernels.h"
 #include "pair_body.cuh"
 

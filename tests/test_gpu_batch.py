@@ -78,6 +78,32 @@ def test_batch_autotune_keeps_results(cuda_device):
     b.close()
 
 
+@pytest.mark.parametrize("shape", [(256, 3, 0), (128, 5, 0), (64, 1, 0), (256, 2, 16), (128, 4, 7)])
+def test_batch_shapes_keep_results(cuda_device, shape):
+    """Every launch shape covers every tile exactly once: the balanced split
+    (item_tiles 0: one equal contiguous range of the members' tiles per block,
+    cut at member boundaries; with fewer tiles than blocks some ranges are
+    empty, with 64 x 1 per SM a range holds a few tiles and some cross a
+    member boundary) and work items taken in turn, eager and replayed."""
+    from paper_1711_03828_gb300 import SomaError
+    descs = _small_batch(7)
+    b = Batch(descs)
+    b.set_shape(*shape)
+    sh = b.shape()
+    assert (sh["block"], sh["blocks_per_sm"], sh["item_tiles"]) == shape
+    singles = [System(d) for d in descs]
+    b.sweep(2)
+    b.sweep(16)
+    for s in singles:
+        s.sweep(18)
+    _compare(b, singles)
+    for bad in [(100, 1, 0), (256, 0, 0), (256, 64, 0), (512, 1, 0), (256, 1, -1)]:
+        with pytest.raises(SomaError):
+            b.set_shape(*bad)
+    assert b.shape() == sh
+    b.close()
+
+
 def test_batch_members_match_oracle(cuda_device):
     """The members' initial states are the oracle's (to one FP32 ulp); one
     batched cycle from those states matches the oracle's cycle per member."""
