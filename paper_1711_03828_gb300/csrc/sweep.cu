@@ -211,22 +211,33 @@ __global__ void __launch_bounds__(256) sweep_uniform_kernel(const SweepArgs p) {
   if (lane == 0 && my_acc) atomicAdd(p.acc, (unsigned long long)my_acc);
 }
 
-// Even N <= 64: the paired tile body of pair_body.cuh over one system.  Each
-// block owns a contiguous range of tiles (spatially ordered chains), walked by
-// its warps in step, so field values repeat in L1; the next tile's positions
-// are loaded while the current one is processed.  IDX is the index type:
-// 32-bit when M < 2^32 (Philox counter word 1 = 0).
+// Even N <= 64: the paired tile body of pair_body.cuh over one system.  One
+// block of 24 warps per SM owns a contiguous range of tiles (spatially
+// ordered chains); its warps take the range's tiles in order from a
+// shared-memory counter, so they work on neighbouring tiles (field values
+// repeat in L1) and all finish within a tile of each other.  With three
+// blocks of a third of the range each, the warp scheduler's preference for
+// the oldest warps finished the first block well before the third, and the
+// SM ran its last sixth at a third or two thirds of its warps.  The next
+// tile's positions are loaded while the current one is processed.  IDX is the
+// index type: 32-bit when M < 2^32 (Philox counter word 1 = 0).
 // MIXED: a mixture of linear architectures (the type sequence of each chain
 // is read per tile); otherwise every chain is the diblock of N_A A particles.
 template <typename WT, typename IDX, bool MIXED>
-__global__ void __launch_bounds__(256, 3) sweep_pair_kernel(const SweepArgs p) {
+__global__ void __launch_bounds__(768, 1) sweep_pair_kernel(const SweepArgs p) {
+  __shared__ uint32_t s_next;
   const int lane = threadIdx.x & 31;
   const uint32_t n_tiles_all = (uint32_t)p.n_tiles;
   const uint32_t chunk = (n_tiles_all + gridDim.x - 1) / gridDim.x;
   const uint32_t t_begin = blockIdx.x * chunk;
   const uint32_t t_end = min(t_begin + chunk, n_tiles_all);
-  const uint32_t warp0 = t_begin + (threadIdx.x >> 5);
-  const uint32_t nwarps = blockDim.x >> 5;
+  if (threadIdx.x == 0) s_next = 0u;
+  __syncthreads();
+  auto claim = [&]() -> uint32_t {
+    uint32_t t = 0u;
+    if (lane == 0) t = atomicAdd(&s_next, 1u);
+    return t_begin + __shfl_sync(FULL, t, 0);
+  };
   const unsigned long long s64 = *p.d_sweep;
   const uint32_t sweep = (uint32_t)s64;
   uint32_t* __restrict__ nacc = ((s64 + 1ull) & 1ull) ? p.n1 : p.n0;
@@ -247,13 +258,15 @@ __global__ void __launch_bounds__(256, 3) sweep_pair_kernel(const SweepArgs p) {
       pz = __ldcs(reinterpret_cast<const float2*>(p.z + b));
     }
   };
-  load_pos(warp0);
+  uint32_t tile = claim();
+  load_pos(tile);
   unsigned my_acc = 0;
-  for (uint32_t tile = warp0; tile < t_end; tile += nwarps) {
+  while (tile < t_end) {
     const bool valid = lane_ok(tile);
     const IDX base = (IDX)tile * TN + L.li0;
     const float x0 = px.x, x1 = px.y, y0 = py.x, y1 = py.y, z0 = pz.x, z1 = pz.y;
-    load_pos(tile + nwarps);
+    const uint32_t next_tile = claim();
+    load_pos(next_tile);
     PairLane<WT> Lt = L;
     if (MIXED) {
       const uint64_t chain = (uint64_t)tile * p.G + L.lane_chain;
@@ -273,6 +286,7 @@ __global__ void __launch_bounds__(256, 3) sweep_pair_kernel(const SweepArgs p) {
       my_acc += pair_tile<WT, IDX, true, false>(p.g, p.g, Lt, p.x, p.y, p.z, nacc, base, cbase, valid,
                                                 sweep, ctr3, p.set_order_random, p.a, p.K_b, x0, x1,
                                                 y0, y1, z0, z1);
+    tile = next_tile;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) my_acc += __shfl_xor_sync(FULL, my_acc, o);
@@ -334,7 +348,7 @@ SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dty
   s.vec = ((uint64_t)s.G * N) % align == 0;
   s.pair = (s.Q == 1) && (N % 2 == 0);
   s.big = n_chains * N >= (1ull << 32) || s.n_tiles >= (1ull << 31);
-  s.block = 256;
+  s.block = (move == 0 && s.pair) ? 768 : 256;   // the paired uniform kernel: one block per SM
   const void* fn = sweep_kernel_ptr(s.Q, s.vec, grid_dtype, s.pair, s.big, s.move, false);
   if (move == 2 && s.pair && !s.big && !learned_fp32) {
     s.learned_tc = true;
