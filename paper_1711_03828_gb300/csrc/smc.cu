@@ -324,13 +324,23 @@ __device__ __forceinline__ bool smc_move(const SweepArgs& p, const float4* tab, 
   return acc;
 }
 
-__global__ void __launch_bounds__(256, 3) sweep_smc_pair_kernel(const SweepArgs p) {
+// Paired smart Monte Carlo sweep (even N <= 64).  One block of 24 warps per
+// SM owns a contiguous range of tiles, which its warps take in order from a
+// shared-memory counter, so all of them finish within a tile of each other.
+__global__ void __launch_bounds__(768, 1) sweep_smc_pair_kernel(const SweepArgs p) {
+  __shared__ uint32_t s_next;
   const int lane = threadIdx.x & 31;
   const uint32_t n_tiles_all = (uint32_t)p.n_tiles;
   const uint32_t chunk = (n_tiles_all + gridDim.x - 1) / gridDim.x;
   const uint32_t t_begin = blockIdx.x * chunk;
   const uint32_t t_end = min(t_begin + chunk, n_tiles_all);
-  const uint32_t nwarps = blockDim.x >> 5;
+  if (threadIdx.x == 0) s_next = 0u;
+  __syncthreads();
+  auto claim = [&]() -> uint32_t {
+    uint32_t t = 0u;
+    if (lane == 0) t = atomicAdd(&s_next, 1u);
+    return t_begin + __shfl_sync(FULL, t, 0);
+  };
   const unsigned long long s64 = *p.d_sweep;
   const uint32_t sweep = (uint32_t)s64;
   uint32_t* __restrict__ nacc = ((s64 + 1ull) & 1ull) ? p.n1 : p.n0;
@@ -351,8 +361,9 @@ __global__ void __launch_bounds__(256, 3) sweep_smc_pair_kernel(const SweepArgs 
       nz = __ldcs(reinterpret_cast<const float2*>(p.z + b));
     }
   };
-  load_pos(t_begin + (threadIdx.x >> 5));
-  for (uint32_t tile = t_begin + (threadIdx.x >> 5); tile < t_end; tile += nwarps) {
+  uint32_t tile = claim();
+  load_pos(tile);
+  while (tile < t_end) {
     const bool valid = tile < (uint32_t)p.full_tiles || L.li0 < p.last_rows;
     const uint32_t base = tile * TN + L.li0;
     float2 px = make_float2(0.f, 0.f), py = px, pz = px;
@@ -361,7 +372,8 @@ __global__ void __launch_bounds__(256, 3) sweep_smc_pair_kernel(const SweepArgs 
       py = ny;
       pz = nz;
     }
-    load_pos(tile + nwarps);
+    const uint32_t next_tile = claim();
+    load_pos(next_tile);
     uint32_t w0, w1;
     const uint32_t cbase = base + (uint32_t)p.g.id_base;
     const SmcSlot s0 = smc_slot(p.g, tab0, px.x, py.x, pz.x, cbase, sweep, ctr3a, valid, &w0);
@@ -397,6 +409,7 @@ __global__ void __launch_bounds__(256, 3) sweep_smc_pair_kernel(const SweepArgs 
       atomicAdd(nacc + A.c, same ? vA + vB : vA);
       if (!same) atomicAdd(nacc + B.c, vB);
     }
+    tile = next_tile;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) my_acc += __shfl_xor_sync(FULL, my_acc, o);

@@ -348,7 +348,8 @@ SweepShape sweep_shape(uint64_t n_chains, uint32_t N, int sm_count, int grid_dty
   s.vec = ((uint64_t)s.G * N) % align == 0;
   s.pair = (s.Q == 1) && (N % 2 == 0);
   s.big = n_chains * N >= (1ull << 32) || s.n_tiles >= (1ull << 31);
-  s.block = (move == 0 && s.pair) ? 768 : 256;   // the paired uniform kernel: one block per SM
+  // the paired uniform and smart Monte Carlo kernels: one block of 24 warps per SM
+  s.block = ((move == 0 && s.pair) || (move == 1 && s.pair && !s.big)) ? 768 : 256;
   const void* fn = sweep_kernel_ptr(s.Q, s.vec, grid_dtype, s.pair, s.big, s.move, false);
   if (move == 2 && s.pair && !s.big && !learned_fp32) {
     s.learned_tc = true;
