@@ -555,6 +555,23 @@ soma_status soma_batch_system(soma_batch_t* b, uint32_t i, soma_t** out);
  * its parallel regions the same way, by timing candidates (Sec. 3.2.2). */
 soma_status soma_batch_autotune(soma_batch_t* b, uint32_t cycles_per_candidate,
                                 soma_tune_entry* table, uint32_t table_len, uint32_t* n_written);
+/* The work items of the batched sweep, computed on the host only (no CUDA
+ * call): what soma_batch_* launches for members of member_tiles[k] warp tiles
+ * (ceil(n_chains / floor(64 / N)) for member k) on a grid of `grid` blocks.
+ * Block j takes items j, j + grid, j + 2 grid, ...
+ *   item_tiles > 0: runs of at most item_tiles tiles of each member in turn
+ *                   (grid unused);
+ *   item_tiles = 0: block j's items cover tiles [T j / grid, T (j+1) / grid)
+ *                   of the members' concatenation (T tiles in all), cut at
+ *                   member boundaries; piece r of block j is item r * grid + j
+ *                   and blocks with fewer pieces get empty items.
+ * items:    host array of 3 * capacity words (member, first tile, end tile) or
+ *           NULL to ask for the count only; *n_items receives the count.
+ * SOMA_EINVAL for NULL member_tiles / n_items, n_members outside
+ * 1..SOMA_BATCH_MAX, item_tiles < 0, grid outside 1..2^20 with item_tiles = 0,
+ * or capacity below the count (nothing written). */
+soma_status soma_batch_plan(const uint32_t* member_tiles, uint32_t n_members, uint32_t grid,
+                            int32_t item_tiles, uint32_t* items, size_t capacity, size_t* n_items);
 /* Use a given launch shape (e.g. one tuned earlier; ms_per_cycle ignored).
  * SOMA_EINVAL unless block is a multiple of 32 the kernel accepts,
  * blocks_per_sm of that block fit on one SM and item_tiles >= 0.  Results do

@@ -385,6 +385,19 @@ class System:
                 "mean_alpha_last": lg.mean_alpha_last, "steps": lg.steps_done}
 
 
+def batch_plan(member_tiles, grid, item_tiles=0):
+    """The batched sweep's work items (``soma_batch_plan``, host only): rows
+    (member, first tile, end tile); block j takes rows j, j + grid, ..."""
+    import numpy as np
+    nt = np.ascontiguousarray(member_tiles, dtype=np.uint32)
+    n = ctypes.c_size_t()
+    _abi.soma_batch_plan(nt.ctypes.data, len(nt), int(grid), int(item_tiles), None, 0, ctypes.byref(n))
+    out = np.zeros((n.value, 3), dtype=np.uint32)
+    _abi.soma_batch_plan(nt.ctypes.data, len(nt), int(grid), int(item_tiles), out.ctypes.data,
+                         n.value, ctypes.byref(n))
+    return out
+
+
 class Batch:
     """Many independent systems advanced by one sweep launch and one field
     launch per cycle (``soma_batch_*``)."""

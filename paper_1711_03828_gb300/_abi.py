@@ -151,6 +151,8 @@ _SIGS = {
     "soma_batch_system": ([_P, _c.c_uint32, _c.POINTER(_P)], _c.c_int),
     "soma_batch_autotune": ([_P, _c.c_uint32, _c.POINTER(SomaTuneEntry), _c.c_uint32,
                              _c.POINTER(_c.c_uint32)], _c.c_int),
+    "soma_batch_plan": ([_c.c_void_p, _c.c_uint32, _c.c_uint32, _c.c_int32, _c.c_void_p, _c.c_size_t,
+                         _c.POINTER(_c.c_size_t)], _c.c_int),
     "soma_batch_set_shape": ([_P, _c.POINTER(SomaTuneEntry)], _c.c_int),
     "soma_batch_get_shape": ([_P, _c.POINTER(SomaTuneEntry)], _c.c_int),
     "soma_batch_set_timing": ([_P, _c.c_int], _c.c_int),
@@ -234,6 +236,7 @@ soma_batch_sweep = _wrap("soma_batch_sweep")
 soma_batch_sync = _wrap("soma_batch_sync")
 soma_batch_system = _wrap("soma_batch_system")
 soma_batch_autotune = _wrap("soma_batch_autotune")
+soma_batch_plan = _wrap("soma_batch_plan")
 soma_batch_set_shape = _wrap("soma_batch_set_shape")
 soma_batch_get_shape = _wrap("soma_batch_get_shape")
 soma_batch_set_timing = _wrap("soma_batch_set_timing")

@@ -1543,42 +1543,49 @@ void batch_release(soma_batch_t* b) {
   delete b;
 }
 
-soma_status batch_items(soma_batch_t* b, int item_tiles) {
+// The work items of a batch whose member k has nt[k] tiles, for a sweep
+// launch of grid blocks (block j takes items j, j + grid, j + 2 grid, ...).
+// item_tiles > 0: runs of item_tiles tiles of each member in turn.
+// item_tiles == 0: one contiguous range of the members' concatenated tiles per
+// block, equal to within a tile, cut at member boundaries into pieces; piece
+// r of block j sits at item r * grid + j, and blocks with fewer pieces get
+// empty items.
+std::vector<BatchItem> batch_plan(const std::vector<uint32_t>& nt, uint32_t grid, int item_tiles) {
   std::vector<BatchItem> items;
   if (item_tiles > 0) {
-    for (uint32_t k = 0; k < b->sys.size(); ++k) {
-      const uint32_t nt = (uint32_t)b->sys[k]->shape.n_tiles;
-      for (uint32_t t0 = 0; t0 < nt; t0 += (uint32_t)item_tiles)
-        items.push_back({k, t0, std::min(nt, t0 + (uint32_t)item_tiles)});
-    }
-  } else {
-    // One contiguous range of the members' concatenated tiles per block,
-    // equal to within a tile, cut at member boundaries into pieces; block j
-    // takes items j, j + grid, j + 2 grid, ... so piece r of block j sits at
-    // r * grid + j, and blocks with fewer pieces get empty ones.
-    const uint32_t grid = (uint32_t)(b->sm_count * b->blocks_per_sm);
-    std::vector<uint64_t> begin(b->sys.size() + 1, 0);
-    for (uint32_t k = 0; k < b->sys.size(); ++k)
-      begin[k + 1] = begin[k] + (uint64_t)b->sys[k]->shape.n_tiles;
-    const uint64_t total = begin.back();
-    std::vector<std::vector<BatchItem>> per(grid);
-    size_t rounds = 1;
-    uint32_t k = 0;
-    for (uint32_t j = 0; j < grid; ++j) {
-      uint64_t g0 = total * j / grid;
-      const uint64_t g1 = total * (j + 1) / grid;
-      while (g0 < g1) {
-        while (begin[k + 1] <= g0) ++k;
-        const uint64_t e = std::min(g1, begin[k + 1]);
-        per[j].push_back({k, (uint32_t)(g0 - begin[k]), (uint32_t)(e - begin[k])});
-        g0 = e;
-      }
-      rounds = std::max(rounds, per[j].size());
-    }
-    items.assign(rounds * grid, BatchItem{0u, 0u, 0u});
-    for (uint32_t j = 0; j < grid; ++j)
-      for (size_t r = 0; r < per[j].size(); ++r) items[r * grid + j] = per[j][r];
+    for (uint32_t k = 0; k < nt.size(); ++k)
+      for (uint32_t t0 = 0; t0 < nt[k]; t0 += (uint32_t)item_tiles)
+        items.push_back({k, t0, std::min(nt[k], t0 + (uint32_t)item_tiles)});
+    return items;
   }
+  std::vector<uint64_t> begin(nt.size() + 1, 0);
+  for (uint32_t k = 0; k < nt.size(); ++k) begin[k + 1] = begin[k] + nt[k];
+  const uint64_t total = begin.back();
+  std::vector<std::vector<BatchItem>> per(grid);
+  size_t rounds = 1;
+  uint32_t k = 0;
+  for (uint32_t j = 0; j < grid; ++j) {
+    uint64_t g0 = total * j / grid;
+    const uint64_t g1 = total * (j + 1) / grid;
+    while (g0 < g1) {
+      while (begin[k + 1] <= g0) ++k;
+      const uint64_t e = std::min(g1, begin[k + 1]);
+      per[j].push_back({k, (uint32_t)(g0 - begin[k]), (uint32_t)(e - begin[k])});
+      g0 = e;
+    }
+    rounds = std::max(rounds, per[j].size());
+  }
+  items.assign(rounds * grid, BatchItem{0u, 0u, 0u});
+  for (uint32_t j = 0; j < grid; ++j)
+    for (size_t r = 0; r < per[j].size(); ++r) items[r * grid + j] = per[j][r];
+  return items;
+}
+
+soma_status batch_items(soma_batch_t* b, int item_tiles) {
+  std::vector<uint32_t> nt(b->sys.size());
+  for (size_t k = 0; k < b->sys.size(); ++k) nt[k] = (uint32_t)b->sys[k]->shape.n_tiles;
+  const std::vector<BatchItem> items =
+      batch_plan(nt, (uint32_t)(b->sm_count * b->blocks_per_sm), item_tiles);
   if (items.size() > b->items_cap) {
     cudaFree(b->d_items);
     b->d_items = nullptr;
@@ -1881,6 +1888,28 @@ soma_status soma_batch_autotune(soma_batch_t* b, uint32_t cycles_per_candidate,
   if (table)
     for (uint32_t k = 0; k < table_len && k < res.size(); ++k) table[k] = res[k];
   if (n_written) *n_written = (uint32_t)res.size();
+  return SOMA_OK;
+}
+
+soma_status soma_batch_plan(const uint32_t* member_tiles, uint32_t n_members, uint32_t grid,
+                            int32_t item_tiles, uint32_t* items, size_t capacity, size_t* n_items) {
+  if (!member_tiles || !n_items) return fail(SOMA_EINVAL, "NULL argument");
+  if (n_members < 1 || n_members > SOMA_BATCH_MAX)
+    return fail(SOMA_EINVAL, "n_members=%u outside 1..%d", n_members, SOMA_BATCH_MAX);
+  if (item_tiles < 0) return fail(SOMA_EINVAL, "item_tiles=%d < 0", (int)item_tiles);
+  if (item_tiles == 0 && (grid < 1 || grid > (1u << 20)))
+    return fail(SOMA_EINVAL, "grid=%u outside 1..2^20", grid);
+  std::vector<uint32_t> nt(member_tiles, member_tiles + n_members);
+  const std::vector<BatchItem> plan = batch_plan(nt, grid, item_tiles);
+  *n_items = plan.size();
+  if (!items) return SOMA_OK;
+  if (capacity < plan.size())
+    return fail(SOMA_EINVAL, "capacity %zu < %zu items", capacity, plan.size());
+  for (size_t i = 0; i < plan.size(); ++i) {
+    items[3 * i] = plan[i].sys;
+    items[3 * i + 1] = plan[i].t0;
+    items[3 * i + 2] = plan[i].t1;
+  }
   return SOMA_OK;
 }
 
